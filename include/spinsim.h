@@ -1,0 +1,204 @@
+/*
+ * spinsim.h -- C ABI of the GB300-native spin-half / spin-one CF4 integrator.
+ *
+ * The library integrates the time-dependent Schroedinger equation
+ * i dpsi/dt = H(t) psi (hbar = 1) for spin-half (N = 2) and spin-one (N = 3)
+ * systems, H(t) = w_x J_x + w_y J_y + w_z J_z (+ w_q Q for spin-one), as in
+ * Tritt et al., arXiv 2204.05586:
+ *   - each output interval [t_{k-1}, t_k] gets its own time-evolution operator
+ *     U_k built from L integration steps of the commutator-free fourth-order
+ *     Magnus method CF4 (Sec. 1.2.2, Eqs. cf4_sample_1/2, cf4_implementation),
+ *   - spin-half exponentials in closed SU(2) form, spin-one exponentials by
+ *     Lie-Trotter with 2^tau residual squarings (Sec. 1.2.3, Eq. lie_trotter_4),
+ *   - optionally inside a per-interval rotating frame (Sec. 1.2.5,
+ *     Eq. exit_rotating_frame),
+ *   - the U_k are chained psi_k = U_k psi_{k-1} (Sec. 1.2.4,
+ *     Eq. integration_compilation) by a parallel ordered prefix product in FP64,
+ *     and psi_k plus <J_x, J_y, J_z>_k (Sec. 1.2.1) are written for every k.
+ *
+ * Conventions used throughout:
+ *   - basis order m = +j ... -j; J = sigma/2 for spin-half; Q = diag(1,-2,1)/3.
+ *   - complex numbers are stored as interleaved (re, im) doubles.
+ *   - K = (t_end - t_start)/dt_out output samples, sample k at
+ *     t_k = t_start + k dt_out, psi_0 = psi0 (the initial state), no sample at
+ *     t_end; L = dt_out/dt integration steps per sample, delta_t = dt_out / L.
+ *   - U_0 is defined as the identity.
+ *
+ * Threading: a handle may be used by one host thread at a time.  All work is
+ * enqueued on the CUDA stream passed in (NULL = the legacy default stream);
+ * results and the per-request status are final once that stream is
+ * synchronised.  No call aborts or exits the process; errors are returned.
+ */
+#ifndef SPINSIM_H
+#define SPINSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPINSIM_ABI_VERSION 1
+#define SPINSIM_MAX_PULSES 4
+
+/* Status codes (negative = error).  A call returns the first error it meets;
+ * spinsim_result.status carries each request's own status. */
+typedef enum {
+    SPINSIM_OK = 0,
+    SPINSIM_PENDING = 1,          /* spinsim_poll: the request has not finished yet          */
+    SPINSIM_E_ARG = -1,           /* NULL pointer, unknown enum value, non-positive step...  */
+    SPINSIM_E_STEP_RATIO = -2,    /* (t_end-t_start)/dt_out or dt_out/dt not an integer (1e-9) */
+    SPINSIM_E_NORM = -3,          /* | ||psi0|| - 1 | > 1e-10 (the state must be normalised)  */
+    SPINSIM_E_NOMEM = -4,         /* scratch over the handle's budget, or cudaMalloc failed   */
+    SPINSIM_E_CUDA = -5,          /* a CUDA runtime call or kernel launch failed              */
+    SPINSIM_E_TIMEOUT = -6,       /* spinsim_poll: waited wait_us without completion          */
+    SPINSIM_E_CAPACITY = -7,      /* result capacity smaller than the request's K             */
+    SPINSIM_E_UNSUPPORTED = -8    /* valid but not provided (e.g. graphs while capturing)     */
+} spinsim_status;
+
+/* spinsim_result.flags bits (warnings; the request still ran). */
+#define SPINSIM_WARN_MAGNUS 1     /* an upper bound of ||H||_2 delta_t reaches the Magnus
+                                     convergence radius xi = 1.0868687 (Sec. 1.2.2)       */
+
+typedef enum {
+    SPINSIM_METHOD_CF4 = 0,       /* Sec. 1.2.2 (default)                                    */
+    SPINSIM_METHOD_MIDPOINT = 1,  /* midpoint Euler sampling, Sec. 1.3.1                     */
+    SPINSIM_METHOD_HEUN = 2       /* Heun-Euler sampling, Sec. 1.3.1                         */
+} spinsim_method;
+
+typedef enum {
+    SPINSIM_PREC_FP64 = 0,        /* every step in FP64                                      */
+    SPINSIM_PREC_FP32_BULK = 1    /* field, exponentials and step products in FP32; U_k
+                                     re-unitarised, frame exit and chain in FP64           */
+} spinsim_precision;
+
+/* Handle configuration.  Zero-initialise, or call spinsim_config_default. */
+typedef struct {
+    int32_t method;               /* spinsim_method                                          */
+    int32_t precision;            /* spinsim_precision                                       */
+    int32_t rotating_frame;       /* 1: per-interval rotating frame (default), 0: lab frame  */
+    int32_t trotter_squares;      /* tau, n = 2^tau Lie-Trotter factors (spin-one); -1 gives
+                                     the precision's default (24 for FP64, Sec. 1.2.3;
+                                     SPINSIM_FP32_DEFAULT_TAU for FP32-bulk); 0..40         */
+    int32_t lanes_per_sample;     /* 0 = autotune; else 1, 2 or 4 threads share one U_k.
+                                     Results do not depend on it (fixed reduction tree).   */
+    int32_t threads_per_block;    /* 0 = autotune; else 64, 128 or 256                        */
+    int32_t use_graphs;           /* 1: replay repeated identical batch shapes as a CUDA graph */
+    int32_t device;               /* CUDA device ordinal                                      */
+    int64_t mem_budget;           /* bytes of device scratch the handle may hold; 0 = 90% of
+                                     the free memory at spinsim_create                     */
+} spinsim_config;
+
+#define SPINSIM_FP32_DEFAULT_TAU 4
+
+/* The fixed parameterised field family (Hz, seconds, radians):
+ *   w_x(t) = 2 pi drive_x_hz cos(2 pi drive_hz t + drive_phase)
+ *   w_y(t) = 2 pi drive_y_hz sin(2 pi drive_hz t + drive_phase)
+ *   w_z(t) = 2 pi (bias_hz + sum_p pulse_amp_hz[p] exp(-(t - pulse_centre_s[p])^2
+ *                                                       / (2 pulse_width_s[p]^2)))
+ *   w_q(t) = 2 pi quad_hz                       (spin-one only; ignored for spin-half)
+ * A linearly polarised drive "2 R cos(2 pi f t)" is drive_x_hz = 2R, drive_y_hz = 0;
+ * a circularly polarised one has drive_x_hz = drive_y_hz.  The detuning of the
+ * drive is drive_hz - bias_hz. */
+typedef struct {
+    double bias_hz;
+    double drive_x_hz;
+    double drive_y_hz;
+    double drive_hz;
+    double drive_phase;
+    double quad_hz;
+    int32_t n_pulses;             /* 0..SPINSIM_MAX_PULSES                                   */
+    int32_t reserved;
+    double pulse_amp_hz[SPINSIM_MAX_PULSES];
+    double pulse_centre_s[SPINSIM_MAX_PULSES];
+    double pulse_width_s[SPINSIM_MAX_PULSES];   /* standard deviation, > 0 when used       */
+} spinsim_field;
+
+/* One simulation (Sec. 1.2.4 problem statement). */
+typedef struct {
+    int32_t spin_x2;              /* 1 = spin-half (N = 2), 2 = spin-one (N = 3)             */
+    int32_t reserved;
+    spinsim_field field;
+    double t_start, t_end;        /* seconds, t_end >= t_start                               */
+    double dt;                    /* integration step delta_t (> 0)                          */
+    double dt_out;                /* output step Delta_t (> 0), an integer multiple of dt    */
+    double psi0[6];               /* initial state, N complex (re, im), normalised           */
+} spinsim_request;
+
+/* Caller-owned output buffers of one request.  Each pointer may be device
+ * memory (written in place) or host memory (the library stages it through
+ * device scratch and copies back on the stream).  The library never frees them. */
+typedef struct {
+    double* states;               /* [capacity][N] complex psi_k, required                   */
+    double* spin;                 /* [capacity][3] <J_x>, <J_y>, <J_z>; NULL = not written   */
+    double* ops;                  /* [capacity][N][N] complex U_k (row-major); NULL = not written */
+    int64_t capacity;             /* samples the buffers can hold (>= K)                     */
+    int64_t n_samples;            /* out: K                                                  */
+    int32_t status;               /* out: this request's spinsim_status                      */
+    int32_t flags;                /* out: SPINSIM_WARN_* bits                                */
+} spinsim_result;
+
+typedef struct spinsim_s* spinsim_handle;
+
+/* Fill *cfg with defaults: CF4, FP32-bulk, rotating frame on, default tau,
+ * autotuned launch shape, graphs off, device 0, budget 0 (90% of free). */
+int spinsim_config_default(spinsim_config* cfg);
+
+/* Create a handle on cfg->device.  The handle owns device scratch (operator
+ * buffer, chain aggregates, parameter tables), pinned staging memory, the
+ * autotuner's cache and the serving queue.  Returns SPINSIM_E_ARG for a bad
+ * configuration, SPINSIM_E_CUDA when the device cannot be used. */
+int spinsim_create(const spinsim_config* cfg, spinsim_handle* out);
+
+/* Release everything the handle owns (after synchronising its work). */
+void spinsim_destroy(spinsim_handle h);
+
+/* K and L of a request, with the same validation spinsim_simulate applies. */
+int spinsim_counts(const spinsim_request* req, int64_t* K, int64_t* L);
+
+/* Bytes of device scratch spinsim_simulate needs for these n requests
+ * (-SPINSIM_E_* on invalid input). */
+int64_t spinsim_footprint(spinsim_handle h, const spinsim_request* reqs, int64_t n);
+
+/* Simulate n independent requests as one batch on `stream` (a cudaStream_t).
+ * Every request is validated first; requests that fail validation get their
+ * status set and are skipped, the others run.  Returns SPINSIM_OK when every
+ * request is valid and all launches were enqueued, else the first error.
+ * res[i].states/spin/ops receive psi_k, <J>_k and U_k for k = 0..K-1. */
+int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_result* res, int64_t n,
+                     void* stream);
+
+/* Continuous-batching serving interface (Sec. 1.2.7's "many simulations from
+ * one compiled simulator", served as they arrive).  spinsim_submit copies the
+ * request, admits it when the handle's device-memory budget allows, and
+ * launches pending requests as a batch on a free internal stream while
+ * earlier batches are still running.  The result buffers must stay valid
+ * until spinsim_poll reports completion.  *ticket identifies the request. */
+int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result* res, int64_t* ticket);
+
+/* Drive the serving queue and report a ticket: SPINSIM_OK when its results
+ * are complete (res->status holds the request status), SPINSIM_PENDING when
+ * not yet (wait_us = 0), SPINSIM_E_TIMEOUT when wait_us > 0 elapsed first, or
+ * SPINSIM_E_ARG for an unknown ticket.  Completed tickets are forgotten. */
+int spinsim_poll(spinsim_handle h, int64_t ticket, int32_t wait_us);
+
+/* Launch shape the last spinsim_simulate call used for its integration
+ * kernel, and how many kernels it launched (for benchmarking). */
+typedef struct {
+    int32_t lanes_per_sample;
+    int32_t threads_per_block;
+    int32_t grid_blocks;
+    int32_t kernels_launched;
+    int32_t trotter_squares;
+    int32_t graph_replayed;
+} spinsim_launch_info;
+int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info);
+
+/* Static description of a status code. */
+const char* spinsim_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPINSIM_H */

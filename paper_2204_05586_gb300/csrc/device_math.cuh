@@ -1,0 +1,618 @@
+// device_math.cuh -- per-thread arithmetic of the integrator (registers only).
+//
+// Everything is templated on the bulk arithmetic type R (float for the
+// FP32-bulk path, double for the FP64 path).  Operators close to the identity
+// are carried as residuals X = U - I throughout (Sec. 1.2.3), so that rounding
+// acts on the small part only.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+// Device functions that are also compiled for the host by the CPU test harness.
+#ifndef SPINSIM_HD
+#define SPINSIM_HD __host__ __device__ __forceinline__
+#endif
+
+namespace spinsim {
+
+template <typename R>
+struct cx {
+    R r, i;
+};
+
+template <typename R>
+SPINSIM_HD cx<R> cmk(R r, R i) { cx<R> c; c.r = r; c.i = i; return c; }
+template <typename R>
+SPINSIM_HD cx<R> cadd(cx<R> a, cx<R> b) { return cmk(a.r + b.r, a.i + b.i); }
+template <typename R>
+SPINSIM_HD cx<R> csub(cx<R> a, cx<R> b) { return cmk(a.r - b.r, a.i - b.i); }
+template <typename R>
+SPINSIM_HD cx<R> cscale(cx<R> a, R s) { return cmk(a.r * s, a.i * s); }
+template <typename R>
+SPINSIM_HD cx<R> cconj(cx<R> a) { return cmk(a.r, -a.i); }
+template <typename R>
+SPINSIM_HD cx<R> cmul(cx<R> a, cx<R> b)
+{
+    return cmk(fma(a.r, b.r, -a.i * b.i), fma(a.r, b.i, a.i * b.r));
+}
+// c + a b
+template <typename R>
+SPINSIM_HD cx<R> cfma(cx<R> a, cx<R> b, cx<R> c)
+{
+    return cmk(fma(a.r, b.r, fma(-a.i, b.i, c.r)), fma(a.r, b.i, fma(a.i, b.r, c.i)));
+}
+// c + conj(a) b
+template <typename R>
+SPINSIM_HD cx<R> cfma_conj(cx<R> a, cx<R> b, cx<R> c)
+{
+    return cmk(fma(a.r, b.r, fma(a.i, b.i, c.r)), fma(a.r, b.i, fma(-a.i, b.r, c.i)));
+}
+
+constexpr double kTwoPi = 6.283185307179586476925287;
+constexpr double kInvSqrt2 = 0.7071067811865475244008444;
+constexpr double kSqrt2 = 1.414213562373095048801689;
+
+// sin and cos of a small angle by their Taylor series (x - x^3/3! + ...,
+// 1 - x^2/2! + ...), which for |x| <= 1/16 leaves a truncation error below
+// 1e-19 relative with the terms used; larger angles use the libdevice call.
+template <typename R>
+SPINSIM_HD void small_sincos(R x, R& s, R& c)
+{
+    if (fabs(x) <= R(0.0625)) {
+        R x2 = x * x;
+        s = x * (R(1) - x2 * (R(1.0 / 6) - x2 * (R(1.0 / 120) - x2 * (R(1.0 / 5040) - x2 * R(1.0 / 362880)))));
+        c = R(1) - x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * (R(1.0 / 720) - x2 * (R(1.0 / 40320) - x2 * R(1.0 / 3628800)))));
+    } else {
+        sincos(x, &s, &c);
+    }
+}
+
+// sin(x) - x and cos(x) - 1 without cancellation: Taylor series for
+// |x| <= 1/16 (truncation below 1e-19 relative), else from sincos with
+// cos(x) - 1 = -2 sin^2(x/2).
+template <typename R>
+SPINSIM_HD void small_sincos_m(R x, R& sm, R& cm)
+{
+    if (fabs(x) <= R(0.0625)) {
+        R x2 = x * x;
+        sm = -x * x2 * (R(1.0 / 6) - x2 * (R(1.0 / 120) - x2 * (R(1.0 / 5040) - x2 * R(1.0 / 362880))));
+        cm = -x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * (R(1.0 / 720) - x2 * (R(1.0 / 40320) - x2 * R(1.0 / 3628800)))));
+    } else {
+        R s, c, h;
+        sincos(x, &s, &c);
+        h = sin(R(0.5) * x);
+        sm = s - x;
+        cm = R(-2) * h * h;
+    }
+}
+
+// -------------------------------------------------------------------------
+// Per-sample context: the field family inside interval k, reduced to values
+// in the bulk type R.  Large phases (the drive phase at t_{k-1}, the pulse
+// offsets) are reduced in FP64 once per sample.
+//
+// FP32 design rule: over 10^7 steps the accumulated rotation angles reach
+// hundreds of radians, so any rounding error that is identical in every step
+// (a constant rounded once, a fixed factor such as 1/3 or 1/sqrt2, a biased
+// approximation) adds up coherently and dominates.  Therefore constants that
+// multiply step data are carried as FP32 (hi, lo) pairs, e^{i beta} comes
+// from FP64, square roots and quotients are the correctly rounded ones, and
+// the one constant that cannot be split (q/3, see expm_one_res) is corrected
+// in FP64 at the end of the sample.  What remains are roundings of varying
+// data, which are unbiased and grow only like a random walk.
+// -------------------------------------------------------------------------
+template <typename R>
+struct SampleCtx {
+    R ebr, ebi;                     // e^{i beta}, beta = drive phase at t_{k-1}
+    R co, counter;                  // drive frequencies seen in the frame: w_d - w_r, w_d + w_r
+    R Ph[4], Pl[4];                 // (hi, lo) of P[0..3]
+    R za, zb, zbias;
+    R qd3;
+    R dt, c1, c2;
+    R amp[kMaxPulses], u0[kMaxPulses], invw[kMaxPulses], ghat[kMaxPulses];
+    int np;
+    bool counter_on;
+};
+
+template <typename R>
+SPINSIM_HD void split_hi_lo(double x, R& hi, R& lo)
+{
+    hi = (R)x;
+    lo = (R)(x - (double)hi);
+}
+
+// Fill the context of interval k (1 <= k < K) and the FP64 phasor
+// e^{-i w_r dt_out} used to leave the frame (Eq. exit_rotating_frame); for
+// spin-half the phasor is e^{-i w_r dt_out / 2}.
+//
+// With the frame on, w_r = 2 pi B + sum_p amp_p ghat_p where ghat_p is the
+// pulse shape at the interval midpoint rounded to R; the frame is an exact
+// change of variables for any constant w_r, and this one is exactly the value
+// the in-frame field subtracts, so leaving the frame undoes entering it.
+struct SampleExact {
+    double ph_re, ph_im;   // e^{-i w_r dt_out} (spin-one) or e^{-i w_r dt_out / 2} (spin-half)
+    double eb_re, eb_im;   // e^{i beta}
+    double dco, dct;       // w_d - w_r, w_d + w_r (rad/s)
+};
+
+template <typename R, int N>
+SPINSIM_HD void make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, SampleExact& x)
+{
+    const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;
+    double cyc = s.drive_hz * t_prev;
+    cyc -= floor(cyc);
+    double beta = kTwoPi * cyc + s.drive_phase;
+    beta -= kTwoPi * rint(beta * (1.0 / kTwoPi));
+    double sb, cb;
+    sincos(beta, &sb, &cb);
+    c.ebr = (R)cb;
+    c.ebi = (R)sb;
+    x.eb_re = cb;
+    x.eb_im = sb;
+#pragma unroll
+    for (int i = 0; i < 4; i++) split_hi_lo<R>(s.P[i], c.Ph[i], c.Pl[i]);
+    c.za = (R)s.za;
+    c.zb = (R)s.zb;
+    c.zbias = (R)s.zbias;
+    c.qd3 = (R)s.qd3;
+    c.dt = (R)s.dt;
+    c.c1 = (R)s.c1;
+    c.c2 = (R)s.c2;
+    c.np = s.n_pulses;
+    c.counter_on = s.counter_on != 0;
+    double gsum = 0.0;  // sum_p amp_p ghat_p, exact products of R values
+#pragma unroll
+    for (int p = 0; p < kMaxPulses; p++) {
+        c.amp[p] = R(0); c.u0[p] = R(0); c.invw[p] = R(0); c.ghat[p] = R(0);
+        if (p < c.np) {
+            c.amp[p] = (R)s.amp[p];
+            c.invw[p] = (R)s.inv_w[p];
+            c.u0[p] = (R)((t_prev - s.centre[p]) * s.inv_w[p]);
+            if (s.frame) {
+                R um = (R)((t_prev + 0.5 * s.dt_out - s.centre[p]) * s.inv_w[p]);
+                R g = exp(R(-0.5) * um * um);
+                c.ghat[p] = g;
+                gsum = fma((double)c.amp[p], (double)g, gsum);
+            }
+        }
+    }
+    if (s.frame) {
+        x.dco = s.w_co0 - gsum;
+        x.dct = s.w_counter0 + gsum;
+        // e^{-i (2 pi B + gsum) dt_out (x 1/2 for spin-half)}: host phasor times e^{-i d}
+        double d = gsum * s.dt_out * (N == 2 ? 0.5 : 1.0);
+        double sd, cd;
+        small_sincos<double>(d, sd, cd);
+        double br = N == 2 ? s.exit_half_re : s.exit_re;
+        double bi = N == 2 ? s.exit_half_im : s.exit_im;
+        x.ph_re = br * cd + bi * sd;       // (br + i bi)(cd - i sd)
+        x.ph_im = bi * cd - br * sd;
+    } else {
+        x.dco = s.w_co0;
+        x.dct = s.w_counter0;
+        x.ph_re = 1.0;
+        x.ph_im = 0.0;
+    }
+    c.co = (R)x.dco;
+    c.counter = (R)x.dct;
+}
+
+// sum_{l=0}^{L-1} (W1 e^{i th (l + c1)} + W2 e^{i th (l + c2)})
+//   = (W1 e^{i th (c1 + (L-1)/2)} + W2 e^{i th (c2 + (L-1)/2)}) sin(L th/2) / sin(th/2),
+// in FP64; th/2 is reduced by multiples of pi first so the ratio stays
+// well conditioned near th = 2 pi m.
+SPINSIM_HD cx<double> node_phasor_sum(double th, int64_t L, double W1, double c1, double W2, double c2)
+{
+    const double x = 0.5 * th;
+    const double m = rint(x * (1.0 / 3.14159265358979323846));
+    const double eps = fma(-m, 3.14159265358979323846, fma(-m, 1.2246467991473532e-16, x));
+    double ratio;
+    if (eps == 0.0) {
+        ratio = (double)L;
+    } else {
+        double sL, cL, s1, c1_;
+        small_sincos<double>((double)L * eps, sL, cL);
+        small_sincos<double>(eps, s1, c1_);
+        ratio = sL / s1;
+    }
+    // (-1)^(m (L - 1)) from sin(L x) / sin(x) with x = m pi + eps
+    const long long ml = (long long)m;
+    if ((ml & 1) && ((L - 1) & 1)) ratio = -ratio;
+    const double mid = 0.5 * (double)(L - 1);
+    double sa, ca, sb, cb;
+    small_sincos<double>(th * (c1 + mid), sa, ca);
+    small_sincos<double>(th * (c2 + mid), sb, cb);
+    return cmk((W1 * ca + W2 * cb) * ratio, (W1 * sa + W2 * sb) * ratio);
+}
+
+// Exact first-order transverse coefficients of U^r_k: the method's quadrature
+// sum over the sample of the in-frame drive,
+//   g_x + i g_y = dt [Om+ e^{i beta} S(w_d - w_r) + Om- conj(e^{i beta} S(w_d + w_r))],
+// S(w) = sum over steps and nodes of weight x e^{i w tau_node}.
+SPINSIM_HD void first_order_exact(const DevSim& s, const SampleExact& x, double& gx, double& gy)
+{
+    const cx<double> eb = cmk(x.eb_re, x.eb_im);
+    cx<double> co = cmul(eb, node_phasor_sum(x.dco * s.dt, s.L, s.W1, s.c1, s.W2, s.c2));
+    cx<double> g = cscale(co, s.om_plus);
+    if (s.om_minus != 0.0) {
+        cx<double> ct = cmul(eb, node_phasor_sum(x.dct * s.dt, s.L, s.W1, s.c1, s.W2, s.c2));
+        g = cadd(g, cscale(cconj(ct), s.om_minus));
+    }
+    gx = g.r * s.dt;
+    gy = g.i * s.dt;
+}
+
+// Field at offset tau from t_{k-1}, in the frame (Sec. 1.2.5): the phasors of
+// the co- and counter-rotating drive terms and the pulse part of w_z'.
+// With a = w_r tau and the drive phase A = beta + w_d tau, the rotation
+//   w_x' = w_x cos a + w_y sin a,  w_y' = -w_x sin a + w_y cos a
+// of w_x = Ax cos A, w_y = Ay sin A is, by product-to-sum identities,
+//   w_x' + i w_y' = Om+ e^{i (beta + (w_d - w_r) tau)} + Om- e^{-i (beta + (w_d + w_r) tau)}
+// with Om+- = (Ax +- Ay)/2.  The co-rotating phasor is e^{i beta} (FP64 per
+// sample) times a small rotation, so the slowly varying term never goes
+// through a large FP32 angle.
+template <typename R>
+struct NodeField {
+    cx<R> co, ct;   // e^{i (beta + (w_d - w_r) tau)}, e^{i (beta + (w_d + w_r) tau)}
+    R z;            // w_z' without the lab-frame bias
+};
+
+template <typename R>
+SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
+{
+    R s1, c1;
+    small_sincos(c.co * tau, s1, c1);
+    f.co = cmk(c.ebr * c1 - c.ebi * s1, fma(c.ebr, s1, c.ebi * c1));
+    if (c.counter_on) {
+        R s2, c2;
+        sincos(c.counter * tau, &s2, &c2);
+        f.ct = cmk(c.ebr * c2 - c.ebi * s2, fma(c.ebr, s2, c.ebi * c2));
+    } else {
+        f.ct = cmk(R(0), R(0));
+    }
+    R z = R(0);
+#pragma unroll
+    for (int p = 0; p < kMaxPulses; p++) {
+        if (p < c.np) {
+            R u = fma(tau, c.invw[p], c.u0[p]);
+            z = fma(c.amp[p], exp(R(-0.5) * u * u) - c.ghat[p], z);
+        }
+    }
+    f.z = z;
+}
+
+// sum_i (hi_i + lo_i) x_i with one final rounding of the lo part.
+template <typename R>
+SPINSIM_HD R dot4_hilo(const R* hi, const R* lo, R x0, R x1, R x2, R x3)
+{
+    R l = lo[0] * x0;
+    l = fma(lo[1], x1, l);
+    l = fma(lo[2], x2, l);
+    l = fma(lo[3], x3, l);
+    R h = fma(hi[0], x0, l);
+    h = fma(hi[1], x1, h);
+    h = fma(hi[2], x2, h);
+    h = fma(hi[3], x3, h);
+    return h;
+}
+
+// Exponent vector v = (H_bar delta_t) of one exponential from the two node
+// fields, with node weights (a, b) (swap = false) or (b, a) (swap = true):
+//   v_x + i v_y = P_a co_1 + P_b co_2 + conj(M_a ct_1 + M_b ct_2)   (w_x' + i w_y' as above)
+template <typename R>
+SPINSIM_HD void exponent(const SampleCtx<R>& c, const NodeField<R>& f1, const NodeField<R>& f2,
+                                         bool swap, R& vx, R& vy, R& vz)
+{
+    R hi[4], lo[4];
+    const int ia = swap ? 1 : 0, ib = swap ? 0 : 1;
+    hi[0] = c.Ph[ia]; lo[0] = c.Pl[ia];
+    hi[1] = c.Ph[ib]; lo[1] = c.Pl[ib];
+    hi[2] = c.Ph[2 + ia]; lo[2] = c.Pl[2 + ia];
+    hi[3] = c.Ph[2 + ib]; lo[3] = c.Pl[2 + ib];
+    vx = dot4_hilo(hi, lo, f1.co.r, f2.co.r, f1.ct.r, f2.ct.r);
+    vy = dot4_hilo(hi, lo, f1.co.i, f2.co.i, -f1.ct.i, -f2.ct.i);
+    const R wa = swap ? c.zb : c.za, wb = swap ? c.za : c.zb;
+    vz = fma(wa, f1.z, fma(wb, f2.z, c.zbias));
+}
+
+// -------------------------------------------------------------------------
+// Split residuals.  An operator close to the identity is carried as
+//   U - I = F(g) + rest,
+// where F(g) is its first-order part, -i times the generator
+// g . (J_x, J_y, J_z, Q) (spin-one) or g . sigma/2 (spin-half), held as the
+// coefficients g, and `rest` holds everything of second and higher order.
+// The first-order coefficients of a step exponential exp(-i v.A) are exactly
+// its exponent v, and those of a product add (U - I = A + B + AB).  At the end
+// of a sample the first-order coefficients are replaced by their exact FP64
+// value (the quadrature sum of the field over the sample), so FP32 rounding
+// only ever touches the second-order part, whose coherent accumulation over
+// 10^7 steps stays far below the target accuracy.  This extends the paper's
+// residual idea (work with U - I, Sec. 1.2.3) one order further.
+// -------------------------------------------------------------------------
+
+// Spin-half: SU(2) elements [[alpha, -conj(beta)], [beta, conj(alpha)]].
+// F(g): alpha - 1 = -i g_z / 2, beta = (g_y - i g_x) / 2.
+template <typename R>
+struct Res2 {
+    R g[3];
+    cx<R> a, b;   // second- and higher-order parts of alpha - 1 and beta
+};
+
+template <typename R>
+SPINSIM_HD void res2_zero(Res2<R>& x)
+{
+    x.g[0] = x.g[1] = x.g[2] = R(0);
+    x.a = cmk(R(0), R(0));
+    x.b = cmk(R(0), R(0));
+}
+
+template <typename R>
+SPINSIM_HD void res2_full(const Res2<R>& x, cx<R>& a, cx<R>& b)
+{
+    a = cmk(x.a.r, fma(R(-0.5), x.g[2], x.a.i));
+    b = cmk(fma(R(0.5), x.g[1], x.b.r), fma(R(-0.5), x.g[0], x.b.i));
+}
+
+// exp(-i (v_x J_x + v_y J_y + v_z J_z)) with v = w delta_t, J = sigma/2, by the
+// SU(2) identity cos(th/2) I - i sin(th/2) (v/th).sigma, th = |v| (Sec. 1.2.3):
+//   alpha - 1 = -(1 - cos(th/2)) - i f v_z,  beta = f (v_y - i v_x),  f = sin(th/2)/th.
+// First order: f -> 1/2.  The rest uses f - 1/2 and 1 - cos(th/2) = 2 sin^2(th/4),
+// both from their Taylor series in y = th^2/4 for th/2 <= 1/16.
+template <typename R>
+SPINSIM_HD void expm_half_res(R vx, R vy, R vz, Res2<R>& e)
+{
+    R t2 = vx * vx + vy * vy + vz * vz;
+    R fm, g;
+    if (t2 <= R(0.015625)) {      // (th/2)^2 <= 1/256
+        R y = R(0.25) * t2;
+        fm = R(-0.5) * y * (R(1.0 / 6) - y * (R(1.0 / 120) - y * (R(1.0 / 5040) - y * R(1.0 / 362880))));
+        g = y * (R(0.5) - y * (R(1.0 / 24) - y * (R(1.0 / 720) - y * (R(1.0 / 40320) - y * R(1.0 / 3628800)))));
+    } else {
+        R th = sqrt(t2);
+        R s4 = sin(R(0.25) * th);
+        fm = sin(R(0.5) * th) / th - R(0.5);
+        g = R(2) * s4 * s4;
+    }
+    e.g[0] = vx; e.g[1] = vy; e.g[2] = vz;
+    e.a = cmk(-g, -fm * vz);
+    e.b = cmk(fm * vy, -fm * vx);
+}
+
+// (I + A)(I + B) - I = A + B + A B, A later in time:
+//   alpha = a1 a2 - conj(b1) b2,  beta = b1 a2 + conj(a1) b2   (full elements)
+template <typename R>
+SPINSIM_HD void res2_mul(const Res2<R>& A, const Res2<R>& B, Res2<R>& C)
+{
+    cx<R> Aa, Ab, Ba, Bb;
+    res2_full(A, Aa, Ab);
+    res2_full(B, Ba, Bb);
+    cx<R> a = cadd(A.a, B.a);
+    a = cfma(Aa, Ba, a);
+    a = csub(a, cmul(cconj(Ab), Bb));
+    cx<R> b = cadd(A.b, B.b);
+    b = cfma(Ab, Ba, b);
+    b = cfma_conj(Aa, Bb, b);
+#pragma unroll
+    for (int i = 0; i < 3; i++) C.g[i] = A.g[i] + B.g[i];
+    C.a = a;
+    C.b = b;
+}
+
+// Spin-one: F(g) = -i (g_x J_x + g_y J_y + g_z J_z + g_q Q), Q = diag(1,-2,1)/3.
+template <typename R>
+struct Res3 {
+    R g[4];
+    cx<R> m[3][3];   // second- and higher-order part
+};
+
+template <typename R>
+SPINSIM_HD void res3_zero(Res3<R>& x)
+{
+#pragma unroll
+    for (int i = 0; i < 4; i++) x.g[i] = R(0);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) x.m[i][j] = cmk(R(0), R(0));
+}
+
+template <typename R>
+SPINSIM_HD void res3_full(const Res3<R>& x, cx<R> F[3][3])
+{
+    const R r = R(kInvSqrt2);
+    const R q3 = x.g[3] * R(1.0 / 3);
+    const cx<R> up = cmk(-x.g[1] * r, -x.g[0] * r);   // -i (g_x - i g_y)/sqrt2
+    const cx<R> dn = cmk(x.g[1] * r, -x.g[0] * r);    // -i (g_x + i g_y)/sqrt2
+    F[0][0] = cmk(x.m[0][0].r, x.m[0][0].i - (x.g[2] + q3));
+    F[1][1] = cmk(x.m[1][1].r, fma(R(2), q3, x.m[1][1].i));
+    F[2][2] = cmk(x.m[2][2].r, x.m[2][2].i + (x.g[2] - q3));
+    F[0][1] = cadd(x.m[0][1], up);
+    F[1][2] = cadd(x.m[1][2], up);
+    F[1][0] = cadd(x.m[1][0], dn);
+    F[2][1] = cadd(x.m[2][1], dn);
+    F[0][2] = x.m[0][2];
+    F[2][0] = x.m[2][0];
+}
+
+// (I + A)(I + B) - I = A + B + A B, A later in time.
+template <typename R>
+SPINSIM_HD void res3_mul(const Res3<R>& A, const Res3<R>& B, Res3<R>& C)
+{
+    cx<R> FA[3][3], FB[3][3];
+    res3_full(A, FA);
+    res3_full(B, FB);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            cx<R> s = cadd(A.m[i][j], B.m[i][j]);
+            s = cfma(FA[i][0], FB[0][j], s);
+            s = cfma(FA[i][1], FB[1][j], s);
+            s = cfma(FA[i][2], FB[2][j], s);
+            C.m[i][j] = s;
+        }
+#pragma unroll
+    for (int i = 0; i < 4; i++) C.g[i] = A.g[i] + B.g[i];
+}
+
+// exp(-i (v_x J_x + v_y J_y + v_z J_z + v_q Q)) ~= T^n, n = 2^tau, returned as a
+// split residual (Sec. 1.2.3, Eqs. lie_trotter, lie_trotter_4).  The
+// quadrupole coefficient is passed as qd3 = v_q / 3 / n.
+//
+// T = e^{-iD/2} e^{-i Phi J_phi} e^{-iD/2} with D = z J_z + q Q, z = v_z/n,
+// q = v_q/n, Phi = |v_perp|/n.  Since e^{-i Phi J_phi} = W e^{-i Phi J_x} W^dagger
+// with the diagonal W = e^{-i phi J_z} = diag(e^{-i phi}, 1, e^{i phi}), which
+// commutes with D, T = W T0 W^dagger where T0 is T at phi = 0 and
+// T^n = W T0^n W^dagger.  T0 is complex symmetric (diagonal x symmetric x
+// diagonal), so its residual squarings s = (a + 2I) a keep it symmetric and
+// need 6 of the 9 entries.  With the diagonal phases th_0 = -(z + q/3),
+// th_1 = 2q/3, th_2 = z - q/3 and S = sin(Phi/2), T0 - I is
+//   a_00 = expm1(i th_0) - S^2 e^{i th_0},  a_11 = expm1(i th_1) - 2 S^2 e^{i th_1},
+//   a_22 = expm1(i th_2) - S^2 e^{i th_2},
+//   a_01 = -i sin(Phi)/sqrt2 e^{-i th_2/2},  a_12 = -i sin(Phi)/sqrt2 e^{-i th_0/2},
+//   a_02 = -S^2 e^{i (th_0 + th_2)/2}.
+// Its first-order part is -i (Phi J_x + z J_z + q Q), i.e. i th_j on the
+// diagonal and -i Phi/sqrt2 next to it; the rest is formed without
+// cancellation from sin x - x and cos x - 1.  A residual squaring
+// (a + 2I) a = 2a + a^2 doubles the first-order part exactly and adds a^2 to
+// the rest.
+template <typename R>
+SPINSIM_HD void expm_one_res(R vx, R vy, R vz, R qd3, int tau, Res3<R>& e)
+{
+    const R inv_n = ldexp(R(1), -tau);
+    const R z = vz * inv_n;
+    const R vp2 = vx * vx + vy * vy;
+    R epr = R(1), epi = R(0);   // e^{i phi}
+    R Phi = R(0);
+    if (vp2 > R(0)) {
+        const R vp = sqrt(vp2);   // correctly rounded
+        epr = vx / vp;
+        epi = vy / vp;
+        Phi = vp * inv_n;
+    }
+    const R h0 = fma(R(-0.5), z, R(-0.5) * qd3);   // th_0 / 2
+    const R h1 = qd3;                              // th_1 / 2
+    const R h2 = fma(R(0.5), z, R(-0.5) * qd3);    // th_2 / 2
+    const R P = R(0.5) * Phi;
+    R sm0, cm0, sm1, cm1, sm2, cm2, smP, cmP;
+    small_sincos_m(h0, sm0, cm0);
+    small_sincos_m(h1, sm1, cm1);
+    small_sincos_m(h2, sm2, cm2);
+    small_sincos_m(P, smP, cmP);
+    const R s0 = h0 + sm0, c0 = R(1) + cm0;       // sin, cos of th_j / 2
+    const R s1 = h1 + sm1, c1 = R(1) + cm1;
+    const R s2 = h2 + sm2, c2 = R(1) + cm2;
+    const R sP = P + smP;
+    const R S2 = sP * sP;
+    // cos th - 1 = -2 sin^2(th/2);  sin th - th = 2 (sm + h cm + sm cm)
+    const cx<R> d0 = cmk(R(-2) * s0 * s0, R(2) * fma(h0, cm0, sm0 * c0));
+    const cx<R> d1 = cmk(R(-2) * s1 * s1, R(2) * fma(h1, cm1, sm1 * c1));
+    const cx<R> d2 = cmk(R(-2) * s2 * s2, R(2) * fma(h2, cm2, sm2 * c2));
+    // e^{i th} = 1 + (cos th - 1) + i sin th
+    const cx<R> p0 = cmk(R(1) + d0.r, R(2) * s0 * c0);
+    const cx<R> p1 = cmk(R(1) + d1.r, R(2) * s1 * c1);
+    const cx<R> p2 = cmk(R(1) + d2.r, R(2) * s2 * c2);
+    // rest of T0 - I (symmetric: b_10 = b_01, b_20 = b_02, b_21 = b_12)
+    cx<R> b00 = csub(d0, cscale(p0, S2));
+    cx<R> b11 = csub(d1, cscale(p1, R(2) * S2));
+    cx<R> b22 = csub(d2, cscale(p2, S2));
+    // -i/sqrt2 [ (sin Phi - Phi) e^{-i h} + Phi (e^{-i h} - 1) ]
+    const R r = R(kInvSqrt2);
+    const R sPm = R(2) * fma(P, cmP, smP * (R(1) + cmP));   // sin Phi - Phi
+    cx<R> t01 = cmk(fma(sPm, c2, Phi * cm2), -(sPm + Phi) * s2);   // (sin Phi - Phi) e^{-i h2} + Phi (e^{-i h2} - 1)
+    cx<R> t12 = cmk(fma(sPm, c0, Phi * cm0), -(sPm + Phi) * s0);
+    cx<R> b01 = cmk(r * t01.i, -r * t01.r);
+    cx<R> b12 = cmk(r * t12.i, -r * t12.r);
+    cx<R> b02 = cscale(cmk(c0 * c2 - s0 * s2, s0 * c2 + c0 * s2), -S2);
+    // first-order coefficients in the phi = 0 frame
+    R fP = Phi, fz = z, fq3 = qd3;
+    for (int it = 0; it < tau; it++) {
+        // full symmetric matrix A = F0 + rest; F0 = -i (Phi J_x + z J_z + q Q)
+        const cx<R> A00 = cmk(b00.r, b00.i - (fz + fq3));
+        const cx<R> A11 = cmk(b11.r, fma(R(2), fq3, b11.i));
+        const cx<R> A22 = cmk(b22.r, b22.i + (fz - fq3));
+        const R o = -fP * r;
+        const cx<R> A01 = cmk(b01.r, b01.i + o);
+        const cx<R> A12 = cmk(b12.r, b12.i + o);
+        const cx<R> A02 = b02;
+        // rest <- 2 rest + A^2
+        b00 = cfma(A02, A02, cfma(A01, A01, cfma(A00, A00, cscale(b00, R(2)))));
+        const cx<R> n01 = cfma(A02, A12, cfma(A01, A11, cfma(A00, A01, cscale(b01, R(2)))));
+        const cx<R> n02 = cfma(A02, A22, cfma(A01, A12, cfma(A00, A02, cscale(b02, R(2)))));
+        b11 = cfma(A12, A12, cfma(A11, A11, cfma(A01, A01, cscale(b11, R(2)))));
+        const cx<R> n12 = cfma(A12, A22, cfma(A11, A12, cfma(A01, A02, cscale(b12, R(2)))));
+        b22 = cfma(A22, A22, cfma(A12, A12, cfma(A02, A02, cscale(b22, R(2)))));
+        b01 = n01; b02 = n02; b12 = n12;
+        fP *= R(2); fz *= R(2); fq3 *= R(2);
+    }
+    // W (rest) W^dagger: entry (j, l) picks up e^{-i phi (m_j - m_l)}
+    const cx<R> ep = cmk(epr, epi), em = cmk(epr, -epi);
+    const cx<R> ep2 = cmul(ep, ep), em2 = cconj(ep2);
+    e.m[0][0] = b00; e.m[1][1] = b11; e.m[2][2] = b22;
+    e.m[0][1] = cmul(b01, em); e.m[1][0] = cmul(b01, ep);
+    e.m[1][2] = cmul(b12, em); e.m[2][1] = cmul(b12, ep);
+    e.m[0][2] = cmul(b02, em2); e.m[2][0] = cmul(b02, ep2);
+    e.g[0] = vx; e.g[1] = vy; e.g[2] = vz; e.g[3] = R(3) * ldexp(qd3, tau);
+}
+
+// -------------------------------------------------------------------------
+// One integration step u(t_{k-1} + (l+1) dt, t_{k-1} + l dt), as a split
+// residual, for the three methods.  METHOD: 0 CF4 (Sec. 1.2.2, nodes
+// c1,2 = (1 -+ 1/sqrt3)/2, u = exp(-i Hbar_2 dt) exp(-i Hbar_1 dt)); 1 midpoint
+// sampling (one exponential at t + dt/2); 2 Heun sampling (one exponential of
+// the average of the end-point fields) (Sec. 1.3.1).  The node offsets and
+// weights come with the context.
+// -------------------------------------------------------------------------
+template <typename R, int METHOD>
+SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res3<R>& x)
+{
+    NodeField<R> f1, f2;
+    field_at(c, (lf + c.c1) * c.dt, f1);
+    if (METHOD == 1) f2 = f1;
+    else field_at(c, (lf + c.c2) * c.dt, f2);
+    R vx, vy, vz;
+    exponent(c, f1, f2, false, vx, vy, vz);
+    if (METHOD == 0) {
+        Res3<R> e1, e2;
+        expm_one_res(vx, vy, vz, c.qd3, tau, e1);
+        exponent(c, f1, f2, true, vx, vy, vz);
+        expm_one_res(vx, vy, vz, c.qd3, tau, e2);
+        res3_mul(e2, e1, x);   // Eq. cf4_implementation
+    } else {
+        expm_one_res(vx, vy, vz, c.qd3, tau, x);
+    }
+}
+
+template <typename R, int METHOD>
+SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res2<R>& x)
+{
+    (void)tau;
+    NodeField<R> f1, f2;
+    field_at(c, (lf + c.c1) * c.dt, f1);
+    if (METHOD == 1) f2 = f1;
+    else field_at(c, (lf + c.c2) * c.dt, f2);
+    R vx, vy, vz;
+    exponent(c, f1, f2, false, vx, vy, vz);
+    if (METHOD == 0) {
+        Res2<R> e1, e2;
+        expm_half_res(vx, vy, vz, e1);
+        exponent(c, f1, f2, true, vx, vy, vz);
+        expm_half_res(vx, vy, vz, e2);
+        res2_mul(e2, e1, x);
+    } else {
+        expm_half_res(vx, vy, vz, x);
+    }
+}
+
+template <typename R>
+SPINSIM_HD void res_zero(Res3<R>& x) { res3_zero(x); }
+template <typename R>
+SPINSIM_HD void res_zero(Res2<R>& x) { res2_zero(x); }
+template <typename R>
+SPINSIM_HD void res_mul(const Res3<R>& A, const Res3<R>& B, Res3<R>& C) { res3_mul(A, B, C); }
+template <typename R>
+SPINSIM_HD void res_mul(const Res2<R>& A, const Res2<R>& B, Res2<R>& C) { res2_mul(A, B, C); }
+
+}  // namespace spinsim

@@ -1,0 +1,80 @@
+// internal.h -- structures shared by the host engine and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spinsim {
+
+constexpr int kMaxPulses = 4;
+constexpr int kSegments = 4;             // canonical split of one U_k's L steps (fixed tree)
+constexpr int kRun = 16;                 // samples one lane chains sequentially
+constexpr int kChunk = 32 * kRun;        // samples one warp chains (never spans simulations)
+
+// Per-simulation parameters on the device, precomputed on the host in FP64.
+struct DevSim {
+    double* states;              // [K][N] complex, device
+    double* spin;                // [K][3] or nullptr
+    double* ops;                 // [K][N][N] complex or nullptr
+    int64_t K, L;
+    int64_t sample_offset;       // first sample of this simulation in the operator buffer
+    int64_t chunk_offset;        // first chain chunk of this simulation
+    double t_start, dt_out, dt;  // dt = dt_out / L
+    double drive_hz, drive_phase;
+    double w_co0, w_counter0;    // frame: 2 pi (f_d - B), 2 pi (f_d + B); lab: 2 pi f_d, 2 pi f_d
+    // Step exponents are built directly from these products of amplitude,
+    // quadrature weight and delta_t (radians), so no FP32-rounded amplitude
+    // or weight enters every step with the same rounding error:
+    //   P[0] = Om+ a dt, P[1] = Om+ b dt, P[2] = Om- a dt, P[3] = Om- b dt,
+    // Om+- = (2 pi drive_x_hz +- 2 pi drive_y_hz)/2, (a, b) the method's
+    // node weights (CF4: Eqs. cf4_sample_1/2; the second CF4 exponential
+    // uses (b, a)).
+    double P[4];
+    double za, zb;               // a dt, b dt for the z field
+    double zbias;                // lab frame: 2 pi B (a + b) dt; frame: 0
+    double c1, c2;               // node offsets in units of dt
+    double qd3;                  // (a + b) w_q dt / 3 / 2^tau (one exponential), in the bulk type
+    double om_plus, om_minus;    // Om+, Om- (rad/s)
+    double W1, W2;               // total quadrature weight of nodes 1 and 2 over one step
+    double gq;                   // exact first-order Q coefficient of one sample: w_q dt_out
+    double exit_re, exit_im;     // e^{-i 2 pi B dt_out} (frame) or 1
+    double exit_half_re, exit_half_im;  // e^{-i pi B dt_out} (frame) or 1
+    double amp[kMaxPulses];      // 2 pi A_p, rad/s
+    double centre[kMaxPulses];
+    double inv_w[kMaxPulses];
+    double psi0[6];
+    int32_t n_pulses, frame, spin_x2, counter_on;
+};
+
+struct IntegrateArgs {
+    const DevSim* sims;
+    const int64_t* sample_offsets;   // n_sims + 1 prefix offsets (device)
+    int n_sims;
+    int64_t total_samples;
+    double* U;                        // operator buffer: spin-one 18, spin-half 4 doubles per sample
+    int tau;
+    unsigned long long* tile_counter; // zeroed before the launch
+    int64_t n_tiles;
+};
+
+struct ChainArgs {
+    const DevSim* sims;
+    const int64_t* chunk_offsets;     // n_sims + 1 prefix offsets (device)
+    int n_sims;
+    int64_t n_chunks;
+    const double* U;
+    double* run_prefix;               // [n_chunks][32] exclusive lane prefixes
+    double* chunk_agg;                // [n_chunks] chunk products
+    double* chunk_start;              // [n_chunks][N] complex states entering each chunk
+};
+
+// Doubles per stored operator in the operator buffer and chain scratch.
+inline int op_doubles(int spin_x2) { return spin_x2 == 2 ? 18 : 4; }
+
+// Host-side launchers (integrate.cu, chain.cu).  precision: 0 FP64, 1 FP32-bulk.
+cudaError_t launch_integrate(int spin_x2, int precision, int method, int lanes, int block, int grid,
+                             const IntegrateArgs& a, cudaStream_t stream);
+size_t integrate_smem_bytes(int spin_x2, int precision, int lanes, int block);
+cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int lanes, int block, int* blocks_per_sm);
+cudaError_t launch_chain(int spin_x2, const ChainArgs& a, int n_sm, cudaStream_t stream);
+
+}  // namespace spinsim

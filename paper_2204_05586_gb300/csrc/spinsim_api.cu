@@ -1,0 +1,1016 @@
+// spinsim_api.cu -- host engine behind the C ABI of include/spinsim.h.
+//
+// One batch = validate requests -> plan (sample/chunk offsets, parameter
+// table) -> upload the table -> integrate kernel (all U_k) -> chain kernels
+// (psi_k, <J>_k, U_k) -> copy back any host-resident outputs.  Requests of
+// both spins may share a batch; each spin is one pass of the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "spinsim.h"
+#include "internal.h"
+
+using namespace spinsim;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double kMagnusXi = 1.0868687;   // Sec. 1.2.2: convergence radius of the Magnus series
+constexpr int64_t kMaxL = int64_t(1) << 24;  // step index stays exact in FP32
+
+// ------------------------------------------------------------- validation
+struct Checked {
+    int status = SPINSIM_OK;
+    int flags = 0;
+    int64_t K = 0, L = 0;
+};
+
+Checked check_request(const spinsim_request* r)
+{
+    Checked c;
+    if (!r) { c.status = SPINSIM_E_ARG; return c; }
+    if (r->spin_x2 != 1 && r->spin_x2 != 2) { c.status = SPINSIM_E_ARG; return c; }
+    const spinsim_field& f = r->field;
+    if (f.n_pulses < 0 || f.n_pulses > SPINSIM_MAX_PULSES) { c.status = SPINSIM_E_ARG; return c; }
+    for (int p = 0; p < f.n_pulses; p++)
+        if (!(f.pulse_width_s[p] > 0.0) || !std::isfinite(f.pulse_amp_hz[p]) || !std::isfinite(f.pulse_centre_s[p])) {
+            c.status = SPINSIM_E_ARG;
+            return c;
+        }
+    const double vals[] = {f.bias_hz, f.drive_x_hz, f.drive_y_hz, f.drive_hz, f.drive_phase, f.quad_hz,
+                           r->t_start, r->t_end, r->dt, r->dt_out};
+    for (double v : vals)
+        if (!std::isfinite(v)) { c.status = SPINSIM_E_ARG; return c; }
+    if (!(r->dt > 0.0) || !(r->dt_out > 0.0) || !(r->t_end >= r->t_start)) { c.status = SPINSIM_E_ARG; return c; }
+    const double rk = (r->t_end - r->t_start) / r->dt_out;
+    const double rl = r->dt_out / r->dt;
+    const double k = std::floor(rk + 0.5), l = std::floor(rl + 0.5);
+    if (std::fabs(rk - k) > 1e-9 * std::max(1.0, rk) || std::fabs(rl - l) > 1e-9 * std::max(1.0, rl) || l < 1.0 ||
+        l > (double)kMaxL || k > 9.0e15) {
+        c.status = SPINSIM_E_STEP_RATIO;
+        return c;
+    }
+    c.K = (int64_t)k;
+    c.L = (int64_t)l;
+    const int n = r->spin_x2 + 1;
+    double nrm = 0.0;
+    for (int i = 0; i < 2 * n; i++) {
+        if (!std::isfinite(r->psi0[i])) { c.status = SPINSIM_E_ARG; return c; }
+        nrm += r->psi0[i] * r->psi0[i];
+    }
+    if (std::fabs(std::sqrt(nrm) - 1.0) > 1e-10) { c.status = SPINSIM_E_NORM; return c; }
+    // ||H||_2 delta_t against the Magnus radius.  ||w.J||_2 = |w| j, ||Q||_2 = 2/3.
+    const double two_pi = 2.0 * kPi;
+    double pulses = 0.0;
+    for (int p = 0; p < f.n_pulses; p++) pulses += std::fabs(f.pulse_amp_hz[p]);
+    const double wperp = two_pi * (std::fabs(f.drive_x_hz) + std::fabs(f.drive_y_hz));
+    const double wz = two_pi * (std::fabs(f.bias_hz) + pulses);
+    const double j = r->spin_x2 == 2 ? 1.0 : 0.5;
+    const double hnorm = std::sqrt(wperp * wperp + wz * wz) * j +
+                         (r->spin_x2 == 2 ? two_pi * std::fabs(f.quad_hz) * 2.0 / 3.0 : 0.0);
+    if (hnorm * (r->dt_out / (double)c.L) >= kMagnusXi) c.flags |= SPINSIM_WARN_MAGNUS;
+    return c;
+}
+
+bool is_device_pointer(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// -------------------------------------------------------------- scratch
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Arena {
+    DevBuf buf;   // one allocation carved into the pieces of a batch
+    size_t bytes() const { return buf.cap; }
+};
+
+struct PinnedBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+struct Group {
+    int spin_x2;
+    std::vector<int64_t> idx;      // request indices
+    int64_t samples = 0, chunks = 0;
+    size_t sims_off = 0, soff_off = 0, coff_off = 0, counter_off = 0, U_off = 0, prefix_off = 0, agg_off = 0,
+           start_off = 0;
+};
+
+struct StagedOut {
+    int64_t req;
+    double* host_states;
+    double* host_spin;
+    double* host_ops;
+    size_t states_off, spin_off, ops_off;  // offsets into the arena
+    size_t states_bytes, spin_bytes, ops_bytes;
+};
+
+struct Plan {
+    std::vector<Group> groups;
+    std::vector<StagedOut> staged;
+    size_t total = 0;
+    size_t pinned_bytes = 0;
+};
+
+struct TuneKey {
+    int spin, precision, method, tau, bucket;
+    bool operator<(const TuneKey& o) const
+    {
+        return std::tie(spin, precision, method, tau, bucket) < std::tie(o.spin, o.precision, o.method, o.tau, o.bucket);
+    }
+};
+struct TuneVal {
+    int lanes, block;
+};
+
+std::mutex g_tune_mu;
+std::map<std::pair<int, TuneKey>, TuneVal> g_tune_cache;   // (device, key) -> choice, shared by handles
+
+}  // namespace
+
+// ------------------------------------------------------------------ handle
+struct Ticket {
+    spinsim_request req;
+    spinsim_result* res;
+    int state;    // 0 pending, 1 in flight, 2 done
+    int slot;
+    size_t bytes;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    std::vector<int64_t> tickets;
+    Arena arena;
+    PinnedBuf pinned;
+    size_t in_flight = 0;
+};
+
+struct spinsim_s {
+    spinsim_config cfg;
+    int device = 0;
+    int n_sm = 0;
+    int tau = 24;
+    size_t budget = 0;
+    cudaStream_t work = nullptr;    // internal stream (graph capture / replay)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_pinned = nullptr;
+    Arena arena;
+    PinnedBuf pinned;
+    spinsim_launch_info last{};
+    std::map<std::tuple<int, int, int>, int> occ;   // (spin, lanes, block) -> resident blocks per SM
+    std::vector<char> table_tmp;                     // host copy of the next parameter table
+    // graph cache: one batch signature
+    std::vector<uint64_t> graph_sig;
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_kernels = 0;
+    spinsim_launch_info graph_info{};
+    // serving
+    std::vector<Slot> slots;
+    std::deque<int64_t> pending;
+    std::unordered_map<int64_t, Ticket> tickets;
+    int64_t next_ticket = 1;
+    size_t bytes_in_flight = 0;
+};
+
+namespace {
+
+int ensure_device(spinsim_s* h, DevBuf& b, size_t need)
+{
+    if (b.cap >= need) return SPINSIM_OK;
+    size_t cap = std::max(need, b.cap + b.cap / 2);
+    cap = round_up(cap, size_t(1) << 20);
+    if (cap > h->budget) cap = need;
+    if (need > h->budget) return SPINSIM_E_NOMEM;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);   // synchronises the device
+        b.p = nullptr;
+        b.cap = 0;
+        if (e != cudaSuccess) return SPINSIM_E_CUDA;
+    }
+    if (cudaMalloc(&b.p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return SPINSIM_E_NOMEM;
+    }
+    b.cap = cap;
+    return SPINSIM_OK;
+}
+
+int ensure_pinned(PinnedBuf& b, size_t need)
+{
+    if (b.cap >= need) return SPINSIM_OK;
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t cap = round_up(std::max<size_t>(need, 4096), 4096);
+    if (cudaMallocHost(&b.p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return SPINSIM_E_NOMEM;
+    }
+    b.cap = cap;
+    return SPINSIM_OK;
+}
+
+// Scratch bytes of one group (spin) of a batch.
+size_t group_bytes(int spin_x2, int64_t n, int64_t samples, int64_t chunks)
+{
+    const size_t opb = (size_t)op_doubles(spin_x2) * sizeof(double);
+    size_t s = 0;
+    s += round_up((size_t)n * sizeof(DevSim), 256);
+    s += 2 * round_up((size_t)(n + 1) * sizeof(int64_t), 256);
+    s += 256;                                          // tile counter
+    s += round_up((size_t)samples * opb, 256);         // operators
+    s += round_up((size_t)chunks * 32 * opb, 256);     // lane prefixes
+    s += round_up((size_t)chunks * opb, 256);          // chunk products
+    s += round_up((size_t)chunks * 2 * (spin_x2 + 1) * sizeof(double), 256);
+    return s;
+}
+
+// Build the plan: offsets inside one arena, the staged outputs, and fill the
+// pinned parameter table.  `checked` holds the validation of every request.
+// While a stream is being captured the pointer kinds cannot be queried; the
+// outputs are then taken to be device memory (only alignment is checked).
+int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, const std::vector<Checked>& checked,
+               bool capturing, Plan& plan)
+{
+    plan = Plan();
+    size_t off = 0;
+    size_t pin = 0;
+    for (int spin = 1; spin <= 2; spin++) {
+        Group g;
+        g.spin_x2 = spin;
+        for (int64_t i = 0; i < n; i++)
+            if (checked[i].status == SPINSIM_OK && reqs[i].spin_x2 == spin) {
+                g.idx.push_back(i);
+                g.samples += checked[i].K;
+                g.chunks += (checked[i].K + kChunk - 1) / kChunk;
+            }
+        if (g.idx.empty()) continue;
+        const int64_t m = (int64_t)g.idx.size();
+        const size_t opb = (size_t)op_doubles(spin) * sizeof(double);
+        g.sims_off = off; off += round_up((size_t)m * sizeof(DevSim), 256);
+        g.soff_off = off; off += round_up((size_t)(m + 1) * sizeof(int64_t), 256);
+        g.coff_off = off; off += round_up((size_t)(m + 1) * sizeof(int64_t), 256);
+        g.counter_off = off; off += 256;
+        g.U_off = off; off += round_up((size_t)g.samples * opb, 256);
+        g.prefix_off = off; off += round_up((size_t)g.chunks * 32 * opb, 256);
+        g.agg_off = off; off += round_up((size_t)g.chunks * opb, 256);
+        g.start_off = off; off += round_up((size_t)g.chunks * 2 * (spin + 1) * sizeof(double), 256);
+        // pinned table: sims, sample offsets, chunk offsets (same relative order)
+        pin += round_up((size_t)m * sizeof(DevSim), 256) + 2 * round_up((size_t)(m + 1) * sizeof(int64_t), 256);
+        plan.groups.push_back(std::move(g));
+    }
+    // host-resident or misaligned outputs are staged through the arena
+    for (const Group& g : plan.groups)
+        for (int64_t i : g.idx) {
+            const int N = reqs[i].spin_x2 + 1;
+            const int64_t K = checked[i].K;
+            spinsim_result& r = res[i];
+            auto needs_stage = [capturing](const void* p) {
+                return p && ((!capturing && !is_device_pointer(p)) || ((uintptr_t)p & 15u) != 0);
+            };
+            bool st = needs_stage(r.states), sp = needs_stage(r.spin), op = needs_stage(r.ops);
+            if (!(st || sp || op)) continue;
+            StagedOut so{};
+            so.req = i;
+            if (st) { so.host_states = r.states; so.states_bytes = (size_t)K * 2 * N * sizeof(double); so.states_off = off; off += round_up(so.states_bytes, 256); }
+            if (sp) { so.host_spin = r.spin; so.spin_bytes = (size_t)K * 3 * sizeof(double); so.spin_off = off; off += round_up(so.spin_bytes, 256); }
+            if (op) { so.host_ops = r.ops; so.ops_bytes = (size_t)K * 2 * N * N * sizeof(double); so.ops_off = off; off += round_up(so.ops_bytes, 256); }
+            plan.staged.push_back(so);
+        }
+    plan.total = std::max<size_t>(off, 256);
+    plan.pinned_bytes = pin;
+    return SPINSIM_OK;
+}
+
+// Fill the pinned parameter tables of every group; `base` is the arena's
+// device base address the tables will refer to.
+void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, const std::vector<Checked>& checked,
+                 const Plan& plan, char* base, char* pinned)
+{
+    size_t pin = 0;
+    for (const Group& g : plan.groups) {
+        const int64_t m = (int64_t)g.idx.size();
+        DevSim* sims = reinterpret_cast<DevSim*>(pinned + pin);
+        int64_t* soff = reinterpret_cast<int64_t*>(pinned + pin + round_up((size_t)m * sizeof(DevSim), 256));
+        int64_t* coff = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(soff) + round_up((size_t)(m + 1) * sizeof(int64_t), 256));
+        pin += round_up((size_t)m * sizeof(DevSim), 256) + 2 * round_up((size_t)(m + 1) * sizeof(int64_t), 256);
+        int64_t so = 0, co = 0;
+        for (int64_t q = 0; q < m; q++) {
+            const int64_t i = g.idx[q];
+            const spinsim_request& r = reqs[i];
+            const spinsim_field& f = r.field;
+            DevSim d;
+            std::memset(&d, 0, sizeof(d));
+            d.states = res[i].states;
+            d.spin = res[i].spin;
+            d.ops = res[i].ops;
+            for (const StagedOut& s : plan.staged)
+                if (s.req == i) {
+                    if (s.host_states) d.states = reinterpret_cast<double*>(base + s.states_off);
+                    if (s.host_spin) d.spin = reinterpret_cast<double*>(base + s.spin_off);
+                    if (s.host_ops) d.ops = reinterpret_cast<double*>(base + s.ops_off);
+                }
+            d.K = checked[i].K;
+            d.L = checked[i].L;
+            d.sample_offset = so;
+            d.chunk_offset = co;
+            soff[q] = so;
+            coff[q] = co;
+            so += d.K;
+            co += (d.K + kChunk - 1) / kChunk;
+            d.t_start = r.t_start;
+            d.dt_out = r.dt_out;
+            d.dt = r.dt_out / (double)d.L;
+            d.drive_hz = f.drive_hz;
+            d.drive_phase = f.drive_phase;
+            const double two_pi = 2.0 * kPi;
+            const double ax = two_pi * f.drive_x_hz, ay = two_pi * f.drive_y_hz;
+            const double om_plus = 0.5 * (ax + ay), om_minus = 0.5 * (ax - ay);
+            // node offsets and weights of the method.  CF4 (Eqs. cf4_sample_1/2):
+            // t_{1,2} = t + (1 -+ 1/sqrt3) dt/2, a = (3 + 2 sqrt3)/12, b = (3 - 2 sqrt3)/12.
+            // Midpoint and Heun sampling (Sec. 1.3.1): one exponential.
+            double c1, c2, wa, wb;
+            int n_exp;
+            if (h->cfg.method == SPINSIM_METHOD_CF4) {
+                c1 = 0.2113248654051871177454256; c2 = 0.7886751345948128822545744;
+                wa = 0.5386751345948128822545744; wb = -0.03867513459481288225457439; n_exp = 2;
+            } else if (h->cfg.method == SPINSIM_METHOD_MIDPOINT) {
+                c1 = 0.5; c2 = 0.5; wa = 1.0; wb = 0.0; n_exp = 1;
+            } else {
+                c1 = 0.0; c2 = 1.0; wa = 0.5; wb = 0.5; n_exp = 1;
+            }
+            d.c1 = c1;
+            d.c2 = c2;
+            d.P[0] = om_plus * wa * d.dt;
+            d.P[1] = om_plus * wb * d.dt;
+            d.P[2] = om_minus * wa * d.dt;
+            d.P[3] = om_minus * wb * d.dt;
+            d.counter_on = om_minus != 0.0 ? 1 : 0;
+            d.za = wa * d.dt;
+            d.zb = wb * d.dt;
+            d.frame = h->cfg.rotating_frame ? 1 : 0;
+            d.zbias = d.frame ? 0.0 : two_pi * f.bias_hz * (wa + wb) * d.dt;
+            if (d.frame) {
+                d.w_co0 = two_pi * (f.drive_hz - f.bias_hz);
+                d.w_counter0 = two_pi * (f.drive_hz + f.bias_hz);
+                const double th = two_pi * f.bias_hz * r.dt_out;
+                d.exit_re = std::cos(th);
+                d.exit_im = -std::sin(th);
+                d.exit_half_re = std::cos(0.5 * th);
+                d.exit_half_im = -std::sin(0.5 * th);
+            } else {
+                d.w_co0 = d.w_counter0 = two_pi * f.drive_hz;
+                d.exit_re = d.exit_half_re = 1.0;
+                d.exit_im = d.exit_half_im = 0.0;
+            }
+            // quadrupole coefficient of one exponential, over 3 and 2^tau, as the
+            // bulk type holds it (its rounding only reaches second order: the
+            // first-order part of every U_k is replaced by the exact gq)
+            const double vq = r.spin_x2 == 2 ? (wa + wb) * two_pi * f.quad_hz * d.dt : 0.0;
+            double qd3 = vq / 3.0 / std::ldexp(1.0, h->tau);
+            if (h->cfg.precision == SPINSIM_PREC_FP32_BULK) qd3 = (double)(float)qd3;
+            d.qd3 = qd3;
+            d.om_plus = om_plus;
+            d.om_minus = om_minus;
+            d.W1 = n_exp == 2 ? wa + wb : wa;
+            d.W2 = n_exp == 2 ? wa + wb : wb;
+            d.gq = r.spin_x2 == 2 ? two_pi * f.quad_hz * r.dt_out : 0.0;
+            d.n_pulses = f.n_pulses;
+            for (int p = 0; p < f.n_pulses; p++) {
+                d.amp[p] = two_pi * f.pulse_amp_hz[p];
+                d.centre[p] = f.pulse_centre_s[p];
+                d.inv_w[p] = 1.0 / f.pulse_width_s[p];
+            }
+            for (int e = 0; e < 6; e++) d.psi0[e] = r.psi0[e];
+            d.spin_x2 = r.spin_x2;
+            sims[q] = d;
+        }
+        soff[m] = so;
+        coff[m] = co;
+    }
+}
+
+// Resident blocks per SM of an integrate shape; computed outside stream
+// capture (it sets the kernel's shared-memory limit) and cached.
+int occupancy(spinsim_s* h, int spin, int lanes, int block, bool capturing, int* per_sm)
+{
+    auto key = std::make_tuple(spin, lanes, block);
+    auto it = h->occ.find(key);
+    if (it != h->occ.end()) {
+        *per_sm = it->second;
+        return SPINSIM_OK;
+    }
+    if (capturing) return SPINSIM_E_UNSUPPORTED;
+    int b = 0;
+    if (integrate_occupancy(spin, h->cfg.precision, h->cfg.method, lanes, block, &b) != cudaSuccess) {
+        cudaGetLastError();
+        return SPINSIM_E_CUDA;
+    }
+    h->occ[key] = b;
+    *per_sm = b;
+    return SPINSIM_OK;
+}
+
+int size_bucket(int64_t samples)
+{
+    int b = 0;
+    while (samples > 1 && b < 60) { samples >>= 1; b++; }
+    return b;
+}
+
+// Choose (lanes per sample, threads per block) for the integrate kernel.
+// Results never depend on this choice; only the time does.
+int choose_shape(spinsim_s* h, int spin, IntegrateArgs a, cudaStream_t stream, bool capturing, int& lanes, int& block,
+                 int& grid)
+{
+    const int precision = h->cfg.precision;
+    const int method = h->cfg.method;
+    lanes = h->cfg.lanes_per_sample;
+    block = h->cfg.threads_per_block;
+    if (lanes == 0 || block == 0) {
+        TuneKey key{spin, precision, method, h->tau, size_bucket(a.total_samples)};
+        bool found = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find({h->device, key});
+            if (it != g_tune_cache.end()) {
+                if (lanes == 0) lanes = it->second.lanes;
+                if (block == 0) block = it->second.block;
+                found = true;
+            }
+        }
+        if (!found) {
+            const int lane_opts[3] = {1, 2, 4};
+            const int block_opts[3] = {64, 128, 256};
+            int best_l = lanes ? lanes : 4, best_b = block ? block : 128;
+            if (!capturing) {
+                float best = 1e30f;
+                cudaEvent_t e0, e1;
+                if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SPINSIM_E_CUDA;
+                for (int li = 0; li < 3; li++) {
+                    const int L = lanes ? lanes : lane_opts[li];
+                    if (lanes && li > 0) break;
+                    for (int bi = 0; bi < 3; bi++) {
+                        const int B = block ? block : block_opts[bi];
+                        if (block && bi > 0) break;
+                        int per_sm = 0;
+                        if (occupancy(h, spin, L, B, false, &per_sm) != SPINSIM_OK || per_sm < 1) continue;
+                        // trial on a prefix of the batch: at most 4 full waves of this shape
+                        IntegrateArgs t = a;
+                        const int64_t wave = (int64_t)h->n_sm * per_sm * (B / L);
+                        t.total_samples = std::min<int64_t>(a.total_samples, 4 * wave);
+                        const int spb = B / L;
+                        t.n_tiles = (t.total_samples + spb - 1) / spb;
+                        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(t.n_tiles, (int64_t)h->n_sm * per_sm));
+                        float ms_best = 1e30f;
+                        for (int rep = 0; rep < 2; rep++) {
+                            cudaMemsetAsync(a.tile_counter, 0, sizeof(unsigned long long), stream);
+                            cudaEventRecord(e0, stream);
+                            launch_integrate(spin, precision, method, L, B, g, t, stream);
+                            cudaEventRecord(e1, stream);
+                            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                                cudaEventDestroy(e0);
+                                cudaEventDestroy(e1);
+                                return SPINSIM_E_CUDA;
+                            }
+                            float ms = 0.f;
+                            cudaEventElapsedTime(&ms, e0, e1);
+                            ms_best = std::min(ms_best, ms);
+                        }
+                        const float per = ms_best / (float)std::max<int64_t>(1, t.total_samples);
+                        if (per < best) {
+                            best = per;
+                            best_l = L;
+                            best_b = B;
+                        }
+                    }
+                }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tune_cache[{h->device, key}] = TuneVal{best_l, best_b};
+            }
+            lanes = best_l;
+            block = best_b;
+        }
+    }
+    int per_sm = 0;
+    int st = occupancy(h, spin, lanes, block, capturing, &per_sm);
+    if (st != SPINSIM_OK) return st;
+    per_sm = std::max(per_sm, 1);
+    const int spb = block / lanes;
+    const int64_t tiles = (a.total_samples + spb - 1) / spb;
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)h->n_sm * per_sm));
+    return SPINSIM_OK;
+}
+
+// Write the parameter tables of `plan` into the pinned buffer.  The buffer
+// may still be read by an earlier, not yet executed, host-to-device copy: when
+// the content is unchanged nothing is written (and nothing waited for);
+// otherwise the earlier copy is waited for through `pinned_free`.
+int refresh_table(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, const std::vector<Checked>& checked,
+                  const Plan& plan, char* base, PinnedBuf& pinned, cudaEvent_t pinned_free, bool capturing)
+{
+    if (h->table_tmp.size() < plan.pinned_bytes) h->table_tmp.resize(plan.pinned_bytes);
+    fill_tables(h, reqs, res, checked, plan, base, h->table_tmp.data());
+    if (plan.pinned_bytes <= pinned.cap && std::memcmp(pinned.p, h->table_tmp.data(), plan.pinned_bytes) == 0)
+        return SPINSIM_OK;
+    if (pinned_free && cudaEventSynchronize(pinned_free) != cudaSuccess) return SPINSIM_E_CUDA;
+    if (plan.pinned_bytes > pinned.cap) {
+        if (capturing) return SPINSIM_E_UNSUPPORTED;
+        int st = ensure_pinned(pinned, plan.pinned_bytes);
+        if (st != SPINSIM_OK) return st;
+    }
+    std::memcpy(pinned.p, h->table_tmp.data(), plan.pinned_bytes);
+    return SPINSIM_OK;
+}
+
+// Enqueue one batch on `stream` using `arena` and the pinned table buffer.
+// Requests with a failed validation are skipped.
+int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, const std::vector<Checked>& checked,
+              const Plan& plan, cudaStream_t stream, Arena& arena, PinnedBuf& pinned, cudaEvent_t pinned_free,
+              bool capturing, int* kernels_out)
+{
+    if (plan.groups.empty()) {
+        if (kernels_out) *kernels_out = 0;
+        return SPINSIM_OK;
+    }
+    if (plan.total > arena.buf.cap) {
+        if (capturing) return SPINSIM_E_UNSUPPORTED;
+        int st = ensure_device(h, arena.buf, plan.total);
+        if (st != SPINSIM_OK) return st;
+    }
+    char* base = static_cast<char*>(arena.buf.p);
+    int st = refresh_table(h, reqs, res, checked, plan, base, pinned, pinned_free, capturing);
+    if (st != SPINSIM_OK) return st;
+    int kernels = 0;
+    size_t pin = 0;
+    for (const Group& g : plan.groups) {
+        const int64_t m = (int64_t)g.idx.size();
+        const size_t tbl = round_up((size_t)m * sizeof(DevSim), 256) + 2 * round_up((size_t)(m + 1) * sizeof(int64_t), 256);
+        // sims, soff, coff are contiguous in both the pinned table and the arena
+        if (cudaMemcpyAsync(base + g.sims_off, static_cast<char*>(pinned.p) + pin, tbl, cudaMemcpyHostToDevice,
+                            stream) != cudaSuccess)
+            return SPINSIM_E_CUDA;
+        pin += tbl;
+        if (pinned_free && cudaEventRecord(pinned_free, stream) != cudaSuccess) return SPINSIM_E_CUDA;
+        IntegrateArgs ia;
+        ia.sims = reinterpret_cast<const DevSim*>(base + g.sims_off);
+        ia.sample_offsets = reinterpret_cast<const int64_t*>(base + g.soff_off);
+        ia.n_sims = (int)m;
+        ia.total_samples = g.samples;
+        ia.U = reinterpret_cast<double*>(base + g.U_off);
+        ia.tau = h->tau;
+        ia.tile_counter = reinterpret_cast<unsigned long long*>(base + g.counter_off);
+        int lanes = 0, block = 0, grid = 0;
+        if (g.samples > 0) {
+            st = choose_shape(h, g.spin_x2, ia, stream, capturing, lanes, block, grid);
+            if (st != SPINSIM_OK) return st;
+            const int spb = block / lanes;
+            ia.n_tiles = (g.samples + spb - 1) / spb;
+            if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
+                return SPINSIM_E_CUDA;
+            if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, lanes, block, grid, ia, stream) !=
+                cudaSuccess)
+                return SPINSIM_E_CUDA;
+            kernels += 1;
+            ChainArgs ca;
+            ca.sims = ia.sims;
+            ca.chunk_offsets = reinterpret_cast<const int64_t*>(base + g.coff_off);
+            ca.n_sims = (int)m;
+            ca.n_chunks = g.chunks;
+            ca.U = ia.U;
+            ca.run_prefix = reinterpret_cast<double*>(base + g.prefix_off);
+            ca.chunk_agg = reinterpret_cast<double*>(base + g.agg_off);
+            ca.chunk_start = reinterpret_cast<double*>(base + g.start_off);
+            if (launch_chain(g.spin_x2, ca, h->n_sm, stream) != cudaSuccess) return SPINSIM_E_CUDA;
+            kernels += 3;
+            h->last.lanes_per_sample = lanes;
+            h->last.threads_per_block = block;
+            h->last.grid_blocks = grid;
+        }
+    }
+    for (const StagedOut& s : plan.staged) {
+        if (s.host_states && cudaMemcpyAsync(s.host_states, base + s.states_off, s.states_bytes, cudaMemcpyDefault, stream) != cudaSuccess)
+            return SPINSIM_E_CUDA;
+        if (s.host_spin && cudaMemcpyAsync(s.host_spin, base + s.spin_off, s.spin_bytes, cudaMemcpyDefault, stream) != cudaSuccess)
+            return SPINSIM_E_CUDA;
+        if (s.host_ops && cudaMemcpyAsync(s.host_ops, base + s.ops_off, s.ops_bytes, cudaMemcpyDefault, stream) != cudaSuccess)
+            return SPINSIM_E_CUDA;
+    }
+    if (kernels_out) *kernels_out = kernels;
+    return SPINSIM_OK;
+}
+
+// Signature of a batch for graph reuse: everything except field values.
+std::vector<uint64_t> batch_signature(const spinsim_request* reqs, const spinsim_result* res, int64_t n,
+                                      const std::vector<Checked>& checked)
+{
+    std::vector<uint64_t> s;
+    s.reserve((size_t)n * 6 + 1);
+    s.push_back((uint64_t)n);
+    for (int64_t i = 0; i < n; i++) {
+        s.push_back((uint64_t)reqs[i].spin_x2 | ((uint64_t)(checked[i].status & 0xff) << 8));
+        s.push_back((uint64_t)checked[i].K);
+        s.push_back((uint64_t)checked[i].L);
+        s.push_back((uint64_t)(uintptr_t)res[i].states);
+        s.push_back((uint64_t)(uintptr_t)res[i].spin);
+        s.push_back((uint64_t)(uintptr_t)res[i].ops);
+    }
+    return s;
+}
+
+void drop_graph(spinsim_s* h)
+{
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+    h->graph_sig.clear();
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+extern "C" {
+
+const char* spinsim_status_string(int status)
+{
+    switch (status) {
+        case SPINSIM_OK: return "ok";
+        case SPINSIM_PENDING: return "pending";
+        case SPINSIM_E_ARG: return "invalid argument";
+        case SPINSIM_E_STEP_RATIO: return "time span, output step and integration step are not integer ratios";
+        case SPINSIM_E_NORM: return "initial state is not normalised";
+        case SPINSIM_E_NOMEM: return "device memory budget exceeded or allocation failed";
+        case SPINSIM_E_CUDA: return "CUDA runtime error";
+        case SPINSIM_E_TIMEOUT: return "timed out";
+        case SPINSIM_E_CAPACITY: return "result capacity smaller than the number of samples";
+        case SPINSIM_E_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+int spinsim_config_default(spinsim_config* cfg)
+{
+    if (!cfg) return SPINSIM_E_ARG;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->method = SPINSIM_METHOD_CF4;
+    cfg->precision = SPINSIM_PREC_FP32_BULK;
+    cfg->rotating_frame = 1;
+    cfg->trotter_squares = -1;
+    return SPINSIM_OK;
+}
+
+int spinsim_create(const spinsim_config* cfg, spinsim_handle* out)
+{
+    if (!cfg || !out) return SPINSIM_E_ARG;
+    *out = nullptr;
+    if (cfg->method < 0 || cfg->method > 2 || cfg->precision < 0 || cfg->precision > 1 ||
+        cfg->trotter_squares < -1 || cfg->trotter_squares > 40 ||
+        !(cfg->lanes_per_sample == 0 || cfg->lanes_per_sample == 1 || cfg->lanes_per_sample == 2 ||
+          cfg->lanes_per_sample == 4) ||
+        !(cfg->threads_per_block == 0 || cfg->threads_per_block == 64 || cfg->threads_per_block == 128 ||
+          cfg->threads_per_block == 256) ||
+        cfg->mem_budget < 0)
+        return SPINSIM_E_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        return SPINSIM_E_CUDA;
+    }
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return SPINSIM_E_CUDA;
+    spinsim_s* h = new (std::nothrow) spinsim_s();
+    if (!h) return SPINSIM_E_NOMEM;
+    h->cfg = *cfg;
+    h->device = cfg->device;
+    h->tau = cfg->trotter_squares >= 0 ? cfg->trotter_squares
+                                      : (cfg->precision == SPINSIM_PREC_FP64 ? 24 : SPINSIM_FP32_DEFAULT_TAU);
+    cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete h;
+        return SPINSIM_E_CUDA;
+    }
+    h->budget = cfg->mem_budget > 0 ? (size_t)cfg->mem_budget : (size_t)(0.9 * (double)free_b);
+    if (cudaStreamCreateWithFlags(&h->work, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_pinned, cudaEventDisableTiming) != cudaSuccess) {
+        spinsim_destroy(h);
+        return SPINSIM_E_CUDA;
+    }
+    *out = h;
+    return SPINSIM_OK;
+}
+
+void spinsim_destroy(spinsim_handle h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    drop_graph(h);
+    for (Slot& s : h->slots) {
+        if (s.arena.buf.p) cudaFree(s.arena.buf.p);
+        if (s.pinned.p) cudaFreeHost(s.pinned.p);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.stream) cudaStreamDestroy(s.stream);
+    }
+    if (h->arena.buf.p) cudaFree(h->arena.buf.p);
+    if (h->pinned.p) cudaFreeHost(h->pinned.p);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->ev_pinned) cudaEventDestroy(h->ev_pinned);
+    if (h->work) cudaStreamDestroy(h->work);
+    delete h;
+}
+
+int spinsim_counts(const spinsim_request* req, int64_t* K, int64_t* L)
+{
+    Checked c = check_request(req);
+    if (c.status != SPINSIM_OK) return c.status;
+    if (K) *K = c.K;
+    if (L) *L = c.L;
+    return SPINSIM_OK;
+}
+
+int64_t spinsim_footprint(spinsim_handle h, const spinsim_request* reqs, int64_t n)
+{
+    if (!h || (n > 0 && !reqs) || n < 0) return SPINSIM_E_ARG;
+    int64_t samples[3] = {0, 0, 0}, chunks[3] = {0, 0, 0}, count[3] = {0, 0, 0};
+    for (int64_t i = 0; i < n; i++) {
+        Checked c = check_request(&reqs[i]);
+        if (c.status != SPINSIM_OK) return c.status;
+        samples[reqs[i].spin_x2] += c.K;
+        chunks[reqs[i].spin_x2] += (c.K + kChunk - 1) / kChunk;
+        count[reqs[i].spin_x2] += 1;
+    }
+    int64_t total = 0;
+    for (int s = 1; s <= 2; s++)
+        if (count[s]) total += (int64_t)group_bytes(s, count[s], samples[s], chunks[s]);
+    return total;
+}
+
+int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_result* res, int64_t n, void* stream_v)
+{
+    if (!h || n < 0 || (n > 0 && (!reqs || !res))) return SPINSIM_E_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SPINSIM_E_CUDA;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    std::vector<Checked> checked((size_t)n);
+    int first_err = SPINSIM_OK;
+    for (int64_t i = 0; i < n; i++) {
+        checked[i] = check_request(&reqs[i]);
+        if (checked[i].status == SPINSIM_OK) {
+            if (!res[i].states) checked[i].status = SPINSIM_E_ARG;
+            else if (res[i].capacity < checked[i].K) checked[i].status = SPINSIM_E_CAPACITY;
+        }
+        res[i].status = checked[i].status;
+        res[i].flags = checked[i].flags;
+        res[i].n_samples = checked[i].status == SPINSIM_OK ? checked[i].K : 0;
+        if (checked[i].status != SPINSIM_OK && first_err == SPINSIM_OK) first_err = checked[i].status;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusNone;
+    }
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    h->last = spinsim_launch_info{};
+    h->last.trotter_squares = h->tau;
+    int kernels = 0;
+    int st = SPINSIM_OK;
+    if (h->cfg.use_graphs && !capturing) {
+        // Run on the internal stream, joined to the caller's stream by events.
+        std::vector<uint64_t> sig = batch_signature(reqs, res, n, checked);
+        if (cudaEventRecord(h->ev_in, stream) != cudaSuccess || cudaStreamWaitEvent(h->work, h->ev_in, 0) != cudaSuccess)
+            return SPINSIM_E_CUDA;
+        Plan plan;
+        build_plan(reqs, res, n, checked, false, plan);
+        if (h->graph_exec && sig == h->graph_sig) {
+            // same shape: refresh the pinned parameter table and replay
+            st = refresh_table(h, reqs, res, checked, plan, static_cast<char*>(h->arena.buf.p), h->pinned,
+                               h->ev_pinned, false);
+            if (st != SPINSIM_OK) return st;
+            if (cudaGraphLaunch(h->graph_exec, h->work) != cudaSuccess) return SPINSIM_E_CUDA;
+            cudaEventRecord(h->ev_pinned, h->work);
+            h->last = h->graph_info;
+            h->last.graph_replayed = 1;
+            kernels = h->graph_kernels;
+        } else {
+            drop_graph(h);
+            // first run eagerly: sizes scratch and tunes the launch shape
+            st = run_batch(h, reqs, res, checked, plan, h->work, h->arena, h->pinned, h->ev_pinned, false, &kernels);
+            if (st != SPINSIM_OK) return st;
+            if (cudaStreamSynchronize(h->work) != cudaSuccess) return SPINSIM_E_CUDA;
+            // then capture the same batch for later replays
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                int k2 = 0;
+                int st2 = run_batch(h, reqs, res, checked, plan, h->work, h->arena, h->pinned, nullptr, true, &k2);
+                cudaError_t ec = cudaStreamEndCapture(h->work, &graph);
+                if (st2 == SPINSIM_OK && ec == cudaSuccess && graph) {
+                    if (cudaGraphInstantiate(&h->graph_exec, graph, 0) == cudaSuccess) {
+                        h->graph_sig = sig;
+                        h->graph_kernels = k2;
+                        h->graph_info = h->last;
+                    } else {
+                        h->graph_exec = nullptr;
+                    }
+                }
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+            } else {
+                cudaGetLastError();
+            }
+            cudaEventRecord(h->ev_pinned, h->work);
+        }
+        if (cudaEventRecord(h->ev_out, h->work) != cudaSuccess || cudaStreamWaitEvent(stream, h->ev_out, 0) != cudaSuccess)
+            return SPINSIM_E_CUDA;
+    } else {
+        Plan plan;
+        build_plan(reqs, res, n, checked, capturing, plan);
+        st = run_batch(h, reqs, res, checked, plan, stream, h->arena, h->pinned, capturing ? nullptr : h->ev_pinned,
+                       capturing, &kernels);
+        if (st != SPINSIM_OK) return st;
+    }
+    h->last.kernels_launched = kernels;
+    if (cudaGetLastError() != cudaSuccess) return SPINSIM_E_CUDA;
+    return first_err;
+}
+
+int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info)
+{
+    if (!h || !info) return SPINSIM_E_ARG;
+    *info = h->last;
+    return SPINSIM_OK;
+}
+
+// ------------------------------------------------------------------ serving
+static int serving_init(spinsim_s* h)
+{
+    if (!h->slots.empty()) return SPINSIM_OK;
+    const int n_slots = 4;
+    h->slots.resize(n_slots);
+    for (Slot& s : h->slots) {
+        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess)
+            return SPINSIM_E_CUDA;
+    }
+    return SPINSIM_OK;
+}
+
+static size_t request_bytes(const spinsim_request& r, const Checked& c)
+{
+    return group_bytes(r.spin_x2, 1, c.K, (c.K + kChunk - 1) / kChunk);
+}
+
+// Retire finished batches, then launch pending requests on free slots while
+// the memory budget admits them (FIFO: the head waits until it fits).
+static int serving_pump(spinsim_s* h)
+{
+    for (size_t si = 0; si < h->slots.size(); si++) {
+        Slot& s = h->slots[si];
+        if (!s.busy) continue;
+        cudaError_t q = cudaEventQuery(s.done);
+        if (q == cudaErrorNotReady) continue;
+        const int st = q == cudaSuccess ? SPINSIM_OK : SPINSIM_E_CUDA;
+        for (int64_t t : s.tickets) {
+            auto it = h->tickets.find(t);
+            if (it == h->tickets.end()) continue;
+            it->second.state = 2;
+            if (st != SPINSIM_OK) it->second.res->status = st;
+        }
+        s.tickets.clear();
+        h->bytes_in_flight -= s.in_flight;
+        s.in_flight = 0;
+        s.busy = false;
+    }
+    for (size_t si = 0; si < h->slots.size() && !h->pending.empty(); si++) {
+        Slot& s = h->slots[si];
+        if (s.busy) continue;
+        std::vector<spinsim_request> reqs;
+        std::vector<spinsim_result> res;
+        std::vector<int64_t> ids;
+        std::vector<Checked> checked;
+        size_t bytes = 0;
+        while (!h->pending.empty()) {
+            const int64_t t = h->pending.front();
+            Ticket& tk = h->tickets[t];
+            if (h->bytes_in_flight + bytes + tk.bytes > h->budget && !ids.empty()) break;
+            if (h->bytes_in_flight + bytes + tk.bytes > h->budget && h->bytes_in_flight > 0) break;
+            h->pending.pop_front();
+            reqs.push_back(tk.req);
+            res.push_back(*tk.res);
+            ids.push_back(t);
+            Checked c = check_request(&tk.req);
+            checked.push_back(c);
+            bytes += tk.bytes;
+        }
+        if (ids.empty()) break;
+        int kernels = 0;
+        Plan plan;
+        build_plan(reqs.data(), res.data(), (int64_t)reqs.size(), checked, false, plan);
+        int st = run_batch(h, reqs.data(), res.data(), checked, plan, s.stream, s.arena, s.pinned, s.done, false,
+                           &kernels);
+        for (size_t q = 0; q < ids.size(); q++) {
+            Ticket& tk = h->tickets[ids[q]];
+            tk.state = 1;
+            tk.slot = (int)si;
+            if (st != SPINSIM_OK) tk.res->status = st;
+        }
+        if (cudaEventRecord(s.done, s.stream) != cudaSuccess) return SPINSIM_E_CUDA;
+        s.tickets = ids;
+        s.busy = true;
+        s.in_flight = bytes;
+        h->bytes_in_flight += bytes;
+    }
+    return SPINSIM_OK;
+}
+
+int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result* res, int64_t* ticket)
+{
+    if (!h || !req || !res || !ticket) return SPINSIM_E_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SPINSIM_E_CUDA;
+    int st = serving_init(h);
+    if (st != SPINSIM_OK) return st;
+    Checked c = check_request(req);
+    if (c.status == SPINSIM_OK) {
+        if (!res->states) c.status = SPINSIM_E_ARG;
+        else if (res->capacity < c.K) c.status = SPINSIM_E_CAPACITY;
+    }
+    res->status = c.status;
+    res->flags = c.flags;
+    res->n_samples = c.status == SPINSIM_OK ? c.K : 0;
+    const int64_t id = h->next_ticket++;
+    Ticket tk;
+    tk.req = *req;
+    tk.res = res;
+    tk.slot = -1;
+    tk.bytes = c.status == SPINSIM_OK ? request_bytes(*req, c) : 0;
+    if (c.status != SPINSIM_OK) {
+        tk.state = 2;
+        h->tickets[id] = tk;
+        *ticket = id;
+        return c.status;
+    }
+    if (tk.bytes > h->budget) {
+        res->status = SPINSIM_E_NOMEM;
+        tk.state = 2;
+        h->tickets[id] = tk;
+        *ticket = id;
+        return SPINSIM_E_NOMEM;
+    }
+    tk.state = 0;
+    h->tickets[id] = tk;
+    h->pending.push_back(id);
+    *ticket = id;
+    return serving_pump(h);
+}
+
+int spinsim_poll(spinsim_handle h, int64_t ticket, int32_t wait_us)
+{
+    if (!h) return SPINSIM_E_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SPINSIM_E_CUDA;
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        int st = serving_pump(h);
+        if (st != SPINSIM_OK) return st;
+        auto it = h->tickets.find(ticket);
+        if (it == h->tickets.end()) return SPINSIM_E_ARG;
+        if (it->second.state == 2) {
+            h->tickets.erase(it);
+            return SPINSIM_OK;
+        }
+        if (wait_us <= 0) return SPINSIM_PENDING;
+        auto dt = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (dt >= wait_us) return SPINSIM_E_TIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+}  // extern "C"

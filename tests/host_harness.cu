@@ -1,0 +1,93 @@
+// Host build of the kernels' per-thread arithmetic (device_math.cuh), so the
+// CPU test-suite can check it against the oracle and scipy without a GPU.
+#include <cstdint>
+#include "../paper_2204_05586_gb300/csrc/device_math.cuh"
+
+using namespace spinsim;
+
+template <typename R>
+static void full3(const Res3<R>& e, double* out)
+{
+    cx<R> F[3][3];
+    res3_full(e, F);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            out[2 * (3 * i + j)] = (double)F[i][j].r + (i == j ? 1.0 : 0.0);
+            out[2 * (3 * i + j) + 1] = (double)F[i][j].i;
+        }
+}
+
+extern "C" {
+// exp(-i (vx Jx + vy Jy + vz Jz + vq Q)) through the split-residual Lie-Trotter.
+void hh_expm_one(double vx, double vy, double vz, double vq, int tau, int fp32, double* out)
+{
+    const double qd3 = vq / 3.0 / std::ldexp(1.0, tau);
+    if (fp32) {
+        Res3<float> e;
+        expm_one_res<float>((float)vx, (float)vy, (float)vz, (float)qd3, tau, e);
+        full3(e, out);
+    } else {
+        Res3<double> e;
+        expm_one_res<double>(vx, vy, vz, qd3, tau, e);
+        full3(e, out);
+    }
+}
+// rest part only (U - I - F(v)) in double
+void hh_expm_one_rest(double vx, double vy, double vz, double vq, int tau, double* out)
+{
+    Res3<double> e;
+    expm_one_res<double>(vx, vy, vz, vq / 3.0 / std::ldexp(1.0, tau), tau, e);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) { out[2 * (3 * i + j)] = e.m[i][j].r; out[2 * (3 * i + j) + 1] = e.m[i][j].i; }
+}
+void hh_expm_half(double vx, double vy, double vz, int fp32, double* out)
+{
+    double a_r, a_i, b_r, b_i;
+    if (fp32) {
+        Res2<float> e; cx<float> a, b;
+        expm_half_res<float>((float)vx, (float)vy, (float)vz, e);
+        res2_full(e, a, b);
+        a_r = a.r; a_i = a.i; b_r = b.r; b_i = b.i;
+    } else {
+        Res2<double> e; cx<double> a, b;
+        expm_half_res<double>(vx, vy, vz, e);
+        res2_full(e, a, b);
+        a_r = a.r; a_i = a.i; b_r = b.r; b_i = b.i;
+    }
+    // [[alpha, -conj(beta)], [beta, conj(alpha)]]
+    double al_r = 1.0 + a_r, al_i = a_i;
+    double m[8] = {al_r, al_i, -b_r, b_i, b_r, b_i, al_r, -al_i};
+    for (int i = 0; i < 8; i++) out[i] = m[i];
+}
+// product of two split residuals given as exponent vectors: exp(-i vB.A) exp(-i vA.A)
+void hh_product_one(const double* vA, const double* vB, int tau, double* out)
+{
+    Res3<double> a, b, c;
+    expm_one_res<double>(vA[0], vA[1], vA[2], vA[3] / 3.0 / std::ldexp(1.0, tau), tau, a);
+    expm_one_res<double>(vB[0], vB[1], vB[2], vB[3] / 3.0 / std::ldexp(1.0, tau), tau, b);
+    res3_mul(b, a, c);
+    full3(c, out);
+}
+void hh_product_half(const double* vA, const double* vB, double* out)
+{
+    Res2<double> a, b, c;
+    expm_half_res<double>(vA[0], vA[1], vA[2], a);
+    expm_half_res<double>(vB[0], vB[1], vB[2], b);
+    res2_mul(b, a, c);
+    cx<double> al, be;
+    res2_full(c, al, be);
+    double m[8] = {1.0 + al.r, al.i, -be.r, be.i, be.r, be.i, 1.0 + al.r, -al.i};
+    for (int i = 0; i < 8; i++) out[i] = m[i];
+}
+void hh_node_phasor_sum(double th, int64_t L, double W1, double c1, double W2, double c2, double* out)
+{
+    cx<double> z = node_phasor_sum(th, L, W1, c1, W2, c2);
+    out[0] = z.r;
+    out[1] = z.i;
+}
+void hh_small_sincos_m(double x, int fp32, double* out)
+{
+    if (fp32) { float s, c; small_sincos_m<float>((float)x, s, c); out[0] = s; out[1] = c; }
+    else { double s, c; small_sincos_m<double>(x, s, c); out[0] = s; out[1] = c; }
+}
+}

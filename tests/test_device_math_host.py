@@ -1,0 +1,147 @@
+"""The kernels' per-thread arithmetic (csrc/device_math.cuh), compiled for the
+host by nvcc, against the oracle and scipy on the CPU: the split-residual
+Lie-Trotter exponential, the SU(2) closed form, residual products and the
+closed-form node-phasor sums used for the exact first-order part."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+from test_oracle_expm import JX1, JY1, JZ1, Q1, SX, SY, SZ
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+DP = ctypes.POINTER(ctypes.c_double)
+
+
+@pytest.fixture(scope="module")
+def hh(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    out = str(tmp_path_factory.mktemp("hh") / "libhh.so")
+    subprocess.check_call([nvcc, "-O2", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-shared",
+                           "-I", os.path.join(ROOT, "include"), os.path.join(HERE, "host_harness.cu"), "-o", out])
+    L = ctypes.CDLL(out)
+    L.hh_expm_one.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.c_int, DP]
+    L.hh_expm_one_rest.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, DP]
+    L.hh_expm_half.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int, DP]
+    L.hh_product_one.argtypes = [DP, DP, ctypes.c_int, DP]
+    L.hh_product_half.argtypes = [DP, DP, DP]
+    L.hh_node_phasor_sum.argtypes = [ctypes.c_double, ctypes.c_int64] + [ctypes.c_double] * 4 + [DP]
+    L.hh_small_sincos_m.argtypes = [ctypes.c_double, ctypes.c_int, DP]
+    return L
+
+
+def P(a):
+    return a.ctypes.data_as(DP)
+
+
+def H1(v):
+    return v[0] * JX1 + v[1] * JY1 + v[2] * JZ1 + v[3] * Q1
+
+
+@pytest.mark.parametrize("scale", [1e-4, 1e-2, 0.3, 1.0])
+def test_expm_one_matches_oracle_and_scipy(hh, oracle_mod, scale):
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        v = rng.normal(size=4) * scale
+        for tau in (0, 3, 8, 24):
+            out = np.zeros(18)
+            hh.hh_expm_one(*v, tau, 0, P(out))
+            E = out.view(np.complex128).reshape(3, 3)
+            ref = oracle_mod.expm_spin_one(*v, 1.0, tau)   # same tau: same Lie-Trotter approximant
+            assert np.abs(E - ref).max() < 1e-14 * max(1.0, scale * 10), (scale, tau)
+        assert np.abs(E - sl.expm(-1j * H1(v))).max() < 3e-15
+
+
+def test_expm_one_rest_is_higher_order(hh):
+    """The rest of exp(-i v.A) - I after removing -i v.A is O(|v|^2) and is
+    carried with full relative precision (50-digit mpmath reference)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    v = np.array([0.3, -0.2, 0.5, 0.4])
+    for s in (1e-2, 1e-3, 1e-4):
+        out = np.zeros(18)
+        hh.hh_expm_one_rest(*(v * s), 24, P(out))
+        rest = out.view(np.complex128).reshape(3, 3)
+        Hm = mp.matrix(H1(v * s).tolist())
+        refm = mp.expm(-1j * Hm) - mp.eye(3) + 1j * Hm
+        ref = np.array([[complex(refm[i, j]) for j in range(3)] for i in range(3)])
+        assert np.abs(rest - ref).max() < 1e-13 * s * s
+        assert np.abs(rest).max() < s * s
+
+
+def test_expm_one_fp32(hh):
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        v = rng.normal(size=4) * 1e-3
+        out = np.zeros(18)
+        hh.hh_expm_one(*v, 4, 1, P(out))
+        E = out.view(np.complex128).reshape(3, 3)
+        ref = sl.expm(-1j * H1(v))
+        assert np.abs(E - ref).max() < 1e-9
+
+
+@pytest.mark.parametrize("scale", [1e-5, 1e-2, 0.5, 2.0])
+def test_expm_half(hh, scale):
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        v = rng.normal(size=3) * scale
+        ref = sl.expm(-1j * (v[0] * SX + v[1] * SY + v[2] * SZ) / 2)
+        for fp32, tol in ((0, 1e-15), (1, 3e-7)):
+            out = np.zeros(8)
+            hh.hh_expm_half(*v, fp32, P(out))
+            assert np.abs(out.view(np.complex128).reshape(2, 2) - ref).max() < tol * max(1.0, scale * scale)
+
+
+def test_residual_products(hh):
+    rng = np.random.default_rng(4)
+    for _ in range(10):
+        vA = rng.normal(size=4) * 0.1
+        vB = rng.normal(size=4) * 0.1
+        out = np.zeros(18)
+        hh.hh_product_one(P(vA), P(vB), 24, P(out))
+        ref = sl.expm(-1j * H1(vB)) @ sl.expm(-1j * H1(vA))   # later operator on the left
+        assert np.abs(out.view(np.complex128).reshape(3, 3) - ref).max() < 1e-15
+        out = np.zeros(8)
+        hh.hh_product_half(P(vA), P(vB), P(out))
+        ref = sl.expm(-0.5j * (vB[0] * SX + vB[1] * SY + vB[2] * SZ)) @ sl.expm(-0.5j * (vA[0] * SX + vA[1] * SY + vA[2] * SZ))
+        assert np.abs(out.view(np.complex128).reshape(2, 2) - ref).max() < 1e-15
+
+
+@pytest.mark.parametrize("th,L", [(0.0, 100), (3e-5, 100), (0.088, 100), (2 * np.pi + 1e-7, 37),
+                                  (6 * np.pi - 0.2, 50), (2 * np.pi, 10), (4 * np.pi, 11), (1.3, 1), (0.5, 2),
+                                  (-0.7, 1000)])
+def test_node_phasor_sum_closed_form(hh, th, L):
+    for (W1, c1, W2, c2) in ((0.5, 0.2113248654051871, 0.5, 0.7886751345948129), (1.0, 0.5, 0.0, 0.5),
+                             (0.5, 0.0, 0.5, 1.0)):
+        out = np.zeros(2)
+        hh.hh_node_phasor_sum(th, L, W1, c1, W2, c2, P(out))
+        l = np.arange(L)
+        ref = np.sum(W1 * np.exp(1j * th * (l + c1)) + W2 * np.exp(1j * th * (l + c2)))
+        assert abs(out[0] + 1j * out[1] - ref) < 1e-12 * max(1, L)
+
+
+def test_small_angle_functions(hh):
+    """sin x - x and cos x - 1 to full relative precision (50-digit mpmath)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    for x in (1e-9, -3e-5, 0.01, 0.0625, -0.2, 1.5):
+        out = np.zeros(2)
+        hh.hh_small_sincos_m(x, 0, P(out))
+        sm = float(mp.sin(mp.mpf(x)) - mp.mpf(x))
+        cm = float(mp.cos(mp.mpf(x)) - 1)
+        if abs(x) <= 0.0625:   # series branch: full relative precision
+            assert abs(out[0] - sm) <= 4e-16 * abs(sm)
+            assert abs(out[1] - cm) <= 4e-16 * abs(cm)
+        else:                  # libdevice branch: absolute precision of sin x
+            assert abs(out[0] - sm) <= 2e-16 * abs(x)
+            assert abs(out[1] - cm) <= 4e-16 * abs(cm)
+    out = np.zeros(2)
+    hh.hh_small_sincos_m(0.0, 0, P(out))
+    assert out[0] == 0.0 and out[1] == 0.0

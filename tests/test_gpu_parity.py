@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (max |psi_gpu - psi_oracle| over every sample and component):
+  FP64 path       1e-10   (both sides are FP64; differences are rounding order)
+  FP32-bulk path  1e-5    (against the oracle at its default tau = 24)
+Spin projections are compared at 2x the state tolerance (|<J>| error <=
+2 |dpsi| for normalised states).  Operators are compared entrywise.
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2204_05586_gb300 import spinsim as S, workloads as W  # noqa: E402
+
+THREADS = os.cpu_count() or 4
+TOL = {S.PREC_FP64: 1e-10, S.PREC_FP32_BULK: 1e-5}
+
+
+def oracle_run(O, req, tau=24, frame=True, method=0, want_ops=False, threads=THREADS):
+    return O.simulate(req["spin_x2"], req["field"], req["t_start"], req["t_end"], req["dt"], req["dt_out"],
+                      req["psi0"], rotating_frame=frame, tau=tau, method=method, want_ops=want_ops, threads=threads)
+
+
+def gpu_run(reqs, want_ops=False, **cfg):
+    with S.Simulator(**cfg) as sim:
+        outs = sim.simulate(reqs, want_ops=want_ops)
+        info = sim.last_launch()
+    return outs, info
+
+
+def assert_parity(out, ref, tol, what=""):
+    assert out["status"] == S.OK, (what, out["status"])
+    st = out["states"].cpu().numpy()
+    assert st.shape == ref["states"].shape, (what, st.shape, ref["states"].shape)
+    err = np.abs(st - ref["states"]).max() if st.size else 0.0
+    assert err <= tol, f"{what}: max |dpsi| = {err:.3e} > {tol:.0e}"
+    if out["spin"] is not None and st.size:
+        serr = np.abs(out["spin"].cpu().numpy() - ref["spin"]).max()
+        assert serr <= 2 * tol, f"{what}: max |d<J>| = {serr:.3e}"
+    return err
+
+
+# --------------------------------------------------------- full-size configs
+@pytest.mark.parametrize("prec", [S.PREC_FP64, S.PREC_FP32_BULK])
+def test_spin_half_rabi_full(oracle_mod, prec):
+    """Spin-half, 20 kHz bias, 2 x 1 kHz drive, 5 ms, 500 samples x 100 steps."""
+    req = W.spin_half_rabi()
+    (out,), _ = gpu_run([req], precision=prec)
+    assert_parity(out, oracle_run(oracle_mod, req), TOL[prec], "spin-half rabi")
+
+
+@pytest.mark.parametrize("prec", [S.PREC_FP64, S.PREC_FP32_BULK])
+def test_spin_one_sensing_full(oracle_mod, prec):
+    """Spin-one sensing workload at full size: 100 ms, 1e5 samples x 100 steps
+    (1e7 CF4 steps), compared on every sample."""
+    req = W.spin_one_sensing()
+    (out,), info = gpu_run([req], precision=prec)
+    ref = oracle_run(oracle_mod, req)
+    err = assert_parity(out, ref, TOL[prec], "spin-one sensing")
+    norms = np.linalg.norm(out["states"].cpu().numpy(), axis=1)
+    assert np.abs(norms - 1).max() < (1e-10 if prec == S.PREC_FP64 else 1e-9)
+    print(f"spin-one sensing prec={prec}: max|dpsi| = {err:.3e}, launch {info}")
+
+
+@pytest.mark.parametrize("prec", [S.PREC_FP64, S.PREC_FP32_BULK])
+def test_spin_one_operators(oracle_mod, prec):
+    req = W.spin_one_sensing(t_end=3e-4)
+    (out,), _ = gpu_run([req], want_ops=True, precision=prec)
+    ref = oracle_run(oracle_mod, req, want_ops=True)
+    dU = np.abs(out["ops"].cpu().numpy() - ref["ops"]).max()
+    assert dU <= (1e-12 if prec == S.PREC_FP64 else 1e-7), dU
+    U = out["ops"].cpu().numpy()
+    gram = np.einsum("kji,kjl->kil", U.conj(), U)
+    assert np.abs(gram - np.eye(3)).max() < 1e-13
+    assert np.abs(np.linalg.det(U) - 1).max() < 1e-12
+
+
+def test_fp32_matches_oracle_at_same_tau(oracle_mod):
+    req = W.spin_one_sensing(t_end=2e-3)
+    (out,), _ = gpu_run([req], precision=S.PREC_FP32_BULK)
+    assert_parity(out, oracle_run(oracle_mod, req, tau=S.FP32_DEFAULT_TAU), 1e-5, "fp32 vs oracle tau4")
+
+
+# ------------------------------------------------- methods, frames, fields
+@pytest.mark.parametrize("spin", [1, 2])
+@pytest.mark.parametrize("frame", [True, False])
+@pytest.mark.parametrize("method", [S.METHOD_CF4, S.METHOD_MIDPOINT, S.METHOD_HEUN])
+def test_methods_and_frames_fp64(oracle_mod, spin, frame, method):
+    f = W.field(bias_hz=300e3, drive_x_hz=3e3, drive_y_hz=1e3, drive_hz=300.2e3, drive_phase=0.7,
+                quad_hz=450.0 if spin == 2 else 0.0, pulses=[(120.0, 4e-4, 1e-4), (-60.0, 6e-4, 2e-4)])
+    rng = np.random.default_rng(3)
+    req = W.request(spin, f, 1e-4, 9e-4, 2e-8, 1e-6, psi0=W.random_state(spin + 1, rng))
+    (out,), _ = gpu_run([req], precision=S.PREC_FP64, method=method, rotating_frame=frame)
+    ref = oracle_run(oracle_mod, req, frame=frame, method=method)
+    assert_parity(out, ref, 1e-10, f"spin={spin} frame={frame} method={method}")
+
+
+@pytest.mark.parametrize("tau", [0, 3, 8])
+def test_trotter_squares_parameter(oracle_mod, tau):
+    req = W.spin_one_sensing(t_end=5e-4, dt=1e-7)
+    (out,), info = gpu_run([req], precision=S.PREC_FP64, tau=tau)
+    assert info["trotter_squares"] == tau
+    assert_parity(out, oracle_run(oracle_mod, req, tau=tau), 1e-10, f"tau={tau}")
+
+
+def test_large_angle_fallbacks(oracle_mod):
+    """Lab frame with few squarings: step angles beyond the series range."""
+    f = W.field(bias_hz=2e5, drive_x_hz=8e4, drive_hz=1.9e5, quad_hz=3e4)
+    req = W.request(2, f, 0.0, 2e-4, 5e-7, 1e-5)
+    (out,), _ = gpu_run([req], precision=S.PREC_FP64, rotating_frame=False, tau=2)
+    assert_parity(out, oracle_run(oracle_mod, req, tau=2, frame=False), 1e-10, "large angles")
+    req = W.request(1, f, 0.0, 2e-4, 5e-7, 1e-5)
+    (out,), _ = gpu_run([req], precision=S.PREC_FP64, rotating_frame=False)
+    assert_parity(out, oracle_run(oracle_mod, req, frame=False), 1e-10, "large angles half")
+
+
+# --------------------------------------------------------------- edge cases
+def test_edge_cases_in_one_batch(oracle_mod):
+    """K = 0, K = 1, L = 1, ragged chunk and run tails, K < 16, mixed spins,
+    and invalid requests that must not stop the valid ones."""
+    base = W.field(bias_hz=150e3, drive_x_hz=4e3, drive_hz=150.5e3, quad_hz=300.0, pulses=[(90.0, 3e-4, 1e-4)])
+    reqs = [
+        W.request(2, base, 0.0, 0.0, 1e-8, 1e-6),          # K = 0
+        W.request(2, base, 0.0, 1e-6, 1e-8, 1e-6),         # K = 1: only psi_0
+        W.request(1, base, 0.0, 7e-6, 1e-6, 1e-6),         # L = 1, K = 7
+        W.request(2, base, 2e-5, 2e-5 + 529e-6, 1e-7, 1e-6),   # K = 529: ragged chunk + run tail
+        W.request(1, base, 0.0, 1037e-6, 2.5e-7, 1e-6),    # K = 1037, L = 4
+        W.request(2, base, 0.0, 3e-6, 1e-6 / 3, 1e-6),     # L = 3: segments of 0, 1, 1, 1 steps
+        W.request(2, base, 0.0, 1e-5, 3e-7, 1e-6),         # invalid ratio
+        W.request(2, base, 0.0, 1e-5, 1e-8, 1e-6, psi0=[1.0, 0.5, 0.0]),  # not normalised
+    ]
+    with S.Simulator(precision=S.PREC_FP64) as sim:
+        outs = sim.allocate(reqs[:6] + [W.request(2, base, 0.0, 1e-5, 1e-7, 1e-6)] * 2)
+        res = sim.results_struct(outs)
+        arr = (S.spinsim_request * len(reqs))(*[S.make_request(q) for q in reqs])
+        st = S.spinsim_simulate(sim.handle, arr, res, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+    assert st == S.E_STEP_RATIO
+    assert res[6].status == S.E_STEP_RATIO and res[7].status == S.E_NORM
+    assert [r.n_samples for r in res[:6]] == [0, 1, 7, 529, 1037, 3]
+    for i in range(6):
+        r = reqs[i]
+        ref = oracle_run(oracle_mod, r)
+        view = S.Simulator._view(outs[i], res[i])
+        assert_parity(view, ref, 1e-10, f"edge case {i}")
+
+
+def test_capacity_error_and_spin_only_outputs(oracle_mod):
+    req = W.spin_half_rabi(t_end=1e-4)
+    with S.Simulator(precision=S.PREC_FP64) as sim:
+        outs = sim.allocate([req], want_spin=False)
+        outs[0]["K"] = 5        # too small
+        res = sim.results_struct(outs)
+        st = S.spinsim_simulate(sim.handle, [S.make_request(req)], res, 0)
+        torch.cuda.synchronize()
+    assert st == S.E_CAPACITY and res[0].status == S.E_CAPACITY
+
+
+# ------------------------------------------------------------- invariance
+def test_launch_shape_does_not_change_results():
+    req = W.spin_one_sensing(t_end=3e-3)
+    got = []
+    for lanes in (1, 2, 4):
+        for block in (64, 256):
+            (out,), info = gpu_run([req], precision=S.PREC_FP32_BULK, lanes=lanes, block=block)
+            assert info["lanes_per_sample"] == lanes and info["threads_per_block"] == block
+            got.append(out["states"].cpu().numpy())
+    for g in got[1:]:
+        assert np.array_equal(g, got[0])
+
+
+def test_alone_equals_in_batch():
+    reqs = W.sweep(24, t_min=1e-4, t_max=3e-3)
+    alone = []
+    for q in reqs[:4]:
+        (o,), _ = gpu_run([q], precision=S.PREC_FP32_BULK, lanes=4, block=128)
+        alone.append(o["states"].cpu().numpy())
+    outs, _ = gpu_run(reqs[::-1], precision=S.PREC_FP32_BULK, lanes=1, block=256)
+    for i in range(4):
+        assert np.array_equal(outs[len(reqs) - 1 - i]["states"].cpu().numpy(), alone[i])
+
+
+def test_host_buffers_match_device_buffers():
+    req = W.spin_one_sensing(t_end=2e-3)
+    (dev,), _ = gpu_run([req], precision=S.PREC_FP32_BULK)
+    with S.Simulator(precision=S.PREC_FP32_BULK) as sim:
+        outs = sim.allocate([req], want_ops=True, device="cpu", pin_memory=False)
+        res = sim.results_struct(outs)
+        st = S.spinsim_simulate(sim.handle, [S.make_request(req)], res, 0)
+        torch.cuda.synchronize()
+    assert st == S.OK
+    host = torch.view_as_complex(outs[0]["states"]).numpy()
+    assert np.array_equal(host, dev["states"].cpu().numpy())
+
+
+def test_graph_replay_matches_eager():
+    reqs = W.sweep(16, t_min=1e-4, t_max=2e-3)
+    eager, _ = gpu_run(reqs, precision=S.PREC_FP32_BULK, lanes=2, block=128)
+    with S.Simulator(precision=S.PREC_FP32_BULK, lanes=2, block=128, use_graphs=True) as sim:
+        outs = sim.allocate(reqs)
+        first = sim.simulate(reqs, outs=outs)
+        a = [o["states"].cpu().numpy().copy() for o in first]
+        for o in outs:
+            o["states"].zero_()
+        second = sim.simulate(reqs, outs=outs)
+        assert sim.last_launch()["graph_replayed"] == 1
+        b = [o["states"].cpu().numpy() for o in second]
+    for x, y, e in zip(a, b, eager):
+        assert np.array_equal(x, y) and np.array_equal(x, e["states"].cpu().numpy())
+
+
+# ------------------------------------------------------- batched sweep
+def test_sweep_full_size_sampled(oracle_mod):
+    """4096-simulation sweep at full size (FP32-bulk) in one launch: every
+    state stays normalised, and a stratified subset of simulations (shortest,
+    median, longest, and some between) matches the oracle on every sample."""
+    reqs = W.sweep(4096)
+    outs, info = gpu_run(reqs, precision=S.PREC_FP32_BULK)
+    assert all(o["status"] == S.OK for o in outs)
+    worst = 0.0
+    for o in outs[::97]:
+        worst = max(worst, float((o["states"].abs().pow(2).sum(1) - 1).abs().max()))
+    assert worst < 1e-9
+    T = np.array([q["t_end"] for q in reqs])
+    order = np.argsort(T)
+    pick = [order[0], order[1], order[len(order) // 4], order[len(order) // 2], order[-1]]
+    for i in pick:
+        ref = oracle_run(oracle_mod, reqs[i])
+        assert_parity(outs[i], ref, 1e-5, f"sweep sim {i} (T={T[i]:.4f})")
+
+
+# ------------------------------------------------------------------ serving
+def test_served_results_equal_alone():
+    arrivals, reqs = W.serving_stream(60, t_max=3e-3)
+    alone = []
+    for q in reqs:
+        (o,), _ = gpu_run([q], precision=S.PREC_FP32_BULK)
+        alone.append(o["states"].cpu().numpy())
+    with S.Simulator(precision=S.PREC_FP32_BULK) as sim:
+        outs = sim.allocate(reqs)
+        res = sim.results_struct(outs)
+        reqs_c = [S.make_request(q) for q in reqs]
+        tickets = []
+        for q, r in zip(reqs_c, res):
+            st, t = S.spinsim_submit(sim.handle, q, r)
+            assert st == S.OK
+            tickets.append(t)
+        for t in tickets:
+            assert S.spinsim_poll(sim.handle, t, 10_000_000) == S.OK
+        assert S.spinsim_poll(sim.handle, tickets[0], 0) == S.E_ARG   # forgotten once reported
+    for o, r, a in zip(outs, res, alone):
+        assert r.status == S.OK
+        assert np.array_equal(torch.view_as_complex(o["states"][:o["K"]]).cpu().numpy(), a)
