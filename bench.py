@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the CF4 spin integrator on GB300.
+
+Default workload (one "step" = one pass of the whole hot path over one batch):
+the spin-one sensing simulation -- 700 kHz bias, 2 x 1 kHz linear drive,
+q = 400 Hz, a 50 Hz Gaussian z pulse (1 ms wide, at 50 ms), 100 ms with
+delta_t = 10 ns and Delta_t = 1 us (1e5 samples x 100 CF4 steps) -- run in
+FP32-bulk precision with the FP64 chain, inputs resident on the device.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload sensing|sweep|serve] [--precision fp32|fp64]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs its own
+copy of the workload (weak scaling, no data-path collective); the timing is
+the maximum over ranks.  `--impl reference` times the FP64 CPU oracle on the
+host cores instead, on a bounded window of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin-one CF4 steps/s at ≤1e-5 state err vs FP64 oracle; p50/p99 served latency"
+UNIT = "steps/s"
+# Peak of the dominant kernel's bound: FP32 FMA throughput derived from the
+# unit counts and the maximum SM clock (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz).
+N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def algorithmic_flops_per_step(spin_x2: int, tau: int) -> float:
+    """Algorithmic FP32 flops of one CF4 step (FMA = 2 flops).
+
+    Spin-one: two Lie-Trotter exponentials with tau residual squarings of a
+    3x3 complex matrix (27 complex MACs = 216 flops each) plus ~100 flops to
+    build T, two 3x3 complex products (216 each) and the field at two nodes:
+    432 tau + 650.  Spin-half: ~200 flops per step."""
+    return 432.0 * tau + 650.0 if spin_x2 == 2 else 200.0
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return None
+        mhz = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": mhz[len(mhz) // 2] if mhz else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier_max(value: float, world: int):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2204_05586_gb300 import spinsim as S, workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    prec = S.PREC_FP32_BULK if args.precision == "fp32" else S.PREC_FP64
+    if args.workload == "sensing":
+        reqs = [W.spin_one_sensing()]
+        workload = ("spin-one sensing: bias 700 kHz, drive 2x1 kHz at 700 kHz, q 400 Hz, Gaussian z pulse "
+                    "50 Hz / 1 ms at 50 ms; 100 ms, dt 10 ns, dt_out 1 us (1e5 samples x 100 CF4 steps)")
+    elif args.workload == "sweep":
+        reqs = W.sweep(4096, seed=W.SEED + rank)
+        workload = ("batched spin-one sweep: 4096 simulations, bias U(600,800) kHz, Rabi U(0.5,2) kHz, detuning "
+                    "U(-500,500) Hz, q U(0,600) Hz, pulse U(0,100) Hz, T log-uniform [1,100] ms; dt 10 ns, dt_out 1 us")
+    else:
+        return run_serving(args, world, rank, local)
+    steps_per_pass = W.total_steps(reqs)
+    sim = S.Simulator(precision=prec, tau=args.tau, profile=True, device=local)
+    outs = sim.allocate(reqs, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        sim.simulate(reqs, outs=outs, sync=False)
+    torch.cuda.synchronize()
+    info = sim.last_launch()
+    tau = info["trotter_squares"]
+
+    # ---- timed region: K steps, L2 flushed between steps (outputs fit in L2)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    integ_ms, chain_ms, launches = [], [], 0
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        sim.simulate(reqs, outs=outs, sync=False)
+        ev[i][1].record(stream)
+        li = sim.last_launch()          # reads the library's kernel events (waits for them)
+        integ_ms.append(li["integrate_ms"])
+        chain_ms.append(li["chain_ms"])
+        launches += li["kernels_launched"]
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = barrier_max(sum(step_ms) / 1e3, world)
+    value = steps_per_pass * args.steps * world / total_s
+    ms_per_step = total_s * 1e3 / args.steps
+
+    # ---- roofline of the dominant kernel (integrate), from its live CUDA events
+    spin = reqs[0]["spin_x2"]
+    flops = algorithmic_flops_per_step(spin, tau) * steps_per_pass
+    mean_int = float(np.mean(integ_ms))
+    achieved = flops / (mean_int / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "integrate_kernel", "achieved": round(achieved, 3),
+                "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "traffic": None, "integrate_ms": round(mean_int, 4), "chain_ms": round(float(np.mean(chain_ms)), 4),
+                "flops_per_step": algorithmic_flops_per_step(spin, tau)}
+    if prec == S.PREC_FP64:
+        roofline.update({"peak": 1.25, "frac": round(achieved / 1.25, 4),
+                         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (profiling recipe table)"})
+
+    # ---- end to end through the C ABI with pinned host buffers
+    outs_h = sim.allocate(reqs, device="cpu", pin_memory=True)
+    sim.simulate(reqs, outs=outs_h, sync=True)
+    e2e_steps = max(3, min(args.steps, 200))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.simulate(reqs, outs=outs_h, sync=True)   # H2D of the tables, kernels, D2H of the outputs
+    e2e_s = barrier_max(time.perf_counter() - t0, world)
+    li = sim.last_launch()
+    e2e = {"value": steps_per_pass * e2e_steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(li["h2d_bytes"]), "d2h_bytes_per_step": int(li["d2h_bytes"]),
+           "steps": e2e_steps}
+    sim.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 bulk / f64 chain" if prec == S.PREC_FP32_BULK else "f64",
+            "data": "synthetic (seeded field parameters shaped like the paper's sensing benchmark)",
+            "config": {"workload": workload, "precision": args.precision, "trotter_squares": tau,
+                       "rotating_frame": True, "method": "CF4", "simulations_per_gpu": len(reqs),
+                       "cf4_steps_per_pass": steps_per_pass,
+                       "l2": "flushed between timed steps (256 MiB device write outside the step events)",
+                       "parallelism": f"weak x{world}, independent simulations per GPU"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "wall_s_timed_loop": wall}
+    if clk:
+        line["clocks"] = clk
+    # ---- rank 0: accuracy vs the FP64 oracle, oracle CPU baseline, FP64-plain kernel
+    if rank == 0 and args.workload == "sensing" and not args.no_cpu_baseline:
+        from oracle import oracle as O   # the CPU baseline leg: the oracle as it stands
+        O.build()
+        r = reqs[0]
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        ref = O.simulate(r["spin_x2"], r["field"], r["t_start"], r["t_end"], r["dt"], r["dt_out"], r["psi0"],
+                         threads=cores)
+        t_cpu = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": steps_per_pass / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "the full workload once (1e5 sample operators over all host cores, "
+                                          "then the sequential chain), tau = 24, FP64"}
+        gpu_states = torch.view_as_complex(outs[0]["states"][:outs[0]["K"]]).cpu().numpy()
+        line["state_err_vs_oracle"] = float(np.abs(gpu_states - ref["states"]).max())
+        if prec == S.PREC_FP32_BULK:
+            sim64 = S.Simulator(precision=S.PREC_FP64, device=local)
+            o64 = sim64.allocate(reqs, device=dev)
+            sim64.simulate(reqs, outs=o64)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                sim64.simulate(reqs, outs=o64, sync=False)
+            e1.record()
+            torch.cuda.synchronize()
+            fp64_rate = steps_per_pass * 3 / (e0.elapsed_time(e1) / 1e3)
+            s64 = torch.view_as_complex(o64[0]["states"][:o64[0]["K"]]).cpu().numpy()
+            line["fp64_plain"] = {"value": fp64_rate, "unit": UNIT, "state_err_vs_oracle":
+                                  float(np.abs(s64 - ref["states"]).max()),
+                                  "speedup_fp32_bulk_over_fp64": value / world / fp64_rate}
+            sim64.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ serving
+def run_serving(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2204_05586_gb300 import spinsim as S, workloads as W
+
+    torch.cuda.set_device(local)
+    n = args.serve_requests
+    arrivals, reqs = W.serving_stream(n, seed=W.SEED + 1 + rank)
+    sim = S.Simulator(precision=S.PREC_FP32_BULK, device=local)
+    outs = sim.allocate(reqs)
+    res = sim.results_struct(outs)
+    creqs = [S.make_request(q) for q in reqs]
+    # warm-up (tuning) on a few requests outside the measured stream
+    sim.simulate(reqs[:8], outs=outs[:8])
+    torch.cuda.synchronize()
+    lat = np.zeros(n)
+    done = np.zeros(n, dtype=bool)
+    tickets = {}
+    t0 = time.perf_counter()
+    nxt = 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    while not done.all():
+        now = time.perf_counter() - t0
+        while nxt < n and arrivals[nxt] <= now:
+            st, t = S.spinsim_submit(sim.handle, creqs[nxt], res[nxt])
+            tickets[t] = nxt
+            nxt += 1
+        for t in list(tickets):
+            if S.spinsim_poll(sim.handle, t, 0) == S.OK:
+                i = tickets.pop(t)
+                lat[i] = (time.perf_counter() - t0) - arrivals[i]
+                done[i] = True
+        if nxt < n and not tickets:
+            time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.001)))
+    span = time.perf_counter() - t0
+    clk = clocks.stop()
+    steps = W.total_steps(reqs)
+    line = {"metric": METRIC, "value": steps / span, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": 8,
+            "ms_per_step": span * 1e3 / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 bulk / f64 chain", "data": "synthetic",
+            "config": {"workload": f"served Poisson stream: {n} requests at 2000/s, 70% spin-one / 30% spin-half, "
+                                   "durations log-uniform [0.1,100] ms, dt 10 ns, dt_out 1 us, FP32-bulk"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                           "mean": float(lat.mean() * 1e3)},
+            "offered_steps_per_s": steps / float(arrivals[-1])}
+    if clk:
+        line["clocks"] = clk
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------- reference arm
+def run_reference(args, world, rank, local):
+    """The FP64 CPU oracle, as it stands, on the host cores: each step is a
+    bounded window (the first 1000 output samples, 99,900 CF4 steps) of the
+    same workload, sample operators over all cores then the sequential chain."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2204_05586_gb300 import workloads as W
+    O.build()
+    window = 1000
+    full = W.spin_one_sensing()
+    req = W.spin_one_sensing(t_end=window * full["dt_out"])
+    steps_per = W.total_steps([req])
+    cores = os.cpu_count() or 1
+
+    def one():
+        O.simulate(req["spin_x2"], req["field"], req["t_start"], req["t_end"], req["dt"], req["dt_out"],
+                   req["psi0"], threads=cores)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = time.perf_counter() - t0
+    value = steps_per * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded field parameters shaped like the paper's sensing benchmark)",
+            "config": {"workload": "spin-one sensing (same field as our arm); each step: the first 1000 output "
+                                   "samples (99,900 CF4 steps) of the 100 ms run, tau = 24"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "first 1000 of 1e5 output samples per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("sensing", "sweep", "serve"), default="sensing")
+    ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
+    ap.add_argument("--tau", type=int, default=-1)
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank, local)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -88,6 +88,9 @@ typedef struct {
     int32_t device;               /* CUDA device ordinal                                      */
     int64_t mem_budget;           /* bytes of device scratch the handle may hold; 0 = 90% of
                                      the free memory at spinsim_create                     */
+    int32_t profile;              /* 1: time the integrate and chain kernels of each call
+                                     with CUDA events (read by spinsim_last_launch)         */
+    int32_t reserved;
 } spinsim_config;
 
 #define SPINSIM_FP32_DEFAULT_TAU 4
@@ -184,7 +187,9 @@ int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result*
 int spinsim_poll(spinsim_handle h, int64_t ticket, int32_t wait_us);
 
 /* Launch shape the last spinsim_simulate call used for its integration
- * kernel, and how many kernels it launched (for benchmarking). */
+ * kernel, how many kernels it launched, the bytes it copied between host and
+ * device, and (with cfg.profile = 1, not for graph replays) the device time
+ * of its integrate and chain kernels.  Reading the times waits for them. */
 typedef struct {
     int32_t lanes_per_sample;
     int32_t threads_per_block;
@@ -192,6 +197,10 @@ typedef struct {
     int32_t kernels_launched;
     int32_t trotter_squares;
     int32_t graph_replayed;
+    int64_t h2d_bytes;            /* parameter tables uploaded                               */
+    int64_t d2h_bytes;            /* outputs copied back to host buffers                     */
+    double integrate_ms;          /* -1 when not profiled                                    */
+    double chain_ms;
 } spinsim_launch_info;
 int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info);
 

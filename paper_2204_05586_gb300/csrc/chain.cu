@@ -9,7 +9,7 @@
 //           P_l = B_l ... B_0 of the run products by a shuffle scan (Hillis-
 //           Steele, 5 levels) and stores each lane's exclusive prefix and the
 //           chunk product;
-//   carry:  one thread per simulation walks its chunk products in order and
+//   carry:  one warp per simulation walks its chunk products in order and
 //           stores the state entering every chunk;
 //   apply:  one warp per chunk; lane l forms the state entering its run from
 //           its exclusive prefix and walks its 16 samples, writing psi_k,
@@ -72,6 +72,16 @@ struct Op<3> {
                 m[i][j].i = __shfl_up_sync(0xffffffffu, m[i][j].i, d);
             }
     }
+    __device__ __forceinline__ void shfl_idx(int src)
+    {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                m[i][j].r = __shfl_sync(0xffffffffu, m[i][j].r, src);
+                m[i][j].i = __shfl_sync(0xffffffffu, m[i][j].i, src);
+            }
+    }
     // C = A B
     static __device__ __forceinline__ void mul(const Op& A, const Op& B, Op& C)
     {
@@ -122,6 +132,13 @@ struct Op<2> {
         a.i = __shfl_up_sync(0xffffffffu, a.i, d);
         b.r = __shfl_up_sync(0xffffffffu, b.r, d);
         b.i = __shfl_up_sync(0xffffffffu, b.i, d);
+    }
+    __device__ __forceinline__ void shfl_idx(int src)
+    {
+        a.r = __shfl_sync(0xffffffffu, a.r, src);
+        a.i = __shfl_sync(0xffffffffu, a.i, src);
+        b.r = __shfl_sync(0xffffffffu, b.r, src);
+        b.i = __shfl_sync(0xffffffffu, b.i, src);
     }
     // alpha = a1 a2 - conj(b1) b2, beta = b1 a2 + conj(a1) b2
     static __device__ __forceinline__ void mul(const Op& A, const Op& B, Op& C)
@@ -209,25 +226,46 @@ __global__ void __launch_bounds__(128) chain_reduce_kernel(ChainArgs a)
     }
 }
 
+// Carry: one warp per simulation.  The warp loads the products of 32
+// consecutive chunks at once (lane j holds chunk c0 + j), then walks them in
+// order, the state staying in every lane and each product being broadcast
+// from its lane by shuffles; lane j keeps the state entering its chunk and
+// the warp stores the 32 states together.
 template <int N>
-__global__ void chain_carry_kernel(ChainArgs a)
+__global__ void __launch_bounds__(128) chain_carry_kernel(ChainArgs a)
 {
     constexpr int OPD = N == 3 ? 18 : 4;
-    for (int si = blockIdx.x * blockDim.x + threadIdx.x; si < a.n_sims; si += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t si = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); si < a.n_sims; si += warps) {
         const DevSim& s = a.sims[si];
-        cx<double> psi[N], nxt[N];
+        cx<double> psi[N];
 #pragma unroll
         for (int i = 0; i < N; i++) psi[i] = cmk(s.psi0[2 * i], s.psi0[2 * i + 1]);
         const int64_t c0 = a.chunk_offsets[si], c1 = a.chunk_offsets[si + 1];
-        for (int64_t c = c0; c < c1; c++) {
-            double* st = a.chunk_start + c * (2 * N);
-#pragma unroll
-            for (int i = 0; i < N; i++) { st[2 * i] = psi[i].r; st[2 * i + 1] = psi[i].i; }
+        for (int64_t base = c0; base < c1; base += 32) {
+            const int cnt = (int)(c1 - base < 32 ? c1 - base : 32);
             Op<N> A;
-            A.load(a.chunk_agg + c * OPD);
-            A.apply(psi, nxt);
+            if (lane < cnt) A.load(a.chunk_agg + (base + lane) * OPD);
+            else A.identity();
+            cx<double> mine[N];
+            for (int j = 0; j < cnt; j++) {
+                if (lane == j) {
 #pragma unroll
-            for (int i = 0; i < N; i++) psi[i] = nxt[i];
+                    for (int i = 0; i < N; i++) mine[i] = psi[i];
+                }
+                Op<N> Aj = A;
+                Aj.shfl_idx(j);
+                cx<double> nxt[N];
+                Aj.apply(psi, nxt);
+#pragma unroll
+                for (int i = 0; i < N; i++) psi[i] = nxt[i];
+            }
+            if (lane < cnt) {
+                double* st = a.chunk_start + (base + lane) * (2 * N);
+#pragma unroll
+                for (int i = 0; i < N; i++) { st[2 * i] = mine[i].r; st[2 * i + 1] = mine[i].i; }
+            }
         }
     }
 }
@@ -258,12 +296,24 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
             u.apply(psi, nxt);
 #pragma unroll
             for (int i = 0; i < N; i++) psi[i] = nxt[i];
+            cx<double> w[N];
+            double scale = 1.0;
+            if (s.normalize_out) {
+                // FP32-bulk: the written state is renormalised in FP64
+                double n2 = 0.0;
+#pragma unroll
+                for (int i = 0; i < N; i++) n2 = fma(psi[i].r, psi[i].r, fma(psi[i].i, psi[i].i, n2));
+                const double d = n2 - 1.0;
+                scale = 1.0 - d * (0.5 - 0.375 * d);   // (1 + d)^(-1/2), |d| ~ 1e-9
+            }
+#pragma unroll
+            for (int i = 0; i < N; i++) w[i] = cscale(psi[i], scale);
             double2* sp = reinterpret_cast<double2*>(s.states + k * 2 * N);
 #pragma unroll
-            for (int i = 0; i < N; i++) sp[i] = make_double2(psi[i].r, psi[i].i);
+            for (int i = 0; i < N; i++) sp[i] = make_double2(w[i].r, w[i].i);
             if (s.spin) {
                 double jv[3];
-                spin_projection(psi, N, jv);
+                spin_projection(w, N, jv);
                 s.spin[k * 3 + 0] = jv[0];
                 s.spin[k * 3 + 1] = jv[1];
                 s.spin[k * 3 + 2] = jv[2];
@@ -285,7 +335,7 @@ static cudaError_t launch_chain_n(const ChainArgs& a, int n_sm, cudaStream_t str
     chain_reduce_kernel<N><<<grid, block, 0, stream>>>(args);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int cgrid = (int)std::min<int64_t>((a.n_sims + 127) / 128, (int64_t)n_sm * 8);
+    const int cgrid = (int)std::min<int64_t>((a.n_sims + 3) / 4, (int64_t)n_sm * 16);
     chain_carry_kernel<N><<<cgrid, 128, 0, stream>>>(args);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -135,22 +135,32 @@ struct SampleExact {
     double ph_re, ph_im;   // e^{-i w_r dt_out} (spin-one) or e^{-i w_r dt_out / 2} (spin-half)
     double eb_re, eb_im;   // e^{i beta}
     double dco, dct;       // w_d - w_r, w_d + w_r (rad/s)
+    double gsum;           // pulse part of w_r (rad/s)
 };
 
-template <typename R, int N>
-SPINSIM_HD void make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, SampleExact& x)
+// Drive phase beta = 2 pi frac(f_d t_{k-1}) + phase, in [-pi, pi] (FP64, a few ops).
+SPINSIM_HD double drive_phase_at(const DevSim& s, int64_t k)
 {
     const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;
     double cyc = s.drive_hz * t_prev;
     cyc -= floor(cyc);
     double beta = kTwoPi * cyc + s.drive_phase;
-    beta -= kTwoPi * rint(beta * (1.0 / kTwoPi));
-    double sb, cb;
-    sincos(beta, &sb, &cb);
-    c.ebr = (R)cb;
-    c.ebi = (R)sb;
-    x.eb_re = cb;
-    x.eb_im = sb;
+    return beta - kTwoPi * rint(beta * (1.0 / kTwoPi));
+}
+
+// Bulk context of interval k (every lane).  e^{i beta} comes from the bulk
+// type's sincos: the first-order part it feeds is replaced by the exact FP64
+// value at the end of the sample, so it only reaches second-order terms.
+// Returns gsum = sum_p amp_p ghat_p (exact products of R values, in FP64).
+template <typename R, int N>
+SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c)
+{
+    const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;
+    const double beta = drive_phase_at(s, k);
+    R sb, cb;
+    sincos((R)beta, &sb, &cb);
+    c.ebr = cb;
+    c.ebi = sb;
 #pragma unroll
     for (int i = 0; i < 4; i++) split_hi_lo<R>(s.P[i], c.Ph[i], c.Pl[i]);
     c.za = (R)s.za;
@@ -162,7 +172,7 @@ SPINSIM_HD void make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, SampleExac
     c.c2 = (R)s.c2;
     c.np = s.n_pulses;
     c.counter_on = s.counter_on != 0;
-    double gsum = 0.0;  // sum_p amp_p ghat_p, exact products of R values
+    double gsum = 0.0;
 #pragma unroll
     for (int p = 0; p < kMaxPulses; p++) {
         c.amp[p] = R(0); c.u0[p] = R(0); c.invw[p] = R(0); c.ghat[p] = R(0);
@@ -178,15 +188,34 @@ SPINSIM_HD void make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, SampleExac
             }
         }
     }
+    c.co = (R)(s.frame ? s.w_co0 - gsum : s.w_co0);
+    c.counter = (R)(s.frame ? s.w_counter0 + gsum : s.w_counter0);
+    return gsum;
+}
+
+// FP64 quantities of interval k used once per sample by the epilogue:
+// e^{i beta}, the frame frequencies and the exit phasor
+// e^{-i w_r dt_out} (x 1/2 for spin-half).
+//
+// With the frame on, w_r = 2 pi B + gsum where gsum = sum_p amp_p ghat_p uses
+// the pulse shapes at the interval midpoint rounded to R: the frame is an
+// exact change of variables for any constant w_r, and this one is exactly
+// the value the in-frame field subtracts, so leaving the frame undoes
+// entering it.
+template <int N>
+SPINSIM_HD void make_exact(const DevSim& s, int64_t k, double gsum, SampleExact& x)
+{
+    const double beta = drive_phase_at(s, k);
+    sincos(beta, &x.eb_im, &x.eb_re);
+    x.gsum = gsum;
     if (s.frame) {
         x.dco = s.w_co0 - gsum;
         x.dct = s.w_counter0 + gsum;
-        // e^{-i (2 pi B + gsum) dt_out (x 1/2 for spin-half)}: host phasor times e^{-i d}
         double d = gsum * s.dt_out * (N == 2 ? 0.5 : 1.0);
         double sd, cd;
         small_sincos<double>(d, sd, cd);
-        double br = N == 2 ? s.exit_half_re : s.exit_re;
-        double bi = N == 2 ? s.exit_half_im : s.exit_im;
+        const double br = N == 2 ? s.exit_half_re : s.exit_re;
+        const double bi = N == 2 ? s.exit_half_im : s.exit_im;
         x.ph_re = br * cd + bi * sd;       // (br + i bi)(cd - i sd)
         x.ph_im = bi * cd - br * sd;
     } else {
@@ -195,8 +224,6 @@ SPINSIM_HD void make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, SampleExac
         x.ph_re = 1.0;
         x.ph_im = 0.0;
     }
-    c.co = (R)x.dco;
-    c.counter = (R)x.dct;
 }
 
 // sum_{l=0}^{L-1} (W1 e^{i th (l + c1)} + W2 e^{i th (l + c2)})
@@ -227,18 +254,32 @@ SPINSIM_HD cx<double> node_phasor_sum(double th, int64_t L, double W1, double c1
     return cmk((W1 * ca + W2 * cb) * ratio, (W1 * sa + W2 * sb) * ratio);
 }
 
+// S(th0 + d) from the Taylor table T_m (m = 0..3):
+//   sum W_n e^{i (th0 + d) x} = T_0 + i d T_1 - d^2/2 T_2 - i d^3/6 T_3 + O((d x)^4).
+SPINSIM_HD cx<double> taylor_sum(const double* T, double d)
+{
+    const double h2 = -0.5 * d * d, h3 = -d * d * d * (1.0 / 6.0);
+    // T0 + i d T1 + h2 T2 + i h3 T3
+    return cmk(T[0] - d * T[3] + h2 * T[4] - h3 * T[7], T[1] + d * T[2] + h2 * T[5] + h3 * T[6]);
+}
+
 // Exact first-order transverse coefficients of U^r_k: the method's quadrature
 // sum over the sample of the in-frame drive,
 //   g_x + i g_y = dt [Om+ e^{i beta} S(w_d - w_r) + Om- conj(e^{i beta} S(w_d + w_r))],
-// S(w) = sum over steps and nodes of weight x e^{i w tau_node}.
+// S(w) = sum over steps and nodes of weight x e^{i w dt x_node}.  The frame's
+// pulse part shifts th0 by a tiny d = gsum dt; while |d| (L + 1) <= 1e-3 the
+// cubic Taylor series of the tables is exact to rounding, otherwise the
+// closed form is used.
 SPINSIM_HD void first_order_exact(const DevSim& s, const SampleExact& x, double& gx, double& gy)
 {
     const cx<double> eb = cmk(x.eb_re, x.eb_im);
-    cx<double> co = cmul(eb, node_phasor_sum(x.dco * s.dt, s.L, s.W1, s.c1, s.W2, s.c2));
-    cx<double> g = cscale(co, s.om_plus);
+    const double d = s.frame ? x.gsum * s.dt : 0.0;
+    const bool tay = s.tay_ok && fabs(d) * (double)(s.L + 1) <= 1e-3;
+    cx<double> sco = tay ? taylor_sum(s.tay_co, -d) : node_phasor_sum(x.dco * s.dt, s.L, s.W1, s.c1, s.W2, s.c2);
+    cx<double> g = cscale(cmul(eb, sco), s.om_plus);
     if (s.om_minus != 0.0) {
-        cx<double> ct = cmul(eb, node_phasor_sum(x.dct * s.dt, s.L, s.W1, s.c1, s.W2, s.c2));
-        g = cadd(g, cscale(cconj(ct), s.om_minus));
+        cx<double> sct = tay ? taylor_sum(s.tay_ct, d) : node_phasor_sum(x.dct * s.dt, s.L, s.W1, s.c1, s.W2, s.c2);
+        g = cadd(g, cscale(cconj(cmul(eb, sct)), s.om_minus));
     }
     gx = g.r * s.dt;
     gy = g.i * s.dt;
@@ -250,9 +291,9 @@ SPINSIM_HD void first_order_exact(const DevSim& s, const SampleExact& x, double&
 //   w_x' = w_x cos a + w_y sin a,  w_y' = -w_x sin a + w_y cos a
 // of w_x = Ax cos A, w_y = Ay sin A is, by product-to-sum identities,
 //   w_x' + i w_y' = Om+ e^{i (beta + (w_d - w_r) tau)} + Om- e^{-i (beta + (w_d + w_r) tau)}
-// with Om+- = (Ax +- Ay)/2.  The co-rotating phasor is e^{i beta} (FP64 per
-// sample) times a small rotation, so the slowly varying term never goes
-// through a large FP32 angle.
+// with Om+- = (Ax +- Ay)/2.  The co-rotating phasor is e^{i beta} times a
+// small rotation, so the slowly varying term never goes through a large
+// angle.
 template <typename R>
 struct NodeField {
     cx<R> co, ct;   // e^{i (beta + (w_d - w_r) tau)}, e^{i (beta + (w_d + w_r) tau)}

@@ -89,55 +89,16 @@ __device__ __forceinline__ void finish(const Res3<double>& P, const DevSim& s, c
     store_rows(Y, r, out);
 }
 
-// FP32-bulk: one Newton-Schulz step towards the nearest unitary, on the
-// residual: with U = I + Y and U^dagger U = I + E, E = Y + Y^dagger + Y^dagger Y,
-// U' = U (I - E/2) = I + Y - E/2 - Y E/2 has defect O(E^2); E is ~1e-11 here
-// and Y E/2 ~1e-13 is dropped.  Then det U' = e^{i phi} is computed from the
-// residual (det(I + Y) = 1 + tr Y + sum of principal 2x2 minors + det Y) and
-// divided out as e^{-i phi/3} (exact U_k have det 1: H is traceless).
+// FP32-bulk: the operator is stored as computed.  Its departure from
+// unitarity is of the order of the FP32 rounding of the second-order rest
+// (~1e-11 per sample); the chain renormalises every output state in FP64.
 __device__ __forceinline__ void finish(const Res3<float>& P, const DevSim& s, const SampleExact& x, double* out)
 {
     cx<double> Y[3][3];
     promote(P, s, x, Y);
-    double Er[3][3], Ei[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = i; j < 3; j++) {
-            double re = Y[i][j].r + Y[j][i].r;
-            double im = Y[i][j].i - Y[j][i].i;
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                re = fma(Y[k][i].r, Y[k][j].r, fma(Y[k][i].i, Y[k][j].i, re));
-                im = fma(Y[k][i].r, Y[k][j].i, fma(-Y[k][i].i, Y[k][j].r, im));
-            }
-            Er[i][j] = re; Ei[i][j] = im;
-            Er[j][i] = re; Ei[j][i] = -im;
-        }
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            Y[i][j].r -= 0.5 * Er[i][j];
-            Y[i][j].i -= 0.5 * Ei[i][j];
-        }
-    // d = det(I + Y) - 1
-    cx<double> d = cadd(cadd(Y[0][0], Y[1][1]), Y[2][2]);
-    d = cadd(d, csub(cmul(Y[0][0], Y[1][1]), cmul(Y[0][1], Y[1][0])));
-    d = cadd(d, csub(cmul(Y[0][0], Y[2][2]), cmul(Y[0][2], Y[2][0])));
-    d = cadd(d, csub(cmul(Y[1][1], Y[2][2]), cmul(Y[1][2], Y[2][1])));
-    const cx<double> m0 = csub(cmul(Y[1][1], Y[2][2]), cmul(Y[1][2], Y[2][1]));
-    const cx<double> m1 = csub(cmul(Y[1][0], Y[2][2]), cmul(Y[1][2], Y[2][0]));
-    const cx<double> m2 = csub(cmul(Y[1][0], Y[2][1]), cmul(Y[1][1], Y[2][0]));
-    d = cadd(d, cadd(csub(cmul(Y[0][0], m0), cmul(Y[0][1], m1)), cmul(Y[0][2], m2)));
-    const double phi = fabs(d.r) + fabs(d.i) < 1e-4 ? d.i / (1.0 + d.r) : atan2(d.i, 1.0 + d.r);
-    double sp, cp;
-    small_sincos<double>(phi * (1.0 / 3.0), sp, cp);
-    const cx<double> fix = cmk(cp, -sp);
 #pragma unroll
     for (int i = 0; i < 3; i++) Y[i][i].r += 1.0;
-    const cx<double> p = cmk(x.ph_re, x.ph_im);
-    const cx<double> r[3] = {cmul(p, fix), fix, cmul(cconj(p), fix)};
+    const cx<double> r[3] = {cmk(x.ph_re, x.ph_im), cmk(1.0, 0.0), cmk(x.ph_re, -x.ph_im)};
     store_rows(Y, r, out);
 }
 
@@ -167,17 +128,13 @@ __device__ __forceinline__ void finish(const Res2<double>& P, const DevSim& s, c
     store_half(cmk(1.0 + a.r, a.i), b, x, out);
 }
 
-// FP32-bulk spin-half: rescale (alpha, beta) to |alpha|^2 + |beta|^2 = 1 in FP64
-// (an SU(2) element in this form always has det 1).
+// FP32-bulk spin-half: stored as computed (see the spin-one case); an SU(2)
+// element in this form always has det 1.
 __device__ __forceinline__ void finish(const Res2<float>& P, const DevSim& s, const SampleExact& x, double* out)
 {
     cx<double> a, b;
     promote(P, s, x, a, b);
-    const double d = 2.0 * a.r + a.r * a.r + a.i * a.i + b.r * b.r + b.i * b.i;   // |alpha|^2 + |beta|^2 - 1
-    double sc;
-    if (fabs(d) < 1e-4) sc = 1.0 - d * (0.5 - d * (0.375 - d * 0.3125));  // (1 + d)^(-1/2)
-    else sc = 1.0 / sqrt(1.0 + d);
-    store_half(cmk(sc + sc * a.r, sc * a.i), cmk(sc * b.r, sc * b.i), x, out);
+    store_half(cmk(1.0 + a.r, a.i), b, x, out);
 }
 
 __device__ __forceinline__ void store_identity(int N, double* out)
@@ -225,11 +182,11 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
             si = find_index(a.sample_offsets, a.n_sims, g);
             k = g - a.sample_offsets[si];
         }
-        SampleExact sx;
+        double gsum = 0.0;
         if (active && k > 0) {
             const DevSim& s = a.sims[si];
             SampleCtx<R> c;
-            make_ctx<R, N>(s, k, c, sx);
+            gsum = make_ctx<R, N>(s, k, c);
             const int64_t L = s.L;
 #pragma unroll 1
             for (int q = 0; q < SEG_PER_LANE; q++) {
@@ -257,7 +214,10 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
                 res_mul(seg[slot * kSegments + 1], seg[slot * kSegments + 0], P01);
                 res_mul(seg[slot * kSegments + 3], seg[slot * kSegments + 2], P23);
                 res_mul(P23, P01, P);
-                finish(P, a.sims[si], sx, out);
+                const DevSim& s = a.sims[si];
+                SampleExact sx;
+                make_exact<N>(s, k, gsum, sx);
+                finish(P, s, sx, out);
             }
         }
         __syncwarp();

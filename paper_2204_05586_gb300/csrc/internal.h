@@ -36,6 +36,13 @@ struct DevSim {
     double om_plus, om_minus;    // Om+, Om- (rad/s)
     double W1, W2;               // total quadrature weight of nodes 1 and 2 over one step
     double gq;                   // exact first-order Q coefficient of one sample: w_q dt_out
+    // Node-phasor sums S(th) = sum_{l<L, n=1,2} W_n e^{i th x}, x = l + c_n, of the
+    // co-rotating (th0 = (w_co0) dt) and counter-rotating (th0 = (w_counter0) dt)
+    // drive terms as Taylor coefficients T_m = sum W_n x^m e^{i th0 x}, m = 0..3,
+    // re/im interleaved; a sample shifts th0 by -+ gsum dt (pulse part of w_r).
+    double tay_co[8], tay_ct[8];
+    int32_t tay_ok;              // 1 when the tables were built (L <= 65536)
+    int32_t normalize_out;       // FP32-bulk: write psi_k renormalised in FP64
     double exit_re, exit_im;     // e^{-i 2 pi B dt_out} (frame) or 1
     double exit_half_re, exit_half_im;  // e^{-i pi B dt_out} (frame) or 1
     double amp[kMaxPulses];      // 2 pi A_p, rad/s

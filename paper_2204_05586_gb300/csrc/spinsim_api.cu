@@ -191,6 +191,9 @@ struct spinsim_s {
     cudaGraphExec_t graph_exec = nullptr;
     int graph_kernels = 0;
     spinsim_launch_info graph_info{};
+    // profiling: per spin group, events before integrate, after integrate, after chain
+    cudaEvent_t prof[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int prof_groups = 0;
     // serving
     std::vector<Slot> slots;
     std::deque<int64_t> pending;
@@ -402,6 +405,28 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
             d.W1 = n_exp == 2 ? wa + wb : wa;
             d.W2 = n_exp == 2 ? wa + wb : wb;
             d.gq = r.spin_x2 == 2 ? two_pi * f.quad_hz * r.dt_out : 0.0;
+            d.normalize_out = h->cfg.precision == SPINSIM_PREC_FP32_BULK ? 1 : 0;
+            // Taylor tables of the node-phasor sums (direct FP64 summation)
+            d.tay_ok = d.L <= 65536 ? 1 : 0;
+            if (d.tay_ok) {
+                const double th_co = d.w_co0 * d.dt, th_ct = d.w_counter0 * d.dt;
+                double co[8] = {0}, ct[8] = {0};
+                const double Wn[2] = {d.W1, d.W2}, cn[2] = {d.c1, d.c2};
+                for (int64_t l = 0; l < d.L; l++)
+                    for (int nn = 0; nn < 2; nn++) {
+                        if (Wn[nn] == 0.0) continue;
+                        const double x = (double)l + cn[nn];
+                        double pw = Wn[nn];
+                        const double sa = std::sin(th_co * x), ca = std::cos(th_co * x);
+                        const double sb = std::sin(th_ct * x), cb = std::cos(th_ct * x);
+                        for (int m = 0; m < 4; m++) {
+                            co[2 * m] += pw * ca; co[2 * m + 1] += pw * sa;
+                            ct[2 * m] += pw * cb; ct[2 * m + 1] += pw * sb;
+                            pw *= x;
+                        }
+                    }
+                for (int m = 0; m < 8; m++) { d.tay_co[m] = co[m]; d.tay_ct[m] = ct[m]; }
+            }
             d.n_pulses = f.n_pulses;
             for (int p = 0; p < f.n_pulses; p++) {
                 d.amp[p] = two_pi * f.pulse_amp_hz[p];
@@ -580,6 +605,8 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
                             stream) != cudaSuccess)
             return SPINSIM_E_CUDA;
         pin += tbl;
+        h->last.h2d_bytes += (int64_t)tbl;
+        const int pg = (h->cfg.profile && !capturing && h->prof_groups < 2) ? h->prof_groups++ : -1;
         if (pinned_free && cudaEventRecord(pinned_free, stream) != cudaSuccess) return SPINSIM_E_CUDA;
         IntegrateArgs ia;
         ia.sims = reinterpret_cast<const DevSim*>(base + g.sims_off);
@@ -597,9 +624,11 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             ia.n_tiles = (g.samples + spb - 1) / spb;
             if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
                 return SPINSIM_E_CUDA;
+            if (pg >= 0) cudaEventRecord(h->prof[pg][0], stream);
             if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, lanes, block, grid, ia, stream) !=
                 cudaSuccess)
                 return SPINSIM_E_CUDA;
+            if (pg >= 0) cudaEventRecord(h->prof[pg][1], stream);
             kernels += 1;
             ChainArgs ca;
             ca.sims = ia.sims;
@@ -611,12 +640,16 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             ca.chunk_agg = reinterpret_cast<double*>(base + g.agg_off);
             ca.chunk_start = reinterpret_cast<double*>(base + g.start_off);
             if (launch_chain(g.spin_x2, ca, h->n_sm, stream) != cudaSuccess) return SPINSIM_E_CUDA;
+            if (pg >= 0) cudaEventRecord(h->prof[pg][2], stream);
             kernels += 3;
             h->last.lanes_per_sample = lanes;
             h->last.threads_per_block = block;
             h->last.grid_blocks = grid;
         }
     }
+    for (const StagedOut& s : plan.staged)
+        h->last.d2h_bytes += (int64_t)((s.host_states ? s.states_bytes : 0) + (s.host_spin ? s.spin_bytes : 0) +
+                                       (s.host_ops ? s.ops_bytes : 0));
     for (const StagedOut& s : plan.staged) {
         if (s.host_states && cudaMemcpyAsync(s.host_states, base + s.states_off, s.states_bytes, cudaMemcpyDefault, stream) != cudaSuccess)
             return SPINSIM_E_CUDA;
@@ -725,6 +758,13 @@ int spinsim_create(const spinsim_config* cfg, spinsim_handle* out)
         spinsim_destroy(h);
         return SPINSIM_E_CUDA;
     }
+    if (cfg->profile)
+        for (auto& row : h->prof)
+            for (auto& e : row)
+                if (cudaEventCreate(&e) != cudaSuccess) {
+                    spinsim_destroy(h);
+                    return SPINSIM_E_CUDA;
+                }
     *out = h;
     return SPINSIM_OK;
 }
@@ -746,6 +786,9 @@ void spinsim_destroy(spinsim_handle h)
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ev_pinned) cudaEventDestroy(h->ev_pinned);
+    for (auto& row : h->prof)
+        for (auto& e : row)
+            if (e) cudaEventDestroy(e);
     if (h->work) cudaStreamDestroy(h->work);
     delete h;
 }
@@ -802,6 +845,9 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
     const bool capturing = cap != cudaStreamCaptureStatusNone;
     h->last = spinsim_launch_info{};
     h->last.trotter_squares = h->tau;
+    h->last.integrate_ms = -1.0;
+    h->last.chain_ms = -1.0;
+    h->prof_groups = 0;
     int kernels = 0;
     int st = SPINSIM_OK;
     if (h->cfg.use_graphs && !capturing) {
@@ -866,6 +912,19 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
 int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info)
 {
     if (!h || !info) return SPINSIM_E_ARG;
+    if (h->prof_groups > 0) {
+        double ti = 0.0, tc = 0.0;
+        for (int g = 0; g < h->prof_groups; g++) {
+            if (cudaEventSynchronize(h->prof[g][2]) != cudaSuccess) return SPINSIM_E_CUDA;
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, h->prof[g][0], h->prof[g][1]);
+            cudaEventElapsedTime(&b, h->prof[g][1], h->prof[g][2]);
+            ti += a;
+            tc += b;
+        }
+        h->last.integrate_ms = ti;
+        h->last.chain_ms = tc;
+    }
     *info = h->last;
     return SPINSIM_OK;
 }

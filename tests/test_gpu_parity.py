@@ -65,7 +65,8 @@ def test_spin_one_sensing_full(oracle_mod, prec):
     ref = oracle_run(oracle_mod, req)
     err = assert_parity(out, ref, TOL[prec], "spin-one sensing")
     norms = np.linalg.norm(out["states"].cpu().numpy(), axis=1)
-    assert np.abs(norms - 1).max() < (1e-10 if prec == S.PREC_FP64 else 1e-9)
+    # FP64: no renormalisation, drift of 1e7 FP64 steps; FP32-bulk: states renormalised in FP64
+    assert np.abs(norms - 1).max() < (1e-10 if prec == S.PREC_FP64 else 1e-14)
     print(f"spin-one sensing prec={prec}: max|dpsi| = {err:.3e}, launch {info}")
 
 
@@ -78,8 +79,9 @@ def test_spin_one_operators(oracle_mod, prec):
     assert dU <= (1e-12 if prec == S.PREC_FP64 else 1e-7), dU
     U = out["ops"].cpu().numpy()
     gram = np.einsum("kji,kjl->kil", U.conj(), U)
-    assert np.abs(gram - np.eye(3)).max() < 1e-13
-    assert np.abs(np.linalg.det(U) - 1).max() < 1e-12
+    tol = 1e-13 if prec == S.PREC_FP64 else 1e-10   # FP32-bulk: defect of the FP32 second-order rest
+    assert np.abs(gram - np.eye(3)).max() < tol
+    assert np.abs(np.linalg.det(U) - 1).max() < tol
 
 
 def test_fp32_matches_oracle_at_same_tau(oracle_mod):
