@@ -7,6 +7,7 @@ and is loaded with ctypes.
 """
 from __future__ import annotations
 
+import fcntl
 import glob
 import hashlib
 import os
@@ -48,8 +49,18 @@ def _fingerprint() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if sources changed) and return the path of libspinsim.so."""
+    """Compile (if sources changed) and return the path of libspinsim.so.
+    Concurrent callers (e.g. parallel test workers) are serialised by a file lock."""
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     stamp = os.path.join(BUILD, "libspinsim.sha256")
     fp = _fingerprint()
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == fp:
