@@ -204,6 +204,31 @@ typedef struct {
 } spinsim_launch_info;
 int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info);
 
+/* Allocation-free variant of spinsim_simulate for one request (the paper has
+ * no counterpart; it exists for callers that cannot let a library allocate:
+ * real-time loops where cudaMalloc/cudaFree would synchronise the device,
+ * frameworks whose pooled allocator already owns all device memory, hosts
+ * that must not allocate while building their own work).
+ * It needs no handle, creates no stream, event or buffer and calls no
+ * allocator: all scratch lives in one file-scope device array of 16 MiB,
+ * which the CUDA runtime places on a GPU when the library's device code is
+ * loaded there (at the latest at the first call on that device) and which
+ * stays until the process exits.  That bounds
+ * the request: up to about 109,000 output samples for spin-one and 480,000
+ * for spin-half; a larger K returns SPINSIM_E_NOMEM without launching.
+ * res->states (and res->spin, res->ops when not NULL) must be 16-byte
+ * aligned device memory, else SPINSIM_E_ARG.  cfg selects method, precision,
+ * frame, tau and the launch shape (0 = lanes 2, 128 threads; no autotuning);
+ * use_graphs, mem_budget and profile are ignored; res->flags is not set.
+ * The first call on a device looks up the device address of the array; make
+ * it before any stream capture.  Every call uses the same array and leaves
+ * its contents behind, so calls that overlap on the GPU (on different
+ * streams, or unsynchronised host threads) race: serialise them, e.g. on one
+ * stream.  Results equal those of spinsim_simulate with the same
+ * configuration. */
+int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_request* req, spinsim_result* res,
+                            void* stream);
+
 /* Static description of a status code. */
 const char* spinsim_status_string(int status);
 

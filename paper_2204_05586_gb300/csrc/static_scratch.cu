@@ -1,0 +1,259 @@
+// static_scratch.cu -- spinsim_simulate_static: one simulation without any
+// device or host allocation by the library.
+//
+// Some callers cannot let a library allocate: real-time control loops where a
+// cudaMalloc/cudaFree would synchronise the device and stall an unrelated
+// pipeline, frameworks that have already partitioned all device memory with
+// their own pooled allocator (a cudaMalloc fails or fragments it), and hosts
+// that must not allocate while building their own work.  For them this entry
+// point runs the same kernels as spinsim_simulate, with all of its scratch
+// (parameter table, sample operators, chain aggregates) in one file-scope
+// device array of fixed size.  The caller passes device buffers for the
+// outputs and a stream; nothing else is created.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+#include "spinsim.h"
+
+using namespace spinsim;
+
+namespace {
+
+// 16 MiB: a spin-one request of up to ~109,000 output samples (a spin-half
+// one of up to ~480,000) fits.  Every GPU that loads the library holds this
+// array until the process exits.
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void* g_scratch_addr[kMaxDevices] = {};   // device address of g_static_scratch, per device
+
+constexpr double kPiS = 3.14159265358979323846264338327950288;
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+bool device_resident(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// The per-simulation parameter table, as the kernels expect it.
+void fill_one(const spinsim_config& cfg, int tau, const spinsim_request& r, int64_t K, int64_t L, double* states,
+              double* spin, double* ops, DevSim& d)
+{
+    std::memset(&d, 0, sizeof(d));
+    const spinsim_field& f = r.field;
+    const double two_pi = 2.0 * kPiS;
+    d.states = states;
+    d.spin = spin;
+    d.ops = ops;
+    d.K = K;
+    d.L = L;
+    d.t_start = r.t_start;
+    d.dt_out = r.dt_out;
+    d.dt = r.dt_out / (double)L;
+    d.drive_hz = f.drive_hz;
+    d.drive_phase = f.drive_phase;
+    const double ax = two_pi * f.drive_x_hz, ay = two_pi * f.drive_y_hz;
+    const double om_plus = 0.5 * (ax + ay), om_minus = 0.5 * (ax - ay);
+    double c1, c2, wa, wb;
+    int n_exp;
+    if (cfg.method == SPINSIM_METHOD_CF4) {
+        c1 = 0.2113248654051871177454256; c2 = 0.7886751345948128822545744;
+        wa = 0.5386751345948128822545744; wb = -0.03867513459481288225457439; n_exp = 2;
+    } else if (cfg.method == SPINSIM_METHOD_MIDPOINT) {
+        c1 = 0.5; c2 = 0.5; wa = 1.0; wb = 0.0; n_exp = 1;
+    } else {
+        c1 = 0.0; c2 = 1.0; wa = 0.5; wb = 0.5; n_exp = 1;
+    }
+    d.c1 = c1;
+    d.c2 = c2;
+    d.P[0] = om_plus * wa * d.dt;
+    d.P[1] = om_plus * wb * d.dt;
+    d.P[2] = om_minus * wa * d.dt;
+    d.P[3] = om_minus * wb * d.dt;
+    d.counter_on = om_minus != 0.0 ? 1 : 0;
+    d.za = wa * d.dt;
+    d.zb = wb * d.dt;
+    d.frame = cfg.rotating_frame ? 1 : 0;
+    d.zbias = d.frame ? 0.0 : two_pi * f.bias_hz * (wa + wb) * d.dt;
+    if (d.frame) {
+        d.w_co0 = two_pi * (f.drive_hz - f.bias_hz);
+        d.w_counter0 = two_pi * (f.drive_hz + f.bias_hz);
+        const double th = two_pi * f.bias_hz * r.dt_out;
+        d.exit_re = std::cos(th);
+        d.exit_im = -std::sin(th);
+        d.exit_half_re = std::cos(0.5 * th);
+        d.exit_half_im = -std::sin(0.5 * th);
+    } else {
+        d.w_co0 = d.w_counter0 = two_pi * f.drive_hz;
+        d.exit_re = d.exit_half_re = 1.0;
+        d.exit_im = d.exit_half_im = 0.0;
+    }
+    const double vq = r.spin_x2 == 2 ? (wa + wb) * two_pi * f.quad_hz * d.dt : 0.0;
+    double qd3 = vq / 3.0 / std::ldexp(1.0, tau);
+    if (cfg.precision == SPINSIM_PREC_FP32_BULK) qd3 = (double)(float)qd3;
+    d.qd3 = qd3;
+    d.om_plus = om_plus;
+    d.om_minus = om_minus;
+    d.W1 = n_exp == 2 ? wa + wb : wa;
+    d.W2 = n_exp == 2 ? wa + wb : wb;
+    d.gq = r.spin_x2 == 2 ? two_pi * f.quad_hz * r.dt_out : 0.0;
+    d.normalize_out = cfg.precision == SPINSIM_PREC_FP32_BULK ? 1 : 0;
+    d.tay_ok = L <= 65536 ? 1 : 0;
+    if (d.tay_ok) {
+        const double th_co = d.w_co0 * d.dt, th_ct = d.w_counter0 * d.dt;
+        double co[8] = {0}, ct[8] = {0};
+        const double Wn[2] = {d.W1, d.W2}, cn[2] = {d.c1, d.c2};
+        for (int64_t l = 0; l < L; l++)
+            for (int nn = 0; nn < 2; nn++) {
+                if (Wn[nn] == 0.0) continue;
+                const double x = (double)l + cn[nn];
+                double pw = Wn[nn];
+                const double sa = std::sin(th_co * x), ca = std::cos(th_co * x);
+                const double sb = std::sin(th_ct * x), cb = std::cos(th_ct * x);
+                for (int m = 0; m < 4; m++) {
+                    co[2 * m] += pw * ca; co[2 * m + 1] += pw * sa;
+                    ct[2 * m] += pw * cb; ct[2 * m + 1] += pw * sb;
+                    pw *= x;
+                }
+            }
+        for (int m = 0; m < 8; m++) { d.tay_co[m] = co[m]; d.tay_ct[m] = ct[m]; }
+    }
+    d.n_pulses = f.n_pulses;
+    for (int p = 0; p < f.n_pulses; p++) {
+        d.amp[p] = two_pi * f.pulse_amp_hz[p];
+        d.centre[p] = f.pulse_centre_s[p];
+        d.inv_w[p] = 1.0 / f.pulse_width_s[p];
+    }
+    for (int e = 0; e < 6; e++) d.psi0[e] = r.psi0[e];
+    d.spin_x2 = r.spin_x2;
+}
+
+}  // namespace
+
+extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_request* req, spinsim_result* res,
+                                       void* stream_v)
+{
+    if (!cfg || !req || !res) return SPINSIM_E_ARG;
+    if (cfg->method < 0 || cfg->method > 2 || cfg->precision < 0 || cfg->precision > 1 ||
+        cfg->trotter_squares < -1 || cfg->trotter_squares > 40 ||
+        !(cfg->lanes_per_sample == 0 || cfg->lanes_per_sample == 1 || cfg->lanes_per_sample == 2 ||
+          cfg->lanes_per_sample == 4) ||
+        !(cfg->threads_per_block == 0 || cfg->threads_per_block == 64 || cfg->threads_per_block == 128 ||
+          cfg->threads_per_block == 256))
+        return SPINSIM_E_ARG;
+    int64_t K = 0, L = 0;
+    int st = spinsim_counts(req, &K, &L);
+    res->status = st;
+    res->flags = 0;
+    res->n_samples = 0;
+    if (st != SPINSIM_OK) return st;
+    if (!res->states || res->capacity < K) {
+        res->status = !res->states ? SPINSIM_E_ARG : SPINSIM_E_CAPACITY;
+        return res->status;
+    }
+    // outputs must already be device memory (staging would need an allocation)
+    const void* outs[3] = {res->states, res->spin, res->ops};
+    for (const void* p : outs)
+        if (p && (!device_resident(p) || ((uintptr_t)p & 15u) != 0)) {
+            res->status = SPINSIM_E_ARG;
+            return SPINSIM_E_ARG;
+        }
+    if (cfg->device < 0 || cfg->device >= kMaxDevices) return res->status = SPINSIM_E_ARG;
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return res->status = SPINSIM_E_CUDA;
+    // set-up, once per device with that device current: the device address of
+    // the static array (its host-side name is not a device address)
+    void* base_v = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_setup_mu);
+        if (!g_scratch_addr[cfg->device]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return res->status = SPINSIM_E_CUDA;
+            }
+            g_scratch_addr[cfg->device] = p;
+        }
+        base_v = g_scratch_addr[cfg->device];
+    }
+    char* base = static_cast<char*>(base_v);
+    const int spin = req->spin_x2;
+    const int opd = op_doubles(spin);
+    const int64_t chunks = (K + kChunk - 1) / kChunk;
+    size_t off = 0;
+    const size_t sims_off = off; off += up256(sizeof(DevSim));
+    const size_t soff_off = off; off += 256;
+    const size_t coff_off = off; off += 256;
+    const size_t counter_off = off; off += 256;
+    const size_t U_off = off; off += up256((size_t)K * opd * 8);
+    const size_t prefix_off = off; off += up256((size_t)chunks * 32 * opd * 8);
+    const size_t agg_off = off; off += up256((size_t)chunks * opd * 8);
+    const size_t start_off = off; off += up256((size_t)chunks * 2 * (spin + 1) * 8);
+    if (off > kStaticScratchBytes) return res->status = SPINSIM_E_NOMEM;   // K beyond the static maximum
+
+    const int tau = cfg->trotter_squares >= 0 ? cfg->trotter_squares
+                                             : (cfg->precision == SPINSIM_PREC_FP64 ? 24 : SPINSIM_FP32_DEFAULT_TAU);
+    DevSim d;
+    fill_one(*cfg, tau, *req, K, L, res->states, res->spin, res->ops, d);
+    int64_t offsets[4] = {0, K, 0, chunks};
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    // Copies from pageable host memory: the source may be reused on return.
+    if (cudaMemcpyAsync(base + sims_off, &d, sizeof(DevSim), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(base + soff_off, offsets, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(base + coff_off, offsets + 2, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess)
+        return res->status = SPINSIM_E_CUDA;
+    if (K > 0) {
+        int n_sm = 0;
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
+        const int lanes = cfg->lanes_per_sample ? cfg->lanes_per_sample : 2;
+        const int block = cfg->threads_per_block ? cfg->threads_per_block : 128;
+        int per_sm = 0;
+        if (integrate_occupancy(spin, cfg->precision, cfg->method, lanes, block, &per_sm) != cudaSuccess) {
+            cudaGetLastError();
+            return res->status = SPINSIM_E_CUDA;
+        }
+        IntegrateArgs ia;
+        ia.sims = reinterpret_cast<const DevSim*>(base + sims_off);
+        ia.sample_offsets = reinterpret_cast<const int64_t*>(base + soff_off);
+        ia.n_sims = 1;
+        ia.total_samples = K;
+        ia.U = reinterpret_cast<double*>(base + U_off);
+        ia.tau = tau;
+        ia.tile_counter = reinterpret_cast<unsigned long long*>(base + counter_off);
+        const int spb = block / lanes;
+        ia.n_tiles = (K + spb - 1) / spb;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ia.n_tiles, (int64_t)n_sm * std::max(per_sm, 1)));
+        // the tile counter keeps the previous call's value: clear it
+        if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
+            return res->status = SPINSIM_E_CUDA;
+        if (launch_integrate(spin, cfg->precision, cfg->method, lanes, block, grid, ia, stream) != cudaSuccess)
+            return res->status = SPINSIM_E_CUDA;
+        ChainArgs ca;
+        ca.sims = ia.sims;
+        ca.chunk_offsets = reinterpret_cast<const int64_t*>(base + coff_off);
+        ca.n_sims = 1;
+        ca.n_chunks = chunks;
+        ca.U = ia.U;
+        ca.run_prefix = reinterpret_cast<double*>(base + prefix_off);
+        ca.chunk_agg = reinterpret_cast<double*>(base + agg_off);
+        ca.chunk_start = reinterpret_cast<double*>(base + start_off);
+        if (launch_chain(spin, ca, n_sm, stream) != cudaSuccess) return res->status = SPINSIM_E_CUDA;
+    }
+    res->n_samples = K;
+    res->status = SPINSIM_OK;
+    return SPINSIM_OK;
+}

@@ -68,7 +68,8 @@ class spinsim_launch_info(ctypes.Structure):
 
 
 EXPORTED = ("spinsim_config_default", "spinsim_create", "spinsim_destroy", "spinsim_counts", "spinsim_footprint",
-            "spinsim_simulate", "spinsim_submit", "spinsim_poll", "spinsim_last_launch", "spinsim_status_string")
+            "spinsim_simulate", "spinsim_submit", "spinsim_poll", "spinsim_last_launch", "spinsim_status_string",
+            "spinsim_simulate_static")
 
 _lib = None
 _lock = threading.Lock()
@@ -103,6 +104,8 @@ def load(build_if_missing: bool = True):
         L.spinsim_submit.argtypes = [ctypes.c_void_p, P(spinsim_request), P(spinsim_result), P(ctypes.c_int64)]
         L.spinsim_poll.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]
         L.spinsim_last_launch.argtypes = [ctypes.c_void_p, P(spinsim_launch_info)]
+        L.spinsim_simulate_static.argtypes = [P(spinsim_config), P(spinsim_request), P(spinsim_result),
+                                              ctypes.c_void_p]
         L.spinsim_status_string.argtypes = [ctypes.c_int]
         L.spinsim_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -143,6 +146,13 @@ def spinsim_simulate(h, reqs, results, stream: int = 0) -> int:
     ra = reqs if isinstance(reqs, ctypes.Array) else (spinsim_request * n)(*reqs)
     rs = results if isinstance(results, ctypes.Array) else (spinsim_result * n)(*results)
     return load().spinsim_simulate(h, ra, rs, n, ctypes.c_void_p(stream))
+
+
+def spinsim_simulate_static(cfg: spinsim_config, req: spinsim_request, res: spinsim_result, stream: int = 0) -> int:
+    """One request with no allocation by the library (scratch in a fixed
+    device array); the outputs must be device buffers."""
+    return load().spinsim_simulate_static(ctypes.byref(cfg), ctypes.byref(req), ctypes.byref(res),
+                                          ctypes.c_void_p(stream))
 
 
 def spinsim_submit(h, req: spinsim_request, res: spinsim_result):
