@@ -78,9 +78,10 @@ typedef struct {
     int32_t method;               /* spinsim_method                                          */
     int32_t precision;            /* spinsim_precision                                       */
     int32_t rotating_frame;       /* 1: per-interval rotating frame (default), 0: lab frame  */
-    int32_t trotter_squares;      /* tau, n = 2^tau Lie-Trotter factors (spin-one); -1 gives
-                                     the precision's default (24 for FP64, Sec. 1.2.3;
-                                     SPINSIM_FP32_DEFAULT_TAU for FP32-bulk); 0..40         */
+    int32_t trotter_squares;      /* tau, n = 2^tau Lie-Trotter factors (spin-one), 0..40;
+                                     -1 = default: 24 for FP64 (Sec. 1.2.3); for FP32-bulk,
+                                     per request the fewest squarings whose Lie-Trotter
+                                     error bound stays ten times under FP32 rounding      */
     int32_t lanes_per_sample;     /* 0 = autotune; else 1, 2 or 4 threads share one U_k.
                                      Results do not depend on it (fixed reduction tree).   */
     int32_t threads_per_block;    /* 0 = autotune; else 64, 128 or 256                        */
@@ -92,8 +93,6 @@ typedef struct {
                                      with CUDA events (read by spinsim_last_launch)         */
     int32_t reserved;
 } spinsim_config;
-
-#define SPINSIM_FP32_DEFAULT_TAU 4
 
 /* The fixed parameterised field family (Hz, seconds, radians):
  *   w_x(t) = 2 pi drive_x_hz cos(2 pi drive_hz t + drive_phase)
@@ -214,7 +213,7 @@ int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info);
  * which the CUDA runtime places on a GPU when the library's device code is
  * loaded there (at the latest at the first call on that device) and which
  * stays until the process exits.  That bounds
- * the request: up to about 109,000 output samples for spin-one and 480,000
+ * the request: up to about 102,000 output samples for spin-one and 460,000
  * for spin-half; a larger K returns SPINSIM_E_NOMEM without launching.
  * res->states (and res->spin, res->ops when not NULL) must be 16-byte
  * aligned device memory, else SPINSIM_E_ARG.  cfg selects method, precision,

@@ -2,18 +2,25 @@
 // write (Sec. 1.2.4, Eq. integration_compilation: psi_k = U_k psi_{k-1}).
 //
 // The paper chains the U_k sequentially on the CPU.  Here the chain is a
-// three-pass parallel scan in FP64 on the device, over chunks of kChunk = 512
-// samples that never straddle two simulations:
-//   reduce: one warp per chunk; lane l multiplies its run of kRun = 16
-//           operators in order, then the warp forms inclusive prefixes
-//           P_l = B_l ... B_0 of the run products by a shuffle scan (Hillis-
-//           Steele, 5 levels) and stores each lane's exclusive prefix and the
-//           chunk product;
-//   carry:  one warp per simulation walks its chunk products in order and
-//           stores the state entering every chunk;
-//   apply:  one warp per chunk; lane l forms the state entering its run from
-//           its exclusive prefix and walks its 16 samples, writing psi_k,
-//           <J>_k and (optionally) U_k.
+// parallel scan in FP64 on the device, over chunks of kChunk = 256 samples
+// and groups of kGroup = 32 chunks, neither of which straddles two
+// simulations:
+//   reduce:     one warp per chunk; lane l multiplies its run of kRun = 8
+//               operators in order, then the warp forms inclusive prefixes
+//               P_l = B_l ... B_0 of the run products by a shuffle scan
+//               (Hillis-Steele, 5 levels) and stores each lane's exclusive
+//               prefix and the chunk product;
+//   group scan: one warp per group scans its 32 chunk products the same way
+//               and stores each chunk's exclusive prefix and the group product;
+//   carry:      one warp per simulation walks its group products in order
+//               (one matrix row per lane) and stores the state entering every
+//               group;
+//   apply:      one warp per chunk forms the state entering the chunk and
+//               each lane's run from the prefixes, then walks its 8 samples,
+//               writing psi_k, <J>_k and (optionally) U_k.
+// On GB300 a 32-lane FP64 instruction keeps an SM sub-partition busy for
+// tens of cycles, so the FP64 work is spread over many warps and the
+// sequential part (the carry) is kept short and row-parallel.
 // Spin-one operators are general 3x3 complex matrices; spin-half operators
 // are kept in SU(2) form (alpha, beta) = first column.
 #include <algorithm>
@@ -226,11 +233,43 @@ __global__ void __launch_bounds__(128) chain_reduce_kernel(ChainArgs a)
     }
 }
 
-// Carry: one warp per simulation.  The warp loads the products of 32
-// consecutive chunks at once (lane j holds chunk c0 + j), then walks them in
-// order, the state staying in every lane and each product being broadcast
-// from its lane by shuffles; lane j keeps the state entering its chunk and
-// the warp stores the 32 states together.
+// Group scan: one warp per group of up to 32 consecutive chunks of one
+// simulation; inclusive prefixes of the chunk products by a shuffle scan.
+template <int N>
+__global__ void __launch_bounds__(128) chain_group_kernel(ChainArgs a)
+{
+    constexpr int OPD = N == 3 ? 18 : 4;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < a.n_groups; g += warps) {
+        const int si = find_chunk_sim(a.group_offsets, a.n_sims, g);
+        const int64_t c_first = a.chunk_offsets[si] + (g - a.group_offsets[si]) * kGroup;
+        const int64_t c_end = a.chunk_offsets[si + 1];
+        const int64_t c = c_first + lane;
+        Op<N> P;
+        if (c < c_end) P.load(a.chunk_agg + c * OPD);
+        else P.identity();
+#pragma unroll
+        for (unsigned d = 1; d < 32; d <<= 1) {
+            Op<N> o = P;
+            o.shfl_up(d);
+            if (lane >= (int)d) {
+                Op<N> t;
+                Op<N>::mul(P, o, t);
+                P = t;
+            }
+        }
+        Op<N> M = P;
+        M.shfl_up(1);
+        if (lane == 0) M.identity();
+        if (c < c_end) M.store(a.chunk_gprefix + c * OPD);
+        if (lane == 31) P.store(a.group_agg + g * OPD);
+    }
+}
+
+// Carry: one warp per simulation walks its group products in order.  Lane r
+// (r < N) holds row r of the product and computes component r of the next
+// state; the state is broadcast to all lanes by shuffles.
 template <int N>
 __global__ void __launch_bounds__(128) chain_carry_kernel(ChainArgs a)
 {
@@ -242,29 +281,33 @@ __global__ void __launch_bounds__(128) chain_carry_kernel(ChainArgs a)
         cx<double> psi[N];
 #pragma unroll
         for (int i = 0; i < N; i++) psi[i] = cmk(s.psi0[2 * i], s.psi0[2 * i + 1]);
-        const int64_t c0 = a.chunk_offsets[si], c1 = a.chunk_offsets[si + 1];
-        for (int64_t base = c0; base < c1; base += 32) {
-            const int cnt = (int)(c1 - base < 32 ? c1 - base : 32);
-            Op<N> A;
-            if (lane < cnt) A.load(a.chunk_agg + (base + lane) * OPD);
-            else A.identity();
-            cx<double> mine[N];
-            for (int j = 0; j < cnt; j++) {
-                if (lane == j) {
-#pragma unroll
-                    for (int i = 0; i < N; i++) mine[i] = psi[i];
-                }
-                Op<N> Aj = A;
-                Aj.shfl_idx(j);
-                cx<double> nxt[N];
-                Aj.apply(psi, nxt);
-#pragma unroll
-                for (int i = 0; i < N; i++) psi[i] = nxt[i];
+        const int64_t g0 = a.group_offsets[si], g1 = a.group_offsets[si + 1];
+        const int r = lane < N ? lane : 0;
+        for (int64_t g = g0; g < g1; g++) {
+            if (lane < N) {
+                double* st = a.group_start + g * (2 * N);
+                st[2 * lane] = psi[lane].r;
+                st[2 * lane + 1] = psi[lane].i;
             }
-            if (lane < cnt) {
-                double* st = a.chunk_start + (base + lane) * (2 * N);
+            // row r of the group product
+            cx<double> row[N];
+            const double* Ag = a.group_agg + g * OPD;
+            if (N == 3) {
 #pragma unroll
-                for (int i = 0; i < N; i++) { st[2 * i] = mine[i].r; st[2 * i + 1] = mine[i].i; }
+                for (int j = 0; j < N; j++) row[j] = cmk(Ag[6 * r + 2 * j], Ag[6 * r + 2 * j + 1]);
+            } else {
+                // [[alpha, -conj(beta)], [beta, conj(alpha)]]
+                const cx<double> al = cmk(Ag[0], Ag[1]), be = cmk(Ag[2], Ag[3]);
+                row[0] = r == 0 ? al : be;
+                row[N - 1] = r == 0 ? cmk(-be.r, be.i) : cconj(al);
+            }
+            cx<double> v = cmul(row[0], psi[0]);
+#pragma unroll
+            for (int j = 1; j < N; j++) v = cfma(row[j], psi[j], v);
+#pragma unroll
+            for (int i = 0; i < N; i++) {
+                psi[i].r = __shfl_sync(0xffffffffu, v.r, i);
+                psi[i].i = __shfl_sync(0xffffffffu, v.i, i);
             }
         }
     }
@@ -283,12 +326,16 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
         const int64_t k0 = j * kChunk + (int64_t)lane * kRun;
         const int64_t k1 = min(k0 + kRun, s.K);
         if (k0 >= k1) continue;
-        cx<double> st[N], psi[N], nxt[N];
+        const int64_t g = a.group_offsets[si] + j / kGroup;
+        cx<double> gs[N], cs[N], psi[N], nxt[N];
 #pragma unroll
-        for (int i = 0; i < N; i++) st[i] = cmk(a.chunk_start[c * 2 * N + 2 * i], a.chunk_start[c * 2 * N + 2 * i + 1]);
+        for (int i = 0; i < N; i++) gs[i] = cmk(a.group_start[g * 2 * N + 2 * i], a.group_start[g * 2 * N + 2 * i + 1]);
+        Op<N> G;
+        G.load(a.chunk_gprefix + c * OPD);
+        G.apply(gs, cs);                 // state entering the chunk
         Op<N> M;
         M.load(a.run_prefix + (c * 32 + lane) * OPD);
-        M.apply(st, psi);
+        M.apply(cs, psi);                // state entering this lane's run
         const double* U = a.U + s.sample_offset * OPD;
         for (int64_t k = k0; k < k1; k++) {
             Op<N> u;
@@ -334,6 +381,10 @@ static cudaError_t launch_chain_n(const ChainArgs& a, int n_sm, cudaStream_t str
     ChainArgs args = a;
     chain_reduce_kernel<N><<<grid, block, 0, stream>>>(args);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int ggrid = (int)std::min<int64_t>((a.n_groups + 3) / 4, (int64_t)n_sm * 16);
+    chain_group_kernel<N><<<ggrid, block, 0, stream>>>(args);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int cgrid = (int)std::min<int64_t>((a.n_sims + 3) / 4, (int64_t)n_sm * 16);
     chain_carry_kernel<N><<<cgrid, 128, 0, stream>>>(args);

@@ -113,6 +113,7 @@ struct SampleCtx {
     R dt, c1, c2;
     R amp[kMaxPulses], u0[kMaxPulses], invw[kMaxPulses], ghat[kMaxPulses];
     int np;
+    int tau;
     bool counter_on;
 };
 
@@ -171,6 +172,7 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c)
     c.c1 = (R)s.c1;
     c.c2 = (R)s.c2;
     c.np = s.n_pulses;
+    c.tau = s.tau;
     c.counter_on = s.counter_on != 0;
     double gsum = 0.0;
 #pragma unroll

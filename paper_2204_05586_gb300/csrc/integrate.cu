@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
 #pragma unroll 1
                 for (int64_t l = lo; l < hi; l++) {
                     Res x, Y;
-                    step_res<R, METHOD>(c, (R)l, a.tau, x);
+                    step_res<R, METHOD>(c, (R)l, c.tau, x);
                     res_mul(x, X, Y);   // premultiply: U <- u_l U
                     X = Y;
                 }

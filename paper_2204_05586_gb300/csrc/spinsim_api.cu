@@ -117,9 +117,9 @@ struct PinnedBuf {
 struct Group {
     int spin_x2;
     std::vector<int64_t> idx;      // request indices
-    int64_t samples = 0, chunks = 0;
-    size_t sims_off = 0, soff_off = 0, coff_off = 0, counter_off = 0, U_off = 0, prefix_off = 0, agg_off = 0,
-           start_off = 0;
+    int64_t samples = 0, chunks = 0, groups = 0;
+    size_t sims_off = 0, soff_off = 0, coff_off = 0, goff_off = 0, counter_off = 0, U_off = 0, chain_off = 0;
+    ChainLayout chain{};
 };
 
 struct StagedOut {
@@ -241,18 +241,18 @@ int ensure_pinned(PinnedBuf& b, size_t need)
 }
 
 // Scratch bytes of one group (spin) of a batch.
-size_t group_bytes(int spin_x2, int64_t n, int64_t samples, int64_t chunks)
+// Parameter table of one spin group: the simulations and their sample,
+// chunk and group offsets, contiguous (uploaded with one copy).
+size_t table_bytes(int64_t n)
+{
+    return round_up((size_t)n * sizeof(DevSim), 256) + 3 * round_up((size_t)(n + 1) * sizeof(int64_t), 256);
+}
+
+size_t group_bytes(int spin_x2, int64_t n, int64_t samples, int64_t chunks, int64_t groups)
 {
     const size_t opb = (size_t)op_doubles(spin_x2) * sizeof(double);
-    size_t s = 0;
-    s += round_up((size_t)n * sizeof(DevSim), 256);
-    s += 2 * round_up((size_t)(n + 1) * sizeof(int64_t), 256);
-    s += 256;                                          // tile counter
-    s += round_up((size_t)samples * opb, 256);         // operators
-    s += round_up((size_t)chunks * 32 * opb, 256);     // lane prefixes
-    s += round_up((size_t)chunks * opb, 256);          // chunk products
-    s += round_up((size_t)chunks * 2 * (spin_x2 + 1) * sizeof(double), 256);
-    return s;
+    return table_bytes(n) + 256 /* tile counter */ + round_up((size_t)samples * opb, 256) +
+           chain_layout(spin_x2, chunks, groups).bytes;
 }
 
 // Build the plan: offsets inside one arena, the staged outputs, and fill the
@@ -272,21 +272,22 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
             if (checked[i].status == SPINSIM_OK && reqs[i].spin_x2 == spin) {
                 g.idx.push_back(i);
                 g.samples += checked[i].K;
-                g.chunks += (checked[i].K + kChunk - 1) / kChunk;
+                g.chunks += n_chunks_of(checked[i].K);
+                g.groups += n_groups_of(checked[i].K);
             }
         if (g.idx.empty()) continue;
         const int64_t m = (int64_t)g.idx.size();
         const size_t opb = (size_t)op_doubles(spin) * sizeof(double);
-        g.sims_off = off; off += round_up((size_t)m * sizeof(DevSim), 256);
-        g.soff_off = off; off += round_up((size_t)(m + 1) * sizeof(int64_t), 256);
-        g.coff_off = off; off += round_up((size_t)(m + 1) * sizeof(int64_t), 256);
+        g.sims_off = off;
+        g.soff_off = off + round_up((size_t)m * sizeof(DevSim), 256);
+        g.coff_off = g.soff_off + round_up((size_t)(m + 1) * sizeof(int64_t), 256);
+        g.goff_off = g.coff_off + round_up((size_t)(m + 1) * sizeof(int64_t), 256);
+        off += table_bytes(m);
         g.counter_off = off; off += 256;
         g.U_off = off; off += round_up((size_t)g.samples * opb, 256);
-        g.prefix_off = off; off += round_up((size_t)g.chunks * 32 * opb, 256);
-        g.agg_off = off; off += round_up((size_t)g.chunks * opb, 256);
-        g.start_off = off; off += round_up((size_t)g.chunks * 2 * (spin + 1) * sizeof(double), 256);
-        // pinned table: sims, sample offsets, chunk offsets (same relative order)
-        pin += round_up((size_t)m * sizeof(DevSim), 256) + 2 * round_up((size_t)(m + 1) * sizeof(int64_t), 256);
+        g.chain = chain_layout(spin, g.chunks, g.groups);
+        g.chain_off = off; off += g.chain.bytes;
+        pin += table_bytes(m);
         plan.groups.push_back(std::move(g));
     }
     // host-resident or misaligned outputs are staged through the arena
@@ -321,10 +322,11 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
     for (const Group& g : plan.groups) {
         const int64_t m = (int64_t)g.idx.size();
         DevSim* sims = reinterpret_cast<DevSim*>(pinned + pin);
-        int64_t* soff = reinterpret_cast<int64_t*>(pinned + pin + round_up((size_t)m * sizeof(DevSim), 256));
-        int64_t* coff = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(soff) + round_up((size_t)(m + 1) * sizeof(int64_t), 256));
-        pin += round_up((size_t)m * sizeof(DevSim), 256) + 2 * round_up((size_t)(m + 1) * sizeof(int64_t), 256);
-        int64_t so = 0, co = 0;
+        int64_t* soff = reinterpret_cast<int64_t*>(pinned + pin + (g.soff_off - g.sims_off));
+        int64_t* coff = reinterpret_cast<int64_t*>(pinned + pin + (g.coff_off - g.sims_off));
+        int64_t* goff = reinterpret_cast<int64_t*>(pinned + pin + (g.goff_off - g.sims_off));
+        pin += table_bytes(m);
+        int64_t so = 0, co = 0, go = 0;
         for (int64_t q = 0; q < m; q++) {
             const int64_t i = g.idx[q];
             const spinsim_request& r = reqs[i];
@@ -344,10 +346,13 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
             d.L = checked[i].L;
             d.sample_offset = so;
             d.chunk_offset = co;
+            d.group_offset = go;
             soff[q] = so;
             coff[q] = co;
+            goff[q] = go;
             so += d.K;
-            co += (d.K + kChunk - 1) / kChunk;
+            co += n_chunks_of(d.K);
+            go += n_groups_of(d.K);
             d.t_start = r.t_start;
             d.dt_out = r.dt_out;
             d.dt = r.dt_out / (double)d.L;
@@ -396,8 +401,15 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
             // quadrupole coefficient of one exponential, over 3 and 2^tau, as the
             // bulk type holds it (its rounding only reaches second order: the
             // first-order part of every U_k is replaced by the exact gq)
+            double pulse_w = 0.0;
+            for (int p = 0; p < f.n_pulses; p++) pulse_w += two_pi * std::fabs(f.pulse_amp_hz[p]);
+            d.tau = choose_tau(h->cfg.trotter_squares, h->cfg.precision, h->cfg.rotating_frame, d.dt,
+                               std::fabs(om_plus), std::fabs(om_minus), two_pi * std::fabs(f.bias_hz), pulse_w,
+                               r.spin_x2 == 2 ? two_pi * std::fabs(f.quad_hz) : 0.0);
+            if (r.spin_x2 == 1) d.tau = 0;   // closed form: no squarings
+            h->last.trotter_squares = std::max(h->last.trotter_squares, d.tau);
             const double vq = r.spin_x2 == 2 ? (wa + wb) * two_pi * f.quad_hz * d.dt : 0.0;
-            double qd3 = vq / 3.0 / std::ldexp(1.0, h->tau);
+            double qd3 = vq / 3.0 / std::ldexp(1.0, d.tau);
             if (h->cfg.precision == SPINSIM_PREC_FP32_BULK) qd3 = (double)(float)qd3;
             d.qd3 = qd3;
             d.om_plus = om_plus;
@@ -439,6 +451,7 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
         }
         soff[m] = so;
         coff[m] = co;
+        goff[m] = go;
     }
 }
 
@@ -599,8 +612,8 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
     size_t pin = 0;
     for (const Group& g : plan.groups) {
         const int64_t m = (int64_t)g.idx.size();
-        const size_t tbl = round_up((size_t)m * sizeof(DevSim), 256) + 2 * round_up((size_t)(m + 1) * sizeof(int64_t), 256);
-        // sims, soff, coff are contiguous in both the pinned table and the arena
+        const size_t tbl = table_bytes(m);
+        // the table is contiguous in both the pinned buffer and the arena
         if (cudaMemcpyAsync(base + g.sims_off, static_cast<char*>(pinned.p) + pin, tbl, cudaMemcpyHostToDevice,
                             stream) != cudaSuccess)
             return SPINSIM_E_CUDA;
@@ -633,15 +646,20 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             ChainArgs ca;
             ca.sims = ia.sims;
             ca.chunk_offsets = reinterpret_cast<const int64_t*>(base + g.coff_off);
+            ca.group_offsets = reinterpret_cast<const int64_t*>(base + g.goff_off);
+            ca.n_groups = g.groups;
             ca.n_sims = (int)m;
             ca.n_chunks = g.chunks;
             ca.U = ia.U;
-            ca.run_prefix = reinterpret_cast<double*>(base + g.prefix_off);
-            ca.chunk_agg = reinterpret_cast<double*>(base + g.agg_off);
-            ca.chunk_start = reinterpret_cast<double*>(base + g.start_off);
+            char* cb = base + g.chain_off;
+            ca.run_prefix = reinterpret_cast<double*>(cb + g.chain.prefix);
+            ca.chunk_agg = reinterpret_cast<double*>(cb + g.chain.agg);
+            ca.chunk_gprefix = reinterpret_cast<double*>(cb + g.chain.gprefix);
+            ca.group_agg = reinterpret_cast<double*>(cb + g.chain.gagg);
+            ca.group_start = reinterpret_cast<double*>(cb + g.chain.gstart);
             if (launch_chain(g.spin_x2, ca, h->n_sm, stream) != cudaSuccess) return SPINSIM_E_CUDA;
             if (pg >= 0) cudaEventRecord(h->prof[pg][2], stream);
-            kernels += 3;
+            kernels += 4;
             h->last.lanes_per_sample = lanes;
             h->last.threads_per_block = block;
             h->last.grid_blocks = grid;
@@ -742,8 +760,7 @@ int spinsim_create(const spinsim_config* cfg, spinsim_handle* out)
     if (!h) return SPINSIM_E_NOMEM;
     h->cfg = *cfg;
     h->device = cfg->device;
-    h->tau = cfg->trotter_squares >= 0 ? cfg->trotter_squares
-                                      : (cfg->precision == SPINSIM_PREC_FP64 ? 24 : SPINSIM_FP32_DEFAULT_TAU);
+    h->tau = cfg->trotter_squares;   // -1: chosen per request (choose_tau)
     cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
@@ -805,17 +822,18 @@ int spinsim_counts(const spinsim_request* req, int64_t* K, int64_t* L)
 int64_t spinsim_footprint(spinsim_handle h, const spinsim_request* reqs, int64_t n)
 {
     if (!h || (n > 0 && !reqs) || n < 0) return SPINSIM_E_ARG;
-    int64_t samples[3] = {0, 0, 0}, chunks[3] = {0, 0, 0}, count[3] = {0, 0, 0};
+    int64_t samples[3] = {0, 0, 0}, chunks[3] = {0, 0, 0}, groups[3] = {0, 0, 0}, count[3] = {0, 0, 0};
     for (int64_t i = 0; i < n; i++) {
         Checked c = check_request(&reqs[i]);
         if (c.status != SPINSIM_OK) return c.status;
         samples[reqs[i].spin_x2] += c.K;
-        chunks[reqs[i].spin_x2] += (c.K + kChunk - 1) / kChunk;
+        chunks[reqs[i].spin_x2] += n_chunks_of(c.K);
+        groups[reqs[i].spin_x2] += n_groups_of(c.K);
         count[reqs[i].spin_x2] += 1;
     }
     int64_t total = 0;
     for (int s = 1; s <= 2; s++)
-        if (count[s]) total += (int64_t)group_bytes(s, count[s], samples[s], chunks[s]);
+        if (count[s]) total += (int64_t)group_bytes(s, count[s], samples[s], chunks[s], groups[s]);
     return total;
 }
 
@@ -844,7 +862,7 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
     }
     const bool capturing = cap != cudaStreamCaptureStatusNone;
     h->last = spinsim_launch_info{};
-    h->last.trotter_squares = h->tau;
+    h->last.trotter_squares = 0;
     h->last.integrate_ms = -1.0;
     h->last.chain_ms = -1.0;
     h->prof_groups = 0;
@@ -945,7 +963,7 @@ static int serving_init(spinsim_s* h)
 
 static size_t request_bytes(const spinsim_request& r, const Checked& c)
 {
-    return group_bytes(r.spin_x2, 1, c.K, (c.K + kChunk - 1) / kChunk);
+    return group_bytes(r.spin_x2, 1, c.K, n_chunks_of(c.K), n_groups_of(c.K));
 }
 
 // Retire finished batches, then launch pending requests on free slots while

@@ -25,8 +25,8 @@ using namespace spinsim;
 
 namespace {
 
-// 16 MiB: a spin-one request of up to ~109,000 output samples (a spin-half
-// one of up to ~480,000) fits.  Every GPU that loads the library holds this
+// 16 MiB: a spin-one request of up to ~102,000 output samples (a spin-half
+// one of up to ~460,000) fits.  Every GPU that loads the library holds this
 // array until the process exits.
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -102,8 +102,13 @@ void fill_one(const spinsim_config& cfg, int tau, const spinsim_request& r, int6
         d.exit_re = d.exit_half_re = 1.0;
         d.exit_im = d.exit_half_im = 0.0;
     }
+    double pulse_w = 0.0;
+    for (int p = 0; p < f.n_pulses; p++) pulse_w += two_pi * std::fabs(f.pulse_amp_hz[p]);
+    d.tau = choose_tau(tau, cfg.precision, cfg.rotating_frame, d.dt, std::fabs(om_plus), std::fabs(om_minus),
+                       two_pi * std::fabs(f.bias_hz), pulse_w, r.spin_x2 == 2 ? two_pi * std::fabs(f.quad_hz) : 0.0);
+    if (r.spin_x2 == 1) d.tau = 0;
     const double vq = r.spin_x2 == 2 ? (wa + wb) * two_pi * f.quad_hz * d.dt : 0.0;
-    double qd3 = vq / 3.0 / std::ldexp(1.0, tau);
+    double qd3 = vq / 3.0 / std::ldexp(1.0, d.tau);
     if (cfg.precision == SPINSIM_PREC_FP32_BULK) qd3 = (double)(float)qd3;
     d.qd3 = qd3;
     d.om_plus = om_plus;
@@ -192,28 +197,29 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     char* base = static_cast<char*>(base_v);
     const int spin = req->spin_x2;
     const int opd = op_doubles(spin);
-    const int64_t chunks = (K + kChunk - 1) / kChunk;
+    const int64_t chunks = n_chunks_of(K), groups = n_groups_of(K);
+    const ChainLayout cl = chain_layout(spin, chunks, groups);
     size_t off = 0;
     const size_t sims_off = off; off += up256(sizeof(DevSim));
     const size_t soff_off = off; off += 256;
     const size_t coff_off = off; off += 256;
+    const size_t goff_off = off; off += 256;
     const size_t counter_off = off; off += 256;
     const size_t U_off = off; off += up256((size_t)K * opd * 8);
-    const size_t prefix_off = off; off += up256((size_t)chunks * 32 * opd * 8);
-    const size_t agg_off = off; off += up256((size_t)chunks * opd * 8);
-    const size_t start_off = off; off += up256((size_t)chunks * 2 * (spin + 1) * 8);
+    const size_t chain_off = off; off += cl.bytes;
     if (off > kStaticScratchBytes) return res->status = SPINSIM_E_NOMEM;   // K beyond the static maximum
 
-    const int tau = cfg->trotter_squares >= 0 ? cfg->trotter_squares
-                                             : (cfg->precision == SPINSIM_PREC_FP64 ? 24 : SPINSIM_FP32_DEFAULT_TAU);
+    const int tau = cfg->trotter_squares;   // -1: chosen per request, as in spinsim_simulate
     DevSim d;
     fill_one(*cfg, tau, *req, K, L, res->states, res->spin, res->ops, d);
-    int64_t offsets[4] = {0, K, 0, chunks};
+    int64_t offsets[6] = {0, K, 0, chunks, 0, groups};
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     // Copies from pageable host memory: the source may be reused on return.
     if (cudaMemcpyAsync(base + sims_off, &d, sizeof(DevSim), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
         cudaMemcpyAsync(base + soff_off, offsets, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
         cudaMemcpyAsync(base + coff_off, offsets + 2, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(base + goff_off, offsets + 4, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, stream) !=
             cudaSuccess)
         return res->status = SPINSIM_E_CUDA;
     if (K > 0) {
@@ -245,12 +251,16 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         ChainArgs ca;
         ca.sims = ia.sims;
         ca.chunk_offsets = reinterpret_cast<const int64_t*>(base + coff_off);
+        ca.group_offsets = reinterpret_cast<const int64_t*>(base + goff_off);
         ca.n_sims = 1;
         ca.n_chunks = chunks;
+        ca.n_groups = groups;
         ca.U = ia.U;
-        ca.run_prefix = reinterpret_cast<double*>(base + prefix_off);
-        ca.chunk_agg = reinterpret_cast<double*>(base + agg_off);
-        ca.chunk_start = reinterpret_cast<double*>(base + start_off);
+        ca.run_prefix = reinterpret_cast<double*>(base + chain_off + cl.prefix);
+        ca.chunk_agg = reinterpret_cast<double*>(base + chain_off + cl.agg);
+        ca.chunk_gprefix = reinterpret_cast<double*>(base + chain_off + cl.gprefix);
+        ca.group_agg = reinterpret_cast<double*>(base + chain_off + cl.gagg);
+        ca.group_start = reinterpret_cast<double*>(base + chain_off + cl.gstart);
         if (launch_chain(spin, ca, n_sm, stream) != cudaSuccess) return res->status = SPINSIM_E_CUDA;
     }
     res->n_samples = K;

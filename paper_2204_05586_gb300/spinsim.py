@@ -23,7 +23,6 @@ E_ARG, E_STEP_RATIO, E_NORM, E_NOMEM, E_CUDA, E_TIMEOUT, E_CAPACITY, E_UNSUPPORT
 WARN_MAGNUS = 1
 METHOD_CF4, METHOD_MIDPOINT, METHOD_HEUN = 0, 1, 2
 PREC_FP64, PREC_FP32_BULK = 0, 1
-FP32_DEFAULT_TAU = 4
 
 
 class SpinsimError(RuntimeError):

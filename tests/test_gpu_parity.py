@@ -84,10 +84,25 @@ def test_spin_one_operators(oracle_mod, prec):
     assert np.abs(np.linalg.det(U) - 1).max() < tol
 
 
-def test_fp32_matches_oracle_at_same_tau(oracle_mod):
+@pytest.mark.parametrize("tau", [-1, 0, 4])
+def test_fp32_matches_oracle_at_same_tau(oracle_mod, tau):
+    """FP32-bulk against the oracle run with the same number of squarings
+    (-1: the per-request choice the library reports)."""
     req = W.spin_one_sensing(t_end=2e-3)
-    (out,), _ = gpu_run([req], precision=S.PREC_FP32_BULK)
-    assert_parity(out, oracle_run(oracle_mod, req, tau=S.FP32_DEFAULT_TAU), 1e-5, "fp32 vs oracle tau4")
+    (out,), info = gpu_run([req], precision=S.PREC_FP32_BULK, tau=tau)
+    used = info["trotter_squares"]
+    assert tau < 0 or used == tau
+    assert_parity(out, oracle_run(oracle_mod, req, tau=used), 1e-5, f"fp32 vs oracle tau={used}")
+
+
+def test_automatic_tau_choice():
+    """FP32-bulk default: fewest squarings with the Lie-Trotter bound under
+    FP32 rounding -- 1 in the rotating frame of the sensing field, more in the
+    lab frame where the step angle is ~0.04 rad; FP64 keeps the paper's 24."""
+    req = W.spin_one_sensing(t_end=2e-4)
+    assert gpu_run([req], precision=S.PREC_FP32_BULK)[1]["trotter_squares"] == 1
+    assert gpu_run([req], precision=S.PREC_FP32_BULK, rotating_frame=False)[1]["trotter_squares"] == 9
+    assert gpu_run([req], precision=S.PREC_FP64)[1]["trotter_squares"] == 24
 
 
 # ------------------------------------------------- methods, frames, fields
