@@ -55,30 +55,41 @@ constexpr double kInvSqrt2 = 0.7071067811865475244008444;
 constexpr double kSqrt2 = 1.414213562373095048801689;
 
 // sin and cos of a small angle by their Taylor series (x - x^3/3! + ...,
-// 1 - x^2/2! + ...), which for |x| <= 1/16 leaves a truncation error below
-// 1e-19 relative with the terms used; larger angles use the libdevice call.
+// 1 - x^2/2! + ...); for |x| <= 1/16 the terms kept leave a relative
+// truncation error below 1e-19 in double and below 2e-11 in float (fewer
+// terms); larger angles use the libdevice call.
 template <typename R>
 SPINSIM_HD void small_sincos(R x, R& s, R& c)
 {
     if (fabs(x) <= R(0.0625)) {
         R x2 = x * x;
-        s = x * (R(1) - x2 * (R(1.0 / 6) - x2 * (R(1.0 / 120) - x2 * (R(1.0 / 5040) - x2 * R(1.0 / 362880)))));
-        c = R(1) - x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * (R(1.0 / 720) - x2 * (R(1.0 / 40320) - x2 * R(1.0 / 3628800)))));
+        if constexpr (sizeof(R) == 4) {
+            s = x * (R(1) - x2 * (R(1.0 / 6) - x2 * R(1.0 / 120)));
+            c = R(1) - x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * R(1.0 / 720)));
+        } else {
+            s = x * (R(1) - x2 * (R(1.0 / 6) - x2 * (R(1.0 / 120) - x2 * (R(1.0 / 5040) - x2 * R(1.0 / 362880)))));
+            c = R(1) - x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * (R(1.0 / 720) - x2 * (R(1.0 / 40320) - x2 * R(1.0 / 3628800)))));
+        }
     } else {
         sincos(x, &s, &c);
     }
 }
 
 // sin(x) - x and cos(x) - 1 without cancellation: Taylor series for
-// |x| <= 1/16 (truncation below 1e-19 relative), else from sincos with
-// cos(x) - 1 = -2 sin^2(x/2).
+// |x| <= 1/16 (relative truncation below 1e-19 in double, 5e-8 in float),
+// else from sincos with cos(x) - 1 = -2 sin^2(x/2).
 template <typename R>
 SPINSIM_HD void small_sincos_m(R x, R& sm, R& cm)
 {
     if (fabs(x) <= R(0.0625)) {
         R x2 = x * x;
-        sm = -x * x2 * (R(1.0 / 6) - x2 * (R(1.0 / 120) - x2 * (R(1.0 / 5040) - x2 * R(1.0 / 362880))));
-        cm = -x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * (R(1.0 / 720) - x2 * (R(1.0 / 40320) - x2 * R(1.0 / 3628800)))));
+        if constexpr (sizeof(R) == 4) {
+            sm = -x * x2 * (R(1.0 / 6) - x2 * R(1.0 / 120));
+            cm = -x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * R(1.0 / 720)));
+        } else {
+            sm = -x * x2 * (R(1.0 / 6) - x2 * (R(1.0 / 120) - x2 * (R(1.0 / 5040) - x2 * R(1.0 / 362880))));
+            cm = -x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * (R(1.0 / 720) - x2 * (R(1.0 / 40320) - x2 * R(1.0 / 3628800)))));
+        }
     } else {
         R s, c, h;
         sincos(x, &s, &c);
@@ -310,7 +321,16 @@ SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
     f.co = cmk(c.ebr * c1 - c.ebi * s1, fma(c.ebr, s1, c.ebi * c1));
     if (c.counter_on) {
         R s2, c2;
-        sincos(c.counter * tau, &s2, &c2);
+        if constexpr (sizeof(R) == 4) {
+            // FP32: the counter-rotating term's first-order part is replaced
+            // exactly at the end of the sample, so the fast hardware sincos
+            // (on an argument reduced to [-pi, pi]) only reaches second order.
+            R xc = c.counter * tau;
+            xc = fma(R(-kTwoPi), rintf(xc * R(1.0 / kTwoPi)), xc);
+            __sincosf(xc, &s2, &c2);
+        } else {
+            sincos(c.counter * tau, &s2, &c2);
+        }
         f.ct = cmk(c.ebr * c2 - c.ebi * s2, fma(c.ebr, s2, c.ebi * c2));
     } else {
         f.ct = cmk(R(0), R(0));
@@ -530,10 +550,12 @@ SPINSIM_HD void expm_one_res(R vx, R vy, R vz, R qd3, int tau, Res3<R>& e)
     R epr = R(1), epi = R(0);   // e^{i phi}
     R Phi = R(0);
     if (vp2 > R(0)) {
-        const R vp = sqrt(vp2);   // correctly rounded
-        epr = vx / vp;
-        epi = vy / vp;
-        Phi = vp * inv_n;
+        // Phi and e^{i phi} enter only the second-order rest (the first-order
+        // part is v itself), so a reciprocal square root is precise enough.
+        const R rinv = rsqrt(vp2);
+        epr = vx * rinv;
+        epi = vy * rinv;
+        Phi = vp2 * rinv * inv_n;
     }
     const R h0 = fma(R(-0.5), z, R(-0.5) * qd3);   // th_0 / 2
     const R h1 = qd3;                              // th_1 / 2
