@@ -42,13 +42,14 @@ INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 85504}
 
 
 def algorithmic_flops_per_step(spin_x2: int, tau: int) -> float:
-    """Algorithmic FP32 flops of one CF4 step (FMA = 2 flops).
-
-    Spin-one: two Lie-Trotter exponentials with tau residual squarings of a
-    3x3 complex matrix (27 complex MACs = 216 flops each) plus ~100 flops to
-    build T, two 3x3 complex products (216 each) and the field at two nodes:
-    432 tau + 650.  Spin-half: ~200 flops per step."""
-    return 432.0 * tau + 650.0 if spin_x2 == 2 else 200.0
+    """Algorithmic FP32 flops of one spin-one CF4 step (FMA = 2 flops): two
+    Lie-Trotter exponentials with tau residual squarings of a 3x3 complex
+    matrix (27 complex MACs = 216 flops each) plus ~100 flops to build T, two
+    3x3 complex products (216 each) and the field at two nodes: 432 tau + 650.
+    The timed workloads are spin-one only."""
+    if spin_x2 != 2:
+        raise ValueError("the flop model covers spin-one steps only")
+    return 432.0 * tau + 650.0
 
 
 class ClockSampler:
@@ -111,14 +112,32 @@ def dist_setup():
     return world, rank, local
 
 
-def barrier_max(value: float, world: int):
+def barrier_max(value: float, world: int, device: str = "cuda"):
+    """Maximum of `value` over all ranks (the slowest rank's time)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def barrier_sum(value: float, world: int, device: str = "cuda"):
+    """Sum of `value` over all ranks."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step: int, steps: int, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed (each rank runs
+    its own copy of the workload) divided by the slowest rank's time."""
+    return units_per_rank_step * steps * world / max_seconds
 
 
 def barrier(world: int):
@@ -184,7 +203,7 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = barrier_max(sum(step_ms) / 1e3, world)
-    value = steps_per_pass * args.steps * world / total_s
+    value = job_rate(steps_per_pass, args.steps, world, total_s)
     ms_per_step = total_s * 1e3 / args.steps
 
     # ---- roofline of the dominant kernel (integrate), from its live CUDA events
@@ -209,12 +228,13 @@ def run_ours(args, world, rank, local):
     sim.simulate(reqs, outs=outs_h, sync=True)
     e2e_steps = max(3, min(args.steps, 200))
     torch.cuda.synchronize()
+    barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         sim.simulate(reqs, outs=outs_h, sync=True)   # H2D of the tables, kernels, D2H of the outputs
     e2e_s = barrier_max(time.perf_counter() - t0, world)
     li = sim.last_launch()
-    e2e = {"value": steps_per_pass * e2e_steps * world / e2e_s, "unit": UNIT,
+    e2e = {"value": job_rate(steps_per_pass, e2e_steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(li["h2d_bytes"]), "d2h_bytes_per_step": int(li["d2h_bytes"]),
            "steps": e2e_steps}
     sim.close()
@@ -306,9 +326,9 @@ def run_serving(args, world, rank, local):
                 done[i] = True
         if nxt < n and not tickets:
             time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.001)))
-    span = time.perf_counter() - t0
+    span = barrier_max(time.perf_counter() - t0, world)
     clk = clocks.stop()
-    steps = W.total_steps(reqs)
+    steps = barrier_sum(W.total_steps(reqs), world)    # every rank serves its own stream
     line = {"metric": METRIC, "value": steps / span, "unit": UNIT, "n_gpus": world, "steps": n, "warmup": 8,
             "ms_per_step": span * 1e3 / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 bulk / f64 chain", "data": "synthetic",
@@ -322,6 +342,9 @@ def run_serving(args, world, rank, local):
     sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 # ---------------------------------------------------------- reference arm
