@@ -60,6 +60,11 @@ typedef enum {
 /* spinsim_result.flags bits (warnings; the request still ran). */
 #define SPINSIM_WARN_MAGNUS 1     /* an upper bound of ||H||_2 delta_t reaches the Magnus
                                      convergence radius xi = 1.0868687 (Sec. 1.2.2)       */
+#define SPINSIM_WARN_FP32_LAB 2   /* FP32-bulk with the rotating frame off and a z field: each
+                                     sample then turns by w_z dt_out and the FP32 rounding of
+                                     that rotation, alike in every sample, adds up over the
+                                     run; the 1e-5 FP32-bulk accuracy is held only in the
+                                     rotating frame (Sec. 1.2.5)                          */
 
 typedef enum {
     SPINSIM_METHOD_CF4 = 0,       /* Sec. 1.2.2 (default)                                    */
@@ -80,8 +85,8 @@ typedef struct {
     int32_t rotating_frame;       /* 1: per-interval rotating frame (default), 0: lab frame  */
     int32_t trotter_squares;      /* tau, n = 2^tau Lie-Trotter factors (spin-one), 0..40;
                                      -1 = default: 24 for FP64 (Sec. 1.2.3); for FP32-bulk,
-                                     per request the fewest squarings whose Lie-Trotter
-                                     error bound stays ten times under FP32 rounding      */
+                                     per request the fewest squarings whose splitting-error
+                                     bound, summed over all steps of the request, is <= 1e-6 */
     int32_t lanes_per_sample;     /* 0 = autotune; else 1, 2 or 4 threads share one U_k.
                                      Results do not depend on it (fixed reduction tree).   */
     int32_t threads_per_block;    /* 0 = autotune; else 64, 128 or 256                        */
@@ -139,6 +144,8 @@ typedef struct {
     int64_t n_samples;            /* out: K                                                  */
     int32_t status;               /* out: this request's spinsim_status                      */
     int32_t flags;                /* out: SPINSIM_WARN_* bits                                */
+    int32_t trotter_squares;      /* out: tau used for this request (0 for spin-half)        */
+    int32_t reserved;             /* set to 0                                                */
 } spinsim_result;
 
 typedef struct spinsim_s* spinsim_handle;

@@ -14,6 +14,12 @@
 #ifndef SPINSIM_HD
 #define SPINSIM_HD __host__ __device__ __forceinline__
 #endif
+// Rarely taken or once-per-sample paths (libm sin/cos with their range
+// reduction) are kept out of line, so the step loop stays small and its
+// register allocation is not sized for them.
+#ifndef SPINSIM_COLD
+#define SPINSIM_COLD __host__ __device__ __noinline__
+#endif
 
 namespace spinsim {
 
@@ -59,6 +65,32 @@ constexpr double kSqrt2 = 1.414213562373095048801689;
 // truncation error below 1e-19 in double and below 2e-11 in float (fewer
 // terms); larger angles use the libdevice call.
 template <typename R>
+struct SinCos {
+    R s, c;
+};
+
+template <typename R>
+SPINSIM_COLD SinCos<R> sincos_cold(R x)
+{
+    SinCos<R> r;
+    sincos(x, &r.s, &r.c);
+    return r;
+}
+
+// (sin x - x, cos x - 1) for |x| > 1/16: cos x - 1 = -2 sin^2(x/2).
+template <typename R>
+SPINSIM_COLD SinCos<R> sincos_m_cold(R x)
+{
+    R s, c;
+    sincos(x, &s, &c);
+    const R h = sin(R(0.5) * x);
+    SinCos<R> r;
+    r.s = s - x;
+    r.c = R(-2) * h * h;
+    return r;
+}
+
+template <typename R>
 SPINSIM_HD void small_sincos(R x, R& s, R& c)
 {
     if (fabs(x) <= R(0.0625)) {
@@ -71,7 +103,9 @@ SPINSIM_HD void small_sincos(R x, R& s, R& c)
             c = R(1) - x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * (R(1.0 / 720) - x2 * (R(1.0 / 40320) - x2 * R(1.0 / 3628800)))));
         }
     } else {
-        sincos(x, &s, &c);
+        const SinCos<R> r = sincos_cold(x);
+        s = r.s;
+        c = r.c;
     }
 }
 
@@ -91,11 +125,9 @@ SPINSIM_HD void small_sincos_m(R x, R& sm, R& cm)
             cm = -x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * (R(1.0 / 720) - x2 * (R(1.0 / 40320) - x2 * R(1.0 / 3628800)))));
         }
     } else {
-        R s, c, h;
-        sincos(x, &s, &c);
-        h = sin(R(0.5) * x);
-        sm = s - x;
-        cm = R(-2) * h * h;
+        const SinCos<R> r = sincos_m_cold(x);
+        sm = r.s;
+        cm = r.c;
     }
 }
 
@@ -169,10 +201,9 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c)
 {
     const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;
     const double beta = drive_phase_at(s, k);
-    R sb, cb;
-    sincos((R)beta, &sb, &cb);
-    c.ebr = cb;
-    c.ebi = sb;
+    const SinCos<R> eb = sincos_cold((R)beta);
+    c.ebr = eb.c;
+    c.ebi = eb.s;
 #pragma unroll
     for (int i = 0; i < 4; i++) split_hi_lo<R>(s.P[i], c.Ph[i], c.Pl[i]);
     c.za = (R)s.za;
@@ -219,7 +250,9 @@ template <int N>
 SPINSIM_HD void make_exact(const DevSim& s, int64_t k, double gsum, SampleExact& x)
 {
     const double beta = drive_phase_at(s, k);
-    sincos(beta, &x.eb_im, &x.eb_re);
+    const SinCos<double> eb = sincos_cold(beta);
+    x.eb_re = eb.c;
+    x.eb_im = eb.s;
     x.gsum = gsum;
     if (s.frame) {
         x.dco = s.w_co0 - gsum;
@@ -669,6 +702,40 @@ SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res2<R>& x)
     } else {
         expm_half_res(vx, vy, vz, x);
     }
+}
+
+// Premultiply the running residual by one step: X <- u X.  For CF4 the two
+// exponentials are applied one after the other, X <- E_2 (E_1 X) (the same
+// product as (E_2 E_1) X, Eq. cf4_implementation, in the same number of
+// operations), so only one step exponential is held in registers at a time.
+template <typename R, int METHOD>
+SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X)
+{
+    NodeField<R> f1, f2;
+    field_at(c, (lf + c.c1) * c.dt, f1);
+    if (METHOD == 1) f2 = f1;
+    else field_at(c, (lf + c.c2) * c.dt, f2);
+    R vx, vy, vz, wx = R(0), wy = R(0), wz = R(0);
+    exponent(c, f1, f2, false, vx, vy, vz);
+    if (METHOD == 0) exponent(c, f1, f2, true, wx, wy, wz);
+    Res3<R> e, Y;
+    expm_one_res(vx, vy, vz, c.qd3, tau, e);
+    res3_mul(e, X, Y);
+    if (METHOD == 0) {
+        expm_one_res(wx, wy, wz, c.qd3, tau, e);
+        res3_mul(e, Y, X);
+    } else {
+        X = Y;
+    }
+}
+
+template <typename R, int METHOD>
+SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res2<R>& X)
+{
+    Res2<R> x, Y;
+    step_res<R, METHOD>(c, lf, tau, x);
+    res2_mul(x, X, Y);
+    X = Y;
 }
 
 template <typename R>

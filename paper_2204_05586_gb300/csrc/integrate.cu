@@ -195,12 +195,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
                 Res X;
                 res_zero(X);
 #pragma unroll 1
-                for (int64_t l = lo; l < hi; l++) {
-                    Res x, Y;
-                    step_res<R, METHOD>(c, (R)l, c.tau, x);
-                    res_mul(x, X, Y);   // premultiply: U <- u_l U
-                    X = Y;
-                }
+                for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD>(c, (R)l, c.tau, X);   // U <- u_l U
                 seg[slot * kSegments + sg] = X;
             }
         }

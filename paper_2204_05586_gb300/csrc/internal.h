@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "spinsim.h"
+
 namespace spinsim {
 
 constexpr int kMaxPulses = 4;
@@ -107,23 +109,79 @@ inline ChainLayout chain_layout(int spin_x2, int64_t chunks, int64_t groups)
     return c;
 }
 
+// ------------------------------------------------- request warning bits
+constexpr double kMagnusXi = 1.0868687;   // Sec. 1.2.2: convergence radius of the Magnus series
+
+// Bounds of |w_perp| and |w_z| over the request (rad/s).
+inline void field_bounds(const spinsim_field& f, double& wperp, double& wz)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double pulses = 0.0;
+    for (int p = 0; p < f.n_pulses; p++) pulses += std::fabs(f.pulse_amp_hz[p]);
+    wperp = two_pi * (std::fabs(f.drive_x_hz) + std::fabs(f.drive_y_hz));
+    wz = two_pi * (std::fabs(f.bias_hz) + pulses);
+}
+
+// SPINSIM_WARN_MAGNUS: an upper bound of ||H||_2 delta_t against the Magnus
+// radius.  ||w.J||_2 = |w| j, ||Q||_2 = 2/3.
+inline int magnus_flags(const spinsim_request& r, int64_t L)
+{
+    double wperp, wz;
+    field_bounds(r.field, wperp, wz);
+    const double j = r.spin_x2 == 2 ? 1.0 : 0.5;
+    const double hnorm = std::sqrt(wperp * wperp + wz * wz) * j +
+                         (r.spin_x2 == 2 ? 6.283185307179586476925286766559 * std::fabs(r.field.quad_hz) * 2.0 / 3.0
+                                         : 0.0);
+    return hnorm * (r.dt_out / (double)L) >= kMagnusXi ? SPINSIM_WARN_MAGNUS : 0;
+}
+
+// SPINSIM_WARN_FP32_LAB: FP32-bulk carries every sample operator as the
+// identity plus an FP32 residual.  In the lab frame a z field turns each
+// sample by w_z dt_out (radians for MHz fields), so the residual is not small
+// and its rounding, the same in every sample of a constant bias, adds up
+// coherently over the run; the rotating frame removes that rotation.
+inline int precision_flags(int precision, int rotating_frame, const spinsim_request& r)
+{
+    double wperp, wz;
+    field_bounds(r.field, wperp, wz);
+    return precision == SPINSIM_PREC_FP32_BULK && !rotating_frame && wz > 0.0 ? SPINSIM_WARN_FP32_LAB : 0;
+}
+
 // Lie-Trotter squarings for a request (Sec. 1.2.3).  An explicit tau (>= 0)
 // is used as given; -1 selects 24 for FP64 (the paper's default) and, for
-// FP32-bulk, the smallest tau whose leapfrog error bound theta^2 / (3 4^tau)
-// (relative to the step angle theta) is below 6e-9, ten times under FP32
-// rounding -- the paper's criterion (fewest squarings at the smallest
-// error) applied to FP32 arithmetic.  theta bounds |H| delta_t in the frame.
-inline int choose_tau(int cfg_tau, int precision, int rotating_frame, double dt, double om_plus, double om_minus,
-                      double bias_w, double pulse_w, double q_w)
+// FP32-bulk, the fewest squarings whose splitting error, summed over every
+// exponential of the run, stays below kTrotterBudget.
+//
+// The bound: T = e^{A/2} e^{B} e^{A/2} with A = -i D, D = v_z J_z + v_q Q, and
+// B = -i Phi J_phi is exp(A + B + E3 + O(5th order)) with
+// E3 = [B,[B,A]]/12 - [A,[A,B]]/24 (symmetric splitting), so T^n with
+// n = 2^tau (each factor built from v/n) is exp(A + B + E3 / 4^tau).  For a
+// Hermitian X, |[X, Y]| <= spread(X) |Y - c I| for any c, which gives
+// |E3| <= Phi^2 sigma / 6 + sigma^2 Phi / 24 with sigma = spread(D)
+// <= 2 |v_z| + |v_q| and spread(Phi J_phi) = 2 Phi.  Each exponential then
+// departs from exp(A + B) by at most |E3| / 4^tau, and unitary propagation
+// adds these departures at most linearly over the run.
+//
+// The exponent bounds: |v_perp| <= (|wa| + |wb|) dt (|Om+| + |Om-|); in the
+// rotating frame |v_z| <= (|wa| + |wb|) dt sum_p |amp_p| (the pulse part
+// minus its midpoint value), in the lab frame plus |wa + wb| dt |w_bias|;
+// |v_q| = |wa + wb| dt |w_q|.
+constexpr double kTrotterBudget = 1e-6;   // a tenth of the FP32-bulk state accuracy (1e-5)
+
+inline int choose_tau(int cfg_tau, int precision, int rotating_frame, int n_exp, double wa, double wb, double dt,
+                      double om_perp, double bias_w, double pulse_w, double q_w, double steps)
 {
     if (cfg_tau >= 0) return cfg_tau;
     if (precision == 0) return 24;
-    const double z = rotating_frame ? pulse_w : bias_w + pulse_w;
-    const double theta = dt * (om_plus + om_minus + z + q_w);
+    const double wabs = std::fabs(wa) + std::fabs(wb), wsum = std::fabs(wa + wb);
+    const double phi = wabs * dt * om_perp;
+    const double vz = wabs * dt * pulse_w + (rotating_frame ? 0.0 : wsum * dt * bias_w);
+    const double vq = wsum * dt * q_w;
+    const double sigma = 2.0 * vz + vq;
+    double err = steps * (double)n_exp * (phi * phi * sigma / 6.0 + sigma * sigma * phi / 24.0);
     int tau = 0;
-    double bound = theta * theta / 3.0;
-    while (bound > 6e-9 && tau < 24) {
-        bound *= 0.25;
+    while (err > kTrotterBudget && tau < 24) {
+        err *= 0.25;
         tau++;
     }
     return tau;

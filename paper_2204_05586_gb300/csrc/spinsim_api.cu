@@ -28,7 +28,6 @@ using namespace spinsim;
 namespace {
 
 constexpr double kPi = 3.14159265358979323846264338327950288;
-constexpr double kMagnusXi = 1.0868687;   // Sec. 1.2.2: convergence radius of the Magnus series
 constexpr int64_t kMaxL = int64_t(1) << 24;  // step index stays exact in FP32
 
 // ------------------------------------------------------------- validation
@@ -72,16 +71,7 @@ Checked check_request(const spinsim_request* r)
         nrm += r->psi0[i] * r->psi0[i];
     }
     if (std::fabs(std::sqrt(nrm) - 1.0) > 1e-10) { c.status = SPINSIM_E_NORM; return c; }
-    // ||H||_2 delta_t against the Magnus radius.  ||w.J||_2 = |w| j, ||Q||_2 = 2/3.
-    const double two_pi = 2.0 * kPi;
-    double pulses = 0.0;
-    for (int p = 0; p < f.n_pulses; p++) pulses += std::fabs(f.pulse_amp_hz[p]);
-    const double wperp = two_pi * (std::fabs(f.drive_x_hz) + std::fabs(f.drive_y_hz));
-    const double wz = two_pi * (std::fabs(f.bias_hz) + pulses);
-    const double j = r->spin_x2 == 2 ? 1.0 : 0.5;
-    const double hnorm = std::sqrt(wperp * wperp + wz * wz) * j +
-                         (r->spin_x2 == 2 ? two_pi * std::fabs(f.quad_hz) * 2.0 / 3.0 : 0.0);
-    if (hnorm * (r->dt_out / (double)c.L) >= kMagnusXi) c.flags |= SPINSIM_WARN_MAGNUS;
+    c.flags = magnus_flags(*r, c.L);
     return c;
 }
 
@@ -403,10 +393,12 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
             // first-order part of every U_k is replaced by the exact gq)
             double pulse_w = 0.0;
             for (int p = 0; p < f.n_pulses; p++) pulse_w += two_pi * std::fabs(f.pulse_amp_hz[p]);
-            d.tau = choose_tau(h->cfg.trotter_squares, h->cfg.precision, h->cfg.rotating_frame, d.dt,
-                               std::fabs(om_plus), std::fabs(om_minus), two_pi * std::fabs(f.bias_hz), pulse_w,
-                               r.spin_x2 == 2 ? two_pi * std::fabs(f.quad_hz) : 0.0);
+            d.tau = choose_tau(h->cfg.trotter_squares, h->cfg.precision, h->cfg.rotating_frame, n_exp, wa, wb, d.dt,
+                               std::fabs(om_plus) + std::fabs(om_minus), two_pi * std::fabs(f.bias_hz), pulse_w,
+                               r.spin_x2 == 2 ? two_pi * std::fabs(f.quad_hz) : 0.0,
+                               (double)(d.K > 0 ? d.K - 1 : 0) * (double)d.L);
             if (r.spin_x2 == 1) d.tau = 0;   // closed form: no squarings
+            res[i].trotter_squares = d.tau;
             h->last.trotter_squares = std::max(h->last.trotter_squares, d.tau);
             const double vq = r.spin_x2 == 2 ? (wa + wb) * two_pi * f.quad_hz * d.dt : 0.0;
             double qd3 = vq / 3.0 / std::ldexp(1.0, d.tau);
@@ -851,7 +843,10 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
             else if (res[i].capacity < checked[i].K) checked[i].status = SPINSIM_E_CAPACITY;
         }
         res[i].status = checked[i].status;
+        if (checked[i].status == SPINSIM_OK)
+            checked[i].flags |= precision_flags(h->cfg.precision, h->cfg.rotating_frame, reqs[i]);
         res[i].flags = checked[i].flags;
+        res[i].trotter_squares = 0;
         res[i].n_samples = checked[i].status == SPINSIM_OK ? checked[i].K : 0;
         if (checked[i].status != SPINSIM_OK && first_err == SPINSIM_OK) first_err = checked[i].status;
     }
@@ -1018,6 +1013,7 @@ static int serving_pump(spinsim_s* h)
             Ticket& tk = h->tickets[ids[q]];
             tk.state = 1;
             tk.slot = (int)si;
+            tk.res->trotter_squares = res[q].trotter_squares;
             if (st != SPINSIM_OK) tk.res->status = st;
         }
         if (cudaEventRecord(s.done, s.stream) != cudaSuccess) return SPINSIM_E_CUDA;
@@ -1040,8 +1036,10 @@ int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result*
         if (!res->states) c.status = SPINSIM_E_ARG;
         else if (res->capacity < c.K) c.status = SPINSIM_E_CAPACITY;
     }
+    if (c.status == SPINSIM_OK) c.flags |= precision_flags(h->cfg.precision, h->cfg.rotating_frame, *req);
     res->status = c.status;
     res->flags = c.flags;
+    res->trotter_squares = 0;
     res->n_samples = c.status == SPINSIM_OK ? c.K : 0;
     const int64_t id = h->next_ticket++;
     Ticket tk;

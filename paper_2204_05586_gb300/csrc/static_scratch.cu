@@ -104,8 +104,9 @@ void fill_one(const spinsim_config& cfg, int tau, const spinsim_request& r, int6
     }
     double pulse_w = 0.0;
     for (int p = 0; p < f.n_pulses; p++) pulse_w += two_pi * std::fabs(f.pulse_amp_hz[p]);
-    d.tau = choose_tau(tau, cfg.precision, cfg.rotating_frame, d.dt, std::fabs(om_plus), std::fabs(om_minus),
-                       two_pi * std::fabs(f.bias_hz), pulse_w, r.spin_x2 == 2 ? two_pi * std::fabs(f.quad_hz) : 0.0);
+    d.tau = choose_tau(tau, cfg.precision, cfg.rotating_frame, n_exp, wa, wb, d.dt,
+                       std::fabs(om_plus) + std::fabs(om_minus), two_pi * std::fabs(f.bias_hz), pulse_w,
+                       r.spin_x2 == 2 ? two_pi * std::fabs(f.quad_hz) : 0.0, (double)(K > 0 ? K - 1 : 0) * (double)L);
     if (r.spin_x2 == 1) d.tau = 0;
     const double vq = r.spin_x2 == 2 ? (wa + wb) * two_pi * f.quad_hz * d.dt : 0.0;
     double qd3 = vq / 3.0 / std::ldexp(1.0, d.tau);
@@ -164,8 +165,10 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     int st = spinsim_counts(req, &K, &L);
     res->status = st;
     res->flags = 0;
+    res->trotter_squares = 0;
     res->n_samples = 0;
     if (st != SPINSIM_OK) return st;
+    res->flags = magnus_flags(*req, L) | precision_flags(cfg->precision, cfg->rotating_frame, *req);
     if (!res->states || res->capacity < K) {
         res->status = !res->states ? SPINSIM_E_ARG : SPINSIM_E_CAPACITY;
         return res->status;
@@ -212,6 +215,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     const int tau = cfg->trotter_squares;   // -1: chosen per request, as in spinsim_simulate
     DevSim d;
     fill_one(*cfg, tau, *req, K, L, res->states, res->spin, res->ops, d);
+    res->trotter_squares = d.tau;
     int64_t offsets[6] = {0, K, 0, chunks, 0, groups};
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     // Copies from pageable host memory: the source may be reused on return.

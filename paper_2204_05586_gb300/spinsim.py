@@ -21,6 +21,7 @@ MAX_PULSES = 4
 OK, PENDING = 0, 1
 E_ARG, E_STEP_RATIO, E_NORM, E_NOMEM, E_CUDA, E_TIMEOUT, E_CAPACITY, E_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7, -8
 WARN_MAGNUS = 1
+WARN_FP32_LAB = 2
 METHOD_CF4, METHOD_MIDPOINT, METHOD_HEUN = 0, 1, 2
 PREC_FP64, PREC_FP32_BULK = 0, 1
 
@@ -55,7 +56,7 @@ class spinsim_request(ctypes.Structure):
 class spinsim_result(ctypes.Structure):
     _fields_ = [("states", ctypes.c_void_p), ("spin", ctypes.c_void_p), ("ops", ctypes.c_void_p),
                 ("capacity", ctypes.c_int64), ("n_samples", ctypes.c_int64), ("status", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("trotter_squares", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class spinsim_launch_info(ctypes.Structure):
@@ -289,7 +290,7 @@ class Simulator:
     def _view(o, r):
         import torch
         K = o["K"]
-        out = {"status": r.status, "flags": r.flags, "K": K,
+        out = {"status": r.status, "flags": r.flags, "trotter_squares": r.trotter_squares, "K": K,
                "states": torch.view_as_complex(o["states"][:K]) if K else o["states"][:0, :, 0].to(torch.complex128)}
         out["spin"] = o["spin"][:K] if o["spin"] is not None else None
         out["ops"] = torch.view_as_complex(o["ops"][:K]) if o["ops"] is not None and K else None

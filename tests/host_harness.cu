@@ -90,4 +90,10 @@ void hh_small_sincos_m(double x, int fp32, double* out)
     if (fp32) { float s, c; small_sincos_m<float>((float)x, s, c); out[0] = s; out[1] = c; }
     else { double s, c; small_sincos_m<double>(x, s, c); out[0] = s; out[1] = c; }
 }
+// automatic Lie-Trotter squarings of a request (host-side rule)
+int hh_choose_tau(int cfg_tau, int precision, int frame, int n_exp, double wa, double wb, double dt, double om_perp,
+                  double bias_w, double pulse_w, double q_w, double steps)
+{
+    return choose_tau(cfg_tau, precision, frame, n_exp, wa, wb, dt, om_perp, bias_w, pulse_w, q_w, steps);
+}
 }

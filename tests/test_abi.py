@@ -111,3 +111,10 @@ def test_workload_generators_are_seeded():
     assert np.all(np.diff(arr) >= 0) and abs(len(reqs) / arr[-1] - 2000) < 200
     spins = np.array([r["spin_x2"] for r in reqs])
     assert abs((spins == 2).mean() - 0.7) < 0.05
+
+
+def test_warning_bits_match_header():
+    src = open(HEADER).read()
+    bits = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define SPINSIM_WARN_([A-Z0-9_]+)\s+(\d+)", src)}
+    assert bits == {"MAGNUS": S.WARN_MAGNUS, "FP32_LAB": S.WARN_FP32_LAB}
+    assert all(v & (v - 1) == 0 for v in bits.values()) and len(set(bits.values())) == len(bits)

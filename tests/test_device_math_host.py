@@ -34,6 +34,8 @@ def hh(tmp_path_factory):
     L.hh_product_half.argtypes = [DP, DP, DP]
     L.hh_node_phasor_sum.argtypes = [ctypes.c_double, ctypes.c_int64] + [ctypes.c_double] * 4 + [DP]
     L.hh_small_sincos_m.argtypes = [ctypes.c_double, ctypes.c_int, DP]
+    L.hh_choose_tau.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double] * 8
+    L.hh_choose_tau.restype = ctypes.c_int
     return L
 
 
@@ -145,3 +147,59 @@ def test_small_angle_functions(hh):
     out = np.zeros(2)
     hh.hh_small_sincos_m(0.0, 0, P(out))
     assert out[0] == 0.0 and out[1] == 0.0
+
+
+# ------------------------------------------------ automatic squarings (tau)
+CF4_A, CF4_B = (3 + 2 * np.sqrt(3)) / 12, (3 - 2 * np.sqrt(3)) / 12
+
+
+def splitting_bound(phi, vz, vq):
+    """|E3| bound of the symmetric splitting for exponent (Phi, v_z, v_q)."""
+    s = 2 * abs(vz) + abs(vq)
+    return phi * phi * s / 6 + s * s * phi / 24
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_splitting_error_bound_holds(seed):
+    """|T^n - exp(-i H)| <= |E3| / 4^tau (to leading order) for the leapfrog
+    T = e^{-iD/2} e^{-i Phi J_phi} e^{-iD/2}, D = v_z J_z + v_q Q; exact
+    exponentials from scipy, so this pins the bound, not the code using it."""
+    rng = np.random.default_rng(seed)
+    for _ in range(20):
+        phi, ang = rng.uniform(1e-3, 0.05), rng.uniform(0, 2 * np.pi)
+        vz, vq = rng.uniform(-0.05, 0.05), rng.uniform(-0.05, 0.05)
+        D = vz * JZ1 + vq * Q1
+        Jp = np.cos(ang) * JX1 + np.sin(ang) * JY1
+        exact = sl.expm(-1j * (phi * Jp + D))
+        for tau in (0, 1, 3):
+            n = 2 ** tau
+            Th = sl.expm(-0.5j * D / n) @ sl.expm(-1j * phi * Jp / n) @ sl.expm(-0.5j * D / n)
+            err = np.abs(np.linalg.matrix_power(Th, n) - exact).max()
+            assert err <= splitting_bound(phi, vz, vq) / 4 ** tau * 1.05 + 1e-15, (phi, vz, vq, tau, err)
+
+
+def tau_rule(frame, n_exp, wa, wb, dt, om_perp, bias_w, pulse_w, q_w, steps, budget=1e-6):
+    wabs, wsum = abs(wa) + abs(wb), abs(wa + wb)
+    phi = wabs * dt * om_perp
+    vz = wabs * dt * pulse_w + (0 if frame else wsum * dt * bias_w)
+    err = steps * n_exp * splitting_bound(phi, vz, wsum * dt * q_w)
+    return next(t for t in range(25) if err / 4 ** t <= budget or t == 24)
+
+
+def test_choose_tau_rule(hh):
+    tp = 2 * np.pi
+    # the 100 ms spin-one sensing run: 2 x 1 kHz drive, 50 Hz pulse, q = 400 Hz, dt 10 ns
+    sensing = dict(dt=1e-8, om_perp=tp * 2e3, bias_w=tp * 700e3, pulse_w=tp * 50, q_w=tp * 400, steps=9999900)
+    cases = [(1, 2, CF4_A, CF4_B), (0, 2, CF4_A, CF4_B), (1, 1, 1.0, 0.0), (1, 1, 0.5, 0.5)]
+    got = []
+    for frame, n_exp, wa, wb in cases:
+        for steps in (9999900, 19900, 1e12):
+            kw = dict(sensing, steps=steps)
+            t = hh.hh_choose_tau(-1, 1, frame, n_exp, wa, wb, kw["dt"], kw["om_perp"], kw["bias_w"],
+                                 kw["pulse_w"], kw["q_w"], kw["steps"])
+            assert t == tau_rule(frame, n_exp, wa, wb, **kw)
+            got.append(t)
+    assert got[0] == 0 and got[3] == 9          # rotating frame vs lab frame, full run
+    assert got[4] < got[3] and got[5] > got[3]  # shorter runs need fewer squarings
+    assert hh.hh_choose_tau(-1, 0, 1, 2, CF4_A, CF4_B, 1e-8, 1e4, 1e6, 0, 0, 1e7) == 24   # FP64 default
+    assert hh.hh_choose_tau(5, 1, 1, 2, CF4_A, CF4_B, 1e-8, 1e4, 1e6, 0, 0, 1e7) == 5     # explicit tau

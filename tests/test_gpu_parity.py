@@ -96,13 +96,42 @@ def test_fp32_matches_oracle_at_same_tau(oracle_mod, tau):
 
 
 def test_automatic_tau_choice():
-    """FP32-bulk default: fewest squarings with the Lie-Trotter bound under
-    FP32 rounding -- 1 in the rotating frame of the sensing field, more in the
-    lab frame where the step angle is ~0.04 rad; FP64 keeps the paper's 24."""
+    """FP32-bulk default: the fewest squarings whose splitting-error bound,
+    summed over the run, is <= 1e-6 -- none in the rotating frame of the
+    sensing field, 9 in the lab frame for the full 100 ms run (step angle
+    ~0.04 rad), fewer for a shorter run; FP64 keeps the paper's 24."""
+    full, short = W.spin_one_sensing(), W.spin_one_sensing(t_end=2e-4)
+    assert gpu_run([full], precision=S.PREC_FP32_BULK)[1]["trotter_squares"] == 0
+    assert gpu_run([full], precision=S.PREC_FP32_BULK, rotating_frame=False)[1]["trotter_squares"] == 9
+    (out,), info = gpu_run([short], precision=S.PREC_FP32_BULK, rotating_frame=False)
+    assert info["trotter_squares"] == 4 and out["trotter_squares"] == 4
+    assert gpu_run([short], precision=S.PREC_FP64)[1]["trotter_squares"] == 24
+    # per request within one batch; the launch reports the largest
+    outs, info = gpu_run([short, full, W.spin_half_rabi()], precision=S.PREC_FP32_BULK, rotating_frame=False)
+    assert [o["trotter_squares"] for o in outs] == [4, 9, 0] and info["trotter_squares"] == 9
+
+
+def test_fp32_lab_frame_is_flagged(oracle_mod):
+    """FP32-bulk without the rotating frame: each 1 us sample of the 700 kHz
+    field turns by 4.4 rad, the FP32 rounding of that rotation is the same in
+    every sample and adds up, so the request is flagged (the run still
+    completes and stays normalised); in the rotating frame, and in FP64, it is
+    not flagged and meets the accuracy targets."""
     req = W.spin_one_sensing(t_end=2e-4)
-    assert gpu_run([req], precision=S.PREC_FP32_BULK)[1]["trotter_squares"] == 1
-    assert gpu_run([req], precision=S.PREC_FP32_BULK, rotating_frame=False)[1]["trotter_squares"] == 9
-    assert gpu_run([req], precision=S.PREC_FP64)[1]["trotter_squares"] == 24
+    ref = oracle_run(oracle_mod, req, frame=False)
+    (lab,), _ = gpu_run([req], precision=S.PREC_FP32_BULK, rotating_frame=False)
+    assert lab["status"] == S.OK and lab["flags"] & S.WARN_FP32_LAB
+    st = lab["states"].cpu().numpy()
+    assert np.abs(np.linalg.norm(st, axis=1) - 1).max() < 1e-8
+    err = np.abs(st - ref["states"]).max()
+    print(f"\nFP32-bulk, lab frame, 0.2 ms sensing field: max |dpsi| = {err:.2e}")
+    assert err < 1e-2
+    (fr,), _ = gpu_run([req], precision=S.PREC_FP32_BULK)
+    assert fr["flags"] == 0
+    assert_parity(fr, oracle_run(oracle_mod, req), 1e-5, "rotating frame")
+    (f64,), _ = gpu_run([req], precision=S.PREC_FP64, rotating_frame=False)
+    assert f64["flags"] == 0
+    assert_parity(f64, ref, 1e-10, "FP64 lab frame")
 
 
 # ------------------------------------------------- methods, frames, fields
