@@ -131,6 +131,42 @@ SPINSIM_HD void small_sincos_m(R x, R& sm, R& cm)
     }
 }
 
+// Small-angle forms of the two series above, for arguments the host has
+// bounded by |x| <= kTinyAngleBound = 2^-6 (every step angle of a
+// rotating-frame FP32 run, see small_angle_request):
+// two terms leave a relative truncation error of at most x^4/120 (sin),
+// x^6/720 (cos), x^4/840 (sin x - x) and x^4/360 (cos x - 1), all below
+// 2e-9, so no branch and no libm fallback is needed.
+template <typename R>
+SPINSIM_HD void small_sincos_tiny(R x, R& s, R& c)
+{
+    const R x2 = x * x;
+    s = fma(x * x2, R(-1.0 / 6), x);
+    c = fma(x2, fma(x2, R(1.0 / 24), R(-0.5)), R(1));
+}
+
+template <typename R>
+SPINSIM_HD void small_sincos_m_tiny(R x, R& sm, R& cm)
+{
+    const R x2 = x * x;
+    sm = x * x2 * fma(x2, R(1.0 / 120), R(-1.0 / 6));
+    cm = x2 * fma(x2, R(1.0 / 24), R(-0.5));
+}
+
+template <typename R, bool SMALL>
+SPINSIM_HD void step_sincos(R x, R& s, R& c)
+{
+    if constexpr (SMALL) small_sincos_tiny(x, s, c);
+    else small_sincos(x, s, c);
+}
+
+template <typename R, bool SMALL>
+SPINSIM_HD void step_sincos_m(R x, R& sm, R& cm)
+{
+    if constexpr (SMALL) small_sincos_m_tiny(x, sm, cm);
+    else small_sincos_m(x, sm, cm);
+}
+
 // -------------------------------------------------------------------------
 // Per-sample context: the field family inside interval k, reduced to values
 // in the bulk type R.  Large phases (the drive phase at t_{k-1}, the pulse
@@ -153,6 +189,8 @@ struct SampleCtx {
     R Ph[4], Pl[4];                 // (hi, lo) of P[0..3]
     R za, zb, zbias;
     R qd3;
+    R inv_n;                        // 2^-tau
+    R q1;                           // first-order Q coefficient of one exponential: 3 qd3 2^tau
     R dt, c1, c2;
     R amp[kMaxPulses], u0[kMaxPulses], invw[kMaxPulses], ghat[kMaxPulses];
     int np;
@@ -215,6 +253,8 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c)
     c.c2 = (R)s.c2;
     c.np = s.n_pulses;
     c.tau = s.tau;
+    c.inv_n = ldexp(R(1), -s.tau);
+    c.q1 = R(3) * ldexp(c.qd3, s.tau);
     c.counter_on = s.counter_on != 0;
     double gsum = 0.0;
 #pragma unroll
@@ -346,11 +386,11 @@ struct NodeField {
     R z;            // w_z' without the lab-frame bias
 };
 
-template <typename R>
+template <typename R, bool SMALL = false>
 SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
 {
     R s1, c1;
-    small_sincos(c.co * tau, s1, c1);
+    step_sincos<R, SMALL>(c.co * tau, s1, c1);
     f.co = cmk(c.ebr * c1 - c.ebi * s1, fma(c.ebr, s1, c.ebi * c1));
     if (c.counter_on) {
         R s2, c2;
@@ -574,10 +614,12 @@ SPINSIM_HD void res3_mul(const Res3<R>& A, const Res3<R>& B, Res3<R>& C)
 // cancellation from sin x - x and cos x - 1.  A residual squaring
 // (a + 2I) a = 2a + a^2 doubles the first-order part exactly and adds a^2 to
 // the rest.
-template <typename R>
-SPINSIM_HD void expm_one_res(R vx, R vy, R vz, R qd3, int tau, Res3<R>& e)
+// expm_one_res_n takes 2^-tau and the first-order quadrupole coefficient
+// q1 = 3 qd3 2^tau precomputed (once per sample) and, with SMALL, uses the
+// small-angle series (all of h_0, h_1, h_2, Phi/2 bounded by 2^-6 on the host).
+template <typename R, bool SMALL = false>
+SPINSIM_HD void expm_one_res_n(R vx, R vy, R vz, R qd3, int tau, R inv_n, R q1, Res3<R>& e)
 {
-    const R inv_n = ldexp(R(1), -tau);
     const R z = vz * inv_n;
     const R vp2 = vx * vx + vy * vy;
     R epr = R(1), epi = R(0);   // e^{i phi}
@@ -595,10 +637,10 @@ SPINSIM_HD void expm_one_res(R vx, R vy, R vz, R qd3, int tau, Res3<R>& e)
     const R h2 = fma(R(0.5), z, R(-0.5) * qd3);    // th_2 / 2
     const R P = R(0.5) * Phi;
     R sm0, cm0, sm1, cm1, sm2, cm2, smP, cmP;
-    small_sincos_m(h0, sm0, cm0);
-    small_sincos_m(h1, sm1, cm1);
-    small_sincos_m(h2, sm2, cm2);
-    small_sincos_m(P, smP, cmP);
+    step_sincos_m<R, SMALL>(h0, sm0, cm0);
+    step_sincos_m<R, SMALL>(h1, sm1, cm1);
+    step_sincos_m<R, SMALL>(h2, sm2, cm2);
+    step_sincos_m<R, SMALL>(P, smP, cmP);
     const R s0 = h0 + sm0, c0 = R(1) + cm0;       // sin, cos of th_j / 2
     const R s1 = h1 + sm1, c1 = R(1) + cm1;
     const R s2 = h2 + sm2, c2 = R(1) + cm2;
@@ -652,7 +694,13 @@ SPINSIM_HD void expm_one_res(R vx, R vy, R vz, R qd3, int tau, Res3<R>& e)
     e.m[0][1] = cmul(b01, em); e.m[1][0] = cmul(b01, ep);
     e.m[1][2] = cmul(b12, em); e.m[2][1] = cmul(b12, ep);
     e.m[0][2] = cmul(b02, em2); e.m[2][0] = cmul(b02, ep2);
-    e.g[0] = vx; e.g[1] = vy; e.g[2] = vz; e.g[3] = R(3) * ldexp(qd3, tau);
+    e.g[0] = vx; e.g[1] = vy; e.g[2] = vz; e.g[3] = q1;
+}
+
+template <typename R, bool SMALL = false>
+SPINSIM_HD void expm_one_res(R vx, R vy, R vz, R qd3, int tau, Res3<R>& e)
+{
+    expm_one_res_n<R, SMALL>(vx, vy, vz, qd3, tau, ldexp(R(1), -tau), R(3) * ldexp(qd3, tau), e);
 }
 
 // -------------------------------------------------------------------------
@@ -683,14 +731,14 @@ SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res3<R>& x)
     }
 }
 
-template <typename R, int METHOD>
+template <typename R, int METHOD, bool SMALL = false>
 SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res2<R>& x)
 {
     (void)tau;
     NodeField<R> f1, f2;
-    field_at(c, (lf + c.c1) * c.dt, f1);
+    field_at<R, SMALL>(c, (lf + c.c1) * c.dt, f1);
     if (METHOD == 1) f2 = f1;
-    else field_at(c, (lf + c.c2) * c.dt, f2);
+    else field_at<R, SMALL>(c, (lf + c.c2) * c.dt, f2);
     R vx, vy, vz;
     exponent(c, f1, f2, false, vx, vy, vz);
     if (METHOD == 0) {
@@ -708,32 +756,32 @@ SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res2<R>& x)
 // exponentials are applied one after the other, X <- E_2 (E_1 X) (the same
 // product as (E_2 E_1) X, Eq. cf4_implementation, in the same number of
 // operations), so only one step exponential is held in registers at a time.
-template <typename R, int METHOD>
+template <typename R, int METHOD, bool SMALL = false>
 SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X)
 {
     NodeField<R> f1, f2;
-    field_at(c, (lf + c.c1) * c.dt, f1);
+    field_at<R, SMALL>(c, (lf + c.c1) * c.dt, f1);
     if (METHOD == 1) f2 = f1;
-    else field_at(c, (lf + c.c2) * c.dt, f2);
+    else field_at<R, SMALL>(c, (lf + c.c2) * c.dt, f2);
     R vx, vy, vz, wx = R(0), wy = R(0), wz = R(0);
     exponent(c, f1, f2, false, vx, vy, vz);
     if (METHOD == 0) exponent(c, f1, f2, true, wx, wy, wz);
     Res3<R> e, Y;
-    expm_one_res(vx, vy, vz, c.qd3, tau, e);
+    expm_one_res_n<R, SMALL>(vx, vy, vz, c.qd3, tau, c.inv_n, c.q1, e);
     res3_mul(e, X, Y);
     if (METHOD == 0) {
-        expm_one_res(wx, wy, wz, c.qd3, tau, e);
+        expm_one_res_n<R, SMALL>(wx, wy, wz, c.qd3, tau, c.inv_n, c.q1, e);
         res3_mul(e, Y, X);
     } else {
         X = Y;
     }
 }
 
-template <typename R, int METHOD>
+template <typename R, int METHOD, bool SMALL = false>
 SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res2<R>& X)
 {
     Res2<R> x, Y;
-    step_res<R, METHOD>(c, lf, tau, x);
+    step_res<R, METHOD, SMALL>(c, lf, tau, x);
     res2_mul(x, X, Y);
     X = Y;
 }

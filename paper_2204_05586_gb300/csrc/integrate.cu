@@ -148,7 +148,7 @@ __device__ __forceinline__ void store_identity(int N, double* out)
 }
 
 // ------------------------------------------------------------------- kernel
-template <int N, typename R, int G, int METHOD>
+template <int N, typename R, int G, int METHOD, bool SMALL>
 __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
 {
     using Res = typename ResType<N, R>::type;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
                 Res X;
                 res_zero(X);
 #pragma unroll 1
-                for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD>(c, (R)l, c.tau, X);   // U <- u_l U
+                for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL>(c, (R)l, c.tau, X);   // U <- u_l U
                 seg[slot * kSegments + sg] = X;
             }
         }
@@ -220,38 +220,46 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
 }
 
 // ----------------------------------------------------------------- launchers
-template <int N, typename R, int G, int METHOD>
+template <int N, typename R, int G, int METHOD, bool SMALL>
 static void* kernel_ptr()
 {
-    return (void*)integrate_kernel<N, R, G, METHOD>;
+    return (void*)integrate_kernel<N, R, G, METHOD, SMALL>;
 }
 
-template <int N, typename R, int METHOD>
+template <int N, typename R, int METHOD, bool SMALL>
 static void* pick_lanes(int lanes)
 {
     switch (lanes) {
-        case 1: return kernel_ptr<N, R, 1, METHOD>();
-        case 2: return kernel_ptr<N, R, 2, METHOD>();
-        case 4: return kernel_ptr<N, R, 4, METHOD>();
+        case 1: return kernel_ptr<N, R, 1, METHOD, SMALL>();
+        case 2: return kernel_ptr<N, R, 2, METHOD, SMALL>();
+        case 4: return kernel_ptr<N, R, 4, METHOD, SMALL>();
         default: return nullptr;
     }
 }
 
-template <int N, typename R>
+template <int N, typename R, bool SMALL>
 static void* pick_method(int method, int lanes)
 {
     switch (method) {
-        case 0: return pick_lanes<N, R, 0>(lanes);
-        case 1: return pick_lanes<N, R, 1>(lanes);
-        case 2: return pick_lanes<N, R, 2>(lanes);
+        case 0: return pick_lanes<N, R, 0, SMALL>(lanes);
+        case 1: return pick_lanes<N, R, 1, SMALL>(lanes);
+        case 2: return pick_lanes<N, R, 2, SMALL>(lanes);
         default: return nullptr;
     }
 }
 
-static void* select_kernel(int spin_x2, int precision, int method, int lanes)
+// The small-angle variant exists for FP32-bulk only; FP64 keeps the general
+// series (its terms are sized for double precision).
+static void* select_kernel(int spin_x2, int precision, int method, int lanes, bool small)
 {
-    if (spin_x2 == 2) return precision ? pick_method<3, float>(method, lanes) : pick_method<3, double>(method, lanes);
-    if (spin_x2 == 1) return precision ? pick_method<2, float>(method, lanes) : pick_method<2, double>(method, lanes);
+    if (spin_x2 == 2) {
+        if (!precision) return pick_method<3, double, false>(method, lanes);
+        return small ? pick_method<3, float, true>(method, lanes) : pick_method<3, float, false>(method, lanes);
+    }
+    if (spin_x2 == 1) {
+        if (!precision) return pick_method<2, double, false>(method, lanes);
+        return small ? pick_method<2, float, true>(method, lanes) : pick_method<2, float, false>(method, lanes);
+    }
     return nullptr;
 }
 
@@ -268,9 +276,10 @@ size_t integrate_smem_bytes(int spin_x2, int precision, int lanes, int block)
 // Must be called (outside stream capture) before the first launch of a
 // (spin, precision, method, lanes) kernel: it raises the kernel's dynamic
 // shared-memory limit to what a 256-thread block needs.
-cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int lanes, int block, int* blocks_per_sm)
+cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int lanes, int block, bool small,
+                                int* blocks_per_sm)
 {
-    void* k = select_kernel(spin_x2, precision, method, lanes);
+    void* k = select_kernel(spin_x2, precision, method, lanes, small);
     if (!k) return cudaErrorInvalidValue;
     size_t smem_max = integrate_smem_bytes(spin_x2, precision, lanes, 256);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
@@ -279,10 +288,10 @@ cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int lane
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, smem);
 }
 
-cudaError_t launch_integrate(int spin_x2, int precision, int method, int lanes, int block, int grid,
+cudaError_t launch_integrate(int spin_x2, int precision, int method, int lanes, int block, int grid, bool small,
                              const IntegrateArgs& a, cudaStream_t stream)
 {
-    void* k = select_kernel(spin_x2, precision, method, lanes);
+    void* k = select_kernel(spin_x2, precision, method, lanes, small);
     if (!k || block % 32 != 0 || block < 32 || block > 256 || grid < 1) return cudaErrorInvalidValue;
     size_t smem = integrate_smem_bytes(spin_x2, precision, lanes, block);
     IntegrateArgs args = a;

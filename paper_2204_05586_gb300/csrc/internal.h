@@ -187,11 +187,27 @@ inline int choose_tau(int cfg_tau, int precision, int rotating_frame, int n_exp,
     return tau;
 }
 
-// Host-side launchers (integrate.cu, chain.cu).  precision: 0 FP64, 1 FP32-bulk.
-cudaError_t launch_integrate(int spin_x2, int precision, int method, int lanes, int block, int grid,
+// Largest step angle for which the FP32 kernels may use the two-term
+// small-angle series (device_math.cuh).
+constexpr double kTinyAngleBound = 0.015625;
+
+// Host-side parameter set-up (params.cu).
+// fill_devsim: the kernels' record of one validated request (K output
+// samples, L steps per sample); the caller sets the output pointers and the
+// sample/chunk/group offsets.
+void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L, DevSim& d);
+// small_angle_request: true when the request runs in FP32-bulk and every
+// argument of the per-step sine/cosine series is bounded by kTinyAngleBound.
+bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, int64_t L);
+
+// Host-side launchers (integrate.cu, chain.cu).  precision: 0 FP64, 1 FP32-bulk;
+// small: the small-angle variant (FP32-bulk only, all requests of the launch
+// satisfying small_angle_request).
+cudaError_t launch_integrate(int spin_x2, int precision, int method, int lanes, int block, int grid, bool small,
                              const IntegrateArgs& a, cudaStream_t stream);
 size_t integrate_smem_bytes(int spin_x2, int precision, int lanes, int block);
-cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int lanes, int block, int* blocks_per_sm);
+cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int lanes, int block, bool small,
+                                int* blocks_per_sm);
 cudaError_t launch_chain(int spin_x2, const ChainArgs& a, int n_sm, cudaStream_t stream);
 
 }  // namespace spinsim

@@ -1,0 +1,158 @@
+// params.cu -- the per-simulation parameter record (DevSim) the kernels read,
+// precomputed on the host in FP64 from a request and the handle's
+// configuration.  Shared by spinsim_simulate / spinsim_submit and by
+// spinsim_simulate_static.
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace spinsim {
+
+namespace {
+
+constexpr double kTwoPiH = 6.283185307179586476925286766559;
+
+// Node offsets (units of delta_t) and weights of the method.  CF4
+// (Eqs. cf4_sample_1/2): t_{1,2} = t + (1 -+ 1/sqrt3) dt/2,
+// a = (3 + 2 sqrt3)/12, b = (3 - 2 sqrt3)/12, two exponentials.  Midpoint and
+// Heun sampling (Sec. 1.3.1): one exponential.
+struct MethodNodes {
+    double c1, c2, wa, wb;
+    int n_exp;
+};
+
+MethodNodes method_nodes(int method)
+{
+    if (method == SPINSIM_METHOD_CF4)
+        return {0.2113248654051871177454256, 0.7886751345948128822545744, 0.5386751345948128822545744,
+                -0.03867513459481288225457439, 2};
+    if (method == SPINSIM_METHOD_MIDPOINT) return {0.5, 0.5, 1.0, 0.0, 1};
+    return {0.0, 1.0, 0.5, 0.5, 1};
+}
+
+double pulse_weight(const spinsim_field& f)
+{
+    double w = 0.0;
+    for (int p = 0; p < f.n_pulses; p++) w += kTwoPiH * std::fabs(f.pulse_amp_hz[p]);
+    return w;
+}
+
+}  // namespace
+
+// Every argument of the per-step sine/cosine series, bounded from the field's
+// amplitudes:
+//   the co-rotating drive phase (w_d - w_r) tau, tau < Delta_t, with
+//   |w_d - w_r| <= |w_co0| + sum_p |amp_p| in the frame (w_co0 = 2 pi f_d in the lab);
+//   the half phases h_j of the Lie-Trotter diagonal, |h_j| <= |z|/2 + |q|/3 with
+//   |z| <= (|a| + |b|) dt (sum_p |amp_p| (+ 2 pi |B| in the lab)), |q| = |a + b| dt 2 pi |q_hz|;
+//   Phi/2 <= (|a| + |b|) dt (|Om+| + |Om-|) / 2.
+// These bounds hold for every number of squarings (each divides the angles by 2^tau).
+bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, int64_t L)
+{
+    if (cfg.precision != SPINSIM_PREC_FP32_BULK || L < 1) return false;
+    const MethodNodes m = method_nodes(cfg.method);
+    const spinsim_field& f = r.field;
+    const double dt = r.dt_out / (double)L;
+    const double wabs = std::fabs(m.wa) + std::fabs(m.wb), wsum = std::fabs(m.wa + m.wb);
+    const double pulse_w = pulse_weight(f);
+    const bool frame = cfg.rotating_frame != 0;
+    const double w_co = frame ? std::fabs(kTwoPiH * (f.drive_hz - f.bias_hz)) + pulse_w : std::fabs(kTwoPiH * f.drive_hz);
+    const double co = w_co * r.dt_out;
+    const double z = wabs * dt * (pulse_w + (frame ? 0.0 : kTwoPiH * std::fabs(f.bias_hz)));
+    const double q = r.spin_x2 == 2 ? wsum * dt * kTwoPiH * std::fabs(f.quad_hz) : 0.0;
+    const double om_perp = 0.5 * kTwoPiH * (std::fabs(f.drive_x_hz + f.drive_y_hz) + std::fabs(f.drive_x_hz - f.drive_y_hz));
+    const double half_phi = 0.5 * wabs * dt * om_perp;
+    const double h = 0.5 * z + q / 3.0;
+    return co <= kTinyAngleBound && h <= kTinyAngleBound && half_phi <= kTinyAngleBound;
+}
+
+void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L, DevSim& d)
+{
+    std::memset(&d, 0, sizeof(d));
+    const spinsim_field& f = r.field;
+    d.K = K;
+    d.L = L;
+    d.t_start = r.t_start;
+    d.dt_out = r.dt_out;
+    d.dt = r.dt_out / (double)L;
+    d.drive_hz = f.drive_hz;
+    d.drive_phase = f.drive_phase;
+    const double ax = kTwoPiH * f.drive_x_hz, ay = kTwoPiH * f.drive_y_hz;
+    const double om_plus = 0.5 * (ax + ay), om_minus = 0.5 * (ax - ay);
+    const MethodNodes mn = method_nodes(cfg.method);
+    const double wa = mn.wa, wb = mn.wb;
+    d.c1 = mn.c1;
+    d.c2 = mn.c2;
+    d.P[0] = om_plus * wa * d.dt;
+    d.P[1] = om_plus * wb * d.dt;
+    d.P[2] = om_minus * wa * d.dt;
+    d.P[3] = om_minus * wb * d.dt;
+    d.counter_on = om_minus != 0.0 ? 1 : 0;
+    d.za = wa * d.dt;
+    d.zb = wb * d.dt;
+    d.frame = cfg.rotating_frame ? 1 : 0;
+    d.zbias = d.frame ? 0.0 : kTwoPiH * f.bias_hz * (wa + wb) * d.dt;
+    if (d.frame) {
+        d.w_co0 = kTwoPiH * (f.drive_hz - f.bias_hz);
+        d.w_counter0 = kTwoPiH * (f.drive_hz + f.bias_hz);
+        const double th = kTwoPiH * f.bias_hz * r.dt_out;
+        d.exit_re = std::cos(th);
+        d.exit_im = -std::sin(th);
+        d.exit_half_re = std::cos(0.5 * th);
+        d.exit_half_im = -std::sin(0.5 * th);
+    } else {
+        d.w_co0 = d.w_counter0 = kTwoPiH * f.drive_hz;
+        d.exit_re = d.exit_half_re = 1.0;
+        d.exit_im = d.exit_half_im = 0.0;
+    }
+    const double pulse_w = pulse_weight(f);
+    d.tau = choose_tau(cfg.trotter_squares, cfg.precision, cfg.rotating_frame, mn.n_exp, wa, wb, d.dt,
+                       std::fabs(om_plus) + std::fabs(om_minus), kTwoPiH * std::fabs(f.bias_hz), pulse_w,
+                       r.spin_x2 == 2 ? kTwoPiH * std::fabs(f.quad_hz) : 0.0, (double)(K > 0 ? K - 1 : 0) * (double)L);
+    if (r.spin_x2 == 1) d.tau = 0;   // closed form: no squarings
+    // quadrupole coefficient of one exponential, over 3 and 2^tau, as the bulk
+    // type holds it (its rounding only reaches second order: the first-order
+    // part of every U_k is replaced by the exact gq)
+    const double vq = r.spin_x2 == 2 ? (wa + wb) * kTwoPiH * f.quad_hz * d.dt : 0.0;
+    double qd3 = vq / 3.0 / std::ldexp(1.0, d.tau);
+    if (cfg.precision == SPINSIM_PREC_FP32_BULK) qd3 = (double)(float)qd3;
+    d.qd3 = qd3;
+    d.om_plus = om_plus;
+    d.om_minus = om_minus;
+    d.W1 = mn.n_exp == 2 ? wa + wb : wa;
+    d.W2 = mn.n_exp == 2 ? wa + wb : wb;
+    d.gq = r.spin_x2 == 2 ? kTwoPiH * f.quad_hz * r.dt_out : 0.0;
+    d.normalize_out = cfg.precision == SPINSIM_PREC_FP32_BULK ? 1 : 0;
+    // Taylor tables of the node-phasor sums (direct FP64 summation)
+    d.tay_ok = L <= 65536 ? 1 : 0;
+    if (d.tay_ok) {
+        const double th_co = d.w_co0 * d.dt, th_ct = d.w_counter0 * d.dt;
+        double co[8] = {0}, ct[8] = {0};
+        const double Wn[2] = {d.W1, d.W2}, cn[2] = {d.c1, d.c2};
+        for (int64_t l = 0; l < L; l++)
+            for (int nn = 0; nn < 2; nn++) {
+                if (Wn[nn] == 0.0) continue;
+                const double x = (double)l + cn[nn];
+                double pw = Wn[nn];
+                const double sa = std::sin(th_co * x), ca = std::cos(th_co * x);
+                const double sb = std::sin(th_ct * x), cb = std::cos(th_ct * x);
+                for (int m = 0; m < 4; m++) {
+                    co[2 * m] += pw * ca; co[2 * m + 1] += pw * sa;
+                    ct[2 * m] += pw * cb; ct[2 * m + 1] += pw * sb;
+                    pw *= x;
+                }
+            }
+        for (int m = 0; m < 8; m++) { d.tay_co[m] = co[m]; d.tay_ct[m] = ct[m]; }
+    }
+    d.n_pulses = f.n_pulses;
+    for (int p = 0; p < f.n_pulses; p++) {
+        d.amp[p] = kTwoPiH * f.pulse_amp_hz[p];
+        d.centre[p] = f.pulse_centre_s[p];
+        d.inv_w[p] = 1.0 / f.pulse_width_s[p];
+    }
+    for (int e = 0; e < 6; e++) d.psi0[e] = r.psi0[e];
+    d.spin_x2 = r.spin_x2;
+}
+
+}  // namespace spinsim

@@ -27,7 +27,6 @@ using namespace spinsim;
 
 namespace {
 
-constexpr double kPi = 3.14159265358979323846264338327950288;
 constexpr int64_t kMaxL = int64_t(1) << 24;  // step index stays exact in FP32
 
 // ------------------------------------------------------------- validation
@@ -35,6 +34,7 @@ struct Checked {
     int status = SPINSIM_OK;
     int flags = 0;
     int64_t K = 0, L = 0;
+    bool small = false;   // small_angle_request under the handle's configuration
 };
 
 Checked check_request(const spinsim_request* r)
@@ -106,6 +106,7 @@ struct PinnedBuf {
 
 struct Group {
     int spin_x2;
+    bool small = true;             // every request of the group takes the small-angle kernel
     std::vector<int64_t> idx;      // request indices
     int64_t samples = 0, chunks = 0, groups = 0;
     size_t sims_off = 0, soff_off = 0, coff_off = 0, goff_off = 0, counter_off = 0, U_off = 0, chain_off = 0;
@@ -129,10 +130,11 @@ struct Plan {
 };
 
 struct TuneKey {
-    int spin, precision, method, tau, bucket;
+    int spin, precision, method, tau, bucket, small;
     bool operator<(const TuneKey& o) const
     {
-        return std::tie(spin, precision, method, tau, bucket) < std::tie(o.spin, o.precision, o.method, o.tau, o.bucket);
+        return std::tie(spin, precision, method, tau, bucket, small) <
+               std::tie(o.spin, o.precision, o.method, o.tau, o.bucket, o.small);
     }
 };
 struct TuneVal {
@@ -174,7 +176,7 @@ struct spinsim_s {
     Arena arena;
     PinnedBuf pinned;
     spinsim_launch_info last{};
-    std::map<std::tuple<int, int, int>, int> occ;   // (spin, lanes, block) -> resident blocks per SM
+    std::map<std::tuple<int, int, int, int>, int> occ;   // (spin, lanes, block, small) -> resident blocks per SM
     std::vector<char> table_tmp;                     // host copy of the next parameter table
     // graph cache: one batch signature
     std::vector<uint64_t> graph_sig;
@@ -261,6 +263,7 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
         for (int64_t i = 0; i < n; i++)
             if (checked[i].status == SPINSIM_OK && reqs[i].spin_x2 == spin) {
                 g.idx.push_back(i);
+                g.small = g.small && checked[i].small;
                 g.samples += checked[i].K;
                 g.chunks += n_chunks_of(checked[i].K);
                 g.groups += n_groups_of(checked[i].K);
@@ -320,9 +323,8 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
         for (int64_t q = 0; q < m; q++) {
             const int64_t i = g.idx[q];
             const spinsim_request& r = reqs[i];
-            const spinsim_field& f = r.field;
             DevSim d;
-            std::memset(&d, 0, sizeof(d));
+            fill_devsim(h->cfg, r, checked[i].K, checked[i].L, d);
             d.states = res[i].states;
             d.spin = res[i].spin;
             d.ops = res[i].ops;
@@ -332,8 +334,6 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
                     if (s.host_spin) d.spin = reinterpret_cast<double*>(base + s.spin_off);
                     if (s.host_ops) d.ops = reinterpret_cast<double*>(base + s.ops_off);
                 }
-            d.K = checked[i].K;
-            d.L = checked[i].L;
             d.sample_offset = so;
             d.chunk_offset = co;
             d.group_offset = go;
@@ -343,101 +343,8 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
             so += d.K;
             co += n_chunks_of(d.K);
             go += n_groups_of(d.K);
-            d.t_start = r.t_start;
-            d.dt_out = r.dt_out;
-            d.dt = r.dt_out / (double)d.L;
-            d.drive_hz = f.drive_hz;
-            d.drive_phase = f.drive_phase;
-            const double two_pi = 2.0 * kPi;
-            const double ax = two_pi * f.drive_x_hz, ay = two_pi * f.drive_y_hz;
-            const double om_plus = 0.5 * (ax + ay), om_minus = 0.5 * (ax - ay);
-            // node offsets and weights of the method.  CF4 (Eqs. cf4_sample_1/2):
-            // t_{1,2} = t + (1 -+ 1/sqrt3) dt/2, a = (3 + 2 sqrt3)/12, b = (3 - 2 sqrt3)/12.
-            // Midpoint and Heun sampling (Sec. 1.3.1): one exponential.
-            double c1, c2, wa, wb;
-            int n_exp;
-            if (h->cfg.method == SPINSIM_METHOD_CF4) {
-                c1 = 0.2113248654051871177454256; c2 = 0.7886751345948128822545744;
-                wa = 0.5386751345948128822545744; wb = -0.03867513459481288225457439; n_exp = 2;
-            } else if (h->cfg.method == SPINSIM_METHOD_MIDPOINT) {
-                c1 = 0.5; c2 = 0.5; wa = 1.0; wb = 0.0; n_exp = 1;
-            } else {
-                c1 = 0.0; c2 = 1.0; wa = 0.5; wb = 0.5; n_exp = 1;
-            }
-            d.c1 = c1;
-            d.c2 = c2;
-            d.P[0] = om_plus * wa * d.dt;
-            d.P[1] = om_plus * wb * d.dt;
-            d.P[2] = om_minus * wa * d.dt;
-            d.P[3] = om_minus * wb * d.dt;
-            d.counter_on = om_minus != 0.0 ? 1 : 0;
-            d.za = wa * d.dt;
-            d.zb = wb * d.dt;
-            d.frame = h->cfg.rotating_frame ? 1 : 0;
-            d.zbias = d.frame ? 0.0 : two_pi * f.bias_hz * (wa + wb) * d.dt;
-            if (d.frame) {
-                d.w_co0 = two_pi * (f.drive_hz - f.bias_hz);
-                d.w_counter0 = two_pi * (f.drive_hz + f.bias_hz);
-                const double th = two_pi * f.bias_hz * r.dt_out;
-                d.exit_re = std::cos(th);
-                d.exit_im = -std::sin(th);
-                d.exit_half_re = std::cos(0.5 * th);
-                d.exit_half_im = -std::sin(0.5 * th);
-            } else {
-                d.w_co0 = d.w_counter0 = two_pi * f.drive_hz;
-                d.exit_re = d.exit_half_re = 1.0;
-                d.exit_im = d.exit_half_im = 0.0;
-            }
-            // quadrupole coefficient of one exponential, over 3 and 2^tau, as the
-            // bulk type holds it (its rounding only reaches second order: the
-            // first-order part of every U_k is replaced by the exact gq)
-            double pulse_w = 0.0;
-            for (int p = 0; p < f.n_pulses; p++) pulse_w += two_pi * std::fabs(f.pulse_amp_hz[p]);
-            d.tau = choose_tau(h->cfg.trotter_squares, h->cfg.precision, h->cfg.rotating_frame, n_exp, wa, wb, d.dt,
-                               std::fabs(om_plus) + std::fabs(om_minus), two_pi * std::fabs(f.bias_hz), pulse_w,
-                               r.spin_x2 == 2 ? two_pi * std::fabs(f.quad_hz) : 0.0,
-                               (double)(d.K > 0 ? d.K - 1 : 0) * (double)d.L);
-            if (r.spin_x2 == 1) d.tau = 0;   // closed form: no squarings
             res[i].trotter_squares = d.tau;
             h->last.trotter_squares = std::max(h->last.trotter_squares, d.tau);
-            const double vq = r.spin_x2 == 2 ? (wa + wb) * two_pi * f.quad_hz * d.dt : 0.0;
-            double qd3 = vq / 3.0 / std::ldexp(1.0, d.tau);
-            if (h->cfg.precision == SPINSIM_PREC_FP32_BULK) qd3 = (double)(float)qd3;
-            d.qd3 = qd3;
-            d.om_plus = om_plus;
-            d.om_minus = om_minus;
-            d.W1 = n_exp == 2 ? wa + wb : wa;
-            d.W2 = n_exp == 2 ? wa + wb : wb;
-            d.gq = r.spin_x2 == 2 ? two_pi * f.quad_hz * r.dt_out : 0.0;
-            d.normalize_out = h->cfg.precision == SPINSIM_PREC_FP32_BULK ? 1 : 0;
-            // Taylor tables of the node-phasor sums (direct FP64 summation)
-            d.tay_ok = d.L <= 65536 ? 1 : 0;
-            if (d.tay_ok) {
-                const double th_co = d.w_co0 * d.dt, th_ct = d.w_counter0 * d.dt;
-                double co[8] = {0}, ct[8] = {0};
-                const double Wn[2] = {d.W1, d.W2}, cn[2] = {d.c1, d.c2};
-                for (int64_t l = 0; l < d.L; l++)
-                    for (int nn = 0; nn < 2; nn++) {
-                        if (Wn[nn] == 0.0) continue;
-                        const double x = (double)l + cn[nn];
-                        double pw = Wn[nn];
-                        const double sa = std::sin(th_co * x), ca = std::cos(th_co * x);
-                        const double sb = std::sin(th_ct * x), cb = std::cos(th_ct * x);
-                        for (int m = 0; m < 4; m++) {
-                            co[2 * m] += pw * ca; co[2 * m + 1] += pw * sa;
-                            ct[2 * m] += pw * cb; ct[2 * m + 1] += pw * sb;
-                            pw *= x;
-                        }
-                    }
-                for (int m = 0; m < 8; m++) { d.tay_co[m] = co[m]; d.tay_ct[m] = ct[m]; }
-            }
-            d.n_pulses = f.n_pulses;
-            for (int p = 0; p < f.n_pulses; p++) {
-                d.amp[p] = two_pi * f.pulse_amp_hz[p];
-                d.centre[p] = f.pulse_centre_s[p];
-                d.inv_w[p] = 1.0 / f.pulse_width_s[p];
-            }
-            for (int e = 0; e < 6; e++) d.psi0[e] = r.psi0[e];
             d.spin_x2 = r.spin_x2;
             sims[q] = d;
         }
@@ -449,9 +356,9 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
 
 // Resident blocks per SM of an integrate shape; computed outside stream
 // capture (it sets the kernel's shared-memory limit) and cached.
-int occupancy(spinsim_s* h, int spin, int lanes, int block, bool capturing, int* per_sm)
+int occupancy(spinsim_s* h, int spin, int lanes, int block, bool small, bool capturing, int* per_sm)
 {
-    auto key = std::make_tuple(spin, lanes, block);
+    auto key = std::make_tuple(spin, lanes, block, (int)small);
     auto it = h->occ.find(key);
     if (it != h->occ.end()) {
         *per_sm = it->second;
@@ -459,7 +366,7 @@ int occupancy(spinsim_s* h, int spin, int lanes, int block, bool capturing, int*
     }
     if (capturing) return SPINSIM_E_UNSUPPORTED;
     int b = 0;
-    if (integrate_occupancy(spin, h->cfg.precision, h->cfg.method, lanes, block, &b) != cudaSuccess) {
+    if (integrate_occupancy(spin, h->cfg.precision, h->cfg.method, lanes, block, small, &b) != cudaSuccess) {
         cudaGetLastError();
         return SPINSIM_E_CUDA;
     }
@@ -477,15 +384,15 @@ int size_bucket(int64_t samples)
 
 // Choose (lanes per sample, threads per block) for the integrate kernel.
 // Results never depend on this choice; only the time does.
-int choose_shape(spinsim_s* h, int spin, IntegrateArgs a, cudaStream_t stream, bool capturing, int& lanes, int& block,
-                 int& grid)
+int choose_shape(spinsim_s* h, int spin, bool small, IntegrateArgs a, cudaStream_t stream, bool capturing, int& lanes,
+                 int& block, int& grid)
 {
     const int precision = h->cfg.precision;
     const int method = h->cfg.method;
     lanes = h->cfg.lanes_per_sample;
     block = h->cfg.threads_per_block;
     if (lanes == 0 || block == 0) {
-        TuneKey key{spin, precision, method, h->tau, size_bucket(a.total_samples)};
+        TuneKey key{spin, precision, method, h->tau, size_bucket(a.total_samples), (int)small};
         bool found = false;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -511,7 +418,7 @@ int choose_shape(spinsim_s* h, int spin, IntegrateArgs a, cudaStream_t stream, b
                         const int B = block ? block : block_opts[bi];
                         if (block && bi > 0) break;
                         int per_sm = 0;
-                        if (occupancy(h, spin, L, B, false, &per_sm) != SPINSIM_OK || per_sm < 1) continue;
+                        if (occupancy(h, spin, L, B, small, false, &per_sm) != SPINSIM_OK || per_sm < 1) continue;
                         // trial on a prefix of the batch: at most 4 full waves of this shape
                         IntegrateArgs t = a;
                         const int64_t wave = (int64_t)h->n_sm * per_sm * (B / L);
@@ -523,7 +430,7 @@ int choose_shape(spinsim_s* h, int spin, IntegrateArgs a, cudaStream_t stream, b
                         for (int rep = 0; rep < 2; rep++) {
                             cudaMemsetAsync(a.tile_counter, 0, sizeof(unsigned long long), stream);
                             cudaEventRecord(e0, stream);
-                            launch_integrate(spin, precision, method, L, B, g, t, stream);
+                            launch_integrate(spin, precision, method, L, B, g, small, t, stream);
                             cudaEventRecord(e1, stream);
                             if (cudaEventSynchronize(e1) != cudaSuccess) {
                                 cudaEventDestroy(e0);
@@ -552,7 +459,7 @@ int choose_shape(spinsim_s* h, int spin, IntegrateArgs a, cudaStream_t stream, b
         }
     }
     int per_sm = 0;
-    int st = occupancy(h, spin, lanes, block, capturing, &per_sm);
+    int st = occupancy(h, spin, lanes, block, small, capturing, &per_sm);
     if (st != SPINSIM_OK) return st;
     per_sm = std::max(per_sm, 1);
     const int spb = block / lanes;
@@ -623,14 +530,14 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
         ia.tile_counter = reinterpret_cast<unsigned long long*>(base + g.counter_off);
         int lanes = 0, block = 0, grid = 0;
         if (g.samples > 0) {
-            st = choose_shape(h, g.spin_x2, ia, stream, capturing, lanes, block, grid);
+            st = choose_shape(h, g.spin_x2, g.small, ia, stream, capturing, lanes, block, grid);
             if (st != SPINSIM_OK) return st;
             const int spb = block / lanes;
             ia.n_tiles = (g.samples + spb - 1) / spb;
             if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
                 return SPINSIM_E_CUDA;
             if (pg >= 0) cudaEventRecord(h->prof[pg][0], stream);
-            if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, lanes, block, grid, ia, stream) !=
+            if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, lanes, block, grid, g.small, ia, stream) !=
                 cudaSuccess)
                 return SPINSIM_E_CUDA;
             if (pg >= 0) cudaEventRecord(h->prof[pg][1], stream);
@@ -680,7 +587,8 @@ std::vector<uint64_t> batch_signature(const spinsim_request* reqs, const spinsim
     s.reserve((size_t)n * 6 + 1);
     s.push_back((uint64_t)n);
     for (int64_t i = 0; i < n; i++) {
-        s.push_back((uint64_t)reqs[i].spin_x2 | ((uint64_t)(checked[i].status & 0xff) << 8));
+        s.push_back((uint64_t)reqs[i].spin_x2 | ((uint64_t)(checked[i].status & 0xff) << 8) |
+                    ((uint64_t)checked[i].small << 16));
         s.push_back((uint64_t)checked[i].K);
         s.push_back((uint64_t)checked[i].L);
         s.push_back((uint64_t)(uintptr_t)res[i].states);
@@ -843,8 +751,10 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
             else if (res[i].capacity < checked[i].K) checked[i].status = SPINSIM_E_CAPACITY;
         }
         res[i].status = checked[i].status;
-        if (checked[i].status == SPINSIM_OK)
+        if (checked[i].status == SPINSIM_OK) {
             checked[i].flags |= precision_flags(h->cfg.precision, h->cfg.rotating_frame, reqs[i]);
+            checked[i].small = small_angle_request(h->cfg, reqs[i], checked[i].L);
+        }
         res[i].flags = checked[i].flags;
         res[i].trotter_squares = 0;
         res[i].n_samples = checked[i].status == SPINSIM_OK ? checked[i].K : 0;
@@ -1000,6 +910,7 @@ static int serving_pump(spinsim_s* h)
             res.push_back(*tk.res);
             ids.push_back(t);
             Checked c = check_request(&tk.req);
+            if (c.status == SPINSIM_OK) c.small = small_angle_request(h->cfg, tk.req, c.L);
             checked.push_back(c);
             bytes += tk.bytes;
         }

@@ -35,7 +35,6 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices] = {};   // device address of g_static_scratch, per device
 
-constexpr double kPiS = 3.14159265358979323846264338327950288;
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -49,104 +48,6 @@ bool device_resident(const void* p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// The per-simulation parameter table, as the kernels expect it.
-void fill_one(const spinsim_config& cfg, int tau, const spinsim_request& r, int64_t K, int64_t L, double* states,
-              double* spin, double* ops, DevSim& d)
-{
-    std::memset(&d, 0, sizeof(d));
-    const spinsim_field& f = r.field;
-    const double two_pi = 2.0 * kPiS;
-    d.states = states;
-    d.spin = spin;
-    d.ops = ops;
-    d.K = K;
-    d.L = L;
-    d.t_start = r.t_start;
-    d.dt_out = r.dt_out;
-    d.dt = r.dt_out / (double)L;
-    d.drive_hz = f.drive_hz;
-    d.drive_phase = f.drive_phase;
-    const double ax = two_pi * f.drive_x_hz, ay = two_pi * f.drive_y_hz;
-    const double om_plus = 0.5 * (ax + ay), om_minus = 0.5 * (ax - ay);
-    double c1, c2, wa, wb;
-    int n_exp;
-    if (cfg.method == SPINSIM_METHOD_CF4) {
-        c1 = 0.2113248654051871177454256; c2 = 0.7886751345948128822545744;
-        wa = 0.5386751345948128822545744; wb = -0.03867513459481288225457439; n_exp = 2;
-    } else if (cfg.method == SPINSIM_METHOD_MIDPOINT) {
-        c1 = 0.5; c2 = 0.5; wa = 1.0; wb = 0.0; n_exp = 1;
-    } else {
-        c1 = 0.0; c2 = 1.0; wa = 0.5; wb = 0.5; n_exp = 1;
-    }
-    d.c1 = c1;
-    d.c2 = c2;
-    d.P[0] = om_plus * wa * d.dt;
-    d.P[1] = om_plus * wb * d.dt;
-    d.P[2] = om_minus * wa * d.dt;
-    d.P[3] = om_minus * wb * d.dt;
-    d.counter_on = om_minus != 0.0 ? 1 : 0;
-    d.za = wa * d.dt;
-    d.zb = wb * d.dt;
-    d.frame = cfg.rotating_frame ? 1 : 0;
-    d.zbias = d.frame ? 0.0 : two_pi * f.bias_hz * (wa + wb) * d.dt;
-    if (d.frame) {
-        d.w_co0 = two_pi * (f.drive_hz - f.bias_hz);
-        d.w_counter0 = two_pi * (f.drive_hz + f.bias_hz);
-        const double th = two_pi * f.bias_hz * r.dt_out;
-        d.exit_re = std::cos(th);
-        d.exit_im = -std::sin(th);
-        d.exit_half_re = std::cos(0.5 * th);
-        d.exit_half_im = -std::sin(0.5 * th);
-    } else {
-        d.w_co0 = d.w_counter0 = two_pi * f.drive_hz;
-        d.exit_re = d.exit_half_re = 1.0;
-        d.exit_im = d.exit_half_im = 0.0;
-    }
-    double pulse_w = 0.0;
-    for (int p = 0; p < f.n_pulses; p++) pulse_w += two_pi * std::fabs(f.pulse_amp_hz[p]);
-    d.tau = choose_tau(tau, cfg.precision, cfg.rotating_frame, n_exp, wa, wb, d.dt,
-                       std::fabs(om_plus) + std::fabs(om_minus), two_pi * std::fabs(f.bias_hz), pulse_w,
-                       r.spin_x2 == 2 ? two_pi * std::fabs(f.quad_hz) : 0.0, (double)(K > 0 ? K - 1 : 0) * (double)L);
-    if (r.spin_x2 == 1) d.tau = 0;
-    const double vq = r.spin_x2 == 2 ? (wa + wb) * two_pi * f.quad_hz * d.dt : 0.0;
-    double qd3 = vq / 3.0 / std::ldexp(1.0, d.tau);
-    if (cfg.precision == SPINSIM_PREC_FP32_BULK) qd3 = (double)(float)qd3;
-    d.qd3 = qd3;
-    d.om_plus = om_plus;
-    d.om_minus = om_minus;
-    d.W1 = n_exp == 2 ? wa + wb : wa;
-    d.W2 = n_exp == 2 ? wa + wb : wb;
-    d.gq = r.spin_x2 == 2 ? two_pi * f.quad_hz * r.dt_out : 0.0;
-    d.normalize_out = cfg.precision == SPINSIM_PREC_FP32_BULK ? 1 : 0;
-    d.tay_ok = L <= 65536 ? 1 : 0;
-    if (d.tay_ok) {
-        const double th_co = d.w_co0 * d.dt, th_ct = d.w_counter0 * d.dt;
-        double co[8] = {0}, ct[8] = {0};
-        const double Wn[2] = {d.W1, d.W2}, cn[2] = {d.c1, d.c2};
-        for (int64_t l = 0; l < L; l++)
-            for (int nn = 0; nn < 2; nn++) {
-                if (Wn[nn] == 0.0) continue;
-                const double x = (double)l + cn[nn];
-                double pw = Wn[nn];
-                const double sa = std::sin(th_co * x), ca = std::cos(th_co * x);
-                const double sb = std::sin(th_ct * x), cb = std::cos(th_ct * x);
-                for (int m = 0; m < 4; m++) {
-                    co[2 * m] += pw * ca; co[2 * m + 1] += pw * sa;
-                    ct[2 * m] += pw * cb; ct[2 * m + 1] += pw * sb;
-                    pw *= x;
-                }
-            }
-        for (int m = 0; m < 8; m++) { d.tay_co[m] = co[m]; d.tay_ct[m] = ct[m]; }
-    }
-    d.n_pulses = f.n_pulses;
-    for (int p = 0; p < f.n_pulses; p++) {
-        d.amp[p] = two_pi * f.pulse_amp_hz[p];
-        d.centre[p] = f.pulse_centre_s[p];
-        d.inv_w[p] = 1.0 / f.pulse_width_s[p];
-    }
-    for (int e = 0; e < 6; e++) d.psi0[e] = r.psi0[e];
-    d.spin_x2 = r.spin_x2;
-}
 
 }  // namespace
 
@@ -214,7 +115,11 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
 
     const int tau = cfg->trotter_squares;   // -1: chosen per request, as in spinsim_simulate
     DevSim d;
-    fill_one(*cfg, tau, *req, K, L, res->states, res->spin, res->ops, d);
+    fill_devsim(*cfg, *req, K, L, d);
+    d.states = res->states;
+    d.spin = res->spin;
+    d.ops = res->ops;
+    const bool small = small_angle_request(*cfg, *req, L);
     res->trotter_squares = d.tau;
     int64_t offsets[6] = {0, K, 0, chunks, 0, groups};
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
@@ -232,7 +137,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         const int lanes = cfg->lanes_per_sample ? cfg->lanes_per_sample : 2;
         const int block = cfg->threads_per_block ? cfg->threads_per_block : 128;
         int per_sm = 0;
-        if (integrate_occupancy(spin, cfg->precision, cfg->method, lanes, block, &per_sm) != cudaSuccess) {
+        if (integrate_occupancy(spin, cfg->precision, cfg->method, lanes, block, small, &per_sm) != cudaSuccess) {
             cudaGetLastError();
             return res->status = SPINSIM_E_CUDA;
         }
@@ -250,7 +155,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         // the tile counter keeps the previous call's value: clear it
         if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
             return res->status = SPINSIM_E_CUDA;
-        if (launch_integrate(spin, cfg->precision, cfg->method, lanes, block, grid, ia, stream) != cudaSuccess)
+        if (launch_integrate(spin, cfg->precision, cfg->method, lanes, block, grid, small, ia, stream) != cudaSuccess)
             return res->status = SPINSIM_E_CUDA;
         ChainArgs ca;
         ca.sims = ia.sims;

@@ -3,6 +3,8 @@
 #include <cstdint>
 #include "../paper_2204_05586_gb300/csrc/device_math.cuh"
 
+// small_angle_request lives in csrc/params.cu, linked into this harness.
+
 using namespace spinsim;
 
 template <typename R>
@@ -32,6 +34,36 @@ void hh_expm_one(double vx, double vy, double vz, double vq, int tau, int fp32, 
         full3(e, out);
     }
 }
+// the FP32 small-angle variant (the kernels use it when the host has bounded
+// every step angle by kTinyAngleBound)
+void hh_expm_one_small(double vx, double vy, double vz, double vq, int tau, double* out)
+{
+    const float qd3 = (float)(vq / 3.0 / std::ldexp(1.0, tau));
+    Res3<float> e;
+    expm_one_res<float, true>((float)vx, (float)vy, (float)vz, qd3, tau, e);
+    full3(e, out);
+}
+// the same FP32 exponential through the general series, for comparison
+void hh_expm_one_general32(double vx, double vy, double vz, double vq, int tau, double* out)
+{
+    const float qd3 = (float)(vq / 3.0 / std::ldexp(1.0, tau));
+    Res3<float> e;
+    expm_one_res<float, false>((float)vx, (float)vy, (float)vz, qd3, tau, e);
+    full3(e, out);
+}
+// small-angle series in float: sin, cos, sin - x, cos - 1
+void hh_tiny_sincos(double x, double* out)
+{
+    float s, c, sm, cm;
+    small_sincos_tiny<float>((float)x, s, c);
+    small_sincos_m_tiny<float>((float)x, sm, cm);
+    out[0] = s; out[1] = c; out[2] = sm; out[3] = cm;
+}
+int hh_small_angle_request(const spinsim_config* cfg, const spinsim_request* r, int64_t L)
+{
+    return small_angle_request(*cfg, *r, L) ? 1 : 0;
+}
+double hh_tiny_angle_bound() { return kTinyAngleBound; }
 // rest part only (U - I - F(v)) in double
 void hh_expm_one_rest(double vx, double vy, double vz, double vq, int tau, double* out)
 {

@@ -25,7 +25,8 @@ def hh(tmp_path_factory):
         pytest.skip("nvcc not available")
     out = str(tmp_path_factory.mktemp("hh") / "libhh.so")
     subprocess.check_call([nvcc, "-O2", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-shared",
-                           "-I", os.path.join(ROOT, "include"), os.path.join(HERE, "host_harness.cu"), "-o", out])
+                           "-I", os.path.join(ROOT, "include"), os.path.join(HERE, "host_harness.cu"),
+                           os.path.join(ROOT, "paper_2204_05586_gb300", "csrc", "params.cu"), "-o", out])
     L = ctypes.CDLL(out)
     L.hh_expm_one.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, ctypes.c_int, DP]
     L.hh_expm_one_rest.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, DP]
@@ -36,6 +37,12 @@ def hh(tmp_path_factory):
     L.hh_small_sincos_m.argtypes = [ctypes.c_double, ctypes.c_int, DP]
     L.hh_choose_tau.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double] * 8
     L.hh_choose_tau.restype = ctypes.c_int
+    L.hh_expm_one_small.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, DP]
+    L.hh_expm_one_general32.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, DP]
+    L.hh_tiny_sincos.argtypes = [ctypes.c_double, DP]
+    L.hh_small_angle_request.restype = ctypes.c_int
+    L.hh_small_angle_request.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+    L.hh_tiny_angle_bound.restype = ctypes.c_double
     return L
 
 
@@ -203,3 +210,66 @@ def test_choose_tau_rule(hh):
     assert got[4] < got[3] and got[5] > got[3]  # shorter runs need fewer squarings
     assert hh.hh_choose_tau(-1, 0, 1, 2, CF4_A, CF4_B, 1e-8, 1e4, 1e6, 0, 0, 1e7) == 24   # FP64 default
     assert hh.hh_choose_tau(5, 1, 1, 2, CF4_A, CF4_B, 1e-8, 1e4, 1e6, 0, 0, 1e7) == 5     # explicit tau
+
+
+# ------------------------------------------------ small-angle FP32 variant
+def test_tiny_series_within_bound(hh):
+    """The two-term series the FP32 kernels use below kTinyAngleBound = 2^-6:
+    sin, cos to FP32 rounding and sin x - x, cos x - 1 to full FP32 relative
+    precision against 50-digit mpmath."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    b = hh.hh_tiny_angle_bound()
+    assert b == 2.0 ** -6
+    for x in np.concatenate([np.linspace(-b, b, 41), [1e-7, -3e-5, 2e-3]]):
+        x = float(np.float32(x))
+        out = np.zeros(4)
+        hh.hh_tiny_sincos(x, P(out))
+        X = mp.mpf(x)
+        assert abs(out[0] - float(mp.sin(X))) <= 1.2e-7 * max(abs(x), 1e-30)
+        assert abs(out[1] - float(mp.cos(X))) <= 1.2e-7
+        if x != 0.0:
+            assert abs(out[2] - float(mp.sin(X) - X)) <= 3e-7 * abs(float(mp.sin(X) - X))
+            assert abs(out[3] - float(mp.cos(X) - 1)) <= 3e-7 * abs(float(mp.cos(X) - 1))
+
+
+def test_small_angle_exponential_matches_general(hh):
+    """Inside the bound the small-angle exponential equals the general FP32
+    one to FP32 rounding and the exact exponential (scipy) to the FP32
+    accuracy of the split residual."""
+    rng = np.random.default_rng(7)
+    for scale in (1e-6, 1e-4, 5e-3):
+        for _ in range(20):
+            v = rng.normal(size=4) * scale
+            for tau in (0, 1, 4):
+                a, g = np.zeros(18), np.zeros(18)
+                hh.hh_expm_one_small(*v, tau, P(a))
+                hh.hh_expm_one_general32(*v, tau, P(g))
+                A = a.view(np.complex128).reshape(3, 3)
+                G = g.view(np.complex128).reshape(3, 3)
+                assert np.abs(A - G).max() <= 2e-7 * max(scale * scale, 1e-12) + 1e-13
+                if tau == 4:
+                    assert np.abs(A - sl.expm(-1j * H1(v))).max() < 1e-8
+
+
+def test_small_angle_rule_on_workloads(hh):
+    """The host picks the small-angle kernel for the rotating-frame FP32 runs
+    of every workload shape and refuses it for FP64, for the lab frame and for
+    a request whose step angles exceed the bound."""
+    from paper_2204_05586_gb300 import spinsim as S, workloads as W
+    def rule(req, **cfg):
+        c = S.make_config(**cfg)
+        r = S.make_request(req)
+        L = int(round(req["dt_out"] / req["dt"]))
+        return hh.hh_small_angle_request(ctypes.addressof(c), ctypes.addressof(r), L)
+    sweep = W.sweep(64, seed=W.SEED)
+    _, served = W.serving_stream(64, seed=W.SEED + 1)
+    for req in [W.spin_one_sensing(), W.spin_half_rabi()] + sweep + served:
+        assert rule(req) == 1
+        assert rule(req, precision=S.PREC_FP64) == 0
+    assert rule(W.spin_one_sensing(), rotating_frame=False) == 0
+    big = W.spin_one_sensing(dt=1e-7)           # 10x larger steps: still inside the bound
+    assert rule(big) == 1
+    far = W.spin_one_sensing()
+    far["field"]["drive_hz"] = far["field"]["bias_hz"] + 3e3   # 3 kHz detuning: (w_d - w_r) dt_out > 2^-6
+    assert rule(far) == 0
