@@ -96,7 +96,9 @@ typedef struct {
                                      the free memory at spinsim_create                     */
     int32_t profile;              /* 1: time the integrate and chain kernels of each call
                                      with CUDA events (read by spinsim_last_launch)         */
-    int32_t reserved;
+    int32_t blocks_per_sm;        /* 0 = autotune; else resident integrate blocks per SM
+                                     (1..32, capped at what the kernel's registers allow).
+                                     Results do not depend on it.                          */
 } spinsim_config;
 
 /* The fixed parameterised field family (Hz, seconds, radians):
@@ -220,12 +222,13 @@ int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info);
  * which the CUDA runtime places on a GPU when the library's device code is
  * loaded there (at the latest at the first call on that device) and which
  * stays until the process exits.  That bounds
- * the request: up to about 102,000 output samples for spin-one and 460,000
+ * the request: up to about 99,000 output samples for spin-one and 460,000
  * for spin-half; a larger K returns SPINSIM_E_NOMEM without launching.
  * res->states (and res->spin, res->ops when not NULL) must be 16-byte
  * aligned device memory, else SPINSIM_E_ARG.  cfg selects method, precision,
- * frame, tau and the launch shape (0 = lanes 2, 128 threads; no autotuning);
- * use_graphs, mem_budget and profile are ignored; res->flags is not set.
+ * frame, tau and the launch shape (0 = lanes 2, 128 threads, as many resident
+ * blocks per SM as fit; no autotuning); use_graphs, mem_budget and profile are
+ * ignored; res->flags receives the request's warning bits.
  * The first call on a device looks up the device address of the array; make
  * it before any stream capture.  Every call uses the same array and leaves
  * its contents behind, so calls that overlap on the GPU (on different

@@ -1,26 +1,30 @@
 // chain.cu -- ordered prefix product of the sample operators and the output
-// write (Sec. 1.2.4, Eq. integration_compilation: psi_k = U_k psi_{k-1}).
+// write (Sec. 1.2.4, Eq. integration_compilation: psi_k = U_k psi_{k-1},
+// psi_0 = psi_init since U_0 = I).
 //
-// The paper chains the U_k sequentially on the CPU.  Here the chain is a
-// parallel scan in FP64 on the device, over chunks of kChunk = 256 samples
-// and groups of kGroup = 32 chunks, neither of which straddles two
-// simulations:
-//   reduce:     one warp per chunk; lane l multiplies its run of kRun = 8
-//               operators in order, then the warp forms inclusive prefixes
-//               P_l = B_l ... B_0 of the run products by a shuffle scan
-//               (Hillis-Steele, 5 levels) and stores each lane's exclusive
-//               prefix and the chunk product;
-//   group scan: one warp per group scans its 32 chunk products the same way
-//               and stores each chunk's exclusive prefix and the group product;
-//   carry:      one warp per simulation walks its group products in order
-//               (one matrix row per lane) and stores the state entering every
-//               group;
-//   apply:      one warp per chunk forms the state entering the chunk and
-//               each lane's run from the prefixes, then walks its 8 samples,
-//               writing psi_k, <J>_k and (optionally) U_k.
-// On GB300 a 32-lane FP64 instruction keeps an SM sub-partition busy for
-// tens of cycles, so the FP64 work is spread over many warps and the
-// sequential part (the carry) is kept short and row-parallel.
+// The paper chains the U_k sequentially on the CPU.  Here the chain is a tree
+// scan in FP64 on the device, per simulation (no node spans two simulations):
+//   level 0:  a node is one warp over kFan runs of `run` consecutive samples;
+//             lane l multiplies its run in order (all lanes busy);
+//   level l:  a node covers kFan consecutive nodes of level l - 1;
+//   up:       each node forms the products of its binary tree over its 32
+//             children (31 products in 5 rounds), keeping the left-child
+//             product of every internal node and the node's total;
+//   down:     from the state entering a node, the states entering its 32
+//             children follow by walking the binary tree down: the left child
+//             receives the state, the right child the left child's product
+//             applied to it (31 matrix-vector products in 5 rounds);
+//   apply:    each lane walks its run from its entering state, writing psi_k,
+//             <J>_k and (optionally) U_k.
+// The top node of a simulation starts the down-sweep from psi_init inside the
+// up kernel of its level.
+//
+// GB300 executes FP64 at 1/64 of the FP32 rate: one FP64 warp instruction
+// keeps an SM sub-partition busy for tens of cycles whether one lane or 32
+// are active.  So every product of the binary trees is spread over the lanes
+// entry by entry (a round of a tree level computes up to 32 entries at once),
+// instead of one lane per product with most lanes idle, and the number of
+// level-0 nodes of a long simulation is matched to the SM sub-partitions.
 // Spin-one operators are general 3x3 complex matrices; spin-half operators
 // are kept in SU(2) form (alpha, beta) = first column.
 #include <algorithm>
@@ -29,12 +33,13 @@
 
 namespace spinsim {
 
-__device__ __forceinline__ int find_chunk_sim(const int64_t* off, int n, int64_t c)
+__device__ __forceinline__ int find_node_sim(const int64_t* off, int n, int64_t j)
 {
+    // largest i in [0, n) with off[i] <= j (off is non-decreasing, off[0] = 0)
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= c) lo = mid;
+        if (off[mid] <= j) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -68,26 +73,6 @@ struct Op<3> {
         double2* q = reinterpret_cast<double2*>(p);
 #pragma unroll
         for (int e = 0; e < 9; e++) q[e] = make_double2(m[e / 3][e % 3].r, m[e / 3][e % 3].i);
-    }
-    __device__ __forceinline__ void shfl_up(unsigned d)
-    {
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                m[i][j].r = __shfl_up_sync(0xffffffffu, m[i][j].r, d);
-                m[i][j].i = __shfl_up_sync(0xffffffffu, m[i][j].i, d);
-            }
-    }
-    __device__ __forceinline__ void shfl_idx(int src)
-    {
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                m[i][j].r = __shfl_sync(0xffffffffu, m[i][j].r, src);
-                m[i][j].i = __shfl_sync(0xffffffffu, m[i][j].i, src);
-            }
     }
     // C = A B
     static __device__ __forceinline__ void mul(const Op& A, const Op& B, Op& C)
@@ -133,20 +118,6 @@ struct Op<2> {
         q[0] = make_double2(a.r, a.i);
         q[1] = make_double2(b.r, b.i);
     }
-    __device__ __forceinline__ void shfl_up(unsigned d)
-    {
-        a.r = __shfl_up_sync(0xffffffffu, a.r, d);
-        a.i = __shfl_up_sync(0xffffffffu, a.i, d);
-        b.r = __shfl_up_sync(0xffffffffu, b.r, d);
-        b.i = __shfl_up_sync(0xffffffffu, b.i, d);
-    }
-    __device__ __forceinline__ void shfl_idx(int src)
-    {
-        a.r = __shfl_sync(0xffffffffu, a.r, src);
-        a.i = __shfl_sync(0xffffffffu, a.i, src);
-        b.r = __shfl_sync(0xffffffffu, b.r, src);
-        b.i = __shfl_sync(0xffffffffu, b.i, src);
-    }
     // alpha = a1 a2 - conj(b1) b2, beta = b1 a2 + conj(a1) b2
     static __device__ __forceinline__ void mul(const Op& A, const Op& B, Op& C)
     {
@@ -191,155 +162,256 @@ __device__ __forceinline__ void spin_projection(const cx<double>* p, int N, doub
     }
 }
 
-// ------------------------------------------------------------------ kernels
-template <int N>
-__global__ void __launch_bounds__(128) chain_reduce_kernel(ChainArgs a)
+// ------------------------------------------------- binary trees of a warp
+// A warp's binary tree over 32 leaves lives in 63 shared-memory slots:
+// height h (0 = leaves) starts at slot 64 - (64 >> h), node p of height h
+// sits at slot tslot(h, p).  Internal node (h, p), h >= 1, multiplies its
+// children: slot(h, p) = slot(h-1, 2p+1) * slot(h-1, 2p) (later on the left).
+__device__ __forceinline__ int tslot(int h, int p) { return (64 - (64 >> h)) + p; }
+
+// Left child of the internal node with slot 32 + t, t in [0, 31): the
+// products a down-sweep needs, stored in this order per node.
+__device__ __forceinline__ int left_child_slot(int t)
 {
-    constexpr int OPD = N == 3 ? 18 : 4;
-    const int lane = threadIdx.x & 31;
+    const int q = 32 + t;
+    int h = 1;
+    while (h < 5 && q >= tslot(h + 1, 0)) h++;
+    return tslot(h - 1, 2 * (q - tslot(h, 0)));
+}
+
+// Entry arithmetic on operators held as doubles in shared memory.
+template <int N>
+struct Tree;
+
+template <>
+struct Tree<3> {
+    static constexpr int D = 18;   // doubles per operator
+    static constexpr int E = 9;    // entries of a product
+    static __device__ __forceinline__ cx<double> at(const double* A, int i, int j)
+    {
+        const double2 v = reinterpret_cast<const double2*>(A)[3 * i + j];
+        return cmk(v.x, v.y);
+    }
+    // entry e = (i, j) of C = A B
+    static __device__ __forceinline__ void prod_entry(const double* A, const double* B, int e, double* C)
+    {
+        const int i = e / 3, j = e - 3 * (e / 3);
+        cx<double> s = cmul(at(A, i, 0), at(B, 0, j));
+        s = cfma(at(A, i, 1), at(B, 1, j), s);
+        s = cfma(at(A, i, 2), at(B, 2, j), s);
+        reinterpret_cast<double2*>(C)[e] = make_double2(s.r, s.i);
+    }
+    // component r of A v (v: 3 complex)
+    static __device__ __forceinline__ cx<double> matvec_row(const double* A, const double* v, int r)
+    {
+        const double2* w = reinterpret_cast<const double2*>(v);
+        cx<double> s = cmul(at(A, r, 0), cmk(w[0].x, w[0].y));
+        s = cfma(at(A, r, 1), cmk(w[1].x, w[1].y), s);
+        s = cfma(at(A, r, 2), cmk(w[2].x, w[2].y), s);
+        return s;
+    }
+};
+
+// SU(2) element [[alpha, -conj(beta)], [beta, conj(alpha)]] stored as (alpha, beta).
+template <>
+struct Tree<2> {
+    static constexpr int D = 4;
+    static constexpr int E = 2;
+    static __device__ __forceinline__ void prod_entry(const double* A, const double* B, int e, double* C)
+    {
+        const double2* a = reinterpret_cast<const double2*>(A);
+        const double2* b = reinterpret_cast<const double2*>(B);
+        const cx<double> a1 = cmk(a[0].x, a[0].y), b1 = cmk(a[1].x, a[1].y);
+        const cx<double> a2 = cmk(b[0].x, b[0].y), b2 = cmk(b[1].x, b[1].y);
+        cx<double> s;
+        if (e == 0) s = csub(cmul(a1, a2), cmul(cconj(b1), b2));   // alpha = a1 a2 - conj(b1) b2
+        else s = cfma_conj(a1, b2, cmul(b1, a2));                  // beta = b1 a2 + conj(a1) b2
+        reinterpret_cast<double2*>(C)[e] = make_double2(s.r, s.i);
+    }
+    static __device__ __forceinline__ cx<double> matvec_row(const double* A, const double* v, int r)
+    {
+        const double2* a = reinterpret_cast<const double2*>(A);
+        const double2* w = reinterpret_cast<const double2*>(v);
+        const cx<double> al = cmk(a[0].x, a[0].y), be = cmk(a[1].x, a[1].y);
+        const cx<double> v0 = cmk(w[0].x, w[0].y), v1 = cmk(w[1].x, w[1].y);
+        // [alpha v0 - conj(beta) v1, beta v0 + conj(alpha) v1]
+        return r == 0 ? csub(cmul(al, v0), cmul(cconj(be), v1)) : cfma_conj(al, v1, cmul(be, v0));
+    }
+};
+
+// Up-sweep of a warp's tree: leaves in slots 0..31, products of every
+// internal node, one entry per lane per round.
+template <int N>
+__device__ __forceinline__ void tree_up(double* S, int lane)
+{
+    constexpr int D = Tree<N>::D, E = Tree<N>::E;
+#pragma unroll 1
+    for (int h = 1; h <= 5; h++) {
+        const int P = 32 >> h;
+        for (int t = lane; t < P * E; t += 32) {
+            const int p = t / E, e = t - E * (t / E);
+            Tree<N>::prod_entry(S + tslot(h - 1, 2 * p + 1) * D, S + tslot(h - 1, 2 * p) * D, e, S + tslot(h, p) * D);
+        }
+        __syncwarp();
+    }
+}
+
+// Down-sweep: the state entering the node is in V slot tslot(5, 0); the
+// states entering the 32 leaves end in slots 0..31.  `left(t)` returns the
+// left-child product of internal node 32 + t.
+template <int N, typename Left>
+__device__ __forceinline__ void tree_down(double* V, Left left, int lane)
+{
+    constexpr int SV = 2 * N;   // doubles per state
+#pragma unroll 1
+    for (int h = 5; h >= 1; h--) {
+        const int P = 32 >> h;
+        for (int t = lane; t < P * N; t += 32) {
+            const int p = t / N, r = t - N * (t / N);
+            const double* v = V + tslot(h, p) * SV;
+            const cx<double> y = Tree<N>::matvec_row(left(tslot(h, p) - 32), v, r);
+            double* vl = V + tslot(h - 1, 2 * p) * SV;
+            double* vr = V + tslot(h - 1, 2 * p + 1) * SV;
+            vl[2 * r] = v[2 * r];
+            vl[2 * r + 1] = v[2 * r + 1];
+            vr[2 * r] = y.r;
+            vr[2 * r + 1] = y.i;
+        }
+        __syncwarp();
+    }
+}
+
+// Shared memory of one warp: the tree (63 operators) and its states (63).
+template <int N>
+constexpr int warp_tree_doubles() { return 63 * Tree<N>::D + 63 * 2 * N; }
+template <int N>
+constexpr int warp_state_doubles() { return 63 * 2 * N; }
+constexpr int kChainWarps = 4;   // warps per block of the chain kernels
+
+// ------------------------------------------------------------------ kernels
+// Up-sweep of level `level`: one warp per node.
+template <int N>
+__global__ void __launch_bounds__(128) chain_up_kernel(ChainArgs a, int level)
+{
+    constexpr int D = Tree<N>::D, SV = 2 * N;
+    extern __shared__ __align__(16) double smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* S = smem + warp * warp_tree_doubles<N>();
+    double* V = S + 63 * D;
+    const int64_t* off = a.level_off + (size_t)level * (a.n_sims + 1);
+    const int64_t* coff = level > 0 ? off - (a.n_sims + 1) : nullptr;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < a.n_chunks; c += warps) {
-        const int si = find_chunk_sim(a.chunk_offsets, a.n_sims, c);
+    for (int64_t node = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; node < a.nodes[level]; node += warps) {
+        const int si = find_node_sim(off, a.n_sims, node);
         const DevSim& s = a.sims[si];
-        const int64_t j = c - a.chunk_offsets[si];
-        const int64_t k0 = j * kChunk + (int64_t)lane * kRun;
-        const int64_t k1 = min(k0 + kRun, s.K);
+        const int64_t local = node - off[si];
         Op<N> B;
         B.identity();
-        const double* U = a.U + (s.sample_offset) * OPD;
-        for (int64_t k = k0; k < k1; k++) {
-            Op<N> u, t;
-            u.load(U + k * OPD);
-            Op<N>::mul(u, B, t);   // later operators multiply from the left
-            B = t;
+        if (level == 0) {
+            // lane run: U_{k1-1} ... U_{k0}
+            const int run = s.chain_run;
+            const int64_t k0 = (local * kFan + lane) * run;
+            const int64_t k1 = min(k0 + run, s.K);
+            const double* U = a.U + s.sample_offset * D;
+            for (int64_t k = k0; k < k1; k++) {
+                Op<N> u, t;
+                u.load(U + k * D);
+                Op<N>::mul(u, B, t);   // later operators multiply from the left
+                B = t;
+            }
+        } else {
+            const int64_t child = local * kFan + lane;
+            if (child < coff[si + 1] - coff[si]) B.load(a.agg[level - 1] + (coff[si] + child) * D);
         }
-        // inclusive prefix P_l = B_l ... B_0 across the warp
-        Op<N> P = B;
+        B.store(S + lane * D);
+        __syncwarp();
+        tree_up<N>(S, lane);
+        if (lane < kLeftPerNode) {
+            const double2* src = reinterpret_cast<const double2*>(S + left_child_slot(lane) * D);
+            double2* dst = reinterpret_cast<double2*>(a.left[level] + (node * kLeftPerNode + lane) * D);
 #pragma unroll
-        for (unsigned d = 1; d < 32; d <<= 1) {
-            Op<N> o = P;
-            o.shfl_up(d);
-            if (lane >= (int)d) {
-                Op<N> t;
-                Op<N>::mul(P, o, t);
-                P = t;
+            for (int i = 0; i < D / 2; i++) dst[i] = src[i];
+        } else {
+            const double2* src = reinterpret_cast<const double2*>(S + tslot(5, 0) * D);
+            double2* dst = reinterpret_cast<double2*>(a.agg[level] + node * D);
+#pragma unroll
+            for (int i = 0; i < D / 2; i++) dst[i] = src[i];
+        }
+        if (level >= 1 && s.chain_top == level) {
+            // top node: the down-sweep starts here from psi_init
+            if (lane < SV) V[tslot(5, 0) * SV + lane] = s.psi0[lane];
+            __syncwarp();
+            tree_down<N>(V, [&](int t) { return (const double*)(S + left_child_slot(t) * D); }, lane);
+            const int64_t child = local * kFan + lane;
+            if (child < coff[si + 1] - coff[si]) {
+                double* dst = a.state[level - 1] + (coff[si] + child) * SV;
+#pragma unroll
+                for (int i = 0; i < SV; i++) dst[i] = V[lane * SV + i];
             }
         }
-        Op<N> M = P;
-        M.shfl_up(1);
-        if (lane == 0) M.identity();
-        M.store(a.run_prefix + (c * 32 + lane) * OPD);
-        if (lane == 31) P.store(a.chunk_agg + c * OPD);
+        __syncwarp();
     }
 }
 
-// Group scan: one warp per group of up to 32 consecutive chunks of one
-// simulation; inclusive prefixes of the chunk products by a shuffle scan.
+// Down-sweep of level `level` >= 1 for nodes below their simulation's top.
 template <int N>
-__global__ void __launch_bounds__(128) chain_group_kernel(ChainArgs a)
+__global__ void __launch_bounds__(128) chain_down_kernel(ChainArgs a, int level)
 {
-    constexpr int OPD = N == 3 ? 18 : 4;
-    const int lane = threadIdx.x & 31;
+    constexpr int D = Tree<N>::D, SV = 2 * N;
+    extern __shared__ __align__(16) double smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* V = smem + warp * warp_state_doubles<N>();
+    const int64_t* off = a.level_off + (size_t)level * (a.n_sims + 1);
+    const int64_t* coff = off - (a.n_sims + 1);
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < a.n_groups; g += warps) {
-        const int si = find_chunk_sim(a.group_offsets, a.n_sims, g);
-        const int64_t c_first = a.chunk_offsets[si] + (g - a.group_offsets[si]) * kGroup;
-        const int64_t c_end = a.chunk_offsets[si + 1];
-        const int64_t c = c_first + lane;
-        Op<N> P;
-        if (c < c_end) P.load(a.chunk_agg + c * OPD);
-        else P.identity();
-#pragma unroll
-        for (unsigned d = 1; d < 32; d <<= 1) {
-            Op<N> o = P;
-            o.shfl_up(d);
-            if (lane >= (int)d) {
-                Op<N> t;
-                Op<N>::mul(P, o, t);
-                P = t;
-            }
-        }
-        Op<N> M = P;
-        M.shfl_up(1);
-        if (lane == 0) M.identity();
-        if (c < c_end) M.store(a.chunk_gprefix + c * OPD);
-        if (lane == 31) P.store(a.group_agg + g * OPD);
-    }
-}
-
-// Carry: one warp per simulation walks its group products in order.  Lane r
-// (r < N) holds row r of the product and computes component r of the next
-// state; the state is broadcast to all lanes by shuffles.
-template <int N>
-__global__ void __launch_bounds__(128) chain_carry_kernel(ChainArgs a)
-{
-    constexpr int OPD = N == 3 ? 18 : 4;
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t si = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); si < a.n_sims; si += warps) {
+    for (int64_t node = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; node < a.nodes[level]; node += warps) {
+        const int si = find_node_sim(off, a.n_sims, node);
         const DevSim& s = a.sims[si];
-        cx<double> psi[N];
+        if (s.chain_top == level) continue;   // done by the up kernel of this level
+        const int64_t local = node - off[si];
+        if (lane < SV) V[tslot(5, 0) * SV + lane] = a.state[level][node * SV + lane];
+        __syncwarp();
+        const double* L = a.left[level] + node * kLeftPerNode * D;
+        tree_down<N>(V, [&](int t) { return L + t * D; }, lane);
+        const int64_t child = local * kFan + lane;
+        if (child < coff[si + 1] - coff[si]) {
+            double* dst = a.state[level - 1] + (coff[si] + child) * SV;
 #pragma unroll
-        for (int i = 0; i < N; i++) psi[i] = cmk(s.psi0[2 * i], s.psi0[2 * i + 1]);
-        const int64_t g0 = a.group_offsets[si], g1 = a.group_offsets[si + 1];
-        const int r = lane < N ? lane : 0;
-        for (int64_t g = g0; g < g1; g++) {
-            if (lane < N) {
-                double* st = a.group_start + g * (2 * N);
-                st[2 * lane] = psi[lane].r;
-                st[2 * lane + 1] = psi[lane].i;
-            }
-            // row r of the group product
-            cx<double> row[N];
-            const double* Ag = a.group_agg + g * OPD;
-            if (N == 3) {
-#pragma unroll
-                for (int j = 0; j < N; j++) row[j] = cmk(Ag[6 * r + 2 * j], Ag[6 * r + 2 * j + 1]);
-            } else {
-                // [[alpha, -conj(beta)], [beta, conj(alpha)]]
-                const cx<double> al = cmk(Ag[0], Ag[1]), be = cmk(Ag[2], Ag[3]);
-                row[0] = r == 0 ? al : be;
-                row[N - 1] = r == 0 ? cmk(-be.r, be.i) : cconj(al);
-            }
-            cx<double> v = cmul(row[0], psi[0]);
-#pragma unroll
-            for (int j = 1; j < N; j++) v = cfma(row[j], psi[j], v);
-#pragma unroll
-            for (int i = 0; i < N; i++) {
-                psi[i].r = __shfl_sync(0xffffffffu, v.r, i);
-                psi[i].i = __shfl_sync(0xffffffffu, v.i, i);
-            }
+            for (int i = 0; i < SV; i++) dst[i] = V[lane * SV + i];
         }
+        __syncwarp();
     }
 }
 
+// Level 0: states entering the lanes' runs, then each lane walks its run.
 template <int N>
 __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
 {
-    constexpr int OPD = N == 3 ? 18 : 4;
-    const int lane = threadIdx.x & 31;
+    constexpr int D = Tree<N>::D, SV = 2 * N;
+    extern __shared__ __align__(16) double smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double* V = smem + warp * warp_state_doubles<N>();
+    const int64_t* off = a.level_off;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < a.n_chunks; c += warps) {
-        const int si = find_chunk_sim(a.chunk_offsets, a.n_sims, c);
+    for (int64_t node = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; node < a.nodes[0]; node += warps) {
+        const int si = find_node_sim(off, a.n_sims, node);
         const DevSim& s = a.sims[si];
-        const int64_t j = c - a.chunk_offsets[si];
-        const int64_t k0 = j * kChunk + (int64_t)lane * kRun;
-        const int64_t k1 = min(k0 + kRun, s.K);
-        if (k0 >= k1) continue;
-        const int64_t g = a.group_offsets[si] + j / kGroup;
-        cx<double> gs[N], cs[N], psi[N], nxt[N];
+        const int64_t local = node - off[si];
+        if (lane < SV) V[tslot(5, 0) * SV + lane] = s.chain_top == 0 ? s.psi0[lane] : a.state[0][node * SV + lane];
+        __syncwarp();
+        const double* L = a.left[0] + node * kLeftPerNode * D;
+        tree_down<N>(V, [&](int t) { return L + t * D; }, lane);
+        cx<double> psi[N], nxt[N];
 #pragma unroll
-        for (int i = 0; i < N; i++) gs[i] = cmk(a.group_start[g * 2 * N + 2 * i], a.group_start[g * 2 * N + 2 * i + 1]);
-        Op<N> G;
-        G.load(a.chunk_gprefix + c * OPD);
-        G.apply(gs, cs);                 // state entering the chunk
-        Op<N> M;
-        M.load(a.run_prefix + (c * 32 + lane) * OPD);
-        M.apply(cs, psi);                // state entering this lane's run
-        const double* U = a.U + s.sample_offset * OPD;
+        for (int i = 0; i < N; i++) psi[i] = cmk(V[lane * SV + 2 * i], V[lane * SV + 2 * i + 1]);
+        __syncwarp();
+        const int run = s.chain_run;
+        const int64_t k0 = (local * kFan + lane) * run;
+        const int64_t k1 = min(k0 + run, s.K);
+        const double* U = a.U + s.sample_offset * D;
         for (int64_t k = k0; k < k1; k++) {
             Op<N> u;
-            u.load(U + k * OPD);
+            u.load(U + k * D);
             u.apply(psi, nxt);
 #pragma unroll
             for (int i = 0; i < N; i++) psi[i] = nxt[i];
@@ -372,32 +444,34 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
 
 // ----------------------------------------------------------------- launcher
 template <int N>
-static cudaError_t launch_chain_n(const ChainArgs& a, int n_sm, cudaStream_t stream)
+static cudaError_t launch_chain_n(const ChainArgs& a, int n_sm, cudaStream_t stream, int* kernels)
 {
-    if (a.n_chunks == 0) return cudaSuccess;
-    const int block = 128;
-    const int64_t want = (a.n_chunks + 3) / 4;
-    const int grid = (int)std::min<int64_t>(want, (int64_t)n_sm * 16);
+    *kernels = 0;
+    if (a.levels < 1 || a.nodes[0] == 0) return cudaSuccess;
+    const int block = 32 * kChainWarps;
+    const size_t up_smem = (size_t)kChainWarps * warp_tree_doubles<N>() * sizeof(double);
+    const size_t down_smem = (size_t)kChainWarps * warp_state_doubles<N>() * sizeof(double);
+    auto grid = [&](int64_t nodes) {
+        return (int)std::max<int64_t>(1, std::min<int64_t>((nodes + kChainWarps - 1) / kChainWarps, (int64_t)n_sm * 16));
+    };
     ChainArgs args = a;
-    chain_reduce_kernel<N><<<grid, block, 0, stream>>>(args);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int ggrid = (int)std::min<int64_t>((a.n_groups + 3) / 4, (int64_t)n_sm * 16);
-    chain_group_kernel<N><<<ggrid, block, 0, stream>>>(args);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    const int cgrid = (int)std::min<int64_t>((a.n_sims + 3) / 4, (int64_t)n_sm * 16);
-    chain_carry_kernel<N><<<cgrid, 128, 0, stream>>>(args);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    chain_apply_kernel<N><<<grid, block, 0, stream>>>(args);
+    for (int l = 0; l < a.levels; l++) {
+        chain_up_kernel<N><<<grid(a.nodes[l]), block, up_smem, stream>>>(args, l);
+        (*kernels)++;
+    }
+    for (int l = a.levels - 2; l >= 1; l--) {
+        chain_down_kernel<N><<<grid(a.nodes[l]), block, down_smem, stream>>>(args, l);
+        (*kernels)++;
+    }
+    chain_apply_kernel<N><<<grid(a.nodes[0]), block, down_smem, stream>>>(args);
+    (*kernels)++;
     return cudaGetLastError();
 }
 
-cudaError_t launch_chain(int spin_x2, const ChainArgs& a, int n_sm, cudaStream_t stream)
+cudaError_t launch_chain(int spin_x2, const ChainArgs& a, int n_sm, cudaStream_t stream, int* kernels)
 {
-    if (spin_x2 == 2) return launch_chain_n<3>(a, n_sm, stream);
-    if (spin_x2 == 1) return launch_chain_n<2>(a, n_sm, stream);
+    if (spin_x2 == 2) return launch_chain_n<3>(a, n_sm, stream, kernels);
+    if (spin_x2 == 1) return launch_chain_n<2>(a, n_sm, stream, kernels);
     return cudaErrorInvalidValue;
 }
 

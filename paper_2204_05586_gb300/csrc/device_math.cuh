@@ -233,24 +233,41 @@ SPINSIM_HD double drive_phase_at(const DevSim& s, int64_t k)
 // Bulk context of interval k (every lane).  e^{i beta} comes from the bulk
 // type's sincos: the first-order part it feeds is replaced by the exact FP64
 // value at the end of the sample, so it only reaches second-order terms.
-// Returns gsum = sum_p amp_p ghat_p (exact products of R values, in FP64).
+// Returns gsum = sum_p amp_p ghat_p (exact products of R values, in FP64)
+// and the drive phase beta (FP64) for the epilogue.  The per-simulation
+// constants come rounded to FP32 from the host for the FP32 path.
 template <typename R, int N>
-SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c)
+SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& beta)
 {
     const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;
-    const double beta = drive_phase_at(s, k);
+    beta = drive_phase_at(s, k);
     const SinCos<R> eb = sincos_cold((R)beta);
     c.ebr = eb.c;
     c.ebi = eb.s;
+    if constexpr (sizeof(R) == 4) {
 #pragma unroll
-    for (int i = 0; i < 4; i++) split_hi_lo<R>(s.P[i], c.Ph[i], c.Pl[i]);
-    c.za = (R)s.za;
-    c.zb = (R)s.zb;
-    c.zbias = (R)s.zbias;
-    c.qd3 = (R)s.qd3;
-    c.dt = (R)s.dt;
-    c.c1 = (R)s.c1;
-    c.c2 = (R)s.c2;
+        for (int i = 0; i < 4; i++) {
+            c.Ph[i] = s.f_ph[i];
+            c.Pl[i] = s.f_pl[i];
+        }
+        c.za = s.f_za;
+        c.zb = s.f_zb;
+        c.zbias = s.f_zbias;
+        c.qd3 = s.f_qd3;
+        c.dt = s.f_dt;
+        c.c1 = s.f_c1;
+        c.c2 = s.f_c2;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; i++) split_hi_lo<R>(s.P[i], c.Ph[i], c.Pl[i]);
+        c.za = (R)s.za;
+        c.zb = (R)s.zb;
+        c.zbias = (R)s.zbias;
+        c.qd3 = (R)s.qd3;
+        c.dt = (R)s.dt;
+        c.c1 = (R)s.c1;
+        c.c2 = (R)s.c2;
+    }
     c.np = s.n_pulses;
     c.tau = s.tau;
     c.inv_n = ldexp(R(1), -s.tau);
@@ -261,8 +278,13 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c)
     for (int p = 0; p < kMaxPulses; p++) {
         c.amp[p] = R(0); c.u0[p] = R(0); c.invw[p] = R(0); c.ghat[p] = R(0);
         if (p < c.np) {
-            c.amp[p] = (R)s.amp[p];
-            c.invw[p] = (R)s.inv_w[p];
+            if constexpr (sizeof(R) == 4) {
+                c.amp[p] = s.f_amp[p];
+                c.invw[p] = s.f_invw[p];
+            } else {
+                c.amp[p] = (R)s.amp[p];
+                c.invw[p] = (R)s.inv_w[p];
+            }
             c.u0[p] = (R)((t_prev - s.centre[p]) * s.inv_w[p]);
             if (s.frame) {
                 R um = (R)((t_prev + 0.5 * s.dt_out - s.centre[p]) * s.inv_w[p]);
@@ -277,8 +299,9 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c)
     return gsum;
 }
 
-// FP64 quantities of interval k used once per sample by the epilogue:
-// e^{i beta}, the frame frequencies and the exit phasor
+// FP64 quantities of interval k used once per sample by the epilogue, from
+// the drive phase beta and gsum that make_ctx returned: e^{i beta}, the frame
+// frequencies and the exit phasor
 // e^{-i w_r dt_out} (x 1/2 for spin-half).
 //
 // With the frame on, w_r = 2 pi B + gsum where gsum = sum_p amp_p ghat_p uses
@@ -287,9 +310,8 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c)
 // the value the in-frame field subtracts, so leaving the frame undoes
 // entering it.
 template <int N>
-SPINSIM_HD void make_exact(const DevSim& s, int64_t k, double gsum, SampleExact& x)
+SPINSIM_HD void make_exact(const DevSim& s, double beta, double gsum, SampleExact& x)
 {
-    const double beta = drive_phase_at(s, k);
     const SinCos<double> eb = sincos_cold(beta);
     x.eb_re = eb.c;
     x.eb_im = eb.s;

@@ -45,13 +45,16 @@ struct ResType<2, R> { using type = Res2<R>; };
 // diagonal of R(-Delta_t): spin-one rows m = +1, 0, -1 by
 // (e^{-i w_r Dt}, 1, e^{+i w_r Dt}), spin-half (alpha, beta) by (e^{-i w_r Dt/2}, e^{+i w_r Dt/2}).
 
-__device__ __forceinline__ void store_rows(const cx<double> U[3][3], const cx<double> r[3], double* out)
+// Rows m = +1 and m = -1 are scaled by the exit phasor and its conjugate;
+// row m = 0 is stored as it is (factor 1).
+__device__ __forceinline__ void store_rows(const cx<double> U[3][3], cx<double> ph, double* out)
 {
+    const cx<double> r[3] = {ph, cmk(1.0, 0.0), cconj(ph)};
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            cx<double> v = cmul(r[i], U[i][j]);
+            const cx<double> v = i == 1 ? U[i][j] : cmul(r[i], U[i][j]);
             out[6 * i + 2 * j] = v.r;
             out[6 * i + 2 * j + 1] = v.i;
         }
@@ -85,8 +88,7 @@ __device__ __forceinline__ void finish(const Res3<double>& P, const DevSim& s, c
     promote(P, s, x, Y);
 #pragma unroll
     for (int i = 0; i < 3; i++) Y[i][i].r += 1.0;
-    const cx<double> r[3] = {cmk(x.ph_re, x.ph_im), cmk(1.0, 0.0), cmk(x.ph_re, -x.ph_im)};
-    store_rows(Y, r, out);
+    store_rows(Y, cmk(x.ph_re, x.ph_im), out);
 }
 
 // FP32-bulk: the operator is stored as computed.  Its departure from
@@ -98,8 +100,7 @@ __device__ __forceinline__ void finish(const Res3<float>& P, const DevSim& s, co
     promote(P, s, x, Y);
 #pragma unroll
     for (int i = 0; i < 3; i++) Y[i][i].r += 1.0;
-    const cx<double> r[3] = {cmk(x.ph_re, x.ph_im), cmk(1.0, 0.0), cmk(x.ph_re, -x.ph_im)};
-    store_rows(Y, r, out);
+    store_rows(Y, cmk(x.ph_re, x.ph_im), out);
 }
 
 template <typename R>
@@ -182,11 +183,11 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
             si = find_index(a.sample_offsets, a.n_sims, g);
             k = g - a.sample_offsets[si];
         }
-        double gsum = 0.0;
+        double gsum = 0.0, beta = 0.0;
         if (active && k > 0) {
             const DevSim& s = a.sims[si];
             SampleCtx<R> c;
-            gsum = make_ctx<R, N>(s, k, c);
+            gsum = make_ctx<R, N>(s, k, c, beta);
             const int64_t L = s.L;
 #pragma unroll 1
             for (int q = 0; q < SEG_PER_LANE; q++) {
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
                 res_mul(P23, P01, P);
                 const DevSim& s = a.sims[si];
                 SampleExact sx;
-                make_exact<N>(s, k, gsum, sx);
+                make_exact<N>(s, beta, gsum, sx);
                 finish(P, s, sx, out);
             }
         }

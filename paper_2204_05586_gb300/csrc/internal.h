@@ -10,9 +10,45 @@ namespace spinsim {
 
 constexpr int kMaxPulses = 4;
 constexpr int kSegments = 4;             // canonical split of one U_k's L steps (fixed tree)
-constexpr int kRun = 8;                  // samples one lane chains sequentially
-constexpr int kChunk = 32 * kRun;        // samples one warp chains (never spans simulations)
-constexpr int kGroup = 32;               // chunks one warp scans (never spans simulations)
+
+// ------------------------------------------------------- chain-tree geometry
+// The ordered product psi_k = U_k ... U_0 psi_init is a tree scan per
+// simulation (chain.cu).  Level 0 nodes cover kFan runs of `run` consecutive
+// samples (one lane multiplies one run in order); a node of level l >= 1
+// covers kFan consecutive nodes of level l - 1; the top level has one node.
+constexpr int kFan = 32;                 // children of a node: one per lane of a warp
+constexpr int kMaxLevels = 12;           // 256 x 32^11 samples exceed any valid K
+constexpr int kLeftPerNode = kFan - 1;   // stored left-child products of a node's binary tree
+// The run length depends on K alone, so a simulation's result does not depend
+// on the batch it is in: at least 4 samples per lane, more once a simulation
+// has more level-0 nodes than a 152-SM GPU has SM sub-partitions (608), at
+// most 8.
+constexpr int64_t kRunSpread = 32 * 608;
+inline int chain_run(int64_t K)
+{
+    const int64_t r = (K + kRunSpread - 1) / kRunSpread;
+    return (int)(r < 4 ? 4 : (r > 8 ? 8 : r));
+}
+
+struct ChainGeom {
+    int run, top;                        // samples per lane run; level of the single top node
+    int64_t nodes[kMaxLevels];           // nodes per level (0 above the top)
+};
+
+inline ChainGeom chain_geom(int64_t K)
+{
+    ChainGeom g{};
+    g.run = chain_run(K);
+    g.top = 0;
+    int64_t n = K > 0 ? (K + (int64_t)kFan * g.run - 1) / ((int64_t)kFan * g.run) : 0;
+    g.nodes[0] = n;
+    while (n > 1 && g.top + 1 < kMaxLevels) {
+        n = (n + kFan - 1) / kFan;
+        g.top++;
+        g.nodes[g.top] = n;
+    }
+    return g;
+}
 
 // Per-simulation parameters on the device, precomputed on the host in FP64.
 struct DevSim {
@@ -21,8 +57,9 @@ struct DevSim {
     double* ops;                 // [K][N][N] complex or nullptr
     int64_t K, L;
     int64_t sample_offset;       // first sample of this simulation in the operator buffer
-    int64_t chunk_offset;        // first chain chunk of this simulation
-    int64_t group_offset;        // first chunk group of this simulation
+    int32_t chain_run;           // samples per lane run at the bottom of the chain tree
+    int32_t chain_top;           // level of the chain tree's top node
+    int64_t chain_pad;
     double t_start, dt_out, dt;  // dt = dt_out / L
     double drive_hz, drive_phase;
     double w_co0, w_counter0;    // frame: 2 pi (f_d - B), 2 pi (f_d + B); lab: 2 pi f_d, 2 pi f_d
@@ -57,6 +94,11 @@ struct DevSim {
     double inv_w[kMaxPulses];
     double psi0[6];
     int32_t n_pulses, frame, spin_x2, counter_on;
+    // The same constants rounded to FP32 once, on the host, for the FP32-bulk
+    // kernels (P as an FP32 (hi, lo) pair: hi = fl(P), lo = fl(P - hi)).
+    float f_ph[4], f_pl[4];
+    float f_za, f_zb, f_zbias, f_qd3, f_dt, f_c1, f_c2, f_pad;
+    float f_amp[kMaxPulses], f_invw[kMaxPulses];
 };
 
 struct IntegrateArgs {
@@ -72,42 +114,60 @@ struct IntegrateArgs {
 
 struct ChainArgs {
     const DevSim* sims;
-    const int64_t* chunk_offsets;     // n_sims + 1 prefix offsets (device)
-    const int64_t* group_offsets;     // n_sims + 1 prefix offsets (device)
     int n_sims;
-    int64_t n_chunks, n_groups;
-    const double* U;
-    double* run_prefix;               // [n_chunks][32] exclusive prefixes of the lanes' runs
-    double* chunk_agg;                // [n_chunks] chunk products
-    double* chunk_gprefix;            // [n_chunks] exclusive prefixes of the chunk products in their group
-    double* group_agg;                // [n_groups] group products
-    double* group_start;              // [n_groups][N] complex states entering each group
+    int levels;                       // 1 + the highest top level of the batch
+    const int64_t* level_off;         // [levels][n_sims + 1] first node of each simulation per level (device)
+    int64_t nodes[kMaxLevels];        // nodes per level, all simulations
+    const double* U;                  // sample operators
+    double* agg[kMaxLevels];          // [nodes] product of the node's samples
+    double* left[kMaxLevels];         // [nodes][kLeftPerNode] left-child products of the node's binary tree
+    double* state[kMaxLevels];        // [nodes][N] complex state entering the node
 };
 
 // Doubles per stored operator in the operator buffer and chain scratch.
 inline int op_doubles(int spin_x2) { return spin_x2 == 2 ? 18 : 4; }
 
-inline int64_t n_chunks_of(int64_t K) { return (K + kChunk - 1) / kChunk; }
-inline int64_t n_groups_of(int64_t K) { return (n_chunks_of(K) + kGroup - 1) / kGroup; }
 inline size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Layout of the chain scratch (offsets from its start, 256-byte aligned).
+// Layout of the chain scratch of a batch (offsets from its start, 256-byte aligned).
 struct ChainLayout {
-    size_t prefix, agg, gprefix, gagg, gstart, bytes;
+    int levels;
+    int64_t nodes[kMaxLevels];
+    size_t agg[kMaxLevels], left[kMaxLevels], state[kMaxLevels], bytes;
 };
-inline ChainLayout chain_layout(int spin_x2, int64_t chunks, int64_t groups)
+
+inline ChainLayout chain_layout(int spin_x2, const int64_t* nodes, int levels)
 {
     const size_t opb = (size_t)op_doubles(spin_x2) * sizeof(double);
-    ChainLayout c;
+    const size_t stb = (size_t)2 * (spin_x2 + 1) * sizeof(double);
+    ChainLayout c{};
+    c.levels = levels;
     size_t off = 0;
-    c.prefix = off; off += round256((size_t)chunks * 32 * opb);
-    c.agg = off; off += round256((size_t)chunks * opb);
-    c.gprefix = off; off += round256((size_t)chunks * opb);
-    c.gagg = off; off += round256((size_t)groups * opb);
-    c.gstart = off; off += round256((size_t)groups * 2 * (spin_x2 + 1) * sizeof(double));
+    for (int l = 0; l < levels; l++) {
+        c.nodes[l] = nodes[l];
+        c.agg[l] = off; off += round256((size_t)nodes[l] * opb);
+        c.left[l] = off; off += round256((size_t)nodes[l] * kLeftPerNode * opb);
+        c.state[l] = off; off += round256((size_t)nodes[l] * stb);
+    }
     c.bytes = off;
     return c;
 }
+
+// Point the per-level arrays of `a` into chain scratch laid out by `cl` at `base`.
+inline void chain_args_set(ChainArgs& a, const ChainLayout& cl, char* base)
+{
+    a.levels = cl.levels;
+    for (int l = 0; l < kMaxLevels; l++) {
+        const bool used = l < cl.levels;
+        a.nodes[l] = used ? cl.nodes[l] : 0;
+        a.agg[l] = used ? reinterpret_cast<double*>(base + cl.agg[l]) : nullptr;
+        a.left[l] = used ? reinterpret_cast<double*>(base + cl.left[l]) : nullptr;
+        a.state[l] = used ? reinterpret_cast<double*>(base + cl.state[l]) : nullptr;
+    }
+}
+
+// Kernels launch_chain issues for a batch whose tallest tree has `levels` levels.
+inline int chain_kernels(int levels) { return levels + (levels > 2 ? levels - 2 : 0) + 1; }
 
 // ------------------------------------------------- request warning bits
 constexpr double kMagnusXi = 1.0868687;   // Sec. 1.2.2: convergence radius of the Magnus series
@@ -208,6 +268,8 @@ cudaError_t launch_integrate(int spin_x2, int precision, int method, int lanes, 
 size_t integrate_smem_bytes(int spin_x2, int precision, int lanes, int block);
 cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int lanes, int block, bool small,
                                 int* blocks_per_sm);
-cudaError_t launch_chain(int spin_x2, const ChainArgs& a, int n_sm, cudaStream_t stream);
+// launch_chain: the chain kernels of a batch in order on `stream`; *kernels
+// receives how many were launched.
+cudaError_t launch_chain(int spin_x2, const ChainArgs& a, int n_sm, cudaStream_t stream, int* kernels);
 
 }  // namespace spinsim

@@ -1,7 +1,7 @@
 // spinsim_api.cu -- host engine behind the C ABI of include/spinsim.h.
 //
-// One batch = validate requests -> plan (sample/chunk offsets, parameter
-// table) -> upload the table -> integrate kernel (all U_k) -> chain kernels
+// One batch = validate requests -> plan (sample offsets, chain-tree node
+// offsets, parameter table) -> upload the table -> integrate kernel (all U_k) -> chain kernels
 // (psi_k, <J>_k, U_k) -> copy back any host-resident outputs.  Requests of
 // both spins may share a batch; each spin is one pass of the kernels.
 #include <cuda_runtime.h>
@@ -108,8 +108,11 @@ struct Group {
     int spin_x2;
     bool small = true;             // every request of the group takes the small-angle kernel
     std::vector<int64_t> idx;      // request indices
-    int64_t samples = 0, chunks = 0, groups = 0;
-    size_t sims_off = 0, soff_off = 0, coff_off = 0, goff_off = 0, counter_off = 0, U_off = 0, chain_off = 0;
+    int64_t samples = 0;
+    double steps = 0.0;            // CF4 (or sampling) steps of the group
+    int levels = 1;                // chain-tree levels of the tallest simulation
+    int64_t nodes[kMaxLevels] = {};  // chain-tree nodes per level, all simulations
+    size_t sims_off = 0, soff_off = 0, loff_off = 0, counter_off = 0, U_off = 0, chain_off = 0;
     ChainLayout chain{};
 };
 
@@ -130,16 +133,22 @@ struct Plan {
 };
 
 struct TuneKey {
-    int spin, precision, method, tau, bucket, small;
+    int spin, precision, method, tau, small;
+    int64_t size;   // samples (small batches) or their power-of-two bucket (large ones)
     bool operator<(const TuneKey& o) const
     {
-        return std::tie(spin, precision, method, tau, bucket, small) <
-               std::tie(o.spin, o.precision, o.method, o.tau, o.bucket, o.small);
+        return std::tie(spin, precision, method, tau, small, size) <
+               std::tie(o.spin, o.precision, o.method, o.tau, o.small, o.size);
     }
 };
 struct TuneVal {
-    int lanes, block;
+    int lanes, block, blocks_per_sm;
 };
+
+// Batches of at most this many CF4 steps are tuned on their full size: their
+// time depends on how the last wave of tiles fills the GPU, which a prefix
+// would not show.  Larger batches are tuned on a prefix of a few waves.
+constexpr double kFullTrialSteps = 4e8;
 
 std::mutex g_tune_mu;
 std::map<std::pair<int, TuneKey>, TuneVal> g_tune_cache;   // (device, key) -> choice, shared by handles
@@ -232,19 +241,20 @@ int ensure_pinned(PinnedBuf& b, size_t need)
     return SPINSIM_OK;
 }
 
-// Scratch bytes of one group (spin) of a batch.
-// Parameter table of one spin group: the simulations and their sample,
-// chunk and group offsets, contiguous (uploaded with one copy).
-size_t table_bytes(int64_t n)
+// Parameter table of one spin group: the simulations, their sample offsets
+// and their first chain-tree node per level, contiguous (uploaded with one copy).
+size_t table_bytes(int64_t n, int levels)
 {
-    return round_up((size_t)n * sizeof(DevSim), 256) + 3 * round_up((size_t)(n + 1) * sizeof(int64_t), 256);
+    return round_up((size_t)n * sizeof(DevSim), 256) + round_up((size_t)(n + 1) * sizeof(int64_t), 256) +
+           round_up((size_t)levels * (n + 1) * sizeof(int64_t), 256);
 }
 
-size_t group_bytes(int spin_x2, int64_t n, int64_t samples, int64_t chunks, int64_t groups)
+// Scratch bytes of one group (spin) of a batch.
+size_t group_bytes(int spin_x2, int64_t n, int64_t samples, const int64_t* nodes, int levels)
 {
     const size_t opb = (size_t)op_doubles(spin_x2) * sizeof(double);
-    return table_bytes(n) + 256 /* tile counter */ + round_up((size_t)samples * opb, 256) +
-           chain_layout(spin_x2, chunks, groups).bytes;
+    return table_bytes(n, levels) + 256 /* tile counter */ + round_up((size_t)samples * opb, 256) +
+           chain_layout(spin_x2, nodes, levels).bytes;
 }
 
 // Build the plan: offsets inside one arena, the staged outputs, and fill the
@@ -265,22 +275,23 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
                 g.idx.push_back(i);
                 g.small = g.small && checked[i].small;
                 g.samples += checked[i].K;
-                g.chunks += n_chunks_of(checked[i].K);
-                g.groups += n_groups_of(checked[i].K);
+                g.steps += (double)checked[i].K * (double)checked[i].L;
+                const ChainGeom cg = chain_geom(checked[i].K);
+                g.levels = std::max(g.levels, cg.top + 1);
+                for (int l = 0; l <= cg.top; l++) g.nodes[l] += cg.nodes[l];
             }
         if (g.idx.empty()) continue;
         const int64_t m = (int64_t)g.idx.size();
         const size_t opb = (size_t)op_doubles(spin) * sizeof(double);
         g.sims_off = off;
         g.soff_off = off + round_up((size_t)m * sizeof(DevSim), 256);
-        g.coff_off = g.soff_off + round_up((size_t)(m + 1) * sizeof(int64_t), 256);
-        g.goff_off = g.coff_off + round_up((size_t)(m + 1) * sizeof(int64_t), 256);
-        off += table_bytes(m);
+        g.loff_off = g.soff_off + round_up((size_t)(m + 1) * sizeof(int64_t), 256);
+        off += table_bytes(m, g.levels);
         g.counter_off = off; off += 256;
         g.U_off = off; off += round_up((size_t)g.samples * opb, 256);
-        g.chain = chain_layout(spin, g.chunks, g.groups);
+        g.chain = chain_layout(spin, g.nodes, g.levels);
         g.chain_off = off; off += g.chain.bytes;
-        pin += table_bytes(m);
+        pin += table_bytes(m, g.levels);
         plan.groups.push_back(std::move(g));
     }
     // host-resident or misaligned outputs are staged through the arena
@@ -316,10 +327,10 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
         const int64_t m = (int64_t)g.idx.size();
         DevSim* sims = reinterpret_cast<DevSim*>(pinned + pin);
         int64_t* soff = reinterpret_cast<int64_t*>(pinned + pin + (g.soff_off - g.sims_off));
-        int64_t* coff = reinterpret_cast<int64_t*>(pinned + pin + (g.coff_off - g.sims_off));
-        int64_t* goff = reinterpret_cast<int64_t*>(pinned + pin + (g.goff_off - g.sims_off));
-        pin += table_bytes(m);
-        int64_t so = 0, co = 0, go = 0;
+        int64_t* loff = reinterpret_cast<int64_t*>(pinned + pin + (g.loff_off - g.sims_off));
+        pin += table_bytes(m, g.levels);
+        int64_t so = 0;
+        int64_t lo[kMaxLevels] = {};
         for (int64_t q = 0; q < m; q++) {
             const int64_t i = g.idx[q];
             const spinsim_request& r = reqs[i];
@@ -335,22 +346,22 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
                     if (s.host_ops) d.ops = reinterpret_cast<double*>(base + s.ops_off);
                 }
             d.sample_offset = so;
-            d.chunk_offset = co;
-            d.group_offset = go;
             soff[q] = so;
-            coff[q] = co;
-            goff[q] = go;
             so += d.K;
-            co += n_chunks_of(d.K);
-            go += n_groups_of(d.K);
+            const ChainGeom cg = chain_geom(d.K);
+            d.chain_run = cg.run;
+            d.chain_top = cg.top;
+            for (int l = 0; l < g.levels; l++) {
+                loff[(size_t)l * (m + 1) + q] = lo[l];
+                lo[l] += l <= cg.top ? cg.nodes[l] : 0;
+            }
             res[i].trotter_squares = d.tau;
             h->last.trotter_squares = std::max(h->last.trotter_squares, d.tau);
             d.spin_x2 = r.spin_x2;
             sims[q] = d;
         }
         soff[m] = so;
-        coff[m] = co;
-        goff[m] = go;
+        for (int l = 0; l < g.levels; l++) loff[(size_t)l * (m + 1) + m] = lo[l];
     }
 }
 
@@ -382,17 +393,22 @@ int size_bucket(int64_t samples)
     return b;
 }
 
-// Choose (lanes per sample, threads per block) for the integrate kernel.
-// Results never depend on this choice; only the time does.
-int choose_shape(spinsim_s* h, int spin, bool small, IntegrateArgs a, cudaStream_t stream, bool capturing, int& lanes,
-                 int& block, int& grid)
+// Choose (lanes per sample, threads per block, resident blocks per SM) for
+// the integrate kernel.  Results never depend on this choice; only the time
+// does.  Explicit configuration values are kept; the rest are tuned by
+// timing trial launches, once per (device, key), and cached.
+int choose_shape(spinsim_s* h, int spin, bool small, double steps, IntegrateArgs a, cudaStream_t stream,
+                 bool capturing, int& lanes, int& block, int& grid)
 {
     const int precision = h->cfg.precision;
     const int method = h->cfg.method;
     lanes = h->cfg.lanes_per_sample;
     block = h->cfg.threads_per_block;
-    if (lanes == 0 || block == 0) {
-        TuneKey key{spin, precision, method, h->tau, size_bucket(a.total_samples), (int)small};
+    int bps = h->cfg.blocks_per_sm;
+    const bool full_trial = steps <= kFullTrialSteps;
+    if (lanes == 0 || block == 0 || bps == 0) {
+        TuneKey key{spin, precision, method, h->tau, (int)small,
+                    full_trial ? a.total_samples : -(int64_t)size_bucket(a.total_samples)};
         bool found = false;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -400,13 +416,14 @@ int choose_shape(spinsim_s* h, int spin, bool small, IntegrateArgs a, cudaStream
             if (it != g_tune_cache.end()) {
                 if (lanes == 0) lanes = it->second.lanes;
                 if (block == 0) block = it->second.block;
+                if (bps == 0) bps = it->second.blocks_per_sm;
                 found = true;
             }
         }
         if (!found) {
             const int lane_opts[3] = {1, 2, 4};
             const int block_opts[3] = {64, 128, 256};
-            int best_l = lanes ? lanes : 4, best_b = block ? block : 128;
+            int best_l = lanes ? lanes : 2, best_b = block ? block : 128, best_p = bps;
             if (!capturing) {
                 float best = 1e30f;
                 cudaEvent_t e0, e1;
@@ -419,49 +436,61 @@ int choose_shape(spinsim_s* h, int spin, bool small, IntegrateArgs a, cudaStream
                         if (block && bi > 0) break;
                         int per_sm = 0;
                         if (occupancy(h, spin, L, B, small, false, &per_sm) != SPINSIM_OK || per_sm < 1) continue;
-                        // trial on a prefix of the batch: at most 4 full waves of this shape
-                        IntegrateArgs t = a;
-                        const int64_t wave = (int64_t)h->n_sm * per_sm * (B / L);
-                        t.total_samples = std::min<int64_t>(a.total_samples, 4 * wave);
-                        const int spb = B / L;
-                        t.n_tiles = (t.total_samples + spb - 1) / spb;
-                        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(t.n_tiles, (int64_t)h->n_sm * per_sm));
-                        float ms_best = 1e30f;
-                        for (int rep = 0; rep < 2; rep++) {
-                            cudaMemsetAsync(a.tile_counter, 0, sizeof(unsigned long long), stream);
-                            cudaEventRecord(e0, stream);
-                            launch_integrate(spin, precision, method, L, B, g, small, t, stream);
-                            cudaEventRecord(e1, stream);
-                            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                                cudaEventDestroy(e0);
-                                cudaEventDestroy(e1);
-                                return SPINSIM_E_CUDA;
+                        // resident blocks per SM to try: the explicit value, else
+                        // the most the kernel allows and (full-size trials only,
+                        // where the last wave matters) up to two fewer
+                        const int p_hi = bps ? std::min(bps, per_sm) : per_sm;
+                        const int p_lo = bps ? p_hi : (full_trial ? std::max(1, per_sm - 2) : per_sm);
+                        for (int P = p_hi; P >= p_lo; P--) {
+                            IntegrateArgs t = a;
+                            const int spb = B / L;
+                            if (!full_trial) {
+                                // a prefix of at most 4 full waves of this shape
+                                const int64_t wave = (int64_t)h->n_sm * P * spb;
+                                t.total_samples = std::min<int64_t>(a.total_samples, 4 * wave);
                             }
-                            float ms = 0.f;
-                            cudaEventElapsedTime(&ms, e0, e1);
-                            ms_best = std::min(ms_best, ms);
-                        }
-                        const float per = ms_best / (float)std::max<int64_t>(1, t.total_samples);
-                        if (per < best) {
-                            best = per;
-                            best_l = L;
-                            best_b = B;
+                            t.n_tiles = (t.total_samples + spb - 1) / spb;
+                            const int g = (int)std::max<int64_t>(1, std::min<int64_t>(t.n_tiles, (int64_t)h->n_sm * P));
+                            float ms_best = 1e30f;
+                            for (int rep = 0; rep < 2; rep++) {
+                                cudaMemsetAsync(a.tile_counter, 0, sizeof(unsigned long long), stream);
+                                cudaEventRecord(e0, stream);
+                                launch_integrate(spin, precision, method, L, B, g, small, t, stream);
+                                cudaEventRecord(e1, stream);
+                                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                                    cudaEventDestroy(e0);
+                                    cudaEventDestroy(e1);
+                                    return SPINSIM_E_CUDA;
+                                }
+                                float ms = 0.f;
+                                cudaEventElapsedTime(&ms, e0, e1);
+                                ms_best = std::min(ms_best, ms);
+                            }
+                            const float per = ms_best / (float)std::max<int64_t>(1, t.total_samples);
+                            if (per < best) {
+                                best = per;
+                                best_l = L;
+                                best_b = B;
+                                best_p = P;
+                            }
                         }
                     }
                 }
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
                 std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tune_cache[{h->device, key}] = TuneVal{best_l, best_b};
+                g_tune_cache[{h->device, key}] = TuneVal{best_l, best_b, best_p};
             }
             lanes = best_l;
             block = best_b;
+            bps = best_p;
         }
     }
     int per_sm = 0;
     int st = occupancy(h, spin, lanes, block, small, capturing, &per_sm);
     if (st != SPINSIM_OK) return st;
     per_sm = std::max(per_sm, 1);
+    if (bps > 0) per_sm = std::min(per_sm, bps);
     const int spb = block / lanes;
     const int64_t tiles = (a.total_samples + spb - 1) / spb;
     grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)h->n_sm * per_sm));
@@ -511,7 +540,7 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
     size_t pin = 0;
     for (const Group& g : plan.groups) {
         const int64_t m = (int64_t)g.idx.size();
-        const size_t tbl = table_bytes(m);
+        const size_t tbl = table_bytes(m, g.levels);
         // the table is contiguous in both the pinned buffer and the arena
         if (cudaMemcpyAsync(base + g.sims_off, static_cast<char*>(pinned.p) + pin, tbl, cudaMemcpyHostToDevice,
                             stream) != cudaSuccess)
@@ -530,7 +559,7 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
         ia.tile_counter = reinterpret_cast<unsigned long long*>(base + g.counter_off);
         int lanes = 0, block = 0, grid = 0;
         if (g.samples > 0) {
-            st = choose_shape(h, g.spin_x2, g.small, ia, stream, capturing, lanes, block, grid);
+            st = choose_shape(h, g.spin_x2, g.small, g.steps, ia, stream, capturing, lanes, block, grid);
             if (st != SPINSIM_OK) return st;
             const int spb = block / lanes;
             ia.n_tiles = (g.samples + spb - 1) / spb;
@@ -544,21 +573,14 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             kernels += 1;
             ChainArgs ca;
             ca.sims = ia.sims;
-            ca.chunk_offsets = reinterpret_cast<const int64_t*>(base + g.coff_off);
-            ca.group_offsets = reinterpret_cast<const int64_t*>(base + g.goff_off);
-            ca.n_groups = g.groups;
             ca.n_sims = (int)m;
-            ca.n_chunks = g.chunks;
+            ca.level_off = reinterpret_cast<const int64_t*>(base + g.loff_off);
             ca.U = ia.U;
-            char* cb = base + g.chain_off;
-            ca.run_prefix = reinterpret_cast<double*>(cb + g.chain.prefix);
-            ca.chunk_agg = reinterpret_cast<double*>(cb + g.chain.agg);
-            ca.chunk_gprefix = reinterpret_cast<double*>(cb + g.chain.gprefix);
-            ca.group_agg = reinterpret_cast<double*>(cb + g.chain.gagg);
-            ca.group_start = reinterpret_cast<double*>(cb + g.chain.gstart);
-            if (launch_chain(g.spin_x2, ca, h->n_sm, stream) != cudaSuccess) return SPINSIM_E_CUDA;
+            chain_args_set(ca, g.chain, base + g.chain_off);
+            int chain_k = 0;
+            if (launch_chain(g.spin_x2, ca, h->n_sm, stream, &chain_k) != cudaSuccess) return SPINSIM_E_CUDA;
             if (pg >= 0) cudaEventRecord(h->prof[pg][2], stream);
-            kernels += 4;
+            kernels += chain_k;
             h->last.lanes_per_sample = lanes;
             h->last.threads_per_block = block;
             h->last.grid_blocks = grid;
@@ -648,7 +670,7 @@ int spinsim_create(const spinsim_config* cfg, spinsim_handle* out)
           cfg->lanes_per_sample == 4) ||
         !(cfg->threads_per_block == 0 || cfg->threads_per_block == 64 || cfg->threads_per_block == 128 ||
           cfg->threads_per_block == 256) ||
-        cfg->mem_budget < 0)
+        cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32 || cfg->mem_budget < 0)
         return SPINSIM_E_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
@@ -722,18 +744,22 @@ int spinsim_counts(const spinsim_request* req, int64_t* K, int64_t* L)
 int64_t spinsim_footprint(spinsim_handle h, const spinsim_request* reqs, int64_t n)
 {
     if (!h || (n > 0 && !reqs) || n < 0) return SPINSIM_E_ARG;
-    int64_t samples[3] = {0, 0, 0}, chunks[3] = {0, 0, 0}, groups[3] = {0, 0, 0}, count[3] = {0, 0, 0};
+    int64_t samples[3] = {0, 0, 0}, count[3] = {0, 0, 0};
+    int64_t nodes[3][kMaxLevels] = {};
+    int levels[3] = {1, 1, 1};
     for (int64_t i = 0; i < n; i++) {
         Checked c = check_request(&reqs[i]);
         if (c.status != SPINSIM_OK) return c.status;
-        samples[reqs[i].spin_x2] += c.K;
-        chunks[reqs[i].spin_x2] += n_chunks_of(c.K);
-        groups[reqs[i].spin_x2] += n_groups_of(c.K);
-        count[reqs[i].spin_x2] += 1;
+        const int sp = reqs[i].spin_x2;
+        samples[sp] += c.K;
+        count[sp] += 1;
+        const ChainGeom cg = chain_geom(c.K);
+        levels[sp] = std::max(levels[sp], cg.top + 1);
+        for (int l = 0; l <= cg.top; l++) nodes[sp][l] += cg.nodes[l];
     }
     int64_t total = 0;
     for (int s = 1; s <= 2; s++)
-        if (count[s]) total += (int64_t)group_bytes(s, count[s], samples[s], chunks[s], groups[s]);
+        if (count[s]) total += (int64_t)group_bytes(s, count[s], samples[s], nodes[s], levels[s]);
     return total;
 }
 
@@ -868,7 +894,8 @@ static int serving_init(spinsim_s* h)
 
 static size_t request_bytes(const spinsim_request& r, const Checked& c)
 {
-    return group_bytes(r.spin_x2, 1, c.K, n_chunks_of(c.K), n_groups_of(c.K));
+    const ChainGeom cg = chain_geom(c.K);
+    return group_bytes(r.spin_x2, 1, c.K, cg.nodes, cg.top + 1);
 }
 
 // Retire finished batches, then launch pending requests on free slots while

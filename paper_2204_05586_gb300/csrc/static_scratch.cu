@@ -25,7 +25,7 @@ using namespace spinsim;
 
 namespace {
 
-// 16 MiB: a spin-one request of up to ~102,000 output samples (a spin-half
+// 16 MiB: a spin-one request of up to ~99,000 output samples (a spin-half
 // one of up to ~460,000) fits.  Every GPU that loads the library holds this
 // array until the process exits.
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;
@@ -60,7 +60,8 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         !(cfg->lanes_per_sample == 0 || cfg->lanes_per_sample == 1 || cfg->lanes_per_sample == 2 ||
           cfg->lanes_per_sample == 4) ||
         !(cfg->threads_per_block == 0 || cfg->threads_per_block == 64 || cfg->threads_per_block == 128 ||
-          cfg->threads_per_block == 256))
+          cfg->threads_per_block == 256) ||
+        cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32)
         return SPINSIM_E_ARG;
     int64_t K = 0, L = 0;
     int st = spinsim_counts(req, &K, &L);
@@ -101,13 +102,12 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     char* base = static_cast<char*>(base_v);
     const int spin = req->spin_x2;
     const int opd = op_doubles(spin);
-    const int64_t chunks = n_chunks_of(K), groups = n_groups_of(K);
-    const ChainLayout cl = chain_layout(spin, chunks, groups);
+    const ChainGeom cg = chain_geom(K);
+    const ChainLayout cl = chain_layout(spin, cg.nodes, cg.top + 1);
     size_t off = 0;
     const size_t sims_off = off; off += up256(sizeof(DevSim));
     const size_t soff_off = off; off += 256;
-    const size_t coff_off = off; off += 256;
-    const size_t goff_off = off; off += 256;
+    const size_t loff_off = off; off += up256(kMaxLevels * 2 * sizeof(int64_t));
     const size_t counter_off = off; off += 256;
     const size_t U_off = off; off += up256((size_t)K * opd * 8);
     const size_t chain_off = off; off += cl.bytes;
@@ -119,17 +119,21 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     d.states = res->states;
     d.spin = res->spin;
     d.ops = res->ops;
+    d.sample_offset = 0;
+    d.chain_run = cg.run;
+    d.chain_top = cg.top;
     const bool small = small_angle_request(*cfg, *req, L);
     res->trotter_squares = d.tau;
-    int64_t offsets[6] = {0, K, 0, chunks, 0, groups};
+    // sample offsets {0, K} and, per chain level, the node offsets {0, nodes}
+    int64_t offsets[2] = {0, K};
+    int64_t level_off[kMaxLevels * 2] = {};
+    for (int l = 0; l <= cg.top; l++) level_off[2 * l + 1] = cg.nodes[l];
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     // Copies from pageable host memory: the source may be reused on return.
     if (cudaMemcpyAsync(base + sims_off, &d, sizeof(DevSim), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-        cudaMemcpyAsync(base + soff_off, offsets, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-        cudaMemcpyAsync(base + coff_off, offsets + 2, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, stream) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(base + goff_off, offsets + 4, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, stream) !=
-            cudaSuccess)
+        cudaMemcpyAsync(base + soff_off, offsets, sizeof(offsets), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+        cudaMemcpyAsync(base + loff_off, level_off, (size_t)(cg.top + 1) * 2 * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return res->status = SPINSIM_E_CUDA;
     if (K > 0) {
         int n_sm = 0;
@@ -151,6 +155,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         ia.tile_counter = reinterpret_cast<unsigned long long*>(base + counter_off);
         const int spb = block / lanes;
         ia.n_tiles = (K + spb - 1) / spb;
+        if (cfg->blocks_per_sm > 0) per_sm = std::min(per_sm, cfg->blocks_per_sm);
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ia.n_tiles, (int64_t)n_sm * std::max(per_sm, 1)));
         // the tile counter keeps the previous call's value: clear it
         if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
@@ -159,18 +164,12 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
             return res->status = SPINSIM_E_CUDA;
         ChainArgs ca;
         ca.sims = ia.sims;
-        ca.chunk_offsets = reinterpret_cast<const int64_t*>(base + coff_off);
-        ca.group_offsets = reinterpret_cast<const int64_t*>(base + goff_off);
         ca.n_sims = 1;
-        ca.n_chunks = chunks;
-        ca.n_groups = groups;
+        ca.level_off = reinterpret_cast<const int64_t*>(base + loff_off);
         ca.U = ia.U;
-        ca.run_prefix = reinterpret_cast<double*>(base + chain_off + cl.prefix);
-        ca.chunk_agg = reinterpret_cast<double*>(base + chain_off + cl.agg);
-        ca.chunk_gprefix = reinterpret_cast<double*>(base + chain_off + cl.gprefix);
-        ca.group_agg = reinterpret_cast<double*>(base + chain_off + cl.gagg);
-        ca.group_start = reinterpret_cast<double*>(base + chain_off + cl.gstart);
-        if (launch_chain(spin, ca, n_sm, stream) != cudaSuccess) return res->status = SPINSIM_E_CUDA;
+        chain_args_set(ca, cl, base + chain_off);
+        int chain_k = 0;
+        if (launch_chain(spin, ca, n_sm, stream, &chain_k) != cudaSuccess) return res->status = SPINSIM_E_CUDA;
     }
     res->n_samples = K;
     res->status = SPINSIM_OK;

@@ -36,7 +36,7 @@ class spinsim_config(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("precision", ctypes.c_int32), ("rotating_frame", ctypes.c_int32),
                 ("trotter_squares", ctypes.c_int32), ("lanes_per_sample", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("mem_budget", ctypes.c_int64), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("mem_budget", ctypes.c_int64), ("profile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
 class spinsim_field(ctypes.Structure):
@@ -198,13 +198,14 @@ def make_request(req: dict) -> spinsim_request:
 
 
 def make_config(precision=PREC_FP32_BULK, method=METHOD_CF4, rotating_frame=True, tau=-1, lanes=0, block=0,
-                use_graphs=False, device=0, mem_budget=0, profile=False) -> spinsim_config:
+                use_graphs=False, device=0, mem_budget=0, profile=False, blocks_per_sm=0) -> spinsim_config:
     c = spinsim_config()
     spinsim_config_default(c)
     c.precision, c.method, c.rotating_frame, c.trotter_squares = precision, method, int(bool(rotating_frame)), tau
     c.lanes_per_sample, c.threads_per_block, c.use_graphs, c.device = lanes, block, int(bool(use_graphs)), device
     c.mem_budget = mem_budget
     c.profile = int(bool(profile))
+    c.blocks_per_sm = blocks_per_sm
     return c
 
 
