@@ -90,7 +90,9 @@ typedef struct {
     int32_t lanes_per_sample;     /* 0 = autotune; else 1, 2 or 4 threads share one U_k.
                                      Results do not depend on it (fixed reduction tree).   */
     int32_t threads_per_block;    /* 0 = autotune; else 64, 128 or 256                        */
-    int32_t use_graphs;           /* 1: replay repeated identical batch shapes as a CUDA graph */
+    int32_t use_graphs;           /* 1: replay repeated identical batch shapes as a CUDA graph
+                                     on the caller's stream (the first call of a shape runs
+                                     eagerly and captures it); calls stay in issue order   */
     int32_t device;               /* CUDA device ordinal                                      */
     int64_t mem_budget;           /* bytes of device scratch the handle may hold; 0 = 90% of
                                      the free memory at spinsim_create                     */

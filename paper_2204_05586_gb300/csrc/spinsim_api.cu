@@ -180,8 +180,12 @@ struct spinsim_s {
     int n_sm = 0;
     int tau = 24;
     size_t budget = 0;
-    cudaStream_t work = nullptr;    // internal stream (graph capture / replay)
+    cudaStream_t work = nullptr;    // internal stream (eager runs and graph capture)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_pinned = nullptr;
+    // Graph replays run on the caller's stream; ev_done marks the end of the
+    // handle's last replay so that the next call, on any stream, starts after it.
+    cudaEvent_t ev_done = nullptr;
+    bool done_pending = false;
     Arena arena;
     PinnedBuf pinned;
     spinsim_launch_info last{};
@@ -191,6 +195,7 @@ struct spinsim_s {
     std::vector<uint64_t> graph_sig;
     cudaGraphExec_t graph_exec = nullptr;
     int graph_kernels = 0;
+    int graph_prof_groups = 0;                      // profiled groups whose events the graph records
     spinsim_launch_info graph_info{};
     // profiling: per spin group, events before integrate, after integrate, after chain
     cudaEvent_t prof[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
@@ -520,10 +525,16 @@ int refresh_table(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res
 
 // Enqueue one batch on `stream` using `arena` and the pinned table buffer.
 // Requests with a failed validation are skipped.
+// With `prof_in_graph`, a capture of the handle's own graph records the
+// profiling events as event nodes, so every replay times its kernels.
 int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, const std::vector<Checked>& checked,
               const Plan& plan, cudaStream_t stream, Arena& arena, PinnedBuf& pinned, cudaEvent_t pinned_free,
-              bool capturing, int* kernels_out)
+              bool capturing, int* kernels_out, bool prof_in_graph = false)
 {
+    auto prof_record = [&](cudaEvent_t e) {
+        if (capturing) cudaEventRecordWithFlags(e, stream, cudaEventRecordExternal);
+        else cudaEventRecord(e, stream);
+    };
     if (plan.groups.empty()) {
         if (kernels_out) *kernels_out = 0;
         return SPINSIM_OK;
@@ -547,7 +558,7 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             return SPINSIM_E_CUDA;
         pin += tbl;
         h->last.h2d_bytes += (int64_t)tbl;
-        const int pg = (h->cfg.profile && !capturing && h->prof_groups < 2) ? h->prof_groups++ : -1;
+        const int pg = (h->cfg.profile && (!capturing || prof_in_graph) && h->prof_groups < 2) ? h->prof_groups++ : -1;
         if (pinned_free && cudaEventRecord(pinned_free, stream) != cudaSuccess) return SPINSIM_E_CUDA;
         IntegrateArgs ia;
         ia.sims = reinterpret_cast<const DevSim*>(base + g.sims_off);
@@ -565,11 +576,11 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             ia.n_tiles = (g.samples + spb - 1) / spb;
             if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
                 return SPINSIM_E_CUDA;
-            if (pg >= 0) cudaEventRecord(h->prof[pg][0], stream);
+            if (pg >= 0) prof_record(h->prof[pg][0]);
             if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, lanes, block, grid, g.small, ia, stream) !=
                 cudaSuccess)
                 return SPINSIM_E_CUDA;
-            if (pg >= 0) cudaEventRecord(h->prof[pg][1], stream);
+            if (pg >= 0) prof_record(h->prof[pg][1]);
             kernels += 1;
             ChainArgs ca;
             ca.sims = ia.sims;
@@ -579,7 +590,7 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             chain_args_set(ca, g.chain, base + g.chain_off);
             int chain_k = 0;
             if (launch_chain(g.spin_x2, ca, h->n_sm, stream, &chain_k) != cudaSuccess) return SPINSIM_E_CUDA;
-            if (pg >= 0) cudaEventRecord(h->prof[pg][2], stream);
+            if (pg >= 0) prof_record(h->prof[pg][2]);
             kernels += chain_k;
             h->last.lanes_per_sample = lanes;
             h->last.threads_per_block = block;
@@ -625,6 +636,7 @@ void drop_graph(spinsim_s* h)
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     h->graph_exec = nullptr;
     h->graph_sig.clear();
+    h->graph_prof_groups = 0;
 }
 
 }  // namespace
@@ -693,7 +705,8 @@ int spinsim_create(const spinsim_config* cfg, spinsim_handle* out)
     if (cudaStreamCreateWithFlags(&h->work, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_pinned, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->ev_pinned, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming) != cudaSuccess) {
         spinsim_destroy(h);
         return SPINSIM_E_CUDA;
     }
@@ -725,6 +738,7 @@ void spinsim_destroy(spinsim_handle h)
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ev_pinned) cudaEventDestroy(h->ev_pinned);
+    if (h->ev_done) cudaEventDestroy(h->ev_done);
     for (auto& row : h->prof)
         for (auto& e : row)
             if (e) cudaEventDestroy(e);
@@ -800,39 +814,58 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
     int kernels = 0;
     int st = SPINSIM_OK;
     if (h->cfg.use_graphs && !capturing) {
-        // Run on the internal stream, joined to the caller's stream by events.
+        // A new batch shape runs eagerly on the internal stream (joined to the
+        // caller's stream by events) and is captured there as a graph; later
+        // calls of the same shape replay the graph on the caller's stream.
         std::vector<uint64_t> sig = batch_signature(reqs, res, n, checked);
-        if (cudaEventRecord(h->ev_in, stream) != cudaSuccess || cudaStreamWaitEvent(h->work, h->ev_in, 0) != cudaSuccess)
-            return SPINSIM_E_CUDA;
         Plan plan;
         build_plan(reqs, res, n, checked, false, plan);
         if (h->graph_exec && sig == h->graph_sig) {
-            // same shape: refresh the pinned parameter table and replay
+            // same shape: refresh the pinned parameter table and replay on the
+            // caller's stream (after the handle's previous replay)
             st = refresh_table(h, reqs, res, checked, plan, static_cast<char*>(h->arena.buf.p), h->pinned,
                                h->ev_pinned, false);
             if (st != SPINSIM_OK) return st;
-            if (cudaGraphLaunch(h->graph_exec, h->work) != cudaSuccess) return SPINSIM_E_CUDA;
-            cudaEventRecord(h->ev_pinned, h->work);
+            if (h->done_pending && cudaStreamWaitEvent(stream, h->ev_done, 0) != cudaSuccess) return SPINSIM_E_CUDA;
+            if (cudaGraphLaunch(h->graph_exec, stream) != cudaSuccess) return SPINSIM_E_CUDA;
+            if (cudaEventRecord(h->ev_pinned, stream) != cudaSuccess || cudaEventRecord(h->ev_done, stream) != cudaSuccess)
+                return SPINSIM_E_CUDA;
+            h->done_pending = true;
             h->last = h->graph_info;
             h->last.graph_replayed = 1;
+            h->last.integrate_ms = -1.0;
+            h->last.chain_ms = -1.0;
+            h->prof_groups = h->graph_prof_groups;   // the replay recorded these events
             kernels = h->graph_kernels;
         } else {
             drop_graph(h);
+            // on the internal stream, after the caller's earlier work and the
+            // handle's last replay
+            if (cudaEventRecord(h->ev_in, stream) != cudaSuccess || cudaStreamWaitEvent(h->work, h->ev_in, 0) != cudaSuccess)
+                return SPINSIM_E_CUDA;
+            if (h->done_pending && cudaStreamWaitEvent(h->work, h->ev_done, 0) != cudaSuccess) return SPINSIM_E_CUDA;
             // first run eagerly: sizes scratch and tunes the launch shape
             st = run_batch(h, reqs, res, checked, plan, h->work, h->arena, h->pinned, h->ev_pinned, false, &kernels);
             if (st != SPINSIM_OK) return st;
             if (cudaStreamSynchronize(h->work) != cudaSuccess) return SPINSIM_E_CUDA;
             // then capture the same batch for later replays
+            // (the eager run's profiling events keep their timestamps: recording
+            // them as graph nodes during the capture does not touch them)
             cudaGraph_t graph = nullptr;
+            const int eager_prof = h->prof_groups;
+            const spinsim_launch_info eager_info = h->last;   // the capture must not count its copies twice
+            h->prof_groups = 0;
             if (cudaStreamBeginCapture(h->work, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
                 int k2 = 0;
-                int st2 = run_batch(h, reqs, res, checked, plan, h->work, h->arena, h->pinned, nullptr, true, &k2);
+                int st2 = run_batch(h, reqs, res, checked, plan, h->work, h->arena, h->pinned, nullptr, true, &k2,
+                                    true);
                 cudaError_t ec = cudaStreamEndCapture(h->work, &graph);
                 if (st2 == SPINSIM_OK && ec == cudaSuccess && graph) {
                     if (cudaGraphInstantiate(&h->graph_exec, graph, 0) == cudaSuccess) {
                         h->graph_sig = sig;
                         h->graph_kernels = k2;
-                        h->graph_info = h->last;
+                        h->graph_prof_groups = h->prof_groups;
+                        h->graph_info = eager_info;
                     } else {
                         h->graph_exec = nullptr;
                     }
@@ -842,10 +875,14 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
             } else {
                 cudaGetLastError();
             }
+            h->prof_groups = eager_prof;
+            h->last = eager_info;
             cudaEventRecord(h->ev_pinned, h->work);
+            if (cudaEventRecord(h->ev_out, h->work) != cudaSuccess || cudaStreamWaitEvent(stream, h->ev_out, 0) != cudaSuccess ||
+                cudaEventRecord(h->ev_done, h->work) != cudaSuccess)
+                return SPINSIM_E_CUDA;
+            h->done_pending = true;
         }
-        if (cudaEventRecord(h->ev_out, h->work) != cudaSuccess || cudaStreamWaitEvent(stream, h->ev_out, 0) != cudaSuccess)
-            return SPINSIM_E_CUDA;
     } else {
         Plan plan;
         build_plan(reqs, res, n, checked, capturing, plan);
