@@ -134,7 +134,7 @@ struct Plan {
 
 struct TuneKey {
     int spin, precision, method, tau, small;
-    int64_t size;   // samples (small batches) or their power-of-two bucket (large ones)
+    int64_t size;   // power-of-two bucket of the batch's samples
     bool operator<(const TuneKey& o) const
     {
         return std::tie(spin, precision, method, tau, small, size) <
@@ -142,12 +142,14 @@ struct TuneKey {
     }
 };
 struct TuneVal {
-    int lanes, block, blocks_per_sm;
+    int lanes, block;
 };
 
-// Batches of at most this many CF4 steps are tuned on their full size: their
+// Batches of at most this many CF4 steps are timed on their full size (their
 // time depends on how the last wave of tiles fills the GPU, which a prefix
-// would not show.  Larger batches are tuned on a prefix of a few waves.
+// would not show); larger batches on a prefix of a few waves.  The choice is
+// cached per power-of-two size bucket, so a stream of batches of varying size
+// (serving) tunes once per bucket.
 constexpr double kFullTrialSteps = 4e8;
 
 std::mutex g_tune_mu;
@@ -398,10 +400,12 @@ int size_bucket(int64_t samples)
     return b;
 }
 
-// Choose (lanes per sample, threads per block, resident blocks per SM) for
-// the integrate kernel.  Results never depend on this choice; only the time
-// does.  Explicit configuration values are kept; the rest are tuned by
-// timing trial launches, once per (device, key), and cached.
+// Choose (lanes per sample, threads per block) for the integrate kernel and
+// its resident blocks per SM.  Results never depend on this choice; only the
+// time does.  Explicit configuration values are kept; lanes and block size are
+// tuned by timing trial launches, once per (device, key), and cached.  The
+// resident blocks per SM are the explicit value or the most the kernel allows
+// (fewer never paid on GB300: the tail they save costs more in issue rate).
 int choose_shape(spinsim_s* h, int spin, bool small, double steps, IntegrateArgs a, cudaStream_t stream,
                  bool capturing, int& lanes, int& block, int& grid)
 {
@@ -411,9 +415,8 @@ int choose_shape(spinsim_s* h, int spin, bool small, double steps, IntegrateArgs
     block = h->cfg.threads_per_block;
     int bps = h->cfg.blocks_per_sm;
     const bool full_trial = steps <= kFullTrialSteps;
-    if (lanes == 0 || block == 0 || bps == 0) {
-        TuneKey key{spin, precision, method, h->tau, (int)small,
-                    full_trial ? a.total_samples : -(int64_t)size_bucket(a.total_samples)};
+    if (lanes == 0 || block == 0) {
+        TuneKey key{spin, precision, method, h->tau, (int)small, (int64_t)size_bucket(a.total_samples)};
         bool found = false;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -421,14 +424,13 @@ int choose_shape(spinsim_s* h, int spin, bool small, double steps, IntegrateArgs
             if (it != g_tune_cache.end()) {
                 if (lanes == 0) lanes = it->second.lanes;
                 if (block == 0) block = it->second.block;
-                if (bps == 0) bps = it->second.blocks_per_sm;
                 found = true;
             }
         }
         if (!found) {
             const int lane_opts[3] = {1, 2, 4};
             const int block_opts[3] = {64, 128, 256};
-            int best_l = lanes ? lanes : 2, best_b = block ? block : 128, best_p = bps;
+            int best_l = lanes ? lanes : 2, best_b = block ? block : 128;
             if (!capturing) {
                 float best = 1e30f;
                 cudaEvent_t e0, e1;
@@ -441,54 +443,46 @@ int choose_shape(spinsim_s* h, int spin, bool small, double steps, IntegrateArgs
                         if (block && bi > 0) break;
                         int per_sm = 0;
                         if (occupancy(h, spin, L, B, small, false, &per_sm) != SPINSIM_OK || per_sm < 1) continue;
-                        // resident blocks per SM to try: the explicit value, else
-                        // the most the kernel allows and (full-size trials only,
-                        // where the last wave matters) up to two fewer
-                        const int p_hi = bps ? std::min(bps, per_sm) : per_sm;
-                        const int p_lo = bps ? p_hi : (full_trial ? std::max(1, per_sm - 2) : per_sm);
-                        for (int P = p_hi; P >= p_lo; P--) {
-                            IntegrateArgs t = a;
-                            const int spb = B / L;
-                            if (!full_trial) {
-                                // a prefix of at most 4 full waves of this shape
-                                const int64_t wave = (int64_t)h->n_sm * P * spb;
-                                t.total_samples = std::min<int64_t>(a.total_samples, 4 * wave);
+                        const int P = bps ? std::min(bps, per_sm) : per_sm;
+                        IntegrateArgs t = a;
+                        const int spb = B / L;
+                        if (!full_trial) {
+                            // a prefix of at most 4 full waves of this shape
+                            const int64_t wave = (int64_t)h->n_sm * P * spb;
+                            t.total_samples = std::min<int64_t>(a.total_samples, 4 * wave);
+                        }
+                        t.n_tiles = (t.total_samples + spb - 1) / spb;
+                        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(t.n_tiles, (int64_t)h->n_sm * P));
+                        float ms_best = 1e30f;
+                        for (int rep = 0; rep < 2; rep++) {
+                            cudaMemsetAsync(a.tile_counter, 0, sizeof(unsigned long long), stream);
+                            cudaEventRecord(e0, stream);
+                            launch_integrate(spin, precision, method, L, B, g, small, t, stream);
+                            cudaEventRecord(e1, stream);
+                            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                                cudaEventDestroy(e0);
+                                cudaEventDestroy(e1);
+                                return SPINSIM_E_CUDA;
                             }
-                            t.n_tiles = (t.total_samples + spb - 1) / spb;
-                            const int g = (int)std::max<int64_t>(1, std::min<int64_t>(t.n_tiles, (int64_t)h->n_sm * P));
-                            float ms_best = 1e30f;
-                            for (int rep = 0; rep < 2; rep++) {
-                                cudaMemsetAsync(a.tile_counter, 0, sizeof(unsigned long long), stream);
-                                cudaEventRecord(e0, stream);
-                                launch_integrate(spin, precision, method, L, B, g, small, t, stream);
-                                cudaEventRecord(e1, stream);
-                                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                                    cudaEventDestroy(e0);
-                                    cudaEventDestroy(e1);
-                                    return SPINSIM_E_CUDA;
-                                }
-                                float ms = 0.f;
-                                cudaEventElapsedTime(&ms, e0, e1);
-                                ms_best = std::min(ms_best, ms);
-                            }
-                            const float per = ms_best / (float)std::max<int64_t>(1, t.total_samples);
-                            if (per < best) {
-                                best = per;
-                                best_l = L;
-                                best_b = B;
-                                best_p = P;
-                            }
+                            float ms = 0.f;
+                            cudaEventElapsedTime(&ms, e0, e1);
+                            ms_best = std::min(ms_best, ms);
+                        }
+                        const float per = ms_best / (float)std::max<int64_t>(1, t.total_samples);
+                        if (per < best) {
+                            best = per;
+                            best_l = L;
+                            best_b = B;
                         }
                     }
                 }
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
                 std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tune_cache[{h->device, key}] = TuneVal{best_l, best_b, best_p};
+                g_tune_cache[{h->device, key}] = TuneVal{best_l, best_b};
             }
             lanes = best_l;
             block = best_b;
-            bps = best_p;
         }
     }
     int per_sm = 0;
