@@ -198,6 +198,22 @@ def test_edge_cases_in_one_batch(oracle_mod):
         assert_parity(view, ref, 1e-10, f"edge case {i}")
 
 
+def test_chain_tree_heights_in_one_batch(oracle_mod):
+    """One FP64 batch whose chain trees have 0, 1, 2 and 3 levels above the lane
+    runs (K = 1 ... 300,000 at one step per sample), spin-one and spin-half:
+    the level-0 apply, the fused top, and the down-sweeps at levels 1 and 2 all
+    run, for simulations of different heights side by side.  Every sample of
+    every simulation against the oracle."""
+    base = W.field(bias_hz=120e3, drive_x_hz=3e3, drive_hz=120.4e3, quad_hz=250.0, pulses=[(60.0, 0.1, 0.03)])
+    Ks = [1, 128, 129, 4097, 140000, 300000]
+    reqs = [W.request(2, base, 0.0, K * 1e-6, 1e-6, 1e-6) for K in Ks]
+    reqs += [W.request(1, base, 1e-4, 1e-4 + K * 1e-6, 1e-6, 1e-6) for K in (4097, 300000)]
+    outs, _ = gpu_run(reqs, precision=S.PREC_FP64)
+    for req, out in zip(reqs, outs):
+        ref = oracle_run(oracle_mod, req)
+        assert_parity(out, ref, TOL[S.PREC_FP64], f"spin_x2 {req['spin_x2']} K {out['K']}")
+
+
 def test_capacity_error_and_spin_only_outputs(oracle_mod):
     req = W.spin_half_rabi(t_end=1e-4)
     with S.Simulator(precision=S.PREC_FP64) as sim:
