@@ -41,7 +41,7 @@ class _Field(ctypes.Structure):
         ("drive_phase", ctypes.c_double),
         ("quad_hz", ctypes.c_double),
         ("n_pulses", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("pulse_sine_mask", ctypes.c_int32),
         ("pulse_amp_hz", ctypes.c_double * MAX_PULSES),
         ("pulse_centre_s", ctypes.c_double * MAX_PULSES),
         ("pulse_width_s", ctypes.c_double * MAX_PULSES),
@@ -115,10 +115,17 @@ def _field(f: dict) -> _Field:
     if len(pulses) > MAX_PULSES:
         raise ValueError("at most 4 pulses")
     s.n_pulses = len(pulses)
-    for i, (amp, centre, width) in enumerate(pulses):
+    s.pulse_sine_mask = 0
+    for i, p in enumerate(pulses):
+        amp, centre, width = p[:3]
+        kind = p[3] if len(p) > 3 else "gauss"
+        if kind not in ("gauss", "sine"):
+            raise ValueError(f"unknown pulse kind {kind!r}")
         s.pulse_amp_hz[i] = amp
         s.pulse_centre_s[i] = centre
         s.pulse_width_s[i] = width
+        if kind == "sine":
+            s.pulse_sine_mask |= 1 << i
     return s
 
 

@@ -58,7 +58,9 @@ typedef double complex cplx;
 /* Field model: a fixed parameterised family of field functions w_j(t)       */
 /* (Sec. 1.2.1 and Sec. 1.2.7 -- the paper's user-supplied field functions,  */
 /* here a bias, a sinusoidal drive of chosen polarisation, a quadratic shift */
-/* and up to four Gaussian pulses on the z field).                            */
+/* and up to four pulses on the z field, each a Gaussian or a single cycle   */
+/* of a sine wave -- the "sinp" signal pulse of the paper's benchmark field, */
+/* Eq. neural_pulse, Sec. 1.3.1).                                            */
 /* ------------------------------------------------------------------------- */
 #define OR_MAX_PULSES 4
 
@@ -69,11 +71,14 @@ typedef struct {
     double drive_hz;     /* drive frequency                                         */
     double drive_phase;  /* drive phase at t = 0, radians                           */
     double quad_hz;      /* w_q = 2 pi quad_hz (spin-one quadrupole term)           */
-    int32_t n_pulses;    /* number of Gaussian z pulses used, 0..4                  */
-    int32_t pad_;
-    double pulse_amp_hz[OR_MAX_PULSES];    /* w_z += 2 pi A exp(-(t-c)^2 / (2 w^2)) */
+    int32_t n_pulses;    /* number of z pulses used, 0..4                           */
+    int32_t pulse_sine_mask; /* bit p set: pulse p is a single sine cycle           */
+    /* Gaussian pulse p:   w_z += 2 pi A exp(-(t-c)^2 / (2 w^2)), w the standard deviation;
+     * sine-cycle pulse p: w_z += 2 pi A sin(2 pi (t-c)/w) for c <= t < c + w, else 0
+     * (c = pulse_centre_s[p] is the start t_p of the cycle, w its period).         */
+    double pulse_amp_hz[OR_MAX_PULSES];
     double pulse_centre_s[OR_MAX_PULSES];
-    double pulse_width_s[OR_MAX_PULSES];   /* standard deviation w                  */
+    double pulse_width_s[OR_MAX_PULSES];
 } oracle_field;
 
 /* Field functions (w_x, w_y, w_z, w_q) at time t, in rad/s. */
@@ -84,7 +89,12 @@ void oracle_field_sample(const oracle_field* f, double t, double w[4])
     for (int p = 0; p < f->n_pulses && p < OR_MAX_PULSES; p++) {
         double d = t - f->pulse_centre_s[p];
         double wd = f->pulse_width_s[p];
-        bz += f->pulse_amp_hz[p] * exp(-(d * d) / (2.0 * wd * wd));
+        if ((f->pulse_sine_mask >> p) & 1) {
+            double cyc = d / wd;   /* cycles since the start of the pulse */
+            if (cyc >= 0.0 && cyc < 1.0) bz += f->pulse_amp_hz[p] * sin(2.0 * OR_PI * cyc);
+        } else {
+            bz += f->pulse_amp_hz[p] * exp(-(d * d) / (2.0 * wd * wd));
+        }
     }
     w[0] = 2.0 * OR_PI * f->drive_x_hz * cos(phase);
     w[1] = 2.0 * OR_PI * f->drive_y_hz * sin(phase);

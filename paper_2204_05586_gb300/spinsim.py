@@ -188,7 +188,10 @@ def make_request(req: dict) -> spinsim_request:
         setattr(r.field, k, float(f.get(k, 0.0)))
     pulses = list(f.get("pulses", ()))
     r.field.n_pulses = len(pulses)
-    for i, (a, c, w) in enumerate(pulses):
+    for i, p in enumerate(pulses):
+        a, c, w = p[:3]
+        if len(p) > 3 and p[3] != "gauss":
+            raise SpinsimError(E_ARG, f"pulse kind {p[3]!r} is not supported by the CUDA path")
         r.field.pulse_amp_hz[i], r.field.pulse_centre_s[i], r.field.pulse_width_s[i] = a, c, w
     r.t_start, r.t_end, r.dt, r.dt_out = req["t_start"], req["t_end"], req["dt"], req["dt_out"]
     psi = np.asarray(req["psi0"], dtype=np.complex128)

@@ -6,11 +6,14 @@ the oracle's callers import.  A request is a plain ``dict``:
 
     spin_x2        1 = spin-half, 2 = spin-one
     field          dict(bias_hz, drive_x_hz, drive_y_hz, drive_hz, drive_phase,
-                        quad_hz, pulses=[(amp_hz, centre_s, width_s), ...])
+                        quad_hz, pulses=[(amp_hz, centre_s, width_s[, kind]), ...])
                    w_x = 2 pi drive_x_hz cos(2 pi drive_hz t + drive_phase)
                    w_y = 2 pi drive_y_hz sin(2 pi drive_hz t + drive_phase)
-                   w_z = 2 pi (bias_hz + sum_p amp_p exp(-(t-c_p)^2 / (2 w_p^2)))
+                   w_z = 2 pi (bias_hz + sum_p amp_p shape_p(t))
                    w_q = 2 pi quad_hz
+                   shape_p: kind "gauss" (default) exp(-(t-c_p)^2 / (2 w_p^2));
+                   kind "sine" a single cycle sin(2 pi (t-c_p)/w_p) for
+                   c_p <= t < c_p + w_p, else 0 (the paper's sinp pulse)
     t_start, t_end, dt, dt_out   seconds
     psi0           complex initial state, basis m = +j ... -j
 
@@ -33,9 +36,14 @@ UP_ONE = np.array([1.0, 0.0, 0.0], dtype=np.complex128)
 
 def field(bias_hz=0.0, drive_x_hz=0.0, drive_y_hz=0.0, drive_hz=0.0, drive_phase=0.0, quad_hz=0.0,
           pulses=()):
+    def pulse(p):
+        kind = p[3] if len(p) > 3 else "gauss"
+        if kind not in ("gauss", "sine"):
+            raise ValueError(f"unknown pulse kind {kind!r}")
+        return (float(p[0]), float(p[1]), float(p[2]), kind)
     return dict(bias_hz=float(bias_hz), drive_x_hz=float(drive_x_hz), drive_y_hz=float(drive_y_hz),
                 drive_hz=float(drive_hz), drive_phase=float(drive_phase), quad_hz=float(quad_hz),
-                pulses=[tuple(map(float, p)) for p in pulses])
+                pulses=[pulse(p) for p in pulses])
 
 
 def request(spin_x2, fld, t_start, t_end, dt, dt_out, psi0=None):

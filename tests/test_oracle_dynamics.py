@@ -136,6 +136,50 @@ def test_gaussian_pulse_phase_closed_form(oracle_mod, frame):
     assert np.abs(out["states"] - ref).max() < 1e-11
 
 
+# ------------------------------- P4': diagonal H with a single-cycle sine pulse
+def sine_cycle_integral(ts, A, tp, T):
+    """int_0^t 2 pi A sinp(2 pi (t' - tp) / T) dt' with sinp one cycle of a sine:
+    A T (1 - cos(2 pi (t - tp) / T)) inside the cycle, 0 before it and after it."""
+    x = np.clip((ts - tp) / T, 0.0, 1.0)
+    return A * T * (1.0 - np.cos(TWO_PI * x))
+
+
+@pytest.mark.parametrize("frame", [False, True])
+def test_sine_cycle_pulse_phase_closed_form(oracle_mod, frame):
+    """The paper's signal pulse (Eq. neural_pulse: Omega_p sinp(Omega (t - t_p)) J_z,
+    sinp a single cycle of a sine wave).  With no transverse field
+    psi_m(t) = psi_m(0) exp(-i int (m w_z + Q_mm w_q)) and the cycle integrates in
+    closed form; the pulse starts and ends on step boundaries, where CF4's
+    two-node quadrature of the phase is fourth order."""
+    B, A, tp, T, q = 2e3, 700.0, 0.8e-3, 1.0e-3, 250.0
+    f = W.field(bias_hz=B, quad_hz=q, pulses=[(A, tp, T, "sine")])
+    rng = np.random.default_rng(29)
+    psi0 = W.random_state(3, rng)
+    out = oracle_mod.simulate(2, f, 0.0, 3e-3, 1e-6, 5e-5, psi0, rotating_frame=frame)
+    ts = times(0.0, 3e-3, 5e-5)
+    iz = TWO_PI * B * ts + sine_cycle_integral(ts, A, tp, T)
+    iq = TWO_PI * q * ts
+    m = np.array([1.0, 0.0, -1.0])
+    qd = np.array([1.0, -2.0, 1.0]) / 3
+    ref = psi0[None, :] * np.exp(-1j * (m[None, :] * iz[:, None] + qd[None, :] * iq[:, None]))
+    assert np.abs(out["states"] - ref).max() < 1e-11
+    # the pulse is really there: without it the phase differs by A T (1 - cos) ~ 1.4 rad at mid-cycle
+    assert np.abs(sine_cycle_integral(ts, A, tp, T)).max() > 1.0
+
+
+def test_sine_cycle_pulse_spin_half_before_during_after(oracle_mod):
+    """Spin-half relative phase through the cycle: zero pulse contribution
+    before t_p, A T (1 - cos) during, and none after the full cycle."""
+    B, A, tp, T = 5e3, -300.0, 1.0e-3, 0.5e-3
+    f = W.field(bias_hz=B, pulses=[(A, tp, T, "sine")])
+    psi0 = np.array([1.0, 1.0], dtype=np.complex128) / np.sqrt(2)
+    out = oracle_mod.simulate(1, f, 0.0, 2.5e-3, 1e-7, 1e-5, psi0)
+    ts = times(0.0, 2.5e-3, 1e-5)
+    rel = np.angle(out["states"][:, 1] / out["states"][:, 0])     # = int w_z (spin-half: m = -+1/2)
+    ref = np.angle(np.exp(1j * (TWO_PI * B * ts + sine_cycle_integral(ts, A, tp, T))))
+    assert np.abs(np.angle(np.exp(1j * (rel - ref)))).max() < 1e-10
+
+
 # ------------------------------------ brute force: independent ODE solver
 def ivp_reference(spin_x2, f, psi0, ts, oracle_mod):
     n = len(psi0)
@@ -153,10 +197,11 @@ def ivp_reference(spin_x2, f, psi0, ts, oracle_mod):
 @pytest.mark.parametrize("spin_x2", [1, 2])
 @pytest.mark.parametrize("frame", [False, True])
 def test_against_adaptive_ode_solver(oracle_mod, spin_x2, frame):
-    """Sensing-like field (bias, linear drive, quadratic shift, Gaussian pulse)
-    vs scipy DOP853 at tight tolerance: the paper's own validation route."""
+    """Sensing-like field (bias, linear drive, quadratic shift, a Gaussian pulse
+    and a single-cycle sine pulse) vs scipy DOP853 at tight tolerance: the
+    paper's own validation route."""
     f = W.field(bias_hz=20e3, drive_x_hz=2e3, drive_hz=20.3e3, quad_hz=300.0 if spin_x2 == 2 else 0.0,
-                pulses=[(400.0, 0.3e-3, 0.1e-3)])
+                pulses=[(400.0, 0.3e-3, 0.1e-3), (250.0, 0.1e-3, 0.2e-3, "sine")])
     rng = np.random.default_rng(17)
     psi0 = W.random_state(2 if spin_x2 == 1 else 3, rng)
     out = oracle_mod.simulate(spin_x2, f, 0.0, 6e-4, 2e-7, 2e-5, psi0, rotating_frame=frame)

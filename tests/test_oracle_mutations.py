@@ -27,6 +27,11 @@ MUTATIONS = {
     "frame_exit_sign": ("cplx ph = cexp(-I * m * w_r * p->dt_out);", "cplx ph = cexp(I * m * w_r * p->dt_out);"),
     "half_sigma_y_sign": ("cplx u01 = -I * s * (vx - I * vy);", "cplx u01 = -I * s * (vx + I * vy);"),
     "gaussian_width": ("exp(-(d * d) / (2.0 * wd * wd))", "exp(-(d * d) / (wd * wd))"),
+    "sine_pulse_cosine": ("bz += f->pulse_amp_hz[p] * sin(2.0 * OR_PI * cyc);",
+                          "bz += f->pulse_amp_hz[p] * cos(2.0 * OR_PI * cyc);"),
+    "sine_pulse_half_period": ("bz += f->pulse_amp_hz[p] * sin(2.0 * OR_PI * cyc);",
+                               "bz += f->pulse_amp_hz[p] * sin(OR_PI * cyc);"),
+    "sine_pulse_window": ("if (cyc >= 0.0 && cyc < 1.0)", "if (cyc >= 0.0 && cyc < 0.5)"),
     "drive_y_cos": ("w[1] = 2.0 * OR_PI * f->drive_y_hz * sin(phase);", "w[1] = 2.0 * OR_PI * f->drive_y_hz * cos(phase);"),
     "jy_sign": ("J[1][0][1] = -I * r; J[1][1][0] = I * r;", "J[1][0][1] = I * r; J[1][1][0] = -I * r;"),
     "chain_transposed": ("s += U[i][j] * psi[j];", "s += U[j][i] * psi[j];"),
