@@ -8,7 +8,7 @@ delta_t = 10 ns and Delta_t = 1 us (1e5 samples x 100 CF4 steps) -- run in
 FP32-bulk precision with the FP64 chain, inputs resident on the device.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sensing|sweep|serve] [--precision fp32|fp64]
+                    [--workload sensing|sweep|serve|neural] [--precision fp32|fp64]
 
 Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs its own
 copy of the workload (weak scaling, no data-path collective); the timing is
@@ -163,6 +163,11 @@ def run_ours(args, world, rank, local):
         reqs = [W.spin_one_sensing()]
         workload = ("spin-one sensing: bias 700 kHz, drive 2x1 kHz at 700 kHz, q 400 Hz, Gaussian z pulse "
                     "50 Hz / 1 ms at 50 ms; 100 ms, dt 10 ns, dt_out 1 us (1e5 samples x 100 CF4 steps)")
+    elif args.workload == "neural":
+        reqs = [W.neural_pulse()]
+        workload = ("spin-one, the paper's benchmark field (Eq. neural_pulse): bias 700 kHz, drive 2x1 kHz at "
+                    "700 kHz, 70 Hz single sine cycle of 1 ms on J_z at 50 ms; 100 ms, dt 100 ns, dt_out 1 us "
+                    "(1e5 samples x 10 CF4 steps)")
     elif args.workload == "sweep":
         reqs = W.sweep(4096, seed=W.SEED + rank)
         workload = ("batched spin-one sweep: 4096 simulations, bias U(600,800) kHz, Rabi U(0.5,2) kHz, detuning "
@@ -256,7 +261,7 @@ def run_ours(args, world, rank, local):
     if clk:
         line["clocks"] = clk
     # ---- rank 0: accuracy vs the FP64 oracle, oracle CPU baseline, FP64-plain kernel
-    if rank == 0 and args.workload == "sensing" and not args.no_cpu_baseline:
+    if rank == 0 and args.workload in ("sensing", "neural") and not args.no_cpu_baseline:
         from oracle import oracle as O   # the CPU baseline leg: the oracle as it stands
         O.build()
         r = reqs[0]
@@ -396,7 +401,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("sensing", "sweep", "serve"), default="sensing")
+    ap.add_argument("--workload", choices=("sensing", "sweep", "serve", "neural"), default="sensing")
     ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
     ap.add_argument("--tau", type=int, default=-1)
     ap.add_argument("--serve-requests", type=int, default=20000)

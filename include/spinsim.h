@@ -106,9 +106,13 @@ typedef struct {
 /* The fixed parameterised field family (Hz, seconds, radians):
  *   w_x(t) = 2 pi drive_x_hz cos(2 pi drive_hz t + drive_phase)
  *   w_y(t) = 2 pi drive_y_hz sin(2 pi drive_hz t + drive_phase)
- *   w_z(t) = 2 pi (bias_hz + sum_p pulse_amp_hz[p] exp(-(t - pulse_centre_s[p])^2
- *                                                       / (2 pulse_width_s[p]^2)))
+ *   w_z(t) = 2 pi (bias_hz + sum_p pulse_amp_hz[p] shape_p(t))
  *   w_q(t) = 2 pi quad_hz                       (spin-one only; ignored for spin-half)
+ * with, for pulse p (c = pulse_centre_s[p], w = pulse_width_s[p] > 0):
+ *   Gaussian (bit p of pulse_sine_mask clear): shape_p(t) = exp(-(t - c)^2 / (2 w^2));
+ *   single sine cycle (bit p set; the "sinp" signal pulse of the paper's benchmark
+ *   field, Eq. neural_pulse): shape_p(t) = sin(2 pi (t - c) / w) for c <= t < c + w,
+ *   else 0 (c is the start of the cycle, w its period).
  * A linearly polarised drive "2 R cos(2 pi f t)" is drive_x_hz = 2R, drive_y_hz = 0;
  * a circularly polarised one has drive_x_hz = drive_y_hz.  The detuning of the
  * drive is drive_hz - bias_hz. */
@@ -120,7 +124,7 @@ typedef struct {
     double drive_phase;
     double quad_hz;
     int32_t n_pulses;             /* 0..SPINSIM_MAX_PULSES                                   */
-    int32_t reserved;
+    int32_t pulse_sine_mask;      /* bit p: pulse p is a single sine cycle, else a Gaussian  */
     double pulse_amp_hz[SPINSIM_MAX_PULSES];
     double pulse_centre_s[SPINSIM_MAX_PULSES];
     double pulse_width_s[SPINSIM_MAX_PULSES];   /* standard deviation, > 0 when used       */

@@ -194,6 +194,7 @@ struct SampleCtx {
     R dt, c1, c2;
     R amp[kMaxPulses], u0[kMaxPulses], invw[kMaxPulses], ghat[kMaxPulses];
     int np;
+    int ng;                         // pulses [0, ng) Gaussian, [ng, np) single sine cycles
     int tau;
     bool counter_on;
 };
@@ -228,6 +229,29 @@ SPINSIM_HD double drive_phase_at(const DevSim& s, int64_t k)
     cyc -= floor(cyc);
     double beta = kTwoPi * cyc + s.drive_phase;
     return beta - kTwoPi * rint(beta * (1.0 / kTwoPi));
+}
+
+// Shape of z pulse p at u = (t - c_p) / w_p: a Gaussian exp(-u^2/2) (w_p the
+// standard deviation), or a single sine cycle sin(2 pi u) for 0 <= u < 1 and 0
+// elsewhere (w_p the period; the paper's sinp pulse, Eq. neural_pulse).
+template <typename R>
+SPINSIM_HD R pulse_shape(bool sine, R u)
+{
+    if (!sine) return exp(R(-0.5) * u * u);
+    if (!(u >= R(0) && u < R(1))) return R(0);
+#ifdef __CUDA_ARCH__
+    return sinpi(R(2) * u);
+#else
+    return sin(R(kTwoPi) * u);
+#endif
+}
+
+// The sine-cycle shape out of line: only requests with such pulses reach it,
+// and the step loop of the others does not carry its code.
+template <typename R>
+SPINSIM_COLD R sine_cycle_cold(R u)
+{
+    return pulse_shape<R>(true, u);
 }
 
 // Bulk context of interval k (every lane).  e^{i beta} comes from the bulk
@@ -269,6 +293,7 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
         c.c2 = (R)s.c2;
     }
     c.np = s.n_pulses;
+    c.ng = s.n_gauss;
     c.tau = s.tau;
     c.inv_n = ldexp(R(1), -s.tau);
     c.q1 = R(3) * ldexp(c.qd3, s.tau);
@@ -288,7 +313,7 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
             c.u0[p] = (R)((t_prev - s.centre[p]) * s.inv_w[p]);
             if (s.frame) {
                 R um = (R)((t_prev + 0.5 * s.dt_out - s.centre[p]) * s.inv_w[p]);
-                R g = exp(R(-0.5) * um * um);
+                R g = pulse_shape<R>(p >= s.n_gauss, um);
                 c.ghat[p] = g;
                 gsum = fma((double)c.amp[p], (double)g, gsum);
             }
@@ -433,9 +458,22 @@ SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
     R z = R(0);
 #pragma unroll
     for (int p = 0; p < kMaxPulses; p++) {
-        if (p < c.np) {
+        if (p < c.ng) {
             R u = fma(tau, c.invw[p], c.u0[p]);
             z = fma(c.amp[p], exp(R(-0.5) * u * u) - c.ghat[p], z);
+        }
+    }
+    // single sine cycles: the general variant only (the small-angle variant is
+    // chosen only for requests without them, and its step loop stays as lean)
+    if constexpr (!SMALL) {
+        if (c.np > c.ng) {
+#pragma unroll
+            for (int p = 0; p < kMaxPulses; p++) {
+                if (p >= c.ng && p < c.np) {
+                    R u = fma(tau, c.invw[p], c.u0[p]);
+                    z = fma(c.amp[p], sine_cycle_cold(u) - c.ghat[p], z);
+                }
+            }
         }
     }
     f.z = z;

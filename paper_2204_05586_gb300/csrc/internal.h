@@ -86,12 +86,12 @@ struct DevSim {
     int32_t tay_ok;              // 1 when the tables were built (L <= 65536)
     int32_t normalize_out;       // FP32-bulk: write psi_k renormalised in FP64
     int32_t tau;                 // Lie-Trotter squarings of this simulation (n = 2^tau)
-    int32_t pad2;
+    int32_t n_gauss;             // pulses [0, n_gauss) are Gaussians, [n_gauss, n_pulses) sine cycles
     double exit_re, exit_im;     // e^{-i 2 pi B dt_out} (frame) or 1
     double exit_half_re, exit_half_im;  // e^{-i pi B dt_out} (frame) or 1
     double amp[kMaxPulses];      // 2 pi A_p, rad/s
-    double centre[kMaxPulses];
-    double inv_w[kMaxPulses];
+    double centre[kMaxPulses];   // Gaussian centre, or start of the sine cycle
+    double inv_w[kMaxPulses];    // 1 / (standard deviation or period)
     double psi0[6];
     int32_t n_pulses, frame, spin_x2, counter_on;
     // The same constants rounded to FP32 once, on the host, for the FP32-bulk
@@ -256,8 +256,9 @@ constexpr double kTinyAngleBound = 0.015625;
 // samples, L steps per sample); the caller sets the output pointers and the
 // sample/chunk/group offsets.
 void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L, DevSim& d);
-// small_angle_request: true when the request runs in FP32-bulk and every
-// argument of the per-step sine/cosine series is bounded by kTinyAngleBound.
+// small_angle_request: true when the request runs in FP32-bulk, has no
+// single-sine-cycle pulse, and every argument of the per-step sine/cosine
+// series is bounded by kTinyAngleBound.
 bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, int64_t L);
 
 // Host-side launchers (integrate.cu, chain.cu).  precision: 0 FP64, 1 FP32-bulk;

@@ -48,9 +48,12 @@ double pulse_weight(const spinsim_field& f)
 //   |z| <= (|a| + |b|) dt (sum_p |amp_p| (+ 2 pi |B| in the lab)), |q| = |a + b| dt 2 pi |q_hz|;
 //   Phi/2 <= (|a| + |b|) dt (|Om+| + |Om-|) / 2.
 // These bounds hold for every number of squarings (each divides the angles by 2^tau).
+// The small-angle variant evaluates Gaussian pulses only: a request with a
+// single-sine-cycle pulse takes the general variant.
 bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, int64_t L)
 {
     if (cfg.precision != SPINSIM_PREC_FP32_BULK || L < 1) return false;
+    if (r.field.n_pulses > 0 && (r.field.pulse_sine_mask & ((1 << r.field.n_pulses) - 1)) != 0) return false;
     const MethodNodes m = method_nodes(cfg.method);
     const spinsim_field& f = r.field;
     const double dt = r.dt_out / (double)L;
@@ -145,12 +148,21 @@ void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K,
             }
         for (int m = 0; m < 8; m++) { d.tay_co[m] = co[m]; d.tay_ct[m] = ct[m]; }
     }
+    // Gaussian pulses first, then the sine cycles, so the step loop handles
+    // each kind in a loop of its own
     d.n_pulses = f.n_pulses;
-    for (int p = 0; p < f.n_pulses; p++) {
-        d.amp[p] = kTwoPiH * f.pulse_amp_hz[p];
-        d.centre[p] = f.pulse_centre_s[p];
-        d.inv_w[p] = 1.0 / f.pulse_width_s[p];
-    }
+    d.n_gauss = 0;
+    int slot = 0;
+    for (int pass = 0; pass < 2; pass++)
+        for (int p = 0; p < f.n_pulses; p++) {
+            const bool sine = (f.pulse_sine_mask >> p) & 1;
+            if (sine != (pass == 1)) continue;
+            d.amp[slot] = kTwoPiH * f.pulse_amp_hz[p];
+            d.centre[slot] = f.pulse_centre_s[p];
+            d.inv_w[slot] = 1.0 / f.pulse_width_s[p];
+            slot++;
+            if (!sine) d.n_gauss++;
+        }
     for (int e = 0; e < 6; e++) d.psi0[e] = r.psi0[e];
     d.spin_x2 = r.spin_x2;
     for (int i = 0; i < 4; i++) {

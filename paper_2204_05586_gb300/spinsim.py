@@ -42,7 +42,7 @@ class spinsim_config(ctypes.Structure):
 class spinsim_field(ctypes.Structure):
     _fields_ = [("bias_hz", ctypes.c_double), ("drive_x_hz", ctypes.c_double), ("drive_y_hz", ctypes.c_double),
                 ("drive_hz", ctypes.c_double), ("drive_phase", ctypes.c_double), ("quad_hz", ctypes.c_double),
-                ("n_pulses", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_pulses", ctypes.c_int32), ("pulse_sine_mask", ctypes.c_int32),
                 ("pulse_amp_hz", ctypes.c_double * MAX_PULSES), ("pulse_centre_s", ctypes.c_double * MAX_PULSES),
                 ("pulse_width_s", ctypes.c_double * MAX_PULSES)]
 
@@ -188,11 +188,15 @@ def make_request(req: dict) -> spinsim_request:
         setattr(r.field, k, float(f.get(k, 0.0)))
     pulses = list(f.get("pulses", ()))
     r.field.n_pulses = len(pulses)
+    r.field.pulse_sine_mask = 0
     for i, p in enumerate(pulses):
         a, c, w = p[:3]
-        if len(p) > 3 and p[3] != "gauss":
-            raise SpinsimError(E_ARG, f"pulse kind {p[3]!r} is not supported by the CUDA path")
+        kind = p[3] if len(p) > 3 else "gauss"
+        if kind not in ("gauss", "sine"):
+            raise SpinsimError(E_ARG, f"unknown pulse kind {kind!r}")
         r.field.pulse_amp_hz[i], r.field.pulse_centre_s[i], r.field.pulse_width_s[i] = a, c, w
+        if kind == "sine":
+            r.field.pulse_sine_mask |= 1 << i
     r.t_start, r.t_end, r.dt, r.dt_out = req["t_start"], req["t_end"], req["dt"], req["dt_out"]
     psi = np.asarray(req["psi0"], dtype=np.complex128)
     for i, z in enumerate(psi):

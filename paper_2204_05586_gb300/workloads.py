@@ -65,6 +65,17 @@ def spin_one_sensing(t_end=0.1, dt=1e-8, dt_out=1e-6):
                             pulses=[(50.0, 50e-3, 1e-3)]), 0.0, t_end, dt, dt_out)
 
 
+def neural_pulse(t_end=0.1, t_p=0.05, dt=1e-7, dt_out=1e-6, spin_x2=2):
+    """The paper's benchmark field, Eq. neural_pulse:
+    H = w J_z + 2 W cos(w t) J_x + W_p sinp(W (t - t_p)) J_z with w = 2 pi 700 kHz,
+    W = 2 pi 1 kHz, W_p = 2 pi 70 Hz and sinp one cycle of a sine wave (1 ms), over
+    100 ms at the 100 ns integration step of the paper's speed benchmark, from
+    |m = +1> (|up> for spin-half).  The printed t_p = 233 ms lies outside the 100 ms
+    run; the pulse is placed at t_p = 50 ms so that the run contains it."""
+    return request(spin_x2, field(bias_hz=700e3, drive_x_hz=2e3, drive_hz=700e3,
+                                  pulses=[(70.0, t_p, 1e-3, "sine")]), 0.0, t_end, dt, dt_out)
+
+
 def sweep(n=4096, seed=SEED, t_min=1e-3, t_max=0.1, dt=1e-8, dt_out=1e-6, spin_x2=2):
     """Batched spin-one sweep over an array of atom clouds.
 

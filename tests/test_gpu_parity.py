@@ -214,6 +214,29 @@ def test_chain_tree_heights_in_one_batch(oracle_mod):
         assert_parity(out, ref, TOL[S.PREC_FP64], f"spin_x2 {req['spin_x2']} K {out['K']}")
 
 
+@pytest.mark.parametrize("prec", [S.PREC_FP64, S.PREC_FP32_BULK])
+def test_neural_pulse_field(oracle_mod, prec):
+    """The paper's benchmark field (Eq. neural_pulse: 700 kHz bias, 2 x 1 kHz drive,
+    a 70 Hz single sine cycle of 1 ms on J_z), the cycle inside a 3 ms run, at
+    the paper's 100 ns step: spin-one and spin-half, every sample against the
+    oracle."""
+    for spin_x2 in (2, 1):
+        req = W.neural_pulse(t_end=3e-3, t_p=1.2e-3, spin_x2=spin_x2)
+        (out,), _ = gpu_run([req], precision=prec)
+        assert_parity(out, oracle_run(oracle_mod, req), TOL[prec], f"neural pulse spin_x2 {spin_x2}")
+
+
+@pytest.mark.parametrize("frame", [True, False])
+def test_mixed_pulse_kinds_fp64(oracle_mod, frame):
+    """Gaussian and sine-cycle pulses in one field, both frames, FP64, with the
+    cycle's edges between steps."""
+    f = W.field(bias_hz=90e3, drive_x_hz=3e3, drive_y_hz=1e3, drive_hz=90.2e3, quad_hz=200.0,
+                pulses=[(150.0, 0.4e-3, 0.1e-3), (400.0, 0.13e-3, 0.37e-3, "sine"), (-90.0, 0.7e-3, 0.2e-3, "sine")])
+    req = W.request(2, f, 0.0, 1.2e-3, 4e-8, 2e-6)
+    (out,), _ = gpu_run([req], precision=S.PREC_FP64, rotating_frame=frame)
+    assert_parity(out, oracle_run(oracle_mod, req, frame=frame), TOL[S.PREC_FP64], f"mixed pulses frame {frame}")
+
+
 def test_capacity_error_and_spin_only_outputs(oracle_mod):
     req = W.spin_half_rabi(t_end=1e-4)
     with S.Simulator(precision=S.PREC_FP64) as sim:
