@@ -244,6 +244,34 @@ int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info);
 int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_request* req, spinsim_result* res,
                             void* stream);
 
+/* One long simulation split into contiguous ranges of output samples, for
+ * example one range per process (Sec. 1.2.4: the U_k are independent, so a
+ * range's operators need nothing from the others; only the ordered product
+ * across ranges is shared, in one exchange of one N x N matrix per range).
+ *
+ * spinsim_range_begin computes the sample operators of one request and their
+ * ordered product agg = U_{K-1} ... U_1 U_0 (U_0 = I): the propagator from
+ * t_start to t_start + (K-1) dt_out, FP64 complex [N][N] row-major, re/im
+ * interleaved (2 N N doubles), written to host memory agg.  It validates the
+ * request like spinsim_simulate (res->status, res->flags, res->n_samples = K;
+ * req->psi0 must be normalised but is not used), runs on `stream` and waits
+ * for it.  The operators stay in the handle's device memory.
+ *
+ * spinsim_range_finish then writes the outputs of that request (res->states,
+ * and res->spin / res->ops when not NULL, as at begin) from the entering
+ * state psi_in (N complex, re/im interleaved, normalised to 1e-10, else
+ * SPINSIM_E_NORM), asynchronously on `stream`.  res must stay valid until then.
+ *
+ * A range whose request ends at t_start + (K-1) dt_out = the next range's
+ * t_start therefore gives that range's entering state as agg applied to its
+ * own.  finish closes the range whatever its result (after SPINSIM_E_NORM the
+ * range must be begun again).  Any other call on the handle between begin and
+ * finish (simulate, submit, another begin) discards the open range; finish
+ * then returns SPINSIM_E_ARG.  Not for use during stream capture. */
+int spinsim_range_begin(spinsim_handle h, const spinsim_request* req, spinsim_result* res, double* agg,
+                        void* stream);
+int spinsim_range_finish(spinsim_handle h, const double* psi_in, void* stream);
+
 /* Static description of a status code. */
 const char* spinsim_status_string(int status);
 

@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(128) chain_up_kernel(ChainArgs a, int level)
 #pragma unroll
             for (int i = 0; i < D / 2; i++) dst[i] = src[i];
         }
-        if (level >= 1 && s.chain_top == level) {
+        if (level >= 1 && s.chain_top == level && a.mode == kChainFull) {
             // top node: the down-sweep starts here from psi_init
             if (lane < SV) V[tslot(5, 0) * SV + lane] = s.psi0[lane];
             __syncwarp();
@@ -353,9 +353,10 @@ __global__ void __launch_bounds__(128) chain_up_kernel(ChainArgs a, int level)
     }
 }
 
-// Down-sweep of level `level` >= 1 for nodes below their simulation's top.
+// Down-sweep of level `level` >= 1 for nodes below their simulation's top,
+// or (top = true) for the top nodes of this level, from psi0.
 template <int N>
-__global__ void __launch_bounds__(128) chain_down_kernel(ChainArgs a, int level)
+__global__ void __launch_bounds__(128) chain_down_kernel(ChainArgs a, int level, bool top)
 {
     constexpr int D = Tree<N>::D, SV = 2 * N;
     extern __shared__ __align__(16) double smem[];
@@ -367,9 +368,9 @@ __global__ void __launch_bounds__(128) chain_down_kernel(ChainArgs a, int level)
     for (int64_t node = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; node < a.nodes[level]; node += warps) {
         const int si = find_node_sim(off, a.n_sims, node);
         const DevSim& s = a.sims[si];
-        if (s.chain_top == level) continue;   // done by the up kernel of this level
+        if ((s.chain_top == level) != top) continue;   // the other launch's node
         const int64_t local = node - off[si];
-        if (lane < SV) V[tslot(5, 0) * SV + lane] = a.state[level][node * SV + lane];
+        if (lane < SV) V[tslot(5, 0) * SV + lane] = top ? s.psi0[lane] : a.state[level][node * SV + lane];
         __syncwarp();
         const double* L = a.left[level] + node * kLeftPerNode * D;
         tree_down<N>(V, [&](int t) { return L + t * D; }, lane);
@@ -455,13 +456,23 @@ static cudaError_t launch_chain_n(const ChainArgs& a, int n_sm, cudaStream_t str
         return (int)std::max<int64_t>(1, std::min<int64_t>((nodes + kChainWarps - 1) / kChainWarps, (int64_t)n_sm * 16));
     };
     ChainArgs args = a;
-    for (int l = 0; l < a.levels; l++) {
-        chain_up_kernel<N><<<grid(a.nodes[l]), block, up_smem, stream>>>(args, l);
-        (*kernels)++;
-    }
-    for (int l = a.levels - 2; l >= 1; l--) {
-        chain_down_kernel<N><<<grid(a.nodes[l]), block, down_smem, stream>>>(args, l);
-        (*kernels)++;
+    if (a.mode != kChainDown)
+        for (int l = 0; l < a.levels; l++) {
+            chain_up_kernel<N><<<grid(a.nodes[l]), block, up_smem, stream>>>(args, l);
+            (*kernels)++;
+        }
+    if (a.mode == kChainUp) return cudaGetLastError();
+    // (kChainDown: the top nodes of levels >= 1 start from psi0 here; in the
+    // full scan the up kernel of their level did that)
+    for (int l = a.levels - 1; l >= 1; l--) {
+        if (a.mode == kChainDown && ((a.top_levels >> l) & 1)) {
+            chain_down_kernel<N><<<grid(a.nodes[l]), block, down_smem, stream>>>(args, l, true);
+            (*kernels)++;
+        }
+        if (l <= a.levels - 2) {
+            chain_down_kernel<N><<<grid(a.nodes[l]), block, down_smem, stream>>>(args, l, false);
+            (*kernels)++;
+        }
     }
     chain_apply_kernel<N><<<grid(a.nodes[0]), block, down_smem, stream>>>(args);
     (*kernels)++;

@@ -112,10 +112,18 @@ struct IntegrateArgs {
     int64_t n_tiles;
 };
 
+// What launch_chain runs: the whole scan, only the up-sweeps (a range whose
+// entering state is not known yet: no down-sweep from a top node), or only
+// the down-sweeps and the write from each simulation's psi0 (the same range
+// once its entering state has been placed in psi0).
+enum ChainMode { kChainFull = 0, kChainUp = 1, kChainDown = 2 };
+
 struct ChainArgs {
     const DevSim* sims;
     int n_sims;
     int levels;                       // 1 + the highest top level of the batch
+    int mode;                         // ChainMode
+    int top_levels;                   // bit l: some simulation's top node is at level l
     const int64_t* level_off;         // [levels][n_sims + 1] first node of each simulation per level (device)
     int64_t nodes[kMaxLevels];        // nodes per level, all simulations
     const double* U;                  // sample operators
@@ -157,6 +165,8 @@ inline ChainLayout chain_layout(int spin_x2, const int64_t* nodes, int levels)
 inline void chain_args_set(ChainArgs& a, const ChainLayout& cl, char* base)
 {
     a.levels = cl.levels;
+    a.mode = kChainFull;
+    a.top_levels = 0;
     for (int l = 0; l < kMaxLevels; l++) {
         const bool used = l < cl.levels;
         a.nodes[l] = used ? cl.nodes[l] : 0;
@@ -166,8 +176,7 @@ inline void chain_args_set(ChainArgs& a, const ChainLayout& cl, char* base)
     }
 }
 
-// Kernels launch_chain issues for a batch whose tallest tree has `levels` levels.
-inline int chain_kernels(int levels) { return levels + (levels > 2 ? levels - 2 : 0) + 1; }
+
 
 // ------------------------------------------------- request warning bits
 constexpr double kMagnusXi = 1.0868687;   // Sec. 1.2.2: convergence radius of the Magnus series

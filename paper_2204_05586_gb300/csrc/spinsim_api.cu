@@ -111,6 +111,7 @@ struct Group {
     int64_t samples = 0;
     double steps = 0.0;            // CF4 (or sampling) steps of the group
     int levels = 1;                // chain-tree levels of the tallest simulation
+    int top_levels = 0;            // bit l: some simulation's chain-tree top is at level l
     int64_t nodes[kMaxLevels] = {};  // chain-tree nodes per level, all simulations
     size_t sims_off = 0, soff_off = 0, loff_off = 0, counter_off = 0, U_off = 0, chain_off = 0;
     ChainLayout chain{};
@@ -202,6 +203,13 @@ struct spinsim_s {
     // profiling: per spin group, events before integrate, after integrate, after chain
     cudaEvent_t prof[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     int prof_groups = 0;
+    // the range opened by spinsim_range_begin, until spinsim_range_finish
+    // (any other call on the handle closes it: they share the arena)
+    bool range_open = false;
+    spinsim_request range_req{};
+    spinsim_result* range_res = nullptr;
+    Plan range_plan;
+    std::vector<Checked> range_checked;
     // serving
     std::vector<Slot> slots;
     std::deque<int64_t> pending;
@@ -285,6 +293,7 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
                 g.steps += (double)checked[i].K * (double)checked[i].L;
                 const ChainGeom cg = chain_geom(checked[i].K);
                 g.levels = std::max(g.levels, cg.top + 1);
+                g.top_levels |= 1 << cg.top;
                 for (int l = 0; l <= cg.top; l++) g.nodes[l] += cg.nodes[l];
             }
         if (g.idx.empty()) continue;
@@ -521,9 +530,15 @@ int refresh_table(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res
 // Requests with a failed validation are skipped.
 // With `prof_in_graph`, a capture of the handle's own graph records the
 // profiling events as event nodes, so every replay times its kernels.
+// `phase`: kPhaseAll the whole path; kPhaseBegin the operators and the chain's
+// up-sweeps only (spinsim_range_begin); kPhaseFinish the chain's down-sweeps
+// and the write from each request's psi0, over operators a kPhaseBegin run of
+// the same plan left in the arena (spinsim_range_finish).
+enum { kPhaseAll = 0, kPhaseBegin = 1, kPhaseFinish = 2 };
+
 int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, const std::vector<Checked>& checked,
               const Plan& plan, cudaStream_t stream, Arena& arena, PinnedBuf& pinned, cudaEvent_t pinned_free,
-              bool capturing, int* kernels_out, bool prof_in_graph = false)
+              bool capturing, int* kernels_out, bool prof_in_graph = false, int phase = kPhaseAll)
 {
     auto prof_record = [&](cudaEvent_t e) {
         if (capturing) cudaEventRecordWithFlags(e, stream, cudaEventRecordExternal);
@@ -564,24 +579,29 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
         ia.tile_counter = reinterpret_cast<unsigned long long*>(base + g.counter_off);
         int lanes = 0, block = 0, grid = 0;
         if (g.samples > 0) {
-            st = choose_shape(h, g.spin_x2, g.small, g.steps, ia, stream, capturing, lanes, block, grid);
-            if (st != SPINSIM_OK) return st;
-            const int spb = block / lanes;
-            ia.n_tiles = (g.samples + spb - 1) / spb;
-            if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
-                return SPINSIM_E_CUDA;
-            if (pg >= 0) prof_record(h->prof[pg][0]);
-            if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, lanes, block, grid, g.small, ia, stream) !=
-                cudaSuccess)
-                return SPINSIM_E_CUDA;
+            if (phase == kPhaseFinish && pg >= 0) prof_record(h->prof[pg][0]);
+            if (phase != kPhaseFinish) {
+                st = choose_shape(h, g.spin_x2, g.small, g.steps, ia, stream, capturing, lanes, block, grid);
+                if (st != SPINSIM_OK) return st;
+                const int spb = block / lanes;
+                ia.n_tiles = (g.samples + spb - 1) / spb;
+                if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
+                    return SPINSIM_E_CUDA;
+                if (pg >= 0) prof_record(h->prof[pg][0]);
+                if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, lanes, block, grid, g.small, ia,
+                                     stream) != cudaSuccess)
+                    return SPINSIM_E_CUDA;
+                kernels += 1;
+            }
             if (pg >= 0) prof_record(h->prof[pg][1]);
-            kernels += 1;
             ChainArgs ca;
             ca.sims = ia.sims;
             ca.n_sims = (int)m;
             ca.level_off = reinterpret_cast<const int64_t*>(base + g.loff_off);
             ca.U = ia.U;
             chain_args_set(ca, g.chain, base + g.chain_off);
+            ca.mode = phase == kPhaseBegin ? kChainUp : (phase == kPhaseFinish ? kChainDown : kChainFull);
+            ca.top_levels = g.top_levels;
             int chain_k = 0;
             if (launch_chain(g.spin_x2, ca, h->n_sm, stream, &chain_k) != cudaSuccess) return SPINSIM_E_CUDA;
             if (pg >= 0) prof_record(h->prof[pg][2]);
@@ -590,6 +610,10 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             h->last.threads_per_block = block;
             h->last.grid_blocks = grid;
         }
+    }
+    if (phase == kPhaseBegin) {
+        if (kernels_out) *kernels_out = kernels;
+        return SPINSIM_OK;
     }
     for (const StagedOut& s : plan.staged)
         h->last.d2h_bytes += (int64_t)((s.host_states ? s.states_bytes : 0) + (s.host_spin ? s.spin_bytes : 0) +
@@ -775,6 +799,7 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
 {
     if (!h || n < 0 || (n > 0 && (!reqs || !res))) return SPINSIM_E_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return SPINSIM_E_CUDA;
+    h->range_open = false;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     std::vector<Checked> checked((size_t)n);
     int first_err = SPINSIM_OK;
@@ -889,6 +914,102 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
     return first_err;
 }
 
+int spinsim_range_begin(spinsim_handle h, const spinsim_request* req, spinsim_result* res, double* agg,
+                        void* stream_v)
+{
+    if (!h || !req || !res || !agg) return SPINSIM_E_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SPINSIM_E_CUDA;
+    h->range_open = false;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    std::vector<Checked> checked(1);
+    checked[0] = check_request(req);
+    Checked& c = checked[0];
+    if (c.status == SPINSIM_OK) {
+        if (!res->states) c.status = SPINSIM_E_ARG;
+        else if (res->capacity < c.K) c.status = SPINSIM_E_CAPACITY;
+    }
+    if (c.status == SPINSIM_OK) {
+        c.flags |= precision_flags(h->cfg.precision, h->cfg.rotating_frame, *req);
+        c.small = small_angle_request(h->cfg, *req, c.L);
+    }
+    res->status = c.status;
+    res->flags = c.flags;
+    res->trotter_squares = 0;
+    res->n_samples = 0;
+    if (c.status != SPINSIM_OK) return c.status;
+    // the arena is shared with graph replays: start after the handle's last
+    // one, and do not replay a graph over the range's operators later
+    if (h->done_pending && cudaStreamWaitEvent(stream, h->ev_done, 0) != cudaSuccess) return SPINSIM_E_CUDA;
+    drop_graph(h);
+    h->last = spinsim_launch_info{};
+    h->last.integrate_ms = -1.0;
+    h->last.chain_ms = -1.0;
+    h->prof_groups = 0;
+    Plan plan;
+    build_plan(req, res, 1, checked, false, plan);
+    int kernels = 0;
+    int st = run_batch(h, req, res, checked, plan, stream, h->arena, h->pinned, h->ev_pinned, false, &kernels, false,
+                       kPhaseBegin);
+    if (st != SPINSIM_OK) return res->status = st;
+    // the ordered product of the range: the top node of its chain tree
+    const int n = req->spin_x2 + 1;
+    double top[18];
+    if (c.K > 0) {
+        const Group& g = plan.groups[0];
+        const ChainGeom cg = chain_geom(c.K);
+        const char* src = static_cast<const char*>(h->arena.buf.p) + g.chain_off + g.chain.agg[cg.top];
+        if (cudaMemcpyAsync(top, src, (size_t)op_doubles(req->spin_x2) * sizeof(double), cudaMemcpyDeviceToHost,
+                            stream) != cudaSuccess)
+            return res->status = SPINSIM_E_CUDA;
+    }
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return res->status = SPINSIM_E_CUDA;
+    if (c.K == 0) {
+        for (int i = 0; i < 2 * n * n; i++) agg[i] = (i % (2 * n + 2) == 0) ? 1.0 : 0.0;
+    } else if (n == 3) {
+        for (int i = 0; i < 18; i++) agg[i] = top[i];
+    } else {
+        // SU(2) (alpha, beta) -> [[alpha, -conj(beta)], [beta, conj(alpha)]]
+        const double ar = top[0], ai = top[1], br = top[2], bi = top[3];
+        const double m[8] = {ar, ai, -br, bi, br, bi, ar, -ai};
+        for (int i = 0; i < 8; i++) agg[i] = m[i];
+    }
+    h->range_req = *req;
+    h->range_res = res;
+    h->range_plan = plan;
+    h->range_checked = checked;
+    h->range_open = true;
+    h->last.kernels_launched = kernels;
+    res->n_samples = c.K;
+    return SPINSIM_OK;
+}
+
+int spinsim_range_finish(spinsim_handle h, const double* psi_in, void* stream_v)
+{
+    if (!h || !psi_in || !h->range_open) return SPINSIM_E_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SPINSIM_E_CUDA;
+    h->range_open = false;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
+    const int n = h->range_req.spin_x2 + 1;
+    double nrm = 0.0;
+    for (int i = 0; i < 2 * n; i++) {
+        if (!std::isfinite(psi_in[i])) return SPINSIM_E_ARG;
+        nrm += psi_in[i] * psi_in[i];
+    }
+    if (std::fabs(std::sqrt(nrm) - 1.0) > 1e-10) return SPINSIM_E_NORM;
+    spinsim_request req = h->range_req;
+    for (int i = 0; i < 6; i++) req.psi0[i] = i < 2 * n ? psi_in[i] : 0.0;
+    h->last = spinsim_launch_info{};
+    h->last.integrate_ms = -1.0;
+    h->last.chain_ms = -1.0;
+    h->prof_groups = 0;
+    int kernels = 0;
+    int st = run_batch(h, &req, h->range_res, h->range_checked, h->range_plan, stream, h->arena, h->pinned,
+                       h->ev_pinned, false, &kernels, false, kPhaseFinish);
+    h->last.kernels_launched = kernels;
+    if (st != SPINSIM_OK) h->range_res->status = st;
+    return st;
+}
+
 int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info)
 {
     if (!h || !info) return SPINSIM_E_ARG;
@@ -998,6 +1119,7 @@ int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result*
 {
     if (!h || !req || !res || !ticket) return SPINSIM_E_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return SPINSIM_E_CUDA;
+    h->range_open = false;
     int st = serving_init(h);
     if (st != SPINSIM_OK) return st;
     Checked c = check_request(req);

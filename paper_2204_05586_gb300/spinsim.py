@@ -69,7 +69,7 @@ class spinsim_launch_info(ctypes.Structure):
 
 EXPORTED = ("spinsim_config_default", "spinsim_create", "spinsim_destroy", "spinsim_counts", "spinsim_footprint",
             "spinsim_simulate", "spinsim_submit", "spinsim_poll", "spinsim_last_launch", "spinsim_status_string",
-            "spinsim_simulate_static")
+            "spinsim_simulate_static", "spinsim_range_begin", "spinsim_range_finish")
 
 _lib = None
 _lock = threading.Lock()
@@ -106,6 +106,9 @@ def load(build_if_missing: bool = True):
         L.spinsim_last_launch.argtypes = [ctypes.c_void_p, P(spinsim_launch_info)]
         L.spinsim_simulate_static.argtypes = [P(spinsim_config), P(spinsim_request), P(spinsim_result),
                                               ctypes.c_void_p]
+        L.spinsim_range_begin.argtypes = [ctypes.c_void_p, P(spinsim_request), P(spinsim_result),
+                                          P(ctypes.c_double), ctypes.c_void_p]
+        L.spinsim_range_finish.argtypes = [ctypes.c_void_p, P(ctypes.c_double), ctypes.c_void_p]
         L.spinsim_status_string.argtypes = [ctypes.c_int]
         L.spinsim_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -153,6 +156,24 @@ def spinsim_simulate_static(cfg: spinsim_config, req: spinsim_request, res: spin
     device array); the outputs must be device buffers."""
     return load().spinsim_simulate_static(ctypes.byref(cfg), ctypes.byref(req), ctypes.byref(res),
                                           ctypes.c_void_p(stream))
+
+
+def spinsim_range_begin(h, req: spinsim_request, res: spinsim_result, stream: int = 0):
+    """Returns (status, agg) with agg the range's ordered product as a
+    complex128 [N, N] numpy array."""
+    import numpy as np
+    n = req.spin_x2 + 1
+    agg = (ctypes.c_double * (2 * n * n))()
+    st = load().spinsim_range_begin(h, ctypes.byref(req), ctypes.byref(res), agg, stream)
+    a = np.frombuffer(agg, dtype=np.float64).copy().view(np.complex128).reshape(n, n)
+    return st, a
+
+
+def spinsim_range_finish(h, psi_in, stream: int = 0) -> int:
+    import numpy as np
+    psi = np.ascontiguousarray(np.asarray(psi_in, dtype=np.complex128)).view(np.float64)
+    buf = (ctypes.c_double * 6)(*([float(x) for x in psi] + [0.0] * (6 - len(psi))))
+    return load().spinsim_range_finish(h, buf, stream)
 
 
 def spinsim_submit(h, req: spinsim_request, res: spinsim_result):
