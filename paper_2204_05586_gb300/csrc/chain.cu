@@ -6,18 +6,21 @@
 // scan in FP64 on the device, per simulation (no node spans two simulations):
 //   level 0:  a node is one warp over kFan runs of `run` consecutive samples;
 //             lane l multiplies its run in order (all lanes busy);
-//   level l:  a node covers kFan consecutive nodes of level l - 1;
-//   up:       each node forms the products of its binary tree over its 32
-//             children (31 products in 5 rounds), keeping the left-child
-//             product of every internal node and the node's total;
-//   down:     from the state entering a node, the states entering its 32
-//             children follow by walking the binary tree down: the left child
-//             receives the state, the right child the left child's product
-//             applied to it (31 matrix-vector products in 5 rounds);
-//   apply:    each lane walks its run from its entering state, writing psi_k,
-//             <J>_k and (optionally) U_k.
-// The top node of a simulation starts the down-sweep from psi_init inside the
-// up kernel of its level.
+//   level l:  a node covers kFan consecutive nodes of level l - 1, up to one
+//             top node per simulation;
+//   up:       one kernel per level; every node forms the products of its
+//             binary tree over its 32 children (31 products in 5 rounds),
+//             keeping the left-child product of every internal node and the
+//             node's total;
+//   down:     the warp that builds a top node also walks its tree down from
+//             psi0 (the left child receives the state, the right child the left
+//             child's product applied to it: 31 matrix-vector products in 5
+//             rounds) and stores the states entering its children;
+//   apply:    per level-0 node, the entering state follows by walking down the
+//             ancestors' trees from there (a matrix-vector product at each step
+//             into a right child), the node's own down-sweep gives every lane
+//             run its entering state, and each lane walks its run, writing
+//             psi_k, <J>_k and (optionally) U_k.
 //
 // GB300 executes FP64 at 1/64 of the FP32 rate: one FP64 warp instruction
 // keeps an SM sub-partition busy for tens of cycles whether one lane or 32
@@ -289,7 +292,11 @@ constexpr int warp_state_doubles() { return 63 * 2 * N; }
 constexpr int kChainWarps = 4;   // warps per block of the chain kernels
 
 // ------------------------------------------------------------------ kernels
-// Up-sweep of level `level`: one warp per node.
+// Up-sweep of level `level`: one warp per node.  The node's leaves are its
+// lanes' runs (level 0) or its children's products; its binary tree's
+// left-child products and its total are stored.  At a simulation's top node
+// (whole scan only) the warp goes on down its tree from psi0 and stores the
+// states entering the top node's children.
 template <int N>
 __global__ void __launch_bounds__(128) chain_up_kernel(ChainArgs a, int level)
 {
@@ -338,7 +345,6 @@ __global__ void __launch_bounds__(128) chain_up_kernel(ChainArgs a, int level)
             for (int i = 0; i < D / 2; i++) dst[i] = src[i];
         }
         if (level >= 1 && s.chain_top == level && a.mode == kChainFull) {
-            // top node: the down-sweep starts here from psi_init
             if (lane < SV) V[tslot(5, 0) * SV + lane] = s.psi0[lane];
             __syncwarp();
             tree_down<N>(V, [&](int t) { return (const double*)(S + left_child_slot(t) * D); }, lane);
@@ -353,38 +359,15 @@ __global__ void __launch_bounds__(128) chain_up_kernel(ChainArgs a, int level)
     }
 }
 
-// Down-sweep of level `level` >= 1 for nodes below their simulation's top,
-// or (top = true) for the top nodes of this level, from psi0.
-template <int N>
-__global__ void __launch_bounds__(128) chain_down_kernel(ChainArgs a, int level, bool top)
-{
-    constexpr int D = Tree<N>::D, SV = 2 * N;
-    extern __shared__ __align__(16) double smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double* V = smem + warp * warp_state_doubles<N>();
-    const int64_t* off = a.level_off + (size_t)level * (a.n_sims + 1);
-    const int64_t* coff = off - (a.n_sims + 1);
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t node = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; node < a.nodes[level]; node += warps) {
-        const int si = find_node_sim(off, a.n_sims, node);
-        const DevSim& s = a.sims[si];
-        if ((s.chain_top == level) != top) continue;   // the other launch's node
-        const int64_t local = node - off[si];
-        if (lane < SV) V[tslot(5, 0) * SV + lane] = top ? s.psi0[lane] : a.state[level][node * SV + lane];
-        __syncwarp();
-        const double* L = a.left[level] + node * kLeftPerNode * D;
-        tree_down<N>(V, [&](int t) { return L + t * D; }, lane);
-        const int64_t child = local * kFan + lane;
-        if (child < coff[si + 1] - coff[si]) {
-            double* dst = a.state[level - 1] + (coff[si] + child) * SV;
-#pragma unroll
-            for (int i = 0; i < SV; i++) dst[i] = V[lane * SV + i];
-        }
-        __syncwarp();
-    }
-}
-
-// Level 0: states entering the lanes' runs, then each lane walks its run.
+// Down-sweep and output: one warp per level-0 node.  The state entering the
+// node follows by walking down to it: in the whole scan from the state the
+// top node's up-sweep stored for its child on this node's path (psi0 for a
+// simulation of one node), in the down-only mode (a range whose entering
+// state arrived later) from psi0 at the top node.  Inside each ancestor's
+// binary tree, a step into a right child applies the left sibling's product
+// (one matrix row per lane).  The node's own tree then gives every lane run
+// its entering state; each lane walks its run, writing psi_k, <J>_k and
+// (optionally) U_k.
 template <int N>
 __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
 {
@@ -392,16 +375,41 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
     extern __shared__ __align__(16) double smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double* V = smem + warp * warp_state_doubles<N>();
-    const int64_t* off = a.level_off;
+    const int64_t stride = a.n_sims + 1;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t node = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; node < a.nodes[0]; node += warps) {
-        const int si = find_node_sim(off, a.n_sims, node);
+        const int si = find_node_sim(a.level_off, a.n_sims, node);
         const DevSim& s = a.sims[si];
-        const int64_t local = node - off[si];
-        if (lane < SV) V[tslot(5, 0) * SV + lane] = s.chain_top == 0 ? s.psi0[lane] : a.state[0][node * SV + lane];
+        const int64_t local = node - a.level_off[si];
+        double* v = V + tslot(5, 0) * SV;
+        int from = s.chain_top;
+        if (a.mode == kChainFull && from >= 1) {
+            from--;
+            const int64_t anc = local >> (5 * from);   // the top node's child on the path
+            if (lane < SV) v[lane] = a.state[from][(a.level_off[(size_t)from * stride + si] + anc) * SV + lane];
+        } else if (lane < SV) {
+            v[lane] = s.psi0[lane];
+        }
         __syncwarp();
-        const double* L = a.left[0] + node * kLeftPerNode * D;
-        tree_down<N>(V, [&](int t) { return L + t * D; }, lane);
+        for (int level = from; level >= 1; level--) {
+            const int64_t anc = local >> (5 * level);                         // ancestor at `level`
+            const int64_t j = (local >> (5 * (level - 1))) - anc * kFan;     // its child on the path
+            const double* L = a.left[level] + (a.level_off[(size_t)level * stride + si] + anc) * kLeftPerNode * D;
+            for (int h = 5; h >= 1; h--) {
+                if (((j >> (h - 1)) & 1) == 0) continue;                    // left child: state unchanged
+                const int p = (int)(j >> h);
+                cx<double> y = cmk(0.0, 0.0);
+                if (lane < N) y = Tree<N>::matvec_row(L + (tslot(h, p) - 32) * D, v, lane);
+                __syncwarp();
+                if (lane < N) {
+                    v[2 * lane] = y.r;
+                    v[2 * lane + 1] = y.i;
+                }
+                __syncwarp();
+            }
+        }
+        const double* L0 = a.left[0] + node * kLeftPerNode * D;
+        tree_down<N>(V, [&](int t) { return L0 + t * D; }, lane);
         cx<double> psi[N], nxt[N];
 #pragma unroll
         for (int i = 0; i < N; i++) psi[i] = cmk(V[lane * SV + 2 * i], V[lane * SV + 2 * i + 1]);
@@ -461,21 +469,10 @@ static cudaError_t launch_chain_n(const ChainArgs& a, int n_sm, cudaStream_t str
             chain_up_kernel<N><<<grid(a.nodes[l]), block, up_smem, stream>>>(args, l);
             (*kernels)++;
         }
-    if (a.mode == kChainUp) return cudaGetLastError();
-    // (kChainDown: the top nodes of levels >= 1 start from psi0 here; in the
-    // full scan the up kernel of their level did that)
-    for (int l = a.levels - 1; l >= 1; l--) {
-        if (a.mode == kChainDown && ((a.top_levels >> l) & 1)) {
-            chain_down_kernel<N><<<grid(a.nodes[l]), block, down_smem, stream>>>(args, l, true);
-            (*kernels)++;
-        }
-        if (l <= a.levels - 2) {
-            chain_down_kernel<N><<<grid(a.nodes[l]), block, down_smem, stream>>>(args, l, false);
-            (*kernels)++;
-        }
+    if (a.mode != kChainUp) {
+        chain_apply_kernel<N><<<grid(a.nodes[0]), block, down_smem, stream>>>(args);
+        (*kernels)++;
     }
-    chain_apply_kernel<N><<<grid(a.nodes[0]), block, down_smem, stream>>>(args);
-    (*kernels)++;
     return cudaGetLastError();
 }
 

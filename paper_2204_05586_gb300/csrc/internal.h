@@ -112,10 +112,10 @@ struct IntegrateArgs {
     int64_t n_tiles;
 };
 
-// What launch_chain runs: the whole scan, only the up-sweeps (a range whose
-// entering state is not known yet: no down-sweep from a top node), or only
-// the down-sweeps and the write from each simulation's psi0 (the same range
-// once its entering state has been placed in psi0).
+// What launch_chain runs: the whole scan, only the up-sweep (the products:
+// a range whose entering state is not known yet), or only the down-sweep and
+// the write from each simulation's psi0 (that range once its entering state
+// has been placed in psi0).
 enum ChainMode { kChainFull = 0, kChainUp = 1, kChainDown = 2 };
 
 struct ChainArgs {
@@ -123,13 +123,13 @@ struct ChainArgs {
     int n_sims;
     int levels;                       // 1 + the highest top level of the batch
     int mode;                         // ChainMode
-    int top_levels;                   // bit l: some simulation's top node is at level l
     const int64_t* level_off;         // [levels][n_sims + 1] first node of each simulation per level (device)
     int64_t nodes[kMaxLevels];        // nodes per level, all simulations
     const double* U;                  // sample operators
     double* agg[kMaxLevels];          // [nodes] product of the node's samples
     double* left[kMaxLevels];         // [nodes][kLeftPerNode] left-child products of the node's binary tree
-    double* state[kMaxLevels];        // [nodes][N] complex state entering the node
+    double* state[kMaxLevels];        // [nodes][N] complex state entering the node (written for the
+                                      // children of top nodes by the up-sweep)
 };
 
 // Doubles per stored operator in the operator buffer and chain scratch.
@@ -166,7 +166,6 @@ inline void chain_args_set(ChainArgs& a, const ChainLayout& cl, char* base)
 {
     a.levels = cl.levels;
     a.mode = kChainFull;
-    a.top_levels = 0;
     for (int l = 0; l < kMaxLevels; l++) {
         const bool used = l < cl.levels;
         a.nodes[l] = used ? cl.nodes[l] : 0;

@@ -111,7 +111,6 @@ struct Group {
     int64_t samples = 0;
     double steps = 0.0;            // CF4 (or sampling) steps of the group
     int levels = 1;                // chain-tree levels of the tallest simulation
-    int top_levels = 0;            // bit l: some simulation's chain-tree top is at level l
     int64_t nodes[kMaxLevels] = {};  // chain-tree nodes per level, all simulations
     size_t sims_off = 0, soff_off = 0, loff_off = 0, counter_off = 0, U_off = 0, chain_off = 0;
     ChainLayout chain{};
@@ -293,7 +292,6 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
                 g.steps += (double)checked[i].K * (double)checked[i].L;
                 const ChainGeom cg = chain_geom(checked[i].K);
                 g.levels = std::max(g.levels, cg.top + 1);
-                g.top_levels |= 1 << cg.top;
                 for (int l = 0; l <= cg.top; l++) g.nodes[l] += cg.nodes[l];
             }
         if (g.idx.empty()) continue;
@@ -601,7 +599,6 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             ca.U = ia.U;
             chain_args_set(ca, g.chain, base + g.chain_off);
             ca.mode = phase == kPhaseBegin ? kChainUp : (phase == kPhaseFinish ? kChainDown : kChainFull);
-            ca.top_levels = g.top_levels;
             int chain_k = 0;
             if (launch_chain(g.spin_x2, ca, h->n_sm, stream, &chain_k) != cudaSuccess) return SPINSIM_E_CUDA;
             if (pg >= 0) prof_record(h->prof[pg][2]);
