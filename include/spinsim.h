@@ -87,7 +87,9 @@ typedef struct {
                                      -1 = default: 24 for FP64 (Sec. 1.2.3); for FP32-bulk,
                                      per request the fewest squarings whose splitting-error
                                      bound, summed over all steps of the request, is <= 1e-6 */
-    int32_t lanes_per_sample;     /* 0 = autotune; else 1, 2 or 4 threads share one U_k.
+    int32_t lanes_per_sample;     /* 0 = default (1); else 1, 2, 4 or 8 threads share one U_k
+                                     in the whole waves of a launch (the samples after the
+                                     last whole wave use one lane per segment of a sample).
                                      Results do not depend on it (fixed reduction tree).   */
     int32_t threads_per_block;    /* 0 = autotune; else 64, 128 or 256                        */
     int32_t use_graphs;           /* 1: replay repeated identical batch shapes as a CUDA graph
@@ -232,7 +234,7 @@ int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info);
  * for spin-half; a larger K returns SPINSIM_E_NOMEM without launching.
  * res->states (and res->spin, res->ops when not NULL) must be 16-byte
  * aligned device memory, else SPINSIM_E_ARG.  cfg selects method, precision,
- * frame, tau and the launch shape (0 = lanes 2, 128 threads, as many resident
+ * frame, tau and the launch shape (0 = lanes 1, 128 threads, as many resident
  * blocks per SM as fit; no autotuning); use_graphs, mem_budget and profile are
  * ignored; res->flags receives the request's warning bits.
  * The first call on a device looks up the device address of the array; make

@@ -6,14 +6,19 @@
 // frame and then moved back to the lab frame (Eq. exit_rotating_frame).
 //
 // Work decomposition (GB300): a persistent grid pulls tiles of consecutive
-// samples from an atomic counter; G = 1, 2 or 4 lanes of a warp share one
-// sample.  The L steps of a sample are always split into the same four
-// segments [s L/4, (s+1) L/4) and reduced by the same tree
-// (S3 S2)(S1 S0), whichever G is used, so the result is bit-for-bit
-// independent of the launch shape and of which other samples share the batch.
-// A lane computes its segments' residual products in registers and leaves
-// them in shared memory; lane 0 of the group combines them, finishes the
-// operator in FP64 and stores it.
+// samples from an atomic counter; G = 1, 2, 4 or 8 lanes of a warp share one
+// sample.  The L steps of a sample are always split into the same eight
+// segments [s L/8, (s+1) L/8) and reduced by the same binary tree
+// ((S7 S6)(S5 S4))((S3 S2)(S1 S0)), whichever G is used, so the result is
+// bit-for-bit independent of the launch shape and of which other samples
+// share the batch.  A lane owns 8/G consecutive segments -- a complete
+// sub-tree, built as its segments finish with a small stack in shared memory.
+// After the tile, one thread per sample combines the lanes' sub-trees and
+// finishes the operator in FP64: on GB300 an FP64 warp instruction costs the
+// same with 1 or 32 active lanes, so this epilogue runs with every lane on a
+// sample of its own.  Whole waves of tiles use the tuned G; the samples left
+// after them use G = 8 (one segment per lane), so the last wave ends in
+// eighths of a sample's steps.
 #include "device_math.cuh"
 
 namespace spinsim {
@@ -149,24 +154,24 @@ __device__ __forceinline__ void store_identity(int N, double* out)
 }
 
 // ------------------------------------------------------------------- kernel
-template <int N, typename R, int G, int METHOD, bool SMALL>
+// Per thread kSlots residual records of shared memory: the stack of the
+// thread's canonical sub-tree (log2 of its segment count) and its result.
+constexpr int kSlots = kSegLog2 + 1;
+
+template <int N, typename R, int METHOD, bool SMALL>
 __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
 {
     using Res = typename ResType<N, R>::type;
     constexpr int OPD = N == 3 ? 18 : 4;
-    constexpr int SEG_PER_LANE = kSegments / G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Res* seg = reinterpret_cast<Res*>(smem_raw);
+    Res* rec = reinterpret_cast<Res*>(smem_raw);                                        // [blockDim][kSlots]
+    double2* bg = reinterpret_cast<double2*>(smem_raw + (size_t)blockDim.x * kSlots * sizeof(Res));  // [blockDim]
     __shared__ unsigned long long s_tile;
-
-    const int spb = blockDim.x / G;
-    const int slot = threadIdx.x / G;
-    const int lane = threadIdx.x % G;
 
     // Never touch shared memory beyond what the launch provided.
     unsigned dyn_smem;
     asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
-    if ((size_t)spb * kSegments * sizeof(Res) > (size_t)dyn_smem) return;
+    if ((size_t)blockDim.x * (kSlots * sizeof(Res) + sizeof(double2)) > (size_t)dyn_smem) return;
 
     for (;;) {
         __syncthreads();
@@ -175,126 +180,170 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
         const unsigned long long tile = s_tile;
         if (tile >= (unsigned long long)a.n_tiles) return;
 
-        const int64_t g = (int64_t)tile * spb + slot;
-        const bool active = g < a.total_samples;
-        int si = 0;
-        int64_t k = 0;
-        if (active) {
-            si = find_index(a.sample_offsets, a.n_sims, g);
-            k = g - a.sample_offsets[si];
-        }
-        double gsum = 0.0, beta = 0.0;
-        if (active && k > 0) {
+        // tile shape: bulk tiles first, then the tail's (more lanes per sample)
+        const bool bulk = tile < (unsigned long long)a.n_bulk_tiles;
+        const int lg = bulk ? a.lg_bulk : a.lg_tail;       // log2 of lanes per sample
+        const int spb = (int)(blockDim.x >> lg);
+        const int64_t base = bulk ? (int64_t)tile * spb
+                                  : a.bulk_samples + (int64_t)(tile - a.n_bulk_tiles) * spb;
+        const int slot = threadIdx.x >> lg;
+        const int lane = threadIdx.x & ((1 << lg) - 1);
+        const int64_t g = base + slot;
+        Res* my = rec + (size_t)threadIdx.x * kSlots;
+        if (g < a.total_samples) {
+            const int si = find_index(a.sample_offsets, a.n_sims, g);
+            const int64_t k = g - a.sample_offsets[si];
             const DevSim& s = a.sims[si];
-            SampleCtx<R> c;
-            gsum = make_ctx<R, N>(s, k, c, beta);
-            const int64_t L = s.L;
+            // lanes in use: at most one per segment; each owns a canonical sub-tree
+            const int lg_use = min(lg, (int)s.seg_log2);
+            const int spl_log2 = s.seg_log2 - lg_use;
+            if (k > 0 && lane < (1 << lg_use)) {
+                SampleCtx<R> c;
+                double beta = 0.0;
+                const double gsum = make_ctx<R, N>(s, k, c, beta);
+                if (lane == 0) bg[slot] = make_double2(beta, gsum);
+                const int64_t L = s.L;
 #pragma unroll 1
-            for (int q = 0; q < SEG_PER_LANE; q++) {
-                const int sg = lane * SEG_PER_LANE + q;
-                const int64_t lo = (sg * L) / kSegments, hi = ((sg + 1) * L) / kSegments;
-                Res X;
-                res_zero(X);
+                for (int q = 0; q < (1 << spl_log2); q++) {
+                    const int sg = (lane << spl_log2) + q;
+                    const int64_t lo = (sg * L) >> s.seg_log2, hi = ((sg + 1) * L) >> s.seg_log2;
+                    Res X;
+                    res_zero(X);
 #pragma unroll 1
-                for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL>(c, (R)l, c.tau, X);   // U <- u_l U
-                seg[slot * kSegments + sg] = X;
+                    for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL>(c, (R)l, c.tau, X);   // U <- u_l U
+                    // canonical tree over the lane's segments: a finished pair of
+                    // equal sub-trees merges (later on the left) until the sizes differ
+                    int h = 0;
+#pragma unroll 1
+                    while ((q >> h) & 1) {
+                        Res t;
+                        res_mul(X, my[h], t);
+                        X = t;
+                        h++;
+                    }
+                    my[h] = X;
+                }
             }
         }
-        __syncwarp();
-        if (active && lane == 0) {
-            double* out = a.U + g * OPD;
-            if (k == 0) {
-                store_identity(N, out);
-            } else {
-                Res P01, P23, P;
-                res_mul(seg[slot * kSegments + 1], seg[slot * kSegments + 0], P01);
-                res_mul(seg[slot * kSegments + 3], seg[slot * kSegments + 2], P23);
-                res_mul(P23, P01, P);
-                const DevSim& s = a.sims[si];
-                SampleExact sx;
-                make_exact<N>(s, beta, gsum, sx);
-                finish(P, s, sx, out);
+        __syncthreads();
+        // epilogue, one thread per sample of the tile: the lanes' sub-trees
+        // combined in the canonical tree, then the FP64 part
+        if (threadIdx.x < spb) {
+            const int t = threadIdx.x;
+            const int64_t gs = base + t;
+            if (gs < a.total_samples) {
+                const int si = find_index(a.sample_offsets, a.n_sims, gs);
+                const int64_t k = gs - a.sample_offsets[si];
+                double* out = a.U + gs * OPD;
+                if (k == 0) {
+                    store_identity(N, out);
+                } else {
+                    const DevSim& s = a.sims[si];
+                    const int lg_use = min(lg, (int)s.seg_log2);
+                    const int spl_log2 = s.seg_log2 - lg_use;
+                    Res* lanes = rec + (size_t)(t << lg) * kSlots;   // lane j's result: lanes[j * kSlots + spl_log2]
+#pragma unroll 1
+                    for (int d = 0; d < lg_use; d++)
+#pragma unroll 1
+                        for (int j = 0; j < (1 << lg_use); j += 2 << d) {
+                            Res tmp;
+                            res_mul(lanes[(j + (1 << d)) * kSlots + spl_log2], lanes[j * kSlots + spl_log2], tmp);
+                            lanes[j * kSlots + spl_log2] = tmp;
+                        }
+                    const double2 b = bg[t];
+                    SampleExact sx;
+                    make_exact<N>(s, b.x, b.y, sx);
+                    finish(lanes[spl_log2], s, sx, out);
+                }
             }
         }
-        __syncwarp();
     }
 }
 
 // ----------------------------------------------------------------- launchers
-template <int N, typename R, int G, int METHOD, bool SMALL>
+template <int N, typename R, int METHOD, bool SMALL>
 static void* kernel_ptr()
 {
-    return (void*)integrate_kernel<N, R, G, METHOD, SMALL>;
-}
-
-template <int N, typename R, int METHOD, bool SMALL>
-static void* pick_lanes(int lanes)
-{
-    switch (lanes) {
-        case 1: return kernel_ptr<N, R, 1, METHOD, SMALL>();
-        case 2: return kernel_ptr<N, R, 2, METHOD, SMALL>();
-        case 4: return kernel_ptr<N, R, 4, METHOD, SMALL>();
-        default: return nullptr;
-    }
+    return (void*)integrate_kernel<N, R, METHOD, SMALL>;
 }
 
 template <int N, typename R, bool SMALL>
-static void* pick_method(int method, int lanes)
+static void* pick_method(int method)
 {
     switch (method) {
-        case 0: return pick_lanes<N, R, 0, SMALL>(lanes);
-        case 1: return pick_lanes<N, R, 1, SMALL>(lanes);
-        case 2: return pick_lanes<N, R, 2, SMALL>(lanes);
+        case 0: return kernel_ptr<N, R, 0, SMALL>();
+        case 1: return kernel_ptr<N, R, 1, SMALL>();
+        case 2: return kernel_ptr<N, R, 2, SMALL>();
         default: return nullptr;
     }
 }
 
 // The small-angle variant exists for FP32-bulk only; FP64 keeps the general
 // series (its terms are sized for double precision).
-static void* select_kernel(int spin_x2, int precision, int method, int lanes, bool small)
+static void* select_kernel(int spin_x2, int precision, int method, bool small)
 {
     if (spin_x2 == 2) {
-        if (!precision) return pick_method<3, double, false>(method, lanes);
-        return small ? pick_method<3, float, true>(method, lanes) : pick_method<3, float, false>(method, lanes);
+        if (!precision) return pick_method<3, double, false>(method);
+        return small ? pick_method<3, float, true>(method) : pick_method<3, float, false>(method);
     }
     if (spin_x2 == 1) {
-        if (!precision) return pick_method<2, double, false>(method, lanes);
-        return small ? pick_method<2, float, true>(method, lanes) : pick_method<2, float, false>(method, lanes);
+        if (!precision) return pick_method<2, double, false>(method);
+        return small ? pick_method<2, float, true>(method) : pick_method<2, float, false>(method);
     }
     return nullptr;
 }
 
-// Dynamic shared memory of one block: kSegments residual records per sample
-// slot, sized from the record type itself.
-size_t integrate_smem_bytes(int spin_x2, int precision, int lanes, int block)
+// Dynamic shared memory of one block: kSlots residual records and the
+// sample's (beta, gsum) per thread, sized from the record type itself.
+size_t integrate_smem_bytes(int spin_x2, int precision, int block)
 {
     size_t res;
     if (spin_x2 == 2) res = precision ? sizeof(Res3<float>) : sizeof(Res3<double>);
     else res = precision ? sizeof(Res2<float>) : sizeof(Res2<double>);
-    return (size_t)(block / lanes) * kSegments * res;
+    return (size_t)block * (kSlots * res + 2 * sizeof(double));
 }
 
 // Must be called (outside stream capture) before the first launch of a
-// (spin, precision, method, lanes) kernel: it raises the kernel's dynamic
+// (spin, precision, method, variant) kernel: it raises the kernel's dynamic
 // shared-memory limit to what a 256-thread block needs.
-cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int lanes, int block, bool small,
-                                int* blocks_per_sm)
+cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int block, bool small, int* blocks_per_sm)
 {
-    void* k = select_kernel(spin_x2, precision, method, lanes, small);
+    void* k = select_kernel(spin_x2, precision, method, small);
     if (!k) return cudaErrorInvalidValue;
-    size_t smem_max = integrate_smem_bytes(spin_x2, precision, lanes, 256);
+    size_t smem_max = integrate_smem_bytes(spin_x2, precision, 256);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     if (e != cudaSuccess) return e;
-    size_t smem = integrate_smem_bytes(spin_x2, precision, lanes, block);
+    size_t smem = integrate_smem_bytes(spin_x2, precision, block);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, smem);
 }
 
-cudaError_t launch_integrate(int spin_x2, int precision, int method, int lanes, int block, int grid, bool small,
+// Tiles of a launch: whole waves of bulk tiles (lanes_bulk lanes per sample)
+// while at least one full wave of them fits, then the remaining samples in
+// tail tiles with as many lanes per sample as every simulation of the launch
+// has segments (one segment per lane), which end the launch in finer steps.
+void integrate_tiles(int64_t total, int lanes_bulk, int block, int64_t wave_blocks, int min_seg_log2,
+                     IntegrateArgs& a)
+{
+    int lg = 0;
+    while ((1 << lg) < lanes_bulk && lg < min_seg_log2) lg++;
+    const int64_t spb_bulk = block >> lg;
+    const int64_t rounds = total / (wave_blocks * spb_bulk);
+    a.lg_bulk = lg;
+    a.lg_tail = min_seg_log2;
+    a.n_bulk_tiles = rounds * wave_blocks;
+    a.bulk_samples = a.n_bulk_tiles * spb_bulk;
+    const int64_t spb_tail = block >> a.lg_tail;
+    a.n_tiles = a.n_bulk_tiles + (total - a.bulk_samples + spb_tail - 1) / spb_tail;
+}
+
+cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, int grid, bool small,
                              const IntegrateArgs& a, cudaStream_t stream)
 {
-    void* k = select_kernel(spin_x2, precision, method, lanes, small);
-    if (!k || block % 32 != 0 || block < 32 || block > 256 || grid < 1) return cudaErrorInvalidValue;
-    size_t smem = integrate_smem_bytes(spin_x2, precision, lanes, block);
+    void* k = select_kernel(spin_x2, precision, method, small);
+    if (!k || block % 32 != 0 || block < 32 || block > 256 || grid < 1 || a.lg_bulk < 0 || a.lg_bulk > kSegLog2 ||
+        a.lg_tail < 0 || a.lg_tail > kSegLog2)
+        return cudaErrorInvalidValue;
+    size_t smem = integrate_smem_bytes(spin_x2, precision, block);
     IntegrateArgs args = a;
     void* params[] = {&args};
     return cudaLaunchKernel(k, dim3(grid), dim3(block), params, smem, stream);

@@ -9,7 +9,16 @@
 namespace spinsim {
 
 constexpr int kMaxPulses = 4;
-constexpr int kSegments = 4;             // canonical split of one U_k's L steps (fixed tree)
+// A sample's L steps are split into 2^seg_log2 canonical segments (at most
+// kSegments) reduced by a fixed binary tree; the split depends on L alone.
+constexpr int kSegLog2 = 3;
+constexpr int kSegments = 1 << kSegLog2;
+// Segments of a sample of L steps: one for L < 4, then 2, 4, 8 from L = 4, 16,
+// 128, so that the tree's 2^s - 1 extra products stay a small fraction of the
+// 2 L step products (CF4) while long samples can be shared by up to 8 lanes
+// (measured on GB300 at L = 100: 4 segments beat 8 for one long simulation
+// and for a batch alike).
+inline int seg_log2_of(int64_t L) { return L >= 128 ? 3 : (L >= 16 ? 2 : (L >= 4 ? 1 : 0)); }
 
 // ------------------------------------------------------- chain-tree geometry
 // The ordered product psi_k = U_k ... U_0 psi_init is a tree scan per
@@ -59,7 +68,8 @@ struct DevSim {
     int64_t sample_offset;       // first sample of this simulation in the operator buffer
     int32_t chain_run;           // samples per lane run at the bottom of the chain tree
     int32_t chain_top;           // level of the chain tree's top node
-    int64_t chain_pad;
+    int32_t seg_log2;            // the sample's L steps in 2^seg_log2 canonical segments
+    int32_t seg_pad;
     double t_start, dt_out, dt;  // dt = dt_out / L
     double drive_hz, drive_phase;
     double w_co0, w_counter0;    // frame: 2 pi (f_d - B), 2 pi (f_d + B); lab: 2 pi f_d, 2 pi f_d
@@ -109,7 +119,9 @@ struct IntegrateArgs {
     double* U;                        // operator buffer: spin-one 18, spin-half 4 doubles per sample
     int tau;
     unsigned long long* tile_counter; // zeroed before the launch
-    int64_t n_tiles;
+    int64_t n_tiles;                  // bulk tiles, then tail tiles
+    int64_t n_bulk_tiles, bulk_samples;
+    int lg_bulk, lg_tail;             // log2 of lanes per sample in bulk / tail tiles
 };
 
 // What launch_chain runs: the whole scan, only the up-sweep (the products:
@@ -272,11 +284,17 @@ bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, in
 // Host-side launchers (integrate.cu, chain.cu).  precision: 0 FP64, 1 FP32-bulk;
 // small: the small-angle variant (FP32-bulk only, all requests of the launch
 // satisfying small_angle_request).
-cudaError_t launch_integrate(int spin_x2, int precision, int method, int lanes, int block, int grid, bool small,
+// launch_integrate: `a` must carry the tile plan of integrate_tiles.
+cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, int grid, bool small,
                              const IntegrateArgs& a, cudaStream_t stream);
-size_t integrate_smem_bytes(int spin_x2, int precision, int lanes, int block);
-cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int lanes, int block, bool small,
-                                int* blocks_per_sm);
+size_t integrate_smem_bytes(int spin_x2, int precision, int block);
+cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int block, bool small, int* blocks_per_sm);
+// integrate_tiles: the tile plan of `total` samples for bulk lanes per sample
+// `lanes_bulk` (1, 2, 4 or 8, at most 2^min_seg_log2), `block` threads and
+// `wave_blocks` resident blocks; the tail uses 2^min_seg_log2 lanes per sample,
+// min_seg_log2 the smallest segment split among the launch's simulations.
+void integrate_tiles(int64_t total, int lanes_bulk, int block, int64_t wave_blocks, int min_seg_log2,
+                     IntegrateArgs& a);
 // launch_chain: the chain kernels of a batch in order on `stream`; *kernels
 // receives how many were launched.
 cudaError_t launch_chain(int spin_x2, const ChainArgs& a, int n_sm, cudaStream_t stream, int* kernels);

@@ -76,6 +76,7 @@ void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K,
     const spinsim_field& f = r.field;
     d.K = K;
     d.L = L;
+    d.seg_log2 = seg_log2_of(L);
     d.t_start = r.t_start;
     d.dt_out = r.dt_out;
     d.dt = r.dt_out / (double)L;

@@ -110,6 +110,7 @@ struct Group {
     std::vector<int64_t> idx;      // request indices
     int64_t samples = 0;
     double steps = 0.0;            // CF4 (or sampling) steps of the group
+    int min_seg_log2 = kSegLog2;   // smallest canonical segment split among the group's simulations
     int levels = 1;                // chain-tree levels of the tallest simulation
     int64_t nodes[kMaxLevels] = {};  // chain-tree nodes per level, all simulations
     size_t sims_off = 0, soff_off = 0, loff_off = 0, counter_off = 0, U_off = 0, chain_off = 0;
@@ -191,7 +192,7 @@ struct spinsim_s {
     Arena arena;
     PinnedBuf pinned;
     spinsim_launch_info last{};
-    std::map<std::tuple<int, int, int, int>, int> occ;   // (spin, lanes, block, small) -> resident blocks per SM
+    std::map<std::tuple<int, int, int>, int> occ;   // (spin, block, small) -> resident blocks per SM
     std::vector<char> table_tmp;                     // host copy of the next parameter table
     // graph cache: one batch signature
     std::vector<uint64_t> graph_sig;
@@ -290,6 +291,7 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
                 g.small = g.small && checked[i].small;
                 g.samples += checked[i].K;
                 g.steps += (double)checked[i].K * (double)checked[i].L;
+                g.min_seg_log2 = std::min(g.min_seg_log2, seg_log2_of(checked[i].L));
                 const ChainGeom cg = chain_geom(checked[i].K);
                 g.levels = std::max(g.levels, cg.top + 1);
                 for (int l = 0; l <= cg.top; l++) g.nodes[l] += cg.nodes[l];
@@ -381,9 +383,9 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
 
 // Resident blocks per SM of an integrate shape; computed outside stream
 // capture (it sets the kernel's shared-memory limit) and cached.
-int occupancy(spinsim_s* h, int spin, int lanes, int block, bool small, bool capturing, int* per_sm)
+int occupancy(spinsim_s* h, int spin, int block, bool small, bool capturing, int* per_sm)
 {
-    auto key = std::make_tuple(spin, lanes, block, (int)small);
+    auto key = std::make_tuple(spin, block, (int)small);
     auto it = h->occ.find(key);
     if (it != h->occ.end()) {
         *per_sm = it->second;
@@ -391,7 +393,7 @@ int occupancy(spinsim_s* h, int spin, int lanes, int block, bool small, bool cap
     }
     if (capturing) return SPINSIM_E_UNSUPPORTED;
     int b = 0;
-    if (integrate_occupancy(spin, h->cfg.precision, h->cfg.method, lanes, block, small, &b) != cudaSuccess) {
+    if (integrate_occupancy(spin, h->cfg.precision, h->cfg.method, block, small, &b) != cudaSuccess) {
         cudaGetLastError();
         return SPINSIM_E_CUDA;
     }
@@ -413,8 +415,8 @@ int size_bucket(int64_t samples)
 // tuned by timing trial launches, once per (device, key), and cached.  The
 // resident blocks per SM are the explicit value or the most the kernel allows
 // (fewer never paid on GB300: the tail they save costs more in issue rate).
-int choose_shape(spinsim_s* h, int spin, bool small, double steps, IntegrateArgs a, cudaStream_t stream,
-                 bool capturing, int& lanes, int& block, int& grid)
+int choose_shape(spinsim_s* h, int spin, bool small, double steps, int min_seg_log2, IntegrateArgs& a,
+                 cudaStream_t stream, bool capturing, int& lanes, int& block, int& grid)
 {
     const int precision = h->cfg.precision;
     const int method = h->cfg.method;
@@ -423,7 +425,7 @@ int choose_shape(spinsim_s* h, int spin, bool small, double steps, IntegrateArgs
     int bps = h->cfg.blocks_per_sm;
     const bool full_trial = steps <= kFullTrialSteps;
     if (lanes == 0 || block == 0) {
-        TuneKey key{spin, precision, method, h->tau, (int)small, (int64_t)size_bucket(a.total_samples)};
+        TuneKey key{spin, precision, method, h->tau, (int)small, (int64_t)size_bucket(a.total_samples) * 8 + min_seg_log2};
         bool found = false;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -435,36 +437,39 @@ int choose_shape(spinsim_s* h, int spin, bool small, double steps, IntegrateArgs
             }
         }
         if (!found) {
-            const int lane_opts[3] = {1, 2, 4};
+            // bulk tiles: one lane per sample unless configured (with the
+            // per-tile epilogue more lanes per sample never paid on GB300;
+            // the samples after the last whole wave use more anyway)
+            const int lane_opts[1] = {1};
             const int block_opts[3] = {64, 128, 256};
-            int best_l = lanes ? lanes : 2, best_b = block ? block : 128;
+            int best_l = lanes ? lanes : 1, best_b = block ? block : 128;
             if (!capturing) {
                 float best = 1e30f;
                 cudaEvent_t e0, e1;
                 if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SPINSIM_E_CUDA;
-                for (int li = 0; li < 3; li++) {
+                for (int li = 0; li < 1; li++) {
                     const int L = lanes ? lanes : lane_opts[li];
                     if (lanes && li > 0) break;
+                    if (!lanes && L > (1 << min_seg_log2)) break;   // no more lanes than segments
                     for (int bi = 0; bi < 3; bi++) {
                         const int B = block ? block : block_opts[bi];
                         if (block && bi > 0) break;
                         int per_sm = 0;
-                        if (occupancy(h, spin, L, B, small, false, &per_sm) != SPINSIM_OK || per_sm < 1) continue;
+                        if (occupancy(h, spin, B, small, false, &per_sm) != SPINSIM_OK || per_sm < 1) continue;
                         const int P = bps ? std::min(bps, per_sm) : per_sm;
+                        const int64_t wave_blocks = (int64_t)h->n_sm * P;
                         IntegrateArgs t = a;
-                        const int spb = B / L;
                         if (!full_trial) {
                             // a prefix of at most 4 full waves of this shape
-                            const int64_t wave = (int64_t)h->n_sm * P * spb;
-                            t.total_samples = std::min<int64_t>(a.total_samples, 4 * wave);
+                            t.total_samples = std::min<int64_t>(a.total_samples, 4 * wave_blocks * (B / L));
                         }
-                        t.n_tiles = (t.total_samples + spb - 1) / spb;
-                        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(t.n_tiles, (int64_t)h->n_sm * P));
+                        integrate_tiles(t.total_samples, L, B, wave_blocks, min_seg_log2, t);
+                        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(t.n_tiles, wave_blocks));
                         float ms_best = 1e30f;
                         for (int rep = 0; rep < 2; rep++) {
                             cudaMemsetAsync(a.tile_counter, 0, sizeof(unsigned long long), stream);
                             cudaEventRecord(e0, stream);
-                            launch_integrate(spin, precision, method, L, B, g, small, t, stream);
+                            launch_integrate(spin, precision, method, B, g, small, t, stream);
                             cudaEventRecord(e1, stream);
                             if (cudaEventSynchronize(e1) != cudaSuccess) {
                                 cudaEventDestroy(e0);
@@ -493,13 +498,13 @@ int choose_shape(spinsim_s* h, int spin, bool small, double steps, IntegrateArgs
         }
     }
     int per_sm = 0;
-    int st = occupancy(h, spin, lanes, block, small, capturing, &per_sm);
+    int st = occupancy(h, spin, block, small, capturing, &per_sm);
     if (st != SPINSIM_OK) return st;
     per_sm = std::max(per_sm, 1);
     if (bps > 0) per_sm = std::min(per_sm, bps);
-    const int spb = block / lanes;
-    const int64_t tiles = (a.total_samples + spb - 1) / spb;
-    grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)h->n_sm * per_sm));
+    const int64_t wave_blocks = (int64_t)h->n_sm * per_sm;
+    integrate_tiles(a.total_samples, lanes, block, wave_blocks, min_seg_log2, a);
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.n_tiles, wave_blocks));
     return SPINSIM_OK;
 }
 
@@ -579,15 +584,14 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
         if (g.samples > 0) {
             if (phase == kPhaseFinish && pg >= 0) prof_record(h->prof[pg][0]);
             if (phase != kPhaseFinish) {
-                st = choose_shape(h, g.spin_x2, g.small, g.steps, ia, stream, capturing, lanes, block, grid);
+                st = choose_shape(h, g.spin_x2, g.small, g.steps, g.min_seg_log2, ia, stream, capturing, lanes, block,
+                                  grid);
                 if (st != SPINSIM_OK) return st;
-                const int spb = block / lanes;
-                ia.n_tiles = (g.samples + spb - 1) / spb;
                 if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
                     return SPINSIM_E_CUDA;
                 if (pg >= 0) prof_record(h->prof[pg][0]);
-                if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, lanes, block, grid, g.small, ia,
-                                     stream) != cudaSuccess)
+                if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, block, grid, g.small, ia, stream) !=
+                    cudaSuccess)
                     return SPINSIM_E_CUDA;
                 kernels += 1;
             }
@@ -694,7 +698,7 @@ int spinsim_create(const spinsim_config* cfg, spinsim_handle* out)
     if (cfg->method < 0 || cfg->method > 2 || cfg->precision < 0 || cfg->precision > 1 ||
         cfg->trotter_squares < -1 || cfg->trotter_squares > 40 ||
         !(cfg->lanes_per_sample == 0 || cfg->lanes_per_sample == 1 || cfg->lanes_per_sample == 2 ||
-          cfg->lanes_per_sample == 4) ||
+          cfg->lanes_per_sample == 4 || cfg->lanes_per_sample == 8) ||
         !(cfg->threads_per_block == 0 || cfg->threads_per_block == 64 || cfg->threads_per_block == 128 ||
           cfg->threads_per_block == 256) ||
         cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32 || cfg->mem_budget < 0)

@@ -58,7 +58,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     if (cfg->method < 0 || cfg->method > 2 || cfg->precision < 0 || cfg->precision > 1 ||
         cfg->trotter_squares < -1 || cfg->trotter_squares > 40 ||
         !(cfg->lanes_per_sample == 0 || cfg->lanes_per_sample == 1 || cfg->lanes_per_sample == 2 ||
-          cfg->lanes_per_sample == 4) ||
+          cfg->lanes_per_sample == 4 || cfg->lanes_per_sample == 8) ||
         !(cfg->threads_per_block == 0 || cfg->threads_per_block == 64 || cfg->threads_per_block == 128 ||
           cfg->threads_per_block == 256) ||
         cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32)
@@ -138,10 +138,10 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     if (K > 0) {
         int n_sm = 0;
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
-        const int lanes = cfg->lanes_per_sample ? cfg->lanes_per_sample : 2;
+        const int lanes = cfg->lanes_per_sample ? cfg->lanes_per_sample : 1;
         const int block = cfg->threads_per_block ? cfg->threads_per_block : 128;
         int per_sm = 0;
-        if (integrate_occupancy(spin, cfg->precision, cfg->method, lanes, block, small, &per_sm) != cudaSuccess) {
+        if (integrate_occupancy(spin, cfg->precision, cfg->method, block, small, &per_sm) != cudaSuccess) {
             cudaGetLastError();
             return res->status = SPINSIM_E_CUDA;
         }
@@ -153,14 +153,14 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         ia.U = reinterpret_cast<double*>(base + U_off);
         ia.tau = tau;
         ia.tile_counter = reinterpret_cast<unsigned long long*>(base + counter_off);
-        const int spb = block / lanes;
-        ia.n_tiles = (K + spb - 1) / spb;
         if (cfg->blocks_per_sm > 0) per_sm = std::min(per_sm, cfg->blocks_per_sm);
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ia.n_tiles, (int64_t)n_sm * std::max(per_sm, 1)));
+        const int64_t wave_blocks = (int64_t)n_sm * std::max(per_sm, 1);
+        integrate_tiles(K, lanes, block, wave_blocks, seg_log2_of(L), ia);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ia.n_tiles, wave_blocks));
         // the tile counter keeps the previous call's value: clear it
         if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
             return res->status = SPINSIM_E_CUDA;
-        if (launch_integrate(spin, cfg->precision, cfg->method, lanes, block, grid, small, ia, stream) != cudaSuccess)
+        if (launch_integrate(spin, cfg->precision, cfg->method, block, grid, small, ia, stream) != cudaSuccess)
             return res->status = SPINSIM_E_CUDA;
         ChainArgs ca;
         ca.sims = ia.sims;
