@@ -25,6 +25,7 @@ _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "libspinsim_oracle.so")
 
 MAX_PULSES = 4
+MAX_TONES = 3
 FIELD_KEYS = ("bias_hz", "drive_x_hz", "drive_y_hz", "drive_hz", "drive_phase",
               "quad_hz", "pulses")
 
@@ -45,6 +46,12 @@ class _Field(ctypes.Structure):
         ("pulse_amp_hz", ctypes.c_double * MAX_PULSES),
         ("pulse_centre_s", ctypes.c_double * MAX_PULSES),
         ("pulse_width_s", ctypes.c_double * MAX_PULSES),
+        ("n_tones", ctypes.c_int32),
+        ("pad2_", ctypes.c_int32),
+        ("tone_x_hz", ctypes.c_double * MAX_TONES),
+        ("tone_y_hz", ctypes.c_double * MAX_TONES),
+        ("tone_hz", ctypes.c_double * MAX_TONES),
+        ("tone_phase", ctypes.c_double * MAX_TONES),
     ]
 
 
@@ -126,6 +133,12 @@ def _field(f: dict) -> _Field:
         s.pulse_width_s[i] = width
         if kind == "sine":
             s.pulse_sine_mask |= 1 << i
+    tones = list(f.get("tones", ()))
+    if len(tones) > MAX_TONES:
+        raise ValueError("at most 3 further tones")
+    s.n_tones = len(tones)
+    for j, (x, y, hz, ph) in enumerate(tones):
+        s.tone_x_hz[j], s.tone_y_hz[j], s.tone_hz[j], s.tone_phase[j] = x, y, hz, ph
     return s
 
 

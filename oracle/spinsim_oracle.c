@@ -63,6 +63,7 @@ typedef double complex cplx;
 /* Eq. neural_pulse, Sec. 1.3.1).                                            */
 /* ------------------------------------------------------------------------- */
 #define OR_MAX_PULSES 4
+#define OR_MAX_TONES 3   /* drive tones besides the first (the paper's "arbitrary number of tones") */
 
 typedef struct {
     double bias_hz;      /* w_z constant part: 2 pi bias_hz                         */
@@ -79,6 +80,15 @@ typedef struct {
     double pulse_amp_hz[OR_MAX_PULSES];
     double pulse_centre_s[OR_MAX_PULSES];
     double pulse_width_s[OR_MAX_PULSES];
+    /* further drive tones j < n_tones, each like the first:
+     * w_x += 2 pi tone_x_hz[j] cos(2 pi tone_hz[j] t + tone_phase[j]),
+     * w_y += 2 pi tone_y_hz[j] sin(2 pi tone_hz[j] t + tone_phase[j])                   */
+    int32_t n_tones;
+    int32_t pad2_;
+    double tone_x_hz[OR_MAX_TONES];
+    double tone_y_hz[OR_MAX_TONES];
+    double tone_hz[OR_MAX_TONES];
+    double tone_phase[OR_MAX_TONES];
 } oracle_field;
 
 /* Field functions (w_x, w_y, w_z, w_q) at time t, in rad/s. */
@@ -98,6 +108,11 @@ void oracle_field_sample(const oracle_field* f, double t, double w[4])
     }
     w[0] = 2.0 * OR_PI * f->drive_x_hz * cos(phase);
     w[1] = 2.0 * OR_PI * f->drive_y_hz * sin(phase);
+    for (int j = 0; j < f->n_tones && j < OR_MAX_TONES; j++) {
+        double ph = 2.0 * OR_PI * f->tone_hz[j] * t + f->tone_phase[j];
+        w[0] += 2.0 * OR_PI * f->tone_x_hz[j] * cos(ph);
+        w[1] += 2.0 * OR_PI * f->tone_y_hz[j] * sin(ph);
+    }
     w[2] = 2.0 * OR_PI * bz;
     w[3] = 2.0 * OR_PI * f->quad_hz;
 }

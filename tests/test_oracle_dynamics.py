@@ -42,6 +42,21 @@ def test_field_sample_formula(oracle_mod):
                                TWO_PI * 400], rtol=1e-13, atol=1e-9)
 
 
+def test_field_sample_formula_extra_tones(oracle_mod):
+    """Further drive tones add to w_x and w_y like the first (Sec. 1.4: drives of
+    any number of tones and polarisations)."""
+    tones = [(1.5e3, -0.4e3, 703e3, 1.1), (0.0, 0.8e3, 698.5e3, -0.7), (-0.3e3, 0.3e3, 1.2e3, 2.9)]
+    f = W.field(bias_hz=700e3, drive_x_hz=2e3, drive_y_hz=0.5e3, drive_hz=701e3, drive_phase=0.3, tones=tones)
+    for t in (0.0, 0.0493, 0.0999):
+        w = oracle_mod.field_sample(f, t)
+        ph = TWO_PI * 701e3 * t + 0.3
+        wx = TWO_PI * 2e3 * np.cos(ph) + sum(TWO_PI * x * np.cos(TWO_PI * hz * t + p) for x, _, hz, p in tones)
+        wy = TWO_PI * 0.5e3 * np.sin(ph) + sum(TWO_PI * y * np.sin(TWO_PI * hz * t + p) for _, y, hz, p in tones)
+        assert np.allclose(w[:3], [wx, wy, TWO_PI * 700e3], rtol=1e-13, atol=1e-8)
+    with pytest.raises(ValueError):
+        oracle_mod.field_sample(W.field(tones=tones + [(1.0, 1.0, 1.0, 0.0)]), 0.0)
+
+
 def test_counts(oracle_mod):
     assert oracle_mod.counts(0.0, 5e-3, 1e-7, 1e-5) == (500, 100)
     assert oracle_mod.counts(0.0, 0.1, 1e-8, 1e-6) == (100000, 100)
@@ -205,6 +220,38 @@ def test_against_adaptive_ode_solver(oracle_mod, spin_x2, frame):
     rng = np.random.default_rng(17)
     psi0 = W.random_state(2 if spin_x2 == 1 else 3, rng)
     out = oracle_mod.simulate(spin_x2, f, 0.0, 6e-4, 2e-7, 2e-5, psi0, rotating_frame=frame)
+    ts = times(0.0, 6e-4, 2e-5)
+    ref = ivp_reference(spin_x2, f, psi0, ts, oracle_mod)
+    assert np.abs(out["states"] - ref).max() < 1e-9
+
+
+@pytest.mark.parametrize("spin_x2", [1, 2])
+def test_circular_drive_split_over_tones(oracle_mod, spin_x2):
+    """The circular drive of the exact-solution case carried by the first tone
+    and two further tones at the same frequency and phase (amplitudes summing
+    to the drive's), plus a zero-amplitude tone elsewhere: the exact solution."""
+    f0, fd, om, q = 50e3, 49.2e3, 4e3, (700.0 if spin_x2 == 2 else 0.0)
+    f = W.field(bias_hz=f0, drive_x_hz=0.5 * om, drive_y_hz=0.25 * om, drive_hz=fd, quad_hz=q,
+                tones=[(0.25 * om, 0.5 * om, fd, 0.0), (0.25 * om, 0.25 * om, fd, 0.0), (0.0, 0.0, 3e3, 1.0)])
+    rng = np.random.default_rng(11)
+    psi0 = W.random_state(2 if spin_x2 == 1 else 3, rng)
+    out = oracle_mod.simulate(spin_x2, f, 0.0, 1e-3, 5e-8, 1e-4, psi0, rotating_frame=True)
+    ts = times(0.0, 1e-3, 1e-4)
+    ref = circular_exact(spin_x2, TWO_PI * f0, TWO_PI * fd, TWO_PI * om, TWO_PI * q, psi0, ts)
+    assert np.abs(out["states"] - ref).max() < 1e-10
+
+
+@pytest.mark.parametrize("spin_x2", [1, 2])
+def test_extra_tones_against_adaptive_ode_solver(oracle_mod, spin_x2):
+    """Four tones of different frequencies, phases and polarisations (two near
+    resonance, one detuned by 40 kHz, one at 7 kHz) with a Gaussian pulse vs
+    scipy DOP853."""
+    f = W.field(bias_hz=20e3, drive_x_hz=2e3, drive_hz=20.3e3, quad_hz=300.0 if spin_x2 == 2 else 0.0,
+                pulses=[(400.0, 0.3e-3, 0.1e-3)],
+                tones=[(1.2e3, 0.9e3, 19.6e3, 0.8), (0.0, 1.5e3, 60e3, -1.3), (0.7e3, 0.0, 7e3, 2.2)])
+    rng = np.random.default_rng(23)
+    psi0 = W.random_state(2 if spin_x2 == 1 else 3, rng)
+    out = oracle_mod.simulate(spin_x2, f, 0.0, 6e-4, 1e-7, 2e-5, psi0, rotating_frame=True)
     ts = times(0.0, 6e-4, 2e-5)
     ref = ivp_reference(spin_x2, f, psi0, ts, oracle_mod)
     assert np.abs(out["states"] - ref).max() < 1e-9

@@ -33,6 +33,11 @@ MUTATIONS = {
                                "bz += f->pulse_amp_hz[p] * sin(OR_PI * cyc);"),
     "sine_pulse_window": ("if (cyc >= 0.0 && cyc < 1.0)", "if (cyc >= 0.0 && cyc < 0.5)"),
     "drive_y_cos": ("w[1] = 2.0 * OR_PI * f->drive_y_hz * sin(phase);", "w[1] = 2.0 * OR_PI * f->drive_y_hz * cos(phase);"),
+    "tone_y_cos": ("w[1] += 2.0 * OR_PI * f->tone_y_hz[j] * sin(ph);", "w[1] += 2.0 * OR_PI * f->tone_y_hz[j] * cos(ph);"),
+    "tone_phase_ignored": ("double ph = 2.0 * OR_PI * f->tone_hz[j] * t + f->tone_phase[j];",
+                           "double ph = 2.0 * OR_PI * f->tone_hz[j] * t;"),
+    "tones_dropped": ("for (int j = 0; j < f->n_tones && j < OR_MAX_TONES; j++) {",
+                      "for (int j = 0; j < f->n_tones - 1 && j < OR_MAX_TONES; j++) {"),
     "jy_sign": ("J[1][0][1] = -I * r; J[1][1][0] = I * r;", "J[1][0][1] = I * r; J[1][1][0] = -I * r;"),
     "chain_transposed": ("s += U[i][j] * psi[j];", "s += U[j][i] * psi[j];"),
     "midpoint_node": ("field_in_frame(f, t + 0.5 * dt, t_ref, w_r, h);", "field_in_frame(f, t + dt, t_ref, w_r, h);"),
