@@ -8,7 +8,7 @@ delta_t = 10 ns and Delta_t = 1 us (1e5 samples x 100 CF4 steps) -- run in
 FP32-bulk precision with the FP64 chain, inputs resident on the device.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sensing|sweep|serve|neural] [--precision fp32|fp64]
+                    [--workload sensing|sweep|serve|neural|multitone] [--precision fp32|fp64]
 
 Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs its own
 copy of the workload (weak scaling, no data-path collective); the timing is
@@ -41,15 +41,18 @@ L2_FLUSH_BYTES = 256 << 20
 INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 67072}
 
 
-def algorithmic_flops_per_step(spin_x2: int, tau: int) -> float:
+def algorithmic_flops_per_step(spin_x2: int, tau: int, n_tones: int = 0) -> float:
     """Algorithmic FP32 flops of one spin-one CF4 step (FMA = 2 flops): two
     Lie-Trotter exponentials with tau residual squarings of a 3x3 complex
     matrix (27 complex MACs = 216 flops each) plus ~100 flops to build T, two
     3x3 complex products (216 each) and the field at two nodes: 432 tau + 650.
-    The timed workloads are spin-one only."""
+    Each further drive tone adds its two phasors at both nodes (a 3-term
+    sine/cosine series and four complex multiply-adds, ~40 flops per node) and
+    its share of both exponents (8): 88 per tone.  The timed workloads are
+    spin-one only."""
     if spin_x2 != 2:
         raise ValueError("the flop model covers spin-one steps only")
-    return 432.0 * tau + 650.0
+    return 432.0 * tau + 650.0 + 88.0 * n_tones
 
 
 class ClockSampler:
@@ -168,6 +171,11 @@ def run_ours(args, world, rank, local):
         workload = ("spin-one, the paper's benchmark field (Eq. neural_pulse): bias 700 kHz, drive 2x1 kHz at "
                     "700 kHz, 70 Hz single sine cycle of 1 ms on J_z at 50 ms; 100 ms, dt 100 ns, dt_out 1 us "
                     "(1e5 samples x 10 CF4 steps)")
+    elif args.workload == "multitone":
+        reqs = [W.multitone_sensing()]
+        workload = ("spin-one sensing field plus three further drive tones (1 kHz circular at +500 Hz, 0.5 kHz "
+                    "linear at -2 kHz, 0.8 kHz y at +5 kHz); 100 ms, dt 10 ns, dt_out 1 us "
+                    "(1e5 samples x 100 CF4 steps)")
     elif args.workload == "sweep":
         reqs = W.sweep(4096, seed=W.SEED + rank)
         workload = ("batched spin-one sweep: 4096 simulations, bias U(600,800) kHz, Rabi U(0.5,2) kHz, detuning "
@@ -214,7 +222,8 @@ def run_ours(args, world, rank, local):
     ms_per_step = total_s * 1e3 / args.steps
 
     # ---- roofline of the dominant kernel (integrate), from its live CUDA events
-    flops = sum(W.total_steps([r]) * algorithmic_flops_per_step(r["spin_x2"], t) for r, t in zip(reqs, taus))
+    flops = sum(W.total_steps([r]) * algorithmic_flops_per_step(r["spin_x2"], t, len(r["field"].get("tones", ())))
+                for r, t in zip(reqs, taus))
     mean_int = float(np.mean(integ_ms))
     achieved = flops / (mean_int / 1e3) / 1e12
     # DRAM traffic of one integrate launch from the ncu capture of this workload
@@ -268,7 +277,7 @@ def run_ours(args, world, rank, local):
     if clk:
         line["clocks"] = clk
     # ---- rank 0: accuracy vs the FP64 oracle, oracle CPU baseline, FP64-plain kernel
-    if rank == 0 and args.workload in ("sensing", "neural") and not args.no_cpu_baseline:
+    if rank == 0 and args.workload in ("sensing", "neural", "multitone") and not args.no_cpu_baseline:
         from oracle import oracle as O   # the CPU baseline leg: the oracle as it stands
         O.build()
         r = reqs[0]
@@ -408,7 +417,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("sensing", "sweep", "serve", "neural"), default="sensing")
+    ap.add_argument("--workload", choices=("sensing", "sweep", "serve", "neural", "multitone"), default="sensing")
     ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
     ap.add_argument("--tau", type=int, default=-1)
     ap.add_argument("--serve-requests", type=int, default=20000)

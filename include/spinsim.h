@@ -39,8 +39,9 @@
 extern "C" {
 #endif
 
-#define SPINSIM_ABI_VERSION 1
+#define SPINSIM_ABI_VERSION 2
 #define SPINSIM_MAX_PULSES 4
+#define SPINSIM_MAX_TONES 3
 
 /* Status codes (negative = error).  A call returns the first error it meets;
  * spinsim_result.status carries each request's own status. */
@@ -107,7 +108,9 @@ typedef struct {
 
 /* The fixed parameterised field family (Hz, seconds, radians):
  *   w_x(t) = 2 pi drive_x_hz cos(2 pi drive_hz t + drive_phase)
+ *            + sum_j 2 pi tone_x_hz[j] cos(2 pi tone_hz[j] t + tone_phase[j])
  *   w_y(t) = 2 pi drive_y_hz sin(2 pi drive_hz t + drive_phase)
+ *            + sum_j 2 pi tone_y_hz[j] sin(2 pi tone_hz[j] t + tone_phase[j])
  *   w_z(t) = 2 pi (bias_hz + sum_p pulse_amp_hz[p] shape_p(t))
  *   w_q(t) = 2 pi quad_hz                       (spin-one only; ignored for spin-half)
  * with, for pulse p (c = pulse_centre_s[p], w = pulse_width_s[p] > 0):
@@ -117,7 +120,9 @@ typedef struct {
  *   else 0 (c is the start of the cycle, w its period).
  * A linearly polarised drive "2 R cos(2 pi f t)" is drive_x_hz = 2R, drive_y_hz = 0;
  * a circularly polarised one has drive_x_hz = drive_y_hz.  The detuning of the
- * drive is drive_hz - bias_hz. */
+ * drive is drive_hz - bias_hz.  Tones j < n_tones are further drive terms of the
+ * same form (a multi-tone drive of any polarisations, Sec. 1.4); requests with
+ * tones run on a kernel variant that evaluates them, the others are unaffected. */
 typedef struct {
     double bias_hz;
     double drive_x_hz;
@@ -130,6 +135,12 @@ typedef struct {
     double pulse_amp_hz[SPINSIM_MAX_PULSES];
     double pulse_centre_s[SPINSIM_MAX_PULSES];
     double pulse_width_s[SPINSIM_MAX_PULSES];   /* standard deviation, > 0 when used       */
+    int32_t n_tones;              /* 0..SPINSIM_MAX_TONES further drive tones                */
+    int32_t reserved;             /* ignored                                                 */
+    double tone_x_hz[SPINSIM_MAX_TONES];
+    double tone_y_hz[SPINSIM_MAX_TONES];
+    double tone_hz[SPINSIM_MAX_TONES];
+    double tone_phase[SPINSIM_MAX_TONES];
 } spinsim_field;
 
 /* One simulation (Sec. 1.2.4 problem statement). */

@@ -193,6 +193,9 @@ struct SampleCtx {
     R q1;                           // first-order Q coefficient of one exponential: 3 qd3 2^tau
     R dt, c1, c2;
     R amp[kMaxPulses], u0[kMaxPulses], invw[kMaxPulses], ghat[kMaxPulses];
+    // further tones (the tones variant only): e^{i beta_j}, in-frame rates, Om+-_j
+    R tbr[kMaxTones], tbi[kMaxTones], tco[kMaxTones], tct[kMaxTones], tomp[kMaxTones], tomm[kMaxTones];
+    int nt;
     int np;
     int ng;                         // pulses [0, ng) Gaussian, [ng, np) single sine cycles
     int tau;
@@ -219,16 +222,23 @@ struct SampleExact {
     double eb_re, eb_im;   // e^{i beta}
     double dco, dct;       // w_d - w_r, w_d + w_r (rad/s)
     double gsum;           // pulse part of w_r (rad/s)
+    double tb_re[kMaxTones], tb_im[kMaxTones];   // e^{i beta_j} of the further tones (tones variant)
 };
 
-// Drive phase beta = 2 pi frac(f_d t_{k-1}) + phase, in [-pi, pi] (FP64, a few ops).
+// Phase 2 pi frac(f t) + phase of a tone of frequency f at t, in [-pi, pi]
+// (FP64, a few ops).
+SPINSIM_HD double tone_phase_at(double hz, double phase, double t)
+{
+    double cyc = hz * t;
+    cyc -= floor(cyc);
+    double beta = kTwoPi * cyc + phase;
+    return beta - kTwoPi * rint(beta * (1.0 / kTwoPi));
+}
+
+// Drive phase beta at t_{k-1}.
 SPINSIM_HD double drive_phase_at(const DevSim& s, int64_t k)
 {
-    const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;
-    double cyc = s.drive_hz * t_prev;
-    cyc -= floor(cyc);
-    double beta = kTwoPi * cyc + s.drive_phase;
-    return beta - kTwoPi * rint(beta * (1.0 / kTwoPi));
+    return tone_phase_at(s.drive_hz, s.drive_phase, s.t_start + (double)(k - 1) * s.dt_out);
 }
 
 // Shape of z pulse p at u = (t - c_p) / w_p: a Gaussian exp(-u^2/2) (w_p the
@@ -260,7 +270,7 @@ SPINSIM_COLD R sine_cycle_cold(R u)
 // Returns gsum = sum_p amp_p ghat_p (exact products of R values, in FP64)
 // and the drive phase beta (FP64) for the epilogue.  The per-simulation
 // constants come rounded to FP32 from the host for the FP32 path.
-template <typename R, int N>
+template <typename R, int N, bool TONES = false>
 SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& beta)
 {
     const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;
@@ -321,6 +331,27 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
     }
     c.co = (R)(s.frame ? s.w_co0 - gsum : s.w_co0);
     c.counter = (R)(s.frame ? s.w_counter0 + gsum : s.w_counter0);
+    if constexpr (TONES) {
+        c.nt = s.n_tones;
+#pragma unroll
+        for (int j = 0; j < kMaxTones; j++) {
+            c.tbr[j] = c.tbi[j] = c.tco[j] = c.tct[j] = c.tomp[j] = c.tomm[j] = R(0);
+            if (j < c.nt) {
+                const SinCos<R> e = sincos_cold((R)tone_phase_at(s.tone_hz[j], s.tone_phase[j], t_prev));
+                c.tbr[j] = e.c;
+                c.tbi[j] = e.s;
+                c.tco[j] = (R)(s.frame ? s.t_co0[j] - gsum : s.t_co0[j]);
+                c.tct[j] = (R)(s.frame ? s.t_ct0[j] + gsum : s.t_ct0[j]);
+                if constexpr (sizeof(R) == 4) {
+                    c.tomp[j] = s.f_tom_plus[j];
+                    c.tomm[j] = s.f_tom_minus[j];
+                } else {
+                    c.tomp[j] = (R)s.t_om_plus[j];
+                    c.tomm[j] = (R)s.t_om_minus[j];
+                }
+            }
+        }
+    }
     return gsum;
 }
 
@@ -334,13 +365,23 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
 // exact change of variables for any constant w_r, and this one is exactly
 // the value the in-frame field subtracts, so leaving the frame undoes
 // entering it.
-template <int N>
-SPINSIM_HD void make_exact(const DevSim& s, double beta, double gsum, SampleExact& x)
+template <int N, bool TONES = false>
+SPINSIM_HD void make_exact(const DevSim& s, int64_t k, double beta, double gsum, SampleExact& x)
 {
     const SinCos<double> eb = sincos_cold(beta);
     x.eb_re = eb.c;
     x.eb_im = eb.s;
     x.gsum = gsum;
+    if constexpr (TONES) {
+        const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;
+        for (int j = 0; j < s.n_tones; j++) {
+            const SinCos<double> e = sincos_cold(tone_phase_at(s.tone_hz[j], s.tone_phase[j], t_prev));
+            x.tb_re[j] = e.c;
+            x.tb_im[j] = e.s;
+        }
+    } else {
+        (void)k;
+    }
     if (s.frame) {
         x.dco = s.w_co0 - gsum;
         x.dct = s.w_counter0 + gsum;
@@ -403,6 +444,8 @@ SPINSIM_HD cx<double> taylor_sum(const double* T, double d)
 // pulse part shifts th0 by a tiny d = gsum dt; while |d| (L + 1) <= 1e-3 the
 // cubic Taylor series of the tables is exact to rounding, otherwise the
 // closed form is used.
+// Further tones add their own terms of the same form (tones variant).
+template <bool TONES = false>
 SPINSIM_HD void first_order_exact(const DevSim& s, const SampleExact& x, double& gx, double& gy)
 {
     const cx<double> eb = cmk(x.eb_re, x.eb_im);
@@ -413,6 +456,21 @@ SPINSIM_HD void first_order_exact(const DevSim& s, const SampleExact& x, double&
     if (s.om_minus != 0.0) {
         cx<double> sct = tay ? taylor_sum(s.tay_ct, d) : node_phasor_sum(x.dct * s.dt, s.L, s.W1, s.c1, s.W2, s.c2);
         g = cadd(g, cscale(cconj(cmul(eb, sct)), s.om_minus));
+    }
+    if constexpr (TONES) {
+        const double gf = s.frame ? x.gsum : 0.0;   // pulse part of w_r
+        for (int j = 0; j < s.n_tones; j++) {
+            const cx<double> ebj = cmk(x.tb_re[j], x.tb_im[j]);
+            const cx<double> tco = tay ? taylor_sum(s.t_tay_co[j], -d)
+                                       : node_phasor_sum((s.t_co0[j] - gf) * s.dt, s.L, s.W1, s.c1, s.W2, s.c2);
+            g = cadd(g, cscale(cmul(ebj, tco), s.t_om_plus[j]));
+            if (s.t_om_minus[j] != 0.0) {
+                const cx<double> tct = tay ? taylor_sum(s.t_tay_ct[j], d)
+                                           : node_phasor_sum((s.t_ct0[j] + gf) * s.dt, s.L, s.W1, s.c1, s.W2,
+                                                             s.c2);
+                g = cadd(g, cscale(cconj(cmul(ebj, tct)), s.t_om_minus[j]));
+            }
+        }
     }
     gx = g.r * s.dt;
     gy = g.i * s.dt;
@@ -427,13 +485,36 @@ SPINSIM_HD void first_order_exact(const DevSim& s, const SampleExact& x, double&
 // with Om+- = (Ax +- Ay)/2.  The co-rotating phasor is e^{i beta} times a
 // small rotation, so the slowly varying term never goes through a large
 // angle.
+// Further tones (tones variant) add their whole in-frame field
+//   sum_j Om+_j e^{i (beta_j + (w_j - w_r) tau)} + Om-_j e^{-i (beta_j + (w_j + w_r) tau)}
+// (rad/s) as `ex`.
 template <typename R>
 struct NodeField {
     cx<R> co, ct;   // e^{i (beta + (w_d - w_r) tau)}, e^{i (beta + (w_d + w_r) tau)}
     R z;            // w_z' without the lab-frame bias
+    cx<R> ex;       // further tones' w_x' + i w_y' (tones variant)
 };
 
-template <typename R, bool SMALL = false>
+// sin and cos of an angle of any size in the bulk type, for terms whose
+// first-order part is replaced exactly at the end of the sample (FP32: the
+// fast hardware sincos on an argument reduced to [-pi, pi]).
+template <typename R>
+SPINSIM_HD void second_order_sincos(R x, R& s, R& c)
+{
+    if constexpr (sizeof(R) == 4) {
+        x = fma(R(-kTwoPi), rintf(x * R(1.0 / kTwoPi)), x);
+#ifdef __CUDA_ARCH__
+        __sincosf(x, &s, &c);
+#else
+        s = sinf(x);
+        c = cosf(x);
+#endif
+    } else {
+        sincos(x, &s, &c);
+    }
+}
+
+template <typename R, bool SMALL = false, bool TONES = false>
 SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
 {
     R s1, c1;
@@ -477,6 +558,23 @@ SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
         }
     }
     f.z = z;
+    if constexpr (TONES) {
+        cx<R> e = cmk(R(0), R(0));
+#pragma unroll
+        for (int j = 0; j < kMaxTones; j++) {
+            if (j < c.nt) {
+                R sj, cj;
+                small_sincos(c.tco[j] * tau, sj, cj);
+                e.r = fma(c.tomp[j], c.tbr[j] * cj - c.tbi[j] * sj, e.r);
+                e.i = fma(c.tomp[j], fma(c.tbr[j], sj, c.tbi[j] * cj), e.i);
+                second_order_sincos(c.tct[j] * tau, sj, cj);
+                // Om-_j conj(e^{i beta_j} e^{i w tau})
+                e.r = fma(c.tomm[j], c.tbr[j] * cj - c.tbi[j] * sj, e.r);
+                e.i = fma(-c.tomm[j], fma(c.tbr[j], sj, c.tbi[j] * cj), e.i);
+            }
+        }
+        f.ex = e;
+    }
 }
 
 // sum_i (hi_i + lo_i) x_i with one final rounding of the lo part.
@@ -497,7 +595,9 @@ SPINSIM_HD R dot4_hilo(const R* hi, const R* lo, R x0, R x1, R x2, R x3)
 // Exponent vector v = (H_bar delta_t) of one exponential from the two node
 // fields, with node weights (a, b) (swap = false) or (b, a) (swap = true):
 //   v_x + i v_y = P_a co_1 + P_b co_2 + conj(M_a ct_1 + M_b ct_2)   (w_x' + i w_y' as above)
-template <typename R>
+// Further tones (TONES): v_x + i v_y += a dt ex_1 + b dt ex_2 (weights swapped
+// likewise).
+template <typename R, bool TONES = false>
 SPINSIM_HD void exponent(const SampleCtx<R>& c, const NodeField<R>& f1, const NodeField<R>& f2,
                                          bool swap, R& vx, R& vy, R& vz)
 {
@@ -511,6 +611,10 @@ SPINSIM_HD void exponent(const SampleCtx<R>& c, const NodeField<R>& f1, const No
     vy = dot4_hilo(hi, lo, f1.co.i, f2.co.i, -f1.ct.i, -f2.ct.i);
     const R wa = swap ? c.zb : c.za, wb = swap ? c.za : c.zb;
     vz = fma(wa, f1.z, fma(wb, f2.z, c.zbias));
+    if constexpr (TONES) {
+        vx = fma(wa, f1.ex.r, fma(wb, f2.ex.r, vx));
+        vy = fma(wa, f1.ex.i, fma(wb, f2.ex.i, vy));
+    }
 }
 
 // -------------------------------------------------------------------------
@@ -791,20 +895,20 @@ SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res3<R>& x)
     }
 }
 
-template <typename R, int METHOD, bool SMALL = false>
+template <typename R, int METHOD, bool SMALL = false, bool TONES = false>
 SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res2<R>& x)
 {
     (void)tau;
     NodeField<R> f1, f2;
-    field_at<R, SMALL>(c, (lf + c.c1) * c.dt, f1);
+    field_at<R, SMALL, TONES>(c, (lf + c.c1) * c.dt, f1);
     if (METHOD == 1) f2 = f1;
-    else field_at<R, SMALL>(c, (lf + c.c2) * c.dt, f2);
+    else field_at<R, SMALL, TONES>(c, (lf + c.c2) * c.dt, f2);
     R vx, vy, vz;
-    exponent(c, f1, f2, false, vx, vy, vz);
+    exponent<R, TONES>(c, f1, f2, false, vx, vy, vz);
     if (METHOD == 0) {
         Res2<R> e1, e2;
         expm_half_res(vx, vy, vz, e1);
-        exponent(c, f1, f2, true, vx, vy, vz);
+        exponent<R, TONES>(c, f1, f2, true, vx, vy, vz);
         expm_half_res(vx, vy, vz, e2);
         res2_mul(e2, e1, x);
     } else {
@@ -816,16 +920,16 @@ SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res2<R>& x)
 // exponentials are applied one after the other, X <- E_2 (E_1 X) (the same
 // product as (E_2 E_1) X, Eq. cf4_implementation, in the same number of
 // operations), so only one step exponential is held in registers at a time.
-template <typename R, int METHOD, bool SMALL = false>
+template <typename R, int METHOD, bool SMALL = false, bool TONES = false>
 SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X)
 {
     NodeField<R> f1, f2;
-    field_at<R, SMALL>(c, (lf + c.c1) * c.dt, f1);
+    field_at<R, SMALL, TONES>(c, (lf + c.c1) * c.dt, f1);
     if (METHOD == 1) f2 = f1;
-    else field_at<R, SMALL>(c, (lf + c.c2) * c.dt, f2);
+    else field_at<R, SMALL, TONES>(c, (lf + c.c2) * c.dt, f2);
     R vx, vy, vz, wx = R(0), wy = R(0), wz = R(0);
-    exponent(c, f1, f2, false, vx, vy, vz);
-    if (METHOD == 0) exponent(c, f1, f2, true, wx, wy, wz);
+    exponent<R, TONES>(c, f1, f2, false, vx, vy, vz);
+    if (METHOD == 0) exponent<R, TONES>(c, f1, f2, true, wx, wy, wz);
     Res3<R> e, Y;
     expm_one_res_n<R, SMALL>(vx, vy, vz, c.qd3, tau, c.inv_n, c.q1, e);
     res3_mul(e, X, Y);
@@ -837,11 +941,11 @@ SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X)
     }
 }
 
-template <typename R, int METHOD, bool SMALL = false>
+template <typename R, int METHOD, bool SMALL = false, bool TONES = false>
 SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res2<R>& X)
 {
     Res2<R> x, Y;
-    step_res<R, METHOD, SMALL>(c, lf, tau, x);
+    step_res<R, METHOD, SMALL, TONES>(c, lf, tau, x);
     res2_mul(x, X, Y);
     X = Y;
 }

@@ -66,11 +66,11 @@ __device__ __forceinline__ void store_rows(const cx<double> U[3][3], cx<double> 
 }
 
 // U^r - I in FP64 from the split residual with exact first-order coefficients.
-template <typename R>
+template <bool TONES, typename R>
 __device__ __forceinline__ void promote(const Res3<R>& P, const DevSim& s, const SampleExact& x, cx<double> Y[3][3])
 {
     double gx, gy;
-    first_order_exact(s, x, gx, gy);
+    first_order_exact<TONES>(s, x, gx, gy);
     const double gz = (double)P.g[2], q3 = s.gq * (1.0 / 3.0);
     const cx<double> up = cmk(-gy * kInvSqrt2, -gx * kInvSqrt2);
     const cx<double> dn = cmk(gy * kInvSqrt2, -gx * kInvSqrt2);
@@ -87,10 +87,11 @@ __device__ __forceinline__ void promote(const Res3<R>& P, const DevSim& s, const
     Y[2][1] = cadd(Y[2][1], dn);
 }
 
+template <bool TONES>
 __device__ __forceinline__ void finish(const Res3<double>& P, const DevSim& s, const SampleExact& x, double* out)
 {
     cx<double> Y[3][3];
-    promote(P, s, x, Y);
+    promote<TONES>(P, s, x, Y);
 #pragma unroll
     for (int i = 0; i < 3; i++) Y[i][i].r += 1.0;
     store_rows(Y, cmk(x.ph_re, x.ph_im), out);
@@ -99,21 +100,22 @@ __device__ __forceinline__ void finish(const Res3<double>& P, const DevSim& s, c
 // FP32-bulk: the operator is stored as computed.  Its departure from
 // unitarity is of the order of the FP32 rounding of the second-order rest
 // (~1e-11 per sample); the chain renormalises every output state in FP64.
+template <bool TONES>
 __device__ __forceinline__ void finish(const Res3<float>& P, const DevSim& s, const SampleExact& x, double* out)
 {
     cx<double> Y[3][3];
-    promote(P, s, x, Y);
+    promote<TONES>(P, s, x, Y);
 #pragma unroll
     for (int i = 0; i < 3; i++) Y[i][i].r += 1.0;
     store_rows(Y, cmk(x.ph_re, x.ph_im), out);
 }
 
-template <typename R>
+template <bool TONES, typename R>
 __device__ __forceinline__ void promote(const Res2<R>& P, const DevSim& s, const SampleExact& x, cx<double>& a,
                                         cx<double>& b)
 {
     double gx, gy;
-    first_order_exact(s, x, gx, gy);
+    first_order_exact<TONES>(s, x, gx, gy);
     const double gz = (double)P.g[2];
     a = cmk((double)P.a.r, (double)P.a.i - 0.5 * gz);
     b = cmk((double)P.b.r + 0.5 * gy, (double)P.b.i - 0.5 * gx);
@@ -127,19 +129,21 @@ __device__ __forceinline__ void store_half(cx<double> al, cx<double> be, const S
     out[0] = a.r; out[1] = a.i; out[2] = b.r; out[3] = b.i;
 }
 
+template <bool TONES>
 __device__ __forceinline__ void finish(const Res2<double>& P, const DevSim& s, const SampleExact& x, double* out)
 {
     cx<double> a, b;
-    promote(P, s, x, a, b);
+    promote<TONES>(P, s, x, a, b);
     store_half(cmk(1.0 + a.r, a.i), b, x, out);
 }
 
 // FP32-bulk spin-half: stored as computed (see the spin-one case); an SU(2)
 // element in this form always has det 1.
+template <bool TONES>
 __device__ __forceinline__ void finish(const Res2<float>& P, const DevSim& s, const SampleExact& x, double* out)
 {
     cx<double> a, b;
-    promote(P, s, x, a, b);
+    promote<TONES>(P, s, x, a, b);
     store_half(cmk(1.0 + a.r, a.i), b, x, out);
 }
 
@@ -158,7 +162,7 @@ __device__ __forceinline__ void store_identity(int N, double* out)
 // thread's canonical sub-tree (log2 of its segment count) and its result.
 constexpr int kSlots = kSegLog2 + 1;
 
-template <int N, typename R, int METHOD, bool SMALL>
+template <int N, typename R, int METHOD, bool SMALL, bool TONES>
 __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
 {
     using Res = typename ResType<N, R>::type;
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
             if (k > 0 && lane < (1 << lg_use)) {
                 SampleCtx<R> c;
                 double beta = 0.0;
-                const double gsum = make_ctx<R, N>(s, k, c, beta);
+                const double gsum = make_ctx<R, N, TONES>(s, k, c, beta);
                 if (lane == 0) bg[slot] = make_double2(beta, gsum);
                 const int64_t L = s.L;
 #pragma unroll 1
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
                     Res X;
                     res_zero(X);
 #pragma unroll 1
-                    for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL>(c, (R)l, c.tau, X);   // U <- u_l U
+                    for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES>(c, (R)l, c.tau, X);   // U <- u_l U
                     // canonical tree over the lane's segments: a finished pair of
                     // equal sub-trees merges (later on the left) until the sizes differ
                     int h = 0;
@@ -252,8 +256,8 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
                         }
                     const double2 b = bg[t];
                     SampleExact sx;
-                    make_exact<N>(s, b.x, b.y, sx);
-                    finish(lanes[spl_log2], s, sx, out);
+                    make_exact<N, TONES>(s, k, b.x, b.y, sx);
+                    finish<TONES>(lanes[spl_log2], s, sx, out);
                 }
             }
         }
@@ -261,35 +265,42 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
 }
 
 // ----------------------------------------------------------------- launchers
-template <int N, typename R, int METHOD, bool SMALL>
+template <int N, typename R, int METHOD, bool SMALL, bool TONES>
 static void* kernel_ptr()
 {
-    return (void*)integrate_kernel<N, R, METHOD, SMALL>;
+    return (void*)integrate_kernel<N, R, METHOD, SMALL, TONES>;
 }
 
-template <int N, typename R, bool SMALL>
+template <int N, typename R, bool SMALL, bool TONES>
 static void* pick_method(int method)
 {
     switch (method) {
-        case 0: return kernel_ptr<N, R, 0, SMALL>();
-        case 1: return kernel_ptr<N, R, 1, SMALL>();
-        case 2: return kernel_ptr<N, R, 2, SMALL>();
+        case 0: return kernel_ptr<N, R, 0, SMALL, TONES>();
+        case 1: return kernel_ptr<N, R, 1, SMALL, TONES>();
+        case 2: return kernel_ptr<N, R, 2, SMALL, TONES>();
         default: return nullptr;
     }
 }
 
-// The small-angle variant exists for FP32-bulk only; FP64 keeps the general
-// series (its terms are sized for double precision).
-static void* select_kernel(int spin_x2, int precision, int method, bool small)
+template <int N, typename R>
+static void* pick_variant(int method, int variant)
 {
-    if (spin_x2 == 2) {
-        if (!precision) return pick_method<3, double, false>(method);
-        return small ? pick_method<3, float, true>(method) : pick_method<3, float, false>(method);
+    switch (variant) {
+        case kVariantGeneral: return pick_method<N, R, false, false>(method);
+        case kVariantTones: return pick_method<N, R, false, true>(method);
+        case kVariantSmall:
+            // the small-angle variant exists for FP32-bulk only; FP64 keeps the
+            // general series (its terms are sized for double precision)
+            if constexpr (sizeof(R) == 4) return pick_method<N, R, true, false>(method);
+            else return nullptr;
+        default: return nullptr;
     }
-    if (spin_x2 == 1) {
-        if (!precision) return pick_method<2, double, false>(method);
-        return small ? pick_method<2, float, true>(method) : pick_method<2, float, false>(method);
-    }
+}
+
+static void* select_kernel(int spin_x2, int precision, int method, int variant)
+{
+    if (spin_x2 == 2) return precision ? pick_variant<3, float>(method, variant) : pick_variant<3, double>(method, variant);
+    if (spin_x2 == 1) return precision ? pick_variant<2, float>(method, variant) : pick_variant<2, double>(method, variant);
     return nullptr;
 }
 
@@ -306,9 +317,9 @@ size_t integrate_smem_bytes(int spin_x2, int precision, int block)
 // Must be called (outside stream capture) before the first launch of a
 // (spin, precision, method, variant) kernel: it raises the kernel's dynamic
 // shared-memory limit to what a 256-thread block needs.
-cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int block, bool small, int* blocks_per_sm)
+cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int block, int variant, int* blocks_per_sm)
 {
-    void* k = select_kernel(spin_x2, precision, method, small);
+    void* k = select_kernel(spin_x2, precision, method, variant);
     if (!k) return cudaErrorInvalidValue;
     size_t smem_max = integrate_smem_bytes(spin_x2, precision, 256);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
@@ -336,10 +347,10 @@ void integrate_tiles(int64_t total, int lanes_bulk, int block, int64_t wave_bloc
     a.n_tiles = a.n_bulk_tiles + (total - a.bulk_samples + spb_tail - 1) / spb_tail;
 }
 
-cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, int grid, bool small,
+cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, int grid, int variant,
                              const IntegrateArgs& a, cudaStream_t stream)
 {
-    void* k = select_kernel(spin_x2, precision, method, small);
+    void* k = select_kernel(spin_x2, precision, method, variant);
     if (!k || block % 32 != 0 || block < 32 || block > 256 || grid < 1 || a.lg_bulk < 0 || a.lg_bulk > kSegLog2 ||
         a.lg_tail < 0 || a.lg_tail > kSegLog2)
         return cudaErrorInvalidValue;

@@ -9,6 +9,7 @@
 namespace spinsim {
 
 constexpr int kMaxPulses = 4;
+constexpr int kMaxTones = SPINSIM_MAX_TONES;
 // A sample's L steps are split into 2^seg_log2 canonical segments (at most
 // kSegments) reduced by a fixed binary tree; the split depends on L alone.
 constexpr int kSegLog2 = 3;
@@ -104,11 +105,20 @@ struct DevSim {
     double inv_w[kMaxPulses];    // 1 / (standard deviation or period)
     double psi0[6];
     int32_t n_pulses, frame, spin_x2, counter_on;
+    // Further drive tones j < n_tones, each handled like the drive: Om+-_j,
+    // the in-frame rates (frame: 2 pi (f_j -+ B); lab: 2 pi f_j) and the
+    // Taylor tables of their node-phasor sums (same layout as tay_co/tay_ct).
+    int32_t n_tones, tone_pad;
+    double tone_hz[kMaxTones], tone_phase[kMaxTones];
+    double t_om_plus[kMaxTones], t_om_minus[kMaxTones];
+    double t_co0[kMaxTones], t_ct0[kMaxTones];
+    double t_tay_co[kMaxTones][8], t_tay_ct[kMaxTones][8];
     // The same constants rounded to FP32 once, on the host, for the FP32-bulk
     // kernels (P as an FP32 (hi, lo) pair: hi = fl(P), lo = fl(P - hi)).
     float f_ph[4], f_pl[4];
     float f_za, f_zb, f_zbias, f_qd3, f_dt, f_c1, f_c2, f_pad;
     float f_amp[kMaxPulses], f_invw[kMaxPulses];
+    float f_tom_plus[kMaxTones], f_tom_minus[kMaxTones];
 };
 
 struct IntegrateArgs {
@@ -199,6 +209,8 @@ inline void field_bounds(const spinsim_field& f, double& wperp, double& wz)
     double pulses = 0.0;
     for (int p = 0; p < f.n_pulses; p++) pulses += std::fabs(f.pulse_amp_hz[p]);
     wperp = two_pi * (std::fabs(f.drive_x_hz) + std::fabs(f.drive_y_hz));
+    for (int j = 0; j < f.n_tones && j < SPINSIM_MAX_TONES; j++)
+        wperp += two_pi * (std::fabs(f.tone_x_hz[j]) + std::fabs(f.tone_y_hz[j]));
     wz = two_pi * (std::fabs(f.bias_hz) + pulses);
 }
 
@@ -277,18 +289,31 @@ constexpr double kTinyAngleBound = 0.015625;
 // sample/chunk/group offsets.
 void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L, DevSim& d);
 // small_angle_request: true when the request runs in FP32-bulk, has no
-// single-sine-cycle pulse, and every argument of the per-step sine/cosine
+// single-sine-cycle pulse and no further tone, and every argument of the per-step sine/cosine
 // series is bounded by kTinyAngleBound.
 bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, int64_t L);
 
+// Integrate kernel variants: the general one; the small-angle one (FP32-bulk,
+// Gaussian pulses, no further tones; small_angle_request); and the one that
+// also evaluates further drive tones (any request; chosen only when a request
+// of the launch has tones, so the others keep the leaner step loop).
+enum IntegrateVariant { kVariantGeneral = 0, kVariantSmall = 1, kVariantTones = 2 };
+// request_variant: the variant a validated request needs on its own;
+// variant_join: the variant serving two sets of requests in one launch.
+int request_variant(const spinsim_config& cfg, const spinsim_request& r, int64_t L);
+inline int variant_join(int a, int b)
+{
+    if (a == kVariantTones || b == kVariantTones) return kVariantTones;
+    return a == kVariantSmall && b == kVariantSmall ? kVariantSmall : kVariantGeneral;
+}
+
 // Host-side launchers (integrate.cu, chain.cu).  precision: 0 FP64, 1 FP32-bulk;
-// small: the small-angle variant (FP32-bulk only, all requests of the launch
-// satisfying small_angle_request).
+// variant: an IntegrateVariant (kVariantSmall for FP32-bulk only).
 // launch_integrate: `a` must carry the tile plan of integrate_tiles.
-cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, int grid, bool small,
+cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, int grid, int variant,
                              const IntegrateArgs& a, cudaStream_t stream);
 size_t integrate_smem_bytes(int spin_x2, int precision, int block);
-cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int block, bool small, int* blocks_per_sm);
+cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int block, int variant, int* blocks_per_sm);
 // integrate_tiles: the tile plan of `total` samples for bulk lanes per sample
 // `lanes_bulk` (1, 2, 4 or 8, at most 2^min_seg_log2), `block` threads and
 // `wave_blocks` resident blocks; the tail uses 2^min_seg_log2 lanes per sample,

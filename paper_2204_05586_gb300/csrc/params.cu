@@ -38,6 +38,25 @@ double pulse_weight(const spinsim_field& f)
     return w;
 }
 
+// Taylor tables T_m = sum_{l<L, n=1,2} W_n x^m e^{i th x}, x = l + c_n, m = 0..3
+// (re/im interleaved) of the node-phasor sum at th (direct FP64 summation).
+void phasor_tables(double th, int64_t L, const double Wn[2], const double cn[2], double T[8])
+{
+    for (int m = 0; m < 8; m++) T[m] = 0.0;
+    for (int64_t l = 0; l < L; l++)
+        for (int nn = 0; nn < 2; nn++) {
+            if (Wn[nn] == 0.0) continue;
+            const double x = (double)l + cn[nn];
+            const double sa = std::sin(th * x), ca = std::cos(th * x);
+            double pw = Wn[nn];
+            for (int m = 0; m < 4; m++) {
+                T[2 * m] += pw * ca;
+                T[2 * m + 1] += pw * sa;
+                pw *= x;
+            }
+        }
+}
+
 }  // namespace
 
 // Every argument of the per-step sine/cosine series, bounded from the field's
@@ -53,6 +72,7 @@ double pulse_weight(const spinsim_field& f)
 bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, int64_t L)
 {
     if (cfg.precision != SPINSIM_PREC_FP32_BULK || L < 1) return false;
+    if (r.field.n_tones > 0) return false;
     if (r.field.n_pulses > 0 && (r.field.pulse_sine_mask & ((1 << r.field.n_pulses) - 1)) != 0) return false;
     const MethodNodes m = method_nodes(cfg.method);
     const spinsim_field& f = r.field;
@@ -68,6 +88,12 @@ bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, in
     const double half_phi = 0.5 * wabs * dt * om_perp;
     const double h = 0.5 * z + q / 3.0;
     return co <= kTinyAngleBound && h <= kTinyAngleBound && half_phi <= kTinyAngleBound;
+}
+
+int request_variant(const spinsim_config& cfg, const spinsim_request& r, int64_t L)
+{
+    if (r.field.n_tones > 0) return kVariantTones;
+    return small_angle_request(cfg, r, L) ? kVariantSmall : kVariantGeneral;
 }
 
 void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L, DevSim& d)
@@ -111,8 +137,23 @@ void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K,
         d.exit_im = d.exit_half_im = 0.0;
     }
     const double pulse_w = pulse_weight(f);
+    // further tones: Om+-_j and their rates as seen in the frame (or the lab)
+    d.n_tones = f.n_tones;
+    double om_perp = std::fabs(om_plus) + std::fabs(om_minus);
+    for (int j = 0; j < f.n_tones; j++) {
+        const double tx = kTwoPiH * f.tone_x_hz[j], ty = kTwoPiH * f.tone_y_hz[j];
+        d.tone_hz[j] = f.tone_hz[j];
+        d.tone_phase[j] = f.tone_phase[j];
+        d.t_om_plus[j] = 0.5 * (tx + ty);
+        d.t_om_minus[j] = 0.5 * (tx - ty);
+        d.t_co0[j] = kTwoPiH * (f.tone_hz[j] - (d.frame ? f.bias_hz : 0.0));
+        d.t_ct0[j] = kTwoPiH * (f.tone_hz[j] + (d.frame ? f.bias_hz : 0.0));
+        d.f_tom_plus[j] = (float)d.t_om_plus[j];
+        d.f_tom_minus[j] = (float)d.t_om_minus[j];
+        om_perp += std::fabs(d.t_om_plus[j]) + std::fabs(d.t_om_minus[j]);
+    }
     d.tau = choose_tau(cfg.trotter_squares, cfg.precision, cfg.rotating_frame, mn.n_exp, wa, wb, d.dt,
-                       std::fabs(om_plus) + std::fabs(om_minus), kTwoPiH * std::fabs(f.bias_hz), pulse_w,
+                       om_perp, kTwoPiH * std::fabs(f.bias_hz), pulse_w,
                        r.spin_x2 == 2 ? kTwoPiH * std::fabs(f.quad_hz) : 0.0, (double)(K > 0 ? K - 1 : 0) * (double)L);
     if (r.spin_x2 == 1) d.tau = 0;   // closed form: no squarings
     // quadrupole coefficient of one exponential, over 3 and 2^tau, as the bulk
@@ -131,23 +172,13 @@ void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K,
     // Taylor tables of the node-phasor sums (direct FP64 summation)
     d.tay_ok = L <= 65536 ? 1 : 0;
     if (d.tay_ok) {
-        const double th_co = d.w_co0 * d.dt, th_ct = d.w_counter0 * d.dt;
-        double co[8] = {0}, ct[8] = {0};
         const double Wn[2] = {d.W1, d.W2}, cn[2] = {d.c1, d.c2};
-        for (int64_t l = 0; l < L; l++)
-            for (int nn = 0; nn < 2; nn++) {
-                if (Wn[nn] == 0.0) continue;
-                const double x = (double)l + cn[nn];
-                double pw = Wn[nn];
-                const double sa = std::sin(th_co * x), ca = std::cos(th_co * x);
-                const double sb = std::sin(th_ct * x), cb = std::cos(th_ct * x);
-                for (int m = 0; m < 4; m++) {
-                    co[2 * m] += pw * ca; co[2 * m + 1] += pw * sa;
-                    ct[2 * m] += pw * cb; ct[2 * m + 1] += pw * sb;
-                    pw *= x;
-                }
-            }
-        for (int m = 0; m < 8; m++) { d.tay_co[m] = co[m]; d.tay_ct[m] = ct[m]; }
+        phasor_tables(d.w_co0 * d.dt, L, Wn, cn, d.tay_co);
+        phasor_tables(d.w_counter0 * d.dt, L, Wn, cn, d.tay_ct);
+        for (int j = 0; j < d.n_tones; j++) {
+            phasor_tables(d.t_co0[j] * d.dt, L, Wn, cn, d.t_tay_co[j]);
+            if (d.t_om_minus[j] != 0.0) phasor_tables(d.t_ct0[j] * d.dt, L, Wn, cn, d.t_tay_ct[j]);
+        }
     }
     // Gaussian pulses first, then the sine cycles, so the step loop handles
     // each kind in a loop of its own

@@ -34,7 +34,7 @@ struct Checked {
     int status = SPINSIM_OK;
     int flags = 0;
     int64_t K = 0, L = 0;
-    bool small = false;   // small_angle_request under the handle's configuration
+    int variant = kVariantGeneral;   // request_variant under the handle's configuration
 };
 
 Checked check_request(const spinsim_request* r)
@@ -44,6 +44,13 @@ Checked check_request(const spinsim_request* r)
     if (r->spin_x2 != 1 && r->spin_x2 != 2) { c.status = SPINSIM_E_ARG; return c; }
     const spinsim_field& f = r->field;
     if (f.n_pulses < 0 || f.n_pulses > SPINSIM_MAX_PULSES) { c.status = SPINSIM_E_ARG; return c; }
+    if (f.n_tones < 0 || f.n_tones > SPINSIM_MAX_TONES) { c.status = SPINSIM_E_ARG; return c; }
+    for (int j = 0; j < f.n_tones; j++)
+        if (!std::isfinite(f.tone_x_hz[j]) || !std::isfinite(f.tone_y_hz[j]) || !std::isfinite(f.tone_hz[j]) ||
+            !std::isfinite(f.tone_phase[j])) {
+            c.status = SPINSIM_E_ARG;
+            return c;
+        }
     for (int p = 0; p < f.n_pulses; p++)
         if (!(f.pulse_width_s[p] > 0.0) || !std::isfinite(f.pulse_amp_hz[p]) || !std::isfinite(f.pulse_centre_s[p])) {
             c.status = SPINSIM_E_ARG;
@@ -106,7 +113,7 @@ struct PinnedBuf {
 
 struct Group {
     int spin_x2;
-    bool small = true;             // every request of the group takes the small-angle kernel
+    int variant = -1;              // integrate variant of the launch (variant_join over the requests)
     std::vector<int64_t> idx;      // request indices
     int64_t samples = 0;
     double steps = 0.0;            // CF4 (or sampling) steps of the group
@@ -134,12 +141,12 @@ struct Plan {
 };
 
 struct TuneKey {
-    int spin, precision, method, tau, small;
+    int spin, precision, method, tau, variant;
     int64_t size;   // power-of-two bucket of the batch's samples
     bool operator<(const TuneKey& o) const
     {
-        return std::tie(spin, precision, method, tau, small, size) <
-               std::tie(o.spin, o.precision, o.method, o.tau, o.small, o.size);
+        return std::tie(spin, precision, method, tau, variant, size) <
+               std::tie(o.spin, o.precision, o.method, o.tau, o.variant, o.size);
     }
 };
 struct TuneVal {
@@ -192,7 +199,7 @@ struct spinsim_s {
     Arena arena;
     PinnedBuf pinned;
     spinsim_launch_info last{};
-    std::map<std::tuple<int, int, int>, int> occ;   // (spin, block, small) -> resident blocks per SM
+    std::map<std::tuple<int, int, int>, int> occ;   // (spin, block, variant) -> resident blocks per SM
     std::vector<char> table_tmp;                     // host copy of the next parameter table
     // graph cache: one batch signature
     std::vector<uint64_t> graph_sig;
@@ -288,7 +295,7 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
         for (int64_t i = 0; i < n; i++)
             if (checked[i].status == SPINSIM_OK && reqs[i].spin_x2 == spin) {
                 g.idx.push_back(i);
-                g.small = g.small && checked[i].small;
+                g.variant = g.variant < 0 ? checked[i].variant : variant_join(g.variant, checked[i].variant);
                 g.samples += checked[i].K;
                 g.steps += (double)checked[i].K * (double)checked[i].L;
                 g.min_seg_log2 = std::min(g.min_seg_log2, seg_log2_of(checked[i].L));
@@ -383,9 +390,9 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
 
 // Resident blocks per SM of an integrate shape; computed outside stream
 // capture (it sets the kernel's shared-memory limit) and cached.
-int occupancy(spinsim_s* h, int spin, int block, bool small, bool capturing, int* per_sm)
+int occupancy(spinsim_s* h, int spin, int block, int variant, bool capturing, int* per_sm)
 {
-    auto key = std::make_tuple(spin, block, (int)small);
+    auto key = std::make_tuple(spin, block, variant);
     auto it = h->occ.find(key);
     if (it != h->occ.end()) {
         *per_sm = it->second;
@@ -393,7 +400,7 @@ int occupancy(spinsim_s* h, int spin, int block, bool small, bool capturing, int
     }
     if (capturing) return SPINSIM_E_UNSUPPORTED;
     int b = 0;
-    if (integrate_occupancy(spin, h->cfg.precision, h->cfg.method, block, small, &b) != cudaSuccess) {
+    if (integrate_occupancy(spin, h->cfg.precision, h->cfg.method, block, variant, &b) != cudaSuccess) {
         cudaGetLastError();
         return SPINSIM_E_CUDA;
     }
@@ -415,7 +422,7 @@ int size_bucket(int64_t samples)
 // tuned by timing trial launches, once per (device, key), and cached.  The
 // resident blocks per SM are the explicit value or the most the kernel allows
 // (fewer never paid on GB300: the tail they save costs more in issue rate).
-int choose_shape(spinsim_s* h, int spin, bool small, double steps, int min_seg_log2, IntegrateArgs& a,
+int choose_shape(spinsim_s* h, int spin, int variant, double steps, int min_seg_log2, IntegrateArgs& a,
                  cudaStream_t stream, bool capturing, int& lanes, int& block, int& grid)
 {
     const int precision = h->cfg.precision;
@@ -425,7 +432,7 @@ int choose_shape(spinsim_s* h, int spin, bool small, double steps, int min_seg_l
     int bps = h->cfg.blocks_per_sm;
     const bool full_trial = steps <= kFullTrialSteps;
     if (lanes == 0 || block == 0) {
-        TuneKey key{spin, precision, method, h->tau, (int)small, (int64_t)size_bucket(a.total_samples) * 8 + min_seg_log2};
+        TuneKey key{spin, precision, method, h->tau, variant, (int64_t)size_bucket(a.total_samples) * 8 + min_seg_log2};
         bool found = false;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -455,7 +462,7 @@ int choose_shape(spinsim_s* h, int spin, bool small, double steps, int min_seg_l
                         const int B = block ? block : block_opts[bi];
                         if (block && bi > 0) break;
                         int per_sm = 0;
-                        if (occupancy(h, spin, B, small, false, &per_sm) != SPINSIM_OK || per_sm < 1) continue;
+                        if (occupancy(h, spin, B, variant, false, &per_sm) != SPINSIM_OK || per_sm < 1) continue;
                         const int P = bps ? std::min(bps, per_sm) : per_sm;
                         const int64_t wave_blocks = (int64_t)h->n_sm * P;
                         IntegrateArgs t = a;
@@ -469,7 +476,7 @@ int choose_shape(spinsim_s* h, int spin, bool small, double steps, int min_seg_l
                         for (int rep = 0; rep < 2; rep++) {
                             cudaMemsetAsync(a.tile_counter, 0, sizeof(unsigned long long), stream);
                             cudaEventRecord(e0, stream);
-                            launch_integrate(spin, precision, method, B, g, small, t, stream);
+                            launch_integrate(spin, precision, method, B, g, variant, t, stream);
                             cudaEventRecord(e1, stream);
                             if (cudaEventSynchronize(e1) != cudaSuccess) {
                                 cudaEventDestroy(e0);
@@ -498,7 +505,7 @@ int choose_shape(spinsim_s* h, int spin, bool small, double steps, int min_seg_l
         }
     }
     int per_sm = 0;
-    int st = occupancy(h, spin, block, small, capturing, &per_sm);
+    int st = occupancy(h, spin, block, variant, capturing, &per_sm);
     if (st != SPINSIM_OK) return st;
     per_sm = std::max(per_sm, 1);
     if (bps > 0) per_sm = std::min(per_sm, bps);
@@ -584,13 +591,13 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
         if (g.samples > 0) {
             if (phase == kPhaseFinish && pg >= 0) prof_record(h->prof[pg][0]);
             if (phase != kPhaseFinish) {
-                st = choose_shape(h, g.spin_x2, g.small, g.steps, g.min_seg_log2, ia, stream, capturing, lanes, block,
+                st = choose_shape(h, g.spin_x2, g.variant, g.steps, g.min_seg_log2, ia, stream, capturing, lanes, block,
                                   grid);
                 if (st != SPINSIM_OK) return st;
                 if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
                     return SPINSIM_E_CUDA;
                 if (pg >= 0) prof_record(h->prof[pg][0]);
-                if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, block, grid, g.small, ia, stream) !=
+                if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, block, grid, g.variant, ia, stream) !=
                     cudaSuccess)
                     return SPINSIM_E_CUDA;
                 kernels += 1;
@@ -640,7 +647,7 @@ std::vector<uint64_t> batch_signature(const spinsim_request* reqs, const spinsim
     s.push_back((uint64_t)n);
     for (int64_t i = 0; i < n; i++) {
         s.push_back((uint64_t)reqs[i].spin_x2 | ((uint64_t)(checked[i].status & 0xff) << 8) |
-                    ((uint64_t)checked[i].small << 16));
+                    ((uint64_t)checked[i].variant << 16));
         s.push_back((uint64_t)checked[i].K);
         s.push_back((uint64_t)checked[i].L);
         s.push_back((uint64_t)(uintptr_t)res[i].states);
@@ -813,7 +820,7 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
         res[i].status = checked[i].status;
         if (checked[i].status == SPINSIM_OK) {
             checked[i].flags |= precision_flags(h->cfg.precision, h->cfg.rotating_frame, reqs[i]);
-            checked[i].small = small_angle_request(h->cfg, reqs[i], checked[i].L);
+            checked[i].variant = request_variant(h->cfg, reqs[i], checked[i].L);
         }
         res[i].flags = checked[i].flags;
         res[i].trotter_squares = 0;
@@ -931,7 +938,7 @@ int spinsim_range_begin(spinsim_handle h, const spinsim_request* req, spinsim_re
     }
     if (c.status == SPINSIM_OK) {
         c.flags |= precision_flags(h->cfg.precision, h->cfg.rotating_frame, *req);
-        c.small = small_angle_request(h->cfg, *req, c.L);
+        c.variant = request_variant(h->cfg, *req, c.L);
     }
     res->status = c.status;
     res->flags = c.flags;
@@ -1090,7 +1097,7 @@ static int serving_pump(spinsim_s* h)
             res.push_back(*tk.res);
             ids.push_back(t);
             Checked c = check_request(&tk.req);
-            if (c.status == SPINSIM_OK) c.small = small_angle_request(h->cfg, tk.req, c.L);
+            if (c.status == SPINSIM_OK) c.variant = request_variant(h->cfg, tk.req, c.L);
             checked.push_back(c);
             bytes += tk.bytes;
         }

@@ -122,7 +122,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     d.sample_offset = 0;
     d.chain_run = cg.run;
     d.chain_top = cg.top;
-    const bool small = small_angle_request(*cfg, *req, L);
+    const int variant = request_variant(*cfg, *req, L);
     res->trotter_squares = d.tau;
     // sample offsets {0, K} and, per chain level, the node offsets {0, nodes}
     int64_t offsets[2] = {0, K};
@@ -141,7 +141,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         const int lanes = cfg->lanes_per_sample ? cfg->lanes_per_sample : 1;
         const int block = cfg->threads_per_block ? cfg->threads_per_block : 128;
         int per_sm = 0;
-        if (integrate_occupancy(spin, cfg->precision, cfg->method, block, small, &per_sm) != cudaSuccess) {
+        if (integrate_occupancy(spin, cfg->precision, cfg->method, block, variant, &per_sm) != cudaSuccess) {
             cudaGetLastError();
             return res->status = SPINSIM_E_CUDA;
         }
@@ -160,7 +160,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         // the tile counter keeps the previous call's value: clear it
         if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
             return res->status = SPINSIM_E_CUDA;
-        if (launch_integrate(spin, cfg->precision, cfg->method, block, grid, small, ia, stream) != cudaSuccess)
+        if (launch_integrate(spin, cfg->precision, cfg->method, block, grid, variant, ia, stream) != cudaSuccess)
             return res->status = SPINSIM_E_CUDA;
         ChainArgs ca;
         ca.sims = ia.sims;

@@ -17,6 +17,7 @@ import numpy as np
 from . import build as _build
 
 MAX_PULSES = 4
+MAX_TONES = 3
 
 OK, PENDING = 0, 1
 E_ARG, E_STEP_RATIO, E_NORM, E_NOMEM, E_CUDA, E_TIMEOUT, E_CAPACITY, E_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7, -8
@@ -44,7 +45,10 @@ class spinsim_field(ctypes.Structure):
                 ("drive_hz", ctypes.c_double), ("drive_phase", ctypes.c_double), ("quad_hz", ctypes.c_double),
                 ("n_pulses", ctypes.c_int32), ("pulse_sine_mask", ctypes.c_int32),
                 ("pulse_amp_hz", ctypes.c_double * MAX_PULSES), ("pulse_centre_s", ctypes.c_double * MAX_PULSES),
-                ("pulse_width_s", ctypes.c_double * MAX_PULSES)]
+                ("pulse_width_s", ctypes.c_double * MAX_PULSES),
+                ("n_tones", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tone_x_hz", ctypes.c_double * MAX_TONES), ("tone_y_hz", ctypes.c_double * MAX_TONES),
+                ("tone_hz", ctypes.c_double * MAX_TONES), ("tone_phase", ctypes.c_double * MAX_TONES)]
 
 
 class spinsim_request(ctypes.Structure):
@@ -218,6 +222,12 @@ def make_request(req: dict) -> spinsim_request:
         r.field.pulse_amp_hz[i], r.field.pulse_centre_s[i], r.field.pulse_width_s[i] = a, c, w
         if kind == "sine":
             r.field.pulse_sine_mask |= 1 << i
+    tones = list(f.get("tones", ()))
+    if len(tones) > MAX_TONES:
+        raise SpinsimError(E_ARG, f"at most {MAX_TONES} further tones")
+    r.field.n_tones = len(tones)
+    for j, (x, y, hz, ph) in enumerate(tones):
+        r.field.tone_x_hz[j], r.field.tone_y_hz[j], r.field.tone_hz[j], r.field.tone_phase[j] = x, y, hz, ph
     r.t_start, r.t_end, r.dt, r.dt_out = req["t_start"], req["t_end"], req["dt"], req["dt_out"]
     psi = np.asarray(req["psi0"], dtype=np.complex128)
     for i, z in enumerate(psi):

@@ -67,6 +67,19 @@ def spin_one_sensing(t_end=0.1, dt=1e-8, dt_out=1e-6):
                             pulses=[(50.0, 50e-3, 1e-3)]), 0.0, t_end, dt, dt_out)
 
 
+MULTITONE = [(1e3, 1e3, 700.5e3, 0.4), (0.5e3, 0.0, 698e3, 1.1), (0.0, 0.8e3, 705e3, -0.6)]
+
+
+def multitone_sensing(t_end=0.1, dt=1e-8, dt_out=1e-6):
+    """The spin-one sensing field with three further drive tones (Sec. 1.4:
+    drives of several tones and polarisations): a circularly polarised tone
+    500 Hz above resonance, a linearly polarised one 2 kHz below, and a
+    y-polarised one 5 kHz above (amplitudes 1, 0.5, 0.8 kHz)."""
+    r = spin_one_sensing(t_end, dt, dt_out)
+    r["field"]["tones"] = list(MULTITONE)
+    return r
+
+
 def neural_pulse(t_end=0.1, t_p=0.05, dt=1e-7, dt_out=1e-6, spin_x2=2):
     """The paper's benchmark field, Eq. neural_pulse:
     H = w J_z + 2 W cos(w t) J_x + W_p sinp(W (t - t_p)) J_z with w = 2 pi 700 kHz,

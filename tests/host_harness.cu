@@ -64,6 +64,27 @@ int hh_small_angle_request(const spinsim_config* cfg, const spinsim_request* r, 
     return small_angle_request(*cfg, *r, L) ? 1 : 0;
 }
 double hh_tiny_angle_bound() { return kTinyAngleBound; }
+
+// The exact first-order transverse coefficients (g_x, g_y) of sample k of a
+// request as the integrate epilogue forms them (fill_devsim, the FP64 sample
+// context with further tones, first_order_exact), and the frame's pulse part
+// gsum: out = (g_x, g_y, gsum).
+void hh_first_order(const spinsim_config* cfg, const spinsim_request* r, int64_t K, int64_t L, int64_t k,
+                    double* out)
+{
+    DevSim d;
+    fill_devsim(*cfg, *r, K, L, d);
+    SampleCtx<double> c;
+    double beta = 0.0;
+    const double gsum = make_ctx<double, 3, true>(d, k, c, beta);
+    SampleExact x;
+    make_exact<3, true>(d, k, beta, gsum, x);
+    double gx, gy;
+    first_order_exact<true>(d, x, gx, gy);
+    out[0] = gx;
+    out[1] = gy;
+    out[2] = gsum;
+}
 // rest part only (U - I - F(v)) in double
 void hh_expm_one_rest(double vx, double vy, double vz, double vq, int tau, double* out)
 {

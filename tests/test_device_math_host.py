@@ -43,6 +43,7 @@ def hh(tmp_path_factory):
     L.hh_small_angle_request.restype = ctypes.c_int
     L.hh_small_angle_request.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
     L.hh_tiny_angle_bound.restype = ctypes.c_double
+    L.hh_first_order.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, DP]
     return L
 
 
@@ -275,3 +276,48 @@ def test_small_angle_rule_on_workloads(hh):
     far = W.spin_one_sensing()
     far["field"]["drive_hz"] = far["field"]["bias_hz"] + 3e3   # 3 kHz detuning: (w_d - w_r) dt_out > 2^-6
     assert rule(far) == 0
+
+
+def quadrature_first_order(req, k, L, frame, gsum):
+    """g_x + i g_y of sample k written out: the CF4 quadrature (both
+    exponentials: node weights a + b at each of the two nodes of every step) of
+    the in-frame transverse field (w_x + i w_y) e^{-i w_r tau}, w_r = 2 pi B +
+    gsum, tau measured from t_{k-1} (Sec. 1.2.5), from the field formula with
+    every tone (numpy, FP64)."""
+    f = req["field"]
+    dt = req["dt_out"] / L
+    t0 = req["t_start"] + (k - 1) * req["dt_out"]
+    c1, c2 = 0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)
+    tau = np.concatenate([(np.arange(L) + c1) * dt, (np.arange(L) + c2) * dt])
+    t = t0 + tau
+    tones = [(f["drive_x_hz"], f["drive_y_hz"], f["drive_hz"], f["drive_phase"])] + list(f.get("tones", ()))
+    w = np.zeros_like(t, dtype=np.complex128)
+    for x, y, hz, ph in tones:
+        a = 2 * np.pi * hz * t + ph
+        w += 2 * np.pi * (x * np.cos(a) + 1j * y * np.sin(a))
+    if frame:
+        w *= np.exp(-1j * (2 * np.pi * f["bias_hz"] + gsum) * tau)
+    g = 0.5 * dt * w.sum()          # a + b = 1/2 per node, two exponentials
+    return g.real, g.imag
+
+
+@pytest.mark.parametrize("L", [7, 100, 70000])
+@pytest.mark.parametrize("frame", [True, False])
+def test_first_order_with_tones_is_the_quadrature(hh, L, frame):
+    """The epilogue's exact first-order coefficients of a three-tone drive
+    (Taylor tables for L <= 65536, else the closed form; with a strong pulse
+    the closed form too) equal the quadrature sum written out."""
+    from paper_2204_05586_gb300 import spinsim as S, workloads as W
+    tones = [(1.2e3, 0.9e3, 19.6e3, 0.8), (0.0, 1.5e3, 60e3, -1.3), (0.7e3, 0.0, 7e3, 2.2)]
+    for pulses in ([], [(3e3, 2.5e-4, 1e-4)]):
+        f = W.field(bias_hz=20e3, drive_x_hz=2e3, drive_y_hz=0.4e3, drive_hz=20.3e3, drive_phase=0.2,
+                    pulses=pulses, tones=tones)
+        req = W.request(2, f, 1e-4, 1e-4 + 40 * 1e-5, 1e-5 / L, 1e-5)
+        cfg = S.make_config(precision=S.PREC_FP64, rotating_frame=frame)
+        r = S.make_request(req)
+        for k in (1, 17, 40):
+            out = np.zeros(3)
+            hh.hh_first_order(ctypes.addressof(cfg), ctypes.addressof(r), 41, L, k, P(out))
+            gx, gy = quadrature_first_order(req, k, L, frame, out[2] if frame else 0.0)
+            scale = np.hypot(gx, gy) + 1e-3
+            assert abs(out[0] - gx) < 1e-11 * scale and abs(out[1] - gy) < 1e-11 * scale, (k, out, gx, gy)

@@ -1,0 +1,114 @@
+"""Further drive tones on the GPU (the tones variant of the integrate kernel):
+every sample against the oracle, in both precisions, spin-one and spin-half,
+all three methods and both frames, and the variant's invariances."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2204_05586_gb300 import spinsim as S, workloads as W  # noqa: E402
+
+THREADS = os.cpu_count() or 4
+TOL = {S.PREC_FP64: 1e-10, S.PREC_FP32_BULK: 1e-5}
+
+# a near-resonant second tone of another polarisation, a far-detuned tone and
+# a slow one, beside a linearly polarised drive
+TONES = [(1.2e3, 0.9e3, 700.4e3, 0.8), (0.0, 1.5e3, 740e3, -1.3), (0.7e3, 0.0, 7e3, 2.2)]
+
+
+def tone_request(spin_x2, t_end=10e-3, dt=1e-8, dt_out=1e-6, tones=TONES, pulses=((60.0, 4e-3, 1e-3),), seed=5):
+    f = W.field(bias_hz=700e3, drive_x_hz=2e3, drive_hz=700e3, quad_hz=300.0 if spin_x2 == 2 else 0.0,
+                pulses=list(pulses), tones=list(tones))
+    rng = np.random.default_rng(seed)
+    return W.request(spin_x2, f, 0.0, t_end, dt, dt_out, psi0=W.random_state(spin_x2 + 1, rng))
+
+
+def oracle_run(O, req, frame=True, method=0, tau=24):
+    return O.simulate(req["spin_x2"], req["field"], req["t_start"], req["t_end"], req["dt"], req["dt_out"],
+                      req["psi0"], rotating_frame=frame, tau=tau, method=method, threads=THREADS)
+
+
+def run(reqs, **cfg):
+    with S.Simulator(**cfg) as sim:
+        return sim.simulate(reqs)
+
+
+def max_err(out, ref):
+    assert out["status"] == S.OK
+    return np.abs(out["states"].cpu().numpy() - ref["states"]).max()
+
+
+@pytest.mark.parametrize("prec", [S.PREC_FP64, S.PREC_FP32_BULK])
+@pytest.mark.parametrize("spin_x2", [2, 1])
+def test_tones_against_oracle(oracle_mod, prec, spin_x2):
+    """10 ms at 10 ns steps (1e4 samples x 100 steps) with three further tones
+    and a Gaussian pulse: every sample."""
+    req = tone_request(spin_x2)
+    (out,) = run([req], precision=prec)
+    err = max_err(out, oracle_run(oracle_mod, req))
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("frame", [True, False])
+@pytest.mark.parametrize("method", [S.METHOD_CF4, S.METHOD_MIDPOINT, S.METHOD_HEUN])
+def test_tones_methods_and_frames_fp64(oracle_mod, frame, method):
+    """Sampling methods and the lab frame with tones and a sine-cycle pulse
+    (FP64, 1 ms, 1e3 samples x 100 steps, the oracle at the same method)."""
+    req = tone_request(2, t_end=1e-3, pulses=[(60.0, 0.2e-3, 0.5e-3, "sine"), (40.0, 0.6e-3, 0.1e-3)])
+    (out,) = run([req], precision=S.PREC_FP64, rotating_frame=frame, method=method)
+    err = max_err(out, oracle_run(oracle_mod, req, frame=frame, method=method))
+    assert err <= TOL[S.PREC_FP64], err
+
+
+def test_zero_tones_equal_no_tones():
+    """Tones of zero amplitude (tones variant) give the run without tones
+    (general or small-angle variant) up to rounding."""
+    for prec in (S.PREC_FP64, S.PREC_FP32_BULK):
+        a = tone_request(2, t_end=2e-3, tones=[(0.0, 0.0, 701e3, 0.3), (0.0, 0.0, 5e3, 0.0)])
+        b = tone_request(2, t_end=2e-3, tones=[])
+        (oa,), (ob,) = run([a], precision=prec), run([b], precision=prec)
+        d = np.abs(oa["states"].cpu().numpy() - ob["states"].cpu().numpy()).max()
+        assert d < (1e-13 if prec == S.PREC_FP64 else 2e-6), (prec, d)
+
+
+def test_drive_and_tone_slots_are_interchangeable():
+    """Swapping the drive with a further tone describes the same field: equal
+    results up to rounding (FP64)."""
+    a = tone_request(2, t_end=2e-3)
+    b = tone_request(2, t_end=2e-3, tones=[(2e3, 0.0, 700e3, 0.0)] + TONES[1:])
+    fb = b["field"]
+    fb["drive_x_hz"], fb["drive_y_hz"], fb["drive_hz"], fb["drive_phase"] = TONES[0]
+    (oa,), (ob,) = run([a], precision=S.PREC_FP64), run([b], precision=S.PREC_FP64)
+    d = np.abs(oa["states"].cpu().numpy() - ob["states"].cpu().numpy()).max()
+    assert d < 1e-12, d
+
+
+def test_mixed_batch(oracle_mod):
+    """A batch of requests with and without tones runs in the tones variant:
+    every request still matches the oracle, and a tone request's result does
+    not depend on the batch around it."""
+    reqs = [tone_request(2, t_end=1e-3, seed=s, tones=TONES[: s % 4]) for s in range(6)]
+    outs = run(reqs, precision=S.PREC_FP32_BULK)
+    for q, o in zip(reqs, outs):
+        assert max_err(o, oracle_run(oracle_mod, q)) <= TOL[S.PREC_FP32_BULK]
+    (alone,) = run([reqs[3]], precision=S.PREC_FP32_BULK)
+    assert np.array_equal(alone["states"].cpu().numpy(), outs[3]["states"].cpu().numpy())
+
+
+def test_tone_count_is_checked():
+    req = tone_request(2, t_end=1e-4)
+    r = S.make_request(req)
+    r.field.n_tones = 4
+    with S.Simulator(precision=S.PREC_FP32_BULK) as sim:
+        outs = sim.allocate([req])
+        res = sim.results_struct(outs)
+        assert S.spinsim_simulate(sim.handle, [r], res, 0) == S.E_ARG
+        r.field.n_tones = 1
+        r.field.tone_hz[0] = float("nan")
+        assert S.spinsim_simulate(sim.handle, [r], res, 0) == S.E_ARG
