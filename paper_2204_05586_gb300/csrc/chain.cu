@@ -32,7 +32,7 @@
 // are kept in SU(2) form (alpha, beta) = first column.
 #include <algorithm>
 
-#include "device_math.cuh"
+#include "sample_epilogue.cuh"
 
 namespace spinsim {
 
@@ -147,23 +147,6 @@ struct Op<2> {
         p[4] = b.r; p[5] = b.i; p[6] = a.r; p[7] = -a.i;
     }
 };
-
-// <J_x>, <J_y>, <J_z> = psi^dagger J psi (Sec. 1.2.1)
-__device__ __forceinline__ void spin_projection(const cx<double>* p, int N, double* out)
-{
-    if (N == 3) {
-        // J_x, J_y have 1/sqrt2 off-diagonals: <J_x> + i <J_y> = sqrt2 (conj(p0) p1 + conj(p1) p2)
-        cx<double> z = cfma_conj(p[1], p[2], cfma_conj(p[0], p[1], cmk(0.0, 0.0)));
-        out[0] = kSqrt2 * z.r;
-        out[1] = kSqrt2 * z.i;
-        out[2] = (p[0].r * p[0].r + p[0].i * p[0].i) - (p[2].r * p[2].r + p[2].i * p[2].i);
-    } else {
-        cx<double> z = cfma_conj(p[0], p[1], cmk(0.0, 0.0));
-        out[0] = z.r;
-        out[1] = z.i;
-        out[2] = 0.5 * ((p[0].r * p[0].r + p[0].i * p[0].i) - (p[1].r * p[1].r + p[1].i * p[1].i));
-    }
-}
 
 // ------------------------------------------------- binary trees of a warp
 // A warp's binary tree over 32 leaves lives in 63 shared-memory slots:

@@ -521,17 +521,10 @@ SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
     step_sincos<R, SMALL>(c.co * tau, s1, c1);
     f.co = cmk(c.ebr * c1 - c.ebi * s1, fma(c.ebr, s1, c.ebi * c1));
     if (c.counter_on) {
+        // the counter-rotating term's first-order part is replaced exactly at
+        // the end of the sample, so it only needs second-order accuracy
         R s2, c2;
-        if constexpr (sizeof(R) == 4) {
-            // FP32: the counter-rotating term's first-order part is replaced
-            // exactly at the end of the sample, so the fast hardware sincos
-            // (on an argument reduced to [-pi, pi]) only reaches second order.
-            R xc = c.counter * tau;
-            xc = fma(R(-kTwoPi), rintf(xc * R(1.0 / kTwoPi)), xc);
-            __sincosf(xc, &s2, &c2);
-        } else {
-            sincos(c.counter * tau, &s2, &c2);
-        }
+        second_order_sincos(c.counter * tau, s2, c2);
         f.ct = cmk(c.ebr * c2 - c.ebi * s2, fma(c.ebr, s2, c.ebi * c2));
     } else {
         f.ct = cmk(R(0), R(0));

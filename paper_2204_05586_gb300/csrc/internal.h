@@ -289,8 +289,8 @@ constexpr double kTinyAngleBound = 0.015625;
 // sample/chunk/group offsets.
 void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L, DevSim& d);
 // small_angle_request: true when the request runs in FP32-bulk, has no
-// single-sine-cycle pulse and no further tone, and every argument of the per-step sine/cosine
-// series is bounded by kTinyAngleBound.
+// single-sine-cycle pulse and no further tone, and every argument of the
+// per-step sine/cosine series is bounded by kTinyAngleBound.
 bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, int64_t L);
 
 // Integrate kernel variants: the general one; the small-angle one (FP32-bulk,
@@ -306,6 +306,16 @@ inline int variant_join(int a, int b)
     if (a == kVariantTones || b == kVariantTones) return kVariantTones;
     return a == kVariantSmall && b == kVariantSmall ? kVariantSmall : kVariantGeneral;
 }
+
+// Request validation (params.cu), shared by every entry point: status,
+// SPINSIM_WARN_MAGNUS, K and L of one request.
+struct Checked {
+    int status = SPINSIM_OK;
+    int flags = 0;
+    int64_t K = 0, L = 0;
+    int variant = kVariantGeneral;   // request_variant under the handle's configuration
+};
+Checked check_request(const spinsim_request* r);
 
 // Host-side launchers (integrate.cu, chain.cu).  precision: 0 FP64, 1 FP32-bulk;
 // variant: an IntegrateVariant (kVariantSmall for FP32-bulk only).

@@ -27,61 +27,6 @@ using namespace spinsim;
 
 namespace {
 
-constexpr int64_t kMaxL = int64_t(1) << 24;  // step index stays exact in FP32
-
-// ------------------------------------------------------------- validation
-struct Checked {
-    int status = SPINSIM_OK;
-    int flags = 0;
-    int64_t K = 0, L = 0;
-    int variant = kVariantGeneral;   // request_variant under the handle's configuration
-};
-
-Checked check_request(const spinsim_request* r)
-{
-    Checked c;
-    if (!r) { c.status = SPINSIM_E_ARG; return c; }
-    if (r->spin_x2 != 1 && r->spin_x2 != 2) { c.status = SPINSIM_E_ARG; return c; }
-    const spinsim_field& f = r->field;
-    if (f.n_pulses < 0 || f.n_pulses > SPINSIM_MAX_PULSES) { c.status = SPINSIM_E_ARG; return c; }
-    if (f.n_tones < 0 || f.n_tones > SPINSIM_MAX_TONES) { c.status = SPINSIM_E_ARG; return c; }
-    for (int j = 0; j < f.n_tones; j++)
-        if (!std::isfinite(f.tone_x_hz[j]) || !std::isfinite(f.tone_y_hz[j]) || !std::isfinite(f.tone_hz[j]) ||
-            !std::isfinite(f.tone_phase[j])) {
-            c.status = SPINSIM_E_ARG;
-            return c;
-        }
-    for (int p = 0; p < f.n_pulses; p++)
-        if (!(f.pulse_width_s[p] > 0.0) || !std::isfinite(f.pulse_amp_hz[p]) || !std::isfinite(f.pulse_centre_s[p])) {
-            c.status = SPINSIM_E_ARG;
-            return c;
-        }
-    const double vals[] = {f.bias_hz, f.drive_x_hz, f.drive_y_hz, f.drive_hz, f.drive_phase, f.quad_hz,
-                           r->t_start, r->t_end, r->dt, r->dt_out};
-    for (double v : vals)
-        if (!std::isfinite(v)) { c.status = SPINSIM_E_ARG; return c; }
-    if (!(r->dt > 0.0) || !(r->dt_out > 0.0) || !(r->t_end >= r->t_start)) { c.status = SPINSIM_E_ARG; return c; }
-    const double rk = (r->t_end - r->t_start) / r->dt_out;
-    const double rl = r->dt_out / r->dt;
-    const double k = std::floor(rk + 0.5), l = std::floor(rl + 0.5);
-    if (std::fabs(rk - k) > 1e-9 * std::max(1.0, rk) || std::fabs(rl - l) > 1e-9 * std::max(1.0, rl) || l < 1.0 ||
-        l > (double)kMaxL || k > 9.0e15) {
-        c.status = SPINSIM_E_STEP_RATIO;
-        return c;
-    }
-    c.K = (int64_t)k;
-    c.L = (int64_t)l;
-    const int n = r->spin_x2 + 1;
-    double nrm = 0.0;
-    for (int i = 0; i < 2 * n; i++) {
-        if (!std::isfinite(r->psi0[i])) { c.status = SPINSIM_E_ARG; return c; }
-        nrm += r->psi0[i] * r->psi0[i];
-    }
-    if (std::fabs(std::sqrt(nrm) - 1.0) > 1e-10) { c.status = SPINSIM_E_NORM; return c; }
-    c.flags = magnus_flags(*r, c.L);
-    return c;
-}
-
 bool is_device_pointer(const void* p)
 {
     if (!p) return false;
