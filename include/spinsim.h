@@ -121,7 +121,7 @@ typedef struct {
  * A linearly polarised drive "2 R cos(2 pi f t)" is drive_x_hz = 2R, drive_y_hz = 0;
  * a circularly polarised one has drive_x_hz = drive_y_hz.  The detuning of the
  * drive is drive_hz - bias_hz.  Tones j < n_tones are further drive terms of the
- * same form (a multi-tone drive of any polarisations, Sec. 1.4); requests with
+ * same form (a multi-tone drive of any polarisations, Sec. 3.1); requests with
  * tones run on a kernel variant that evaluates them, the others are unaffected. */
 typedef struct {
     double bias_hz;

@@ -1,9 +1,15 @@
-"""Build the CUDA shared library ``_build/libspinsim.so`` in-tree.
+"""Build the shared libraries in-tree.
 
-nvcc compiles every ``csrc/*.cu`` for sm_103a in parallel, then links them
-into one shared object with the static CUDA runtime.  No cmake, no torch
-extension machinery: the library exposes a plain C ABI (``include/spinsim.h``)
-and is loaded with ctypes.
+``_build/libspinsim.so``: nvcc compiles every ``csrc/*.cu`` for sm_103a in
+parallel and links them into one shared object with the static CUDA runtime
+(the C ABI of ``include/spinsim.h``).
+
+``_build/libspinsim_cpu.so``: the multicore CPU backend
+(``include/spinsim_cpu.h``): ``csrc/cpu/*.cu`` and the shared host logic of
+``csrc/params.cu``, compiled as C++ by the host compiler (the device-math
+headers compile as plain C++), no CUDA runtime.
+
+No cmake, no torch extension machinery; both are loaded with ctypes.
 """
 from __future__ import annotations
 
@@ -21,10 +27,21 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libspinsim.so")
+CPU_LIB = os.path.join(BUILD, "libspinsim_cpu.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
+
+
+CXX_FLAGS = ["-x", "c++", "-O3", "-std=c++17", "-fPIC", "-pthread"]
+
+
+def cxx() -> str:
+    for cand in (os.environ.get("CXX"), shutil.which("g++"), shutil.which("c++")):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("no C++ compiler found for libspinsim_cpu")
 
 
 def nvcc() -> str:
@@ -38,13 +55,18 @@ def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def _cpu_sources():
+    return sorted(glob.glob(os.path.join(CSRC, "cpu", "*.cu")))
+
+
 def _fingerprint() -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(CSRC, "*")) + [os.path.join(INCLUDE, "spinsim.h")]):
+    for p in sorted(glob.glob(os.path.join(CSRC, "*.*")) + _cpu_sources() +
+                    [os.path.join(INCLUDE, "spinsim.h"), os.path.join(INCLUDE, "spinsim_cpu.h")]):
         with open(p, "rb") as f:
             h.update(os.path.basename(p).encode())
             h.update(f.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH + NVCC_FLAGS + CXX_FLAGS).encode())
     return h.hexdigest()
 
 
@@ -63,7 +85,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 def _build_locked(force: bool, verbose: bool) -> str:
     stamp = os.path.join(BUILD, "libspinsim.sha256")
     fp = _fingerprint()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == fp:
+    if (not force and os.path.exists(LIB) and os.path.exists(CPU_LIB) and os.path.exists(stamp)
+            and open(stamp).read() == fp):
         return LIB
     exe = nvcc()
     objs = []
@@ -78,15 +101,35 @@ def _build_locked(force: bool, verbose: bool) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
         return obj
 
+    cuda_include = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(exe))), "include")
+
+    def compile_host(src):
+        obj = os.path.join(BUILD, "host_" + os.path.basename(src)[:-3] + ".o")
+        cmd = [cxx(), *CXX_FLAGS, "-I", INCLUDE, "-I", cuda_include, "-c", src, "-o", obj]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"host compile failed on {src}:\n{r.stdout}\n{r.stderr}")
+        return obj
+
     srcs = _sources()
-    with ThreadPoolExecutor(max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [exe, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    host_srcs = _cpu_sources() + [os.path.join(CSRC, "params.cu")]
+    with ThreadPoolExecutor(max(1, min(len(srcs) + len(host_srcs), os.cpu_count() or 1))) as ex:
+        gpu_jobs = [ex.submit(compile_one, s) for s in srcs]
+        host_jobs = [ex.submit(compile_host, s) for s in host_srcs]
+        gpu_objs = [j.result() for j in gpu_jobs]
+        host_objs = [j.result() for j in host_jobs]
+
+    def link(out, cmd):
+        tmp = out + f".tmp{os.getpid()}"
+        r = subprocess.run(cmd + ["-o", tmp], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link of {os.path.basename(out)} failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, out)
+
+    link(LIB, [exe, *ARCH, "-shared", "-cudart", "static", *gpu_objs])
+    link(CPU_LIB, [cxx(), "-shared", "-pthread", *host_objs])
     with open(stamp, "w") as f:
         f.write(fp)
     return LIB

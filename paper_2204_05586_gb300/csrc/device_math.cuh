@@ -10,7 +10,8 @@
 
 #include "internal.h"
 
-// Device functions that are also compiled for the host by the CPU test harness.
+#if defined(__CUDACC__)
+// Device functions, also compiled for the host by nvcc (the CPU test harness).
 #ifndef SPINSIM_HD
 #define SPINSIM_HD __host__ __device__ __forceinline__
 #endif
@@ -19,6 +20,28 @@
 // register allocation is not sized for them.
 #ifndef SPINSIM_COLD
 #define SPINSIM_COLD __host__ __device__ __noinline__
+#endif
+#else
+// A host C++ compiler (the multicore CPU backend): plain inline functions and
+// the C++ library's maths under the names the device code uses.
+#include <cmath>
+#define SPINSIM_HD inline
+#define SPINSIM_COLD __attribute__((noinline))
+namespace spinsim {
+using std::cos;
+using std::exp;
+using std::fabs;
+using std::floor;
+using std::fma;
+using std::ldexp;
+using std::rint;
+using std::sin;
+using std::sqrt;
+inline void sincos(float x, float* s, float* c) { *s = std::sin(x); *c = std::cos(x); }
+inline void sincos(double x, double* s, double* c) { *s = std::sin(x); *c = std::cos(x); }
+inline float rsqrt(float x) { return 1.0f / std::sqrt(x); }
+inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
+}  // namespace spinsim
 #endif
 
 namespace spinsim {

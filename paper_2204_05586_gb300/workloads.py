@@ -71,7 +71,7 @@ MULTITONE = [(1e3, 1e3, 700.5e3, 0.4), (0.5e3, 0.0, 698e3, 1.1), (0.0, 0.8e3, 70
 
 
 def multitone_sensing(t_end=0.1, dt=1e-8, dt_out=1e-6):
-    """The spin-one sensing field with three further drive tones (Sec. 1.4:
+    """The spin-one sensing field with three further drive tones (Sec. 3.1:
     drives of several tones and polarisations): a circularly polarised tone
     500 Hz above resonance, a linearly polarised one 2 kHz below, and a
     y-polarised one 5 kHz above (amplitudes 1, 0.5, 0.8 kHz)."""

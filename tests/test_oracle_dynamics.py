@@ -43,7 +43,7 @@ def test_field_sample_formula(oracle_mod):
 
 
 def test_field_sample_formula_extra_tones(oracle_mod):
-    """Further drive tones add to w_x and w_y like the first (Sec. 1.4: drives of
+    """Further drive tones add to w_x and w_y like the first (Sec. 3.1: drives of
     any number of tones and polarisations)."""
     tones = [(1.5e3, -0.4e3, 703e3, 1.1), (0.0, 0.8e3, 698.5e3, -0.7), (-0.3e3, 0.3e3, 1.2e3, 2.9)]
     f = W.field(bias_hz=700e3, drive_x_hz=2e3, drive_y_hz=0.5e3, drive_hz=701e3, drive_phase=0.3, tones=tones)
