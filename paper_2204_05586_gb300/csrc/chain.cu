@@ -285,6 +285,10 @@ __global__ void __launch_bounds__(128) chain_up_kernel(ChainArgs a, int level)
 {
     constexpr int D = Tree<N>::D, SV = 2 * N;
     extern __shared__ __align__(16) double smem[];
+    // programmatic dependent launch: the previous kernel's results are
+    // visible after this wait; the next chain kernel may be scheduled now
+    grid_dependency_wait();
+    allow_dependent_launch();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double* S = smem + warp * warp_tree_doubles<N>();
     double* V = S + 63 * D;
@@ -356,6 +360,7 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
 {
     constexpr int D = Tree<N>::D, SV = 2 * N;
     extern __shared__ __align__(16) double smem[];
+    grid_dependency_wait();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double* V = smem + warp * warp_state_doubles<N>();
     const int64_t stride = a.n_sims + 1;
@@ -447,13 +452,30 @@ static cudaError_t launch_chain_n(const ChainArgs& a, int n_sm, cudaStream_t str
         return (int)std::max<int64_t>(1, std::min<int64_t>((nodes + kChainWarps - 1) / kChainWarps, (int64_t)n_sm * 16));
     };
     ChainArgs args = a;
+    // Programmatic dependent launches: each chain kernel may be scheduled
+    // while its predecessor finishes and waits (griddepcontrol.wait) for its
+    // results, which hides the launch gap between the dependent kernels.
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(block);
+    cfg.stream = stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     if (a.mode != kChainDown)
         for (int l = 0; l < a.levels; l++) {
-            chain_up_kernel<N><<<grid(a.nodes[l]), block, up_smem, stream>>>(args, l);
+            cfg.gridDim = dim3(grid(a.nodes[l]));
+            cfg.dynamicSmemBytes = up_smem;
+            const cudaError_t e = cudaLaunchKernelEx(&cfg, chain_up_kernel<N>, args, l);
+            if (e != cudaSuccess) return e;
             (*kernels)++;
         }
     if (a.mode != kChainUp) {
-        chain_apply_kernel<N><<<grid(a.nodes[0]), block, down_smem, stream>>>(args);
+        cfg.gridDim = dim3(grid(a.nodes[0]));
+        cfg.dynamicSmemBytes = down_smem;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, chain_apply_kernel<N>, args);
+        if (e != cudaSuccess) return e;
         (*kernels)++;
     }
     return cudaGetLastError();

@@ -46,6 +46,26 @@ inline double rsqrt(double x) { return 1.0 / std::sqrt(x); }
 
 namespace spinsim {
 
+#if defined(__CUDACC__)
+// Programmatic dependent launch (sm_90 and later): a kernel launched with the
+// programmatic-serialization attribute may start before its predecessor has
+// finished; grid_dependency_wait() blocks until the predecessor grid has
+// completed and its memory is visible (it returns at once for a normal
+// launch), and allow_dependent_launch() lets the successor be scheduled.
+__device__ __forceinline__ void grid_dependency_wait()
+{
+#if defined(__CUDA_ARCH__)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void allow_dependent_launch()
+{
+#if defined(__CUDA_ARCH__)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+#endif
+
 template <typename R>
 struct cx {
     R r, i;
@@ -408,13 +428,20 @@ SPINSIM_HD void make_exact(const DevSim& s, int64_t k, double beta, double gsum,
     if (s.frame) {
         x.dco = s.w_co0 - gsum;
         x.dct = s.w_counter0 + gsum;
-        double d = gsum * s.dt_out * (N == 2 ? 0.5 : 1.0);
-        double sd, cd;
-        small_sincos<double>(d, sd, cd);
         const double br = N == 2 ? s.exit_half_re : s.exit_re;
         const double bi = N == 2 ? s.exit_half_im : s.exit_im;
-        x.ph_re = br * cd + bi * sd;       // (br + i bi)(cd - i sd)
-        x.ph_im = bi * cd - br * sd;
+        if (gsum == 0.0) {
+            // no pulse reaches this interval's midpoint (the usual case away
+            // from the pulses): the exit phasor is the bias's alone
+            x.ph_re = br;
+            x.ph_im = bi;
+        } else {
+            double d = gsum * s.dt_out * (N == 2 ? 0.5 : 1.0);
+            double sd, cd;
+            small_sincos<double>(d, sd, cd);
+            x.ph_re = br * cd + bi * sd;       // (br + i bi)(cd - i sd)
+            x.ph_im = bi * cd - br * sd;
+        }
     } else {
         x.dco = s.w_co0;
         x.dct = s.w_counter0;
@@ -455,6 +482,7 @@ SPINSIM_HD cx<double> node_phasor_sum(double th, int64_t L, double W1, double c1
 //   sum W_n e^{i (th0 + d) x} = T_0 + i d T_1 - d^2/2 T_2 - i d^3/6 T_3 + O((d x)^4).
 SPINSIM_HD cx<double> taylor_sum(const double* T, double d)
 {
+    if (d == 0.0) return cmk(T[0], T[1]);
     const double h2 = -0.5 * d * d, h3 = -d * d * d * (1.0 / 6.0);
     // T0 + i d T1 + h2 T2 + i h3 T3
     return cmk(T[0] - d * T[3] + h2 * T[4] - h3 * T[7], T[1] + d * T[2] + h2 * T[5] + h3 * T[6]);

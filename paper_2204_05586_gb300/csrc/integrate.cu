@@ -54,6 +54,10 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
     unsigned dyn_smem;
     asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
     if ((size_t)blockDim.x * (kSlots * sizeof(Res) + sizeof(double2)) > (size_t)dyn_smem) return;
+    // every block of the persistent grid is resident from the start: the
+    // chain's first kernel may be scheduled as blocks retire (it waits for
+    // this grid's results before reading them)
+    allow_dependent_launch();
 
     for (;;) {
         __syncthreads();
