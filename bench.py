@@ -38,7 +38,7 @@ FP32_PEAK_TFLOPS = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one integrate launch
 # (profiles/integrate_kernel_spin_one_sensing.md); the operators it writes stay in L2.
-INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 67072}
+INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 67328}
 
 
 def algorithmic_flops_per_step(spin_x2: int, tau: int, n_tones: int = 0) -> float:

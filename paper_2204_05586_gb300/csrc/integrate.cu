@@ -40,8 +40,12 @@ __device__ __forceinline__ int find_index(const int64_t* off, int n, int64_t g)
 // thread's canonical sub-tree (log2 of its segment count) and its result.
 constexpr int kSlots = kSegLog2 + 1;
 
+// The tones variant is held to 128 registers (two 256-thread blocks per SM):
+// uncapped it takes 152 and three 128-thread blocks fit, and the fourth
+// block's latency hiding is worth more than the few spilled registers
+// (measured on the multi-tone sensing run: 0.616 -> 0.555 ms).
 template <int N, typename R, int METHOD, bool SMALL, bool TONES>
-__global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
+__global__ void __launch_bounds__(256, TONES ? 2 : 1) integrate_kernel(IntegrateArgs a)
 {
     using Res = typename ResType<N, R>::type;
     constexpr int OPD = N == 3 ? 18 : 4;
