@@ -192,8 +192,10 @@ constexpr size_t kGroupDoubles = (size_t)32 << 20;       // 256 MiB of operators
 
 using namespace spinsim;
 
-extern "C" int spinsim_cpu_simulate(const spinsim_config* cfg_in, const spinsim_request* reqs, spinsim_result* res,
-                                    int64_t n, int32_t threads)
+namespace {
+
+int cpu_simulate(const spinsim_config* cfg_in, const spinsim_request* reqs, spinsim_result* res, int64_t n,
+                 int32_t threads)
 {
     if (n < 0 || (n > 0 && (!reqs || !res)) || threads < 0) return SPINSIM_E_ARG;
     spinsim_config cfg{};
@@ -283,4 +285,18 @@ extern "C" int spinsim_cpu_simulate(const spinsim_config* cfg_in, const spinsim_
         g0 = g1;
     }
     return first_err;
+}
+
+}  // namespace
+
+// The C entry point: no C++ exception leaves it (a thread or an allocation
+// that fails is reported as SPINSIM_E_NOMEM).
+extern "C" int spinsim_cpu_simulate(const spinsim_config* cfg, const spinsim_request* reqs, spinsim_result* res,
+                                    int64_t n, int32_t threads)
+{
+    try {
+        return cpu_simulate(cfg, reqs, res, n, threads);
+    } catch (...) {
+        return SPINSIM_E_NOMEM;
+    }
 }
