@@ -7,18 +7,19 @@
 //
 // Work decomposition (GB300): a persistent grid pulls tiles of consecutive
 // samples from an atomic counter; G = 1, 2, 4 or 8 lanes of a warp share one
-// sample.  The L steps of a sample are always split into the same eight
-// segments [s L/8, (s+1) L/8) and reduced by the same binary tree
+// sample.  The L steps of a sample are always split into the same 2^s
+// segments [q L/2^s, (q+1) L/2^s) (s from L alone: 3 for L >= 128, 2 from 16,
+// 1 from 4, else 0) and reduced by the same binary tree, e.g. for s = 3
 // ((S7 S6)(S5 S4))((S3 S2)(S1 S0)), whichever G is used, so the result is
 // bit-for-bit independent of the launch shape and of which other samples
-// share the batch.  A lane owns 8/G consecutive segments -- a complete
+// share the launch.  A lane owns 2^s/G consecutive segments -- a complete
 // sub-tree, built as its segments finish with a small stack in shared memory.
 // After the tile, one thread per sample combines the lanes' sub-trees and
 // finishes the operator in FP64: on GB300 an FP64 warp instruction costs the
 // same with 1 or 32 active lanes, so this epilogue runs with every lane on a
 // sample of its own.  Whole waves of tiles use the tuned G; the samples left
-// after them use G = 8 (one segment per lane), so the last wave ends in
-// eighths of a sample's steps.
+// after them use one lane per segment, so the last wave ends in segments of a
+// sample's steps.
 #include "sample_epilogue.cuh"
 
 namespace spinsim {
@@ -40,12 +41,9 @@ __device__ __forceinline__ int find_index(const int64_t* off, int n, int64_t g)
 // thread's canonical sub-tree (log2 of its segment count) and its result.
 constexpr int kSlots = kSegLog2 + 1;
 
-// The tones variant is held to 128 registers (two 256-thread blocks per SM):
-// uncapped it takes 152 and three 128-thread blocks fit, and the fourth
-// block's latency hiding is worth more than the few spilled registers
-// (measured on the multi-tone sensing run: 0.616 -> 0.555 ms).
+// The body of both integrate kernels (below).
 template <int N, typename R, int METHOD, bool SMALL, bool TONES>
-__global__ void __launch_bounds__(256, TONES ? 2 : 1) integrate_kernel(IntegrateArgs a)
+__device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
 {
     using Res = typename ResType<N, R>::type;
     constexpr int OPD = N == 3 ? 18 : 4;
@@ -150,11 +148,32 @@ __global__ void __launch_bounds__(256, TONES ? 2 : 1) integrate_kernel(Integrate
     }
 }
 
+// The general and small-angle variants.
+template <int N, typename R, int METHOD, bool SMALL>
+__global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
+{
+    integrate_body<N, R, METHOD, SMALL, false>(a);
+}
+
+// The variant with further drive tones; in FP32 held to 128 registers (two
+// 256-thread blocks per SM): uncapped it takes 152 and three 128-thread blocks
+// fit, and the fourth block's latency hiding is worth more than the few
+// spilled registers (measured on the multi-tone sensing run: 0.616 -> 0.555
+// ms).  The cap is on this kernel alone: given to the others, even as a
+// minimum of one block, it changes their register allocation (126 -> 140) and
+// costs 9%.
+template <int N, typename R, int METHOD>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) integrate_tones_kernel(IntegrateArgs a)
+{
+    integrate_body<N, R, METHOD, false, true>(a);
+}
+
 // ----------------------------------------------------------------- launchers
 template <int N, typename R, int METHOD, bool SMALL, bool TONES>
 static void* kernel_ptr()
 {
-    return (void*)integrate_kernel<N, R, METHOD, SMALL, TONES>;
+    if constexpr (TONES) return (void*)integrate_tones_kernel<N, R, METHOD>;
+    else return (void*)integrate_kernel<N, R, METHOD, SMALL>;
 }
 
 template <int N, typename R, bool SMALL, bool TONES>

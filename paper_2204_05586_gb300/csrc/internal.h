@@ -295,17 +295,14 @@ bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, in
 
 // Integrate kernel variants: the general one; the small-angle one (FP32-bulk,
 // Gaussian pulses, no further tones; small_angle_request); and the one that
-// also evaluates further drive tones (any request; chosen only when a request
-// of the launch has tones, so the others keep the leaner step loop).
+// also evaluates further drive tones (requests with tones only, so the others
+// keep the leaner step loop).  A batch runs one launch group per (spin,
+// variant), each request in the variant it needs on its own.
 enum IntegrateVariant { kVariantGeneral = 0, kVariantSmall = 1, kVariantTones = 2 };
-// request_variant: the variant a validated request needs on its own;
-// variant_join: the variant serving two sets of requests in one launch.
+constexpr int kVariants = 3;
+constexpr int kMaxGroups = 2 * kVariants;   // launch groups of one batch: spin-half and spin-one
+// request_variant: the variant a validated request needs.
 int request_variant(const spinsim_config& cfg, const spinsim_request& r, int64_t L);
-inline int variant_join(int a, int b)
-{
-    if (a == kVariantTones || b == kVariantTones) return kVariantTones;
-    return a == kVariantSmall && b == kVariantSmall ? kVariantSmall : kVariantGeneral;
-}
 
 // Request validation (params.cu), shared by every entry point: status,
 // SPINSIM_WARN_MAGNUS, K and L of one request.

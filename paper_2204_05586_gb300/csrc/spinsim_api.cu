@@ -58,7 +58,7 @@ struct PinnedBuf {
 
 struct Group {
     int spin_x2;
-    int variant = -1;              // integrate variant of the launch (variant_join over the requests)
+    int variant = kVariantGeneral; // integrate variant of the launch, the same for all its requests
     std::vector<int64_t> idx;      // request indices
     int64_t samples = 0;
     double steps = 0.0;            // CF4 (or sampling) steps of the group
@@ -152,8 +152,8 @@ struct spinsim_s {
     int graph_kernels = 0;
     int graph_prof_groups = 0;                      // profiled groups whose events the graph records
     spinsim_launch_info graph_info{};
-    // profiling: per spin group, events before integrate, after integrate, after chain
-    cudaEvent_t prof[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    // profiling: per launch group, events before integrate, after integrate, after chain
+    cudaEvent_t prof[kMaxGroups][3] = {};
     int prof_groups = 0;
     // the range opened by spinsim_range_begin, until spinsim_range_finish
     // (any other call on the handle closes it: they share the arena)
@@ -234,13 +234,16 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
     plan = Plan();
     size_t off = 0;
     size_t pin = 0;
-    for (int spin = 1; spin <= 2; spin++) {
+    // one launch group per (spin, kernel variant): every request runs the
+    // variant it needs on its own, so its result never depends on the batch
+    for (int gi = 0; gi < kMaxGroups; gi++) {
+        const int spin = 1 + gi / kVariants, variant = gi % kVariants;
         Group g;
         g.spin_x2 = spin;
+        g.variant = variant;
         for (int64_t i = 0; i < n; i++)
-            if (checked[i].status == SPINSIM_OK && reqs[i].spin_x2 == spin) {
+            if (checked[i].status == SPINSIM_OK && reqs[i].spin_x2 == spin && checked[i].variant == variant) {
                 g.idx.push_back(i);
-                g.variant = g.variant < 0 ? checked[i].variant : variant_join(g.variant, checked[i].variant);
                 g.samples += checked[i].K;
                 g.steps += (double)checked[i].K * (double)checked[i].L;
                 g.min_seg_log2 = std::min(g.min_seg_log2, seg_log2_of(checked[i].L));
@@ -522,7 +525,9 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             return SPINSIM_E_CUDA;
         pin += tbl;
         h->last.h2d_bytes += (int64_t)tbl;
-        const int pg = (h->cfg.profile && (!capturing || prof_in_graph) && h->prof_groups < 2) ? h->prof_groups++ : -1;
+        const int pg = (h->cfg.profile && (!capturing || prof_in_graph) && h->prof_groups < kMaxGroups)
+                           ? h->prof_groups++
+                           : -1;
         if (pinned_free && cudaEventRecord(pinned_free, stream) != cudaSuccess) return SPINSIM_E_CUDA;
         IntegrateArgs ia;
         ia.sims = reinterpret_cast<const DevSim*>(base + g.sims_off);
@@ -729,22 +734,24 @@ int spinsim_counts(const spinsim_request* req, int64_t* K, int64_t* L)
 int64_t spinsim_footprint(spinsim_handle h, const spinsim_request* reqs, int64_t n)
 {
     if (!h || (n > 0 && !reqs) || n < 0) return SPINSIM_E_ARG;
-    int64_t samples[3] = {0, 0, 0}, count[3] = {0, 0, 0};
-    int64_t nodes[3][kMaxLevels] = {};
-    int levels[3] = {1, 1, 1};
+    // the launch groups of build_plan: one per (spin, kernel variant)
+    int64_t samples[kMaxGroups] = {}, count[kMaxGroups] = {};
+    int64_t nodes[kMaxGroups][kMaxLevels] = {};
+    int levels[kMaxGroups];
+    for (int g = 0; g < kMaxGroups; g++) levels[g] = 1;
     for (int64_t i = 0; i < n; i++) {
         Checked c = check_request(&reqs[i]);
         if (c.status != SPINSIM_OK) return c.status;
-        const int sp = reqs[i].spin_x2;
-        samples[sp] += c.K;
-        count[sp] += 1;
+        const int g = (reqs[i].spin_x2 - 1) * kVariants + request_variant(h->cfg, reqs[i], c.L);
+        samples[g] += c.K;
+        count[g] += 1;
         const ChainGeom cg = chain_geom(c.K);
-        levels[sp] = std::max(levels[sp], cg.top + 1);
-        for (int l = 0; l <= cg.top; l++) nodes[sp][l] += cg.nodes[l];
+        levels[g] = std::max(levels[g], cg.top + 1);
+        for (int l = 0; l <= cg.top; l++) nodes[g][l] += cg.nodes[l];
     }
     int64_t total = 0;
-    for (int s = 1; s <= 2; s++)
-        if (count[s]) total += (int64_t)group_bytes(s, count[s], samples[s], nodes[s], levels[s]);
+    for (int g = 0; g < kMaxGroups; g++)
+        if (count[g]) total += (int64_t)group_bytes(1 + g / kVariants, count[g], samples[g], nodes[g], levels[g]);
     return total;
 }
 

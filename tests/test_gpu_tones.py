@@ -90,15 +90,17 @@ def test_drive_and_tone_slots_are_interchangeable():
 
 
 def test_mixed_batch(oracle_mod):
-    """A batch of requests with and without tones runs in the tones variant:
-    every request still matches the oracle, and a tone request's result does
-    not depend on the batch around it."""
-    reqs = [tone_request(2, t_end=1e-3, seed=s, tones=TONES[: s % 4]) for s in range(6)]
+    """A batch of requests with and without tones, and of both spins: each
+    request runs the kernel variant it needs on its own (one launch per spin
+    and variant), so every result matches the oracle and equals its run
+    alone bit for bit."""
+    reqs = [tone_request(2 if s % 3 else 1, t_end=1e-3, seed=s, tones=TONES[: s % 4]) for s in range(8)]
+    reqs.append(W.neural_pulse(t_end=1e-3, t_p=0.2e-3))       # general variant (sine-cycle pulse)
     outs = run(reqs, precision=S.PREC_FP32_BULK)
     for q, o in zip(reqs, outs):
         assert max_err(o, oracle_run(oracle_mod, q)) <= TOL[S.PREC_FP32_BULK]
-    (alone,) = run([reqs[3]], precision=S.PREC_FP32_BULK)
-    assert np.array_equal(alone["states"].cpu().numpy(), outs[3]["states"].cpu().numpy())
+        (alone,) = run([q], precision=S.PREC_FP32_BULK)
+        assert np.array_equal(alone["states"].cpu().numpy(), o["states"].cpu().numpy())
 
 
 def test_tone_count_is_checked():
