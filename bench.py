@@ -37,8 +37,9 @@ N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one integrate launch
-# (profiles/integrate_kernel_spin_one_sensing.md); the operators it writes stay in L2.
-INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 67328}
+# (profiles/integrate_kernel_spin_one_sensing.md, integrate_tones_kernel_multitone.md);
+# the operators it writes stay in L2.
+INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 67328, ("multitone", "fp32"): 108800}
 
 
 def algorithmic_flops_per_step(spin_x2: int, tau: int, n_tones: int = 0) -> float:
@@ -229,7 +230,8 @@ def run_ours(args, world, rank, local):
     # DRAM traffic of one integrate launch from the ncu capture of this workload
     # (dram__bytes_read.sum + dram__bytes_write.sum), see profiles/.
     traffic = INTEGRATE_TRAFFIC_BYTES.get((args.workload, args.precision))
-    roofline = {"bound": "alu", "kernel": "integrate_kernel", "achieved": round(achieved, 3),
+    kernel = "integrate_tones_kernel" if any(r["field"].get("tones") for r in reqs) else "integrate_kernel"
+    roofline = {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3),
                 "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "traffic": traffic, "integrate_ms": round(mean_int, 4), "chain_ms": round(float(np.mean(chain_ms)), 4),
