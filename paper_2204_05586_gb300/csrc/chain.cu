@@ -302,12 +302,14 @@ __global__ void __launch_bounds__(128) chain_up_kernel(ChainArgs a, int level)
         Op<N> B;
         B.identity();
         if (level == 0) {
-            // lane run: U_{k1-1} ... U_{k0}
+            // lane run: U_{k1-1} ... U_{k0} (the first operator loaded, not
+            // multiplied into the identity)
             const int run = s.chain_run;
             const int64_t k0 = (local * kFan + lane) * run;
             const int64_t k1 = min(k0 + run, s.K);
             const double* U = a.U + s.sample_offset * D;
-            for (int64_t k = k0; k < k1; k++) {
+            if (k0 < k1) B.load(U + k0 * D);
+            for (int64_t k = k0 + 1; k < k1; k++) {
                 Op<N> u, t;
                 u.load(U + k * D);
                 Op<N>::mul(u, B, t);   // later operators multiply from the left
