@@ -34,7 +34,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 
 
-CXX_FLAGS = ["-x", "c++", "-O3", "-std=c++17", "-fPIC", "-pthread"]
+# -ffp-contract=off: no multiply-add is fused unless the source says fma(), so
+# the host backend gives the same results on every host architecture
+CXX_FLAGS = ["-x", "c++", "-O3", "-std=c++17", "-ffp-contract=off", "-fPIC", "-pthread"]
 
 
 def cxx() -> str:
@@ -61,7 +63,7 @@ def _cpu_sources():
 
 def _fingerprint() -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(CSRC, "*.*")) + _cpu_sources() +
+    for p in sorted(glob.glob(os.path.join(CSRC, "*.*")) + glob.glob(os.path.join(CSRC, "cpu", "*.*")) +
                     [os.path.join(INCLUDE, "spinsim.h"), os.path.join(INCLUDE, "spinsim_cpu.h")]):
         with open(p, "rb") as f:
             h.update(os.path.basename(p).encode())

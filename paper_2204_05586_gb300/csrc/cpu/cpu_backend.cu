@@ -8,6 +8,10 @@
 // each simulation's states psi_k = U_k psi_{k-1} in order, in FP64 (Eq.
 // integration_compilation), as the paper's CPU chain does.
 //
+// The small-angle FP32 variant advances four samples per thread at once
+// (lanes4.h: one SIMD vector per quantity), each lane bit-identical to the
+// one-sample path.
+//
 // Host code only: this file is linked with params.cu into
 // libspinsim_cpu.so, which calls no CUDA API and needs no GPU.
 #include <sched.h>
@@ -21,6 +25,7 @@
 
 #include "spinsim_cpu.h"
 #include "../sample_epilogue.cuh"
+#include "lanes4.h"
 
 namespace spinsim {
 namespace {
@@ -57,7 +62,104 @@ void sample_operator(const DevSim& s, int64_t k, double* out)
     finish<TONES>(stack[s.seg_log2], s, x, out);
 }
 
+// Four samples k .. k+3 (all >= 1) of one simulation at once in the
+// small-angle variant (FP32): their contexts packed lane by lane into F4
+// values, the same step loop and segment tree on F4, then each lane's
+// epilogue.  Every lane computes exactly what sample_operator computes.
+void pack(const SampleCtx<float> (&c)[4], SampleCtx<F4>& v)
+{
+    auto put = [](F4& dst, float a, float b, float d, float e) { dst.v = F4::V{a, b, d, e}; };
+#define SPINSIM_PACK(f) put(v.f, c[0].f, c[1].f, c[2].f, c[3].f)
+    SPINSIM_PACK(ebr); SPINSIM_PACK(ebi); SPINSIM_PACK(co); SPINSIM_PACK(counter);
+    for (int i = 0; i < 4; i++) { SPINSIM_PACK(Ph[i]); SPINSIM_PACK(Pl[i]); }
+    SPINSIM_PACK(za); SPINSIM_PACK(zb); SPINSIM_PACK(zbias); SPINSIM_PACK(qd3); SPINSIM_PACK(inv_n);
+    SPINSIM_PACK(q1); SPINSIM_PACK(dt); SPINSIM_PACK(c1); SPINSIM_PACK(c2);
+    for (int p = 0; p < kMaxPulses; p++) {
+        SPINSIM_PACK(amp[p]); SPINSIM_PACK(u0[p]); SPINSIM_PACK(invw[p]); SPINSIM_PACK(ghat[p]);
+    }
+    for (int j = 0; j < kMaxTones; j++) {
+        SPINSIM_PACK(tbr[j]); SPINSIM_PACK(tbi[j]); SPINSIM_PACK(tco[j]); SPINSIM_PACK(tct[j]);
+        SPINSIM_PACK(tomp[j]); SPINSIM_PACK(tomm[j]);
+    }
+#undef SPINSIM_PACK
+    v.nt = c[0].nt;            // per simulation: the same in every lane
+    v.np = c[0].np;
+    v.ng = c[0].ng;
+    v.tau = c[0].tau;
+    v.counter_on = c[0].counter_on;
+}
+
+void unpack(const Res3<F4>& v, int i, Res3<float>& x)
+{
+    for (int q = 0; q < 4; q++) x.g[q] = lane(v.g[q], i);
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) x.m[a][b] = cmk(lane(v.m[a][b].r, i), lane(v.m[a][b].i, i));
+}
+
+void unpack(const Res2<F4>& v, int i, Res2<float>& x)
+{
+    for (int q = 0; q < 3; q++) x.g[q] = lane(v.g[q], i);
+    x.a = cmk(lane(v.a.r, i), lane(v.a.i, i));
+    x.b = cmk(lane(v.b.r, i), lane(v.b.i, i));
+}
+
+template <int N, int METHOD>
+void sample_operators4(const DevSim& s, int64_t k, double* out)
+{
+    using Res = typename ResType<N, float>::type;
+    using Res4 = typename ResType<N, F4>::type;
+    constexpr int OPD = N == 3 ? 18 : 4;
+    SampleCtx<float> c1[4];
+    double beta[4], gsum[4];
+    for (int i = 0; i < 4; i++) gsum[i] = make_ctx<float, N, false>(s, k + i, c1[i], beta[i]);
+    SampleCtx<F4> c;
+    pack(c1, c);
+    Res4 stack[kSegLog2 + 1];
+    const int nseg = 1 << s.seg_log2;
+    for (int q = 0; q < nseg; q++) {
+        const int64_t lo = ((int64_t)q * s.L) >> s.seg_log2, hi = ((int64_t)(q + 1) * s.L) >> s.seg_log2;
+        Res4 X;
+        res_zero(X);
+        for (int64_t l = lo; l < hi; l++) step_apply<F4, METHOD, true, false>(c, F4((float)l), c.tau, X);
+        int h = 0;
+        while ((q >> h) & 1) {
+            Res4 t;
+            res_mul(X, stack[h], t);
+            X = t;
+            h++;
+        }
+        stack[h] = X;
+    }
+    for (int i = 0; i < 4; i++) {
+        Res r;
+        unpack(stack[s.seg_log2], i, r);
+        SampleExact x;
+        make_exact<N, false>(s, k + i, beta[i], gsum[i], x);
+        finish<false>(r, s, x, out + i * OPD);
+    }
+}
+
 using SampleFn = void (*)(const DevSim&, int64_t, double*);
+
+// The four-sample form of the small-angle FP32 variant, or nullptr.
+SampleFn select_sample4_fn(int spin_x2, int precision, int method, int variant)
+{
+    if (!precision || variant != kVariantSmall) return nullptr;
+    if (spin_x2 == 2) {
+        switch (method) {
+            case SPINSIM_METHOD_CF4: return sample_operators4<3, 0>;
+            case SPINSIM_METHOD_MIDPOINT: return sample_operators4<3, 1>;
+            case SPINSIM_METHOD_HEUN: return sample_operators4<3, 2>;
+            default: return nullptr;
+        }
+    }
+    switch (method) {
+        case SPINSIM_METHOD_CF4: return sample_operators4<2, 0>;
+        case SPINSIM_METHOD_MIDPOINT: return sample_operators4<2, 1>;
+        case SPINSIM_METHOD_HEUN: return sample_operators4<2, 2>;
+        default: return nullptr;
+    }
+}
 
 template <int N, typename R, bool SMALL, bool TONES>
 SampleFn pick_method(int method)
@@ -181,6 +283,7 @@ struct Job {
     int64_t req;
     DevSim d;
     SampleFn fn;
+    SampleFn fn4;   // four samples at once, or nullptr
     size_t u_off;   // offset of its operators in the group buffer (doubles)
 };
 
@@ -232,7 +335,9 @@ int cpu_simulate(const spinsim_config* cfg_in, const spinsim_request* reqs, spin
         Job j;
         j.req = i;
         fill_devsim(cfg, reqs[i], c.K, c.L, j.d);
-        j.fn = select_sample_fn(reqs[i].spin_x2, cfg.precision, cfg.method, request_variant(cfg, reqs[i], c.L));
+        const int variant = request_variant(cfg, reqs[i], c.L);
+        j.fn = select_sample_fn(reqs[i].spin_x2, cfg.precision, cfg.method, variant);
+        j.fn4 = select_sample4_fn(reqs[i].spin_x2, cfg.precision, cfg.method, variant);
         j.u_off = 0;
         res[i].trotter_squares = j.d.tau;
         if (!j.fn) {
@@ -271,11 +376,12 @@ int cpu_simulate(const spinsim_config* cfg_in, const spinsim_request* reqs, spin
             const Job& jb = jobs[items[it].first];
             const int opd = jb.d.spin_x2 == 2 ? 18 : 4;
             const int64_t k1 = std::min(items[it].second + kChunk, jb.d.K);
-            for (int64_t k = items[it].second; k < k1; k++) {
-                double* out = Ub + jb.u_off + k * opd;
-                if (k == 0) store_identity(jb.d.spin_x2 + 1, out);
-                else jb.fn(jb.d, k, out);
-            }
+            int64_t k = items[it].second;
+            if (k == 0) store_identity(jb.d.spin_x2 + 1, Ub + jb.u_off);
+            k = std::max<int64_t>(k, 1);
+            if (jb.fn4)
+                for (; k + 4 <= k1; k += 4) jb.fn4(jb.d, k, Ub + jb.u_off + k * opd);
+            for (; k < k1; k++) jb.fn(jb.d, k, Ub + jb.u_off + k * opd);
         });
         parallel_for(nt, (int64_t)(g1 - g0), [&](int64_t j) {
             const Job& jb = jobs[g0 + j];

@@ -66,6 +66,16 @@ __device__ __forceinline__ void allow_dependent_launch()
 }
 #endif
 
+// The bulk type's precision class: FP32 (float, or a host vector of floats
+// that carries several samples at once, which specialises this) or FP64.
+template <typename R>
+struct BulkTraits {
+    static constexpr bool fp32 = sizeof(R) == 4;
+    static constexpr int lanes = 1;   // samples carried by one value
+};
+template <typename R>
+constexpr bool kFP32 = BulkTraits<R>::fp32;
+
 template <typename R>
 struct cx {
     R r, i;
@@ -138,7 +148,7 @@ SPINSIM_HD void small_sincos(R x, R& s, R& c)
 {
     if (fabs(x) <= R(0.0625)) {
         R x2 = x * x;
-        if constexpr (sizeof(R) == 4) {
+        if constexpr (kFP32<R>) {
             s = x * (R(1) - x2 * (R(1.0 / 6) - x2 * R(1.0 / 120)));
             c = R(1) - x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * R(1.0 / 720)));
         } else {
@@ -160,7 +170,7 @@ SPINSIM_HD void small_sincos_m(R x, R& sm, R& cm)
 {
     if (fabs(x) <= R(0.0625)) {
         R x2 = x * x;
-        if constexpr (sizeof(R) == 4) {
+        if constexpr (kFP32<R>) {
             sm = -x * x2 * (R(1.0 / 6) - x2 * R(1.0 / 120));
             cm = -x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * R(1.0 / 720)));
         } else {
@@ -321,7 +331,7 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
     const SinCos<R> eb = sincos_cold((R)beta);
     c.ebr = eb.c;
     c.ebi = eb.s;
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (kFP32<R>) {
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             c.Ph[i] = s.f_ph[i];
@@ -356,7 +366,7 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
     for (int p = 0; p < kMaxPulses; p++) {
         c.amp[p] = R(0); c.u0[p] = R(0); c.invw[p] = R(0); c.ghat[p] = R(0);
         if (p < c.np) {
-            if constexpr (sizeof(R) == 4) {
+            if constexpr (kFP32<R>) {
                 c.amp[p] = s.f_amp[p];
                 c.invw[p] = s.f_invw[p];
             } else {
@@ -385,7 +395,7 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
                 c.tbi[j] = e.s;
                 c.tco[j] = (R)(s.frame ? s.t_co0[j] - gsum : s.t_co0[j]);
                 c.tct[j] = (R)(s.frame ? s.t_ct0[j] + gsum : s.t_ct0[j]);
-                if constexpr (sizeof(R) == 4) {
+                if constexpr (kFP32<R>) {
                     c.tomp[j] = s.f_tom_plus[j];
                     c.tomm[j] = s.f_tom_minus[j];
                 } else {
@@ -552,7 +562,7 @@ struct NodeField {
 template <typename R>
 SPINSIM_HD void second_order_sincos(R x, R& s, R& c)
 {
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (kFP32<R>) {
         x = fma(R(-kTwoPi), rintf(x * R(1.0 / kTwoPi)), x);
 #ifdef __CUDA_ARCH__
         __sincosf(x, &s, &c);
@@ -704,11 +714,10 @@ SPINSIM_HD void res2_full(const Res2<R>& x, cx<R>& a, cx<R>& b)
 //   alpha - 1 = -(1 - cos(th/2)) - i f v_z,  beta = f (v_y - i v_x),  f = sin(th/2)/th.
 // First order: f -> 1/2.  The rest uses f - 1/2 and 1 - cos(th/2) = 2 sin^2(th/4),
 // both from their Taylor series in y = th^2/4 for th/2 <= 1/16.
+// f - 1/2 and 1 - cos(th/2) of the SU(2) exponential from t2 = th^2.
 template <typename R>
-SPINSIM_HD void expm_half_res(R vx, R vy, R vz, Res2<R>& e)
+SPINSIM_HD void half_angle_terms(R t2, R& fm, R& g)
 {
-    R t2 = vx * vx + vy * vy + vz * vz;
-    R fm, g;
     if (t2 <= R(0.015625)) {      // (th/2)^2 <= 1/256
         R y = R(0.25) * t2;
         fm = R(-0.5) * y * (R(1.0 / 6) - y * (R(1.0 / 120) - y * (R(1.0 / 5040) - y * R(1.0 / 362880))));
@@ -719,6 +728,13 @@ SPINSIM_HD void expm_half_res(R vx, R vy, R vz, Res2<R>& e)
         fm = sin(R(0.5) * th) / th - R(0.5);
         g = R(2) * s4 * s4;
     }
+}
+
+template <typename R>
+SPINSIM_HD void expm_half_res(R vx, R vy, R vz, Res2<R>& e)
+{
+    R fm, g;
+    half_angle_terms(vx * vx + vy * vy + vz * vz, fm, g);
     e.g[0] = vx; e.g[1] = vy; e.g[2] = vz;
     e.a = cmk(-g, -fm * vz);
     e.b = cmk(fm * vy, -fm * vx);
@@ -832,13 +848,17 @@ SPINSIM_HD void expm_one_res_n(R vx, R vy, R vz, R qd3, int tau, R inv_n, R q1, 
     const R vp2 = vx * vx + vy * vy;
     R epr = R(1), epi = R(0);   // e^{i phi}
     R Phi = R(0);
-    if (vp2 > R(0)) {
-        // Phi and e^{i phi} enter only the second-order rest (the first-order
-        // part is v itself), so a reciprocal square root is precise enough.
-        const R rinv = rsqrt(vp2);
-        epr = vx * rinv;
-        epi = vy * rinv;
-        Phi = vp2 * rinv * inv_n;
+    if constexpr (BulkTraits<R>::lanes == 1) {
+        if (vp2 > R(0)) {
+            // Phi and e^{i phi} enter only the second-order rest (the first-order
+            // part is v itself), so a reciprocal square root is precise enough.
+            const R rinv = rsqrt(vp2);
+            epr = vx * rinv;
+            epi = vy * rinv;
+            Phi = vp2 * rinv * inv_n;
+        }
+    } else {
+        transverse_axis_lanes(vx, vy, vp2, inv_n, epr, epi, Phi);   // the same, lane by lane
     }
     const R h0 = fma(R(-0.5), z, R(-0.5) * qd3);   // th_0 / 2
     const R h1 = qd3;                              // th_1 / 2
