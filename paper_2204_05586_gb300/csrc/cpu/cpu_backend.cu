@@ -8,9 +8,8 @@
 // each simulation's states psi_k = U_k psi_{k-1} in order, in FP64 (Eq.
 // integration_compilation), as the paper's CPU chain does.
 //
-// The small-angle FP32 variant advances four samples per thread at once
-// (lanes4.h: one SIMD vector per quantity), each lane bit-identical to the
-// one-sample path.
+// In FP32 each thread advances four samples at once (lanes4.h: one SIMD
+// vector per quantity), each lane bit-identical to the one-sample path.
 //
 // Host code only: this file is linked with params.cu into
 // libspinsim_cpu.so, which calls no CUDA API and needs no GPU.
@@ -62,10 +61,10 @@ void sample_operator(const DevSim& s, int64_t k, double* out)
     finish<TONES>(stack[s.seg_log2], s, x, out);
 }
 
-// Four samples k .. k+3 (all >= 1) of one simulation at once in the
-// small-angle variant (FP32): their contexts packed lane by lane into F4
-// values, the same step loop and segment tree on F4, then each lane's
-// epilogue.  Every lane computes exactly what sample_operator computes.
+// Four samples k .. k+3 (all >= 1) of one simulation at once (FP32): their
+// contexts packed lane by lane into F4 values, the same step loop and
+// segment tree on F4, then each lane's epilogue.  Every lane computes exactly
+// what sample_operator computes.
 void pack(const SampleCtx<float> (&c)[4], SampleCtx<F4>& v)
 {
     auto put = [](F4& dst, float a, float b, float d, float e) { dst.v = F4::V{a, b, d, e}; };
@@ -103,7 +102,7 @@ void unpack(const Res2<F4>& v, int i, Res2<float>& x)
     x.b = cmk(lane(v.b.r, i), lane(v.b.i, i));
 }
 
-template <int N, int METHOD>
+template <int N, int METHOD, bool SMALL, bool TONES>
 void sample_operators4(const DevSim& s, int64_t k, double* out)
 {
     using Res = typename ResType<N, float>::type;
@@ -111,7 +110,7 @@ void sample_operators4(const DevSim& s, int64_t k, double* out)
     constexpr int OPD = N == 3 ? 18 : 4;
     SampleCtx<float> c1[4];
     double beta[4], gsum[4];
-    for (int i = 0; i < 4; i++) gsum[i] = make_ctx<float, N, false>(s, k + i, c1[i], beta[i]);
+    for (int i = 0; i < 4; i++) gsum[i] = make_ctx<float, N, TONES>(s, k + i, c1[i], beta[i]);
     SampleCtx<F4> c;
     pack(c1, c);
     Res4 stack[kSegLog2 + 1];
@@ -120,7 +119,7 @@ void sample_operators4(const DevSim& s, int64_t k, double* out)
         const int64_t lo = ((int64_t)q * s.L) >> s.seg_log2, hi = ((int64_t)(q + 1) * s.L) >> s.seg_log2;
         Res4 X;
         res_zero(X);
-        for (int64_t l = lo; l < hi; l++) step_apply<F4, METHOD, true, false>(c, F4((float)l), c.tau, X);
+        for (int64_t l = lo; l < hi; l++) step_apply<F4, METHOD, SMALL, TONES>(c, F4((float)l), c.tau, X);
         int h = 0;
         while ((q >> h) & 1) {
             Res4 t;
@@ -134,31 +133,40 @@ void sample_operators4(const DevSim& s, int64_t k, double* out)
         Res r;
         unpack(stack[s.seg_log2], i, r);
         SampleExact x;
-        make_exact<N, false>(s, k + i, beta[i], gsum[i], x);
-        finish<false>(r, s, x, out + i * OPD);
+        make_exact<N, TONES>(s, k + i, beta[i], gsum[i], x);
+        finish<TONES>(r, s, x, out + i * OPD);
     }
 }
 
 using SampleFn = void (*)(const DevSim&, int64_t, double*);
 
-// The four-sample form of the small-angle FP32 variant, or nullptr.
-SampleFn select_sample4_fn(int spin_x2, int precision, int method, int variant)
+template <int N, bool SMALL, bool TONES>
+SampleFn pick_method4(int method)
 {
-    if (!precision || variant != kVariantSmall) return nullptr;
-    if (spin_x2 == 2) {
-        switch (method) {
-            case SPINSIM_METHOD_CF4: return sample_operators4<3, 0>;
-            case SPINSIM_METHOD_MIDPOINT: return sample_operators4<3, 1>;
-            case SPINSIM_METHOD_HEUN: return sample_operators4<3, 2>;
-            default: return nullptr;
-        }
-    }
     switch (method) {
-        case SPINSIM_METHOD_CF4: return sample_operators4<2, 0>;
-        case SPINSIM_METHOD_MIDPOINT: return sample_operators4<2, 1>;
-        case SPINSIM_METHOD_HEUN: return sample_operators4<2, 2>;
+        case SPINSIM_METHOD_CF4: return sample_operators4<N, 0, SMALL, TONES>;
+        case SPINSIM_METHOD_MIDPOINT: return sample_operators4<N, 1, SMALL, TONES>;
+        case SPINSIM_METHOD_HEUN: return sample_operators4<N, 2, SMALL, TONES>;
         default: return nullptr;
     }
+}
+
+template <int N>
+SampleFn pick_variant4(int method, int variant)
+{
+    switch (variant) {
+        case kVariantGeneral: return pick_method4<N, false, false>(method);
+        case kVariantSmall: return pick_method4<N, true, false>(method);
+        case kVariantTones: return pick_method4<N, false, true>(method);
+        default: return nullptr;
+    }
+}
+
+// The four-sample form of an FP32 variant (FP64 runs one sample at a time).
+SampleFn select_sample4_fn(int spin_x2, int precision, int method, int variant)
+{
+    if (!precision) return nullptr;
+    return spin_x2 == 2 ? pick_variant4<3>(method, variant) : pick_variant4<2>(method, variant);
 }
 
 template <int N, typename R, bool SMALL, bool TONES>

@@ -8,8 +8,8 @@
 // at once.  Every operation is the float operation of the scalar path applied
 // lane by lane (std::fma for fma, the C library for exp / sin / cos / rint),
 // so each lane's result is bit-identical to the scalar computation.  Only
-// what the small-angle variant's step loop uses is provided; its two
-// value-dependent branches have lane-wise overloads here.
+// what the step loops use is provided; their value-dependent branches have
+// lane-wise overloads here.
 #pragma once
 #include <cmath>
 #include <type_traits>
@@ -67,7 +67,45 @@ inline F4 sinf(F4 a) { return lanewise(a, [](float x) { return std::sin(x); }); 
 inline F4 cosf(F4 a) { return lanewise(a, [](float x) { return std::cos(x); }); }
 inline F4 rintf(F4 a) { return lanewise(a, [](float x) { return std::rint(x); }); }
 
-// Lane-wise forms of the step arithmetic's value-dependent branches.
+// Lane-wise forms of the step arithmetic's value-dependent branches: the
+// small-angle series when every lane's angle is small, else lane by lane.
+inline bool all_small(F4 x)
+{
+    bool r = true;
+    for (int i = 0; i < 4; i++) r = r && std::fabs(x.v[i]) <= 0.0625f;
+    return r;
+}
+
+inline void small_sincos(F4 x, F4& s, F4& c)
+{
+    if (all_small(x)) {
+        sincos_series(x, s, c);
+        return;
+    }
+    for (int i = 0; i < 4; i++) {
+        float a, b;
+        small_sincos<float>(x.v[i], a, b);
+        s.v[i] = a;
+        c.v[i] = b;
+    }
+}
+
+inline void small_sincos_m(F4 x, F4& sm, F4& cm)
+{
+    if (all_small(x)) {
+        sincos_m_series(x, sm, cm);
+        return;
+    }
+    for (int i = 0; i < 4; i++) {
+        float a, b;
+        small_sincos_m<float>(x.v[i], a, b);
+        sm.v[i] = a;
+        cm.v[i] = b;
+    }
+}
+
+inline F4 sine_cycle_cold(F4 u) { return lanewise(u, [](float x) { return sine_cycle_cold<float>(x); }); }
+
 inline void half_angle_terms(F4 t2, F4& fm, F4& g)
 {
     for (int i = 0; i < 4; i++) {

@@ -184,6 +184,36 @@ SPINSIM_HD void small_sincos_m(R x, R& sm, R& cm)
     }
 }
 
+// The branch-free series of small_sincos and small_sincos_m alone (|x| <= 1/16),
+// the same expressions, for a host type that carries several samples and
+// takes the series only when every sample's angle is small (the tests check
+// that both give the same bits).
+template <typename R>
+SPINSIM_HD void sincos_series(R x, R& s, R& c)
+{
+    R x2 = x * x;
+    if constexpr (kFP32<R>) {
+        s = x * (R(1) - x2 * (R(1.0 / 6) - x2 * R(1.0 / 120)));
+        c = R(1) - x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * R(1.0 / 720)));
+    } else {
+        s = x * (R(1) - x2 * (R(1.0 / 6) - x2 * (R(1.0 / 120) - x2 * (R(1.0 / 5040) - x2 * R(1.0 / 362880)))));
+        c = R(1) - x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * (R(1.0 / 720) - x2 * (R(1.0 / 40320) - x2 * R(1.0 / 3628800)))));
+    }
+}
+
+template <typename R>
+SPINSIM_HD void sincos_m_series(R x, R& sm, R& cm)
+{
+    R x2 = x * x;
+    if constexpr (kFP32<R>) {
+        sm = -x * x2 * (R(1.0 / 6) - x2 * R(1.0 / 120));
+        cm = -x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * R(1.0 / 720)));
+    } else {
+        sm = -x * x2 * (R(1.0 / 6) - x2 * (R(1.0 / 120) - x2 * (R(1.0 / 5040) - x2 * R(1.0 / 362880))));
+        cm = -x2 * (R(0.5) - x2 * (R(1.0 / 24) - x2 * (R(1.0 / 720) - x2 * (R(1.0 / 40320) - x2 * R(1.0 / 3628800)))));
+    }
+}
+
 // Small-angle forms of the two series above, for arguments the host has
 // bounded by |x| <= kTinyAngleBound = 2^-6 (every step angle of a
 // rotating-frame FP32 run, see small_angle_request):

@@ -65,6 +65,26 @@ int hh_small_angle_request(const spinsim_config* cfg, const spinsim_request* r, 
 }
 double hh_tiny_angle_bound() { return kTinyAngleBound; }
 
+// 1 when the branch-free series (sincos_series, sincos_m_series) give the same
+// bits as small_sincos / small_sincos_m at x (|x| <= 1/16), in float or double.
+int hh_series_match(double x, int fp32)
+{
+    if (fp32) {
+        float s1, c1, s2, c2, m1, n1, m2, n2;
+        small_sincos<float>((float)x, s1, c1);
+        sincos_series<float>((float)x, s2, c2);
+        small_sincos_m<float>((float)x, m1, n1);
+        sincos_m_series<float>((float)x, m2, n2);
+        return s1 == s2 && c1 == c2 && m1 == m2 && n1 == n2;
+    }
+    double s1, c1, s2, c2, m1, n1, m2, n2;
+    small_sincos<double>(x, s1, c1);
+    sincos_series<double>(x, s2, c2);
+    small_sincos_m<double>(x, m1, n1);
+    sincos_m_series<double>(x, m2, n2);
+    return s1 == s2 && c1 == c2 && m1 == m2 && n1 == n2;
+}
+
 // The exact first-order transverse coefficients (g_x, g_y) of sample k of a
 // request as the integrate epilogue forms them (fill_devsim, the FP64 sample
 // context with further tones, first_order_exact), and the frame's pulse part

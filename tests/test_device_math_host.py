@@ -44,6 +44,8 @@ def hh(tmp_path_factory):
     L.hh_small_angle_request.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
     L.hh_tiny_angle_bound.restype = ctypes.c_double
     L.hh_first_order.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, DP]
+    L.hh_series_match.argtypes = [ctypes.c_double, ctypes.c_int]
+    L.hh_series_match.restype = ctypes.c_int
     return L
 
 
@@ -321,3 +323,12 @@ def test_first_order_with_tones_is_the_quadrature(hh, L, frame):
             gx, gy = quadrature_first_order(req, k, L, frame, out[2] if frame else 0.0)
             scale = np.hypot(gx, gy) + 1e-3
             assert abs(out[0] - gx) < 1e-11 * scale and abs(out[1] - gy) < 1e-11 * scale, (k, out, gx, gy)
+
+
+def test_branch_free_series_match_the_branching_ones(hh):
+    """The CPU backend's four-sample type takes the series without the branch
+    when every lane is small: the same bits as the one-sample functions."""
+    rng = np.random.default_rng(9)
+    for x in np.concatenate([rng.uniform(-0.0625, 0.0625, 2000), [0.0, 0.0625, -0.0625, 1e-30, -3e-8]]):
+        assert hh.hh_series_match(float(x), 1) == 1, x
+        assert hh.hh_series_match(float(x), 0) == 1, x
