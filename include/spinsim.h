@@ -195,7 +195,9 @@ int64_t spinsim_footprint(spinsim_handle h, const spinsim_request* reqs, int64_t
  * Every request is validated first; requests that fail validation get their
  * status set and are skipped, the others run.  Returns SPINSIM_OK when every
  * request is valid and all launches were enqueued, else the first error.
- * res[i].states/spin/ops receive psi_k, <J>_k and U_k for k = 0..K-1. */
+ * res[i].states/spin/ops receive psi_k, <J>_k and U_k for k = 0..K-1.  The
+ * batch runs as one launch per spin and kernel variant, so each request's
+ * results are bit-identical to running it alone, whatever it is batched with. */
 int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_result* res, int64_t n,
                      void* stream);
 
