@@ -82,7 +82,7 @@ def test_ranks_get_distinct_sweep_inputs():
 
 
 def test_reference_arm_under_torchrun_prints_once():
-    """`bench.py --impl reference` launched as the driver launches it for N = 2:
+    """`bench.py --impl reference` launched under torchrun with N = 2:
     rank 0 times the oracle and prints one line, rank 1 exits 0 without work."""
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(free_port()),

@@ -88,7 +88,7 @@ def test_entering_states_are_the_ordered_products():
 
 
 def test_split_equals_unsplit_in_one_process(oracle_mod):
-    """The driver with an in-process exchange: every range's states equal the
+    """The split with an in-process exchange: every range's states equal the
     unsplit oracle run (spin-one and spin-half, 1 to 4 ranges)."""
     for spin_x2 in (2, 1):
         req = long_request(spin_x2)
