@@ -114,3 +114,23 @@ def test_tone_count_is_checked():
         r.field.n_tones = 1
         r.field.tone_hz[0] = float("nan")
         assert S.spinsim_simulate(sim.handle, [r], res, 0) == S.E_ARG
+
+
+def test_served_mix_equals_alone():
+    """Requests with and without tones through the serving queue: each result
+    is bit-identical to the request run alone."""
+    reqs = [tone_request(2 if s % 2 else 1, t_end=5e-4, seed=s, tones=TONES[: s % 4]) for s in range(10)]
+    alone = [run([q], precision=S.PREC_FP32_BULK)[0]["states"].cpu().numpy() for q in reqs]
+    with S.Simulator(precision=S.PREC_FP32_BULK) as sim:
+        outs = sim.allocate(reqs)
+        res = sim.results_struct(outs)
+        tickets = []
+        for q, r in zip([S.make_request(q) for q in reqs], res):
+            st, t = S.spinsim_submit(sim.handle, q, r)
+            assert st == S.OK
+            tickets.append(t)
+        for t in tickets:
+            assert S.spinsim_poll(sim.handle, t, 10_000_000) == S.OK
+    for o, r, a in zip(outs, res, alone):
+        assert r.status == S.OK
+        assert np.array_equal(torch.view_as_complex(o["states"][:o["K"]]).cpu().numpy(), a)
