@@ -121,7 +121,11 @@ def _build_locked(force: bool, verbose: bool) -> str:
         gpu_jobs = [ex.submit(compile_one, s) for s in srcs]
         host_jobs = [ex.submit(compile_host, s) for s in host_srcs]
         gpu_objs = [j.result() for j in gpu_jobs]
-        host_objs = [j.result() for j in host_jobs]
+        host_objs, host_error = None, None
+        try:
+            host_objs = [j.result() for j in host_jobs]
+        except (RuntimeError, OSError) as e:   # the GPU library does not depend on it
+            host_error = e
 
     def link(out, cmd):
         tmp = out + f".tmp{os.getpid()}"
@@ -131,6 +135,11 @@ def _build_locked(force: bool, verbose: bool) -> str:
         os.replace(tmp, out)
 
     link(LIB, [exe, *ARCH, "-shared", "-cudart", "static", *gpu_objs])
+    if host_error is not None:
+        # the CPU backend library is left unbuilt (its binding raises when it is
+        # loaded); no stamp, so the next build tries again
+        print(f"libspinsim_cpu not built: {host_error}", file=sys.stderr)
+        return LIB
     link(CPU_LIB, [cxx(), "-shared", "-pthread", *host_objs])
     with open(stamp, "w") as f:
         f.write(fp)
