@@ -226,6 +226,15 @@ def test_neural_pulse_field(oracle_mod, prec):
         assert_parity(out, oracle_run(oracle_mod, req), TOL[prec], f"neural pulse spin_x2 {spin_x2}")
 
 
+@pytest.mark.parametrize("prec", [S.PREC_FP64, S.PREC_FP32_BULK])
+def test_neural_workload_full_size(oracle_mod, prec):
+    """The paper's benchmark field exactly as the bench times it (100 ms at the
+    100 ns step, 1e5 samples x 10 steps, graph replay): every sample."""
+    req = W.neural_pulse()
+    (out,), _ = gpu_run([req], precision=prec, use_graphs=True)
+    assert_parity(out, oracle_run(oracle_mod, req), TOL[prec], "neural workload, full size")
+
+
 @pytest.mark.parametrize("frame", [True, False])
 def test_mixed_pulse_kinds_fp64(oracle_mod, frame):
     """Gaussian and sine-cycle pulses in one field, both frames, FP64, with the
