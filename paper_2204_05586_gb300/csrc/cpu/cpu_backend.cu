@@ -282,7 +282,13 @@ void parallel_for(int threads, int64_t count, F&& f)
     const int extra = (int)std::min<int64_t>(threads - 1, std::max<int64_t>(count - 1, 0));
     std::vector<std::thread> pool;
     pool.reserve(extra);
-    for (int t = 0; t < extra; t++) pool.emplace_back(worker);
+    for (int t = 0; t < extra; t++) {
+        try {
+            pool.emplace_back(worker);
+        } catch (...) {   // fewer threads: the ones running (and this one) drain the items
+            break;
+        }
+    }
     worker();
     for (auto& t : pool) t.join();
 }
