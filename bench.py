@@ -35,6 +35,19 @@ UNIT = "steps/s"
 # unit counts and the maximum SM clock (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz).
 N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# FP64 DFMA rate of this GPU measured with an FMA-chain probe (0.05 warp-DFMA per
+# clock per SM at 2.07 GHz): the chain kernels' bound
+FP64_MEASURED_TFLOPS = 0.98
+
+
+def chain_flops_per_sample(spin_x2: int, run: int) -> float:
+    """Algorithmic FP64 flops of the chain per sample (FMA = 2): the lane runs'
+    products ((run - 1) / run 3x3 complex products of 216 flops, spin-one; SU(2)
+    products of 32 for spin-half), one matrix-vector product (72 / 16), the
+    renormalisation and <J> (~60 / ~30); the trees add under 2 %."""
+    if spin_x2 == 2:
+        return (run - 1) / run * 216.0 + 72.0 + 60.0
+    return (run - 1) / run * 32.0 + 16.0 + 30.0
 L2_FLUSH_BYTES = 256 << 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one integrate launch
 # (profiles/integrate_kernel_spin_one_sensing.md, integrate_tones_kernel_multitone.md);
@@ -236,6 +249,20 @@ def run_ours(args, world, rank, local):
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "traffic": traffic, "integrate_ms": round(mean_int, 4), "chain_ms": round(float(np.mean(chain_ms)), 4),
                 "flops_per_step": round(flops / steps_per_pass, 1)}
+    # the chain's share of the step against the FP64 rate (the chain always runs in FP64)
+    def chain_run(K):   # the library's lane-run length: one level-0 warp per SM sub-partition, 4..8
+        return min(8, max(4, -(-K // (32 * 608))))
+
+    def samples(r):
+        return int(round((r["t_end"] - r["t_start"]) / r["dt_out"]))
+    cflops = sum(samples(r) * chain_flops_per_sample(r["spin_x2"], chain_run(samples(r))) for r in reqs)
+    mean_chain = float(np.mean(chain_ms))
+    chain_tf = cflops / (mean_chain / 1e3) / 1e12
+    chain_roofline = {"bound": "fp64", "kernels": "chain_up_kernel, chain_apply_kernel",
+                      "achieved": round(chain_tf, 4), "peak": FP64_MEASURED_TFLOPS, "unit": "TFLOP/s",
+                      "frac": round(chain_tf / FP64_MEASURED_TFLOPS, 4),
+                      "peak_source": "measured FMA-chain probe on this GPU model",
+                      "flops_per_sample": round(cflops / sum(samples(r) for r in reqs), 1)}
     if prec == S.PREC_FP64:
         roofline.update({"peak": 1.25, "frac": round(achieved / 1.25, 4),
                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (profiling recipe table)"})
@@ -275,7 +302,8 @@ def run_ours(args, world, rank, local):
                        "l2": "flushed between timed steps (256 MiB device write outside the step events)",
                        "launch": "each step one CUDA graph replay (integrate + chain kernels)",
                        "parallelism": f"weak x{world}, independent simulations per GPU"},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "wall_s_timed_loop": wall}
+            "roofline": roofline, "chain_roofline": chain_roofline, "e2e": e2e, "gpu_launches": launches,
+            "wall_s_timed_loop": wall}
     if clk:
         line["clocks"] = clk
     # ---- rank 0: accuracy vs the FP64 oracle, oracle CPU baseline, FP64-plain kernel
