@@ -321,6 +321,10 @@ def run_ours(args, world, rank, local):
                                           "then the sequential chain), tau = 24, FP64"}
         gpu_states = torch.view_as_complex(outs[0]["states"][:outs[0]["K"]]).cpu().numpy()
         line["state_err_vs_oracle"] = float(np.abs(gpu_states - ref["states"]).max())
+        # the paper's own error measure (Eq. error, 1/K outside the root as printed) and the
+        # states' norm drift, beside the primary max |dpsi|
+        line["paper_error_metric_vs_oracle"] = float(O.error_metric(np.ascontiguousarray(gpu_states), ref["states"]))
+        line["norm_drift"] = float(np.abs(np.linalg.norm(gpu_states, axis=1) - 1.0).max())
         if prec == S.PREC_FP32_BULK:
             sim64 = S.Simulator(precision=S.PREC_FP64, device=local)
             o64 = sim64.allocate(reqs, device=dev)
@@ -335,6 +339,7 @@ def run_ours(args, world, rank, local):
             s64 = torch.view_as_complex(o64[0]["states"][:o64[0]["K"]]).cpu().numpy()
             line["fp64_plain"] = {"value": fp64_rate, "unit": UNIT, "state_err_vs_oracle":
                                   float(np.abs(s64 - ref["states"]).max()),
+                                  "norm_drift": float(np.abs(np.linalg.norm(s64, axis=1) - 1.0).max()),
                                   "speedup_fp32_bulk_over_fp64": value / world / fp64_rate}
             sim64.close()
         # the library's own multicore CPU backend (same algorithm and precision,
