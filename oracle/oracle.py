@@ -52,6 +52,12 @@ class _Field(ctypes.Structure):
         ("tone_y_hz", ctypes.c_double * MAX_TONES),
         ("tone_hz", ctypes.c_double * MAX_TONES),
         ("tone_phase", ctypes.c_double * MAX_TONES),
+        ("qd_on", ctypes.c_int32),
+        ("pad3_", ctypes.c_int32),
+        ("qd_x_hz", ctypes.c_double * 2),
+        ("qd_y_hz", ctypes.c_double * 2),
+        ("qd_hz", ctypes.c_double * 2),
+        ("qd_phase", ctypes.c_double * 2),
     ]
 
 
@@ -91,6 +97,8 @@ def _load():
             lib = ctypes.CDLL(os.environ.get("SPINSIM_ORACLE_LIB") or build())
             dp = ctypes.POINTER(ctypes.c_double)
             lib.oracle_field_sample.argtypes = [ctypes.POINTER(_Field), ctypes.c_double, dp]
+            lib.oracle_field_sample_quad.argtypes = [ctypes.POINTER(_Field), ctypes.c_double, dp]
+            lib.oracle_expm_general.argtypes = [dp, ctypes.c_double, dp]
             lib.oracle_expm_spin_half.argtypes = [ctypes.c_double] * 4 + [dp]
             for name in ("oracle_trotter_T", "oracle_expm_spin_one", "oracle_expm_spin_one_residual"):
                 getattr(lib, name).argtypes = [ctypes.c_double] * 5 + [ctypes.c_int, dp]
@@ -139,6 +147,12 @@ def _field(f: dict) -> _Field:
     s.n_tones = len(tones)
     for j, (x, y, hz, ph) in enumerate(tones):
         s.tone_x_hz[j], s.tone_y_hz[j], s.tone_hz[j], s.tone_phase[j] = x, y, hz, ph
+    qdrives = list(f.get("qdrives", ()))
+    if len(qdrives) > 2:
+        raise ValueError("two quadrupole drives at most")
+    s.qd_on = 1 if qdrives else 0
+    for p, (x, y, hz, ph) in enumerate(qdrives):
+        s.qd_x_hz[p], s.qd_y_hz[p], s.qd_hz[p], s.qd_phase[p] = x, y, hz, ph
     return s
 
 
@@ -163,6 +177,22 @@ def field_sample(field: dict, t: float) -> np.ndarray:
     out = np.zeros(4)
     _load().oracle_field_sample(ctypes.byref(_field(field)), t, _dp(out))
     return out
+
+
+def field_sample_quad(field: dict, t: float) -> np.ndarray:
+    """(w_xz, w_yz, w_x2y2, w_xy) of the quadrupole drives at time t in rad/s."""
+    out = np.zeros(4)
+    _load().oracle_field_sample_quad(ctypes.byref(_field(field)), t, _dp(out))
+    return out
+
+
+def expm_general(w, dt) -> np.ndarray:
+    """exp(-i dt sum_j w_j G_j) over the spin-one su(3) basis (J_x, J_y, J_z, Q,
+    D_xz, D_yz, D_x2y2, D_xy)."""
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    out = np.zeros(18)
+    _load().oracle_expm_general(_dp(w), dt, _dp(out))
+    return out.view(np.complex128).reshape(3, 3)
 
 
 def expm_spin_half(wx, wy, wz, dt) -> np.ndarray:
@@ -246,6 +276,8 @@ def simulate(spin_x2, field, t_start, t_end, dt, dt_out, psi0, *, rotating_frame
     psi0 = np.ascontiguousarray(np.asarray(psi0, dtype=np.complex128))
     if psi0.shape != (n,):
         raise ValueError("psi0 has the wrong length")
+    if spin_x2 == 1 and field.get("qdrives"):
+        raise ValueError("quadrupole drives need spin one")
     if threads > 1:
         ops = sample_operators(spin_x2, field, t_start, t_end, dt, dt_out, rotating_frame=rotating_frame,
                                tau=tau, method=method, threads=threads)

@@ -18,6 +18,8 @@
  *   spin-half exponential      Sec. 1.2.3 (analytic SU(2) form)
  *   spin-one exponential       Sec. 1.2.3 (Eqs. lie_trotter, lie_trotter_4,
  *                              residual squaring s = (a + 2I) a, expm1 diagonal)
+ *   full su(3) spin-one        Sec. 1.2.1 (an arbitrary point in su(3): the
+ *                              exponential series with scaling and squaring)
  *   sample operators U_k       Sec. 1.2.4 (U_k = u_{L-1} ... u_0, delta_t = Delta_t / L)
  *   state chain                Sec. 1.2.4 (Eq. integration_compilation, psi_k = U_k psi_{k-1})
  *   spin projection            Sec. 1.2.1 (<J> = psi^dagger J psi)
@@ -40,6 +42,9 @@
  *     samples and none at t_end.
  *   - The quadratic shift multiplies the traceless Q = diag(1,-2,1)/3.
  *   - Basis order is m = +j ... -j.
+ *   - The four operators that complete su(3) (the paper's U_1, U_2, V_1, V_2
+ *     come from a basis it cites but does not print) are taken as the
+ *     symmetric products D_xz, D_yz, D_x2y2, D_xy of the spin matrices.
  *
  * Build: gcc -O2 -fPIC -shared -std=c11 spinsim_oracle.c -o libspinsim_oracle.so -lm
  * (no fast-math: every transcendental is the correctly-behaved libm one).
@@ -89,6 +94,18 @@ typedef struct {
     double tone_y_hz[OR_MAX_TONES];
     double tone_hz[OR_MAX_TONES];
     double tone_phase[OR_MAX_TONES];
+    /* quadrupole drives (spin-one, qd_on = 1), completing su(3) with the four
+     * symmetric products D_xz = {J_x, J_z}, D_yz = {J_y, J_z},
+     * D_x2y2 = J_x^2 - J_y^2, D_xy = {J_x, J_y} ({A, B} = AB + BA):
+     *   w_xz  = 2 pi qd_x_hz[0] cos(ph_0),  w_yz = 2 pi qd_y_hz[0] sin(ph_0),
+     *   w_x2y2 = 2 pi qd_x_hz[1] cos(ph_1), w_xy = 2 pi qd_y_hz[1] sin(ph_1),
+     * ph_p = 2 pi qd_hz[p] t + qd_phase[p].                                     */
+    int32_t qd_on;
+    int32_t pad3_;
+    double qd_x_hz[2];
+    double qd_y_hz[2];
+    double qd_hz[2];
+    double qd_phase[2];
 } oracle_field;
 
 /* Field functions (w_x, w_y, w_z, w_q) at time t, in rad/s. */
@@ -115,6 +132,16 @@ void oracle_field_sample(const oracle_field* f, double t, double w[4])
     }
     w[2] = 2.0 * OR_PI * bz;
     w[3] = 2.0 * OR_PI * f->quad_hz;
+}
+
+/* Quadrupole-drive coefficients (w_xz, w_yz, w_x2y2, w_xy) at time t, in rad/s. */
+void oracle_field_sample_quad(const oracle_field* f, double t, double u[4])
+{
+    for (int p = 0; p < 2; p++) {
+        double ph = 2.0 * OR_PI * f->qd_hz[p] * t + f->qd_phase[p];
+        u[2 * p] = f->qd_on ? 2.0 * OR_PI * f->qd_x_hz[p] * cos(ph) : 0.0;
+        u[2 * p + 1] = f->qd_on ? 2.0 * OR_PI * f->qd_y_hz[p] * sin(ph) : 0.0;
+    }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -292,9 +319,96 @@ void oracle_expm_spin_one_residual(double wx, double wy, double wz, double wq, d
         }
 }
 
-/* One exponential exp(-i H dt) for H = w.A in the chosen spin. */
-static void expm_field(int spin_x2, const double w[4], double dt, int tau, cplx E[3][3])
+/* ------------------------------------------------------------------------- */
+/* Full su(3) spin-one Hamiltonians (Sec. 1.2.1: "an arbitrary point in       */
+/* su(3)").  Basis: J_x, J_y, J_z, Q and the symmetric products D_xz, D_yz,   */
+/* D_x2y2, D_xy of the spin matrices, formed here by matrix products.          */
+/* ------------------------------------------------------------------------- */
+static void su3_basis(cplx G[8][3][3])
 {
+    cplx J[3][3][3];
+    memset(J, 0, sizeof(J));
+    double r = 1.0 / sqrt(2.0);
+    J[0][0][1] = r; J[0][1][0] = r; J[0][1][2] = r; J[0][2][1] = r;
+    J[1][1][0] = I * r; J[1][0][1] = -I * r; J[1][2][1] = I * r; J[1][1][2] = -I * r;
+    J[2][0][0] = 1.0; J[2][2][2] = -1.0;
+    memset(G, 0, 8 * sizeof(G[0]));
+    for (int a = 0; a < 3; a++) mat_copy(G[a], J[a]);
+    G[3][0][0] = 1.0 / 3.0; G[3][1][1] = -2.0 / 3.0; G[3][2][2] = 1.0 / 3.0;
+    cplx xz[3][3], zx[3][3], yz[3][3], zy[3][3], xx[3][3], yy[3][3], xy[3][3], yx[3][3];
+    mat_mul(3, J[0], J[2], xz); mat_mul(3, J[2], J[0], zx);
+    mat_mul(3, J[1], J[2], yz); mat_mul(3, J[2], J[1], zy);
+    mat_mul(3, J[0], J[0], xx); mat_mul(3, J[1], J[1], yy);
+    mat_mul(3, J[0], J[1], xy); mat_mul(3, J[1], J[0], yx);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            G[4][i][j] = xz[i][j] + zx[i][j];
+            G[5][i][j] = yz[i][j] + zy[i][j];
+            G[6][i][j] = xx[i][j] - yy[i][j];
+            G[7][i][j] = xy[i][j] + yx[i][j];
+        }
+}
+
+/* exp(-i H dt) for H = sum_j w_j G_j (spin-one, 8 coefficients), by the series
+ * sum_k A^k / k! of A = -i H dt / 2^s (s halvings until the row-sum norm is at
+ * most 1/2, 30 terms) followed by s squarings. */
+static void expm_general(const double w[8], double dt, cplx E[3][3])
+{
+    cplx G[8][3][3], A[3][3];
+    su3_basis(G);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            cplx h = 0.0;
+            for (int a = 0; a < 8; a++) h += w[a] * G[a][i][j];
+            A[i][j] = -I * h * dt;
+        }
+    double norm = 0.0;
+    for (int i = 0; i < 3; i++) {
+        double row = 0.0;
+        for (int j = 0; j < 3; j++) row += cabs(A[i][j]);
+        if (row > norm) norm = row;
+    }
+    int s = 0;
+    while (norm > 0.5) { norm *= 0.5; s++; }
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) A[i][j] = ldexp(1.0, -s) * A[i][j];
+    cplx term[3][3], tmp[3][3];
+    mat_identity(3, E);
+    mat_identity(3, term);
+    for (int k = 1; k <= 30; k++) {
+        mat_mul(3, term, A, tmp);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                term[i][j] = tmp[i][j] / (double)k;
+                E[i][j] += term[i][j];
+            }
+    }
+    for (int q = 0; q < s; q++) {
+        mat_mul(3, E, E, tmp);
+        mat_copy(E, tmp);
+    }
+}
+
+void oracle_expm_general(const double w[8], double dt, double* out /* [3][3] re,im */)
+{
+    cplx E[3][3];
+    expm_general(w, dt, E);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            out[2 * (3 * i + j)] = creal(E[i][j]);
+            out[2 * (3 * i + j) + 1] = cimag(E[i][j]);
+        }
+}
+
+/* One exponential exp(-i H dt) for H = w.A in the chosen spin (w: the 4
+ * coefficients of J_x, J_y, J_z, Q, then with `quad` the 4 of the quadrupole
+ * drives). */
+static void expm_field(int spin_x2, const double w[8], double dt, int tau, int quad, cplx E[3][3])
+{
+    if (spin_x2 == 2 && quad) {
+        expm_general(w, dt, E);
+        return;
+    }
     if (spin_x2 == 1) {
         double u[8];
         oracle_expm_spin_half(w[0], w[1], w[2], dt, u);
@@ -316,14 +430,23 @@ static void expm_field(int spin_x2, const double w[4], double dt, int tau, cplx 
 /* coefficients  w_x' = w_x cos a + w_y sin a,  w_y' = -w_x sin a + w_y cos a, */
 /* w_z' = w_z - w_r,  w_q' = w_q,  with a = w_r t.                            */
 /* ------------------------------------------------------------------------- */
-static void field_in_frame(const oracle_field* f, double t, double t_ref, double w_r, double w[4])
+/* The quadrupole drives transform under R as well: the pair (D_xz, D_yz)   */
+/* connects m and m -+ 1 and turns by a like (J_x, J_y); the pair            */
+/* (D_x2y2, D_xy) connects m = +1 and -1 and turns by 2a.                     */
+static void field_in_frame(const oracle_field* f, double t, double t_ref, double w_r, double w[8])
 {
     oracle_field_sample(f, t, w);
+    oracle_field_sample_quad(f, t, w + 4);
     double a = w_r * (t - t_ref);
     double wx = w[0], wy = w[1];
     w[0] = wx * cos(a) + wy * sin(a);
     w[1] = -wx * sin(a) + wy * cos(a);
     w[2] = w[2] - w_r;
+    double u0 = w[4], u1 = w[5], u2 = w[6], u3 = w[7];
+    w[4] = u0 * cos(a) + u1 * sin(a);
+    w[5] = -u0 * sin(a) + u1 * cos(a);
+    w[6] = u2 * cos(2.0 * a) + u3 * sin(2.0 * a);
+    w[7] = -u2 * sin(2.0 * a) + u3 * cos(2.0 * a);
 }
 
 /* Integration methods: 0 = CF4 (Sec. 1.2.2), 1 = midpoint Euler sampling,
@@ -344,29 +467,29 @@ static void integration_step(int spin_x2, int method, const oracle_field* f, dou
         double t2 = t + 0.5 * (1.0 + 1.0 / r3) * dt;
         double wa = (3.0 + 2.0 * r3) / 12.0;
         double wb = (3.0 - 2.0 * r3) / 12.0;
-        double h1[4], h2[4], hb1[4], hb2[4];
+        double h1[8], h2[8], hb1[8], hb2[8];
         field_in_frame(f, t1, t_ref, w_r, h1);
         field_in_frame(f, t2, t_ref, w_r, h2);
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < 8; j++) {
             hb1[j] = wa * h1[j] + wb * h2[j];
             hb2[j] = wb * h1[j] + wa * h2[j];
         }
         /* Eq. cf4_implementation: u = exp(-i Hbar_2 dt) exp(-i Hbar_1 dt) */
         cplx E1[3][3], E2[3][3];
-        expm_field(spin_x2, hb1, dt, tau, E1);
-        expm_field(spin_x2, hb2, dt, tau, E2);
+        expm_field(spin_x2, hb1, dt, tau, f->qd_on, E1);
+        expm_field(spin_x2, hb2, dt, tau, f->qd_on, E2);
         mat_identity(3, u);
         mat_mul(n, E2, E1, u);
     } else if (method == OR_METHOD_MIDPOINT) {
-        double h[4];
+        double h[8];
         field_in_frame(f, t + 0.5 * dt, t_ref, w_r, h);
-        expm_field(spin_x2, h, dt, tau, u);
+        expm_field(spin_x2, h, dt, tau, f->qd_on, u);
     } else {
-        double h0[4], h1[4], hm[4];
+        double h0[8], h1[8], hm[8];
         field_in_frame(f, t, t_ref, w_r, h0);
         field_in_frame(f, t + dt, t_ref, w_r, h1);
-        for (int j = 0; j < 4; j++) hm[j] = 0.5 * (h0[j] + h1[j]);
-        expm_field(spin_x2, hm, dt, tau, u);
+        for (int j = 0; j < 8; j++) hm[j] = 0.5 * (h0[j] + h1[j]);
+        expm_field(spin_x2, hm, dt, tau, f->qd_on, u);
     }
 }
 

@@ -16,6 +16,9 @@ the oracle's callers import.  A request is a plain ``dict``:
                    c_p <= t < c_p + w_p, else 0 (the paper's sinp pulse)
                    tones=[(x_hz, y_hz, hz, phase), ...]: up to 3 further drive
                    tones, each added to w_x, w_y like the first
+                   qdrives=[(x_hz, y_hz, hz, phase), (x_hz, y_hz, hz, phase)]: up to
+                   two quadrupole drives (spin-one), of the same form, on
+                   (D_xz, D_yz) and (D_x2y2, D_xy), completing su(3)
     t_start, t_end, dt, dt_out   seconds
     psi0           complex initial state, basis m = +j ... -j
 
@@ -37,7 +40,7 @@ UP_ONE = np.array([1.0, 0.0, 0.0], dtype=np.complex128)
 
 
 def field(bias_hz=0.0, drive_x_hz=0.0, drive_y_hz=0.0, drive_hz=0.0, drive_phase=0.0, quad_hz=0.0,
-          pulses=(), tones=()):
+          pulses=(), tones=(), qdrives=()):
     def pulse(p):
         kind = p[3] if len(p) > 3 else "gauss"
         if kind not in ("gauss", "sine"):
@@ -45,7 +48,8 @@ def field(bias_hz=0.0, drive_x_hz=0.0, drive_y_hz=0.0, drive_hz=0.0, drive_phase
         return (float(p[0]), float(p[1]), float(p[2]), kind)
     return dict(bias_hz=float(bias_hz), drive_x_hz=float(drive_x_hz), drive_y_hz=float(drive_y_hz),
                 drive_hz=float(drive_hz), drive_phase=float(drive_phase), quad_hz=float(quad_hz),
-                pulses=[pulse(p) for p in pulses], tones=[tuple(map(float, t)) for t in tones])
+                pulses=[pulse(p) for p in pulses], tones=[tuple(map(float, t)) for t in tones],
+                qdrives=[tuple(map(float, q)) for q in qdrives])
 
 
 def request(spin_x2, fld, t_start, t_end, dt, dt_out, psi0=None):

@@ -38,6 +38,11 @@ MUTATIONS = {
                            "double ph = 2.0 * OR_PI * f->tone_hz[j] * t;"),
     "tones_dropped": ("for (int j = 0; j < f->n_tones && j < OR_MAX_TONES; j++) {",
                       "for (int j = 0; j < f->n_tones - 1 && j < OR_MAX_TONES; j++) {"),
+    "su3_dxy_antisymmetric": ("G[7][i][j] = xy[i][j] + yx[i][j];", "G[7][i][j] = xy[i][j] - yx[i][j];"),
+    "su3_pair2_single_angle": ("w[6] = u2 * cos(2.0 * a) + u3 * sin(2.0 * a);", "w[6] = u2 * cos(a) + u3 * sin(a);"),
+    "qdrive_y_cos": ("u[2 * p + 1] = f->qd_on ? 2.0 * OR_PI * f->qd_y_hz[p] * sin(ph) : 0.0;",
+                     "u[2 * p + 1] = f->qd_on ? 2.0 * OR_PI * f->qd_y_hz[p] * cos(ph) : 0.0;"),
+    "su3_squaring_dropped": ("for (int q = 0; q < s; q++) {", "for (int q = 1; q < s; q++) {"),
     "jy_sign": ("J[1][0][1] = -I * r; J[1][1][0] = I * r;", "J[1][0][1] = I * r; J[1][1][0] = -I * r;"),
     "chain_transposed": ("s += U[i][j] * psi[j];", "s += U[j][i] * psi[j];"),
     "midpoint_node": ("field_in_frame(f, t + 0.5 * dt, t_ref, w_r, h);", "field_in_frame(f, t + dt, t_ref, w_r, h);"),
@@ -58,6 +63,7 @@ def test_pins_detect_mutation(name, tmp_path):
     env = dict(os.environ, SPINSIM_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_expm.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_dynamics.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_dynamics.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_su3.py")],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutation {name} survived the oracle pins:\n{r.stdout[-2000:]}"
