@@ -55,7 +55,7 @@ typedef enum {
     SPINSIM_E_CUDA = -5,          /* a CUDA runtime call or kernel launch failed              */
     SPINSIM_E_TIMEOUT = -6,       /* spinsim_poll: waited wait_us without completion          */
     SPINSIM_E_CAPACITY = -7,      /* result capacity smaller than the request's K             */
-    SPINSIM_E_UNSUPPORTED = -8    /* valid but not provided (e.g. graphs while capturing)     */
+    SPINSIM_E_UNSUPPORTED = -8    /* valid but not provided (graphs while capturing, su(3) FP32) */
 } spinsim_status;
 
 /* spinsim_result.flags bits (warnings; the request still ran). */
@@ -122,7 +122,17 @@ typedef struct {
  * a circularly polarised one has drive_x_hz = drive_y_hz.  The detuning of the
  * drive is drive_hz - bias_hz.  Tones j < n_tones are further drive terms of the
  * same form (a multi-tone drive of any polarisations, Sec. 3.1); requests with
- * tones run on a kernel variant that evaluates them, the others are unaffected. */
+ * tones run on a kernel variant that evaluates them, the others are unaffected.
+ *
+ * Full su(3) spin-one Hamiltonians (Sec. 1.2.1): with qd_on = 1 two quadrupole
+ * drives of the same form act on the symmetric products of the spin matrices
+ * D_xz = J_x J_z + J_z J_x, D_yz = J_y J_z + J_z J_y (pair 0) and
+ * D_x2y2 = J_x^2 - J_y^2, D_xy = J_x J_y + J_y J_x (pair 1):
+ *   w_xz = 2 pi qd_x_hz[0] cos(ph_0), w_yz = 2 pi qd_y_hz[0] sin(ph_0),
+ *   w_x2y2 = 2 pi qd_x_hz[1] cos(ph_1), w_xy = 2 pi qd_y_hz[1] sin(ph_1),
+ *   ph_p = 2 pi qd_hz[p] t + qd_phase[p];
+ * with J_x, J_y, J_z and Q they span su(3).  Spin-one and SPINSIM_PREC_FP64
+ * only (SPINSIM_E_ARG for spin-half, SPINSIM_E_UNSUPPORTED in FP32-bulk). */
 typedef struct {
     double bias_hz;
     double drive_x_hz;
@@ -141,6 +151,12 @@ typedef struct {
     double tone_y_hz[SPINSIM_MAX_TONES];
     double tone_hz[SPINSIM_MAX_TONES];
     double tone_phase[SPINSIM_MAX_TONES];
+    int32_t qd_on;                /* 1: the two quadrupole drives below are on (spin-one)     */
+    int32_t reserved2;            /* ignored                                                 */
+    double qd_x_hz[2];
+    double qd_y_hz[2];
+    double qd_hz[2];
+    double qd_phase[2];
 } spinsim_field;
 
 /* One simulation (Sec. 1.2.4 problem statement). */

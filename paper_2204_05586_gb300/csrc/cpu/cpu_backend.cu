@@ -33,20 +33,20 @@ namespace {
 // the 2^seg_log2 canonical segments, merged by the fixed binary tree (a
 // finished pair of equal sub-trees merges, later on the left), then the
 // epilogue.  The integrate kernel's lane that owns all segments does the same.
-template <int N, typename R, int METHOD, bool SMALL, bool TONES>
+template <int N, typename R, int METHOD, bool SMALL, bool TONES, bool SU3 = false>
 void sample_operator(const DevSim& s, int64_t k, double* out)
 {
     using Res = typename ResType<N, R>::type;
     SampleCtx<R> c;
     double beta = 0.0;
-    const double gsum = make_ctx<R, N, TONES>(s, k, c, beta);
+    const double gsum = make_ctx<R, N, TONES, SU3>(s, k, c, beta);
     Res stack[kSegLog2 + 1];
     const int nseg = 1 << s.seg_log2;
     for (int q = 0; q < nseg; q++) {
         const int64_t lo = ((int64_t)q * s.L) >> s.seg_log2, hi = ((int64_t)(q + 1) * s.L) >> s.seg_log2;
         Res X;
         res_zero(X);
-        for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES>(c, (R)l, c.tau, X);
+        for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES, SU3>(c, (R)l, c.tau, X);
         int h = 0;
         while ((q >> h) & 1) {
             Res t;
@@ -189,6 +189,17 @@ SampleFn pick_variant(int method, int variant)
         case kVariantSmall:
             if constexpr (sizeof(R) == 4) return pick_method<N, R, true, false>(method);
             else return nullptr;
+        case kVariantSU3:   // full su(3): spin-one, FP64
+            if constexpr (N == 3 && sizeof(R) == 8) {
+                switch (method) {
+                    case SPINSIM_METHOD_CF4: return sample_operator<3, double, 0, false, true, true>;
+                    case SPINSIM_METHOD_MIDPOINT: return sample_operator<3, double, 1, false, true, true>;
+                    case SPINSIM_METHOD_HEUN: return sample_operator<3, double, 2, false, true, true>;
+                    default: return nullptr;
+                }
+            } else {
+                return nullptr;
+            }
         default: return nullptr;
     }
 }
@@ -334,6 +345,7 @@ int cpu_simulate(const spinsim_config* cfg_in, const spinsim_request* reqs, spin
     std::vector<Job> jobs;
     for (int64_t i = 0; i < n; i++) {
         Checked c = check_request(&reqs[i]);
+        if (c.status == SPINSIM_OK) c.status = precision_status(cfg, reqs[i]);
         if (c.status == SPINSIM_OK) {
             if (!res[i].states) c.status = SPINSIM_E_ARG;
             else if (res[i].capacity < c.K) c.status = SPINSIM_E_CAPACITY;

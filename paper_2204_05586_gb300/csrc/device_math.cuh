@@ -278,6 +278,8 @@ struct SampleCtx {
     R amp[kMaxPulses], u0[kMaxPulses], invw[kMaxPulses], ghat[kMaxPulses];
     // further tones (the tones variant only): e^{i beta_j}, in-frame rates, Om+-_j
     R tbr[kMaxTones], tbi[kMaxTones], tco[kMaxTones], tct[kMaxTones], tomp[kMaxTones], tomm[kMaxTones];
+    // quadrupole drives (the su(3) variant only): the same per pair
+    R qbr[2], qbi[2], qco[2], qct[2], qomp[2], qomm[2];
     int nt;
     int np;
     int ng;                         // pulses [0, ng) Gaussian, [ng, np) single sine cycles
@@ -353,7 +355,7 @@ SPINSIM_COLD R sine_cycle_cold(R u)
 // Returns gsum = sum_p amp_p ghat_p (exact products of R values, in FP64)
 // and the drive phase beta (FP64) for the epilogue.  The per-simulation
 // constants come rounded to FP32 from the host for the FP32 path.
-template <typename R, int N, bool TONES = false>
+template <typename R, int N, bool TONES = false, bool SU3 = false>
 SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& beta)
 {
     const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;
@@ -433,6 +435,20 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
                     c.tomm[j] = (R)s.t_om_minus[j];
                 }
             }
+        }
+    }
+    if constexpr (SU3) {
+        // pair p turns at (p + 1) w_r in the frame, pulse part included
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+            const SinCos<R> e = sincos_cold((R)tone_phase_at(s.qd_hz[p], s.qd_phase[p], t_prev));
+            const double kg = s.frame ? (double)(p + 1) * gsum : 0.0;
+            c.qbr[p] = e.c;
+            c.qbi[p] = e.s;
+            c.qco[p] = (R)(s.qd_co0[p] - kg);
+            c.qct[p] = (R)(s.qd_ct0[p] + kg);
+            c.qomp[p] = (R)s.qd_om_plus[p];
+            c.qomm[p] = (R)s.qd_om_minus[p];
         }
     }
     return gsum;
@@ -584,6 +600,7 @@ struct NodeField {
     cx<R> co, ct;   // e^{i (beta + (w_d - w_r) tau)}, e^{i (beta + (w_d + w_r) tau)}
     R z;            // w_z' without the lab-frame bias
     cx<R> ex;       // further tones' w_x' + i w_y' (tones variant)
+    cx<R> qd[2];    // quadrupole drive pairs' u_a' + i u_b' (su(3) variant)
 };
 
 // sin and cos of an angle of any size in the bulk type, for terms whose
@@ -605,7 +622,7 @@ SPINSIM_HD void second_order_sincos(R x, R& s, R& c)
     }
 }
 
-template <typename R, bool SMALL = false, bool TONES = false>
+template <typename R, bool SMALL = false, bool TONES = false, bool SU3 = false>
 SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
 {
     R s1, c1;
@@ -658,6 +675,19 @@ SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
             }
         }
         f.ex = e;
+    }
+    if constexpr (SU3) {
+        // like a drive: Om+ e^{i (beta + (w - k w_r) tau)} + Om- e^{-i (beta + (w + k w_r) tau)}
+#pragma unroll
+        for (int p = 0; p < 2; p++) {
+            R sj, cj;
+            small_sincos(c.qco[p] * tau, sj, cj);
+            cx<R> e = cscale(cmk(c.qbr[p] * cj - c.qbi[p] * sj, fma(c.qbr[p], sj, c.qbi[p] * cj)), c.qomp[p]);
+            second_order_sincos(c.qct[p] * tau, sj, cj);
+            e.r = fma(c.qomm[p], c.qbr[p] * cj - c.qbi[p] * sj, e.r);
+            e.i = fma(-c.qomm[p], fma(c.qbr[p], sj, c.qbi[p] * cj), e.i);
+            f.qd[p] = e;
+        }
     }
 }
 
@@ -961,6 +991,117 @@ SPINSIM_HD void expm_one_res(R vx, R vy, R vz, R qd3, int tau, Res3<R>& e)
     expm_one_res_n<R, SMALL>(vx, vy, vz, qd3, tau, ldexp(R(1), -tau), R(3) * ldexp(qd3, tau), e);
 }
 
+// exp(-i H) - I as a split residual for a full su(3) spin-one H (radians):
+//   H = v_x J_x + v_y J_y + v_z J_z + v_q Q + u_0 D_xz + u_1 D_yz + u_2 D_x2y2 + u_3 D_xy,
+// D_ab the symmetric products of the spin matrices.  In the basis m = +1, 0, -1,
+// with t = v_x - i v_y, c = u_0 - i u_1 and d = u_2 - i u_3:
+//   H_00 = v_z + v_q/3, H_11 = -2 v_q/3, H_22 = -v_z + v_q/3,
+//   H_01 = (t + c)/sqrt2, H_12 = (t - c)/sqrt2, H_02 = d, H_ji = conj(H_ij).
+// The series sum_{k>=1} B^k / k! of B = -i H / 2^s (Horner over 12 terms, s
+// halvings until the row sums are at most 1/4: truncation below 3e-18), then
+// s residual squarings a <- (a + 2I) a; the first-order part of the J and Q
+// terms is taken out as g, the rest (the quadrupole drives' first order and
+// all higher orders) stays in the full matrix.  FP64 (the su(3) variant).
+template <typename R>
+SPINSIM_HD void expm_general_res(R vx, R vy, R vz, R vq, const R u[4], Res3<R>& e)
+{
+    const R r = R(kInvSqrt2);
+    const R q3 = vq * R(1.0 / 3);
+    const cx<R> t = cmk(vx, -vy), c = cmk(u[0], -u[1]), d = cmk(u[2], -u[3]);
+    cx<R> H[3][3];
+    H[0][0] = cmk(vz + q3, R(0));
+    H[1][1] = cmk(R(-2) * q3, R(0));
+    H[2][2] = cmk(q3 - vz, R(0));
+    H[0][1] = cscale(cadd(t, c), r);
+    H[1][2] = cscale(csub(t, c), r);
+    H[0][2] = d;
+    H[1][0] = cconj(H[0][1]);
+    H[2][1] = cconj(H[1][2]);
+    H[2][0] = cconj(d);
+    R norm = R(0);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        R row = R(0);
+#pragma unroll
+        for (int j = 0; j < 3; j++) row += fabs(H[i][j].r) + fabs(H[i][j].i);
+        norm = row > norm ? row : norm;
+    }
+    int s = 0;
+    R scale = R(1);
+    while (norm * scale > R(0.25) && s < 60) {
+        scale *= R(0.5);
+        s++;
+    }
+    cx<R> B[3][3], P[3][3], T[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) B[i][j] = cmk(H[i][j].i * scale, -H[i][j].r * scale);   // -i H 2^-s
+    // Horner: P = I + B/12, then P <- I + B P / k for k = 11 .. 2, and a = B P
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) P[i][j] = cadd(cscale(B[i][j], R(1.0 / 12)), cmk(i == j ? R(1) : R(0), R(0)));
+#pragma unroll 1
+    for (int k = 11; k >= 2; k--) {
+        const R inv = R(1) / R(k);
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+                T[i][j] = cfma(B[i][2], P[2][j], cfma(B[i][1], P[1][j], cmul(B[i][0], P[0][j])));
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) P[i][j] = cadd(cscale(T[i][j], inv), cmk(i == j ? R(1) : R(0), R(0)));
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) T[i][j] = cfma(B[i][2], P[2][j], cfma(B[i][1], P[1][j], cmul(B[i][0], P[0][j])));
+    // T = exp(B) - I; residual squarings
+#pragma unroll 1
+    for (int q = 0; q < s; q++) {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) P[i][j] = cadd(T[i][j], cmk(i == j ? R(2) : R(0), R(0)));
+        cx<R> S[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) S[i][j] = cfma(P[i][2], T[2][j], cfma(P[i][1], T[1][j], cmul(P[i][0], T[0][j])));
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) T[i][j] = S[i][j];
+    }
+    // split off the first order of the J and Q terms
+    Res3<R> f;
+    res3_zero(f);
+    f.g[0] = vx; f.g[1] = vy; f.g[2] = vz; f.g[3] = vq;
+    cx<R> F[3][3];
+    res3_full(f, F);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) e.m[i][j] = csub(T[i][j], F[i][j]);
+    e.g[0] = vx; e.g[1] = vy; e.g[2] = vz; e.g[3] = vq;
+}
+
+// The quadrupole-drive part of one exponential's exponent, weights as in
+// `exponent`: u_2p + i u_2p+1 = a dt qd_p(node 1) + b dt qd_p(node 2).
+template <typename R>
+SPINSIM_HD void exponent_qd(const SampleCtx<R>& c, const NodeField<R>& f1, const NodeField<R>& f2, bool swap, R u[4])
+{
+    const R wa = swap ? c.zb : c.za, wb = swap ? c.za : c.zb;
+#pragma unroll
+    for (int p = 0; p < 2; p++) {
+        u[2 * p] = fma(wa, f1.qd[p].r, wb * f2.qd[p].r);
+        u[2 * p + 1] = fma(wa, f1.qd[p].i, wb * f2.qd[p].i);
+    }
+}
+
 // -------------------------------------------------------------------------
 // One integration step u(t_{k-1} + (l+1) dt, t_{k-1} + l dt), as a split
 // residual, for the three methods.  METHOD: 0 CF4 (Sec. 1.2.2, nodes
@@ -1014,16 +1155,32 @@ SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res2<R>& x)
 // exponentials are applied one after the other, X <- E_2 (E_1 X) (the same
 // product as (E_2 E_1) X, Eq. cf4_implementation, in the same number of
 // operations), so only one step exponential is held in registers at a time.
-template <typename R, int METHOD, bool SMALL = false, bool TONES = false>
+template <typename R, int METHOD, bool SMALL = false, bool TONES = false, bool SU3 = false>
 SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X)
 {
     NodeField<R> f1, f2;
-    field_at<R, SMALL, TONES>(c, (lf + c.c1) * c.dt, f1);
+    field_at<R, SMALL, TONES, SU3>(c, (lf + c.c1) * c.dt, f1);
     if (METHOD == 1) f2 = f1;
-    else field_at<R, SMALL, TONES>(c, (lf + c.c2) * c.dt, f2);
+    else field_at<R, SMALL, TONES, SU3>(c, (lf + c.c2) * c.dt, f2);
     R vx, vy, vz, wx = R(0), wy = R(0), wz = R(0);
     exponent<R, TONES>(c, f1, f2, false, vx, vy, vz);
     if (METHOD == 0) exponent<R, TONES>(c, f1, f2, true, wx, wy, wz);
+    if constexpr (SU3) {
+        // full su(3): the general exponential of each step exponent (v_q = q1)
+        R u[4];
+        Res3<R> e, Y;
+        exponent_qd(c, f1, f2, false, u);
+        expm_general_res(vx, vy, vz, c.q1, u, e);
+        res3_mul(e, X, Y);
+        if (METHOD == 0) {
+            exponent_qd(c, f1, f2, true, u);
+            expm_general_res(wx, wy, wz, c.q1, u, e);
+            res3_mul(e, Y, X);
+        } else {
+            X = Y;
+        }
+        return;
+    }
     Res3<R> e, Y;
     expm_one_res_n<R, SMALL>(vx, vy, vz, c.qd3, tau, c.inv_n, c.q1, e);
     res3_mul(e, X, Y);
@@ -1035,9 +1192,10 @@ SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X)
     }
 }
 
-template <typename R, int METHOD, bool SMALL = false, bool TONES = false>
+template <typename R, int METHOD, bool SMALL = false, bool TONES = false, bool SU3 = false>
 SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res2<R>& X)
 {
+    static_assert(!SU3, "quadrupole drives need spin one");
     Res2<R> x, Y;
     step_res<R, METHOD, SMALL, TONES>(c, lf, tau, x);
     res2_mul(x, X, Y);

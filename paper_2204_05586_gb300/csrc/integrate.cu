@@ -42,7 +42,7 @@ __device__ __forceinline__ int find_index(const int64_t* off, int n, int64_t g)
 constexpr int kSlots = kSegLog2 + 1;
 
 // The body of both integrate kernels (below).
-template <int N, typename R, int METHOD, bool SMALL, bool TONES>
+template <int N, typename R, int METHOD, bool SMALL, bool TONES, bool SU3 = false>
 __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
 {
     using Res = typename ResType<N, R>::type;
@@ -88,7 +88,7 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
             if (k > 0 && lane < (1 << lg_use)) {
                 SampleCtx<R> c;
                 double beta = 0.0;
-                const double gsum = make_ctx<R, N, TONES>(s, k, c, beta);
+                const double gsum = make_ctx<R, N, TONES, SU3>(s, k, c, beta);
                 if (lane == 0) bg[slot] = make_double2(beta, gsum);
                 const int64_t L = s.L;
 #pragma unroll 1
@@ -98,7 +98,7 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
                     Res X;
                     res_zero(X);
 #pragma unroll 1
-                    for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES>(c, (R)l, c.tau, X);   // U <- u_l U
+                    for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES, SU3>(c, (R)l, c.tau, X);   // U <- u_l U
                     // canonical tree over the lane's segments: a finished pair of
                     // equal sub-trees merges (later on the left) until the sizes differ
                     int h = 0;
@@ -168,7 +168,19 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) integrate_tones_k
     integrate_body<N, R, METHOD, false, true>(a);
 }
 
+// Full su(3) spin-one Hamiltonians (quadrupole drives, tones included): FP64.
+template <int METHOD>
+__global__ void __launch_bounds__(256) integrate_su3_kernel(IntegrateArgs a)
+{
+    integrate_body<3, double, METHOD, false, true, true>(a);
+}
+
 // ----------------------------------------------------------------- launchers
+template <int METHOD>
+static void* su3_kernel_ptr()
+{
+    return (void*)integrate_su3_kernel<METHOD>;
+}
 template <int N, typename R, int METHOD, bool SMALL, bool TONES>
 static void* kernel_ptr()
 {
@@ -198,6 +210,17 @@ static void* pick_variant(int method, int variant)
             // general series (its terms are sized for double precision)
             if constexpr (sizeof(R) == 4) return pick_method<N, R, true, false>(method);
             else return nullptr;
+        case kVariantSU3:
+            if constexpr (N == 3 && sizeof(R) == 8) {
+                switch (method) {
+                    case 0: return su3_kernel_ptr<0>();
+                    case 1: return su3_kernel_ptr<1>();
+                    case 2: return su3_kernel_ptr<2>();
+                    default: return nullptr;
+                }
+            } else {
+                return nullptr;
+            }
         default: return nullptr;
     }
 }

@@ -119,6 +119,12 @@ struct DevSim {
     float f_za, f_zb, f_zbias, f_qd3, f_dt, f_c1, f_c2, f_pad;
     float f_amp[kMaxPulses], f_invw[kMaxPulses];
     float f_tom_plus[kMaxTones], f_tom_minus[kMaxTones];
+    // Quadrupole drives (full su(3), FP64 only): pair p on (D_xz, D_yz) (k = 1)
+    // or (D_x2y2, D_xy) (k = 2), Om+-_p and the rates seen in the frame,
+    // 2 pi (f_p -+ k B) (lab: 2 pi f_p).
+    int32_t qd_on, qd_pad;
+    double qd_hz[2], qd_phase[2];
+    double qd_om_plus[2], qd_om_minus[2], qd_co0[2], qd_ct0[2];
 };
 
 struct IntegrateArgs {
@@ -211,6 +217,8 @@ inline void field_bounds(const spinsim_field& f, double& wperp, double& wz)
     wperp = two_pi * (std::fabs(f.drive_x_hz) + std::fabs(f.drive_y_hz));
     for (int j = 0; j < f.n_tones && j < SPINSIM_MAX_TONES; j++)
         wperp += two_pi * (std::fabs(f.tone_x_hz[j]) + std::fabs(f.tone_y_hz[j]));
+    if (f.qd_on)   // the quadrupole drives' operators have norm 1, as J_x and J_y
+        for (int p = 0; p < 2; p++) wperp += two_pi * (std::fabs(f.qd_x_hz[p]) + std::fabs(f.qd_y_hz[p]));
     wz = two_pi * (std::fabs(f.bias_hz) + pulses);
 }
 
@@ -296,13 +304,18 @@ bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, in
 // Integrate kernel variants: the general one; the small-angle one (FP32-bulk,
 // Gaussian pulses, no further tones; small_angle_request); and the one that
 // also evaluates further drive tones (requests with tones only, so the others
-// keep the leaner step loop).  A batch runs one launch group per (spin,
+// keep the leaner step loop); and the full su(3) one (quadrupole drives,
+// spin-one, FP64, tones included).  A batch runs one launch group per (spin,
 // variant), each request in the variant it needs on its own.
-enum IntegrateVariant { kVariantGeneral = 0, kVariantSmall = 1, kVariantTones = 2 };
-constexpr int kVariants = 3;
+enum IntegrateVariant { kVariantGeneral = 0, kVariantSmall = 1, kVariantTones = 2, kVariantSU3 = 3 };
+constexpr int kVariants = 4;
 constexpr int kMaxGroups = 2 * kVariants;   // launch groups of one batch: spin-half and spin-one
-// request_variant: the variant a validated request needs.
+// request_variant: the variant a validated request needs (kVariantSU3: its
+// quadrupole drives; FP64 only, see precision_status).
 int request_variant(const spinsim_config& cfg, const spinsim_request& r, int64_t L);
+// precision_status: SPINSIM_E_UNSUPPORTED for a request the configured
+// precision cannot run (quadrupole drives in FP32-bulk), else SPINSIM_OK.
+int precision_status(const spinsim_config& cfg, const spinsim_request& r);
 
 // Request validation (params.cu), shared by every entry point: status,
 // SPINSIM_WARN_MAGNUS, K and L of one request.

@@ -76,6 +76,14 @@ Checked check_request(const spinsim_request* r)
             c.status = SPINSIM_E_ARG;
             return c;
         }
+    if (f.qd_on != 0 && (f.qd_on != 1 || r->spin_x2 != 2)) { c.status = SPINSIM_E_ARG; return c; }
+    if (f.qd_on)
+        for (int p = 0; p < 2; p++)
+            if (!std::isfinite(f.qd_x_hz[p]) || !std::isfinite(f.qd_y_hz[p]) || !std::isfinite(f.qd_hz[p]) ||
+                !std::isfinite(f.qd_phase[p])) {
+                c.status = SPINSIM_E_ARG;
+                return c;
+            }
     for (int p = 0; p < f.n_pulses; p++)
         if (!(f.pulse_width_s[p] > 0.0) || !std::isfinite(f.pulse_amp_hz[p]) || !std::isfinite(f.pulse_centre_s[p])) {
             c.status = SPINSIM_E_ARG;
@@ -120,7 +128,7 @@ Checked check_request(const spinsim_request* r)
 bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, int64_t L)
 {
     if (cfg.precision != SPINSIM_PREC_FP32_BULK || L < 1) return false;
-    if (r.field.n_tones > 0) return false;
+    if (r.field.n_tones > 0 || r.field.qd_on) return false;
     if (r.field.n_pulses > 0 && (r.field.pulse_sine_mask & ((1 << r.field.n_pulses) - 1)) != 0) return false;
     const MethodNodes m = method_nodes(cfg.method);
     const spinsim_field& f = r.field;
@@ -140,8 +148,14 @@ bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, in
 
 int request_variant(const spinsim_config& cfg, const spinsim_request& r, int64_t L)
 {
+    if (r.field.qd_on) return kVariantSU3;
     if (r.field.n_tones > 0) return kVariantTones;
     return small_angle_request(cfg, r, L) ? kVariantSmall : kVariantGeneral;
+}
+
+int precision_status(const spinsim_config& cfg, const spinsim_request& r)
+{
+    return r.field.qd_on && cfg.precision != SPINSIM_PREC_FP64 ? SPINSIM_E_UNSUPPORTED : SPINSIM_OK;
 }
 
 void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L, DevSim& d)
@@ -199,6 +213,18 @@ void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K,
         d.f_tom_plus[j] = (float)d.t_om_plus[j];
         d.f_tom_minus[j] = (float)d.t_om_minus[j];
         om_perp += std::fabs(d.t_om_plus[j]) + std::fabs(d.t_om_minus[j]);
+    }
+    // quadrupole drives: pair p turns at (p + 1) w_r in the frame
+    d.qd_on = f.qd_on ? 1 : 0;
+    for (int p = 0; p < 2 && d.qd_on; p++) {
+        const double qx = kTwoPiH * f.qd_x_hz[p], qy = kTwoPiH * f.qd_y_hz[p];
+        const double kb = d.frame ? (double)(p + 1) * f.bias_hz : 0.0;
+        d.qd_hz[p] = f.qd_hz[p];
+        d.qd_phase[p] = f.qd_phase[p];
+        d.qd_om_plus[p] = 0.5 * (qx + qy);
+        d.qd_om_minus[p] = 0.5 * (qx - qy);
+        d.qd_co0[p] = kTwoPiH * (f.qd_hz[p] - kb);
+        d.qd_ct0[p] = kTwoPiH * (f.qd_hz[p] + kb);
     }
     d.tau = choose_tau(cfg.trotter_squares, cfg.precision, cfg.rotating_frame, mn.n_exp, wa, wb, d.dt,
                        om_perp, kTwoPiH * std::fabs(f.bias_hz), pulse_w,

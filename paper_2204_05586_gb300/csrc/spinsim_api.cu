@@ -765,6 +765,7 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
     int first_err = SPINSIM_OK;
     for (int64_t i = 0; i < n; i++) {
         checked[i] = check_request(&reqs[i]);
+        if (checked[i].status == SPINSIM_OK) checked[i].status = precision_status(h->cfg, reqs[i]);
         if (checked[i].status == SPINSIM_OK) {
             if (!res[i].states) checked[i].status = SPINSIM_E_ARG;
             else if (res[i].capacity < checked[i].K) checked[i].status = SPINSIM_E_CAPACITY;
@@ -883,6 +884,7 @@ int spinsim_range_begin(spinsim_handle h, const spinsim_request* req, spinsim_re
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
     std::vector<Checked> checked(1);
     checked[0] = check_request(req);
+    if (checked[0].status == SPINSIM_OK) checked[0].status = precision_status(h->cfg, *req);
     Checked& c = checked[0];
     if (c.status == SPINSIM_OK) {
         if (!res->states) c.status = SPINSIM_E_ARG;
@@ -1049,6 +1051,7 @@ static int serving_pump(spinsim_s* h)
             res.push_back(*tk.res);
             ids.push_back(t);
             Checked c = check_request(&tk.req);
+            if (c.status == SPINSIM_OK) c.status = precision_status(h->cfg, tk.req);
             if (c.status == SPINSIM_OK) c.variant = request_variant(h->cfg, tk.req, c.L);
             checked.push_back(c);
             bytes += tk.bytes;
@@ -1083,6 +1086,7 @@ int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result*
     int st = serving_init(h);
     if (st != SPINSIM_OK) return st;
     Checked c = check_request(req);
+    if (c.status == SPINSIM_OK) c.status = precision_status(h->cfg, *req);
     if (c.status == SPINSIM_OK) {
         if (!res->states) c.status = SPINSIM_E_ARG;
         else if (res->capacity < c.K) c.status = SPINSIM_E_CAPACITY;

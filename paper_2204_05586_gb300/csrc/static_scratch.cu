@@ -70,6 +70,8 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     res->trotter_squares = 0;
     res->n_samples = 0;
     if (st != SPINSIM_OK) return st;
+    st = precision_status(*cfg, *req);
+    if (st != SPINSIM_OK) return res->status = st;
     res->flags = magnus_flags(*req, L) | precision_flags(cfg->precision, cfg->rotating_frame, *req);
     if (!res->states || res->capacity < K) {
         res->status = !res->states ? SPINSIM_E_ARG : SPINSIM_E_CAPACITY;

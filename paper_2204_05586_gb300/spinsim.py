@@ -48,7 +48,10 @@ class spinsim_field(ctypes.Structure):
                 ("pulse_width_s", ctypes.c_double * MAX_PULSES),
                 ("n_tones", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("tone_x_hz", ctypes.c_double * MAX_TONES), ("tone_y_hz", ctypes.c_double * MAX_TONES),
-                ("tone_hz", ctypes.c_double * MAX_TONES), ("tone_phase", ctypes.c_double * MAX_TONES)]
+                ("tone_hz", ctypes.c_double * MAX_TONES), ("tone_phase", ctypes.c_double * MAX_TONES),
+                ("qd_on", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("qd_x_hz", ctypes.c_double * 2), ("qd_y_hz", ctypes.c_double * 2),
+                ("qd_hz", ctypes.c_double * 2), ("qd_phase", ctypes.c_double * 2)]
 
 
 class spinsim_request(ctypes.Structure):
@@ -228,6 +231,12 @@ def make_request(req: dict) -> spinsim_request:
     r.field.n_tones = len(tones)
     for j, (x, y, hz, ph) in enumerate(tones):
         r.field.tone_x_hz[j], r.field.tone_y_hz[j], r.field.tone_hz[j], r.field.tone_phase[j] = x, y, hz, ph
+    qdrives = list(f.get("qdrives", ()))
+    if len(qdrives) > 2:
+        raise SpinsimError(E_ARG, "two quadrupole drives at most")
+    r.field.qd_on = 1 if qdrives else 0
+    for p, (x, y, hz, ph) in enumerate(qdrives):
+        r.field.qd_x_hz[p], r.field.qd_y_hz[p], r.field.qd_hz[p], r.field.qd_phase[p] = x, y, hz, ph
     r.t_start, r.t_end, r.dt, r.dt_out = req["t_start"], req["t_end"], req["dt"], req["dt_out"]
     psi = np.asarray(req["psi0"], dtype=np.complex128)
     for i, z in enumerate(psi):

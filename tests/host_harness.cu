@@ -65,6 +65,16 @@ int hh_small_angle_request(const spinsim_config* cfg, const spinsim_request* r, 
 }
 double hh_tiny_angle_bound() { return kTinyAngleBound; }
 
+// exp(-i H) for a full su(3) H = w . (J_x, J_y, J_z, Q, D_xz, D_yz, D_x2y2, D_xy)
+// (radians) through the split-residual general exponential, as a full matrix.
+void hh_expm_general(const double* w, double* out)
+{
+    Res3<double> e;
+    const double u[4] = {w[4], w[5], w[6], w[7]};
+    expm_general_res<double>(w[0], w[1], w[2], w[3], u, e);
+    full3(e, out);
+}
+
 // 1 when the branch-free series (sincos_series, sincos_m_series) give the same
 // bits as small_sincos / small_sincos_m at x (|x| <= 1/16), in float or double.
 int hh_series_match(double x, int fp32)

@@ -125,3 +125,28 @@ def test_call_errors():
     assert lib.spinsim_cpu_simulate(ctypes.byref(bad), reqs, res, 1, 0) == S.E_ARG
     assert lib.spinsim_cpu_simulate(ctypes.byref(cfg), reqs, res, 1, 0) == S.E_ARG   # states NULL
     assert res[0].status == S.E_ARG
+
+
+def su3_request(t_end=1e-3):
+    f = W.field(bias_hz=700e3, drive_x_hz=2e3, drive_hz=700e3, quad_hz=300.0, pulses=[(60.0, 0.5e-3, 0.2e-3)],
+                qdrives=[(1.2e3, 0.7e3, 700.3e3, 0.4), (0.9e3, 0.9e3, 1400.2e3, -0.8)],
+                tones=[(0.5e3, 0.2e3, 699.7e3, 1.0)])
+    return W.request(2, f, 0.0, t_end, 1e-8, 1e-6, psi0=W.random_state(3, np.random.default_rng(4)))
+
+
+@pytest.mark.parametrize("frame", [True, False])
+def test_full_su3_fp64_against_oracle(oracle_mod, frame):
+    """Both quadrupole drives (near the one- and two-quantum resonances), a
+    tone and a pulse: FP64, every sample."""
+    req = su3_request()
+    (out,) = C.simulate([req], precision=S.PREC_FP64, rotating_frame=frame)
+    check(out, oracle_run(oracle_mod, req, frame=frame), 1e-10, f"su3 frame={frame}")
+
+
+def test_full_su3_needs_fp64_and_spin_one():
+    (o32,) = C.simulate([su3_request(1e-4)])
+    assert o32["status"] == S.E_UNSUPPORTED
+    half = W.spin_half_rabi(t_end=1e-4)
+    half["field"]["qdrives"] = [(1.0, 1.0, 1.0, 0.0)]
+    (oh,) = C.simulate([half], precision=S.PREC_FP64)
+    assert oh["status"] == S.E_ARG

@@ -45,6 +45,7 @@ def hh(tmp_path_factory):
     L.hh_tiny_angle_bound.restype = ctypes.c_double
     L.hh_first_order.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, DP]
     L.hh_series_match.argtypes = [ctypes.c_double, ctypes.c_int]
+    L.hh_expm_general.argtypes = [DP, DP]
     L.hh_series_match.restype = ctypes.c_int
     return L
 
@@ -332,3 +333,20 @@ def test_branch_free_series_match_the_branching_ones(hh):
     for x in np.concatenate([rng.uniform(-0.0625, 0.0625, 2000), [0.0, 0.0625, -0.0625, 1e-30, -3e-8]]):
         assert hh.hh_series_match(float(x), 1) == 1, x
         assert hh.hh_series_match(float(x), 0) == 1, x
+
+
+@pytest.mark.parametrize("scale", [1e-5, 3e-2, 0.7, 9.0])
+def test_general_su3_exponential(hh, oracle_mod, scale):
+    """The kernels' split-residual exponential of a full su(3) spin-one
+    Hamiltonian (quadrupole drives) against the oracle's series and scipy."""
+    from test_oracle_su3 import hamiltonian8
+    rng = np.random.default_rng(int(scale * 1e5) + 11)
+    for _ in range(10):
+        w = rng.normal(size=8) * scale
+        out = np.zeros(18)
+        hh.hh_expm_general(P(w), P(out))
+        E = out.view(np.complex128).reshape(3, 3)
+        ref = sl.expm(-1j * hamiltonian8(w))
+        tol = 3e-15 * max(1.0, 8 * scale)
+        assert np.abs(E - ref).max() < tol
+        assert np.abs(E - oracle_mod.expm_general(w, 1.0)).max() < tol
