@@ -8,7 +8,7 @@ delta_t = 10 ns and Delta_t = 1 us (1e5 samples x 100 CF4 steps) -- run in
 FP32-bulk precision with the FP64 chain, inputs resident on the device.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sensing|sweep|serve|neural|multitone] [--precision fp32|fp64]
+                    [--workload sensing|sweep|serve|neural|multitone|su3] [--precision fp32|fp64]
 
 Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs its own
 copy of the workload (weak scaling, no data-path collective); the timing is
@@ -50,9 +50,10 @@ def chain_flops_per_sample(spin_x2: int, run: int) -> float:
     return (run - 1) / run * 32.0 + 16.0 + 30.0
 L2_FLUSH_BYTES = 256 << 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one integrate launch
-# (profiles/integrate_kernel_spin_one_sensing.md, integrate_tones_kernel_multitone.md);
+# (profiles/integrate_kernel_spin_one_sensing.md, integrate_tones_kernel_multitone.md,
+# integrate_su3_kernel_su3.md);
 # the operators it writes stay in L2.
-INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 67328, ("multitone", "fp32"): 108800}
+INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 67328, ("multitone", "fp32"): 108800, ("su3", "fp64"): 329728}
 
 
 def algorithmic_flops_per_step(spin_x2: int, tau: int, n_tones: int = 0) -> float:
@@ -67,6 +68,29 @@ def algorithmic_flops_per_step(spin_x2: int, tau: int, n_tones: int = 0) -> floa
     if spin_x2 != 2:
         raise ValueError("the flop model covers spin-one steps only")
     return 432.0 * tau + 650.0 + 88.0 * n_tones
+
+
+def su3_flops_per_step(degree: int, squarings: int = 0) -> float:
+    """Algorithmic FP64 flops of one CF4 step with quadrupole drives (full
+    su(3), spin-one; FMA = 2, add or multiply = 1).  Per exponential: the
+    Hermitian exponent and its norm (40), B^2 with its six distinct entries
+    (108), floor((degree - 1) / 2) products of the Hermitian B^2 with a general
+    matrix (162 each) and the blocks I/(2j)! + B/(2j+1)! added in (54), T + B
+    (18), the first-order split (36) and 252 per squaring.  Per step: two
+    exponentials, two residual products (262 each) and, at both nodes, the
+    field (drive and quadrupole-drive phasors with the counter-rotating
+    sin/cos, the Gaussian pulse: ~260) and the weighted exponents (46)."""
+    per_exp = 40.0 + 108.0 + 162.0 * ((degree - 1) // 2) + 54.0 + 18.0 + 36.0 + 252.0 * squarings
+    return 2 * per_exp + 2 * 262.0 + 2 * (260.0 + 46.0)
+
+
+# FP64 peak from the unit counts: 152 SMs x 2 FP64 FMA lanes per cycle
+# (the dfma peak_sustained ncu reports) x 2 flop x 2070 MHz.
+FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# Taylor degree of the su(3) exponential on the su3 workload: every CF4
+# exponent's max-row norm stays below 1.5e-4 there (under the 2.0e-4 switch to 5).
+SU3_DEGREE = 4
 
 
 class ClockSampler:
@@ -190,6 +214,12 @@ def run_ours(args, world, rank, local):
         workload = ("spin-one sensing field plus three further drive tones (1 kHz circular at +500 Hz, 0.5 kHz "
                     "linear at -2 kHz, 0.8 kHz y at +5 kHz); 100 ms, dt 10 ns, dt_out 1 us "
                     "(1e5 samples x 100 CF4 steps)")
+    elif args.workload == "su3":
+        reqs = [W.su3_sensing()]
+        prec, args.precision = S.PREC_FP64, "fp64"      # full su(3) runs in FP64 only
+        workload = ("spin-one sensing field plus two quadrupole drives (full su(3)): 1 kHz circular on "
+                    "(D_xz, D_yz) at 700.3 kHz, 0.5 kHz circular on (D_x2y2, D_xy) at 1400.2 kHz; 100 ms, "
+                    "dt 10 ns, dt_out 1 us (1e5 samples x 100 CF4 steps), FP64")
     elif args.workload == "sweep":
         reqs = W.sweep(4096, seed=W.SEED + rank)
         workload = ("batched spin-one sweep: 4096 simulations, bias U(600,800) kHz, Rabi U(0.5,2) kHz, detuning "
@@ -236,14 +266,18 @@ def run_ours(args, world, rank, local):
     ms_per_step = total_s * 1e3 / args.steps
 
     # ---- roofline of the dominant kernel (integrate), from its live CUDA events
-    flops = sum(W.total_steps([r]) * algorithmic_flops_per_step(r["spin_x2"], t, len(r["field"].get("tones", ())))
-                for r, t in zip(reqs, taus))
+    if args.workload == "su3":
+        flops = sum(W.total_steps([r]) * su3_flops_per_step(SU3_DEGREE) for r in reqs)
+    else:
+        flops = sum(W.total_steps([r]) * algorithmic_flops_per_step(r["spin_x2"], t, len(r["field"].get("tones", ())))
+                    for r, t in zip(reqs, taus))
     mean_int = float(np.mean(integ_ms))
     achieved = flops / (mean_int / 1e3) / 1e12
     # DRAM traffic of one integrate launch from the ncu capture of this workload
     # (dram__bytes_read.sum + dram__bytes_write.sum), see profiles/.
     traffic = INTEGRATE_TRAFFIC_BYTES.get((args.workload, args.precision))
-    kernel = "integrate_tones_kernel" if any(r["field"].get("tones") for r in reqs) else "integrate_kernel"
+    kernel = ("integrate_su3_kernel" if any(r["field"].get("qdrives") for r in reqs) else
+              "integrate_tones_kernel" if any(r["field"].get("tones") for r in reqs) else "integrate_kernel")
     roofline = {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3),
                 "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
@@ -263,7 +297,11 @@ def run_ours(args, world, rank, local):
                       "frac": round(chain_tf / FP64_MEASURED_TFLOPS, 4),
                       "peak_source": "measured FMA-chain probe on this GPU model",
                       "flops_per_sample": round(cflops / sum(samples(r) for r in reqs), 1)}
-    if prec == S.PREC_FP64:
+    if args.workload == "su3":
+        roofline.update({"bound": "fp64", "peak": round(FP64_DERIVED_TFLOPS, 3),
+                         "frac": round(achieved / FP64_DERIVED_TFLOPS, 4),
+                         "peak_source": "derived: 152 SMs x 2 FP64 FMA lanes x 2 flop x 2070 MHz"})
+    elif prec == S.PREC_FP64:
         roofline.update({"peak": 1.25, "frac": round(achieved / 1.25, 4),
                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (profiling recipe table)"})
 
@@ -304,22 +342,31 @@ def run_ours(args, world, rank, local):
                        "parallelism": f"weak x{world}, independent simulations per GPU"},
             "roofline": roofline, "chain_roofline": chain_roofline, "e2e": e2e, "gpu_launches": launches,
             "wall_s_timed_loop": wall}
+    if args.workload == "su3":      # the general exponential takes no Lie-Trotter squarings
+        line["config"].pop("steps_by_trotter_squares")
+        line["config"]["trotter_squares"] = None
+        line["config"]["taylor_degree"] = SU3_DEGREE
     if clk:
         line["clocks"] = clk
     # ---- rank 0: accuracy vs the FP64 oracle, oracle CPU baseline, FP64-plain kernel
-    if rank == 0 and args.workload in ("sensing", "neural", "multitone") and not args.no_cpu_baseline:
+    if rank == 0 and args.workload in ("sensing", "neural", "multitone", "su3") and not args.no_cpu_baseline:
         from oracle import oracle as O   # the CPU baseline leg: the oracle as it stands
         O.build()
-        r = reqs[0]
+        r = dict(reqs[0])
         cores = os.cpu_count() or 1
+        sample = ("the full workload once (1e5 sample operators over all host cores, then the sequential "
+                  "chain), tau = 24, FP64")
+        if args.workload == "su3":   # the oracle's 12-term su(3) series: a bounded prefix of the run
+            r["t_end"] = r["t_start"] + 1e4 * r["dt_out"]
+            sample = ("the first 1e4 of 1e5 output samples (10 ms, 1e6 CF4 steps) over all host cores, then "
+                      "the sequential chain, FP64; states compared over that prefix")
         t0 = time.perf_counter()
         ref = O.simulate(r["spin_x2"], r["field"], r["t_start"], r["t_end"], r["dt"], r["dt_out"], r["psi0"],
                          threads=cores)
         t_cpu = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": steps_per_pass / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "the full workload once (1e5 sample operators over all host cores, "
-                                          "then the sequential chain), tau = 24, FP64"}
-        gpu_states = torch.view_as_complex(outs[0]["states"][:outs[0]["K"]]).cpu().numpy()
+        line["cpu_baseline"] = {"value": W.total_steps([r]) / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+        gpu_states = torch.view_as_complex(outs[0]["states"][:len(ref["states"])]).cpu().numpy()
         line["state_err_vs_oracle"] = float(np.abs(gpu_states - ref["states"]).max())
         # the paper's own error measure (Eq. error, 1/K outside the root as printed) and the
         # states' norm drift, beside the primary max |dpsi|
@@ -352,7 +399,7 @@ def run_ours(args, world, rank, local):
         line["cpu_backend"] = {"value": steps_per_pass / t_cb, "unit": UNIT, "cores": cores,
                                "precision": args.precision, "kind": "libspinsim_cpu (same algorithm on host cores)",
                                "sample": "the full workload once, all host cores",
-                               "state_err_vs_oracle": float(np.abs(cb["states"] - ref["states"]).max())}
+                               "state_err_vs_oracle": float(np.abs(cb["states"][:len(ref["states"])] - ref["states"]).max())}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -463,7 +510,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("sensing", "sweep", "serve", "neural", "multitone"), default="sensing")
+    ap.add_argument("--workload", choices=("sensing", "sweep", "serve", "neural", "multitone", "su3"), default="sensing")
     ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
     ap.add_argument("--tau", type=int, default=-1)
     ap.add_argument("--serve-requests", type=int, default=20000)

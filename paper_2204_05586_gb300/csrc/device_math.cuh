@@ -991,14 +991,36 @@ SPINSIM_HD void expm_one_res(R vx, R vy, R vz, R qd3, int tau, Res3<R>& e)
     expm_one_res_n<R, SMALL>(vx, vy, vz, qd3, tau, ldexp(R(1), -tau), R(3) * ldexp(qd3, tau), e);
 }
 
+// 1/k! rounded once (k! is exact in double up to k = 18), the Taylor coefficients.
+SPINSIM_HD constexpr double inv_factorial(int k)
+{
+    double f = 1.0;
+    for (int i = 2; i <= k; i++) f *= i;
+    return 1.0 / f;
+}
+
+// C = A P for a Hermitian A with a real diagonal (entries above and below the
+// diagonal both stored) and a general P.
+template <typename R>
+SPINSIM_HD void herm_mul3(const cx<R> (&A)[3][3], const cx<R> (&P)[3][3], cx<R> (&C)[3][3])
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const int k1 = (i + 1) % 3, k2 = (i + 2) % 3;
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            C[i][j] = cfma(A[i][k2], P[k2][j], cfma(A[i][k1], P[k1][j], cscale(P[i][j], A[i][i].r)));
+    }
+}
+
 // exp(-i H) - I as a split residual for a full su(3) spin-one H (radians):
 //   H = v_x J_x + v_y J_y + v_z J_z + v_q Q + u_0 D_xz + u_1 D_yz + u_2 D_x2y2 + u_3 D_xy,
 // D_ab the symmetric products of the spin matrices.  In the basis m = +1, 0, -1,
 // with t = v_x - i v_y, c = u_0 - i u_1 and d = u_2 - i u_3:
 //   H_00 = v_z + v_q/3, H_11 = -2 v_q/3, H_22 = -v_z + v_q/3,
 //   H_01 = (t + c)/sqrt2, H_12 = (t - c)/sqrt2, H_02 = d, H_ji = conj(H_ij).
-// The series sum_{k>=1} B^k / k! of B = -i H / 2^s (Horner over 12 terms, s
-// halvings until the row sums are at most 1/4: truncation below 3e-18), then
+// The series sum_{k>=1} B^k / k! of B = -i H / 2^s (s halvings until the row
+// sums are at most 1/4; degree 3 to 12 by the scaled norm), then
 // s residual squarings a <- (a + 2I) a; the first-order part of the J and Q
 // terms is taken out as g, the rest (the quadrupole drives' first order and
 // all higher orders) stays in the full matrix.  FP64 (the su(3) variant).
@@ -1037,28 +1059,74 @@ SPINSIM_HD void expm_general_res(R vx, R vy, R vz, R vq, const R u[4], Res3<R>& 
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) B[i][j] = cmk(H[i][j].i * scale, -H[i][j].r * scale);   // -i H 2^-s
-    // Horner: P = I + B/12, then P <- I + B P / k for k = 11 .. 2, and a = B P
+    // Taylor degree m: the smallest whose remainder bound at the scaled norm,
+    // theta^(m+1) e^theta / (m+1)!, stays below 2^-56 theta (relative to the
+    // first-order term); theta <= 1/4 needs the full m = 12.
+    const R th = norm * scale;
+    const int m = th <= R(6.9e-6) ? 3 : th <= R(2.0e-4) ? 4 : th <= R(1.58e-3) ? 5 : th <= R(6.4e-3) ? 6
+                : th <= R(1.77e-2) ? 7 : th <= R(3.85e-2) ? 8 : th <= R(7.1e-2) ? 9 : th <= R(0.117) ? 10
+                : th <= R(0.177) ? 11 : 12;
+    // The degree-m Taylor polynomial without its constant term, evaluated in
+    // powers of B2 = B^2 (Paterson-Stockmeyer with two blocks):
+    //   T = B + B2 (Y_1 + B2 (Y_2 + ... + B2 Y_J)),  Y_j = I/(2j)! + B/(2j+1)!,
+    // J = floor(m/2), terms beyond degree m dropped.  B2 = -(H 2^-s)^2 is
+    // Hermitian with a real diagonal: six entries are computed.
+    cx<R> B2[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; i++)
+    for (int i = 0; i < 3; i++) {
+        R d = R(0);
 #pragma unroll
-        for (int j = 0; j < 3; j++) P[i][j] = cadd(cscale(B[i][j], R(1.0 / 12)), cmk(i == j ? R(1) : R(0), R(0)));
-#pragma unroll 1
-    for (int k = 11; k >= 2; k--) {
-        const R inv = R(1) / R(k);
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++)
-                T[i][j] = cfma(B[i][2], P[2][j], cfma(B[i][1], P[1][j], cmul(B[i][0], P[0][j])));
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) P[i][j] = cadd(cscale(T[i][j], inv), cmk(i == j ? R(1) : R(0), R(0)));
+        for (int k = 0; k < 3; k++) d = fma(-B[i][k].r, B[i][k].r, fma(-B[i][k].i, B[i][k].i, d));
+        B2[i][i] = cmk(d, R(0));
     }
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) T[i][j] = cfma(B[i][2], P[2][j], cfma(B[i][1], P[1][j], cmul(B[i][0], P[0][j])));
+        for (int j = i + 1; j < 3; j++) {
+            B2[i][j] = cfma(B[i][2], B[2][j], cfma(B[i][1], B[1][j], cmul(B[i][0], B[0][j])));
+            B2[j][i] = cconj(B2[i][j]);
+        }
+    const int J = m / 2;
+    // innermost block: Y_J, or for even m the scalar I/m! folded into the next block
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) P[i][j] = cmk(R(0), R(0));
+#pragma unroll
+    for (int jb = 6; jb >= 1; jb--) {
+        if (jb > J) continue;
+        const R ce = R(inv_factorial(2 * jb)), co = R(inv_factorial(2 * jb + 1));
+        if (jb == J) {
+            if (m & 1) {
+#pragma unroll
+                for (int i = 0; i < 3; i++)
+#pragma unroll
+                    for (int j = 0; j < 3; j++)
+                        P[i][j] = cadd(cscale(B[i][j], co), cmk(i == j ? ce : R(0), R(0)));
+            }
+            continue;
+        }
+        if (jb == J - 1 && !(m & 1)) {       // P = Y_jb + B2 / (2J)!
+            const R cJ = R(inv_factorial(2 * jb + 2));
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++)
+                    P[i][j] = cadd(cadd(cscale(B[i][j], co), cscale(B2[i][j], cJ)), cmk(i == j ? ce : R(0), R(0)));
+            continue;
+        }
+        herm_mul3(B2, P, T);                  // P = Y_jb + B2 P
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+                P[i][j] = cadd(cadd(T[i][j], cscale(B[i][j], co)), cmk(i == j ? ce : R(0), R(0)));
+    }
+    herm_mul3(B2, P, T);                      // T = B + B2 P (m >= 3, so P is set)
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) T[i][j] = cadd(T[i][j], B[i][j]);
     // T = exp(B) - I; residual squarings
 #pragma unroll 1
     for (int q = 0; q < s; q++) {

@@ -84,6 +84,19 @@ def multitone_sensing(t_end=0.1, dt=1e-8, dt_out=1e-6):
     return r
 
 
+QDRIVES = [(1e3, 1e3, 700.3e3, 0.4), (0.5e3, 0.5e3, 1400.2e3, -0.8)]
+
+
+def su3_sensing(t_end=0.1, dt=1e-8, dt_out=1e-6):
+    """The spin-one sensing field with both quadrupole drives (Sec. 1.2.1: an
+    arbitrary point in su(3)): a circular 1 kHz drive on (D_xz, D_yz) 300 Hz
+    above the one-quantum resonance and a circular 0.5 kHz drive on
+    (D_x2y2, D_xy) 200 Hz above the two-quantum resonance.  FP64 only."""
+    r = spin_one_sensing(t_end, dt, dt_out)
+    r["field"]["qdrives"] = list(QDRIVES)
+    return r
+
+
 def neural_pulse(t_end=0.1, t_p=0.05, dt=1e-7, dt_out=1e-6, spin_x2=2):
     """The paper's benchmark field, Eq. neural_pulse:
     H = w J_z + 2 W cos(w t) J_x + W_p sinp(W (t - t_p)) J_z with w = 2 pi 700 kHz,

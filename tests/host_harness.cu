@@ -75,6 +75,21 @@ void hh_expm_general(const double* w, double* out)
     full3(e, out);
 }
 
+// The part of exp(-i H) - I beyond -i (w_x J_x + w_y J_y + w_z J_z + w_q Q)
+// (the quadrupole-drive first order and every higher order), as the
+// split-residual general exponential carries it.
+void hh_expm_general_rest(const double* w, double* out)
+{
+    Res3<double> e;
+    const double u[4] = {w[4], w[5], w[6], w[7]};
+    expm_general_res<double>(w[0], w[1], w[2], w[3], u, e);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            out[2 * (3 * i + j)] = e.m[i][j].r;
+            out[2 * (3 * i + j) + 1] = e.m[i][j].i;
+        }
+}
+
 // 1 when the branch-free series (sincos_series, sincos_m_series) give the same
 // bits as small_sincos / small_sincos_m at x (|x| <= 1/16), in float or double.
 int hh_series_match(double x, int fp32)

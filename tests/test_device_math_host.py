@@ -46,6 +46,7 @@ def hh(tmp_path_factory):
     L.hh_first_order.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, DP]
     L.hh_series_match.argtypes = [ctypes.c_double, ctypes.c_int]
     L.hh_expm_general.argtypes = [DP, DP]
+    L.hh_expm_general_rest.argtypes = [DP, DP]
     L.hh_series_match.restype = ctypes.c_int
     return L
 
@@ -350,3 +351,28 @@ def test_general_su3_exponential(hh, oracle_mod, scale):
         tol = 3e-15 * max(1.0, 8 * scale)
         assert np.abs(E - ref).max() < tol
         assert np.abs(E - oracle_mod.expm_general(w, 1.0)).max() < tol
+
+
+def test_general_exponential_degree_choice(hh):
+    """The Taylor degree is chosen from the scaled norm: just below each
+    switch point (and at norms that need scaling) the carried rest of
+    exp(-i H) - I still has the accuracy of the first-order term, against a
+    50-digit mpmath exponential.  One degree less would miss by 1e-13 and
+    more relative to the norm."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    from test_oracle_su3 import hamiltonian8
+    rng = np.random.default_rng(21)
+    for theta in (1e-9, 6.8e-6, 1.99e-4, 1.57e-3, 6.3e-3, 1.76e-2, 3.8e-2, 7.0e-2, 0.116, 0.176, 0.25, 0.9, 3.0):
+        for _ in range(3):
+            w = rng.normal(size=8)
+            H = hamiltonian8(w)
+            w *= theta / np.max(np.sum(np.abs(H.real) + np.abs(H.imag), axis=1))
+            out = np.zeros(18)
+            hh.hh_expm_general_rest(P(w), P(out))
+            rest = out.view(np.complex128).reshape(3, 3)
+            Hm = mp.matrix(hamiltonian8(w).tolist())
+            HJ = mp.matrix(H1(w[:4]).tolist())
+            refm = mp.expm(-1j * Hm) - mp.eye(3) + 1j * HJ
+            ref = np.array([[complex(refm[i, j]) for j in range(3)] for i in range(3)])
+            assert np.abs(rest - ref).max() < 1e-15 * max(theta, theta ** 2), theta
