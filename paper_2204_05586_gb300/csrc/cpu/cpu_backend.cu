@@ -46,7 +46,13 @@ void sample_operator(const DevSim& s, int64_t k, double* out)
         const int64_t lo = ((int64_t)q * s.L) >> s.seg_log2, hi = ((int64_t)(q + 1) * s.L) >> s.seg_log2;
         Res X;
         res_zero(X);
-        for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES, SU3>(c, (R)l, c.tau, X);
+        if constexpr (SU3) {
+            CounterPhasors<R> ph;
+            counter_phasors_at<R, METHOD>(c, lo, ph);
+            for (int64_t l = lo; l < hi; l++) step_apply_su3<R, METHOD, TONES>(c, (R)l, ph, X);
+        } else {
+            for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES>(c, (R)l, c.tau, X);
+        }
         int h = 0;
         while ((q >> h) & 1) {
             Res t;

@@ -622,12 +622,70 @@ SPINSIM_HD void second_order_sincos(R x, R& s, R& c)
     }
 }
 
-template <typename R, bool SMALL = false, bool TONES = false, bool SU3 = false>
-SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
+// The counter-rotating phasors of the su(3) variant at both nodes of a step,
+// e^{i beta} e^{i w_ct tau} (drive) and e^{i beta_p} e^{i w_ct,p tau}
+// (quadrupole pairs), tau = (l + c_j) dt.  They are set from sin/cos at the
+// first step of a canonical segment and then turned by e^{i w dt} per step, so
+// the result depends on the step index alone (not on the launch shape); the
+// rounding of the turns grows as (steps into the segment) x 2^-53 relative,
+// on terms of size Omega dt.
+template <typename R>
+struct CounterPhasors {
+    cx<R> d[2], q[2][2];   // [node], [pair][node]
+    cx<R> rd, rq[2];       // turns per step
+};
+
+template <typename R, int METHOD>
+SPINSIM_HD void counter_phasors_at(const SampleCtx<R>& c, int64_t lo, CounterPhasors<R>& p)
+{
+    R s, co;
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        if (METHOD == 1 && j == 1) break;   // one node
+        const R tau = ((R)lo + (j ? c.c2 : c.c1)) * c.dt;
+        if (c.counter_on) {
+            second_order_sincos(c.counter * tau, s, co);
+            p.d[j] = cmk(c.ebr * co - c.ebi * s, fma(c.ebr, s, c.ebi * co));
+        } else {
+            p.d[j] = cmk(R(0), R(0));
+        }
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            second_order_sincos(c.qct[q] * tau, s, co);
+            p.q[q][j] = cmk(c.qbr[q] * co - c.qbi[q] * s, fma(c.qbr[q], s, c.qbi[q] * co));
+        }
+    }
+    second_order_sincos(c.counter * c.dt, s, co);
+    p.rd = cmk(co, s);
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        second_order_sincos(c.qct[q] * c.dt, s, co);
+        p.rq[q] = cmk(co, s);
+    }
+}
+
+template <typename R, int METHOD>
+SPINSIM_HD void counter_phasors_advance(CounterPhasors<R>& p)
+{
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        if (METHOD == 1 && j == 1) break;
+        p.d[j] = cmul(p.d[j], p.rd);
+#pragma unroll
+        for (int q = 0; q < 2; q++) p.q[q][j] = cmul(p.q[q][j], p.rq[q]);
+    }
+}
+
+template <typename R, bool SMALL = false, bool TONES = false, bool SU3 = false, bool PH = false>
+SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f, const CounterPhasors<R>* ph = nullptr,
+                         int node = 0)
 {
     R s1, c1;
     step_sincos<R, SMALL>(c.co * tau, s1, c1);
     f.co = cmk(c.ebr * c1 - c.ebi * s1, fma(c.ebr, s1, c.ebi * c1));
+    if constexpr (PH) {
+        f.ct = ph->d[node];   // zero when the counter-rotating term is off
+    } else {
     if (c.counter_on) {
         // the counter-rotating term's first-order part is replaced exactly at
         // the end of the sample, so it only needs second-order accuracy
@@ -636,6 +694,7 @@ SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
         f.ct = cmk(c.ebr * c2 - c.ebi * s2, fma(c.ebr, s2, c.ebi * c2));
     } else {
         f.ct = cmk(R(0), R(0));
+    }
     }
     R z = R(0);
 #pragma unroll
@@ -683,9 +742,14 @@ SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f)
             R sj, cj;
             small_sincos(c.qco[p] * tau, sj, cj);
             cx<R> e = cscale(cmk(c.qbr[p] * cj - c.qbi[p] * sj, fma(c.qbr[p], sj, c.qbi[p] * cj)), c.qomp[p]);
-            second_order_sincos(c.qct[p] * tau, sj, cj);
-            e.r = fma(c.qomm[p], c.qbr[p] * cj - c.qbi[p] * sj, e.r);
-            e.i = fma(-c.qomm[p], fma(c.qbr[p], sj, c.qbi[p] * cj), e.i);
+            if constexpr (PH) {
+                e.r = fma(c.qomm[p], ph->q[p][node].r, e.r);
+                e.i = fma(-c.qomm[p], ph->q[p][node].i, e.i);
+            } else {
+                second_order_sincos(c.qct[p] * tau, sj, cj);
+                e.r = fma(c.qomm[p], c.qbr[p] * cj - c.qbi[p] * sj, e.r);
+                e.i = fma(-c.qomm[p], fma(c.qbr[p], sj, c.qbi[p] * cj), e.i);
+            }
             f.qd[p] = e;
         }
     }
@@ -1223,32 +1287,44 @@ SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res2<R>& x)
 // exponentials are applied one after the other, X <- E_2 (E_1 X) (the same
 // product as (E_2 E_1) X, Eq. cf4_implementation, in the same number of
 // operations), so only one step exponential is held in registers at a time.
-template <typename R, int METHOD, bool SMALL = false, bool TONES = false, bool SU3 = false>
-SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X)
+// One CF4 (or midpoint / Heun) step of the su(3) variant: the counter-rotating
+// phasors come from the segment's running turns and advance by one step.
+template <typename R, int METHOD, bool TONES>
+SPINSIM_HD void step_apply_su3(const SampleCtx<R>& c, R lf, CounterPhasors<R>& ph, Res3<R>& X)
 {
     NodeField<R> f1, f2;
-    field_at<R, SMALL, TONES, SU3>(c, (lf + c.c1) * c.dt, f1);
+    field_at<R, false, TONES, true, true>(c, (lf + c.c1) * c.dt, f1, &ph, 0);
     if (METHOD == 1) f2 = f1;
-    else field_at<R, SMALL, TONES, SU3>(c, (lf + c.c2) * c.dt, f2);
+    else field_at<R, false, TONES, true, true>(c, (lf + c.c2) * c.dt, f2, &ph, 1);
+    counter_phasors_advance<R, METHOD>(ph);
     R vx, vy, vz, wx = R(0), wy = R(0), wz = R(0);
     exponent<R, TONES>(c, f1, f2, false, vx, vy, vz);
     if (METHOD == 0) exponent<R, TONES>(c, f1, f2, true, wx, wy, wz);
-    if constexpr (SU3) {
-        // full su(3): the general exponential of each step exponent (v_q = q1)
-        R u[4];
-        Res3<R> e, Y;
-        exponent_qd(c, f1, f2, false, u);
-        expm_general_res(vx, vy, vz, c.q1, u, e);
-        res3_mul(e, X, Y);
-        if (METHOD == 0) {
-            exponent_qd(c, f1, f2, true, u);
-            expm_general_res(wx, wy, wz, c.q1, u, e);
-            res3_mul(e, Y, X);
-        } else {
-            X = Y;
-        }
-        return;
+    // the general exponential of each step exponent (v_q = q1)
+    R u[4];
+    Res3<R> e, Y;
+    exponent_qd(c, f1, f2, false, u);
+    expm_general_res(vx, vy, vz, c.q1, u, e);
+    res3_mul(e, X, Y);
+    if (METHOD == 0) {
+        exponent_qd(c, f1, f2, true, u);
+        expm_general_res(wx, wy, wz, c.q1, u, e);
+        res3_mul(e, Y, X);
+    } else {
+        X = Y;
     }
+}
+
+template <typename R, int METHOD, bool SMALL = false, bool TONES = false>
+SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X)
+{
+    NodeField<R> f1, f2;
+    field_at<R, SMALL, TONES>(c, (lf + c.c1) * c.dt, f1);
+    if (METHOD == 1) f2 = f1;
+    else field_at<R, SMALL, TONES>(c, (lf + c.c2) * c.dt, f2);
+    R vx, vy, vz, wx = R(0), wy = R(0), wz = R(0);
+    exponent<R, TONES>(c, f1, f2, false, vx, vy, vz);
+    if (METHOD == 0) exponent<R, TONES>(c, f1, f2, true, wx, wy, wz);
     Res3<R> e, Y;
     expm_one_res_n<R, SMALL>(vx, vy, vz, c.qd3, tau, c.inv_n, c.q1, e);
     res3_mul(e, X, Y);

@@ -97,8 +97,15 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
                     const int64_t lo = (sg * L) >> s.seg_log2, hi = ((sg + 1) * L) >> s.seg_log2;
                     Res X;
                     res_zero(X);
+                    if constexpr (SU3) {
+                        CounterPhasors<R> ph;
+                        counter_phasors_at<R, METHOD>(c, lo, ph);
 #pragma unroll 1
-                    for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES, SU3>(c, (R)l, c.tau, X);   // U <- u_l U
+                        for (int64_t l = lo; l < hi; l++) step_apply_su3<R, METHOD, TONES>(c, (R)l, ph, X);
+                    } else {
+#pragma unroll 1
+                        for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES>(c, (R)l, c.tau, X);   // U <- u_l U
+                    }
                     // canonical tree over the lane's segments: a finished pair of
                     // equal sub-trees merges (later on the left) until the sizes differ
                     int h = 0;
