@@ -94,3 +94,46 @@ def test_su3_through_the_static_entry_point():
     assert st == S.OK and res.status == S.OK
     (ref,) = run([req], precision=S.PREC_FP64)
     assert np.array_equal(torch.view_as_complex(states).cpu().numpy(), ref["states"].cpu().numpy())
+
+
+def test_su3_served_mix_equals_alone():
+    """su(3) requests and plain ones through the serving queue (FP64): each
+    result is bit-identical to the request run alone."""
+    reqs = [su3_request(4e-4, seed=s) if s % 2 else W.spin_one_sensing(t_end=4e-4) for s in range(6)]
+    alone = [run([q], precision=S.PREC_FP64)[0]["states"].cpu().numpy() for q in reqs]
+    with S.Simulator(precision=S.PREC_FP64) as sim:
+        outs = sim.allocate(reqs)
+        res = sim.results_struct(outs)
+        tickets = []
+        for q, r in zip([S.make_request(q) for q in reqs], res):
+            st, t = S.spinsim_submit(sim.handle, q, r)
+            assert st == S.OK
+            tickets.append(t)
+        for t in tickets:
+            assert S.spinsim_poll(sim.handle, t, 10_000_000) == S.OK
+    for o, r, a in zip(outs, res, alone):
+        assert r.status == S.OK
+        assert np.array_equal(torch.view_as_complex(o["states"][:o["K"]]).cpu().numpy(), a)
+
+
+def test_su3_split_into_ranges(oracle_mod):
+    """One su(3) simulation (2e3 samples x 100 steps) in three ranges through
+    spinsim_range_begin / spinsim_range_finish: equal to the unsplit run and
+    to the oracle."""
+    from paper_2204_05586_gb300 import sharded as SH
+    req = su3_request(2e-3, seed=9)
+    (full,) = run([req], precision=S.PREC_FP64)
+    full = full["states"].cpu().numpy()
+    K = S.spinsim_counts(S.make_request(req))[1]
+    rs = SH.ranges(K, 3)
+    backends = [SH.CudaRange(precision=S.PREC_FP64) for _ in rs]
+    try:
+        aggs = [b.begin(SH.range_request(req, k0, k1, r == len(rs) - 1)) for r, (b, (k0, k1)) in
+                enumerate(zip(backends, rs))]
+        psis = SH.entering_states(aggs, req["psi0"])
+        got = np.concatenate([b.finish(p)[: k1 - k0] for b, p, (k0, k1) in zip(backends, psis, rs)])
+    finally:
+        for b in backends:
+            b.close()
+    assert np.abs(got - full).max() < 1e-10
+    assert np.abs(got - oracle_run(oracle_mod, req)["states"]).max() < 1e-10
