@@ -384,7 +384,7 @@ def run_ours(args, world, rank, local):
         cores = os.cpu_count() or 1
         sample = ("the full workload once (1e5 sample operators over all host cores, then the sequential "
                   "chain), tau = 24, FP64")
-        if args.workload == "su3":   # the oracle's 12-term su(3) series: a bounded prefix of the run
+        if args.workload == "su3":   # the oracle's 30-term su(3) series: a bounded prefix of the run
             r["t_end"] = r["t_start"] + 1e4 * r["dt_out"]
             sample = ("the first 1e4 of 1e5 output samples (10 ms, 1e6 CF4 steps) over all host cores, then "
                       "the sequential chain, FP64; states compared over that prefix")
