@@ -53,7 +53,7 @@ L2_FLUSH_BYTES = 256 << 20
 # (profiles/integrate_kernel_spin_one_sensing.md, integrate_tones_kernel_multitone.md,
 # integrate_su3_kernel_su3.md);
 # the operators it writes stay in L2.
-INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 67328, ("multitone", "fp32"): 108800, ("su3", "fp64"): 957184}
+INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 67328, ("multitone", "fp32"): 108800, ("su3", "fp64"): 969472}
 
 
 def algorithmic_flops_per_step(spin_x2: int, tau: int, n_tones: int = 0) -> float:
@@ -75,13 +75,15 @@ def su3_flops_per_step(degree: int, squarings: int = 0) -> float:
     su(3), spin-one; FMA = 2, add or multiply = 1).  Per exponential: the
     Hermitian exponent and its norm (40), B^2 with its six distinct entries
     (108), floor((degree - 1) / 2) products of the Hermitian B^2 with a general
-    matrix (162 each) and the blocks I/(2j)! + B/(2j+1)! added in (54), T + B
-    (18), the first-order split (36) and 252 per squaring.  Per step: two
+    matrix (162 each) and the blocks I/(2j)! + B/(2j+1)! added in (54), and
+    the rest beyond the J and Q first order: with no halving formed directly
+    (12), else T + B (18), 252 per squaring and the first-order split (36).  Per step: two
     exponentials, two residual products (262 each) and, at both nodes, the
     field (the co-rotating drive and quadrupole-drive phasors by their sine
     and cosine series, the counter-rotating ones turned by one step, the
     Gaussian pulse: ~190) and the weighted exponents (46)."""
-    per_exp = 40.0 + 108.0 + 162.0 * ((degree - 1) // 2) + 54.0 + 18.0 + 36.0 + 252.0 * squarings
+    per_exp = 40.0 + 108.0 + 162.0 * ((degree - 1) // 2) + 54.0 + (12.0 if squarings == 0 else
+                                                                    18.0 + 252.0 * squarings + 36.0)
     return 2 * per_exp + 2 * 262.0 + 2 * (190.0 + 46.0)
 
 

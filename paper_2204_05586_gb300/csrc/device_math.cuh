@@ -7,6 +7,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cstring>
 
 #include "internal.h"
 
@@ -1063,6 +1064,35 @@ SPINSIM_HD constexpr double inv_factorial(int k)
     return 1.0 / f;
 }
 
+// The IEEE bit pattern of a double as a signed integer.
+SPINSIM_HD int64_t double_bits(double x)
+{
+#ifdef __CUDA_ARCH__
+    return __double_as_longlong(x);
+#else
+    int64_t b;
+    std::memcpy(&b, &x, sizeof b);
+    return b;
+#endif
+}
+
+// The Taylor degree of the general exponential at scaled norm th >= 0 (see
+// expm_general_res); for doubles the bit patterns are compared as integers.
+template <typename R>
+SPINSIM_HD int taylor_degree(R th)
+{
+    if constexpr (kFP32<R>) {
+        return th <= R(6.9e-6) ? 3 : th <= R(2.0e-4) ? 4 : th <= R(1.58e-3) ? 5 : th <= R(6.4e-3) ? 6
+             : th <= R(1.77e-2) ? 7 : th <= R(3.85e-2) ? 8 : th <= R(7.1e-2) ? 9 : th <= R(0.117) ? 10
+             : th <= R(0.177) ? 11 : 12;
+    } else {
+        const int64_t b = double_bits(th);
+        return b <= double_bits(6.9e-6) ? 3 : b <= double_bits(2.0e-4) ? 4 : b <= double_bits(1.58e-3) ? 5
+             : b <= double_bits(6.4e-3) ? 6 : b <= double_bits(1.77e-2) ? 7 : b <= double_bits(3.85e-2) ? 8
+             : b <= double_bits(7.1e-2) ? 9 : b <= double_bits(0.117) ? 10 : b <= double_bits(0.177) ? 11 : 12;
+    }
+}
+
 // C = A P for a Hermitian A with a real diagonal (entries above and below the
 // diagonal both stored) and a general P.
 template <typename R>
@@ -1122,14 +1152,19 @@ SPINSIM_HD void expm_general_res(R vx, R vy, R vz, R vq, const R u[4], Res3<R>& 
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) B[i][j] = cmk(H[i][j].i * scale, -H[i][j].r * scale);   // -i H 2^-s
+        for (int j = 0; j < 3; j++) B[i][j] = cmk(H[i][j].i, -H[i][j].r);   // -i H
+    if (s > 0) {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) B[i][j] = cscale(B[i][j], scale);   // -i H 2^-s
+    }
     // Taylor degree m: the smallest whose remainder bound at the scaled norm,
     // theta^(m+1) e^theta / (m+1)!, stays below 2^-56 theta (relative to the
-    // first-order term); theta <= 1/4 needs the full m = 12.
-    const R th = norm * scale;
-    const int m = th <= R(6.9e-6) ? 3 : th <= R(2.0e-4) ? 4 : th <= R(1.58e-3) ? 5 : th <= R(6.4e-3) ? 6
-                : th <= R(1.77e-2) ? 7 : th <= R(3.85e-2) ? 8 : th <= R(7.1e-2) ? 9 : th <= R(0.117) ? 10
-                : th <= R(0.177) ? 11 : 12;
+    // first-order term); theta <= 1/4 needs the full m = 12.  The norm is
+    // non-negative, so its bit pattern orders like its value: the comparisons
+    // run as integer compares.
+    const int m = taylor_degree(norm * scale);
     // The degree-m Taylor polynomial without its constant term, evaluated in
     // powers of B2 = B^2 (Paterson-Stockmeyer with two blocks):
     //   T = B + B2 (Y_1 + B2 (Y_2 + ... + B2 Y_J)),  Y_j = I/(2j)! + B/(2j+1)!,
@@ -1186,11 +1221,31 @@ SPINSIM_HD void expm_general_res(R vx, R vy, R vz, R vq, const R u[4], Res3<R>& 
             for (int j = 0; j < 3; j++)
                 P[i][j] = cadd(cadd(T[i][j], cscale(B[i][j], co)), cmk(i == j ? ce : R(0), R(0)));
     }
-    herm_mul3(B2, P, T);                      // T = B + B2 P (m >= 3, so P is set)
+    herm_mul3(B2, P, T);                      // B2 P (m >= 3, so P is set)
+    if (s == 0) {
+        // exp(B) - I = B + B2 P with B = -i H: the rest beyond the J and Q
+        // first order is B2 P plus -i times the quadrupole part of H (off the
+        // diagonal only), formed directly
+        const cx<R> cr = cscale(c, r);
+        const cx<R> m01 = cmk(cr.i, -cr.r), m10 = cmk(-cr.i, -cr.r);   // -i c/sqrt2, -i conj(c)/sqrt2
+        const cx<R> m02 = cmk(d.i, -d.r), m20 = cmk(-d.i, -d.r);       // -i d, -i conj(d)
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) e.m[i][j] = T[i][j];
+        e.m[0][1] = cadd(e.m[0][1], m01);
+        e.m[1][2] = csub(e.m[1][2], m01);
+        e.m[1][0] = cadd(e.m[1][0], m10);
+        e.m[2][1] = csub(e.m[2][1], m10);
+        e.m[0][2] = cadd(e.m[0][2], m02);
+        e.m[2][0] = cadd(e.m[2][0], m20);
+        e.g[0] = vx; e.g[1] = vy; e.g[2] = vz; e.g[3] = vq;
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) T[i][j] = cadd(T[i][j], B[i][j]);
+        for (int j = 0; j < 3; j++) T[i][j] = cadd(T[i][j], B[i][j]);   // T = exp(B) - I
     // T = exp(B) - I; residual squarings
 #pragma unroll 1
     for (int q = 0; q < s; q++) {
