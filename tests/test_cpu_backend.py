@@ -150,3 +150,20 @@ def test_full_su3_needs_fp64_and_spin_one():
     half["field"]["qdrives"] = [(1.0, 1.0, 1.0, 0.0)]
     (oh,) = C.simulate([half], precision=S.PREC_FP64)
     assert oh["status"] == S.E_ARG
+
+
+@pytest.mark.parametrize("method", [S.METHOD_MIDPOINT, S.METHOD_HEUN])
+def test_full_su3_other_methods(oracle_mod, method):
+    req = su3_request(5e-4)
+    (out,) = C.simulate([req], precision=S.PREC_FP64, method=method)
+    check(out, oracle_run(oracle_mod, req, method=method), 1e-10, f"su3 method={method}")
+
+
+def test_full_su3_scaled_and_squared_steps(oracle_mod):
+    """Lab frame with a 0.5 us step: every exponent's norm is above 1, so the
+    general exponential halves it three times and squares back three times."""
+    f = W.field(bias_hz=700e3, drive_x_hz=40e3, drive_hz=700e3, quad_hz=3e3,
+                qdrives=[(30e3, 20e3, 700e3, 0.4), (25e3, 25e3, 1400e3, -0.8)])
+    req = W.request(2, f, 0.0, 2e-4, 5e-7, 2e-6, psi0=W.random_state(3, np.random.default_rng(8)))
+    (out,) = C.simulate([req], precision=S.PREC_FP64, rotating_frame=False)
+    check(out, oracle_run(oracle_mod, req, frame=False), 1e-10, "su3 squared")

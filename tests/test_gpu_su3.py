@@ -137,3 +137,14 @@ def test_su3_split_into_ranges(oracle_mod):
             b.close()
     assert np.abs(got - full).max() < 1e-10
     assert np.abs(got - oracle_run(oracle_mod, req)["states"]).max() < 1e-10
+
+
+def test_su3_scaled_and_squared_steps(oracle_mod):
+    """Lab frame with a 0.5 us step: every exponent's norm is above 1, so the
+    general exponential halves it three times and squares back three times."""
+    f = W.field(bias_hz=700e3, drive_x_hz=40e3, drive_hz=700e3, quad_hz=3e3,
+                qdrives=[(30e3, 20e3, 700e3, 0.4), (25e3, 25e3, 1400e3, -0.8)])
+    req = W.request(2, f, 0.0, 2e-4, 5e-7, 2e-6, psi0=W.random_state(3, np.random.default_rng(8)))
+    (out,) = run([req], precision=S.PREC_FP64, rotating_frame=False)
+    ref = oracle_run(oracle_mod, req, frame=False)
+    assert np.abs(out["states"].cpu().numpy() - ref["states"]).max() < 1e-10
