@@ -35,9 +35,11 @@ UNIT = "steps/s"
 # unit counts and the maximum SM clock (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz).
 N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-# FP64 DFMA rate of this GPU measured with an FMA-chain probe (0.05 warp-DFMA per
-# clock per SM at 2.07 GHz): the chain kernels' bound
-FP64_MEASURED_TFLOPS = 0.98
+# FP64 peak from the unit counts: 152 SMs x 2 FP64 FMA lanes per cycle (the dfma
+# peak_sustained ncu reports) x 2 flop x 2070 MHz; an FMA-chain probe of dependent
+# chains reached 0.98 TFLOP/s of it, the su(3) integrate kernel keeps the pipe 91 % busy
+FP64_DERIVED_TFLOPS = N_SM * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP64_PEAK_SOURCE = "derived: 152 SMs x 2 FP64 FMA lanes x 2 flop x 2070 MHz"
 
 
 def chain_flops_per_sample(spin_x2: int, run: int) -> float:
@@ -86,10 +88,6 @@ def su3_flops_per_step(degree: int, squarings: int = 0) -> float:
                                                                     18.0 + 252.0 * squarings + 36.0)
     return 2 * per_exp + 2 * 262.0 + 2 * (190.0 + 46.0)
 
-
-# FP64 peak from the unit counts: 152 SMs x 2 FP64 FMA lanes per cycle
-# (the dfma peak_sustained ncu reports) x 2 flop x 2070 MHz.
-FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 # Taylor degree of the su(3) exponential on the su3 workload: every CF4
 # exponent's max-row norm stays below 1.5e-4 there (under the 2.0e-4 switch to 5).
@@ -296,17 +294,13 @@ def run_ours(args, world, rank, local):
     mean_chain = float(np.mean(chain_ms))
     chain_tf = cflops / (mean_chain / 1e3) / 1e12
     chain_roofline = {"bound": "fp64", "kernels": "chain_up_kernel, chain_apply_kernel",
-                      "achieved": round(chain_tf, 4), "peak": FP64_MEASURED_TFLOPS, "unit": "TFLOP/s",
-                      "frac": round(chain_tf / FP64_MEASURED_TFLOPS, 4),
-                      "peak_source": "measured FMA-chain probe on this GPU model",
+                      "achieved": round(chain_tf, 4), "peak": round(FP64_DERIVED_TFLOPS, 3), "unit": "TFLOP/s",
+                      "frac": round(chain_tf / FP64_DERIVED_TFLOPS, 4),
+                      "peak_source": FP64_PEAK_SOURCE,
                       "flops_per_sample": round(cflops / sum(samples(r) for r in reqs), 1)}
-    if args.workload == "su3":
+    if prec == S.PREC_FP64:
         roofline.update({"bound": "fp64", "peak": round(FP64_DERIVED_TFLOPS, 3),
-                         "frac": round(achieved / FP64_DERIVED_TFLOPS, 4),
-                         "peak_source": "derived: 152 SMs x 2 FP64 FMA lanes x 2 flop x 2070 MHz"})
-    elif prec == S.PREC_FP64:
-        roofline.update({"peak": 1.25, "frac": round(achieved / 1.25, 4),
-                         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (profiling recipe table)"})
+                         "frac": round(achieved / FP64_DERIVED_TFLOPS, 4), "peak_source": FP64_PEAK_SOURCE})
 
     # ---- end to end through the C ABI with pinned host buffers: the request
     # structs are marshalled once, each step is one spinsim_simulate call
