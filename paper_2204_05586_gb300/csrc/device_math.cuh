@@ -1173,10 +1173,10 @@ SPINSIM_HD void expm_general_res(R vx, R vy, R vz, R vq, const R u[4], Res3<R>& 
     cx<R> B2[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        R d = R(0);
+        R acc = R(0);
 #pragma unroll
-        for (int k = 0; k < 3; k++) d = fma(-B[i][k].r, B[i][k].r, fma(-B[i][k].i, B[i][k].i, d));
-        B2[i][i] = cmk(d, R(0));
+        for (int k = 0; k < 3; k++) acc = fma(-B[i][k].r, B[i][k].r, fma(-B[i][k].i, B[i][k].i, acc));
+        B2[i][i] = cmk(acc, R(0));
     }
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -1246,7 +1246,7 @@ SPINSIM_HD void expm_general_res(R vx, R vy, R vz, R vq, const R u[4], Res3<R>& 
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) T[i][j] = cadd(T[i][j], B[i][j]);   // T = exp(B) - I
-    // T = exp(B) - I; residual squarings
+    // residual squarings
 #pragma unroll 1
     for (int q = 0; q < s; q++) {
 #pragma unroll
