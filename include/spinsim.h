@@ -75,8 +75,10 @@ typedef enum {
 
 typedef enum {
     SPINSIM_PREC_FP64 = 0,        /* every step in FP64                                      */
-    SPINSIM_PREC_FP32_BULK = 1    /* field, exponentials and step products in FP32; U_k
-                                     re-unitarised, frame exit and chain in FP64           */
+    SPINSIM_PREC_FP32_BULK = 1    /* field, exponentials and step products in FP32; first
+                                     order, frame exit and chain in FP64; U_k stored as
+                                     computed (not re-unitarised), every written psi_k
+                                     renormalised in FP64                                  */
 } spinsim_precision;
 
 /* Handle configuration.  Zero-initialise, or call spinsim_config_default. */
@@ -97,13 +99,21 @@ typedef struct {
                                      on the caller's stream (the first call of a shape runs
                                      eagerly and captures it); calls stay in issue order   */
     int32_t device;               /* CUDA device ordinal                                      */
-    int64_t mem_budget;           /* bytes of device scratch the handle may hold; 0 = 90% of
-                                     the free memory at spinsim_create                     */
+    int64_t mem_budget;           /* bytes of device memory the handle may hold in total
+                                     (its arena for spinsim_simulate and ranges plus its
+                                     serving pool); 0 = 90% of the free memory at
+                                     spinsim_create                                        */
     int32_t profile;              /* 1: time the integrate and chain kernels of each call
                                      with CUDA events (read by spinsim_last_launch)         */
     int32_t blocks_per_sm;        /* 0 = autotune; else resident integrate blocks per SM
                                      (1..32, capped at what the kernel's registers allow).
                                      Results do not depend on it.                          */
+    int32_t chain_precision;      /* 0 = FP64 (default): the cross-sample product and the
+                                     state propagation in double precision; 1 = FP32: the
+                                     same kernels with every product rounded to single
+                                     precision, a control for precision studies (it shows
+                                     why the product stays FP64); ignored by the CPU backend */
+    int32_t reserved_cfg;         /* set to 0                                                */
 } spinsim_config;
 
 /* The fixed parameterised field family (Hz, seconds, radians):
@@ -194,7 +204,15 @@ int spinsim_config_default(spinsim_config* cfg);
 /* Create a handle on cfg->device.  The handle owns device scratch (operator
  * buffer, chain aggregates, parameter tables), pinned staging memory, the
  * autotuner's cache and the serving queue.  Returns SPINSIM_E_ARG for a bad
- * configuration, SPINSIM_E_CUDA when the device cannot be used. */
+ * configuration, SPINSIM_E_CUDA when the device cannot be used.
+ *
+ * Fault injection for testing failure handling without a GPU fault: when the
+ * environment variable SPINSIM_FAIL_ALLOC (SPINSIM_FAIL_LAUNCH) holds a
+ * positive integer n at spinsim_create, the handle's n-th device allocation
+ * (n-th kernel launch of a batch, counting the integrate and chain launches)
+ * is not made and reports failure as cudaMalloc (a launch) would:
+ * SPINSIM_E_NOMEM (SPINSIM_E_CUDA) for the batch and its requests.  Later
+ * calls on the handle run normally. */
 int spinsim_create(const spinsim_config* cfg, spinsim_handle* out);
 
 /* Release everything the handle owns (after synchronising its work). */
@@ -203,8 +221,12 @@ void spinsim_destroy(spinsim_handle h);
 /* K and L of a request, with the same validation spinsim_simulate applies. */
 int spinsim_counts(const spinsim_request* req, int64_t* K, int64_t* L);
 
-/* Bytes of device scratch spinsim_simulate needs for these n requests
- * (-SPINSIM_E_* on invalid input). */
+/* Bytes of device scratch spinsim_simulate needs for these n requests with
+ * device-resident outputs (host-resident or unaligned outputs add their own
+ * size, staged); -SPINSIM_E_* on invalid input.  A batch whose footprint
+ * exceeds the handle's mem_budget gets SPINSIM_E_NOMEM from spinsim_simulate,
+ * and a single request whose footprint exceeds it gets SPINSIM_E_NOMEM from
+ * spinsim_submit. */
 int64_t spinsim_footprint(spinsim_handle h, const spinsim_request* reqs, int64_t n);
 
 /* Simulate n independent requests as one batch on `stream` (a cudaStream_t).
@@ -219,10 +241,17 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
 
 /* Continuous-batching serving interface (Sec. 1.2.7's "many simulations from
  * one compiled simulator", served as they arrive).  spinsim_submit copies the
- * request, admits it when the handle's device-memory budget allows, and
- * launches pending requests as a batch on a free internal stream while
- * earlier batches are still running.  The result buffers must stay valid
- * until spinsim_poll reports completion.  *ticket identifies the request. */
+ * request and queues it; pending requests are launched in arrival order as
+ * one batch on a free internal stream (four) while earlier batches are still
+ * running.  A batch's device scratch is a piece of one serving pool: the
+ * queue's head waits until a stream is free and its scratch fits in the
+ * pool's free memory.  The pool grows only while no served batch is in
+ * flight (so no allocation stalls work on the device), and the pool plus the
+ * handle's arena never exceed mem_budget (spinsim_memory).  A request whose
+ * own footprint (spinsim_footprint, plus staging of host outputs) exceeds
+ * mem_budget is refused with SPINSIM_E_NOMEM and completes at once.  The
+ * result buffers must stay valid until spinsim_poll or spinsim_poll_any
+ * reports completion.  *ticket identifies the request. */
 int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result* res, int64_t* ticket);
 
 /* Drive the serving queue and report a ticket: SPINSIM_OK when its results
@@ -230,6 +259,27 @@ int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result*
  * not yet (wait_us = 0), SPINSIM_E_TIMEOUT when wait_us > 0 elapsed first, or
  * SPINSIM_E_ARG for an unknown ticket.  Completed tickets are forgotten. */
 int spinsim_poll(spinsim_handle h, int64_t ticket, int32_t wait_us);
+
+/* Drive the serving queue and report completed tickets in order of
+ * completion: up to `capacity` of them are written to tickets[] (and
+ * forgotten), *n_done receives their number.  Returns SPINSIM_OK when at
+ * least one was written (or capacity = 0), SPINSIM_PENDING when none had
+ * completed (wait_us = 0), SPINSIM_E_TIMEOUT when wait_us > 0 elapsed first.
+ * Tickets already reported by spinsim_poll are not reported again. */
+int spinsim_poll_any(spinsim_handle h, int64_t* tickets, int64_t capacity, int32_t wait_us, int64_t* n_done);
+
+/* Device memory of a handle (bytes), read on the host without waiting. */
+typedef struct {
+    int64_t budget;               /* mem_budget in effect                                    */
+    int64_t held;                 /* arena + serving pool now held                           */
+    int64_t peak_held;            /* the most held at any time since spinsim_create          */
+    int64_t arena;                /* main arena (spinsim_simulate, ranges)                   */
+    int64_t pool;                 /* serving pool                                            */
+    int64_t pool_in_use;          /* pool bytes carved for served batches in flight          */
+    int64_t pending;              /* submitted requests waiting for a stream or memory       */
+    int64_t in_flight;            /* submitted requests in batches on the device             */
+} spinsim_memory_info;
+int spinsim_memory(spinsim_handle h, spinsim_memory_info* info);
 
 /* Launch shape the last spinsim_simulate call used for its integration
  * kernel, how many kernels it launched, the bytes it copied between host and
@@ -302,6 +352,21 @@ int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_request* re
 int spinsim_range_begin(spinsim_handle h, const spinsim_request* req, spinsim_result* res, double* agg,
                         void* stream);
 int spinsim_range_finish(spinsim_handle h, const double* psi_in, void* stream);
+
+/* The exchange step between ranges (Sec. 1.2.4, Eq. integration_compilation
+ * applied range by range): the state entering range `rank`,
+ *   psi_out = A_{rank-1} ... A_1 A_0 psi_init,
+ * from the propagators A_r that spinsim_range_begin returned for ranges
+ * r = 0 .. rank - 1 (aggs: rank consecutive FP64 complex [N][N] matrices,
+ * row-major, re/im interleaved; may be NULL for rank 0) and the simulation's
+ * initial state psi_init (N complex).  Host arithmetic in FP64, in range
+ * order, the state renormalised after each range (FP32-bulk operators are
+ * not exactly unitary; the library renormalises every state it writes).
+ * psi_out receives N complex.  Needs no handle and no GPU.  Returns
+ * SPINSIM_E_ARG for a bad spin, rank < 0, NULL pointers or non-finite
+ * values, SPINSIM_E_NORM when psi_init is not normalised to 1e-10. */
+int spinsim_range_entering_state(int32_t spin_x2, const double* aggs, int32_t rank, const double* psi_init,
+                                 double* psi_out);
 
 /* Static description of a status code. */
 const char* spinsim_status_string(int status);

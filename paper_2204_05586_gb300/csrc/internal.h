@@ -341,7 +341,9 @@ cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int bloc
 void integrate_tiles(int64_t total, int lanes_bulk, int block, int64_t wave_blocks, int min_seg_log2,
                      IntegrateArgs& a);
 // launch_chain: the chain kernels of a batch in order on `stream`; *kernels
-// receives how many were launched.
-cudaError_t launch_chain(int spin_x2, const ChainArgs& a, int n_sm, cudaStream_t stream, int* kernels);
+// receives how many were launched; fp32: the products and the state
+// propagation in single precision (the precision-study control), else FP64.
+cudaError_t launch_chain(int spin_x2, const ChainArgs& a, int n_sm, cudaStream_t stream, int* kernels,
+                         bool fp32 = false);
 
 }  // namespace spinsim

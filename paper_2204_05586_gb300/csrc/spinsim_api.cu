@@ -10,8 +10,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <iterator>
 #include <map>
 #include <mutex>
 #include <new>
@@ -48,7 +50,6 @@ size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Arena {
     DevBuf buf;   // one allocation carved into the pieces of a batch
-    size_t bytes() const { return buf.cap; }
 };
 
 struct PinnedBuf {
@@ -116,17 +117,19 @@ struct Ticket {
     spinsim_result* res;
     int state;    // 0 pending, 1 in flight, 2 done
     int slot;
-    size_t bytes;
+    size_t bytes;    // scratch of the request alone (staging included)
+    size_t staged;   // staging bytes of its host-resident outputs
 };
 
+// A serving stream.  Its batch's scratch is a piece [off, off + len) of the
+// handle's serving pool, returned to the pool when the batch retires.
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
     std::vector<int64_t> tickets;
-    Arena arena;
+    size_t off = 0, len = 0;
     PinnedBuf pinned;
-    size_t in_flight = 0;
 };
 
 struct spinsim_s {
@@ -162,35 +165,100 @@ struct spinsim_s {
     spinsim_result* range_res = nullptr;
     Plan range_plan;
     std::vector<Checked> range_checked;
-    // serving
+    // device memory the handle holds (arena + serving pool), never above budget
+    size_t held = 0, peak_held = 0;
+    // host-side fault injection (SPINSIM_FAIL_ALLOC / SPINSIM_FAIL_LAUNCH at
+    // spinsim_create): the n-th device allocation or kernel launch of the
+    // handle reports failure instead of being made; 0 = off
+    int64_t fail_alloc_at = 0, fail_launch_at = 0;
+    int64_t allocs = 0, launches = 0;
+    // serving: one pool of device memory, carved into the scratch of the
+    // batches in flight (first fit; free pieces by offset, coalesced)
     std::vector<Slot> slots;
+    DevBuf pool;
+    std::map<size_t, size_t> pool_free;   // offset -> length of the free pieces
+    size_t pool_in_use = 0;
     std::deque<int64_t> pending;
+    std::deque<int64_t> done_order;       // tickets in order of completion (spinsim_poll_any)
     std::unordered_map<int64_t, Ticket> tickets;
     int64_t next_ticket = 1;
-    size_t bytes_in_flight = 0;
+    int64_t requests_in_flight = 0;
 };
 
 namespace {
 
+// Host-side fault injection: true when this allocation (or launch) is the
+// one the handle was told to fail.  Nothing is sent to the GPU for it, so the
+// failure paths (E_NOMEM, E_CUDA, per-request statuses, the handle staying
+// usable) can be exercised without a GPU fault.
+bool inject_alloc_failure(spinsim_s* h) { return h->fail_alloc_at > 0 && ++h->allocs == h->fail_alloc_at; }
+bool inject_launch_failure(spinsim_s* h) { return h->fail_launch_at > 0 && ++h->launches == h->fail_launch_at; }
+
+// Every device buffer of a handle is its main arena or its serving pool, and
+// the two together never exceed the handle's budget.
+void note_held(spinsim_s* h)
+{
+    h->held = h->arena.buf.cap + h->pool.cap;
+    h->peak_held = std::max(h->peak_held, h->held);
+}
+
+int release_device(spinsim_s* h, DevBuf& b)
+{
+    if (!b.p) return SPINSIM_OK;
+    const cudaError_t e = cudaFree(b.p);   // synchronises the device
+    b.p = nullptr;
+    b.cap = 0;
+    note_held(h);
+    return e == cudaSuccess ? SPINSIM_OK : SPINSIM_E_CUDA;
+}
+
+// Grow buffer b (the arena or the pool) to at least `need` bytes, keeping the
+// handle's total within its budget (1.5x headroom while it fits, else exact).
 int ensure_device(spinsim_s* h, DevBuf& b, size_t need)
 {
     if (b.cap >= need) return SPINSIM_OK;
-    size_t cap = std::max(need, b.cap + b.cap / 2);
-    cap = round_up(cap, size_t(1) << 20);
-    if (cap > h->budget) cap = need;
-    if (need > h->budget) return SPINSIM_E_NOMEM;
-    if (b.p) {
-        cudaError_t e = cudaFree(b.p);   // synchronises the device
-        b.p = nullptr;
-        b.cap = 0;
-        if (e != cudaSuccess) return SPINSIM_E_CUDA;
-    }
-    if (cudaMalloc(&b.p, cap) != cudaSuccess) {
+    const size_t others = h->held - b.cap;
+    if (need > h->budget || others > h->budget - need) return SPINSIM_E_NOMEM;
+    size_t cap = round_up(std::max(need, b.cap + b.cap / 2), size_t(1) << 20);
+    if (cap > h->budget - others) cap = need;
+    int st = release_device(h, b);
+    if (st != SPINSIM_OK) return st;
+    if (inject_alloc_failure(h) || cudaMalloc(&b.p, cap) != cudaSuccess) {
         cudaGetLastError();
+        b.p = nullptr;
         return SPINSIM_E_NOMEM;
     }
     b.cap = cap;
+    note_held(h);
     return SPINSIM_OK;
+}
+
+bool serving_busy(const spinsim_s* h)
+{
+    for (const Slot& s : h->slots)
+        if (s.busy) return true;
+    return false;
+}
+
+// Free the serving pool (no batch may be in flight on it).
+int release_pool(spinsim_s* h)
+{
+    h->pool_free.clear();
+    h->pool_in_use = 0;
+    return release_device(h, h->pool);
+}
+
+// Grow the main arena; when the serving pool's memory stands in the way and
+// no served batch is in flight, the pool is given back first.
+int ensure_arena(spinsim_s* h, size_t need)
+{
+    int st = ensure_device(h, h->arena.buf, need);
+    if (st == SPINSIM_E_NOMEM && h->pool.p && !serving_busy(h) && need <= h->budget) {
+        st = release_pool(h);
+        if (st != SPINSIM_OK) return st;
+        st = ensure_device(h, h->arena.buf, need);
+    }
+    return st;
 }
 
 int ensure_pinned(PinnedBuf& b, size_t need)
@@ -223,6 +291,56 @@ size_t group_bytes(int spin_x2, int64_t n, int64_t samples, const int64_t* nodes
     return table_bytes(n, levels) + 256 /* tile counter */ + round_up((size_t)samples * opb, 256) +
            chain_layout(spin_x2, nodes, levels).bytes;
 }
+
+// Outputs that are not 16-byte aligned device memory are staged through the
+// batch's scratch.  While a stream is being captured pointer kinds cannot be
+// queried; outputs are then taken to be device memory.
+bool needs_stage(const void* p, bool capturing)
+{
+    return p && ((!capturing && !is_device_pointer(p)) || ((uintptr_t)p & 15u) != 0);
+}
+
+// Staging bytes of one request's outputs (each piece 256-byte aligned).
+size_t staging_bytes(const spinsim_request& r, const spinsim_result& res, int64_t K, bool capturing)
+{
+    const size_t N = (size_t)r.spin_x2 + 1;
+    size_t b = 0;
+    if (needs_stage(res.states, capturing)) b += round_up((size_t)K * 2 * N * sizeof(double), 256);
+    if (needs_stage(res.spin, capturing)) b += round_up((size_t)K * 3 * sizeof(double), 256);
+    if (needs_stage(res.ops, capturing)) b += round_up((size_t)K * 2 * N * N * sizeof(double), 256);
+    return b;
+}
+
+// Device scratch of a batch, accumulated request by request: one group per
+// (spin, kernel variant) as build_plan forms them, plus the staged outputs.
+// total() is the plan.total build_plan gives the same batch.
+struct Footprint {
+    int64_t count[kMaxGroups] = {}, samples[kMaxGroups] = {};
+    int64_t nodes[kMaxGroups][kMaxLevels] = {};
+    int levels[kMaxGroups];
+    size_t staged = 0;
+    Footprint()
+    {
+        for (int& l : levels) l = 1;
+    }
+    void add(int spin_x2, int variant, int64_t K, size_t staged_bytes)
+    {
+        const int g = (spin_x2 - 1) * kVariants + variant;
+        count[g] += 1;
+        samples[g] += K;
+        const ChainGeom cg = chain_geom(K);
+        levels[g] = std::max(levels[g], cg.top + 1);
+        for (int l = 0; l <= cg.top; l++) nodes[g][l] += cg.nodes[l];
+        staged += staged_bytes;
+    }
+    size_t total() const
+    {
+        size_t t = staged;
+        for (int g = 0; g < kMaxGroups; g++)
+            if (count[g]) t += group_bytes(1 + g / kVariants, count[g], samples[g], nodes[g], levels[g]);
+        return std::max<size_t>(t, 256);
+    }
+};
 
 // Build the plan: offsets inside one arena, the staged outputs, and fill the
 // pinned parameter table.  `checked` holds the validation of every request.
@@ -271,10 +389,8 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
             const int N = reqs[i].spin_x2 + 1;
             const int64_t K = checked[i].K;
             spinsim_result& r = res[i];
-            auto needs_stage = [capturing](const void* p) {
-                return p && ((!capturing && !is_device_pointer(p)) || ((uintptr_t)p & 15u) != 0);
-            };
-            bool st = needs_stage(r.states), sp = needs_stage(r.spin), op = needs_stage(r.ops);
+            bool st = needs_stage(r.states, capturing), sp = needs_stage(r.spin, capturing),
+                 op = needs_stage(r.ops, capturing);
             if (!(st || sp || op)) continue;
             StagedOut so{};
             so.req = i;
@@ -507,8 +623,10 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
         return SPINSIM_OK;
     }
     if (plan.total > arena.buf.cap) {
-        if (capturing) return SPINSIM_E_UNSUPPORTED;
-        int st = ensure_device(h, arena.buf, plan.total);
+        // only the handle's own arena grows here; a serving batch's piece of
+        // the pool is carved at its plan's size
+        if (capturing || &arena != &h->arena) return SPINSIM_E_UNSUPPORTED;
+        int st = ensure_arena(h, plan.total);
         if (st != SPINSIM_OK) return st;
     }
     char* base = static_cast<char*>(arena.buf.p);
@@ -547,8 +665,9 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
                 if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
                     return SPINSIM_E_CUDA;
                 if (pg >= 0) prof_record(h->prof[pg][0]);
-                if (launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, block, grid, g.variant, ia, stream) !=
-                    cudaSuccess)
+                if (inject_launch_failure(h) ||
+                    launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, block, grid, g.variant, ia, stream) !=
+                        cudaSuccess)
                     return SPINSIM_E_CUDA;
                 kernels += 1;
             }
@@ -561,7 +680,9 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             chain_args_set(ca, g.chain, base + g.chain_off);
             ca.mode = phase == kPhaseBegin ? kChainUp : (phase == kPhaseFinish ? kChainDown : kChainFull);
             int chain_k = 0;
-            if (launch_chain(g.spin_x2, ca, h->n_sm, stream, &chain_k) != cudaSuccess) return SPINSIM_E_CUDA;
+            if (inject_launch_failure(h) ||
+                launch_chain(g.spin_x2, ca, h->n_sm, stream, &chain_k, h->cfg.chain_precision == 1) != cudaSuccess)
+                return SPINSIM_E_CUDA;
             if (pg >= 0) prof_record(h->prof[pg][2]);
             kernels += chain_k;
             h->last.lanes_per_sample = lanes;
@@ -658,7 +779,8 @@ int spinsim_create(const spinsim_config* cfg, spinsim_handle* out)
           cfg->lanes_per_sample == 4 || cfg->lanes_per_sample == 8) ||
         !(cfg->threads_per_block == 0 || cfg->threads_per_block == 64 || cfg->threads_per_block == 128 ||
           cfg->threads_per_block == 256) ||
-        cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32 || cfg->mem_budget < 0)
+        cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32 || cfg->mem_budget < 0 || cfg->chain_precision < 0 ||
+        cfg->chain_precision > 1)
         return SPINSIM_E_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
@@ -678,6 +800,15 @@ int spinsim_create(const spinsim_config* cfg, spinsim_handle* out)
         return SPINSIM_E_CUDA;
     }
     h->budget = cfg->mem_budget > 0 ? (size_t)cfg->mem_budget : (size_t)(0.9 * (double)free_b);
+    auto env_count = [](const char* name) -> int64_t {
+        const char* v = std::getenv(name);
+        if (!v || !*v) return 0;
+        char* end = nullptr;
+        const long long n = std::strtoll(v, &end, 10);
+        return (end && *end == '\0' && n > 0) ? (int64_t)n : 0;
+    };
+    h->fail_alloc_at = env_count("SPINSIM_FAIL_ALLOC");
+    h->fail_launch_at = env_count("SPINSIM_FAIL_LAUNCH");
     if (cudaStreamCreateWithFlags(&h->work, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess ||
@@ -704,12 +835,12 @@ void spinsim_destroy(spinsim_handle h)
     cudaDeviceSynchronize();
     drop_graph(h);
     for (Slot& s : h->slots) {
-        if (s.arena.buf.p) cudaFree(s.arena.buf.p);
         if (s.pinned.p) cudaFreeHost(s.pinned.p);
         if (s.done) cudaEventDestroy(s.done);
         if (s.stream) cudaStreamDestroy(s.stream);
     }
     if (h->arena.buf.p) cudaFree(h->arena.buf.p);
+    if (h->pool.p) cudaFree(h->pool.p);
     if (h->pinned.p) cudaFreeHost(h->pinned.p);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
@@ -734,25 +865,13 @@ int spinsim_counts(const spinsim_request* req, int64_t* K, int64_t* L)
 int64_t spinsim_footprint(spinsim_handle h, const spinsim_request* reqs, int64_t n)
 {
     if (!h || (n > 0 && !reqs) || n < 0) return SPINSIM_E_ARG;
-    // the launch groups of build_plan: one per (spin, kernel variant)
-    int64_t samples[kMaxGroups] = {}, count[kMaxGroups] = {};
-    int64_t nodes[kMaxGroups][kMaxLevels] = {};
-    int levels[kMaxGroups];
-    for (int g = 0; g < kMaxGroups; g++) levels[g] = 1;
+    Footprint fp;
     for (int64_t i = 0; i < n; i++) {
         Checked c = check_request(&reqs[i]);
         if (c.status != SPINSIM_OK) return c.status;
-        const int g = (reqs[i].spin_x2 - 1) * kVariants + request_variant(h->cfg, reqs[i], c.L);
-        samples[g] += c.K;
-        count[g] += 1;
-        const ChainGeom cg = chain_geom(c.K);
-        levels[g] = std::max(levels[g], cg.top + 1);
-        for (int l = 0; l <= cg.top; l++) nodes[g][l] += cg.nodes[l];
+        fp.add(reqs[i].spin_x2, request_variant(h->cfg, reqs[i], c.L), c.K, 0);
     }
-    int64_t total = 0;
-    for (int g = 0; g < kMaxGroups; g++)
-        if (count[g]) total += (int64_t)group_bytes(1 + g / kVariants, count[g], samples[g], nodes[g], levels[g]);
-    return total;
+    return n > 0 ? (int64_t)fp.total() : 0;
 }
 
 int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_result* res, int64_t n, void* stream_v)
@@ -786,6 +905,15 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
         cap = cudaStreamCaptureStatusNone;
     }
     const bool capturing = cap != cudaStreamCaptureStatusNone;
+    // a batch that cannot run: every request that was to run carries the error
+    auto fail = [&](int e) {
+        for (int64_t i = 0; i < n; i++)
+            if (checked[i].status == SPINSIM_OK) {
+                res[i].status = e;
+                res[i].n_samples = 0;
+            }
+        return e;
+    };
     h->last = spinsim_launch_info{};
     h->last.trotter_squares = 0;
     h->last.integrate_ms = -1.0;
@@ -805,11 +933,11 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
             // caller's stream (after the handle's previous replay)
             st = refresh_table(h, reqs, res, checked, plan, static_cast<char*>(h->arena.buf.p), h->pinned,
                                h->ev_pinned, false);
-            if (st != SPINSIM_OK) return st;
-            if (h->done_pending && cudaStreamWaitEvent(stream, h->ev_done, 0) != cudaSuccess) return SPINSIM_E_CUDA;
-            if (cudaGraphLaunch(h->graph_exec, stream) != cudaSuccess) return SPINSIM_E_CUDA;
+            if (st != SPINSIM_OK) return fail(st);
+            if (h->done_pending && cudaStreamWaitEvent(stream, h->ev_done, 0) != cudaSuccess) return fail(SPINSIM_E_CUDA);
+            if (cudaGraphLaunch(h->graph_exec, stream) != cudaSuccess) return fail(SPINSIM_E_CUDA);
             if (cudaEventRecord(h->ev_pinned, stream) != cudaSuccess || cudaEventRecord(h->ev_done, stream) != cudaSuccess)
-                return SPINSIM_E_CUDA;
+                return fail(SPINSIM_E_CUDA);
             h->done_pending = true;
             h->last = h->graph_info;
             h->last.graph_replayed = 1;
@@ -822,12 +950,12 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
             // on the internal stream, after the caller's earlier work and the
             // handle's last replay
             if (cudaEventRecord(h->ev_in, stream) != cudaSuccess || cudaStreamWaitEvent(h->work, h->ev_in, 0) != cudaSuccess)
-                return SPINSIM_E_CUDA;
-            if (h->done_pending && cudaStreamWaitEvent(h->work, h->ev_done, 0) != cudaSuccess) return SPINSIM_E_CUDA;
+                return fail(SPINSIM_E_CUDA);
+            if (h->done_pending && cudaStreamWaitEvent(h->work, h->ev_done, 0) != cudaSuccess) return fail(SPINSIM_E_CUDA);
             // first run eagerly: sizes scratch and tunes the launch shape
             st = run_batch(h, reqs, res, checked, plan, h->work, h->arena, h->pinned, h->ev_pinned, false, &kernels);
-            if (st != SPINSIM_OK) return st;
-            if (cudaStreamSynchronize(h->work) != cudaSuccess) return SPINSIM_E_CUDA;
+            if (st != SPINSIM_OK) return fail(st);
+            if (cudaStreamSynchronize(h->work) != cudaSuccess) return fail(SPINSIM_E_CUDA);
             // then capture the same batch for later replays
             // (the eager run's profiling events keep their timestamps: recording
             // them as graph nodes during the capture does not touch them)
@@ -860,7 +988,7 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
             cudaEventRecord(h->ev_pinned, h->work);
             if (cudaEventRecord(h->ev_out, h->work) != cudaSuccess || cudaStreamWaitEvent(stream, h->ev_out, 0) != cudaSuccess ||
                 cudaEventRecord(h->ev_done, h->work) != cudaSuccess)
-                return SPINSIM_E_CUDA;
+                return fail(SPINSIM_E_CUDA);
             h->done_pending = true;
         }
     } else {
@@ -868,10 +996,10 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
         build_plan(reqs, res, n, checked, capturing, plan);
         st = run_batch(h, reqs, res, checked, plan, stream, h->arena, h->pinned, capturing ? nullptr : h->ev_pinned,
                        capturing, &kernels);
-        if (st != SPINSIM_OK) return st;
+        if (st != SPINSIM_OK) return fail(st);
     }
     h->last.kernels_launched = kernels;
-    if (cudaGetLastError() != cudaSuccess) return SPINSIM_E_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return fail(SPINSIM_E_CUDA);
     return first_err;
 }
 
@@ -972,6 +1100,45 @@ int spinsim_range_finish(spinsim_handle h, const double* psi_in, void* stream_v)
     return st;
 }
 
+int spinsim_range_entering_state(int32_t spin_x2, const double* aggs, int32_t rank, const double* psi_init,
+                                 double* psi_out)
+{
+    if ((spin_x2 != 1 && spin_x2 != 2) || rank < 0 || !psi_init || !psi_out || (rank > 0 && !aggs))
+        return SPINSIM_E_ARG;
+    const int n = spin_x2 + 1;
+    double psi[6] = {}, nrm = 0.0;
+    for (int i = 0; i < 2 * n; i++) {
+        if (!std::isfinite(psi_init[i])) return SPINSIM_E_ARG;
+        psi[i] = psi_init[i];
+        nrm += psi[i] * psi[i];
+    }
+    if (std::fabs(std::sqrt(nrm) - 1.0) > 1e-10) return SPINSIM_E_NORM;
+    // psi <- A_r psi for r = 0 .. rank - 1 (later ranges on the left), FP64,
+    // renormalised after each range as every written state is
+    for (int r = 0; r < rank; r++) {
+        const double* A = aggs + (size_t)r * 2 * n * n;
+        double out[6] = {};
+        for (int i = 0; i < n; i++) {
+            double re = 0.0, im = 0.0;
+            for (int j = 0; j < n; j++) {
+                const double ar = A[2 * (i * n + j)], ai = A[2 * (i * n + j) + 1];
+                if (!std::isfinite(ar) || !std::isfinite(ai)) return SPINSIM_E_ARG;
+                re += ar * psi[2 * j] - ai * psi[2 * j + 1];
+                im += ar * psi[2 * j + 1] + ai * psi[2 * j];
+            }
+            out[2 * i] = re;
+            out[2 * i + 1] = im;
+        }
+        double n2 = 0.0;
+        for (int i = 0; i < 2 * n; i++) n2 += out[i] * out[i];
+        if (!(n2 > 0.0)) return SPINSIM_E_ARG;
+        const double inv = 1.0 / std::sqrt(n2);
+        for (int i = 0; i < 2 * n; i++) psi[i] = out[i] * inv;
+    }
+    for (int i = 0; i < 2 * n; i++) psi_out[i] = psi[i];
+    return SPINSIM_OK;
+}
+
 int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info)
 {
     if (!h || !info) return SPINSIM_E_ARG;
@@ -993,6 +1160,14 @@ int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info)
 }
 
 // ------------------------------------------------------------------ serving
+// Continuous batching: requests wait in FIFO order until a stream slot is
+// free and their scratch fits in the serving pool; every batch's scratch is a
+// piece of that one pool.  The pool grows (cudaFree + cudaMalloc, which
+// synchronise the device) only while no served batch is in flight, so no
+// allocation ever stalls work already on the device, and the pool plus the
+// main arena never exceed the handle's budget.
+static constexpr size_t kPoolMinBytes = size_t(64) << 20;
+
 static int serving_init(spinsim_s* h)
 {
     if (!h->slots.empty()) return SPINSIM_OK;
@@ -1006,74 +1181,170 @@ static int serving_init(spinsim_s* h)
     return SPINSIM_OK;
 }
 
-static size_t request_bytes(const spinsim_request& r, const Checked& c)
+// First fit of `len` bytes (a multiple of 256) in the pool's free pieces.
+static bool pool_carve(spinsim_s* h, size_t len, size_t* off)
 {
-    const ChainGeom cg = chain_geom(c.K);
-    return group_bytes(r.spin_x2, 1, c.K, cg.nodes, cg.top + 1);
+    for (auto it = h->pool_free.begin(); it != h->pool_free.end(); ++it)
+        if (it->second >= len) {
+            const size_t o = it->first, rest = it->second - len;
+            h->pool_free.erase(it);
+            if (rest) h->pool_free[o + len] = rest;
+            h->pool_in_use += len;
+            *off = o;
+            return true;
+        }
+    return false;
+}
+
+// Give a piece back, merging it with free neighbours.
+static void pool_return(spinsim_s* h, size_t off, size_t len)
+{
+    if (!len) return;
+    h->pool_in_use -= len;
+    auto next = h->pool_free.lower_bound(off);
+    if (next != h->pool_free.end() && off + len == next->first) {
+        len += next->second;
+        next = h->pool_free.erase(next);
+    }
+    if (next != h->pool_free.begin()) {
+        auto prev = std::prev(next);
+        if (prev->first + prev->second == off) {
+            prev->second += len;
+            return;
+        }
+    }
+    h->pool_free[off] = len;
+}
+
+static size_t pool_largest_free(const spinsim_s* h)
+{
+    size_t m = 0;
+    for (const auto& f : h->pool_free) m = std::max(m, f.second);
+    return m;
+}
+
+// Replace the (idle) pool by one of at least `need` bytes: twice the old
+// size or kPoolMinBytes when the budget allows.  The main arena is given
+// back first when it leaves too little of the budget.
+static int pool_grow(spinsim_s* h, size_t need)
+{
+    if (need > h->budget) return SPINSIM_E_NOMEM;
+    int st = release_pool(h);
+    if (st != SPINSIM_OK) return st;
+    if (h->arena.buf.cap > h->budget - need) {
+        drop_graph(h);   // the handle's graph refers to the arena
+        h->range_open = false;
+        st = release_device(h, h->arena.buf);
+        if (st != SPINSIM_OK) return st;
+    }
+    const size_t room = h->budget - h->arena.buf.cap;
+    size_t cap = round_up(std::max({need, 2 * h->pool.cap, kPoolMinBytes}), size_t(1) << 20);
+    cap = std::min(cap, room);
+    if (cap < need) return SPINSIM_E_NOMEM;
+    if (inject_alloc_failure(h) || cudaMalloc(&h->pool.p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        h->pool.p = nullptr;
+        return SPINSIM_E_NOMEM;
+    }
+    h->pool.cap = cap;
+    note_held(h);
+    h->pool_free[0] = cap;
+    return SPINSIM_OK;
+}
+
+static void ticket_done(spinsim_s* h, int64_t id, Ticket& tk)
+{
+    tk.state = 2;
+    h->done_order.push_back(id);
 }
 
 // Retire finished batches, then launch pending requests on free slots while
-// the memory budget admits them (FIFO: the head waits until it fits).
+// their scratch fits in the pool (FIFO: the head waits until it fits).
 static int serving_pump(spinsim_s* h)
 {
-    for (size_t si = 0; si < h->slots.size(); si++) {
-        Slot& s = h->slots[si];
+    for (Slot& s : h->slots) {
         if (!s.busy) continue;
         cudaError_t q = cudaEventQuery(s.done);
         if (q == cudaErrorNotReady) continue;
         const int st = q == cudaSuccess ? SPINSIM_OK : SPINSIM_E_CUDA;
+        if (q != cudaSuccess) cudaGetLastError();
         for (int64_t t : s.tickets) {
             auto it = h->tickets.find(t);
             if (it == h->tickets.end()) continue;
-            it->second.state = 2;
             if (st != SPINSIM_OK) it->second.res->status = st;
+            ticket_done(h, t, it->second);
         }
+        h->requests_in_flight -= (int64_t)s.tickets.size();
         s.tickets.clear();
-        h->bytes_in_flight -= s.in_flight;
-        s.in_flight = 0;
+        pool_return(h, s.off, s.len);
+        s.off = s.len = 0;
         s.busy = false;
     }
-    for (size_t si = 0; si < h->slots.size() && !h->pending.empty(); si++) {
-        Slot& s = h->slots[si];
+    for (Slot& s : h->slots) {
+        if (h->pending.empty()) break;
         if (s.busy) continue;
+        size_t room = pool_largest_free(h);
+        {
+            Ticket& head = h->tickets[h->pending.front()];
+            if (head.bytes > room && !serving_busy(h)) {
+                // nothing in flight: the pool may be replaced without stalling work
+                const int st = pool_grow(h, head.bytes);
+                if (st != SPINSIM_OK) {
+                    head.res->status = st;
+                    ticket_done(h, h->pending.front(), head);
+                    h->pending.pop_front();
+                    continue;
+                }
+                room = pool_largest_free(h);
+            }
+        }
         std::vector<spinsim_request> reqs;
         std::vector<spinsim_result> res;
         std::vector<int64_t> ids;
         std::vector<Checked> checked;
-        size_t bytes = 0;
+        Footprint fp;
         while (!h->pending.empty()) {
             const int64_t t = h->pending.front();
             Ticket& tk = h->tickets[t];
-            if (h->bytes_in_flight + bytes + tk.bytes > h->budget && !ids.empty()) break;
-            if (h->bytes_in_flight + bytes + tk.bytes > h->budget && h->bytes_in_flight > 0) break;
+            Checked c = check_request(&tk.req);
+            if (c.status == SPINSIM_OK) c.status = precision_status(h->cfg, tk.req);
+            if (c.status == SPINSIM_OK) c.variant = request_variant(h->cfg, tk.req, c.L);
+            Footprint next = fp;
+            next.add(tk.req.spin_x2, c.variant, c.K, tk.staged);
+            if (next.total() > room) break;
+            fp = next;
             h->pending.pop_front();
             reqs.push_back(tk.req);
             res.push_back(*tk.res);
             ids.push_back(t);
-            Checked c = check_request(&tk.req);
-            if (c.status == SPINSIM_OK) c.status = precision_status(h->cfg, tk.req);
-            if (c.status == SPINSIM_OK) c.variant = request_variant(h->cfg, tk.req, c.L);
             checked.push_back(c);
-            bytes += tk.bytes;
         }
-        if (ids.empty()) break;
-        int kernels = 0;
+        if (ids.empty()) break;   // the head waits for a batch to retire
         Plan plan;
         build_plan(reqs.data(), res.data(), (int64_t)reqs.size(), checked, false, plan);
-        int st = run_batch(h, reqs.data(), res.data(), checked, plan, s.stream, s.arena, s.pinned, s.done, false,
+        size_t off = 0;
+        int st = SPINSIM_OK;
+        if (!pool_carve(h, round_up(plan.total, 256), &off)) st = SPINSIM_E_NOMEM;   // total() bounds plan.total
+        int kernels = 0;
+        if (st == SPINSIM_OK) {
+            s.off = off;
+            s.len = round_up(plan.total, 256);
+            Arena piece;
+            piece.buf.p = static_cast<char*>(h->pool.p) + off;
+            piece.buf.cap = s.len;
+            st = run_batch(h, reqs.data(), res.data(), checked, plan, s.stream, piece, s.pinned, s.done, false,
                            &kernels);
+        }
         for (size_t q = 0; q < ids.size(); q++) {
             Ticket& tk = h->tickets[ids[q]];
             tk.state = 1;
-            tk.slot = (int)si;
             tk.res->trotter_squares = res[q].trotter_squares;
             if (st != SPINSIM_OK) tk.res->status = st;
         }
         if (cudaEventRecord(s.done, s.stream) != cudaSuccess) return SPINSIM_E_CUDA;
         s.tickets = ids;
         s.busy = true;
-        s.in_flight = bytes;
-        h->bytes_in_flight += bytes;
+        h->requests_in_flight += (int64_t)ids.size();
     }
     return SPINSIM_OK;
 }
@@ -1101,24 +1372,23 @@ int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result*
     tk.req = *req;
     tk.res = res;
     tk.slot = -1;
-    tk.bytes = c.status == SPINSIM_OK ? request_bytes(*req, c) : 0;
+    tk.state = 0;
+    tk.staged = 0;
+    tk.bytes = 0;
+    if (c.status == SPINSIM_OK) {
+        tk.staged = staging_bytes(*req, *res, c.K, false);
+        Footprint fp;
+        fp.add(req->spin_x2, request_variant(h->cfg, *req, c.L), c.K, tk.staged);
+        tk.bytes = round_up(fp.total(), 256);
+        if (tk.bytes > h->budget) c.status = res->status = SPINSIM_E_NOMEM;   // could never be admitted
+    }
+    h->tickets[id] = tk;
+    *ticket = id;
     if (c.status != SPINSIM_OK) {
-        tk.state = 2;
-        h->tickets[id] = tk;
-        *ticket = id;
+        ticket_done(h, id, h->tickets[id]);
         return c.status;
     }
-    if (tk.bytes > h->budget) {
-        res->status = SPINSIM_E_NOMEM;
-        tk.state = 2;
-        h->tickets[id] = tk;
-        *ticket = id;
-        return SPINSIM_E_NOMEM;
-    }
-    tk.state = 0;
-    h->tickets[id] = tk;
     h->pending.push_back(id);
-    *ticket = id;
     return serving_pump(h);
 }
 
@@ -1141,6 +1411,45 @@ int spinsim_poll(spinsim_handle h, int64_t ticket, int32_t wait_us)
         if (dt >= wait_us) return SPINSIM_E_TIMEOUT;
         std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+}
+
+int spinsim_poll_any(spinsim_handle h, int64_t* tickets, int64_t capacity, int32_t wait_us, int64_t* n_done)
+{
+    if (!h || !n_done || capacity < 0 || (capacity > 0 && !tickets)) return SPINSIM_E_ARG;
+    *n_done = 0;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SPINSIM_E_CUDA;
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        int st = serving_pump(h);
+        if (st != SPINSIM_OK) return st;
+        while (*n_done < capacity && !h->done_order.empty()) {
+            const int64_t t = h->done_order.front();
+            h->done_order.pop_front();
+            auto it = h->tickets.find(t);
+            if (it == h->tickets.end()) continue;   // already reported by spinsim_poll
+            h->tickets.erase(it);
+            tickets[(*n_done)++] = t;
+        }
+        if (*n_done > 0 || capacity == 0) return SPINSIM_OK;
+        if (wait_us <= 0) return SPINSIM_PENDING;
+        auto dt = std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (dt >= wait_us) return SPINSIM_E_TIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+int spinsim_memory(spinsim_handle h, spinsim_memory_info* info)
+{
+    if (!h || !info) return SPINSIM_E_ARG;
+    info->budget = (int64_t)h->budget;
+    info->held = (int64_t)h->held;
+    info->peak_held = (int64_t)h->peak_held;
+    info->arena = (int64_t)h->arena.buf.cap;
+    info->pool = (int64_t)h->pool.cap;
+    info->pool_in_use = (int64_t)h->pool_in_use;
+    info->pending = (int64_t)h->pending.size();
+    info->in_flight = h->requests_in_flight;
+    return SPINSIM_OK;
 }
 
 }  // extern "C"

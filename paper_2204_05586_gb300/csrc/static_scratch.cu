@@ -48,6 +48,50 @@ bool device_resident(const void* p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Everything the kernels read from the parameter table, passed by value to a
+// set-up kernel that writes it into the static array: no host staging buffer
+// and no copy from pageable memory.
+struct StaticTable {
+    DevSim sim;
+    int64_t K;
+    int64_t nodes[kMaxLevels];
+    int32_t levels;
+};
+
+__global__ void static_table_kernel(StaticTable t, DevSim* sims, int64_t* sample_offsets, int64_t* level_off,
+                                    unsigned long long* tile_counter)
+{
+    // the record as 8-byte words, one per thread in turn
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(&t.sim);
+    uint64_t* dst = reinterpret_cast<uint64_t*>(sims);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevSim) / sizeof(uint64_t)); i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) {
+        sample_offsets[0] = 0;
+        sample_offsets[1] = t.K;
+        for (int l = 0; l < t.levels; l++) {
+            level_off[2 * l] = 0;
+            level_off[2 * l + 1] = t.nodes[l];
+        }
+        *tile_counter = 0;   // the previous call left its final count here
+    }
+}
+static_assert(sizeof(DevSim) % sizeof(uint64_t) == 0, "DevSim is copied as 8-byte words");
+
+// Restores the caller's current device when the entry point returns.
+struct DeviceGuard {
+    int prev = -1;
+    DeviceGuard()
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 }  // namespace
 
@@ -61,7 +105,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
           cfg->lanes_per_sample == 4 || cfg->lanes_per_sample == 8) ||
         !(cfg->threads_per_block == 0 || cfg->threads_per_block == 64 || cfg->threads_per_block == 128 ||
           cfg->threads_per_block == 256) ||
-        cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32)
+        cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32 || cfg->chain_precision < 0 || cfg->chain_precision > 1)
         return SPINSIM_E_ARG;
     int64_t K = 0, L = 0;
     int st = spinsim_counts(req, &K, &L);
@@ -85,6 +129,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
             return SPINSIM_E_ARG;
         }
     if (cfg->device < 0 || cfg->device >= kMaxDevices) return res->status = SPINSIM_E_ARG;
+    DeviceGuard keep_device;   // the caller's current device is restored on return
     if (cudaSetDevice(cfg->device) != cudaSuccess) return res->status = SPINSIM_E_CUDA;
     // set-up, once per device with that device current: the device address of
     // the static array (its host-side name is not a device address)
@@ -126,17 +171,20 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     d.chain_top = cg.top;
     const int variant = request_variant(*cfg, *req, L);
     res->trotter_squares = d.tau;
-    // sample offsets {0, K} and, per chain level, the node offsets {0, nodes}
-    int64_t offsets[2] = {0, K};
-    int64_t level_off[kMaxLevels * 2] = {};
-    for (int l = 0; l <= cg.top; l++) level_off[2 * l + 1] = cg.nodes[l];
+    // the parameter table (the record, sample offsets {0, K}, per chain level
+    // the node offsets {0, nodes}) and a cleared tile counter, written on the
+    // stream by one small kernel from its by-value argument
+    StaticTable tbl;
+    tbl.sim = d;
+    tbl.K = K;
+    tbl.levels = cg.top + 1;
+    for (int l = 0; l < kMaxLevels; l++) tbl.nodes[l] = l <= cg.top ? cg.nodes[l] : 0;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
-    // Copies from pageable host memory: the source may be reused on return.
-    if (cudaMemcpyAsync(base + sims_off, &d, sizeof(DevSim), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-        cudaMemcpyAsync(base + soff_off, offsets, sizeof(offsets), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-        cudaMemcpyAsync(base + loff_off, level_off, (size_t)(cg.top + 1) * 2 * sizeof(int64_t),
-                        cudaMemcpyHostToDevice, stream) != cudaSuccess)
-        return res->status = SPINSIM_E_CUDA;
+    static_table_kernel<<<1, 32, 0, stream>>>(tbl, reinterpret_cast<DevSim*>(base + sims_off),
+                                              reinterpret_cast<int64_t*>(base + soff_off),
+                                              reinterpret_cast<int64_t*>(base + loff_off),
+                                              reinterpret_cast<unsigned long long*>(base + counter_off));
+    if (cudaGetLastError() != cudaSuccess) return res->status = SPINSIM_E_CUDA;
     if (K > 0) {
         int n_sm = 0;
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, cfg->device);
@@ -159,9 +207,6 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         const int64_t wave_blocks = (int64_t)n_sm * std::max(per_sm, 1);
         integrate_tiles(K, lanes, block, wave_blocks, seg_log2_of(L), ia);
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ia.n_tiles, wave_blocks));
-        // the tile counter keeps the previous call's value: clear it
-        if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
-            return res->status = SPINSIM_E_CUDA;
         if (launch_integrate(spin, cfg->precision, cfg->method, block, grid, variant, ia, stream) != cudaSuccess)
             return res->status = SPINSIM_E_CUDA;
         ChainArgs ca;
@@ -171,7 +216,8 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         ca.U = ia.U;
         chain_args_set(ca, cl, base + chain_off);
         int chain_k = 0;
-        if (launch_chain(spin, ca, n_sm, stream, &chain_k) != cudaSuccess) return res->status = SPINSIM_E_CUDA;
+        if (launch_chain(spin, ca, n_sm, stream, &chain_k, cfg->chain_precision == 1) != cudaSuccess)
+            return res->status = SPINSIM_E_CUDA;
     }
     res->n_samples = K;
     res->status = SPINSIM_OK;

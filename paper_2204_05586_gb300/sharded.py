@@ -1,4 +1,5 @@
-"""One long simulation split over processes (Sec. 1.2.4).
+"""Work split over processes: a batch of independent simulations
+(``partition``), and one long simulation split into ranges (Sec. 1.2.4).
 
 The sample operators U_k depend only on the field, so contiguous ranges of
 output samples can be computed by different processes (one per GPU).  What
@@ -10,8 +11,9 @@ A_j the propagator over range j.  So each process
      (``spinsim_range_begin``; the operators stay on its GPU),
   2. exchanges A_r with every other process (one all-gather of one N x N
      FP64 complex matrix per range),
-  3. forms its entering state from the gathered products (every process
-     does the same tiny product, in FP64, in range order) and
+  3. forms its entering state from the gathered products
+     (``spinsim_range_entering_state``: every process does the same tiny
+     product, in FP64, in range order) and
   4. writes its states from that entering state (``spinsim_range_finish``).
 
 A range r < last is run as the request for its samples plus one: its K
@@ -25,6 +27,34 @@ transport.
 from __future__ import annotations
 
 import numpy as np
+
+
+def estimated_steps(req: dict) -> int:
+    """Integration steps of a request, (K - 1) L: the sample operators U_1 ..
+    U_{K-1} of L steps each (U_0 is the identity); the measure of work by
+    which a batch is split."""
+    K = int(round((req["t_end"] - req["t_start"]) / req["dt_out"]))
+    L = int(round(req["dt_out"] / req["dt"]))
+    return max(K - 1, 0) * L
+
+
+def partition(reqs, world: int):
+    """Split a batch of independent simulations over `world` processes by
+    estimated steps, greedily longest first: requests in decreasing order of
+    steps (ties: lower index first), each to the process with the fewest
+    steps so far (ties: lower rank).  Returns one ascending index list per
+    rank.  Every process then runs its share as one batch; no data passes
+    between them (a request's result does not depend on its batch)."""
+    if world < 1:
+        raise ValueError("world >= 1 required")
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    steps = [estimated_steps(r) for r in reqs]
+    for i in sorted(range(len(reqs)), key=lambda j: (-steps[j], j)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += steps[i]
+    return [sorted(p) for p in parts]
 
 
 def ranges(K: int, world: int):
@@ -53,16 +83,18 @@ def range_request(req: dict, k0: int, k1: int, last: bool) -> dict:
 
 
 def entering_states(aggs, psi_init):
-    """States entering every range: psi_0 = psi_init, psi_{r+1} = A_r psi_r
-    (FP64, in range order), each renormalised: FP32-bulk operators depart from
-    unitarity by the rounding of their second-order part, and the library
-    renormalises every state it writes in the same way."""
-    psi = np.asarray(psi_init, dtype=np.complex128)
-    out = [psi.copy()]
-    for A in aggs[:-1]:
-        psi = np.asarray(A, dtype=np.complex128) @ psi
-        psi = psi / np.linalg.norm(psi)
-        out.append(psi.copy())
+    """States entering every range: psi_0 = psi_init, psi_{r+1} = A_r psi_r,
+    formed by the library (spinsim_range_entering_state: FP64, in range
+    order, renormalised after each range as every written state is)."""
+    from . import spinsim as S
+    psi_init = np.asarray(psi_init, dtype=np.complex128)
+    spin_x2 = psi_init.shape[0] - 1
+    out = []
+    for r in range(len(aggs)):
+        st, psi = S.spinsim_range_entering_state(spin_x2, aggs, r, psi_init)
+        if st != S.OK:
+            raise S.SpinsimError(st, "spinsim_range_entering_state")
+        out.append(psi)
     return out
 
 

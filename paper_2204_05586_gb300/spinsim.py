@@ -37,7 +37,8 @@ class spinsim_config(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("precision", ctypes.c_int32), ("rotating_frame", ctypes.c_int32),
                 ("trotter_squares", ctypes.c_int32), ("lanes_per_sample", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("mem_budget", ctypes.c_int64), ("profile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+                ("mem_budget", ctypes.c_int64), ("profile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("chain_precision", ctypes.c_int32), ("reserved_cfg", ctypes.c_int32)]
 
 
 class spinsim_field(ctypes.Structure):
@@ -74,9 +75,17 @@ class spinsim_launch_info(ctypes.Structure):
                 ("chain_ms", ctypes.c_double)]
 
 
+class spinsim_memory_info(ctypes.Structure):
+    _fields_ = [("budget", ctypes.c_int64), ("held", ctypes.c_int64), ("peak_held", ctypes.c_int64),
+                ("arena", ctypes.c_int64), ("pool", ctypes.c_int64), ("pool_in_use", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("in_flight", ctypes.c_int64)]
+
+
 EXPORTED = ("spinsim_config_default", "spinsim_create", "spinsim_destroy", "spinsim_counts", "spinsim_footprint",
-            "spinsim_simulate", "spinsim_submit", "spinsim_poll", "spinsim_last_launch", "spinsim_status_string",
-            "spinsim_simulate_static", "spinsim_range_begin", "spinsim_range_finish")
+            "spinsim_simulate", "spinsim_submit", "spinsim_poll", "spinsim_poll_any", "spinsim_memory",
+            "spinsim_last_launch", "spinsim_status_string",
+            "spinsim_simulate_static", "spinsim_range_begin", "spinsim_range_finish",
+            "spinsim_range_entering_state")
 
 _lib = None
 _lock = threading.Lock()
@@ -110,12 +119,17 @@ def load(build_if_missing: bool = True):
                                        ctypes.c_void_p]
         L.spinsim_submit.argtypes = [ctypes.c_void_p, P(spinsim_request), P(spinsim_result), P(ctypes.c_int64)]
         L.spinsim_poll.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32]
+        L.spinsim_poll_any.argtypes = [ctypes.c_void_p, P(ctypes.c_int64), ctypes.c_int64, ctypes.c_int32,
+                                       P(ctypes.c_int64)]
+        L.spinsim_memory.argtypes = [ctypes.c_void_p, P(spinsim_memory_info)]
         L.spinsim_last_launch.argtypes = [ctypes.c_void_p, P(spinsim_launch_info)]
         L.spinsim_simulate_static.argtypes = [P(spinsim_config), P(spinsim_request), P(spinsim_result),
                                               ctypes.c_void_p]
         L.spinsim_range_begin.argtypes = [ctypes.c_void_p, P(spinsim_request), P(spinsim_result),
                                           P(ctypes.c_double), ctypes.c_void_p]
         L.spinsim_range_finish.argtypes = [ctypes.c_void_p, P(ctypes.c_double), ctypes.c_void_p]
+        L.spinsim_range_entering_state.argtypes = [ctypes.c_int32, P(ctypes.c_double), ctypes.c_int32,
+                                                   P(ctypes.c_double), P(ctypes.c_double)]
         L.spinsim_status_string.argtypes = [ctypes.c_int]
         L.spinsim_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -183,6 +197,22 @@ def spinsim_range_finish(h, psi_in, stream: int = 0) -> int:
     return load().spinsim_range_finish(h, buf, stream)
 
 
+def spinsim_range_entering_state(spin_x2: int, aggs, rank: int, psi_init):
+    """Returns (status, psi) with psi the complex128 [N] state entering range
+    `rank` from the ranges' propagators aggs[0 .. rank-1] (complex [N, N])."""
+    n = spin_x2 + 1
+    a = np.ascontiguousarray(np.asarray(aggs[:rank], dtype=np.complex128).reshape(-1)).view(np.float64) \
+        if rank > 0 else np.zeros(2, np.float64)
+    p = np.ascontiguousarray(np.asarray(psi_init, dtype=np.complex128)).view(np.float64)
+    if p.size != 2 * n:
+        return E_ARG, None
+    out = np.zeros(2 * n, np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = load().spinsim_range_entering_state(spin_x2, a.ctypes.data_as(dp), rank, p.ctypes.data_as(dp),
+                                             out.ctypes.data_as(dp))
+    return st, out.view(np.complex128)
+
+
 def spinsim_submit(h, req: spinsim_request, res: spinsim_result):
     t = ctypes.c_int64()
     st = load().spinsim_submit(h, ctypes.byref(req), ctypes.byref(res), ctypes.byref(t))
@@ -191,6 +221,22 @@ def spinsim_submit(h, req: spinsim_request, res: spinsim_result):
 
 def spinsim_poll(h, ticket: int, wait_us: int = 0) -> int:
     return load().spinsim_poll(h, ticket, wait_us)
+
+
+def spinsim_poll_any(h, buf, wait_us: int = 0):
+    """buf: a ctypes c_int64 array receiving completed tickets.
+    Returns (status, number written)."""
+    n = ctypes.c_int64()
+    st = load().spinsim_poll_any(h, buf, len(buf), wait_us, ctypes.byref(n))
+    return st, n.value
+
+
+def spinsim_memory(h) -> dict:
+    info = spinsim_memory_info()
+    st = load().spinsim_memory(h, ctypes.byref(info))
+    if st != OK:
+        raise SpinsimError(st, "spinsim_memory")
+    return {f: getattr(info, f) for f, _ in spinsim_memory_info._fields_}
 
 
 def spinsim_last_launch(h) -> spinsim_launch_info:
@@ -245,7 +291,8 @@ def make_request(req: dict) -> spinsim_request:
 
 
 def make_config(precision=PREC_FP32_BULK, method=METHOD_CF4, rotating_frame=True, tau=-1, lanes=0, block=0,
-                use_graphs=False, device=0, mem_budget=0, profile=False, blocks_per_sm=0) -> spinsim_config:
+                use_graphs=False, device=0, mem_budget=0, profile=False, blocks_per_sm=0,
+                chain_fp32=False) -> spinsim_config:
     c = spinsim_config()
     spinsim_config_default(c)
     c.precision, c.method, c.rotating_frame, c.trotter_squares = precision, method, int(bool(rotating_frame)), tau
@@ -253,6 +300,7 @@ def make_config(precision=PREC_FP32_BULK, method=METHOD_CF4, rotating_frame=True
     c.mem_budget = mem_budget
     c.profile = int(bool(profile))
     c.blocks_per_sm = blocks_per_sm
+    c.chain_precision = 1 if chain_fp32 else 0
     return c
 
 
@@ -292,19 +340,43 @@ class Simulator:
             raise SpinsimError(st, "spinsim_counts")
         return K, L
 
-    def allocate(self, reqs, want_spin=True, want_ops=False, device="cuda", pin_memory=False):
+    def allocate(self, reqs, want_spin=True, want_ops=False, device="cuda", pin_memory=False, one_buffer=False):
+        """Output buffers per request.  With one_buffer, every buffer is a view
+        of one allocation (each piece 256-byte aligned), e.g. one pinned host
+        block for a large batch instead of thousands of small ones."""
         import torch
-        outs = []
+        shapes = []
         for q in reqs:
             st, K, _ = spinsim_counts(make_request(q))
             K = max(K, 0)
             n = 2 if q["spin_x2"] == 1 else 3
-            kw = dict(dtype=torch.float64, device=device)
-            if device == "cpu":
-                kw["pin_memory"] = pin_memory
-            o = {"states": torch.empty((max(K, 1), n, 2), **kw)}
-            o["spin"] = torch.empty((max(K, 1), 3), **kw) if want_spin else None
-            o["ops"] = torch.empty((max(K, 1), n, n, 2), **kw) if want_ops else None
+            shapes.append((K, n))
+        kw = dict(dtype=torch.float64, device=device)
+        if device == "cpu":
+            kw["pin_memory"] = pin_memory
+        if one_buffer:
+            def pad(x):
+                return -(-x // 32) * 32
+            sizes = [pad(max(K, 1) * n * 2) + (pad(max(K, 1) * 3) if want_spin else 0) +
+                     (pad(max(K, 1) * n * n * 2) if want_ops else 0) for K, n in shapes]
+            flat = torch.empty(sum(sizes), **kw)
+            at = [0]
+
+            def take(shape):
+                numel = 1
+                for d in shape:
+                    numel *= d
+                v = flat[at[0]:at[0] + numel].view(shape)
+                at[0] += pad(numel)
+                return v
+        else:
+            def take(shape):
+                return torch.empty(shape, **kw)
+        outs = []
+        for K, n in shapes:
+            o = {"states": take((max(K, 1), n, 2))}
+            o["spin"] = take((max(K, 1), 3)) if want_spin else None
+            o["ops"] = take((max(K, 1), n, n, 2)) if want_ops else None
             o["K"] = K
             outs.append(o)
         return outs

@@ -87,6 +87,30 @@ def test_entering_states_are_the_ordered_products():
     assert np.allclose(psis[3], mats[2] @ mats[1] @ mats[0] @ psi0)   # later ranges on the left
 
 
+def test_entering_state_entry_point():
+    """spinsim_range_entering_state (host arithmetic in the library, no GPU):
+    the ordered products renormalised after each range, both spins, and its
+    argument checks."""
+    from paper_2204_05586_gb300 import spinsim as S
+    rng = np.random.default_rng(9)
+    for n in (2, 3):
+        mats = [1.01 * np.linalg.qr(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))[0] for _ in range(3)]
+        psi0 = W.random_state(n, rng)
+        psi = psi0.copy()
+        for r in range(4):
+            st, got = S.spinsim_range_entering_state(n - 1, mats, r, psi0)
+            assert st == S.OK
+            assert np.abs(got - psi).max() < 1e-14 and abs(np.linalg.norm(got) - 1) < 1e-15
+            if r < 3:
+                psi = mats[r] @ psi
+                psi = psi / np.linalg.norm(psi)      # the 1.01 scale is taken out at every range
+    one = [np.eye(3, dtype=np.complex128)]
+    assert S.spinsim_range_entering_state(3, one, 1, W.UP_ONE)[0] == S.E_ARG
+    assert S.spinsim_range_entering_state(2, one, -1, W.UP_ONE)[0] == S.E_ARG
+    assert S.spinsim_range_entering_state(2, one, 1, 1.1 * W.UP_ONE)[0] == S.E_NORM
+    assert S.spinsim_range_entering_state(2, [np.full((3, 3), np.nan)], 1, W.UP_ONE)[0] == S.E_ARG
+
+
 def test_split_equals_unsplit_in_one_process(oracle_mod):
     """The split with an in-process exchange: every range's states equal the
     unsplit oracle run (spin-one and spin-half, 1 to 4 ranges)."""
