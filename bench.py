@@ -289,9 +289,14 @@ def measure_batch(args, reqs, prec, dev, local, world, tag):
     sim = S.Simulator(precision=prec, tau=args.tau, profile=True, device=local, use_graphs=True)
     outs = sim.allocate(reqs, device=dev, one_buffer=True)
     stream = torch.cuda.current_stream()
+    raw_stream = stream.cuda_stream
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    # the requests marshalled once: every timed step is one spinsim_simulate call
+    req_arr = (S.spinsim_request * len(reqs))(*[S.make_request(q) for q in reqs])
+    res_dev = sim.results_struct(outs)
     for _ in range(args.warmup):
-        sim.simulate(reqs, outs=outs, sync=False)
+        if S.spinsim_simulate(sim.handle, req_arr, res_dev, raw_stream) != S.OK:
+            raise RuntimeError("spinsim_simulate failed in the warm-up")
     torch.cuda.synchronize()
     # the squarings the automatic choice gave each request (they can differ per request)
     taus = [v["trotter_squares"] for v in sim.simulate(reqs, outs=outs)]
@@ -307,7 +312,8 @@ def measure_batch(args, reqs, prec, dev, local, world, tag):
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        sim.simulate(reqs, outs=outs, sync=False)
+        if S.spinsim_simulate(sim.handle, req_arr, res_dev, raw_stream) != S.OK:
+            raise RuntimeError("spinsim_simulate failed in the timed loop")
         ev[i][1].record(stream)
         li = sim.last_launch()          # reads the library's kernel events (waits for them)
         integ_ms.append(li["integrate_ms"])
@@ -357,59 +363,86 @@ def measure_batch(args, reqs, prec, dev, local, world, tag):
     chain_roofline["output_bytes"] = out_bytes
     chain_roofline["output_gbs"] = round(out_bytes / (mean_chain / 1e3) / 1e9, 1)
 
-    # ---- end to end through the C ABI with pinned host buffers: the request
-    # structs are marshalled once, each step is one spinsim_simulate call
-    # (H2D of the parameter tables, kernels, D2H of states and <J>)
-    outs_h = sim.allocate(reqs, device="cpu", pin_memory=True, one_buffer=True)
-    sim.simulate(reqs, outs=outs_h, sync=True)
-    req_arr = (S.spinsim_request * len(reqs))(*[S.make_request(q) for q in reqs])
-    res_h = sim.results_struct(outs_h)
-    raw_stream = stream.cuda_stream
-    e2e_steps = max(3, min(args.steps, 200))
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        if S.spinsim_simulate(sim.handle, req_arr, res_h, raw_stream) != S.OK:
-            raise RuntimeError("spinsim_simulate failed in the end-to-end loop")
-        stream.synchronize()
-    e2e_serial_s = barrier_max(time.perf_counter() - t0, world)
-    li = sim.last_launch()
-    # double-buffered, as a throughput user would call it: two handles on two
-    # streams with their own pinned host buffers, each pass still one
-    # spinsim_simulate call with its own parameter upload and copy-back; a
-    # buffer is reused only after its previous pass has finished, so pass
-    # i + 1's kernels overlap pass i's copy-back
-    sim_b = S.Simulator(precision=prec, tau=args.tau, device=local, use_graphs=True)
-    streams = [stream, torch.cuda.Stream(device=dev)]
-    outs_b = sim_b.allocate(reqs, device="cpu", pin_memory=True, one_buffer=True)
-    sim_b.simulate(reqs, outs=outs_b, stream=streams[1], sync=True)
-    pipe = [(sim.handle, res_h), (sim_b.handle, sim_b.results_struct(outs_b))]
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    for i in range(e2e_steps):
-        h, r = pipe[i % 2]
-        st = streams[i % 2]
-        st.synchronize()                      # this buffer's previous pass is complete
-        if S.spinsim_simulate(h, req_arr, r, st.cuda_stream) != S.OK:
-            raise RuntimeError("spinsim_simulate failed in the end-to-end loop")
-    for st in streams:
-        st.synchronize()
-    e2e_s = barrier_max(time.perf_counter() - t0, world)
-    e2e = {"value": all_steps * e2e_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(li["h2d_bytes"]), "d2h_bytes_per_step": int(li["d2h_bytes"]),
-           "steps": e2e_steps,
-           "calling": "two handles on two streams, pinned host buffers; each pass one spinsim_simulate call "
-                      "(parameters in, states and <J> out), a buffer reused after its pass completes",
-           "serial_value": all_steps * e2e_steps / e2e_serial_s,
-           "serial_calling": "one handle, a wait after every call"}
-    sim_b.close()
-    del outs_b, outs_h
+    # ---- end to end through the C ABI with pinned host buffers (e2e_measure)
     sim.close()
+    e2e = e2e_measure(args, reqs, prec, dev, local, world, all_steps)
     return {"value": value, "ms_per_step": ms_per_step, "roofline": roofline, "chain_roofline": chain_roofline,
             "e2e": e2e, "gpu_launches": launches, "wall_s_timed_loop": wall, "clocks": clk, "taus": taus,
             "outs": outs, "steps_per_pass": steps_per_pass}
+
+
+def e2e_measure(args, reqs, prec, dev, local, world, all_steps):
+    """The metric end to end through spinsim_simulate with pinned host
+    buffers: every step one call that takes new parameters (two parameter
+    sets alternate, so each call validates the requests, fills and uploads
+    the parameter tables), runs the kernels and delivers states and <J> to
+    host memory.  Timed one call at a time (serial) and double-buffered (two
+    handles on two streams, a buffer reused only after its previous pass
+    completed), for the two ways results reach host memory: staged in device
+    memory and copied back, and written directly by the kernels into the
+    mapped pinned buffers (direct_host_outputs).  The faster double-buffered
+    form is the line's e2e value; all four are reported."""
+    import copy
+
+    import torch
+
+    from paper_2204_05586_gb300 import spinsim as S
+
+    alt = copy.deepcopy(reqs)
+    for q in alt:                        # the second parameter set: another drive phase
+        q["field"]["drive_phase"] = float(q["field"].get("drive_phase", 0.0)) + 0.25
+    sets = [(S.spinsim_request * len(reqs))(*[S.make_request(q) for q in reqs]),
+            (S.spinsim_request * len(alt))(*[S.make_request(q) for q in alt])]
+    e2e_steps = max(3, min(args.steps, 200))
+    streams = [torch.cuda.current_stream(), torch.cuda.Stream(device=dev)]
+    probe = S.Simulator(precision=prec, tau=args.tau, device=local)
+    bufs = [probe.allocate(reqs, device="cpu", pin_memory=True, one_buffer=True) for _ in range(2)]
+    probe.close()
+    out = {}
+    for direct in (False, True):
+        sims = [S.Simulator(precision=prec, tau=args.tau, device=local, use_graphs=True, direct_host_outputs=direct)
+                for _ in range(2)]
+        res = [sm.results_struct(b) for sm, b in zip(sims, bufs)]
+        for j in range(2):               # first calls: tuning, scratch, graph capture
+            for q in sets:
+                if S.spinsim_simulate(sims[j].handle, q, res[j], streams[j].cuda_stream) != S.OK:
+                    raise RuntimeError("spinsim_simulate failed before the end-to-end loop")
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            if S.spinsim_simulate(sims[0].handle, sets[i % 2], res[0], streams[0].cuda_stream) != S.OK:
+                raise RuntimeError("spinsim_simulate failed in the end-to-end loop")
+            streams[0].synchronize()
+        serial_s = barrier_max(time.perf_counter() - t0, world)
+        li = sims[0].last_launch()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            j = i % 2
+            streams[j].synchronize()      # this buffer's previous pass is complete
+            if S.spinsim_simulate(sims[j].handle, sets[(i // 2) % 2], res[j], streams[j].cuda_stream) != S.OK:
+                raise RuntimeError("spinsim_simulate failed in the end-to-end loop")
+        for st in streams:
+            st.synchronize()
+        piped_s = barrier_max(time.perf_counter() - t0, world)
+        out[direct] = {"value": all_steps * e2e_steps / piped_s, "serial_value": all_steps * e2e_steps / serial_s,
+                       "h2d": int(li["h2d_bytes"]), "d2h": int(li["d2h_bytes"])}
+        for sm in sims:
+            sm.close()
+    best = True if out[True]["value"] >= out[False]["value"] else False
+    b = out[best]
+    return {"value": b["value"], "unit": UNIT, "h2d_bytes_per_step": b["h2d"], "d2h_bytes_per_step": b["d2h"],
+            "steps": e2e_steps,
+            "calling": ("each step one spinsim_simulate call with new parameters (two sets alternate: validation, "
+                        "parameter tables filled and uploaded), states and <J> into pinned host buffers; two "
+                        "handles on two streams, a buffer reused after its pass completes; results "
+                        + ("written directly into the mapped pinned buffers by the kernels (direct_host_outputs = 1)"
+                           if best else "staged in device memory and copied back")),
+            "serial_value": b["serial_value"], "serial_calling": "one handle, a wait after every call",
+            "staged": {"value": out[False]["value"], "serial_value": out[False]["serial_value"]},
+            "direct_host_outputs": {"value": out[True]["value"], "serial_value": out[True]["serial_value"]}}
 
 
 def fp64_plain(reqs, local, dev, ref_states, value_fp32_per_gpu, tau=-1):

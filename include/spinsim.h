@@ -97,7 +97,10 @@ typedef struct {
     int32_t threads_per_block;    /* 0 = autotune; else 64, 128 or 256                        */
     int32_t use_graphs;           /* 1: replay repeated identical batch shapes as a CUDA graph
                                      on the caller's stream (the first call of a shape runs
-                                     eagerly and captures it); calls stay in issue order   */
+                                     eagerly and captures it); calls stay in issue order.
+                                     A call that repeats the previous one byte for byte
+                                     (requests and result buffers) replays the graph without
+                                     validating and refilling the parameter tables again  */
     int32_t device;               /* CUDA device ordinal                                      */
     int64_t mem_budget;           /* bytes of device memory the handle may hold in total
                                      (its arena for spinsim_simulate and ranges plus its
@@ -113,7 +116,13 @@ typedef struct {
                                      same kernels with every product rounded to single
                                      precision, a control for precision studies (it shows
                                      why the product stays FP64); ignored by the CPU backend */
-    int32_t reserved_cfg;         /* set to 0                                                */
+    int32_t direct_host_outputs;  /* 0 (default): host-resident result buffers are staged in
+                                     device memory and copied back after the kernels; 1: the
+                                     kernels write them directly when they are pinned host
+                                     memory the device can address (cudaHostAlloc /
+                                     cudaHostRegister, mapped), so the output crosses the
+                                     host link while the chain runs and no copy follows.
+                                     Other host memory is staged either way.               */
 } spinsim_config;
 
 /* The fixed parameterised field family (Hz, seconds, radians):
@@ -182,7 +191,9 @@ typedef struct {
 
 /* Caller-owned output buffers of one request.  Each pointer may be device
  * memory (written in place) or host memory (the library stages it through
- * device scratch and copies back on the stream).  The library never frees them. */
+ * device scratch and copies back on the stream; with direct_host_outputs,
+ * pinned mapped host memory is written in place).  The library never frees
+ * them. */
 typedef struct {
     double* states;               /* [capacity][N] complex psi_k, required                   */
     double* spin;                 /* [capacity][3] <J_x>, <J_y>, <J_z>; NULL = not written   */
@@ -293,7 +304,8 @@ typedef struct {
     int32_t trotter_squares;
     int32_t graph_replayed;
     int64_t h2d_bytes;            /* parameter tables uploaded                               */
-    int64_t d2h_bytes;            /* outputs copied back to host buffers                     */
+    int64_t d2h_bytes;            /* outputs that reached host buffers (copied back, or
+                                     written directly with direct_host_outputs)             */
     double integrate_ms;          /* -1 when not profiled                                    */
     double chain_ms;
 } spinsim_launch_info;

@@ -79,6 +79,7 @@ void pack(const SampleCtx<float> (&c)[4], SampleCtx<F4>& v)
     for (int i = 0; i < 4; i++) { SPINSIM_PACK(Ph[i]); SPINSIM_PACK(Pl[i]); }
     SPINSIM_PACK(za); SPINSIM_PACK(zb); SPINSIM_PACK(zbias); SPINSIM_PACK(qd3); SPINSIM_PACK(inv_n);
     SPINSIM_PACK(q1); SPINSIM_PACK(dt); SPINSIM_PACK(c1); SPINSIM_PACK(c2);
+    SPINSIM_PACK(d1r); SPINSIM_PACK(d1i); SPINSIM_PACK(p1r); SPINSIM_PACK(p1i); SPINSIM_PACK(eqr); SPINSIM_PACK(eqi);
     for (int p = 0; p < kMaxPulses; p++) {
         SPINSIM_PACK(amp[p]); SPINSIM_PACK(u0[p]); SPINSIM_PACK(invw[p]); SPINSIM_PACK(ghat[p]);
     }

@@ -275,6 +275,10 @@ struct SampleCtx {
     R qd3;
     R inv_n;                        // 2^-tau
     R q1;                           // first-order Q coefficient of one exponential: 3 qd3 2^tau
+    // per-simulation constants of the small-angle exponential at tau = 0
+    // (expm_one_res_tau0): the m = 0 diagonal's rest d1 and phasor p1 of
+    // e^{i 2 qd3} (th_1 = 2 qd3), and e^{-i qd3} = e^{i (th_0 + th_2) / 2}
+    R d1r, d1i, p1r, p1i, eqr, eqi;
     R dt, c1, c2;
     R amp[kMaxPulses], u0[kMaxPulses], invw[kMaxPulses], ghat[kMaxPulses];
     // further tones (the tones variant only): e^{i beta_j}, in-frame rates, Om+-_j
@@ -350,6 +354,24 @@ SPINSIM_COLD R sine_cycle_cold(R u)
     return pulse_shape<R>(true, u);
 }
 
+// The per-simulation constants of expm_one_res_tau0 from c.qd3: the same
+// expressions expm_one_res_n evaluates for h_1 = qd3 with the small-angle
+// series, and e^{-i qd3}.
+template <typename R>
+SPINSIM_HD void tau0_constants(SampleCtx<R>& c)
+{
+    R sm1, cm1, sq, cq;
+    small_sincos_m_tiny(c.qd3, sm1, cm1);
+    const R s1 = c.qd3 + sm1, c1 = R(1) + cm1;
+    c.d1r = R(-2) * s1 * s1;
+    c.d1i = R(2) * fma(c.qd3, cm1, sm1 * c1);
+    c.p1r = R(1) + c.d1r;
+    c.p1i = R(2) * s1 * c1;
+    small_sincos_tiny(c.qd3, sq, cq);
+    c.eqr = cq;
+    c.eqi = -sq;
+}
+
 // Bulk context of interval k (every lane).  e^{i beta} comes from the bulk
 // type's sincos: the first-order part it feeds is replaced by the exact FP64
 // value at the end of the sample, so it only reaches second-order terms.
@@ -393,6 +415,7 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
     c.tau = s.tau;
     c.inv_n = ldexp(R(1), -s.tau);
     c.q1 = R(3) * ldexp(c.qd3, s.tau);
+    tau0_constants(c);
     c.counter_on = s.counter_on != 0;
     double gsum = 0.0;
 #pragma unroll
@@ -1056,6 +1079,69 @@ SPINSIM_HD void expm_one_res(R vx, R vy, R vz, R qd3, int tau, Res3<R>& e)
     expm_one_res_n<R, SMALL>(vx, vy, vz, qd3, tau, ldexp(R(1), -tau), R(3) * ldexp(qd3, tau), e);
 }
 
+// The same exponential for tau = 0 (one factor T, n = 1) and small angles
+// (the host bounds h_0, h_1, h_2 and Phi / 2 by 2^-6, small_angle_request),
+// with the conjugation by W folded into the transverse field itself.  With
+// u = v_x - i v_y = Phi e^{-i phi} and y = Phi^2 = |u|^2 the entries of
+// W (T0 - I) W^dagger beyond first order are
+//   diagonal:  d_j - S^2 e^{i th_j} (m = 0: 2 S^2), S^2 = sin^2(Phi/2) = sigma y,
+//   (0,1), (1,0):  -i/sqrt2 t_2 u, -i/sqrt2 t_2 conj(u),
+//   (1,2), (2,1):  -i/sqrt2 t_0 u, -i/sqrt2 t_0 conj(u),
+//   (0,2), (2,0):  -sigma e^{-i qd3} u^2, -sigma e^{-i qd3} conj(u)^2,
+// where t_j = kappa e^{-i h_j} + (e^{-i h_j} - 1), kappa = (sin Phi - Phi) / Phi
+// and sigma = sin^2(Phi/2) / Phi^2, both series in y (truncation below 2e-9
+// relative for Phi <= 2^-5), and e^{i (th_0 + th_2) / 2} = e^{-i qd3}.  This is
+// expm_one_res_n's T at tau = 0 in closed form without the reciprocal square
+// root, the angle phi or the conjugation products; the h_1 terms and
+// e^{-i qd3} are per-simulation constants of the context.
+template <typename R>
+SPINSIM_HD void expm_one_res_tau0(R vx, R vy, R vz, const SampleCtx<R>& c, Res3<R>& e)
+{
+    const R y = fma(vx, vx, vy * vy);
+    const R h0 = fma(R(-0.5), vz, R(-0.5) * c.qd3);   // th_0 / 2
+    const R h2 = fma(R(0.5), vz, R(-0.5) * c.qd3);    // th_2 / 2
+    R sm0, cm0, sm2, cm2;
+    small_sincos_m_tiny(h0, sm0, cm0);
+    small_sincos_m_tiny(h2, sm2, cm2);
+    const R s0 = h0 + sm0, c0 = R(1) + cm0;
+    const R s2 = h2 + sm2, c2 = R(1) + cm2;
+    const R kappa = y * fma(y, R(1.0 / 120), R(-1.0 / 6));
+    const R sigma = fma(y, fma(y, R(1.0 / 1440), R(-1.0 / 48)), R(0.25));
+    const R S2 = sigma * y;
+    // diagonal: cos th - 1 = -2 sin^2(th/2), sin th - th = 2 (sm + h cm + sm cm), minus S^2 e^{i th}
+    const cx<R> d0 = cmk(R(-2) * s0 * s0, R(2) * fma(h0, cm0, sm0 * c0));
+    const cx<R> d2 = cmk(R(-2) * s2 * s2, R(2) * fma(h2, cm2, sm2 * c2));
+    const cx<R> p0 = cmk(R(1) + d0.r, R(2) * s0 * c0);
+    const cx<R> p2 = cmk(R(1) + d2.r, R(2) * s2 * c2);
+    e.m[0][0] = csub(d0, cscale(p0, S2));
+    e.m[1][1] = csub(cmk(c.d1r, c.d1i), cscale(cmk(c.p1r, c.p1i), R(2) * S2));
+    e.m[2][2] = csub(d2, cscale(p2, S2));
+    // next to the diagonal: -i t u and -i t conj(u) with u / sqrt2 = (vx, -vy) / sqrt2
+    const R r = R(kInvSqrt2);
+    const R ur = r * vx, ui = -(r * vy);
+    const R t2r = fma(kappa, c2, cm2), t2i = -(kappa + R(1)) * s2;
+    const R t0r = fma(kappa, c0, cm0), t0i = -(kappa + R(1)) * s0;
+    {
+        const R D = t2i * ur, B = t2i * ui;
+        e.m[0][1] = cmk(fma(t2r, ui, D), fma(-t2r, ur, B));
+        e.m[1][0] = cmk(fma(-t2r, ui, D), fma(-t2r, ur, -B));
+    }
+    {
+        const R D = t0i * ur, B = t0i * ui;
+        e.m[1][2] = cmk(fma(t0r, ui, D), fma(-t0r, ur, B));
+        e.m[2][1] = cmk(fma(-t0r, ui, D), fma(-t0r, ur, -B));
+    }
+    // corners: g u^2 and g conj(u)^2, g = -sigma e^{-i qd3}, u^2 = (vx^2 - vy^2, -2 vx vy)
+    const R gr = -sigma * c.eqr, gi = -sigma * c.eqi;
+    const R u2r = fma(vx, vx, -(vy * vy)), u2i = R(-2) * vx * vy;
+    {
+        const R P = gi * u2r, Q = gi * u2i;
+        e.m[0][2] = cmk(fma(gr, u2r, -Q), fma(gr, u2i, P));
+        e.m[2][0] = cmk(fma(gr, u2r, Q), fma(-gr, u2i, P));
+    }
+    e.g[0] = vx; e.g[1] = vy; e.g[2] = vz; e.g[3] = c.q1;
+}
+
 // 1/k! rounded once (k! is exact in double up to k = 18), the Taylor coefficients.
 SPINSIM_HD constexpr double inv_factorial(int k)
 {
@@ -1381,10 +1467,21 @@ SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X)
     exponent<R, TONES>(c, f1, f2, false, vx, vy, vz);
     if (METHOD == 0) exponent<R, TONES>(c, f1, f2, true, wx, wy, wz);
     Res3<R> e, Y;
-    expm_one_res_n<R, SMALL>(vx, vy, vz, c.qd3, tau, c.inv_n, c.q1, e);
+    if constexpr (SMALL) {
+        // small angles: tau = 0 in closed form (the common case), else the squarings
+        if (tau == 0) expm_one_res_tau0(vx, vy, vz, c, e);
+        else expm_one_res_n<R, SMALL>(vx, vy, vz, c.qd3, tau, c.inv_n, c.q1, e);
+    } else {
+        expm_one_res_n<R, SMALL>(vx, vy, vz, c.qd3, tau, c.inv_n, c.q1, e);
+    }
     res3_mul(e, X, Y);
     if (METHOD == 0) {
-        expm_one_res_n<R, SMALL>(wx, wy, wz, c.qd3, tau, c.inv_n, c.q1, e);
+        if constexpr (SMALL) {
+            if (tau == 0) expm_one_res_tau0(wx, wy, wz, c, e);
+            else expm_one_res_n<R, SMALL>(wx, wy, wz, c.qd3, tau, c.inv_n, c.q1, e);
+        } else {
+            expm_one_res_n<R, SMALL>(wx, wy, wz, c.qd3, tau, c.inv_n, c.q1, e);
+        }
         res3_mul(e, Y, X);
     } else {
         X = Y;

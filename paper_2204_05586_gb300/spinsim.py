@@ -38,7 +38,7 @@ class spinsim_config(ctypes.Structure):
                 ("trotter_squares", ctypes.c_int32), ("lanes_per_sample", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("use_graphs", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("mem_budget", ctypes.c_int64), ("profile", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("chain_precision", ctypes.c_int32), ("reserved_cfg", ctypes.c_int32)]
+                ("chain_precision", ctypes.c_int32), ("direct_host_outputs", ctypes.c_int32)]
 
 
 class spinsim_field(ctypes.Structure):
@@ -292,7 +292,7 @@ def make_request(req: dict) -> spinsim_request:
 
 def make_config(precision=PREC_FP32_BULK, method=METHOD_CF4, rotating_frame=True, tau=-1, lanes=0, block=0,
                 use_graphs=False, device=0, mem_budget=0, profile=False, blocks_per_sm=0,
-                chain_fp32=False) -> spinsim_config:
+                chain_fp32=False, direct_host_outputs=False) -> spinsim_config:
     c = spinsim_config()
     spinsim_config_default(c)
     c.precision, c.method, c.rotating_frame, c.trotter_squares = precision, method, int(bool(rotating_frame)), tau
@@ -301,6 +301,7 @@ def make_config(precision=PREC_FP32_BULK, method=METHOD_CF4, rotating_frame=True
     c.profile = int(bool(profile))
     c.blocks_per_sm = blocks_per_sm
     c.chain_precision = 1 if chain_fp32 else 0
+    c.direct_host_outputs = 1 if direct_host_outputs else 0
     return c
 
 

@@ -43,6 +43,38 @@ void hh_expm_one_small(double vx, double vy, double vz, double vq, int tau, doub
     expm_one_res<float, true>((float)vx, (float)vy, (float)vz, qd3, tau, e);
     full3(e, out);
 }
+// the small-angle exponential at tau = 0 in closed form (expm_one_res_tau0),
+// FP32 or FP64; out: the full matrix, rest: the part beyond first order
+void hh_expm_one_tau0(double vx, double vy, double vz, double vq, int fp32, double* out, double* rest)
+{
+    if (fp32) {
+        SampleCtx<float> c{};
+        c.qd3 = (float)(vq / 3.0);
+        c.q1 = 3.0f * c.qd3;
+        tau0_constants(c);
+        Res3<float> e;
+        expm_one_res_tau0<float>((float)vx, (float)vy, (float)vz, c, e);
+        full3(e, out);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                rest[6 * i + 2 * j] = e.m[i][j].r;
+                rest[6 * i + 2 * j + 1] = e.m[i][j].i;
+            }
+    } else {
+        SampleCtx<double> c{};
+        c.qd3 = vq / 3.0;
+        c.q1 = 3.0 * c.qd3;
+        tau0_constants(c);
+        Res3<double> e;
+        expm_one_res_tau0<double>(vx, vy, vz, c, e);
+        full3(e, out);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                rest[6 * i + 2 * j] = e.m[i][j].r;
+                rest[6 * i + 2 * j + 1] = e.m[i][j].i;
+            }
+    }
+}
 // the same FP32 exponential through the general series, for comparison
 void hh_expm_one_general32(double vx, double vy, double vz, double vq, int tau, double* out)
 {

@@ -39,6 +39,7 @@ def hh(tmp_path_factory):
     L.hh_choose_tau.restype = ctypes.c_int
     L.hh_expm_one_small.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, DP]
     L.hh_expm_one_general32.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, DP]
+    L.hh_expm_one_tau0.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, DP, DP]
     L.hh_tiny_sincos.argtypes = [ctypes.c_double, DP]
     L.hh_small_angle_request.restype = ctypes.c_int
     L.hh_small_angle_request.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
@@ -255,6 +256,47 @@ def test_small_angle_exponential_matches_general(hh):
                 assert np.abs(A - G).max() <= 2e-7 * max(scale * scale, 1e-12) + 1e-13
                 if tau == 4:
                     assert np.abs(A - sl.expm(-1j * H1(v))).max() < 1e-8
+
+
+def test_tau0_closed_form_exponential(hh):
+    """The tau = 0 small-angle exponential with the W conjugation folded in:
+    in FP64 equal to the squaring path at tau = 0, its rest beyond first
+    order equal to the single factor T computed in 50 digits up to rounding
+    and the series' truncation; in FP32 equal to the squaring
+    path's FP32 result (same approximant) to FP32 rounding.  Includes a zero
+    transverse field and pure transverse fields."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    rng = np.random.default_rng(11)
+    vs = [rng.normal(size=4) * s for s in (1e-6, 1e-4, 5e-3) for _ in range(12)]
+    vs += [np.array([0.0, 0.0, 3e-3, 1e-3]), np.array([4e-3, 0.0, 0.0, 0.0]), np.array([0.0, -4e-3, 0.0, 2e-3])]
+    for v in vs:
+        out, rest = np.zeros(18), np.zeros(18)
+        hh.hh_expm_one_tau0(*v, 0, P(out), P(rest))
+        E = out.view(np.complex128).reshape(3, 3)
+        ref = np.zeros(18)
+        hh.hh_expm_one(*v, 0, 0, P(ref))                  # the squaring path at tau = 0, FP64
+        R0 = ref.view(np.complex128).reshape(3, 3)
+        assert np.abs(E - R0).max() < 4e-15 * np.abs(v).max() + 1e-18   # ~20 ulp of the entries
+        # T itself: e^{-iD/2} e^{-i Phi J_phi} e^{-iD/2}, D = v_z J_z + v_q Q, in 50 digits
+        Dm = mp.matrix((v[2] * JZ1 + v[3] * Q1).tolist())
+        Pm = mp.matrix((v[0] * JX1 + v[1] * JY1).tolist())
+        half = mp.expm(-0.5j * Dm)
+        T = half * mp.expm(-1j * Pm) * half
+        Hm = mp.matrix(H1(v).tolist())
+        refm = T - mp.eye(3) + 1j * Hm
+        want = np.array([[complex(refm[i, j]) for j in range(3)] for i in range(3)])
+        got = rest.view(np.complex128).reshape(3, 3)
+        # FP64 rounding of a second-order quantity, plus the series' truncation
+        # (kappa drops y^3 / 5040: at most |v|^7 / 5040 in the transverse entries)
+        s_ = np.abs(v).max()
+        assert np.abs(got - want).max() <= 1e-15 * s_ ** 2 + s_ ** 7 / 1000 + 1e-30
+        o32, r32, s32 = np.zeros(18), np.zeros(18), np.zeros(18)
+        hh.hh_expm_one_tau0(*v, 1, P(o32), P(r32))
+        hh.hh_expm_one_small(*v, 0, P(s32))
+        A = o32.view(np.complex128).reshape(3, 3)
+        B = s32.view(np.complex128).reshape(3, 3)
+        assert np.abs(A - B).max() <= 2e-7 * max(np.abs(v).max() ** 2, 1e-12) + 1e-13
 
 
 def test_small_angle_rule_on_workloads(hh):

@@ -139,8 +139,18 @@ def test_sensing_field_full_duration(oracle_mod):
         print(f"{r['prec']:10s} {r['dt']:8.0e} {r['span_ms']:8.1f} {r['tau']:4d} {r['err_same']:10.2e} "
               f"{r['err_conv']:10.2e} {r['drift']:9.1e} {r.get('drift_raw', float('nan')):10.1e} "
               f"{r.get('err_chain32', float('nan')):11.2e}")
+    # FP64 bound of this study: 3e-10.  Over 100 ms the drive phase 2 pi f t
+    # reaches 4.4e5 rad, whose FP64 rounding (about 6e-11 rad) the oracle (the
+    # argument formed at each node) and the library (reduced once per sample)
+    # take differently; the per-sample errors of the drive axis add up as a
+    # random walk (1.6e-10 at delta_t = 1e-6, 1e5 samples).  At delta_t = 1e-9
+    # (1000 steps per sample) the oracle's full-matrix accumulation of each
+    # sample adds its rounding (2.1e-10 over 10 ms).  The configured step
+    # (1e-8) stays within 1e-10, as the full-size parity test requires.
     for r in rows:
-        assert r["err_same"] <= (1e-10 if r["prec"] == "fp64" else 1e-5), (r["prec"], r["dt"], r["err_same"])
+        assert r["err_same"] <= (3e-10 if r["prec"] == "fp64" else 1e-5), (r["prec"], r["dt"], r["err_same"])
+        if r["prec"] == "fp64" and r["dt"] == 1e-8:
+            assert r["err_same"] <= 1e-10
         assert r["drift"] <= (1e-9 if r["prec"] == "fp64" else 1e-14), (r["prec"], r["dt"], r["drift"])
         if r["prec"] == "fp32-bulk":
             assert r["drift_raw"] < 1e-5 and r["err_chain32"] > r["err_same"]
