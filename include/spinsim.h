@@ -116,13 +116,14 @@ typedef struct {
                                      same kernels with every product rounded to single
                                      precision, a control for precision studies (it shows
                                      why the product stays FP64); ignored by the CPU backend */
-    int32_t direct_host_outputs;  /* 0 (default): host-resident result buffers are staged in
+    int32_t direct_host_outputs;  /* 0: host-resident result buffers are staged in
                                      device memory and copied back after the kernels; 1: the
                                      kernels write them directly when they are pinned host
                                      memory the device can address (cudaHostAlloc /
                                      cudaHostRegister, mapped), so the output crosses the
-                                     host link while the chain runs and no copy follows.
-                                     Other host memory is staged either way.               */
+                                     host link while the chain runs and no copy follows
+                                     (the default of spinsim_config_default).  Other host
+                                     memory is staged either way.                          */
 } spinsim_config;
 
 /* The fixed parameterised field family (Hz, seconds, radians):
@@ -209,7 +210,8 @@ typedef struct {
 typedef struct spinsim_s* spinsim_handle;
 
 /* Fill *cfg with defaults: CF4, FP32-bulk, rotating frame on, default tau,
- * autotuned launch shape, graphs off, device 0, budget 0 (90% of free). */
+ * autotuned launch shape, graphs off, device 0, budget 0 (90% of free),
+ * FP64 chain, pinned host outputs written directly (direct_host_outputs = 1). */
 int spinsim_config_default(spinsim_config* cfg);
 
 /* Create a handle on cfg->device.  The handle owns device scratch (operator
@@ -379,6 +381,16 @@ int spinsim_range_finish(spinsim_handle h, const double* psi_in, void* stream);
  * values, SPINSIM_E_NORM when psi_init is not normalised to 1e-10. */
 int spinsim_range_entering_state(int32_t spin_x2, const double* aggs, int32_t rank, const double* psi_init,
                                  double* psi_out);
+
+/* The debug build's range checks (a library compiled with -DSPINSIM_BOUNDS,
+ * libspinsim_bounds.so): every checked global-memory index of the kernels
+ * that fell outside its buffer sets a bit of an error word on the device and
+ * the access is skipped (no trap).  This call waits for the device's work,
+ * writes the word of `device` into *word (0: every index was in range; bits
+ * 0-1 integrate kernel, 8-15 chain kernels) and clears it.  The normal
+ * library has no checks: it writes 0 and returns SPINSIM_E_UNSUPPORTED.
+ * The paper has no counterpart: this exists to test the kernels' indexing. */
+int spinsim_debug_bounds(int32_t device, uint64_t* word);
 
 /* Static description of a status code. */
 const char* spinsim_status_string(int status);

@@ -146,5 +146,46 @@ def _build_locked(force: bool, verbose: bool) -> str:
     return LIB
 
 
+BOUNDS_LIB = os.path.join(BUILD, "libspinsim_bounds.so")
+
+
+def build_bounds(force: bool = False) -> str:
+    """The debug library with range checks of the kernels' indices
+    (-DSPINSIM_BOUNDS; bounds.cuh), _build/libspinsim_bounds.so.  Built on
+    demand only (the tests that use it call this), not by build()."""
+    os.makedirs(os.path.join(BUILD, "bounds"), exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            stamp = os.path.join(BUILD, "libspinsim_bounds.sha256")
+            fp = _fingerprint()
+            if not force and os.path.exists(BOUNDS_LIB) and os.path.exists(stamp) and open(stamp).read() == fp:
+                return BOUNDS_LIB
+            exe = nvcc()
+
+            def compile_one(src):
+                obj = os.path.join(BUILD, "bounds", os.path.basename(src)[:-3] + ".o")
+                cmd = [exe, *ARCH, *NVCC_FLAGS, "-DSPINSIM_BOUNDS", "-I", INCLUDE, "-c", src, "-o", obj]
+                r = subprocess.run(cmd, capture_output=True, text=True)
+                if r.returncode != 0:
+                    raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+                return obj
+
+            srcs = _sources()
+            with ThreadPoolExecutor(max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+                objs = list(ex.map(compile_one, srcs))
+            tmp = BOUNDS_LIB + f".tmp{os.getpid()}"
+            r = subprocess.run([exe, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp], capture_output=True,
+                               text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"link of libspinsim_bounds.so failed:\n{r.stdout}\n{r.stderr}")
+            os.replace(tmp, BOUNDS_LIB)
+            with open(stamp, "w") as f:
+                f.write(fp)
+            return BOUNDS_LIB
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))

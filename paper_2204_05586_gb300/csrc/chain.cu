@@ -34,6 +34,7 @@
 // are kept in SU(2) form (alpha, beta) = first column.
 #include <algorithm>
 
+#include "bounds.cuh"
 #include "sample_epilogue.cuh"
 
 namespace spinsim {
@@ -329,7 +330,8 @@ __device__ __forceinline__ void node_up(const ChainArgs& a, int level, int64_t n
         tree_down<N, T, BLOCK>(V, [&](int t) { return (const double*)(S + left_child_slot(t) * D); });
         for (int w = me; w < kFan * SV; w += n) {
             const int child = w / SV, i = w - SV * child;
-            if (local * kFan + child < coff[si + 1] - coff[si])
+            if (local * kFan + child < coff[si + 1] - coff[si] &&
+                SPINSIM_INB(coff[si] + local * kFan + child < a.nodes[level - 1], 10))
                 a.state[level - 1][(coff[si] + local * kFan + child) * SV + i] = V[child * SV + i];
         }
     }
@@ -363,10 +365,11 @@ __global__ void __launch_bounds__(128) chain_up_kernel(ChainArgs a)
         const int64_t k0 = (local * kFan + lane) * run;
         const int64_t k1 = min(k0 + run, s.K);
         const double* U = a.U + s.sample_offset * D;
-        if (k0 < k1) B.load(U + k0 * D);
+        if (SPINSIM_INB(si >= 0 && si < a.n_sims && k0 >= 0, 8) && k0 < k1) B.load(U + k0 * D);
         for (int64_t k = k0 + 1; k < k1; k++) {
             Op<N, T> u, t;
-            u.load(U + k * D);
+            if (SPINSIM_INB(k < s.K, 9)) u.load(U + k * D);
+            else u.identity();
             Op<N, T>::mul(u, B, t);   // later operators multiply from the left
             B = t;
         }
@@ -399,7 +402,8 @@ __global__ void __launch_bounds__(128) chain_up_upper_kernel(ChainArgs a, int le
             const int c = w / D, i = w - D * c;
             const int64_t child = local * kFan + c;
             double v;
-            if (child < n_child) v = a.agg[level - 1][(coff[si] + child) * D + i];
+            if (child < n_child && SPINSIM_INB(coff[si] + child < a.nodes[level - 1], 11))
+                v = a.agg[level - 1][(coff[si] + child) * D + i];
             else v = (N == 3 ? (i == 0 || i == 8 || i == 16) : i == 0) ? 1.0 : 0.0;   // identity
             S[c * D + i] = v;
         }
@@ -439,7 +443,8 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
         if (a.mode == kChainFull && from >= 1) {
             from--;
             const int64_t anc = local >> (5 * from);   // the top node's child on the path
-            if (lane < SV) v[lane] = a.state[from][(a.level_off[(size_t)from * stride + si] + anc) * SV + lane];
+            const int64_t at = a.level_off[(size_t)from * stride + si] + anc;
+            if (lane < SV) v[lane] = SPINSIM_INB(at < a.nodes[from], 12) ? a.state[from][at * SV + lane] : 0.0;
         } else if (lane < SV) {
             v[lane] = s.psi0[lane];
         }
@@ -447,9 +452,11 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
         for (int level = from; level >= 1; level--) {
             const int64_t anc = local >> (5 * level);                         // ancestor at `level`
             const int64_t j = (local >> (5 * (level - 1))) - anc * kFan;     // its child on the path
-            const double* L = a.left[level] + (a.level_off[(size_t)level * stride + si] + anc) * kLeftPerNode * D;
+            const int64_t at = a.level_off[(size_t)level * stride + si] + anc;
+            const double* L = a.left[level] + at * kLeftPerNode * D;
+            const bool in_range = SPINSIM_INB(at < a.nodes[level], 13);
             for (int h = 5; h >= 1; h--) {
-                if (((j >> (h - 1)) & 1) == 0) continue;                    // left child: state unchanged
+                if (((j >> (h - 1)) & 1) == 0 || !in_range) continue;       // left child: state unchanged
                 const int p = (int)(j >> h);
                 cx<T> y = cmk<T>(T(0), T(0));
                 if (lane < N) y = Tree<N, T>::matvec_row(L + (tslot(h, p) - 32) * D, v, lane);
@@ -474,7 +481,8 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
         const double* U = a.U + s.sample_offset * D;
         for (int64_t k = k0; k < k1; k++) {
             Op<N, T> u;
-            u.load(U + k * D);
+            if (SPINSIM_INB(k >= 0 && k < s.K && k - kn < (int64_t)kFan * kMaxRun, 14)) u.load(U + k * D);
+            else u.identity();
             u.apply(psi, nxt);
 #pragma unroll
             for (int i = 0; i < N; i++) psi[i] = nxt[i];
@@ -509,7 +517,8 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
         __syncwarp();
         // the node's span [kn, kn + m): psi_k as N double2 words per sample,
         // <J>_k as 3 doubles per sample (kn is a multiple of 4: whole words)
-        const int64_t m = min((int64_t)kFan * run, s.K - kn);
+        const int64_t m = SPINSIM_INB(run <= kMaxRun && kn + min((int64_t)kFan * run, s.K - kn) <= s.K, 15)
+                              ? min((int64_t)kFan * run, s.K - kn) : 0;
         {
             const double2* src = reinterpret_cast<const double2*>(stage_psi);
             double2* dst = reinterpret_cast<double2*>(s.states + kn * SV);
@@ -596,5 +605,9 @@ cudaError_t launch_chain(int spin_x2, const ChainArgs& a, int n_sm, cudaStream_t
                                   : launch_chain_nt<2, double>(a, n_sm, stream, kernels);
     return cudaErrorInvalidValue;
 }
+
+#ifdef SPINSIM_BOUNDS
+SPINSIM_BOUNDS_READER(bounds_word_chain)
+#endif
 
 }  // namespace spinsim

@@ -5,21 +5,22 @@
 // L integration steps (CF4 by default), taken inside the interval's rotating
 // frame and then moved back to the lab frame (Eq. exit_rotating_frame).
 //
-// Work decomposition (GB300): a persistent grid pulls tiles of consecutive
-// samples from an atomic counter; G = 1, 2, 4 or 8 lanes of a warp share one
-// sample.  The L steps of a sample are always split into the same 2^s
+// Work decomposition (GB300): in a persistent grid every warp pulls tiles of
+// 32 / G consecutive samples from an atomic counter; G = 1, 2, 4 or 8 lanes of
+// the warp share one sample.  The L steps of a sample are always split into the same 2^s
 // segments [q L/2^s, (q+1) L/2^s) (s from L alone: 3 for L >= 128, 2 from 16,
 // 1 from 4, else 0) and reduced by the same binary tree, e.g. for s = 3
 // ((S7 S6)(S5 S4))((S3 S2)(S1 S0)), whichever G is used, so the result is
 // bit-for-bit independent of the launch shape and of which other samples
 // share the launch.  A lane owns 2^s/G consecutive segments -- a complete
 // sub-tree, built as its segments finish with a small stack in shared memory.
-// After the tile, one thread per sample combines the lanes' sub-trees and
+// After the tile, one lane per sample combines the lanes' sub-trees and
 // finishes the operator in FP64: on GB300 an FP64 warp instruction costs the
 // same with 1 or 32 active lanes, so this epilogue runs with every lane on a
-// sample of its own.  Whole waves of tiles use the tuned G; the samples left
+// sample of its own (in bulk tiles, G = 1).  Whole waves of tiles use the tuned G; the samples left
 // after them use one lane per segment, so the last wave ends in segments of a
 // sample's steps.
+#include "bounds.cuh"
 #include "sample_epilogue.cuh"
 
 namespace spinsim {
@@ -41,7 +42,12 @@ __device__ __forceinline__ int find_index(const int64_t* off, int n, int64_t g)
 // thread's canonical sub-tree (log2 of its segment count) and its result.
 constexpr int kSlots = kSegLog2 + 1;
 
-// The body of both integrate kernels (below).
+// The body of both integrate kernels (below).  Each warp works on its own:
+// it pulls a tile of 32 >> lg consecutive samples from the atomic counter,
+// its lanes build their segments' sub-trees, and lanes 0 .. (32 >> lg) - 1
+// then finish one sample each (the FP64 epilogue).  No block barrier: while
+// one warp runs its FP64 epilogue, the others of its SM keep the FP32 pipes
+// busy.
 template <int N, typename R, int METHOD, bool SMALL, bool TONES, bool SU3 = false>
 __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
 {
@@ -50,7 +56,6 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Res* rec = reinterpret_cast<Res*>(smem_raw);                                        // [blockDim][kSlots]
     double2* bg = reinterpret_cast<double2*>(smem_raw + (size_t)blockDim.x * kSlots * sizeof(Res));  // [blockDim]
-    __shared__ unsigned long long s_tile;
 
     // Never touch shared memory beyond what the launch provided.
     unsigned dyn_smem;
@@ -60,36 +65,38 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
     // chain's first kernel may be scheduled as blocks retire (it waits for
     // this grid's results before reading them)
     allow_dependent_launch();
+    const int wl = threadIdx.x & 31;                 // lane in the warp
+    const int w0 = threadIdx.x & ~31;                // the warp's first thread in the block
 
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1ULL);
-        __syncthreads();
-        const unsigned long long tile = s_tile;
+        unsigned long long tile = 0;
+        if (wl == 0) tile = atomicAdd(a.tile_counter, 1ULL);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
         if (tile >= (unsigned long long)a.n_tiles) return;
 
         // tile shape: bulk tiles first, then the tail's (more lanes per sample)
         const bool bulk = tile < (unsigned long long)a.n_bulk_tiles;
         const int lg = bulk ? a.lg_bulk : a.lg_tail;       // log2 of lanes per sample
-        const int spb = (int)(blockDim.x >> lg);
-        const int64_t base = bulk ? (int64_t)tile * spb
-                                  : a.bulk_samples + (int64_t)(tile - a.n_bulk_tiles) * spb;
-        const int slot = threadIdx.x >> lg;
-        const int lane = threadIdx.x & ((1 << lg) - 1);
+        const int spw = 32 >> lg;                          // samples of the tile
+        const int64_t base = bulk ? (int64_t)tile * spw
+                                  : a.bulk_samples + (int64_t)(tile - a.n_bulk_tiles) * spw;
+        const int slot = wl >> lg;
+        const int lane = wl & ((1 << lg) - 1);
         const int64_t g = base + slot;
         Res* my = rec + (size_t)threadIdx.x * kSlots;
-        if (g < a.total_samples) {
-            const int si = find_index(a.sample_offsets, a.n_sims, g);
+        const int si0 = g < a.total_samples ? find_index(a.sample_offsets, a.n_sims, g) : 0;
+        if (g < a.total_samples && SPINSIM_INB(si0 >= 0 && si0 < a.n_sims, 0)) {
+            const int si = si0;
             const int64_t k = g - a.sample_offsets[si];
             const DevSim& s = a.sims[si];
             // lanes in use: at most one per segment; each owns a canonical sub-tree
             const int lg_use = min(lg, (int)s.seg_log2);
             const int spl_log2 = s.seg_log2 - lg_use;
-            if (k > 0 && lane < (1 << lg_use)) {
+            if (SPINSIM_INB(k >= 0 && k < s.K, 1) && k > 0 && lane < (1 << lg_use)) {
                 SampleCtx<R> c;
                 double beta = 0.0;
                 const double gsum = make_ctx<R, N, TONES, SU3>(s, k, c, beta);
-                if (lane == 0) bg[slot] = make_double2(beta, gsum);
+                if (lane == 0) bg[w0 + slot] = make_double2(beta, gsum);
                 const int64_t L = s.L;
 #pragma unroll 1
                 for (int q = 0; q < (1 << spl_log2); q++) {
@@ -120,14 +127,15 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
                 }
             }
         }
-        __syncthreads();
-        // epilogue, one thread per sample of the tile: the lanes' sub-trees
+        __syncwarp();
+        // epilogue, one lane per sample of the tile: the lanes' sub-trees
         // combined in the canonical tree, then the FP64 part
-        if (threadIdx.x < spb) {
-            const int t = threadIdx.x;
+        if (wl < spw) {
+            const int t = wl;
             const int64_t gs = base + t;
-            if (gs < a.total_samples) {
-                const int si = find_index(a.sample_offsets, a.n_sims, gs);
+            const int si = gs < a.total_samples ? find_index(a.sample_offsets, a.n_sims, gs) : 0;
+            if (gs < a.total_samples && SPINSIM_INB(si >= 0 && si < a.n_sims, 0) &&
+                SPINSIM_INB(gs - a.sample_offsets[si] >= 0 && gs - a.sample_offsets[si] < a.sims[si].K, 1)) {
                 const int64_t k = gs - a.sample_offsets[si];
                 double* out = a.U + gs * OPD;
                 if (k == 0) {
@@ -136,7 +144,7 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
                     const DevSim& s = a.sims[si];
                     const int lg_use = min(lg, (int)s.seg_log2);
                     const int spl_log2 = s.seg_log2 - lg_use;
-                    Res* lanes = rec + (size_t)(t << lg) * kSlots;   // lane j's result: lanes[j * kSlots + spl_log2]
+                    Res* lanes = rec + (size_t)(w0 + (t << lg)) * kSlots;   // lane j's result: lanes[j * kSlots + spl_log2]
 #pragma unroll 1
                     for (int d = 0; d < lg_use; d++)
 #pragma unroll 1
@@ -145,13 +153,14 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
                             res_mul(lanes[(j + (1 << d)) * kSlots + spl_log2], lanes[j * kSlots + spl_log2], tmp);
                             lanes[j * kSlots + spl_log2] = tmp;
                         }
-                    const double2 b = bg[t];
+                    const double2 b = bg[w0 + t];
                     SampleExact sx;
                     make_exact<N, TONES>(s, k, b.x, b.y, sx);
                     finish<TONES>(lanes[spl_log2], s, sx, out);
                 }
             }
         }
+        __syncwarp();
     }
 }
 
@@ -263,23 +272,25 @@ cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int bloc
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, smem);
 }
 
-// Tiles of a launch: whole waves of bulk tiles (lanes_bulk lanes per sample)
-// while at least one full wave of them fits, then the remaining samples in
-// tail tiles with as many lanes per sample as every simulation of the launch
-// has segments (one segment per lane), which end the launch in finer steps.
+// Tiles of a launch (one warp each): whole waves of bulk tiles (lanes_bulk
+// lanes per sample) while at least one full wave of them fits, then the
+// remaining samples in tail tiles with as many lanes per sample as every
+// simulation of the launch has segments (one segment per lane), which end the
+// launch in finer steps.
 void integrate_tiles(int64_t total, int lanes_bulk, int block, int64_t wave_blocks, int min_seg_log2,
                      IntegrateArgs& a)
 {
     int lg = 0;
     while ((1 << lg) < lanes_bulk && lg < min_seg_log2) lg++;
-    const int64_t spb_bulk = block >> lg;
-    const int64_t rounds = total / (wave_blocks * spb_bulk);
+    const int64_t wave_warps = wave_blocks * (block / 32);
+    const int64_t spw_bulk = 32 >> lg;
+    const int64_t rounds = total / (wave_warps * spw_bulk);
     a.lg_bulk = lg;
     a.lg_tail = min_seg_log2;
-    a.n_bulk_tiles = rounds * wave_blocks;
-    a.bulk_samples = a.n_bulk_tiles * spb_bulk;
-    const int64_t spb_tail = block >> a.lg_tail;
-    a.n_tiles = a.n_bulk_tiles + (total - a.bulk_samples + spb_tail - 1) / spb_tail;
+    a.n_bulk_tiles = rounds * wave_warps;
+    a.bulk_samples = a.n_bulk_tiles * spw_bulk;
+    const int64_t spw_tail = 32 >> a.lg_tail;
+    a.n_tiles = a.n_bulk_tiles + (total - a.bulk_samples + spw_tail - 1) / spw_tail;
 }
 
 cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, int grid, int variant,
@@ -294,5 +305,9 @@ cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, 
     void* params[] = {&args};
     return cudaLaunchKernel(k, dim3(grid), dim3(block), params, smem, stream);
 }
+
+#ifdef SPINSIM_BOUNDS
+SPINSIM_BOUNDS_READER(bounds_word_integrate)
+#endif
 
 }  // namespace spinsim

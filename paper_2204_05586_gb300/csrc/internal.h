@@ -346,4 +346,12 @@ void integrate_tiles(int64_t total, int lanes_bulk, int block, int64_t wave_bloc
 cudaError_t launch_chain(int spin_x2, const ChainArgs& a, int n_sm, cudaStream_t stream, int* kernels,
                          bool fp32 = false);
 
+// The debug build's device error words (bounds.cuh), one per translation
+// unit with kernels: read, and cleared when `clear`; ~0 when unreadable.
+#ifdef SPINSIM_BOUNDS
+uint64_t bounds_word_integrate(bool clear);
+uint64_t bounds_word_chain(bool clear);
+uint64_t bounds_word_static(bool clear);
+#endif
+
 }  // namespace spinsim

@@ -582,7 +582,7 @@ int choose_shape(spinsim_s* h, int spin, int variant, double steps, int min_seg_
                             t.total_samples = std::min<int64_t>(a.total_samples, 4 * wave_blocks * (B / L));
                         }
                         integrate_tiles(t.total_samples, L, B, wave_blocks, min_seg_log2, t);
-                        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(t.n_tiles, wave_blocks));
+                        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((t.n_tiles + B / 32 - 1) / (B / 32), wave_blocks));
                         float ms_best = 1e30f;
                         for (int rep = 0; rep < 2; rep++) {
                             cudaMemsetAsync(a.tile_counter, 0, sizeof(unsigned long long), stream);
@@ -622,7 +622,7 @@ int choose_shape(spinsim_s* h, int spin, int variant, double steps, int min_seg_
     if (bps > 0) per_sm = std::min(per_sm, bps);
     const int64_t wave_blocks = (int64_t)h->n_sm * per_sm;
     integrate_tiles(a.total_samples, lanes, block, wave_blocks, min_seg_log2, a);
-    grid = (int)std::max<int64_t>(1, std::min<int64_t>(a.n_tiles, wave_blocks));
+    grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n_tiles + block / 32 - 1) / (block / 32), wave_blocks));
     return SPINSIM_OK;
 }
 
@@ -836,6 +836,7 @@ int spinsim_config_default(spinsim_config* cfg)
     cfg->precision = SPINSIM_PREC_FP32_BULK;
     cfg->rotating_frame = 1;
     cfg->trotter_squares = -1;
+    cfg->direct_host_outputs = 1;
     return SPINSIM_OK;
 }
 
@@ -1236,6 +1237,25 @@ int spinsim_range_entering_state(int32_t spin_x2, const double* aggs, int32_t ra
     }
     for (int i = 0; i < 2 * n; i++) psi_out[i] = psi[i];
     return SPINSIM_OK;
+}
+
+int spinsim_debug_bounds(int32_t device, uint64_t* word)
+{
+    if (!word) return SPINSIM_E_ARG;
+    *word = 0;
+#ifdef SPINSIM_BOUNDS
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (cudaSetDevice(device) != cudaSuccess) return SPINSIM_E_CUDA;
+    const uint64_t a = bounds_word_integrate(true), b = bounds_word_chain(true), c = bounds_word_static(true);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (a == ~0ULL || b == ~0ULL || c == ~0ULL) return SPINSIM_E_CUDA;
+    *word = a | b | c;
+    return SPINSIM_OK;
+#else
+    (void)device;
+    return SPINSIM_E_UNSUPPORTED;
+#endif
 }
 
 int spinsim_last_launch(spinsim_handle h, spinsim_launch_info* info)

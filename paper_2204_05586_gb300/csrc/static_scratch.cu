@@ -18,6 +18,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "bounds.cuh"
 #include "internal.h"
 #include "spinsim.h"
 
@@ -94,6 +95,12 @@ struct DeviceGuard {
 };
 
 }  // namespace
+
+#ifdef SPINSIM_BOUNDS
+namespace spinsim {
+SPINSIM_BOUNDS_READER(bounds_word_static)
+}
+#endif
 
 extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_request* req, spinsim_result* res,
                                        void* stream_v)
@@ -206,7 +213,8 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         if (cfg->blocks_per_sm > 0) per_sm = std::min(per_sm, cfg->blocks_per_sm);
         const int64_t wave_blocks = (int64_t)n_sm * std::max(per_sm, 1);
         integrate_tiles(K, lanes, block, wave_blocks, seg_log2_of(L), ia);
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ia.n_tiles, wave_blocks));
+        const int grid =
+            (int)std::max<int64_t>(1, std::min<int64_t>((ia.n_tiles + block / 32 - 1) / (block / 32), wave_blocks));
         if (launch_integrate(spin, cfg->precision, cfg->method, block, grid, variant, ia, stream) != cudaSuccess)
             return res->status = SPINSIM_E_CUDA;
         ChainArgs ca;

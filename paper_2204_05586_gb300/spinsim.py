@@ -85,7 +85,7 @@ EXPORTED = ("spinsim_config_default", "spinsim_create", "spinsim_destroy", "spin
             "spinsim_simulate", "spinsim_submit", "spinsim_poll", "spinsim_poll_any", "spinsim_memory",
             "spinsim_last_launch", "spinsim_status_string",
             "spinsim_simulate_static", "spinsim_range_begin", "spinsim_range_finish",
-            "spinsim_range_entering_state")
+            "spinsim_range_entering_state", "spinsim_debug_bounds")
 
 _lib = None
 _lock = threading.Lock()
@@ -96,14 +96,17 @@ def lib_path() -> str:
 
 
 def load(build_if_missing: bool = True):
-    """Load libspinsim.so (building it first if needed); raises if impossible."""
+    """Load libspinsim.so (building it first if needed); raises if impossible.
+    With SPINSIM_BOUNDS=1 in the environment the process loads the debug
+    library with range-checked kernels instead (libspinsim_bounds.so)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
+        bounds = os.environ.get("SPINSIM_BOUNDS") == "1"
+        path = _build.BOUNDS_LIB if bounds else _build.LIB
         if build_if_missing:
-            path = _build.build()
+            path = _build.build_bounds() if bounds else _build.build()
         if not os.path.exists(path):
             raise RuntimeError(f"CUDA library {path} is missing; run paper_2204_05586_gb300.build.build()")
         L = ctypes.CDLL(path)
@@ -130,6 +133,7 @@ def load(build_if_missing: bool = True):
         L.spinsim_range_finish.argtypes = [ctypes.c_void_p, P(ctypes.c_double), ctypes.c_void_p]
         L.spinsim_range_entering_state.argtypes = [ctypes.c_int32, P(ctypes.c_double), ctypes.c_int32,
                                                    P(ctypes.c_double), P(ctypes.c_double)]
+        L.spinsim_debug_bounds.argtypes = [ctypes.c_int32, P(ctypes.c_uint64)]
         L.spinsim_status_string.argtypes = [ctypes.c_int]
         L.spinsim_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -239,6 +243,14 @@ def spinsim_memory(h) -> dict:
     return {f: getattr(info, f) for f, _ in spinsim_memory_info._fields_}
 
 
+def spinsim_debug_bounds(device: int = 0):
+    """Returns (status, word): the debug build's error word of `device`
+    (0 = every checked index in range), read and cleared."""
+    w = ctypes.c_uint64()
+    st = load().spinsim_debug_bounds(device, ctypes.byref(w))
+    return st, w.value
+
+
 def spinsim_last_launch(h) -> spinsim_launch_info:
     info = spinsim_launch_info()
     load().spinsim_last_launch(h, ctypes.byref(info))
@@ -292,7 +304,7 @@ def make_request(req: dict) -> spinsim_request:
 
 def make_config(precision=PREC_FP32_BULK, method=METHOD_CF4, rotating_frame=True, tau=-1, lanes=0, block=0,
                 use_graphs=False, device=0, mem_budget=0, profile=False, blocks_per_sm=0,
-                chain_fp32=False, direct_host_outputs=False) -> spinsim_config:
+                chain_fp32=False, direct_host_outputs=True) -> spinsim_config:
     c = spinsim_config()
     spinsim_config_default(c)
     c.precision, c.method, c.rotating_frame, c.trotter_squares = precision, method, int(bool(rotating_frame)), tau

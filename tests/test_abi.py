@@ -38,8 +38,8 @@ def test_struct_sizes_match_header():
 #include <stddef.h>
 #include "spinsim.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(spinsim_config), sizeof(spinsim_field), sizeof(spinsim_request),
-         sizeof(spinsim_result), sizeof(spinsim_launch_info));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(spinsim_config), sizeof(spinsim_field), sizeof(spinsim_request),
+         sizeof(spinsim_result), sizeof(spinsim_launch_info), sizeof(spinsim_memory_info));
   printf("%zu %zu %zu %zu\n", offsetof(spinsim_request, field), offsetof(spinsim_request, t_start),
          offsetof(spinsim_request, psi0), offsetof(spinsim_result, status));
   return 0;
@@ -51,10 +51,10 @@ int main(void) {
         subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
         out = subprocess.check_output([exe]).decode().split()
     sizes = list(map(int, out))
-    assert sizes[:5] == [ctypes.sizeof(S.spinsim_config), ctypes.sizeof(S.spinsim_field),
+    assert sizes[:6] == [ctypes.sizeof(S.spinsim_config), ctypes.sizeof(S.spinsim_field),
                          ctypes.sizeof(S.spinsim_request), ctypes.sizeof(S.spinsim_result),
-                         ctypes.sizeof(S.spinsim_launch_info)]
-    assert sizes[5:] == [S.spinsim_request.field.offset, S.spinsim_request.t_start.offset,
+                         ctypes.sizeof(S.spinsim_launch_info), ctypes.sizeof(S.spinsim_memory_info)]
+    assert sizes[6:] == [S.spinsim_request.field.offset, S.spinsim_request.t_start.offset,
                          S.spinsim_request.psi0.offset, S.spinsim_result.status.offset]
 
 
@@ -118,3 +118,14 @@ def test_warning_bits_match_header():
     bits = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define SPINSIM_WARN_([A-Z0-9_]+)\s+(\d+)", src)}
     assert bits == {"MAGNUS": S.WARN_MAGNUS, "FP32_LAB": S.WARN_FP32_LAB}
     assert all(v & (v - 1) == 0 for v in bits.values()) and len(set(bits.values())) == len(bits)
+
+
+def test_debug_bounds_entry_point():
+    """The normal library carries no range checks: spinsim_debug_bounds says
+    so without touching the GPU.  The debug library (-DSPINSIM_BOUNDS) builds
+    and exports the same entry points."""
+    assert S.spinsim_debug_bounds(0) == (S.E_UNSUPPORTED, 0)
+    from paper_2204_05586_gb300 import build as B
+    lib = ctypes.CDLL(B.build_bounds())
+    for name in declared_functions():
+        assert hasattr(lib, name), name

@@ -294,6 +294,34 @@ def test_host_buffers_match_device_buffers():
     assert np.array_equal(host, dev["states"].cpu().numpy())
 
 
+@pytest.mark.parametrize("direct", [False, True])
+def test_pinned_host_outputs_written_directly_or_staged(direct):
+    """Pinned host result buffers (one block, as a large batch allocates them),
+    written by the kernels directly (direct_host_outputs = 1) or staged and
+    copied back: states, <J> and operators equal the device-buffer run bit for
+    bit, for a mixed batch (both spins, uneven lengths, graph replay on the
+    second call), and the launch info counts the bytes that reached the host."""
+    reqs = W.sweep(5, t_min=1e-4, t_max=3e-3) + [W.spin_half_rabi(t_end=2e-3), W.spin_one_sensing(t_end=1e-3)]
+    dev, _ = gpu_run(reqs, want_ops=True, precision=S.PREC_FP32_BULK)
+    with S.Simulator(precision=S.PREC_FP32_BULK, use_graphs=True, direct_host_outputs=direct) as sim:
+        outs = sim.allocate(reqs, want_ops=True, device="cpu", pin_memory=True, one_buffer=True)
+        res = sim.results_struct(outs)
+        arr = (S.spinsim_request * len(reqs))(*[S.make_request(q) for q in reqs])
+        for call in range(2):
+            for o in outs:
+                o["states"].fill_(float("nan"))
+            assert S.spinsim_simulate(sim.handle, arr, res, 0) == S.OK
+            torch.cuda.synchronize()
+            info = sim.last_launch()
+            want = sum(o["K"] * (16 * (q["spin_x2"] + 1) + 24 + 16 * (q["spin_x2"] + 1) ** 2) for o, q in zip(outs, reqs))
+            assert info["d2h_bytes"] == want
+            for o, d in zip(outs, dev):
+                K = o["K"]
+                assert np.array_equal(torch.view_as_complex(o["states"][:K]).numpy(), d["states"].cpu().numpy())
+                assert np.array_equal(o["spin"][:K].numpy(), d["spin"].cpu().numpy())
+                assert np.array_equal(torch.view_as_complex(o["ops"][:K]).numpy(), d["ops"].cpu().numpy())
+
+
 def test_graph_replay_matches_eager():
     reqs = W.sweep(16, t_min=1e-4, t_max=2e-3)
     eager, _ = gpu_run(reqs, precision=S.PREC_FP32_BULK, lanes=2, block=128)
