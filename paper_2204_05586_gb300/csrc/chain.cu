@@ -366,12 +366,22 @@ __global__ void __launch_bounds__(128) chain_up_kernel(ChainArgs a)
         const int64_t k1 = min(k0 + run, s.K);
         const double* U = a.U + s.sample_offset * D;
         if (SPINSIM_INB(si >= 0 && si < a.n_sims && k0 >= 0, 8) && k0 < k1) B.load(U + k0 * D);
-        for (int64_t k = k0 + 1; k < k1; k++) {
-            Op<N, T> u, t;
-            if (SPINSIM_INB(k < s.K, 9)) u.load(U + k * D);
+        // the next operator is loaded while the current product runs (L2 latency
+        // off the dependent chain of products)
+        Op<N, T> u;
+        if (k0 + 1 < k1) {
+            if (SPINSIM_INB(k0 + 1 < s.K, 9)) u.load(U + (k0 + 1) * D);
             else u.identity();
+        }
+        for (int64_t k = k0 + 1; k < k1; k++) {
+            Op<N, T> t, nx;
+            if (k + 1 < k1) {
+                if (SPINSIM_INB(k + 1 < s.K, 9)) nx.load(U + (k + 1) * D);
+                else nx.identity();
+            }
             Op<N, T>::mul(u, B, t);   // later operators multiply from the left
             B = t;
+            u = nx;
         }
         B.store(S + lane * D);
         __syncwarp();
@@ -479,10 +489,18 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
         const int64_t k0 = kn + (int64_t)lane * run;
         const int64_t k1 = min(k0 + run, s.K);
         const double* U = a.U + s.sample_offset * D;
-        for (int64_t k = k0; k < k1; k++) {
-            Op<N, T> u;
-            if (SPINSIM_INB(k >= 0 && k < s.K && k - kn < (int64_t)kFan * kMaxRun, 14)) u.load(U + k * D);
+        // U_{k+1} is loaded while sample k is computed and written
+        Op<N, T> u;
+        if (k0 < k1) {
+            if (SPINSIM_INB(k0 >= 0 && k0 < s.K && k0 - kn < (int64_t)kFan * kMaxRun, 14)) u.load(U + k0 * D);
             else u.identity();
+        }
+        for (int64_t k = k0; k < k1; k++) {
+            Op<N, T> un;
+            if (k + 1 < k1) {
+                if (SPINSIM_INB(k + 1 < s.K && k + 1 - kn < (int64_t)kFan * kMaxRun, 14)) un.load(U + (k + 1) * D);
+                else un.identity();
+            }
             u.apply(psi, nxt);
 #pragma unroll
             for (int i = 0; i < N; i++) psi[i] = nxt[i];
@@ -513,6 +531,7 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
                 stage_spin[q * 3 + 2] = jv[2];
             }
             if (s.ops) u.store_full(s.ops + k * 2 * N * N);
+            u = un;
         }
         __syncwarp();
         // the node's span [kn, kn + m): psi_k as N double2 words per sample,
