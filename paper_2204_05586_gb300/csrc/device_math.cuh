@@ -67,85 +67,6 @@ __device__ __forceinline__ void allow_dependent_launch()
 }
 #endif
 
-// Exact conversions between FP32 and FP64 by integer operations.  On GB300
-// cvt.f64.f32 and cvt.f32.f64 occupy the FP64 unit as long as a DFMA (measured:
-// an FP64 add stream fed by conversions takes twice as long as one without),
-// while the same conversions done on the bits run on the integer pipes and
-// hide behind the FP64 work.  Both give the IEEE result bit for bit (FP64 to
-// FP32 rounds to nearest, ties to even); subnormals, infinities and NaN, and
-// FP64 values outside FP32's normal range, take the hardware conversion.
-SPINSIM_HD uint32_t f32_bits(float f)
-{
-    uint32_t u;
-    std::memcpy(&u, &f, sizeof u);
-    return u;
-}
-SPINSIM_HD float f32_from_bits(uint32_t u)
-{
-    float f;
-    std::memcpy(&f, &u, sizeof f);
-    return f;
-}
-SPINSIM_HD uint64_t f64_bits(double d)
-{
-    uint64_t u;
-    std::memcpy(&u, &d, sizeof u);
-    return u;
-}
-SPINSIM_HD double f64_from_bits(uint64_t u)
-{
-    double d;
-    std::memcpy(&d, &u, sizeof d);
-    return d;
-}
-
-SPINSIM_HD double f32_to_f64_bits(float f)
-{
-    const uint32_t u = f32_bits(f);
-    const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
-    if (e == 0xffu || (e == 0u && m != 0u)) return (double)f;   // inf, NaN, subnormal
-    const uint32_t sign = u & 0x80000000u;
-    const uint32_t hi = e == 0u ? sign : (sign | ((e + 896u) << 20) | (m >> 3));
-    const uint32_t lo = e == 0u ? 0u : (m << 29);
-    return f64_from_bits(((uint64_t)hi << 32) | lo);
-}
-
-SPINSIM_HD float f64_to_f32_bits(double d)
-{
-    const uint64_t u = f64_bits(d);
-    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
-    const uint32_t e = (hi >> 20) & 0x7ffu;
-    if (e < 897u || e > 1150u) return (float)d;   // zero, FP32 subnormal or out of range, inf, NaN
-    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);   // the 23 kept mantissa bits
-    const uint32_t r = lo & 0x1fffffffu;                      // the 29 dropped bits
-    uint32_t out = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
-    if (r > 0x10000000u || (r == 0x10000000u && (m & 1u))) out += 1u;   // a carry into the exponent is right
-    return f32_from_bits(out);
-}
-
-// widen / narrow: FP32 <-> FP64 in device code through the integer forms, a
-// plain conversion in host code; the identity for FP64.
-template <typename R>
-SPINSIM_HD double widen(R x)
-{
-#if defined(__CUDA_ARCH__)
-    if constexpr (sizeof(R) == 4) return f32_to_f64_bits(x);
-    else return (double)x;
-#else
-    return (double)x;
-#endif
-}
-template <typename R>
-SPINSIM_HD R narrow(double x)
-{
-#if defined(__CUDA_ARCH__)
-    if constexpr (sizeof(R) == 4) return f64_to_f32_bits(x);
-    else return (R)x;
-#else
-    return (R)x;
-#endif
-}
-
 // The bulk type's precision class: FP32 (float, or a host vector of floats
 // that carries several samples at once, which specialises this) or FP64.
 template <typename R>
@@ -462,7 +383,7 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
 {
     const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;
     beta = drive_phase_at(s, k);
-    const SinCos<R> eb = sincos_cold(narrow<R>(beta));
+    const SinCos<R> eb = sincos_cold((R)beta);
     c.ebr = eb.c;
     c.ebi = eb.s;
     if constexpr (kFP32<R>) {
@@ -508,17 +429,17 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
                 c.amp[p] = (R)s.amp[p];
                 c.invw[p] = (R)s.inv_w[p];
             }
-            c.u0[p] = narrow<R>((t_prev - s.centre[p]) * s.inv_w[p]);
+            c.u0[p] = (R)((t_prev - s.centre[p]) * s.inv_w[p]);
             if (s.frame) {
-                R um = narrow<R>((t_prev + 0.5 * s.dt_out - s.centre[p]) * s.inv_w[p]);
+                R um = (R)((t_prev + 0.5 * s.dt_out - s.centre[p]) * s.inv_w[p]);
                 R g = pulse_shape<R>(p >= s.n_gauss, um);
                 c.ghat[p] = g;
-                gsum = fma(widen(c.amp[p]), widen(g), gsum);
+                gsum = fma((double)c.amp[p], (double)g, gsum);
             }
         }
     }
-    c.co = narrow<R>(s.frame ? s.w_co0 - gsum : s.w_co0);
-    c.counter = narrow<R>(s.frame ? s.w_counter0 + gsum : s.w_counter0);
+    c.co = (R)(s.frame ? s.w_co0 - gsum : s.w_co0);
+    c.counter = (R)(s.frame ? s.w_counter0 + gsum : s.w_counter0);
     if constexpr (TONES) {
         c.nt = s.n_tones;
 #pragma unroll

@@ -44,13 +44,13 @@ SPINSIM_HD void promote(const Res3<R>& P, const DevSim& s, const SampleExact& x,
 {
     double gx, gy;
     first_order_exact<TONES>(s, x, gx, gy);
-    const double gz = widen(P.g[2]), q3 = s.gq * (1.0 / 3.0);
+    const double gz = (double)P.g[2], q3 = s.gq * (1.0 / 3.0);
     const cx<double> up = cmk(-gy * kInvSqrt2, -gx * kInvSqrt2);
     const cx<double> dn = cmk(gy * kInvSqrt2, -gx * kInvSqrt2);
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) Y[i][j] = cmk(widen(P.m[i][j].r), widen(P.m[i][j].i));
+        for (int j = 0; j < 3; j++) Y[i][j] = cmk((double)P.m[i][j].r, (double)P.m[i][j].i);
     Y[0][0].i -= gz + q3;
     Y[1][1].i += 2.0 * q3;
     Y[2][2].i += gz - q3;
@@ -89,9 +89,9 @@ SPINSIM_HD void promote(const Res2<R>& P, const DevSim& s, const SampleExact& x,
 {
     double gx, gy;
     first_order_exact<TONES>(s, x, gx, gy);
-    const double gz = widen(P.g[2]);
-    a = cmk(widen(P.a.r), widen(P.a.i) - 0.5 * gz);
-    b = cmk(widen(P.b.r) + 0.5 * gy, widen(P.b.i) - 0.5 * gx);
+    const double gz = (double)P.g[2];
+    a = cmk((double)P.a.r, (double)P.a.i - 0.5 * gz);
+    b = cmk((double)P.b.r + 0.5 * gy, (double)P.b.i - 0.5 * gx);
 }
 
 SPINSIM_HD void store_half(cx<double> al, cx<double> be, const SampleExact& x, double* out)

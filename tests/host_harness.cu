@@ -75,15 +75,6 @@ void hh_expm_one_tau0(double vx, double vy, double vz, double vq, int fp32, doub
             }
     }
 }
-// the integer forms of the FP32 <-> FP64 conversions, element by element
-void hh_f64_to_f32(const double* x, float* y, int64_t n)
-{
-    for (int64_t i = 0; i < n; i++) y[i] = f64_to_f32_bits(x[i]);
-}
-void hh_f32_to_f64(const float* x, double* y, int64_t n)
-{
-    for (int64_t i = 0; i < n; i++) y[i] = f32_to_f64_bits(x[i]);
-}
 // the same FP32 exponential through the general series, for comparison
 void hh_expm_one_general32(double vx, double vy, double vz, double vq, int tau, double* out)
 {

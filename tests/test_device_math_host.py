@@ -40,9 +40,6 @@ def hh(tmp_path_factory):
     L.hh_expm_one_small.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, DP]
     L.hh_expm_one_general32.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, DP]
     L.hh_expm_one_tau0.argtypes = [ctypes.c_double] * 4 + [ctypes.c_int, DP, DP]
-    FP = ctypes.POINTER(ctypes.c_float)
-    L.hh_f64_to_f32.argtypes = [DP, FP, ctypes.c_int64]
-    L.hh_f32_to_f64.argtypes = [FP, DP, ctypes.c_int64]
     L.hh_tiny_sincos.argtypes = [ctypes.c_double, DP]
     L.hh_small_angle_request.restype = ctypes.c_int
     L.hh_small_angle_request.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
@@ -422,38 +419,3 @@ def test_general_exponential_degree_choice(hh):
             ref = np.array([[complex(refm[i, j]) for j in range(3)] for i in range(3)])
             assert np.abs(rest - ref).max() < 1e-15 * max(theta, theta ** 2), theta
 
-
-def test_integer_conversions_equal_ieee_casts(hh):
-    """The kernels' FP32 <-> FP64 conversions done on the bits (kept off the
-    FP64 unit) give the IEEE casts bit for bit: FP64 -> FP32 rounds to
-    nearest, ties to even, across the whole exponent range (normal results,
-    the subnormal and overflow boundaries, exact ties, zeros, infinities, NaN);
-    FP32 -> FP64 is exact for every FP32 value."""
-    rng = np.random.default_rng(17)
-    FP = ctypes.POINTER(ctypes.c_float)
-    # FP64 -> FP32: random mantissas over every relevant exponent, plus constructed ties
-    mant = rng.uniform(1.0, 2.0, 200000)
-    expo = rng.integers(-160, 140, 200000)
-    x = np.ldexp(mant, expo) * rng.choice([-1.0, 1.0], 200000)
-    f = rng.uniform(-1e30, 1e30, 20000).astype(np.float32)
-    half_ulp = np.spacing(np.abs(f)).astype(np.float64) / 2
-    ties = np.concatenate([f.astype(np.float64) + half_ulp, f.astype(np.float64) - half_ulp])
-    edge = np.array([0.0, -0.0, np.inf, -np.inf, 3.4028234663852886e38, 3.4028235677973366e38,
-                     1.1754943508222875e-38, 1.1754942807573643e-38, 1e-45, 5e-324, 1.0, -1.5,
-                     np.finfo(np.float32).max * (1 + 2.0 ** -25)])
-    xs = np.ascontiguousarray(np.concatenate([x, ties, edge]))
-    got = np.zeros(xs.size, np.float32)
-    hh.hh_f64_to_f32(xs.ctypes.data_as(DP), got.ctypes.data_as(FP), xs.size)
-    want = xs.astype(np.float32)
-    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
-    nan = np.array([np.nan]); out = np.zeros(1, np.float32)
-    hh.hh_f64_to_f32(nan.ctypes.data_as(DP), out.ctypes.data_as(FP), 1)
-    assert np.isnan(out[0])
-    # FP32 -> FP64: random bit patterns (no NaN) and the special values
-    bits = rng.integers(0, 2 ** 32, 300000, dtype=np.uint64).astype(np.uint32)
-    fs = bits.view(np.float32)
-    fs = np.ascontiguousarray(np.concatenate([fs[~np.isnan(fs)], np.array([0.0, -0.0, np.inf, -np.inf, 1e-45, -1e-40],
-                                                                           np.float32)]))
-    got64 = np.zeros(fs.size, np.float64)
-    hh.hh_f32_to_f64(fs.ctypes.data_as(FP), got64.ctypes.data_as(DP), fs.size)
-    assert np.array_equal(got64.view(np.uint64), fs.astype(np.float64).view(np.uint64))
