@@ -50,6 +50,10 @@ void sample_operator(const DevSim& s, int64_t k, double* out)
             CounterPhasors<R> ph;
             counter_phasors_at<R, METHOD>(c, lo, ph);
             for (int64_t l = lo; l < hi; l++) step_apply_su3<R, METHOD, TONES>(c, (R)l, ph, X);
+        } else if constexpr (SMALL && N == 3) {
+            DrivePhasors<R> dp;
+            drive_phasors_at<R, METHOD>(c, lo, dp);
+            for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES>(c, (R)l, c.tau, X, &dp);
         } else {
             for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES>(c, (R)l, c.tau, X);
         }
@@ -126,7 +130,13 @@ void sample_operators4(const DevSim& s, int64_t k, double* out)
         const int64_t lo = ((int64_t)q * s.L) >> s.seg_log2, hi = ((int64_t)(q + 1) * s.L) >> s.seg_log2;
         Res4 X;
         res_zero(X);
-        for (int64_t l = lo; l < hi; l++) step_apply<F4, METHOD, SMALL, TONES>(c, F4((float)l), c.tau, X);
+        if constexpr (SMALL && N == 3) {
+            DrivePhasors<F4> dp;
+            drive_phasors_at<F4, METHOD>(c, lo, dp);
+            for (int64_t l = lo; l < hi; l++) step_apply<F4, METHOD, SMALL, TONES>(c, F4((float)l), c.tau, X, &dp);
+        } else {
+            for (int64_t l = lo; l < hi; l++) step_apply<F4, METHOD, SMALL, TONES>(c, F4((float)l), c.tau, X);
+        }
         int h = 0;
         while ((q >> h) & 1) {
             Res4 t;

@@ -700,10 +700,66 @@ SPINSIM_HD void counter_phasors_advance(CounterPhasors<R>& p)
     }
 }
 
+// The drive's in-frame phasors at both nodes of a step in the small-angle
+// variant: co-rotating e^{i beta} e^{i (w_d - w_r) tau} and counter-rotating
+// e^{i beta} e^{i (w_d + w_r) tau}, tau = (l + c_j) dt.  They are set from the
+// series (co-rotating) and the hardware sincos (counter-rotating) at the first
+// step of each canonical segment and then turned by e^{i w dt} per step, one
+// complex product each instead of a series or a sincos with its range
+// reduction and a rotation by e^{i beta}.  Both reach only second order (the
+// first-order transverse part is replaced by its exact FP64 quadrature at the
+// end of the sample); the turns' rounding grows as (steps into the segment)
+// x 2^-24 on those second-order terms, and the result depends on the step
+// index alone, not on the launch shape.
+template <typename R>
+struct DrivePhasors {
+    cx<R> co[2], ct[2];   // [node]
+    cx<R> rco, rct;       // turns per step
+};
+
+template <typename R, int METHOD>
+SPINSIM_HD void drive_phasors_at(const SampleCtx<R>& c, int64_t lo, DrivePhasors<R>& p)
+{
+    R s, co;
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        p.co[j] = cmk(R(0), R(0));
+        p.ct[j] = cmk(R(0), R(0));
+        if (METHOD == 1 && j == 1) break;   // one node
+        const R tau = ((R)lo + (j ? c.c2 : c.c1)) * c.dt;
+        small_sincos_tiny(c.co * tau, s, co);
+        p.co[j] = cmk(c.ebr * co - c.ebi * s, fma(c.ebr, s, c.ebi * co));
+        if (c.counter_on) {
+            second_order_sincos(c.counter * tau, s, co);
+            p.ct[j] = cmk(c.ebr * co - c.ebi * s, fma(c.ebr, s, c.ebi * co));
+        }
+    }
+    small_sincos_tiny(c.co * c.dt, s, co);
+    p.rco = cmk(co, s);
+    second_order_sincos(c.counter * c.dt, s, co);
+    p.rct = cmk(co, s);
+}
+
+template <typename R, int METHOD>
+SPINSIM_HD void drive_phasors_advance(DrivePhasors<R>& p)
+{
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+        if (METHOD == 1 && j == 1) break;
+        p.co[j] = cmul(p.co[j], p.rco);
+        p.ct[j] = cmul(p.ct[j], p.rct);
+    }
+}
+
 template <typename R, bool SMALL = false, bool TONES = false, bool SU3 = false, bool PH = false>
 SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f, const CounterPhasors<R>* ph = nullptr,
-                         int node = 0)
+                         int node = 0, const DrivePhasors<R>* dp = nullptr)
 {
+    if (dp) {
+        // small-angle variant: both drive phasors turned per step (DrivePhasors)
+        f.co = dp->co[node];
+        f.ct = dp->ct[node];
+    } else {
     R s1, c1;
     step_sincos<R, SMALL>(c.co * tau, s1, c1);
     f.co = cmk(c.ebr * c1 - c.ebi * s1, fma(c.ebr, s1, c.ebi * c1));
@@ -718,6 +774,7 @@ SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f, const Co
         f.ct = cmk(c.ebr * c2 - c.ebi * s2, fma(c.ebr, s2, c.ebi * c2));
     } else {
         f.ct = cmk(R(0), R(0));
+    }
     }
     }
     R z = R(0);
@@ -1457,12 +1514,13 @@ SPINSIM_HD void step_apply_su3(const SampleCtx<R>& c, R lf, CounterPhasors<R>& p
 }
 
 template <typename R, int METHOD, bool SMALL = false, bool TONES = false>
-SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X)
+SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X, DrivePhasors<R>* dp = nullptr)
 {
     NodeField<R> f1, f2;
-    field_at<R, SMALL, TONES>(c, (lf + c.c1) * c.dt, f1);
+    field_at<R, SMALL, TONES>(c, (lf + c.c1) * c.dt, f1, nullptr, 0, dp);
     if (METHOD == 1) f2 = f1;
-    else field_at<R, SMALL, TONES>(c, (lf + c.c2) * c.dt, f2);
+    else field_at<R, SMALL, TONES>(c, (lf + c.c2) * c.dt, f2, nullptr, 1, dp);
+    if (dp) drive_phasors_advance<R, METHOD>(*dp);
     R vx, vy, vz, wx = R(0), wy = R(0), wz = R(0);
     exponent<R, TONES>(c, f1, f2, false, vx, vy, vz);
     if (METHOD == 0) exponent<R, TONES>(c, f1, f2, true, wx, wy, wz);

@@ -109,6 +109,12 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
                         counter_phasors_at<R, METHOD>(c, lo, ph);
 #pragma unroll 1
                         for (int64_t l = lo; l < hi; l++) step_apply_su3<R, METHOD, TONES>(c, (R)l, ph, X);
+                    } else if constexpr (SMALL && N == 3) {
+                        // small angles: the drive phasors turned per step from the segment's start
+                        DrivePhasors<R> dp;
+                        drive_phasors_at<R, METHOD>(c, lo, dp);
+#pragma unroll 1
+                        for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES>(c, (R)l, c.tau, X, &dp);
                     } else {
 #pragma unroll 1
                         for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES>(c, (R)l, c.tau, X);   // U <- u_l U
