@@ -86,6 +86,7 @@ void pack(const SampleCtx<float> (&c)[4], SampleCtx<F4>& v)
     SPINSIM_PACK(d1r); SPINSIM_PACK(d1i); SPINSIM_PACK(p1r); SPINSIM_PACK(p1i); SPINSIM_PACK(eqr); SPINSIM_PACK(eqi);
     for (int p = 0; p < kMaxPulses; p++) {
         SPINSIM_PACK(amp[p]); SPINSIM_PACK(u0[p]); SPINSIM_PACK(invw[p]); SPINSIM_PACK(ghat[p]);
+        SPINSIM_PACK(u0b[p]); SPINSIM_PACK(invwb[p]);
     }
     for (int j = 0; j < kMaxTones; j++) {
         SPINSIM_PACK(tbr[j]); SPINSIM_PACK(tbi[j]); SPINSIM_PACK(tco[j]); SPINSIM_PACK(tct[j]);

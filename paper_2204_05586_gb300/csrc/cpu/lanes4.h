@@ -63,6 +63,7 @@ inline F4 fma(F4 a, F4 b, F4 c)
     return r;
 }
 inline F4 exp(F4 a) { return lanewise(a, [](float x) { return std::exp(x); }); }
+inline F4 exp2(F4 a) { return lanewise(a, [](float x) { return std::exp2(x); }); }
 inline F4 sinf(F4 a) { return lanewise(a, [](float x) { return std::sin(x); }); }
 inline F4 cosf(F4 a) { return lanewise(a, [](float x) { return std::cos(x); }); }
 inline F4 rintf(F4 a) { return lanewise(a, [](float x) { return std::rint(x); }); }

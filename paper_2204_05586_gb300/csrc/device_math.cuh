@@ -31,6 +31,7 @@
 namespace spinsim {
 using std::cos;
 using std::exp;
+using std::exp2;
 using std::fabs;
 using std::floor;
 using std::fma;
@@ -281,6 +282,7 @@ struct SampleCtx {
     R d1r, d1i, p1r, p1i, eqr, eqi;
     R dt, c1, c2;
     R amp[kMaxPulses], u0[kMaxPulses], invw[kMaxPulses], ghat[kMaxPulses];
+    R u0b[kMaxPulses], invwb[kMaxPulses];   // u0, invw in base-2 Gaussian units (small-angle variant)
     // further tones (the tones variant only): e^{i beta_j}, in-frame rates, Om+-_j
     R tbr[kMaxTones], tbi[kMaxTones], tco[kMaxTones], tct[kMaxTones], tomp[kMaxTones], tomm[kMaxTones];
     // quadrupole drives (the su(3) variant only): the same per pair
@@ -421,15 +423,19 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
 #pragma unroll
     for (int p = 0; p < kMaxPulses; p++) {
         c.amp[p] = R(0); c.u0[p] = R(0); c.invw[p] = R(0); c.ghat[p] = R(0);
+        c.u0b[p] = R(0); c.invwb[p] = R(0);
         if (p < c.np) {
             if constexpr (kFP32<R>) {
                 c.amp[p] = s.f_amp[p];
                 c.invw[p] = s.f_invw[p];
+                c.invwb[p] = s.f_invwb[p];
             } else {
                 c.amp[p] = (R)s.amp[p];
                 c.invw[p] = (R)s.inv_w[p];
+                c.invwb[p] = (R)(s.inv_w[p] * kGaussBase2);
             }
             c.u0[p] = (R)((t_prev - s.centre[p]) * s.inv_w[p]);
+            c.u0b[p] = (R)((t_prev - s.centre[p]) * s.inv_w[p] * kGaussBase2);
             if (s.frame) {
                 R um = (R)((t_prev + 0.5 * s.dt_out - s.centre[p]) * s.inv_w[p]);
                 R g = pulse_shape<R>(p >= s.n_gauss, um);
@@ -778,11 +784,22 @@ SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f, const Co
     }
     }
     R z = R(0);
+    if constexpr (SMALL) {
+        // Gaussians only: exp(-u^2/2) as 2^(-ub^2), ub = u sqrt(log2(e)/2) (one
+        // exp2 instead of a scaled exp), the loop ending at the pulse count
 #pragma unroll
-    for (int p = 0; p < kMaxPulses; p++) {
-        if (p < c.ng) {
-            R u = fma(tau, c.invw[p], c.u0[p]);
-            z = fma(c.amp[p], exp(R(-0.5) * u * u) - c.ghat[p], z);
+        for (int p = 0; p < kMaxPulses; p++) {
+            if (p >= c.ng) break;
+            const R ub = fma(tau, c.invwb[p], c.u0b[p]);
+            z = fma(c.amp[p], exp2(-(ub * ub)) - c.ghat[p], z);
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < kMaxPulses; p++) {
+            if (p < c.ng) {
+                R u = fma(tau, c.invw[p], c.u0[p]);
+                z = fma(c.amp[p], exp(R(-0.5) * u * u) - c.ghat[p], z);
+            }
         }
     }
     // single sine cycles: the general variant only (the small-angle variant is

@@ -9,6 +9,8 @@
 namespace spinsim {
 
 constexpr int kMaxPulses = 4;
+// A Gaussian pulse in base-2 units: exp(-u^2 / 2) = 2^(-(u k)^2), k = sqrt(log2(e) / 2).
+constexpr double kGaussBase2 = 0.84932180028801904272150283410289;
 constexpr int kMaxTones = SPINSIM_MAX_TONES;
 // A sample's L steps are split into 2^seg_log2 canonical segments (at most
 // kSegments) reduced by a fixed binary tree; the split depends on L alone.
@@ -118,6 +120,7 @@ struct DevSim {
     float f_ph[4], f_pl[4];
     float f_za, f_zb, f_zbias, f_qd3, f_dt, f_c1, f_c2, f_pad;
     float f_amp[kMaxPulses], f_invw[kMaxPulses];
+    float f_invwb[kMaxPulses];   // inv_w sqrt(log2(e) / 2): the Gaussian in base-2 units
     float f_tom_plus[kMaxTones], f_tom_minus[kMaxTones];
     // Quadrupole drives (full su(3), FP64 only): pair p on (D_xz, D_yz) (k = 1)
     // or (D_x2y2, D_xy) (k = 2), Om+-_p and the rates seen in the frame,

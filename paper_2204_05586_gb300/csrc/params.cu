@@ -285,6 +285,7 @@ void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K,
     for (int p = 0; p < f.n_pulses; p++) {
         d.f_amp[p] = (float)d.amp[p];
         d.f_invw[p] = (float)d.inv_w[p];
+        d.f_invwb[p] = (float)(d.inv_w[p] * kGaussBase2);
     }
 }
 
