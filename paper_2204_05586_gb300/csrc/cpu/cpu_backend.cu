@@ -80,7 +80,7 @@ void pack(const SampleCtx<float> (&c)[4], SampleCtx<F4>& v)
     auto put = [](F4& dst, float a, float b, float d, float e) { dst.v = F4::V{a, b, d, e}; };
 #define SPINSIM_PACK(f) put(v.f, c[0].f, c[1].f, c[2].f, c[3].f)
     SPINSIM_PACK(ebr); SPINSIM_PACK(ebi); SPINSIM_PACK(co); SPINSIM_PACK(counter);
-    for (int i = 0; i < 4; i++) { SPINSIM_PACK(Ph[i]); SPINSIM_PACK(Pl[i]); }
+    for (int i = 0; i < 4; i++) SPINSIM_PACK(Ph[i]);
     SPINSIM_PACK(za); SPINSIM_PACK(zb); SPINSIM_PACK(zbias); SPINSIM_PACK(qd3); SPINSIM_PACK(inv_n);
     SPINSIM_PACK(q1); SPINSIM_PACK(dt); SPINSIM_PACK(c1); SPINSIM_PACK(c2);
     SPINSIM_PACK(d1r); SPINSIM_PACK(d1i); SPINSIM_PACK(p1r); SPINSIM_PACK(p1i); SPINSIM_PACK(eqr); SPINSIM_PACK(eqi);

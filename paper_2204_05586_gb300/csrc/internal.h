@@ -115,9 +115,8 @@ struct DevSim {
     double t_om_plus[kMaxTones], t_om_minus[kMaxTones];
     double t_co0[kMaxTones], t_ct0[kMaxTones];
     double t_tay_co[kMaxTones][8], t_tay_ct[kMaxTones][8];
-    // The same constants rounded to FP32 once, on the host, for the FP32-bulk
-    // kernels (P as an FP32 (hi, lo) pair: hi = fl(P), lo = fl(P - hi)).
-    float f_ph[4], f_pl[4];
+    // The same constants rounded to FP32 once, on the host, for the FP32-bulk kernels.
+    float f_ph[4];
     float f_za, f_zb, f_zbias, f_qd3, f_dt, f_c1, f_c2, f_pad;
     float f_amp[kMaxPulses], f_invw[kMaxPulses];
     float f_invwb[kMaxPulses];   // inv_w sqrt(log2(e) / 2): the Gaussian in base-2 units

@@ -271,10 +271,7 @@ void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K,
         }
     for (int e = 0; e < 6; e++) d.psi0[e] = r.psi0[e];
     d.spin_x2 = r.spin_x2;
-    for (int i = 0; i < 4; i++) {
-        d.f_ph[i] = (float)d.P[i];
-        d.f_pl[i] = (float)(d.P[i] - (double)d.f_ph[i]);
-    }
+    for (int i = 0; i < 4; i++) d.f_ph[i] = (float)d.P[i];
     d.f_za = (float)d.za;
     d.f_zb = (float)d.zb;
     d.f_zbias = (float)d.zbias;
