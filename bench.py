@@ -58,9 +58,11 @@ def chain_flops_per_sample(spin_x2: int, run: int) -> float:
 L2_FLUSH_BYTES = 256 << 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one integrate launch
 # (profiles/integrate_kernel_spin_one_sensing.md, integrate_tones_kernel_multitone.md,
-# integrate_su3_kernel_su3.md);
-# the operators it writes stay in L2.
-INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 67328, ("multitone", "fp32"): 108800, ("su3", "fp64"): 969472}
+# integrate_su3_kernel_su3.md: the operators stay in L2; profiles/launches_sweep512.md:
+# a 512-simulation sweep's launch scaled by samples to the 4096-simulation sweep, whose
+# 12.7 GB of operators go to HBM)
+INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 70144, ("multitone", "fp32"): 108800, ("su3", "fp64"): 969472,
+                           ("sweep", "fp32"): 12530000000}
 
 
 def algorithmic_flops_per_step(spin_x2: int, tau: int, n_tones: int = 0) -> float:
