@@ -33,7 +33,7 @@ namespace {
 // the 2^seg_log2 canonical segments, merged by the fixed binary tree (a
 // finished pair of equal sub-trees merges, later on the left), then the
 // epilogue.  The integrate kernel's lane that owns all segments does the same.
-template <int N, typename R, int METHOD, bool SMALL, bool TONES, bool SU3 = false>
+template <int N, typename R, int METHOD, int SMALL, bool TONES, bool SU3 = false>
 void sample_operator(const DevSim& s, int64_t k, double* out)
 {
     using Res = typename ResType<N, R>::type;
@@ -114,7 +114,7 @@ void unpack(const Res2<F4>& v, int i, Res2<float>& x)
     x.b = cmk(lane(v.b.r, i), lane(v.b.i, i));
 }
 
-template <int N, int METHOD, bool SMALL, bool TONES>
+template <int N, int METHOD, int SMALL, bool TONES>
 void sample_operators4(const DevSim& s, int64_t k, double* out)
 {
     using Res = typename ResType<N, float>::type;
@@ -158,7 +158,7 @@ void sample_operators4(const DevSim& s, int64_t k, double* out)
 
 using SampleFn = void (*)(const DevSim&, int64_t, double*);
 
-template <int N, bool SMALL, bool TONES>
+template <int N, int SMALL, bool TONES>
 SampleFn pick_method4(int method)
 {
     switch (method) {
@@ -174,7 +174,8 @@ SampleFn pick_variant4(int method, int variant)
 {
     switch (variant) {
         case kVariantGeneral: return pick_method4<N, false, false>(method);
-        case kVariantSmall: return pick_method4<N, true, false>(method);
+        case kVariantSmall: return pick_method4<N, 1, false>(method);
+        case kVariantSmallSine: return pick_method4<N, 2, false>(method);
         case kVariantTones: return pick_method4<N, false, true>(method);
         default: return nullptr;
     }
@@ -187,7 +188,7 @@ SampleFn select_sample4_fn(int spin_x2, int precision, int method, int variant)
     return spin_x2 == 2 ? pick_variant4<3>(method, variant) : pick_variant4<2>(method, variant);
 }
 
-template <int N, typename R, bool SMALL, bool TONES>
+template <int N, typename R, int SMALL, bool TONES>
 SampleFn pick_method(int method)
 {
     switch (method) {
@@ -205,7 +206,10 @@ SampleFn pick_variant(int method, int variant)
         case kVariantGeneral: return pick_method<N, R, false, false>(method);
         case kVariantTones: return pick_method<N, R, false, true>(method);
         case kVariantSmall:
-            if constexpr (sizeof(R) == 4) return pick_method<N, R, true, false>(method);
+            if constexpr (sizeof(R) == 4) return pick_method<N, R, 1, false>(method);
+            else return nullptr;
+        case kVariantSmallSine:
+            if constexpr (sizeof(R) == 4) return pick_method<N, R, 2, false>(method);
             else return nullptr;
         case kVariantSU3:   // full su(3): spin-one, FP64
             if constexpr (N == 3 && sizeof(R) == 8) {

@@ -106,6 +106,7 @@ inline void small_sincos_m(F4 x, F4& sm, F4& cm)
 }
 
 inline F4 sine_cycle_cold(F4 u) { return lanewise(u, [](float x) { return sine_cycle_cold<float>(x); }); }
+inline F4 sine_cycle(F4 u) { return lanewise(u, [](float x) { return sine_cycle<float>(x); }); }
 
 inline void half_angle_terms(F4 t2, F4& fm, F4& g)
 {

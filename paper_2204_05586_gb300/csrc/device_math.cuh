@@ -238,14 +238,14 @@ SPINSIM_HD void small_sincos_m_tiny(R x, R& sm, R& cm)
     cm = x2 * fma(x2, R(1.0 / 24), R(-0.5));
 }
 
-template <typename R, bool SMALL>
+template <typename R, int SMALL>
 SPINSIM_HD void step_sincos(R x, R& s, R& c)
 {
     if constexpr (SMALL) small_sincos_tiny(x, s, c);
     else small_sincos(x, s, c);
 }
 
-template <typename R, bool SMALL>
+template <typename R, int SMALL>
 SPINSIM_HD void step_sincos_m(R x, R& sm, R& cm)
 {
     if constexpr (SMALL) small_sincos_m_tiny(x, sm, cm);
@@ -343,6 +343,13 @@ SPINSIM_HD R pulse_shape(bool sine, R u)
 #else
     return sin(R(kTwoPi) * u);
 #endif
+}
+
+// The sine-cycle shape inline (the small-angle variant with sine cycles).
+template <typename R>
+SPINSIM_HD R sine_cycle(R u)
+{
+    return pulse_shape<R>(true, u);
 }
 
 // The sine-cycle shape out of line: only requests with such pulses reach it,
@@ -753,7 +760,7 @@ SPINSIM_HD void drive_phasors_advance(DrivePhasors<R>& p)
     }
 }
 
-template <typename R, bool SMALL = false, bool TONES = false, bool SU3 = false, bool PH = false>
+template <typename R, int SMALL = false, bool TONES = false, bool SU3 = false, bool PH = false>
 SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f, const CounterPhasors<R>* ph = nullptr,
                          int node = 0, const DrivePhasors<R>* dp = nullptr)
 {
@@ -788,6 +795,17 @@ SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f, const Co
             if (p >= c.ng) break;
             const R ub = fma(tau, c.invwb[p], c.u0b[p]);
             z = fma(c.amp[p], exp2(-(ub * ub)) - c.ghat[p], z);
+        }
+        if constexpr (SMALL == 2) {
+            // the variant with single sine cycles (after the Gaussians), inline
+#pragma unroll
+            for (int p = 0; p < kMaxPulses; p++) {
+                if (p >= c.np) break;
+                if (p >= c.ng) {
+                    const R u = fma(tau, c.invw[p], c.u0[p]);
+                    z = fma(c.amp[p], sine_cycle(u) - c.ghat[p], z);
+                }
+            }
         }
     } else {
 #pragma unroll
@@ -1055,7 +1073,7 @@ SPINSIM_HD void res3_mul(const Res3<R>& A, const Res3<R>& B, Res3<R>& C)
 // expm_one_res_n takes 2^-tau and the first-order quadrupole coefficient
 // q1 = 3 qd3 2^tau precomputed (once per sample) and, with SMALL, uses the
 // small-angle series (all of h_0, h_1, h_2, Phi/2 bounded by 2^-6 on the host).
-template <typename R, bool SMALL = false>
+template <typename R, int SMALL = false>
 SPINSIM_HD void expm_one_res_n(R vx, R vy, R vz, R qd3, int tau, R inv_n, R q1, Res3<R>& e)
 {
     const R z = vz * inv_n;
@@ -1139,7 +1157,7 @@ SPINSIM_HD void expm_one_res_n(R vx, R vy, R vz, R qd3, int tau, R inv_n, R q1, 
     e.g[0] = vx; e.g[1] = vy; e.g[2] = vz; e.g[3] = q1;
 }
 
-template <typename R, bool SMALL = false>
+template <typename R, int SMALL = false>
 SPINSIM_HD void expm_one_res(R vx, R vy, R vz, R qd3, int tau, Res3<R>& e)
 {
     expm_one_res_n<R, SMALL>(vx, vy, vz, qd3, tau, ldexp(R(1), -tau), R(3) * ldexp(qd3, tau), e);
@@ -1469,7 +1487,7 @@ SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res3<R>& x)
     }
 }
 
-template <typename R, int METHOD, bool SMALL = false, bool TONES = false>
+template <typename R, int METHOD, int SMALL = false, bool TONES = false>
 SPINSIM_HD void step_res(const SampleCtx<R>& c, R lf, int tau, Res2<R>& x)
 {
     (void)tau;
@@ -1522,7 +1540,7 @@ SPINSIM_HD void step_apply_su3(const SampleCtx<R>& c, R lf, CounterPhasors<R>& p
     }
 }
 
-template <typename R, int METHOD, bool SMALL = false, bool TONES = false>
+template <typename R, int METHOD, int SMALL = false, bool TONES = false>
 SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X, DrivePhasors<R>* dp = nullptr)
 {
     NodeField<R> f1, f2;
@@ -1555,7 +1573,7 @@ SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X, Dri
     }
 }
 
-template <typename R, int METHOD, bool SMALL = false, bool TONES = false, bool SU3 = false>
+template <typename R, int METHOD, int SMALL = false, bool TONES = false, bool SU3 = false>
 SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res2<R>& X)
 {
     static_assert(!SU3, "quadrupole drives need spin one");

@@ -48,7 +48,7 @@ constexpr int kSlots = kSegLog2 + 1;
 // then finish one sample each (the FP64 epilogue).  No block barrier: while
 // one warp runs its FP64 epilogue, the others of its SM keep the FP32 pipes
 // busy.
-template <int N, typename R, int METHOD, bool SMALL, bool TONES, bool SU3 = false>
+template <int N, typename R, int METHOD, int SMALL, bool TONES, bool SU3 = false>
 __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
 {
     using Res = typename ResType<N, R>::type;
@@ -171,7 +171,7 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
 }
 
 // The general and small-angle variants.
-template <int N, typename R, int METHOD, bool SMALL>
+template <int N, typename R, int METHOD, int SMALL>
 __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
 {
     integrate_body<N, R, METHOD, SMALL, false>(a);
@@ -203,14 +203,14 @@ static void* su3_kernel_ptr()
 {
     return (void*)integrate_su3_kernel<METHOD>;
 }
-template <int N, typename R, int METHOD, bool SMALL, bool TONES>
+template <int N, typename R, int METHOD, int SMALL, bool TONES>
 static void* kernel_ptr()
 {
     if constexpr (TONES) return (void*)integrate_tones_kernel<N, R, METHOD>;
     else return (void*)integrate_kernel<N, R, METHOD, SMALL>;
 }
 
-template <int N, typename R, bool SMALL, bool TONES>
+template <int N, typename R, int SMALL, bool TONES>
 static void* pick_method(int method)
 {
     switch (method) {
@@ -228,9 +228,12 @@ static void* pick_variant(int method, int variant)
         case kVariantGeneral: return pick_method<N, R, false, false>(method);
         case kVariantTones: return pick_method<N, R, false, true>(method);
         case kVariantSmall:
-            // the small-angle variant exists for FP32-bulk only; FP64 keeps the
+            // the small-angle variants exist for FP32-bulk only; FP64 keeps the
             // general series (its terms are sized for double precision)
-            if constexpr (sizeof(R) == 4) return pick_method<N, R, true, false>(method);
+            if constexpr (sizeof(R) == 4) return pick_method<N, R, 1, false>(method);
+            else return nullptr;
+        case kVariantSmallSine:
+            if constexpr (sizeof(R) == 4) return pick_method<N, R, 2, false>(method);
             else return nullptr;
         case kVariantSU3:
             if constexpr (N == 3 && sizeof(R) == 8) {

@@ -299,18 +299,21 @@ constexpr double kTinyAngleBound = 0.015625;
 // sample/chunk/group offsets.
 void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L, DevSim& d);
 // small_angle_request: true when the request runs in FP32-bulk, has no
-// single-sine-cycle pulse and no further tone, and every argument of the
-// per-step sine/cosine series is bounded by kTinyAngleBound.
+// further tone, and every argument of the per-step sine/cosine series is
+// bounded by kTinyAngleBound (Gaussian and single-sine-cycle pulses alike).
 bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, int64_t L);
 
 // Integrate kernel variants: the general one; the small-angle one (FP32-bulk,
-// Gaussian pulses, no further tones; small_angle_request); and the one that
-// also evaluates further drive tones (requests with tones only, so the others
-// keep the leaner step loop); and the full su(3) one (quadrupole drives,
-// spin-one, FP64, tones included).  A batch runs one launch group per (spin,
-// variant), each request in the variant it needs on its own.
-enum IntegrateVariant { kVariantGeneral = 0, kVariantSmall = 1, kVariantTones = 2, kVariantSU3 = 3 };
-constexpr int kVariants = 4;
+// Gaussian pulses, no further tones; small_angle_request) and its twin that
+// also evaluates single-sine-cycle pulses (the paper's benchmark field; its
+// own kernel so that the Gaussian-only step loop does not carry that code);
+// the one that also evaluates further drive tones (requests with tones only,
+// so the others keep the leaner step loop); and the full su(3) one
+// (quadrupole drives, spin-one, FP64, tones included).  A batch runs one
+// launch group per (spin, variant), each request in the variant it needs on
+// its own.
+enum IntegrateVariant { kVariantGeneral = 0, kVariantSmall = 1, kVariantTones = 2, kVariantSU3 = 3, kVariantSmallSine = 4 };
+constexpr int kVariants = 5;
 constexpr int kMaxGroups = 2 * kVariants;   // launch groups of one batch: spin-half and spin-one
 // request_variant: the variant a validated request needs (kVariantSU3: its
 // quadrupole drives; FP64 only, see precision_status).

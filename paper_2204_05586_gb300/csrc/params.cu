@@ -129,7 +129,6 @@ bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, in
 {
     if (cfg.precision != SPINSIM_PREC_FP32_BULK || L < 1) return false;
     if (r.field.n_tones > 0 || r.field.qd_on) return false;
-    if (r.field.n_pulses > 0 && (r.field.pulse_sine_mask & ((1 << r.field.n_pulses) - 1)) != 0) return false;
     const MethodNodes m = method_nodes(cfg.method);
     const spinsim_field& f = r.field;
     const double dt = r.dt_out / (double)L;
@@ -150,7 +149,9 @@ int request_variant(const spinsim_config& cfg, const spinsim_request& r, int64_t
 {
     if (r.field.qd_on) return kVariantSU3;
     if (r.field.n_tones > 0) return kVariantTones;
-    return small_angle_request(cfg, r, L) ? kVariantSmall : kVariantGeneral;
+    if (!small_angle_request(cfg, r, L)) return kVariantGeneral;
+    const bool sine = r.field.n_pulses > 0 && (r.field.pulse_sine_mask & ((1 << r.field.n_pulses) - 1)) != 0;
+    return sine ? kVariantSmallSine : kVariantSmall;
 }
 
 int precision_status(const spinsim_config& cfg, const spinsim_request& r)

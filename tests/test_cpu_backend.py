@@ -79,6 +79,21 @@ def test_tones_and_pulse_kinds(oracle_mod, prec):
     check(out, oracle_run(oracle_mod, req), TOL[prec], "tones")
 
 
+@pytest.mark.parametrize("spin", [2, 1])
+def test_small_angle_sine_cycle_variant(oracle_mod, spin):
+    """The paper's benchmark field (a single sine cycle on J_z) in FP32-bulk takes
+    the small-angle kernel's twin with sine cycles; with a Gaussian beside the
+    cycle both pulse kinds meet in one step loop.  Against the oracle at the
+    FP32-bulk tolerance, both spins."""
+    for req in (W.neural_pulse(t_end=3e-3, t_p=1.2e-3, spin_x2=spin),
+                W.request(spin, W.field(bias_hz=700e3, drive_x_hz=2e3, drive_hz=700.1e3,
+                                        quad_hz=250.0 if spin == 2 else 0.0,
+                                        pulses=[(40.0, 0.6e-3, 0.2e-3), (70.0, 1.0e-3, 1e-3, "sine")]),
+                          0.0, 2.5e-3, 1e-7, 1e-6)):
+        (out,) = C.simulate([req], precision=S.PREC_FP32_BULK)
+        check(out, oracle_run(oracle_mod, req), 1e-5, f"small-angle sine cycles, spin_x2 {spin}")
+
+
 def test_batch_edge_cases_and_determinism(oracle_mod):
     """A batch with K = 0, K = 1, L = 1, L = 3, both spins, an invalid request
     and a short capacity: statuses as documented, every valid request equal

@@ -300,9 +300,10 @@ def test_tau0_closed_form_exponential(hh):
 
 
 def test_small_angle_rule_on_workloads(hh):
-    """The host picks the small-angle kernel for the rotating-frame FP32 runs
-    of every workload shape and refuses it for FP64, for the lab frame, for a
-    request with a single-sine-cycle pulse, and for a request whose step
+    """The host picks the small-angle kernels for the rotating-frame FP32 runs
+    of every workload shape, the paper's benchmark field with its
+    single-sine-cycle pulse included (the sine-cycle twin of the kernel), and
+    refuses them for FP64, for the lab frame and for a request whose step
     angles exceed the bound."""
     from paper_2204_05586_gb300 import spinsim as S, workloads as W
     def rule(req, **cfg):
@@ -316,7 +317,8 @@ def test_small_angle_rule_on_workloads(hh):
         assert rule(req) == 1
         assert rule(req, precision=S.PREC_FP64) == 0
     assert rule(W.spin_one_sensing(), rotating_frame=False) == 0
-    assert rule(W.neural_pulse()) == 0          # sine-cycle pulse: the general variant
+    assert rule(W.neural_pulse()) == 1          # sine-cycle pulse: the small-angle twin with sine cycles
+    assert rule(W.neural_pulse(), precision=S.PREC_FP64) == 0
     big = W.spin_one_sensing(dt=1e-7)           # 10x larger steps: still inside the bound
     assert rule(big) == 1
     far = W.spin_one_sensing()
