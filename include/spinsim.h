@@ -387,7 +387,8 @@ int spinsim_range_entering_state(int32_t spin_x2, const double* aggs, int32_t ra
  * that fell outside its buffer sets a bit of an error word on the device and
  * the access is skipped (no trap).  This call waits for the device's work,
  * writes the word of `device` into *word (0: every index was in range; bits
- * 0-1 integrate kernel, 8-15 chain kernels) and clears it.  The normal
+ * 0-1 integrate kernel, 2 drive phasor tables, 8-15 chain kernels) and
+ * clears it.  The normal
  * library has no checks: it writes 0 and returns SPINSIM_E_UNSUPPORTED.
  * The paper has no counterpart: this exists to test the kernels' indexing. */
 int spinsim_debug_bounds(int32_t device, uint64_t* word);

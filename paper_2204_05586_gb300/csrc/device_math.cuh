@@ -330,6 +330,48 @@ SPINSIM_HD double drive_phase_at(const DevSim& s, int64_t k)
     return tone_phase_at(s.drive_hz, s.drive_phase, s.t_start + (double)(k - 1) * s.dt_out);
 }
 
+// The fractional part of f (t0 + m dt) in cycles, to a few 1e-16: with
+// f dt = a + b and m a = p + q split exactly by FMA (Dekker's product), and
+// f t0 = c + d likewise, the fractional parts of the large terms p and c are
+// taken exactly and only the sum of two numbers below 1 and the small terms
+// is rounded.  Unlike tone_phase_at, the rounding does not grow with f t.
+SPINSIM_HD double drive_cycles_frac(double f, double t0, double dt, int64_t m)
+{
+    const double a = f * dt, b = fma(f, dt, -a);
+    const double md = (double)m;   // exact for |m| < 2^53
+    const double p = md * a, q = fma(md, a, -p);
+    const double c = f * t0, d = fma(f, t0, -c);
+    double x = (p - floor(p)) + (c - floor(c));
+    x += fma(md, b, q + d);
+    return x - floor(x);
+}
+
+// Entry e of a simulation's drive phasor tables (see kPhaseLo): the turn
+// e^{i 2 pi f_d dt_out e} for e < kPhaseLo, else e^{i beta} at interval
+// k - 1 = (e - kPhaseLo) kPhaseLo.
+SPINSIM_HD cx<double> drive_phasor_entry(const DevSim& s, int64_t e)
+{
+    const bool turn = e < kPhaseLo;
+    const double cyc = turn ? drive_cycles_frac(s.drive_hz, 0.0, s.dt_out, e)
+                            : drive_cycles_frac(s.drive_hz, s.t_start, s.dt_out, (e - kPhaseLo) << kPhaseLoLog2);
+    double b = kTwoPi * cyc + (turn ? 0.0 : s.drive_phase);
+    b -= kTwoPi * rint(b * (1.0 / kTwoPi));
+    const SinCos<double> sc = sincos_cold(b);
+    return cmk(sc.c, sc.s);
+}
+
+// e^{i beta_k} of interval k >= 1 from the tables (two roundings): the
+// epilogue's FP64 drive phasor.  (The bulk keeps its FP32 sine and cosine of
+// the drive phase: reading the table at the start of every tile measured
+// slower in the issue-bound step loop.)
+SPINSIM_HD cx<double> drive_phasor_tab(const DevSim& s, int64_t k)
+{
+    const int64_t m = k - 1;
+    const double* lo = s.eb_tab + 2 * (m & (kPhaseLo - 1));
+    const double* hi = s.eb_tab + 2 * (kPhaseLo + (m >> kPhaseLoLog2));
+    return cmul(cmk(hi[0], hi[1]), cmk(lo[0], lo[1]));
+}
+
 // Shape of z pulse p at u = (t - c_p) / w_p: a Gaussian exp(-u^2/2) (w_p the
 // standard deviation), or a single sine cycle sin(2 pi u) for 0 <= u < 1 and 0
 // elsewhere (w_p the period; the paper's sinp pulse, Eq. neural_pulse).
@@ -488,7 +530,8 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
 }
 
 // FP64 quantities of interval k used once per sample by the epilogue, from
-// the drive phase beta and gsum that make_ctx returned: e^{i beta}, the frame
+// the drive phase beta (or the drive phasor tables, when the simulation has
+// them) and gsum that make_ctx returned: e^{i beta}, the frame
 // frequencies and the exit phasor
 // e^{-i w_r dt_out} (x 1/2 for spin-half).
 //
@@ -500,9 +543,15 @@ SPINSIM_HD double make_ctx(const DevSim& s, int64_t k, SampleCtx<R>& c, double& 
 template <int N, bool TONES = false>
 SPINSIM_HD void make_exact(const DevSim& s, int64_t k, double beta, double gsum, SampleExact& x)
 {
-    const SinCos<double> eb = sincos_cold(beta);
-    x.eb_re = eb.c;
-    x.eb_im = eb.s;
+    if (s.eb_tab) {
+        const cx<double> eb = drive_phasor_tab(s, k);
+        x.eb_re = eb.r;
+        x.eb_im = eb.i;
+    } else {
+        const SinCos<double> eb = sincos_cold(beta);
+        x.eb_re = eb.c;
+        x.eb_im = eb.s;
+    }
     x.gsum = gsum;
     if constexpr (TONES) {
         const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;

@@ -197,6 +197,38 @@ __global__ void __launch_bounds__(256) integrate_su3_kernel(IntegrateArgs a)
     integrate_body<3, double, METHOD, false, true, true>(a);
 }
 
+// The drive phasor tables of a launch group, one thread per entry: the
+// simulation that owns entry j is the last one whose first entry is at most j
+// (simulations with no entries share their successor's offset).
+__global__ void __launch_bounds__(256) phase_table_kernel(const DevSim* sims, int n_sims, int64_t n_entries,
+                                                          double* tab)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_entries; j += stride) {
+        int lo = 0, hi = n_sims - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sims[mid].eb_off <= j) lo = mid;
+            else hi = mid - 1;
+        }
+        const DevSim& s = sims[lo];
+        const int64_t e = j - s.eb_off;
+        if (!SPINSIM_INB(e >= 0, 2) || e >= phase_entries(s.K)) continue;   // past the last entry (layout slack)
+        const cx<double> v = drive_phasor_entry(s, e);
+        tab[2 * j] = v.r;
+        tab[2 * j + 1] = v.i;
+    }
+}
+
+cudaError_t launch_phase_table(const DevSim* sims, int n_sims, int64_t n_entries, double* tab, int n_sm,
+                               cudaStream_t stream)
+{
+    if (n_entries <= 0 || n_sims <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n_entries + 255) / 256, (int64_t)std::max(n_sm, 1) * 8);
+    phase_table_kernel<<<(unsigned)blocks, 256, 0, stream>>>(sims, n_sims, n_entries, tab);
+    return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------- launchers
 template <int METHOD>
 static void* su3_kernel_ptr()

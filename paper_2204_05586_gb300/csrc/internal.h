@@ -62,6 +62,22 @@ inline ChainGeom chain_geom(int64_t K)
     return g;
 }
 
+// Drive phasor tables (GPU path): the FP64 drive phasor of interval k,
+// e^{i beta_k} with beta_k the drive phase at t_{k-1}, is the product of two
+// table entries, hi[(k - 1) >> kPhaseLoLog2] (the phasor at every kPhaseLo-th
+// interval) and lo[(k - 1) & (kPhaseLo - 1)] (the turn over the remaining
+// intervals), instead of a sine and cosine per sample.  Entries of one
+// simulation: the kPhaseLo turns, then the hi phasors.
+constexpr int kPhaseLoLog2 = 7;
+constexpr int kPhaseLo = 1 << kPhaseLoLog2;
+__host__ __device__ inline int64_t phase_entries(int64_t K) { return K >= 2 ? kPhaseLo + ((K - 2) >> kPhaseLoLog2) + 1 : 0; }
+// An upper bound of the entries of `count` simulations with `samples` samples
+// in all (the arena layout of a group).
+inline int64_t phase_entries_bound(int64_t count, int64_t samples)
+{
+    return count * (kPhaseLo + 1) + samples / kPhaseLo;
+}
+
 // Per-simulation parameters on the device, precomputed on the host in FP64.
 struct DevSim {
     double* states;              // [K][N] complex, device
@@ -69,6 +85,10 @@ struct DevSim {
     double* ops;                 // [K][N][N] complex or nullptr
     int64_t K, L;
     int64_t sample_offset;       // first sample of this simulation in the operator buffer
+    // drive phasor tables of this simulation, (re, im) pairs in FP64
+    // (nullptr: a sine and cosine of the drive phase per sample instead)
+    const double* eb_tab;
+    int64_t eb_off;              // first entry of this simulation in its launch group's table
     int32_t chain_run;           // samples per lane run at the bottom of the chain tree
     int32_t chain_top;           // level of the chain tree's top node
     int32_t seg_log2;            // the sample's L steps in 2^seg_log2 canonical segments
@@ -339,6 +359,10 @@ cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, 
                              const IntegrateArgs& a, cudaStream_t stream);
 size_t integrate_smem_bytes(int spin_x2, int precision, int block);
 cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int block, int variant, int* blocks_per_sm);
+// launch_phase_table: fill the drive phasor tables of `n_sims` simulations
+// (their eb_off ascending; `n_entries` in all) at tab, on `stream`.
+cudaError_t launch_phase_table(const DevSim* sims, int n_sims, int64_t n_entries, double* tab, int n_sm,
+                               cudaStream_t stream);
 // integrate_tiles: the tile plan of `total` samples for bulk lanes per sample
 // `lanes_bulk` (1, 2, 4 or 8, at most 2^min_seg_log2), `block` threads and
 // `wave_blocks` resident blocks; the tail uses 2^min_seg_log2 lanes per sample,

@@ -67,6 +67,8 @@ struct Group {
     int levels = 1;                // chain-tree levels of the tallest simulation
     int64_t nodes[kMaxLevels] = {};  // chain-tree nodes per level, all simulations
     size_t sims_off = 0, soff_off = 0, loff_off = 0, counter_off = 0, U_off = 0, chain_off = 0;
+    size_t phase_off = 0;                   // drive phasor tables (FP64 pairs)
+    int64_t phase_n = 0;                    // their entries, all simulations of the group
     ChainLayout chain{};
 };
 
@@ -296,11 +298,14 @@ size_t table_bytes(int64_t n, int levels)
 }
 
 // Scratch bytes of one group (spin) of a batch.
-size_t group_bytes(int spin_x2, int64_t n, int64_t samples, const int64_t* nodes, int levels)
+// The drive phasor tables of `entries` entries: FP64 (re, im) pairs.
+size_t phase_bytes(int64_t entries) { return round_up((size_t)entries * 2 * sizeof(double), 256); }
+
+size_t group_bytes(int spin_x2, int64_t n, int64_t samples, const int64_t* nodes, int levels, int64_t phase_n)
 {
     const size_t opb = (size_t)op_doubles(spin_x2) * sizeof(double);
     return table_bytes(n, levels) + 256 /* tile counter */ + round_up((size_t)samples * opb, 256) +
-           chain_layout(spin_x2, nodes, levels).bytes;
+           phase_bytes(phase_n) + chain_layout(spin_x2, nodes, levels).bytes;
 }
 
 // Where the kernels can write an output: 16-byte aligned device memory as it
@@ -349,7 +354,7 @@ size_t staging_bytes(const spinsim_request& r, const spinsim_result& res, int64_
 // (spin, kernel variant) as build_plan forms them, plus the staged outputs.
 // total() is the plan.total build_plan gives the same batch.
 struct Footprint {
-    int64_t count[kMaxGroups] = {}, samples[kMaxGroups] = {};
+    int64_t count[kMaxGroups] = {}, samples[kMaxGroups] = {}, phase[kMaxGroups] = {};
     int64_t nodes[kMaxGroups][kMaxLevels] = {};
     int levels[kMaxGroups];
     size_t staged = 0;
@@ -362,6 +367,7 @@ struct Footprint {
         const int g = (spin_x2 - 1) * kVariants + variant;
         count[g] += 1;
         samples[g] += K;
+        phase[g] += phase_entries(K);
         const ChainGeom cg = chain_geom(K);
         levels[g] = std::max(levels[g], cg.top + 1);
         for (int l = 0; l <= cg.top; l++) nodes[g][l] += cg.nodes[l];
@@ -371,7 +377,7 @@ struct Footprint {
     {
         size_t t = staged;
         for (int g = 0; g < kMaxGroups; g++)
-            if (count[g]) t += group_bytes(1 + g / kVariants, count[g], samples[g], nodes[g], levels[g]);
+            if (count[g]) t += group_bytes(1 + g / kVariants, count[g], samples[g], nodes[g], levels[g], phase[g]);
         return std::max<size_t>(t, 256);
     }
 };
@@ -401,6 +407,7 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
             if (checked[i].status == SPINSIM_OK && reqs[i].spin_x2 == spin && checked[i].variant == variant) {
                 g.idx.push_back(i);
                 g.samples += checked[i].K;
+                g.phase_n += phase_entries(checked[i].K);
                 g.steps += (double)checked[i].K * (double)checked[i].L;
                 g.min_seg_log2 = std::min(g.min_seg_log2, seg_log2_of(checked[i].L));
                 const ChainGeom cg = chain_geom(checked[i].K);
@@ -416,6 +423,7 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
         off += table_bytes(m, g.levels);
         g.counter_off = off; off += 256;
         g.U_off = off; off += round_up((size_t)g.samples * opb, 256);
+        g.phase_off = off; off += phase_bytes(g.phase_n);
         g.chain = chain_layout(spin, g.nodes, g.levels);
         g.chain_off = off; off += g.chain.bytes;
         pin += table_bytes(m, g.levels);
@@ -463,7 +471,7 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
         int64_t* soff = reinterpret_cast<int64_t*>(pinned + pin + (g.soff_off - g.sims_off));
         int64_t* loff = reinterpret_cast<int64_t*>(pinned + pin + (g.loff_off - g.sims_off));
         pin += table_bytes(m, g.levels);
-        int64_t so = 0;
+        int64_t so = 0, eo = 0;
         int64_t lo[kMaxLevels] = {};
         for (int64_t q = 0; q < m; q++) {
             const int64_t i = g.idx[q];
@@ -482,6 +490,9 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
             d.sample_offset = so;
             soff[q] = so;
             so += d.K;
+            d.eb_tab = reinterpret_cast<const double*>(base + g.phase_off) + 2 * eo;
+            d.eb_off = eo;
+            eo += phase_entries(d.K);
             const ChainGeom cg = chain_geom(d.K);
             d.chain_run = cg.run;
             d.chain_top = cg.top;
@@ -711,6 +722,13 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
                 if (st != SPINSIM_OK) return st;
                 if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
                     return SPINSIM_E_CUDA;
+                if (g.phase_n > 0) {
+                    if (inject_launch_failure(h) ||
+                        launch_phase_table(ia.sims, (int)m, g.phase_n, reinterpret_cast<double*>(base + g.phase_off),
+                                           h->n_sm, stream) != cudaSuccess)
+                        return SPINSIM_E_CUDA;
+                    kernels += 1;
+                }
                 if (pg >= 0) prof_record(h->prof[pg][0]);
                 if (inject_launch_failure(h) ||
                     launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, block, grid, g.variant, ia, stream) !=

@@ -164,6 +164,8 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     const size_t loff_off = off; off += up256(kMaxLevels * 2 * sizeof(int64_t));
     const size_t counter_off = off; off += 256;
     const size_t U_off = off; off += up256((size_t)K * opd * 8);
+    const int64_t phase_n = phase_entries(K);
+    const size_t phase_off = off; off += up256((size_t)phase_n * 2 * sizeof(double));
     const size_t chain_off = off; off += cl.bytes;
     if (off > kStaticScratchBytes) return res->status = SPINSIM_E_NOMEM;   // K beyond the static maximum
 
@@ -174,6 +176,8 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     d.spin = res->spin;
     d.ops = res->ops;
     d.sample_offset = 0;
+    d.eb_tab = reinterpret_cast<const double*>(base + phase_off);
+    d.eb_off = 0;
     d.chain_run = cg.run;
     d.chain_top = cg.top;
     const int variant = request_variant(*cfg, *req, L);
@@ -202,6 +206,9 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
             cudaGetLastError();
             return res->status = SPINSIM_E_CUDA;
         }
+        if (launch_phase_table(reinterpret_cast<const DevSim*>(base + sims_off), 1, phase_n,
+                               reinterpret_cast<double*>(base + phase_off), n_sm, stream) != cudaSuccess)
+            return res->status = SPINSIM_E_CUDA;
         IntegrateArgs ia;
         ia.sims = reinterpret_cast<const DevSim*>(base + sims_off);
         ia.sample_offsets = reinterpret_cast<const int64_t*>(base + soff_off);

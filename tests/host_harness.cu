@@ -1,5 +1,6 @@
 // Host build of the kernels' per-thread arithmetic (device_math.cuh), so the
 // CPU test-suite can check it against the oracle and scipy without a GPU.
+#include <vector>
 #include <cstdint>
 #include "../paper_2204_05586_gb300/csrc/device_math.cuh"
 
@@ -162,6 +163,37 @@ void hh_first_order(const spinsim_config* cfg, const spinsim_request* r, int64_t
     out[1] = gy;
     out[2] = gsum;
 }
+// The fractional drive cycles f (t0 + m dt) (drive_cycles_frac).
+double hh_drive_cycles_frac(double f, double t0, double dt, int64_t m) { return drive_cycles_frac(f, t0, dt, m); }
+
+// The FP64 drive phasor e^{i beta_k} of interval k of a request, from the
+// two-level tables the integrate epilogue reads (built here on the host by
+// drive_phasor_entry, read by drive_phasor_tab; table = 1), or from the drive
+// phase and a sine and cosine (table = 0): out = (re, im).
+void hh_drive_phasor(const spinsim_config* cfg, const spinsim_request* r, int64_t K, int64_t L, int64_t k, int table,
+                     double* out)
+{
+    DevSim d;
+    fill_devsim(*cfg, *r, K, L, d);
+    if (table) {
+        const int64_t n = phase_entries(K);
+        std::vector<double> tab((size_t)(2 * n));
+        for (int64_t e = 0; e < n; e++) {
+            const cx<double> v = drive_phasor_entry(d, e);
+            tab[(size_t)(2 * e)] = v.r;
+            tab[(size_t)(2 * e + 1)] = v.i;
+        }
+        d.eb_tab = tab.data();
+        const cx<double> v = drive_phasor_tab(d, k);
+        out[0] = v.r;
+        out[1] = v.i;
+    } else {
+        const SinCos<double> e = sincos_cold(drive_phase_at(d, k));
+        out[0] = e.c;
+        out[1] = e.s;
+    }
+}
+
 // rest part only (U - I - F(v)) in double
 void hh_expm_one_rest(double vx, double vy, double vz, double vq, int tau, double* out)
 {

@@ -45,6 +45,10 @@ def hh(tmp_path_factory):
     L.hh_small_angle_request.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
     L.hh_tiny_angle_bound.restype = ctypes.c_double
     L.hh_first_order.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, DP]
+    L.hh_drive_cycles_frac.restype = ctypes.c_double
+    L.hh_drive_cycles_frac.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int64]
+    L.hh_drive_phasor.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_int, DP]
     L.hh_series_match.argtypes = [ctypes.c_double, ctypes.c_int]
     L.hh_expm_general.argtypes = [DP, DP]
     L.hh_expm_general_rest.argtypes = [DP, DP]
@@ -421,3 +425,76 @@ def test_general_exponential_degree_choice(hh):
             ref = np.array([[complex(refm[i, j]) for j in range(3)] for i in range(3)])
             assert np.abs(rest - ref).max() < 1e-15 * max(theta, theta ** 2), theta
 
+
+
+def exact_cycles(f, t0, dt, m):
+    """frac(f (t0 + m dt)) of the binary values f, t0, dt, in exact rational
+    arithmetic."""
+    from fractions import Fraction as Fr
+    x = Fr(f) * (Fr(t0) + m * Fr(dt))
+    return x - (x.numerator // x.denominator)
+
+
+def cyc_dist(a, b):
+    d = abs(float(a) - float(b)) % 1.0
+    return min(d, 1.0 - d)
+
+
+def test_drive_cycles_are_exact_to_rounding(hh):
+    """The drive phase's fractional cycles at t0 + m dt, split by Dekker
+    products, equal the exact rational value to a few 1e-16 cycles at every
+    size of f t, where the plain product f t loses about 2^-53 f t."""
+    rng = np.random.default_rng(17)
+    worst, worst_plain = 0.0, 0.0
+    for _ in range(400):
+        f = float(rng.uniform(1e5, 3e6))
+        t0 = float(rng.choice([0.0, rng.uniform(-1e-2, 0.2)]))
+        dt = float(rng.choice([1e-6, 1e-7, 2.5e-7, rng.uniform(1e-8, 1e-5)]))
+        m = int(rng.integers(0, 10**7))
+        ex = exact_cycles(f, t0, dt, m)
+        got = hh.hh_drive_cycles_frac(f, t0, dt, m)
+        assert 0.0 <= got < 1.0
+        worst = max(worst, cyc_dist(got, ex))
+        ft = f * (t0 + m * dt)
+        worst_plain = max(worst_plain, cyc_dist(ft - np.floor(ft), ex))
+    assert worst < 5e-16, worst
+    assert worst_plain > 1e-13   # what the split avoids
+    # special cases: no drive, m = 0, t0 = 0
+    assert hh.hh_drive_cycles_frac(0.0, 0.3, 1e-6, 12345) == 0.0
+    assert cyc_dist(hh.hh_drive_cycles_frac(7e5, 0.0, 1e-6, 0), 0) == 0.0
+    assert cyc_dist(hh.hh_drive_cycles_frac(7e5 + 0.25, 0.0, 1.0, 3), exact_cycles(7e5 + 0.25, 0.0, 1.0, 3)) == 0.0
+
+
+@pytest.mark.parametrize("K", [2, 129, 100001])
+def test_drive_phasor_tables_match_the_exact_phasor(hh, K):
+    """e^{i beta_k} from the two-level tables (every interval, both table
+    edges, the last) against the exact phase and 30-digit sin/cos: within
+    1.5e-15 (the roundings of 2 pi cyc + phase and of its reduction, the
+    sine and cosine, the product: a few 2^-53 each), where the sine and
+    cosine of the FP64 drive phase err by the phase's rounding, which grows
+    with f t."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    from paper_2204_05586_gb300 import spinsim as S, workloads as W
+    f = W.field(bias_hz=700e3, drive_x_hz=2e3, drive_hz=700.7e3, drive_phase=1.1, quad_hz=400.0)
+    dt_out = 1e-6
+    req = W.request(2, f, 3e-3, 3e-3 + K * dt_out, 1e-8, dt_out)
+    cfg = S.make_config(precision=S.PREC_FP64)
+    r = S.make_request(req)
+    assert S.spinsim_counts(r)[1] == K
+    ks = sorted({1, 2, min(128, K - 1), min(129, K - 1), min(130, K - 1), K - 1, K // 2 + 1})
+    rng = np.random.default_rng(3)
+    ks += [int(x) for x in rng.integers(1, K, 20)]
+    worst_tab, worst_sin = 0.0, 0.0
+    for k in ks:
+        out = np.zeros(4)
+        hh.hh_drive_phasor(ctypes.addressof(cfg), ctypes.addressof(r), K, 100, k, 1, P(out))
+        cyc = exact_cycles(f["drive_hz"], req["t_start"], dt_out, k - 1)
+        b = 2 * mpmath.pi * mpmath.mpf(cyc.numerator) / cyc.denominator + f["drive_phase"]
+        ex = complex(mpmath.cos(b), mpmath.sin(b))
+        worst_tab = max(worst_tab, abs(complex(out[0], out[1]) - ex))
+        old = np.zeros(4)
+        hh.hh_drive_phasor(ctypes.addressof(cfg), ctypes.addressof(r), K, 100, k, 0, P(old))
+        worst_sin = max(worst_sin, abs(complex(old[0], old[1]) - ex))
+    assert worst_tab < 1.5e-15, worst_tab
+    assert worst_sin < 1e-10, worst_sin
