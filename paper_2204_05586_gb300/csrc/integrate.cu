@@ -135,7 +135,9 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
         }
         __syncwarp();
         // epilogue, one lane per sample of the tile: the lanes' sub-trees
-        // combined in the canonical tree, then the FP64 part
+        // combined in the canonical tree, then the FP64 part (which reads the
+        // drive phasor tables: their kernel has completed after this wait)
+        grid_dependency_wait();
         if (wl < spw) {
             const int t = wl;
             const int64_t gs = base + t;
@@ -203,6 +205,9 @@ __global__ void __launch_bounds__(256) integrate_su3_kernel(IntegrateArgs a)
 __global__ void __launch_bounds__(256) phase_table_kernel(const DevSim* sims, int n_sims, int64_t n_entries,
                                                           double* tab)
 {
+    // the integrate kernel that follows may be scheduled at once (it waits
+    // for this grid before its epilogue reads the tables)
+    allow_dependent_launch();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_entries; j += stride) {
         int lo = 0, hi = n_sims - 1;
@@ -335,7 +340,7 @@ void integrate_tiles(int64_t total, int lanes_bulk, int block, int64_t wave_bloc
 }
 
 cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, int grid, int variant,
-                             const IntegrateArgs& a, cudaStream_t stream)
+                             const IntegrateArgs& a, cudaStream_t stream, bool after_phase_table)
 {
     void* k = select_kernel(spin_x2, precision, method, variant);
     if (!k || block % 32 != 0 || block < 32 || block > 256 || grid < 1 || a.lg_bulk < 0 || a.lg_bulk > kSegLog2 ||
@@ -344,7 +349,21 @@ cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, 
     size_t smem = integrate_smem_bytes(spin_x2, precision, block);
     IntegrateArgs args = a;
     void* params[] = {&args};
-    return cudaLaunchKernel(k, dim3(grid), dim3(block), params, smem, stream);
+    if (!after_phase_table) return cudaLaunchKernel(k, dim3(grid), dim3(block), params, smem, stream);
+    // a programmatic dependent launch of the drive phasor tables' kernel: the
+    // step loops start while the tables are filled; the epilogue, which reads
+    // them, waits for that kernel first (griddepcontrol.wait)
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, k, params);
 }
 
 #ifdef SPINSIM_BOUNDS

@@ -354,9 +354,11 @@ Checked check_request(const spinsim_request* r);
 
 // Host-side launchers (integrate.cu, chain.cu).  precision: 0 FP64, 1 FP32-bulk;
 // variant: an IntegrateVariant (kVariantSmall for FP32-bulk only).
-// launch_integrate: `a` must carry the tile plan of integrate_tiles.
+// launch_integrate: `a` must carry the tile plan of integrate_tiles;
+// `after_phase_table`: the drive phasor tables' kernel is the stream's last
+// launch (the integrate kernel then overlaps it, see launch_integrate).
 cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, int grid, int variant,
-                             const IntegrateArgs& a, cudaStream_t stream);
+                             const IntegrateArgs& a, cudaStream_t stream, bool after_phase_table = false);
 size_t integrate_smem_bytes(int spin_x2, int precision, int block);
 cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int block, int variant, int* blocks_per_sm);
 // launch_phase_table: fill the drive phasor tables of `n_sims` simulations

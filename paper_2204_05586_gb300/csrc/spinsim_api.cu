@@ -722,6 +722,9 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
                 if (st != SPINSIM_OK) return st;
                 if (cudaMemsetAsync(ia.tile_counter, 0, sizeof(unsigned long long), stream) != cudaSuccess)
                     return SPINSIM_E_CUDA;
+                // the integrate time includes the drive phasor tables' kernel,
+                // which it overlaps (nothing may stand between the two launches)
+                if (pg >= 0) prof_record(h->prof[pg][0]);
                 if (g.phase_n > 0) {
                     if (inject_launch_failure(h) ||
                         launch_phase_table(ia.sims, (int)m, g.phase_n, reinterpret_cast<double*>(base + g.phase_off),
@@ -729,9 +732,9 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
                         return SPINSIM_E_CUDA;
                     kernels += 1;
                 }
-                if (pg >= 0) prof_record(h->prof[pg][0]);
                 if (inject_launch_failure(h) ||
-                    launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, block, grid, g.variant, ia, stream) !=
+                    launch_integrate(g.spin_x2, h->cfg.precision, h->cfg.method, block, grid, g.variant, ia, stream,
+                                     g.phase_n > 0) !=
                         cudaSuccess)
                     return SPINSIM_E_CUDA;
                 kernels += 1;

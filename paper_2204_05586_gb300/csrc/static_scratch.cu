@@ -222,7 +222,8 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         integrate_tiles(K, lanes, block, wave_blocks, seg_log2_of(L), ia);
         const int grid =
             (int)std::max<int64_t>(1, std::min<int64_t>((ia.n_tiles + block / 32 - 1) / (block / 32), wave_blocks));
-        if (launch_integrate(spin, cfg->precision, cfg->method, block, grid, variant, ia, stream) != cudaSuccess)
+        if (launch_integrate(spin, cfg->precision, cfg->method, block, grid, variant, ia, stream, phase_n > 0) !=
+            cudaSuccess)
             return res->status = SPINSIM_E_CUDA;
         ChainArgs ca;
         ca.sims = ia.sims;
