@@ -174,8 +174,11 @@ SampleFn pick_variant4(int method, int variant)
 {
     switch (variant) {
         case kVariantGeneral: return pick_method4<N, false, false>(method);
-        case kVariantSmall: return pick_method4<N, 1, false>(method);
-        case kVariantSmallSine: return pick_method4<N, 2, false>(method);
+        // the tau = 0 variants run the same arithmetic with tau taken at run time
+        case kVariantSmall:
+        case kVariantSmallTau0: return pick_method4<N, 1, false>(method);
+        case kVariantSmallSine:
+        case kVariantSmallSineTau0: return pick_method4<N, 2, false>(method);
         case kVariantTones: return pick_method4<N, false, true>(method);
         default: return nullptr;
     }
@@ -206,9 +209,11 @@ SampleFn pick_variant(int method, int variant)
         case kVariantGeneral: return pick_method<N, R, false, false>(method);
         case kVariantTones: return pick_method<N, R, false, true>(method);
         case kVariantSmall:
+        case kVariantSmallTau0:
             if constexpr (sizeof(R) == 4) return pick_method<N, R, 1, false>(method);
             else return nullptr;
         case kVariantSmallSine:
+        case kVariantSmallSineTau0:
             if constexpr (sizeof(R) == 4) return pick_method<N, R, 2, false>(method);
             else return nullptr;
         case kVariantSU3:   // full su(3): spin-one, FP64
@@ -383,7 +388,7 @@ int cpu_simulate(const spinsim_config* cfg_in, const spinsim_request* reqs, spin
         Job j;
         j.req = i;
         fill_devsim(cfg, reqs[i], c.K, c.L, j.d);
-        const int variant = request_variant(cfg, reqs[i], c.L);
+        const int variant = request_variant(cfg, reqs[i], c.K, c.L);
         j.fn = select_sample_fn(reqs[i].spin_x2, cfg.precision, cfg.method, variant);
         j.fn4 = select_sample4_fn(reqs[i].spin_x2, cfg.precision, cfg.method, variant);
         j.u_off = 0;

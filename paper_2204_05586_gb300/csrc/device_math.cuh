@@ -845,7 +845,7 @@ SPINSIM_HD void field_at(const SampleCtx<R>& c, R tau, NodeField<R>& f, const Co
             const R ub = fma(tau, c.invwb[p], c.u0b[p]);
             z = fma(c.amp[p], exp2(-(ub * ub)) - c.ghat[p], z);
         }
-        if constexpr (SMALL == 2) {
+        if constexpr ((SMALL & kSmallSine) != 0) {
             // the variant with single sine cycles (after the Gaussians), inline
 #pragma unroll
             for (int p = 0; p < kMaxPulses; p++) {
@@ -1601,8 +1601,11 @@ SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X, Dri
     exponent<R, TONES>(c, f1, f2, false, vx, vy, vz);
     if (METHOD == 0) exponent<R, TONES>(c, f1, f2, true, wx, wy, wz);
     Res3<R> e, Y;
-    if constexpr (SMALL) {
-        // small angles: tau = 0 in closed form (the common case), else the squarings
+    if constexpr ((SMALL & kSmallTau0) != 0) {
+        // tau = 0 known at compile time: the closed form only
+        expm_one_res_tau0(vx, vy, vz, c, e);
+    } else if constexpr (SMALL) {
+        // small angles: tau = 0 in closed form, else the squarings
         if (tau == 0) expm_one_res_tau0(vx, vy, vz, c, e);
         else expm_one_res_n<R, SMALL>(vx, vy, vz, c.qd3, tau, c.inv_n, c.q1, e);
     } else {
@@ -1610,7 +1613,9 @@ SPINSIM_HD void step_apply(const SampleCtx<R>& c, R lf, int tau, Res3<R>& X, Dri
     }
     res3_mul(e, X, Y);
     if (METHOD == 0) {
-        if constexpr (SMALL) {
+        if constexpr ((SMALL & kSmallTau0) != 0) {
+            expm_one_res_tau0(wx, wy, wz, c, e);
+        } else if constexpr (SMALL) {
             if (tau == 0) expm_one_res_tau0(wx, wy, wz, c, e);
             else expm_one_res_n<R, SMALL>(wx, wy, wz, c.qd3, tau, c.inv_n, c.q1, e);
         } else {

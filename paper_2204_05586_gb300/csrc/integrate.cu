@@ -179,6 +179,15 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
     integrate_body<N, R, METHOD, SMALL, false>(a);
 }
 
+// The small-angle variants with single sine cycles, held to 128 registers
+// (two 256-thread blocks per SM): at tau = 0 the compiler otherwise takes 164
+// and one block fits.
+template <int N, typename R, int METHOD, int SMALL>
+__global__ void __launch_bounds__(256, 2) integrate_sine_kernel(IntegrateArgs a)
+{
+    integrate_body<N, R, METHOD, SMALL, false>(a);
+}
+
 // The variant with further drive tones; in FP32 held to 128 registers (two
 // 256-thread blocks per SM): uncapped it takes 152 and three 128-thread blocks
 // fit, and the fourth block's latency hiding is worth more than the few
@@ -244,6 +253,7 @@ template <int N, typename R, int METHOD, int SMALL, bool TONES>
 static void* kernel_ptr()
 {
     if constexpr (TONES) return (void*)integrate_tones_kernel<N, R, METHOD>;
+    else if constexpr ((SMALL & kSmallSine) != 0) return (void*)integrate_sine_kernel<N, R, METHOD, SMALL>;
     else return (void*)integrate_kernel<N, R, METHOD, SMALL>;
 }
 
@@ -271,6 +281,13 @@ static void* pick_variant(int method, int variant)
             else return nullptr;
         case kVariantSmallSine:
             if constexpr (sizeof(R) == 4) return pick_method<N, R, 2, false>(method);
+            else return nullptr;
+        case kVariantSmallTau0:
+            // spin-one only (spin-half has no squarings to specialise away)
+            if constexpr (N == 3 && sizeof(R) == 4) return pick_method<N, R, kSmallGauss | kSmallTau0, false>(method);
+            else return nullptr;
+        case kVariantSmallSineTau0:
+            if constexpr (N == 3 && sizeof(R) == 4) return pick_method<N, R, kSmallSine | kSmallTau0, false>(method);
             else return nullptr;
         case kVariantSU3:
             if constexpr (N == 3 && sizeof(R) == 8) {

@@ -332,12 +332,29 @@ bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, in
 // (quadrupole drives, spin-one, FP64, tones included).  A batch runs one
 // launch group per (spin, variant), each request in the variant it needs on
 // its own.
-enum IntegrateVariant { kVariantGeneral = 0, kVariantSmall = 1, kVariantTones = 2, kVariantSU3 = 3, kVariantSmallSine = 4 };
-constexpr int kVariants = 5;
+// The small-angle variants of spin-one requests whose Lie-Trotter squarings
+// come out as tau = 0 (the usual case in the rotating frame) have kernels of
+// their own, with the closed-form exponential and no runtime tau branch in the
+// step loop.
+enum IntegrateVariant {
+    kVariantGeneral = 0,
+    kVariantSmall = 1,
+    kVariantTones = 2,
+    kVariantSU3 = 3,
+    kVariantSmallSine = 4,
+    kVariantSmallTau0 = 5,
+    kVariantSmallSineTau0 = 6
+};
+constexpr int kVariants = 7;
 constexpr int kMaxGroups = 2 * kVariants;   // launch groups of one batch: spin-half and spin-one
-// request_variant: the variant a validated request needs (kVariantSU3: its
-// quadrupole drives; FP64 only, see precision_status).
-int request_variant(const spinsim_config& cfg, const spinsim_request& r, int64_t L);
+// The kernels' SMALL template argument: 0 general series; bit 0 the
+// small-angle series with Gaussian pulses, bit 1 with single sine cycles as
+// well (1 or 2); bit 2 (added to either) tau = 0 known at compile time.
+constexpr int kSmallGauss = 1, kSmallSine = 2, kSmallTau0 = 4;
+// request_variant: the variant a validated request of K samples and L steps
+// per sample needs (kVariantSU3: its quadrupole drives; FP64 only, see
+// precision_status).
+int request_variant(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L);
 // precision_status: SPINSIM_E_UNSUPPORTED for a request the configured
 // precision cannot run (quadrupole drives in FP32-bulk), else SPINSIM_OK.
 int precision_status(const spinsim_config& cfg, const spinsim_request& r);

@@ -145,12 +145,32 @@ bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, in
     return co <= kTinyAngleBound && h <= kTinyAngleBound && half_phi <= kTinyAngleBound;
 }
 
-int request_variant(const spinsim_config& cfg, const spinsim_request& r, int64_t L)
+// The Lie-Trotter squarings of a request (choose_tau from its field's
+// amplitudes; spin-half: none, its exponential is closed-form).
+int request_tau(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L)
+{
+    if (r.spin_x2 == 1) return 0;
+    const spinsim_field& f = r.field;
+    const double dt = r.dt_out / (double)L;
+    const double ax = kTwoPiH * f.drive_x_hz, ay = kTwoPiH * f.drive_y_hz;
+    double om_perp = std::fabs(0.5 * (ax + ay)) + std::fabs(0.5 * (ax - ay));
+    for (int j = 0; j < f.n_tones; j++) {
+        const double tx = kTwoPiH * f.tone_x_hz[j], ty = kTwoPiH * f.tone_y_hz[j];
+        om_perp += std::fabs(0.5 * (tx + ty)) + std::fabs(0.5 * (tx - ty));
+    }
+    const MethodNodes mn = method_nodes(cfg.method);
+    return choose_tau(cfg.trotter_squares, cfg.precision, cfg.rotating_frame, mn.n_exp, mn.wa, mn.wb, dt, om_perp,
+                      kTwoPiH * std::fabs(f.bias_hz), pulse_weight(f), kTwoPiH * std::fabs(f.quad_hz),
+                      (double)(K > 0 ? K - 1 : 0) * (double)L);
+}
+
+int request_variant(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L)
 {
     if (r.field.qd_on) return kVariantSU3;
     if (r.field.n_tones > 0) return kVariantTones;
     if (!small_angle_request(cfg, r, L)) return kVariantGeneral;
     const bool sine = r.field.n_pulses > 0 && (r.field.pulse_sine_mask & ((1 << r.field.n_pulses) - 1)) != 0;
+    if (r.spin_x2 == 2 && request_tau(cfg, r, K, L) == 0) return sine ? kVariantSmallSineTau0 : kVariantSmallTau0;
     return sine ? kVariantSmallSine : kVariantSmall;
 }
 
@@ -199,10 +219,8 @@ void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K,
         d.exit_re = d.exit_half_re = 1.0;
         d.exit_im = d.exit_half_im = 0.0;
     }
-    const double pulse_w = pulse_weight(f);
     // further tones: Om+-_j and their rates as seen in the frame (or the lab)
     d.n_tones = f.n_tones;
-    double om_perp = std::fabs(om_plus) + std::fabs(om_minus);
     for (int j = 0; j < f.n_tones; j++) {
         const double tx = kTwoPiH * f.tone_x_hz[j], ty = kTwoPiH * f.tone_y_hz[j];
         d.tone_hz[j] = f.tone_hz[j];
@@ -213,7 +231,6 @@ void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K,
         d.t_ct0[j] = kTwoPiH * (f.tone_hz[j] + (d.frame ? f.bias_hz : 0.0));
         d.f_tom_plus[j] = (float)d.t_om_plus[j];
         d.f_tom_minus[j] = (float)d.t_om_minus[j];
-        om_perp += std::fabs(d.t_om_plus[j]) + std::fabs(d.t_om_minus[j]);
     }
     // quadrupole drives: pair p turns at (p + 1) w_r in the frame
     d.qd_on = f.qd_on ? 1 : 0;
@@ -227,10 +244,7 @@ void fill_devsim(const spinsim_config& cfg, const spinsim_request& r, int64_t K,
         d.qd_co0[p] = kTwoPiH * (f.qd_hz[p] - kb);
         d.qd_ct0[p] = kTwoPiH * (f.qd_hz[p] + kb);
     }
-    d.tau = choose_tau(cfg.trotter_squares, cfg.precision, cfg.rotating_frame, mn.n_exp, wa, wb, d.dt,
-                       om_perp, kTwoPiH * std::fabs(f.bias_hz), pulse_w,
-                       r.spin_x2 == 2 ? kTwoPiH * std::fabs(f.quad_hz) : 0.0, (double)(K > 0 ? K - 1 : 0) * (double)L);
-    if (r.spin_x2 == 1) d.tau = 0;   // closed form: no squarings
+    d.tau = request_tau(cfg, r, K, L);
     // quadrupole coefficient of one exponential, over 3 and 2^tau, as the bulk
     // type holds it (its rounding only reaches second order: the first-order
     // part of every U_k is replaced by the exact gq)

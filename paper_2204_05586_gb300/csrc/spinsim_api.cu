@@ -961,7 +961,7 @@ int64_t spinsim_footprint(spinsim_handle h, const spinsim_request* reqs, int64_t
     for (int64_t i = 0; i < n; i++) {
         Checked c = check_request(&reqs[i]);
         if (c.status != SPINSIM_OK) return c.status;
-        fp.add(reqs[i].spin_x2, request_variant(h->cfg, reqs[i], c.L), c.K, 0);
+        fp.add(reqs[i].spin_x2, request_variant(h->cfg, reqs[i], c.K, c.L), c.K, 0);
     }
     return n > 0 ? (int64_t)fp.total() : 0;
 }
@@ -1012,7 +1012,7 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
         res[i].status = checked[i].status;
         if (checked[i].status == SPINSIM_OK) {
             checked[i].flags |= precision_flags(h->cfg.precision, h->cfg.rotating_frame, reqs[i]);
-            checked[i].variant = request_variant(h->cfg, reqs[i], checked[i].L);
+            checked[i].variant = request_variant(h->cfg, reqs[i], checked[i].K, checked[i].L);
         }
         res[i].flags = checked[i].flags;
         res[i].trotter_squares = 0;
@@ -1141,7 +1141,7 @@ int spinsim_range_begin(spinsim_handle h, const spinsim_request* req, spinsim_re
     }
     if (c.status == SPINSIM_OK) {
         c.flags |= precision_flags(h->cfg.precision, h->cfg.rotating_frame, *req);
-        c.variant = request_variant(h->cfg, *req, c.L);
+        c.variant = request_variant(h->cfg, *req, c.K, c.L);
     }
     res->status = c.status;
     res->flags = c.flags;
@@ -1448,7 +1448,7 @@ static int serving_pump(spinsim_s* h)
             Ticket& tk = h->tickets[t];
             Checked c = check_request(&tk.req);
             if (c.status == SPINSIM_OK) c.status = precision_status(h->cfg, tk.req);
-            if (c.status == SPINSIM_OK) c.variant = request_variant(h->cfg, tk.req, c.L);
+            if (c.status == SPINSIM_OK) c.variant = request_variant(h->cfg, tk.req, c.K, c.L);
             Footprint next = fp;
             next.add(tk.req.spin_x2, c.variant, c.K, tk.staged);
             if (next.total() > room) break;
@@ -1518,7 +1518,7 @@ int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result*
     if (c.status == SPINSIM_OK) {
         tk.staged = staging_bytes(*req, *res, c.K, false, h->cfg.direct_host_outputs != 0);
         Footprint fp;
-        fp.add(req->spin_x2, request_variant(h->cfg, *req, c.L), c.K, tk.staged);
+        fp.add(req->spin_x2, request_variant(h->cfg, *req, c.K, c.L), c.K, tk.staged);
         tk.bytes = round_up(fp.total(), 256);
         if (tk.bytes > h->budget) c.status = res->status = SPINSIM_E_NOMEM;   // could never be admitted
     }

@@ -180,7 +180,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     d.eb_off = 0;
     d.chain_run = cg.run;
     d.chain_top = cg.top;
-    const int variant = request_variant(*cfg, *req, L);
+    const int variant = request_variant(*cfg, *req, K, L);
     res->trotter_squares = d.tau;
     // the parameter table (the record, sample offsets {0, K}, per chain level
     // the node offsets {0, nodes}) and a cleared tile counter, written on the

@@ -98,6 +98,16 @@ int hh_small_angle_request(const spinsim_config* cfg, const spinsim_request* r, 
 }
 double hh_tiny_angle_bound() { return kTinyAngleBound; }
 
+// The integrate variant the host picks for a request (request_variant), and
+// the squarings fill_devsim gives it.
+int hh_request_variant(const spinsim_config* cfg, const spinsim_request* r, int64_t K, int64_t L, int* tau)
+{
+    DevSim d;
+    fill_devsim(*cfg, *r, K, L, d);
+    *tau = d.tau;
+    return request_variant(*cfg, *r, K, L);
+}
+
 // exp(-i H) for a full su(3) H = w . (J_x, J_y, J_z, Q, D_xz, D_yz, D_x2y2, D_xy)
 // (radians) through the split-residual general exponential, as a full matrix.
 void hh_expm_general(const double* w, double* out)

@@ -44,6 +44,9 @@ def hh(tmp_path_factory):
     L.hh_small_angle_request.restype = ctypes.c_int
     L.hh_small_angle_request.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
     L.hh_tiny_angle_bound.restype = ctypes.c_double
+    L.hh_request_variant.restype = ctypes.c_int
+    L.hh_request_variant.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                     ctypes.POINTER(ctypes.c_int)]
     L.hh_first_order.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, DP]
     L.hh_drive_cycles_frac.restype = ctypes.c_double
     L.hh_drive_cycles_frac.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int64]
@@ -301,6 +304,36 @@ def test_tau0_closed_form_exponential(hh):
         A = o32.view(np.complex128).reshape(3, 3)
         B = s32.view(np.complex128).reshape(3, 3)
         assert np.abs(A - B).max() <= 2e-7 * max(np.abs(v).max() ** 2, 1e-12) + 1e-13
+
+
+def test_tau0_variants_follow_the_squarings(hh):
+    """Small-angle spin-one requests whose squarings come out as tau = 0 run
+    the tau = 0 kernels (no runtime tau branch), exactly when fill_devsim gives
+    them tau = 0; others keep the small-angle kernels with tau at run time;
+    spin-half never takes them (no squarings); FP64 never takes a small-angle
+    kernel."""
+    from paper_2204_05586_gb300 import spinsim as S, workloads as W
+    GEN, SMALL, SINE, T0, SINE_T0 = 0, 1, 4, 5, 6
+
+    def pick(req, **cfg):
+        c = S.make_config(**cfg)
+        r = S.make_request(req)
+        st, K, L = S.spinsim_counts(r)
+        assert st == 0
+        tau = ctypes.c_int()
+        v = hh.hh_request_variant(ctypes.addressof(c), ctypes.addressof(r), K, L, ctypes.byref(tau))
+        return v, tau.value
+    assert pick(W.spin_one_sensing()) == (T0, 0)
+    assert pick(W.spin_one_sensing(), precision=S.PREC_FP64)[0] == GEN
+    v, tau = pick(W.neural_pulse())
+    assert (v, tau) == (SINE, 2)                # 100 ns steps: two squarings
+    short = W.neural_pulse()
+    short["dt"] = 1e-8                          # 10 ns steps: tau = 0
+    assert pick(short) == (SINE_T0, 0)
+    assert pick(W.spin_half_rabi())[0] == SMALL
+    for req in W.sweep(64, seed=W.SEED):
+        v, tau = pick(req)
+        assert v == (T0 if tau == 0 else SMALL), (v, tau)
 
 
 def test_small_angle_rule_on_workloads(hh):
