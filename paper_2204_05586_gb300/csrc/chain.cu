@@ -179,29 +179,64 @@ struct Tree;
 template <typename T>
 struct Tree<3, T> {
     static constexpr int D = 18;   // doubles per operator
-    static constexpr int E = 9;    // entries of a product
     static __device__ __forceinline__ cx<T> at(const double* A, int i, int j)
     {
         const double2 v = reinterpret_cast<const double2*>(A)[3 * i + j];
         return cmk<T>((T)v.x, (T)v.y);
     }
-    // entry e = (i, j) of C = A B
-    static __device__ __forceinline__ void prod_entry(const double* A, const double* B, int e, double* C)
+    // Real (c = 0) or imaginary (c = 1) part of sum_k a_k b_k, as cmul and
+    // cfma round it: sum_k a_k.r P_k + Q_k R_k with (P, Q, R) = (b.r, -a.i,
+    // b.i) or (b.i, a.i, b.r).  Lanes working on different parts run the same
+    // FP64 instructions (the parts are selected by integer operations): a
+    // branch on the part would issue both paths' FP64 instructions, each of
+    // which holds an SM sub-partition's FP64 unit whatever the lanes in use.
+    static __device__ __forceinline__ T dot_part(const cx<T> (&a)[3], const cx<T> (&b)[3], int c)
     {
-        const int i = e / 3, j = e - 3 * (e / 3);
-        cx<T> s = cmul(at(A, i, 0), at(B, 0, j));
-        s = cfma(at(A, i, 1), at(B, 1, j), s);
-        s = cfma(at(A, i, 2), at(B, 2, j), s);
-        reinterpret_cast<double2*>(C)[e] = make_double2((double)s.r, (double)s.i);
-    }
-    // component r of A v (v: 3 complex)
-    static __device__ __forceinline__ cx<T> matvec_row(const double* A, const double* v, int r)
-    {
-        const double2* w = reinterpret_cast<const double2*>(v);
-        cx<T> s = cmul(at(A, r, 0), cmk<T>((T)w[0].x, (T)w[0].y));
-        s = cfma(at(A, r, 1), cmk<T>((T)w[1].x, (T)w[1].y), s);
-        s = cfma(at(A, r, 2), cmk<T>((T)w[2].x, (T)w[2].y), s);
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const T P = c ? b[k].i : b[k].r, R = c ? b[k].r : b[k].i;
+            const T Q = flip_sign(a[k].i, !c);
+            s = k == 0 ? fma(a[k].r, P, Q * R) : fma(a[k].r, P, fma(Q, R, s));
+        }
         return s;
+    }
+    static __device__ __forceinline__ double flip_sign(double x, bool neg)
+    {
+        return __hiloint2double(__double2hiint(x) ^ (neg ? (int)0x80000000 : 0), __double2loint(x));
+    }
+    static __device__ __forceinline__ float flip_sign(float x, bool neg)
+    {
+        return __int_as_float(__float_as_int(x) ^ (neg ? (int)0x80000000 : 0));
+    }
+    // parts (re, im of each entry) of a product: one per task of a tree round
+    static constexpr int PARTS = 18;
+    // part t = 2 e + c of C = A B, e = 3 i + j (C as doubles: C[t])
+    static __device__ __forceinline__ void prod_part(const double* A, const double* B, int t, double* C)
+    {
+        const int e = t >> 1, i = e / 3, j = e - 3 * (e / 3);
+        const cx<T> a[3] = {at(A, i, 0), at(A, i, 1), at(A, i, 2)};
+        const cx<T> b[3] = {at(B, 0, j), at(B, 1, j), at(B, 2, j)};
+        C[t] = (double)dot_part(a, b, t & 1);
+    }
+    // parts of a matrix-vector product (re, im of each component)
+    static constexpr int VPARTS = 6;
+    // part t = 2 r + c of A v (v: 3 complex), as doubles: (A v)[t]
+    static __device__ __forceinline__ T matvec_part(const double* A, const double* v, int t)
+    {
+        const int r = t >> 1;
+        const double2* w = reinterpret_cast<const double2*>(v);
+        const cx<T> a[3] = {at(A, r, 0), at(A, r, 1), at(A, r, 2)};
+        const cx<T> b[3] = {cmk<T>((T)w[0].x, (T)w[0].y), cmk<T>((T)w[1].x, (T)w[1].y), cmk<T>((T)w[2].x, (T)w[2].y)};
+        return dot_part(a, b, t & 1);
+    }
+    // tree_down's task: part t of the parent's state v goes to the left child
+    // vl, part t of A v to the right child vr
+    static __device__ __forceinline__ void down_part(const double* A, const double* v, int t, double* vl, double* vr)
+    {
+        const T y = matvec_part(A, v, t);
+        vl[t] = v[t];
+        vr[t] = (double)y;
     }
 };
 
@@ -209,7 +244,6 @@ struct Tree<3, T> {
 template <typename T>
 struct Tree<2, T> {
     static constexpr int D = 4;
-    static constexpr int E = 2;
     static __device__ __forceinline__ void prod_entry(const double* A, const double* B, int e, double* C)
     {
         const double2* a = reinterpret_cast<const double2*>(A);
@@ -230,6 +264,22 @@ struct Tree<2, T> {
         // [alpha v0 - conj(beta) v1, beta v0 + conj(alpha) v1]
         return r == 0 ? csub(cmul(al, v0), cmul(cconj(be), v1)) : cfma_conj(al, v1, cmul(be, v0));
     }
+    // tasks of a tree round: the two entries (alpha, beta) of a product, the
+    // two components of a matrix-vector product
+    static constexpr int PARTS = 2;
+    static __device__ __forceinline__ void prod_part(const double* A, const double* B, int t, double* C)
+    {
+        prod_entry(A, B, t, C);
+    }
+    static constexpr int VPARTS = 2;
+    static __device__ __forceinline__ void down_part(const double* A, const double* v, int r, double* vl, double* vr)
+    {
+        const cx<T> y = matvec_row(A, v, r);
+        vl[2 * r] = v[2 * r];
+        vl[2 * r + 1] = v[2 * r + 1];
+        vr[2 * r] = (double)y.r;
+        vr[2 * r + 1] = (double)y.i;
+    }
 };
 
 // The threads that share one tree: a warp (nodes of level 0) or a whole
@@ -247,19 +297,20 @@ struct Team {
 };
 
 // Up-sweep of a tree: leaves in slots 0..31, products of every internal
-// node, one entry per thread per round.
+// node, one part (spin-one: the real or imaginary part of an entry) per
+// thread per round.
 template <int N, typename T, bool BLOCK>
 __device__ __forceinline__ void tree_up(double* S)
 {
-    constexpr int D = Tree<N, T>::D, E = Tree<N, T>::E;
+    constexpr int D = Tree<N, T>::D, E = Tree<N, T>::PARTS;
     const int me = Team<BLOCK>::rank(), n = Team<BLOCK>::size();
 #pragma unroll 1
     for (int h = 1; h <= 5; h++) {
         const int P = 32 >> h;
         for (int t = me; t < P * E; t += n) {
             const int p = t / E, e = t - E * (t / E);
-            Tree<N, T>::prod_entry(S + tslot(h - 1, 2 * p + 1) * D, S + tslot(h - 1, 2 * p) * D, e,
-                                   S + tslot(h, p) * D);
+            Tree<N, T>::prod_part(S + tslot(h - 1, 2 * p + 1) * D, S + tslot(h - 1, 2 * p) * D, e,
+                                  S + tslot(h, p) * D);
         }
         Team<BLOCK>::sync();
     }
@@ -272,20 +323,15 @@ template <int N, typename T, bool BLOCK, typename Left>
 __device__ __forceinline__ void tree_down(double* V, Left left)
 {
     constexpr int SV = 2 * N;   // doubles per state
+    constexpr int VP = Tree<N, T>::VPARTS;
     const int me = Team<BLOCK>::rank(), n = Team<BLOCK>::size();
 #pragma unroll 1
     for (int h = 5; h >= 1; h--) {
         const int P = 32 >> h;
-        for (int t = me; t < P * N; t += n) {
-            const int p = t / N, r = t - N * (t / N);
-            const double* v = V + tslot(h, p) * SV;
-            const cx<T> y = Tree<N, T>::matvec_row(left(tslot(h, p) - 32), v, r);
-            double* vl = V + tslot(h - 1, 2 * p) * SV;
-            double* vr = V + tslot(h - 1, 2 * p + 1) * SV;
-            vl[2 * r] = v[2 * r];
-            vl[2 * r + 1] = v[2 * r + 1];
-            vr[2 * r] = (double)y.r;
-            vr[2 * r + 1] = (double)y.i;
+        for (int t = me; t < P * VP; t += n) {
+            const int p = t / VP, r = t - VP * (t / VP);
+            Tree<N, T>::down_part(left(tslot(h, p) - 32), V + tslot(h, p) * SV, r, V + tslot(h - 1, 2 * p) * SV,
+                                  V + tslot(h - 1, 2 * p + 1) * SV);
         }
         Team<BLOCK>::sync();
     }
@@ -468,12 +514,21 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
             for (int h = 5; h >= 1; h--) {
                 if (((j >> (h - 1)) & 1) == 0 || !in_range) continue;       // left child: state unchanged
                 const int p = (int)(j >> h);
-                cx<T> y = cmk<T>(T(0), T(0));
-                if (lane < N) y = Tree<N, T>::matvec_row(L + (tslot(h, p) - 32) * D, v, lane);
-                __syncwarp();
-                if (lane < N) {
-                    v[2 * lane] = (double)y.r;
-                    v[2 * lane + 1] = (double)y.i;
+                const double* A = L + (tslot(h, p) - 32) * D;
+                if constexpr (N == 3) {
+                    // one part of the new state per lane (six lanes)
+                    T y = T(0);
+                    if (lane < Tree<N, T>::VPARTS) y = Tree<N, T>::matvec_part(A, v, lane);
+                    __syncwarp();
+                    if (lane < Tree<N, T>::VPARTS) v[lane] = (double)y;
+                } else {
+                    cx<T> y = cmk<T>(T(0), T(0));
+                    if (lane < N) y = Tree<N, T>::matvec_row(A, v, lane);
+                    __syncwarp();
+                    if (lane < N) {
+                        v[2 * lane] = (double)y.r;
+                        v[2 * lane + 1] = (double)y.i;
+                    }
                 }
                 __syncwarp();
             }
