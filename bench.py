@@ -340,8 +340,11 @@ def measure_batch(args, reqs, prec, dev, local, world, tag):
                     for r, t in zip(reqs, taus))
     mean_int = float(np.mean(integ_ms))
     achieved = flops / (mean_int / 1e3) / 1e12
+    sine = prec == S.PREC_FP32_BULK and any(len(p) > 3 and p[3] == "sine" for r in reqs
+                                             for p in r["field"].get("pulses", ()))
     kernel = ("integrate_su3_kernel" if su3 else
-              "integrate_tones_kernel" if any(r["field"].get("tones") for r in reqs) else "integrate_kernel")
+              "integrate_tones_kernel" if any(r["field"].get("tones") for r in reqs) else
+              "integrate_sine_kernel" if sine else "integrate_kernel")
     roofline = {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3),
                 "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
