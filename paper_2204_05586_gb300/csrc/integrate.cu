@@ -22,6 +22,7 @@
 // sample's steps.
 #include "bounds.cuh"
 #include "sample_epilogue.cuh"
+#include "lanes2.cuh"
 
 namespace spinsim {
 
@@ -172,11 +173,146 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
     }
 }
 
+// The paired body (spin-one FP32-bulk, the small-angle kernels at tau = 0):
+// every slot of a tile is a pair of consecutive samples (k, k + 1) of one
+// simulation, advanced together in F2 (lanes2.cuh: one packed f32x2
+// instruction for both samples, each lane rounded as the scalar float
+// operation, so neither sample's result depends on its partner).  Each
+// simulation starts at an even index of the operator buffer (the host pads an
+// odd sample count by one unused slot), so a pair never spans two
+// simulations; the slot past an odd simulation's last sample is computed
+// with its partner's context and not stored.  Tiles hold 2 x (32 >> lg)
+// samples, G = 2^lg lanes per pair as in integrate_body; the epilogue's lanes
+// finish both samples of their pair.
+template <int METHOD, int SMALL>
+__device__ __forceinline__ void integrate_pair_body(const IntegrateArgs& a)
+{
+    using Res = Res3<F2>;
+    constexpr int OPD = 18;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Res* rec = reinterpret_cast<Res*>(smem_raw);                                                 // [blockDim][kSlots]
+    double2* bg = reinterpret_cast<double2*>(smem_raw + (size_t)blockDim.x * kSlots * sizeof(Res));  // [blockDim][2]
+    unsigned dyn_smem;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_smem));
+    if ((size_t)blockDim.x * (kSlots * sizeof(Res) + 2 * sizeof(double2)) > (size_t)dyn_smem) return;
+    allow_dependent_launch();
+    const int wl = threadIdx.x & 31;
+    const int w0 = threadIdx.x & ~31;
+
+    for (;;) {
+        unsigned long long tile = 0;
+        if (wl == 0) tile = atomicAdd(a.tile_counter, 1ULL);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= (unsigned long long)a.n_tiles) return;
+
+        const bool bulk = tile < (unsigned long long)a.n_bulk_tiles;
+        const int lg = bulk ? a.lg_bulk : a.lg_tail;       // log2 of lanes per pair
+        const int spw = 32 >> lg;                          // pairs of the tile
+        const int64_t base = bulk ? (int64_t)tile * 2 * spw
+                                  : a.bulk_samples + (int64_t)(tile - a.n_bulk_tiles) * 2 * spw;
+        const int slot = wl >> lg;
+        const int lane = wl & ((1 << lg) - 1);
+        const int64_t g = base + 2 * slot;                 // the pair's first sample
+        Res* my = rec + (size_t)threadIdx.x * kSlots;
+        const int si0 = g < a.total_samples ? find_index(a.sample_offsets, a.n_sims, g) : 0;
+        if (g < a.total_samples && SPINSIM_INB(si0 >= 0 && si0 < a.n_sims, 0)) {
+            const int si = si0;
+            const int64_t k = g - a.sample_offsets[si];
+            const DevSim& s = a.sims[si];
+            const int lg_use = min(lg, (int)s.seg_log2);
+            const int spl_log2 = s.seg_log2 - lg_use;
+            if (SPINSIM_INB(k >= 0 && (k & 1) == 0, 1) && k < s.K && lane < (1 << lg_use)) {
+                const int64_t k1 = k + 1 < s.K ? k + 1 : k;   // past the end: the partner's context again
+                SampleCtx<float> c1[2];
+                double beta0 = 0.0, beta1 = 0.0;
+                const double gsum0 = make_ctx<float, 3>(s, k, c1[0], beta0);
+                const double gsum1 = make_ctx<float, 3>(s, k1, c1[1], beta1);
+                if (lane == 0) {
+                    bg[2 * (w0 + slot)] = make_double2(beta0, gsum0);
+                    bg[2 * (w0 + slot) + 1] = make_double2(beta1, gsum1);
+                }
+                SampleCtx<F2> c;
+                pack(c1, c);
+                const int64_t L = s.L;
+#pragma unroll 1
+                for (int q = 0; q < (1 << spl_log2); q++) {
+                    const int sg = (lane << spl_log2) + q;
+                    const int64_t lo = (sg * L) >> s.seg_log2, hi = ((sg + 1) * L) >> s.seg_log2;
+                    Res X;
+                    res_zero(X);
+                    DrivePhasors<F2> dp;
+                    drive_phasors_at<F2, METHOD>(c, lo, dp);
+#pragma unroll 1
+                    for (int64_t l = lo; l < hi; l++) step_apply<F2, METHOD, SMALL, false>(c, F2((float)l), 0, X, &dp);
+                    int h = 0;
+#pragma unroll 1
+                    while ((q >> h) & 1) {
+                        Res t;
+                        res_mul(X, my[h], t);
+                        X = t;
+                        h++;
+                    }
+                    my[h] = X;
+                }
+            }
+        }
+        __syncwarp();
+        // epilogue, one lane per pair of the tile: the lanes' sub-trees
+        // combined in the canonical tree, then the FP64 part of both samples
+        grid_dependency_wait();
+        if (wl < spw) {
+            const int t = wl;
+            const int64_t gp = base + 2 * t;
+            const int si = gp < a.total_samples ? find_index(a.sample_offsets, a.n_sims, gp) : 0;
+            if (gp < a.total_samples && SPINSIM_INB(si >= 0 && si < a.n_sims, 0) &&
+                SPINSIM_INB(gp - a.sample_offsets[si] >= 0, 1) && gp - a.sample_offsets[si] < a.sims[si].K) {
+                const int64_t k = gp - a.sample_offsets[si];
+                const DevSim& s = a.sims[si];
+                const int lg_use = min(lg, (int)s.seg_log2);
+                const int spl_log2 = s.seg_log2 - lg_use;
+                Res* lanes = rec + (size_t)(w0 + (t << lg)) * kSlots;   // lane j's result: lanes[j * kSlots + spl_log2]
+#pragma unroll 1
+                for (int d = 0; d < lg_use; d++)
+#pragma unroll 1
+                    for (int j = 0; j < (1 << lg_use); j += 2 << d) {
+                        Res tmp;
+                        res_mul(lanes[(j + (1 << d)) * kSlots + spl_log2], lanes[j * kSlots + spl_log2], tmp);
+                        lanes[j * kSlots + spl_log2] = tmp;
+                    }
+#pragma unroll 1
+                for (int h = 0; h < 2; h++) {
+                    const int64_t kh = k + h;
+                    if (kh >= s.K) break;                    // the unused slot of an odd simulation
+                    double* out = a.U + (gp + h) * OPD;
+                    if (kh == 0) {
+                        store_identity(3, out);
+                    } else {
+                        Res3<float> r;
+                        unpack(lanes[spl_log2], h, r);
+                        const double2 b = bg[2 * (w0 + t) + h];
+                        SampleExact sx;
+                        make_exact<3, false>(s, kh, b.x, b.y, sx);
+                        finish<false>(r, s, sx, out);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // The general and small-angle variants.
 template <int N, typename R, int METHOD, int SMALL>
 __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
 {
     integrate_body<N, R, METHOD, SMALL, false>(a);
+}
+
+// The paired small-angle kernels (spin-one, FP32-bulk, tau = 0).
+template <int METHOD, int SMALL>
+__global__ void __launch_bounds__(256) integrate_pair_kernel(IntegrateArgs a)
+{
+    integrate_pair_body<METHOD, SMALL>(a);
 }
 
 // The small-angle variants with single sine cycles, held to 128 registers
@@ -283,9 +419,18 @@ static void* pick_variant(int method, int variant)
             if constexpr (sizeof(R) == 4) return pick_method<N, R, 2, false>(method);
             else return nullptr;
         case kVariantSmallTau0:
-            // spin-one only (spin-half has no squarings to specialise away)
-            if constexpr (N == 3 && sizeof(R) == 4) return pick_method<N, R, kSmallGauss | kSmallTau0, false>(method);
-            else return nullptr;
+            // spin-one only (spin-half has no squarings to specialise away):
+            // the paired kernel, two samples per thread
+            if constexpr (N == 3 && sizeof(R) == 4) {
+                switch (method) {
+                    case 0: return (void*)integrate_pair_kernel<0, kSmallGauss | kSmallTau0>;
+                    case 1: return (void*)integrate_pair_kernel<1, kSmallGauss | kSmallTau0>;
+                    case 2: return (void*)integrate_pair_kernel<2, kSmallGauss | kSmallTau0>;
+                    default: return nullptr;
+                }
+            } else {
+                return nullptr;
+            }
         case kVariantSmallSineTau0:
             if constexpr (N == 3 && sizeof(R) == 4) return pick_method<N, R, kSmallSine | kSmallTau0, false>(method);
             else return nullptr;
@@ -313,8 +458,10 @@ static void* select_kernel(int spin_x2, int precision, int method, int variant)
 
 // Dynamic shared memory of one block: kSlots residual records and the
 // sample's (beta, gsum) per thread, sized from the record type itself.
-size_t integrate_smem_bytes(int spin_x2, int precision, int block)
+size_t integrate_smem_bytes(int spin_x2, int precision, int block, int variant)
 {
+    if (variant_pairs(spin_x2, precision, variant))
+        return (size_t)block * (kSlots * sizeof(Res3<F2>) + 2 * sizeof(double2));
     size_t res;
     if (spin_x2 == 2) res = precision ? sizeof(Res3<float>) : sizeof(Res3<double>);
     else res = precision ? sizeof(Res2<float>) : sizeof(Res2<double>);
@@ -328,10 +475,10 @@ cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int bloc
 {
     void* k = select_kernel(spin_x2, precision, method, variant);
     if (!k) return cudaErrorInvalidValue;
-    size_t smem_max = integrate_smem_bytes(spin_x2, precision, 256);
+    size_t smem_max = integrate_smem_bytes(spin_x2, precision, 256, variant);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     if (e != cudaSuccess) return e;
-    size_t smem = integrate_smem_bytes(spin_x2, precision, block);
+    size_t smem = integrate_smem_bytes(spin_x2, precision, block, variant);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, smem);
 }
 
@@ -341,18 +488,18 @@ cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int bloc
 // simulation of the launch has segments (one segment per lane), which end the
 // launch in finer steps.
 void integrate_tiles(int64_t total, int lanes_bulk, int block, int64_t wave_blocks, int min_seg_log2,
-                     IntegrateArgs& a)
+                     IntegrateArgs& a, int per_slot)
 {
     int lg = 0;
     while ((1 << lg) < lanes_bulk && lg < min_seg_log2) lg++;
     const int64_t wave_warps = wave_blocks * (block / 32);
-    const int64_t spw_bulk = 32 >> lg;
+    const int64_t spw_bulk = (int64_t)per_slot * (32 >> lg);   // samples of a bulk tile
     const int64_t rounds = total / (wave_warps * spw_bulk);
     a.lg_bulk = lg;
     a.lg_tail = min_seg_log2;
     a.n_bulk_tiles = rounds * wave_warps;
     a.bulk_samples = a.n_bulk_tiles * spw_bulk;
-    const int64_t spw_tail = 32 >> a.lg_tail;
+    const int64_t spw_tail = (int64_t)per_slot * (32 >> a.lg_tail);
     a.n_tiles = a.n_bulk_tiles + (total - a.bulk_samples + spw_tail - 1) / spw_tail;
 }
 
@@ -363,7 +510,7 @@ cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, 
     if (!k || block % 32 != 0 || block < 32 || block > 256 || grid < 1 || a.lg_bulk < 0 || a.lg_bulk > kSegLog2 ||
         a.lg_tail < 0 || a.lg_tail > kSegLog2)
         return cudaErrorInvalidValue;
-    size_t smem = integrate_smem_bytes(spin_x2, precision, block);
+    size_t smem = integrate_smem_bytes(spin_x2, precision, block, variant);
     IntegrateArgs args = a;
     void* params[] = {&args};
     if (!after_phase_table) return cudaLaunchKernel(k, dim3(grid), dim3(block), params, smem, stream);

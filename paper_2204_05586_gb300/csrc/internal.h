@@ -351,6 +351,15 @@ constexpr int kMaxGroups = 2 * kVariants;   // launch groups of one batch: spin-
 // small-angle series with Gaussian pulses, bit 1 with single sine cycles as
 // well (1 or 2); bit 2 (added to either) tau = 0 known at compile time.
 constexpr int kSmallGauss = 1, kSmallSine = 2, kSmallTau0 = 4;
+// The paired kernels (integrate_pair_kernel: two consecutive samples per
+// thread in packed f32x2 arithmetic) run the spin-one small-angle requests at
+// tau = 0 in FP32-bulk.  Their launch groups place every simulation at an even
+// index of the operator buffer: K samples take pair_slots(K) slots.
+inline bool variant_pairs(int spin_x2, int precision, int variant)
+{
+    return spin_x2 == 2 && precision == SPINSIM_PREC_FP32_BULK && variant == kVariantSmallTau0;
+}
+inline int64_t pair_slots(int64_t K) { return K + (K & 1); }
 // request_variant: the variant a validated request of K samples and L steps
 // per sample needs (kVariantSU3: its quadrupole drives; FP64 only, see
 // precision_status).
@@ -376,7 +385,7 @@ Checked check_request(const spinsim_request* r);
 // launch (the integrate kernel then overlaps it, see launch_integrate).
 cudaError_t launch_integrate(int spin_x2, int precision, int method, int block, int grid, int variant,
                              const IntegrateArgs& a, cudaStream_t stream, bool after_phase_table = false);
-size_t integrate_smem_bytes(int spin_x2, int precision, int block);
+size_t integrate_smem_bytes(int spin_x2, int precision, int block, int variant);
 cudaError_t integrate_occupancy(int spin_x2, int precision, int method, int block, int variant, int* blocks_per_sm);
 // launch_phase_table: fill the drive phasor tables of `n_sims` simulations
 // (their eb_off ascending; `n_entries` in all) at tab, on `stream`.
@@ -385,9 +394,10 @@ cudaError_t launch_phase_table(const DevSim* sims, int n_sims, int64_t n_entries
 // integrate_tiles: the tile plan of `total` samples for bulk lanes per sample
 // `lanes_bulk` (1, 2, 4 or 8, at most 2^min_seg_log2), `block` threads and
 // `wave_blocks` resident blocks; the tail uses 2^min_seg_log2 lanes per sample,
-// min_seg_log2 the smallest segment split among the launch's simulations.
+// min_seg_log2 the smallest segment split among the launch's simulations;
+// `per_slot` samples per lane group (2 for the paired kernels).
 void integrate_tiles(int64_t total, int lanes_bulk, int block, int64_t wave_blocks, int min_seg_log2,
-                     IntegrateArgs& a);
+                     IntegrateArgs& a, int per_slot = 1);
 // launch_chain: the chain kernels of a batch in order on `stream`; *kernels
 // receives how many were launched; fp32: the products and the state
 // propagation in single precision (the precision-study control), else FP64.

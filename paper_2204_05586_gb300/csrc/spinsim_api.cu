@@ -354,11 +354,12 @@ size_t staging_bytes(const spinsim_request& r, const spinsim_result& res, int64_
 // (spin, kernel variant) as build_plan forms them, plus the staged outputs.
 // total() is the plan.total build_plan gives the same batch.
 struct Footprint {
+    int precision;
     int64_t count[kMaxGroups] = {}, samples[kMaxGroups] = {}, phase[kMaxGroups] = {};
     int64_t nodes[kMaxGroups][kMaxLevels] = {};
     int levels[kMaxGroups];
     size_t staged = 0;
-    Footprint()
+    explicit Footprint(int prec) : precision(prec)
     {
         for (int& l : levels) l = 1;
     }
@@ -366,7 +367,7 @@ struct Footprint {
     {
         const int g = (spin_x2 - 1) * kVariants + variant;
         count[g] += 1;
-        samples[g] += K;
+        samples[g] += variant_pairs(spin_x2, precision, variant) ? pair_slots(K) : K;
         phase[g] += phase_entries(K);
         const ChainGeom cg = chain_geom(K);
         levels[g] = std::max(levels[g], cg.top + 1);
@@ -387,7 +388,7 @@ struct Footprint {
 // While a stream is being captured the pointer kinds cannot be queried; the
 // outputs are then taken to be device memory (only alignment is checked).
 int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, const std::vector<Checked>& checked,
-               bool capturing, Plan& plan, bool direct_host = false)
+               int precision, bool capturing, Plan& plan, bool direct_host = false)
 {
     plan = Plan();
     plan.staged_of.assign((size_t)n, -1);
@@ -406,7 +407,7 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
         for (int64_t i = 0; i < n; i++)
             if (checked[i].status == SPINSIM_OK && reqs[i].spin_x2 == spin && checked[i].variant == variant) {
                 g.idx.push_back(i);
-                g.samples += checked[i].K;
+                g.samples += variant_pairs(spin, precision, variant) ? pair_slots(checked[i].K) : checked[i].K;
                 g.phase_n += phase_entries(checked[i].K);
                 g.steps += (double)checked[i].K * (double)checked[i].L;
                 g.min_seg_log2 = std::min(g.min_seg_log2, seg_log2_of(checked[i].L));
@@ -489,7 +490,7 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
             }
             d.sample_offset = so;
             soff[q] = so;
-            so += d.K;
+            so += variant_pairs(g.spin_x2, h->cfg.precision, g.variant) ? pair_slots(d.K) : d.K;
             d.eb_tab = reinterpret_cast<const double*>(base + g.phase_off) + 2 * eo;
             d.eb_off = eo;
             eo += phase_entries(d.K);
@@ -549,6 +550,7 @@ int choose_shape(spinsim_s* h, int spin, int variant, double steps, int min_seg_
 {
     const int precision = h->cfg.precision;
     const int method = h->cfg.method;
+    const int per_slot = variant_pairs(spin, precision, variant) ? 2 : 1;   // samples per lane group
     lanes = h->cfg.lanes_per_sample;
     block = h->cfg.threads_per_block;
     int bps = h->cfg.blocks_per_sm;
@@ -590,9 +592,9 @@ int choose_shape(spinsim_s* h, int spin, int variant, double steps, int min_seg_
                         IntegrateArgs t = a;
                         if (!full_trial) {
                             // a prefix of at most 4 full waves of this shape
-                            t.total_samples = std::min<int64_t>(a.total_samples, 4 * wave_blocks * (B / L));
+                            t.total_samples = std::min<int64_t>(a.total_samples, 4 * wave_blocks * (B / L) * per_slot);
                         }
-                        integrate_tiles(t.total_samples, L, B, wave_blocks, min_seg_log2, t);
+                        integrate_tiles(t.total_samples, L, B, wave_blocks, min_seg_log2, t, per_slot);
                         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((t.n_tiles + B / 32 - 1) / (B / 32), wave_blocks));
                         float ms_best = 1e30f;
                         for (int rep = 0; rep < 2; rep++) {
@@ -632,7 +634,7 @@ int choose_shape(spinsim_s* h, int spin, int variant, double steps, int min_seg_
     per_sm = std::max(per_sm, 1);
     if (bps > 0) per_sm = std::min(per_sm, bps);
     const int64_t wave_blocks = (int64_t)h->n_sm * per_sm;
-    integrate_tiles(a.total_samples, lanes, block, wave_blocks, min_seg_log2, a);
+    integrate_tiles(a.total_samples, lanes, block, wave_blocks, min_seg_log2, a, per_slot);
     grid = (int)std::max<int64_t>(1, std::min<int64_t>((a.n_tiles + block / 32 - 1) / (block / 32), wave_blocks));
     return SPINSIM_OK;
 }
@@ -957,7 +959,7 @@ int spinsim_counts(const spinsim_request* req, int64_t* K, int64_t* L)
 int64_t spinsim_footprint(spinsim_handle h, const spinsim_request* reqs, int64_t n)
 {
     if (!h || (n > 0 && !reqs) || n < 0) return SPINSIM_E_ARG;
-    Footprint fp;
+    Footprint fp(h->cfg.precision);
     for (int64_t i = 0; i < n; i++) {
         Checked c = check_request(&reqs[i]);
         if (c.status != SPINSIM_OK) return c.status;
@@ -1047,7 +1049,7 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
         // calls of the same shape replay the graph on the caller's stream.
         std::vector<uint64_t> sig = batch_signature(reqs, res, n, checked);
         Plan plan;
-        build_plan(reqs, res, n, checked, false, plan, h->cfg.direct_host_outputs != 0);
+        build_plan(reqs, res, n, checked, h->cfg.precision, false, plan, h->cfg.direct_host_outputs != 0);
         if (h->graph_exec && sig == h->graph_sig) {
             // same shape: refresh the pinned parameter table and replay on the
             // caller's stream (after the handle's previous replay)
@@ -1113,7 +1115,7 @@ int spinsim_simulate(spinsim_handle h, const spinsim_request* reqs, spinsim_resu
         }
     } else {
         Plan plan;
-        build_plan(reqs, res, n, checked, capturing, plan, h->cfg.direct_host_outputs != 0);
+        build_plan(reqs, res, n, checked, h->cfg.precision, capturing, plan, h->cfg.direct_host_outputs != 0);
         st = run_batch(h, reqs, res, checked, plan, stream, h->arena, h->pinned, capturing ? nullptr : h->ev_pinned,
                        capturing, &kernels);
         if (st != SPINSIM_OK) return fail(st);
@@ -1157,7 +1159,7 @@ int spinsim_range_begin(spinsim_handle h, const spinsim_request* req, spinsim_re
     h->last.chain_ms = -1.0;
     h->prof_groups = 0;
     Plan plan;
-    build_plan(req, res, 1, checked, false, plan, h->cfg.direct_host_outputs != 0);
+    build_plan(req, res, 1, checked, h->cfg.precision, false, plan, h->cfg.direct_host_outputs != 0);
     int kernels = 0;
     int st = run_batch(h, req, res, checked, plan, stream, h->arena, h->pinned, h->ev_pinned, false, &kernels, false,
                        kPhaseBegin);
@@ -1442,7 +1444,7 @@ static int serving_pump(spinsim_s* h)
         std::vector<spinsim_result> res;
         std::vector<int64_t> ids;
         std::vector<Checked> checked;
-        Footprint fp;
+        Footprint fp(h->cfg.precision);
         while (!h->pending.empty()) {
             const int64_t t = h->pending.front();
             Ticket& tk = h->tickets[t];
@@ -1461,7 +1463,7 @@ static int serving_pump(spinsim_s* h)
         }
         if (ids.empty()) break;   // the head waits for a batch to retire
         Plan plan;
-        build_plan(reqs.data(), res.data(), (int64_t)reqs.size(), checked, false, plan, h->cfg.direct_host_outputs != 0);
+        build_plan(reqs.data(), res.data(), (int64_t)reqs.size(), checked, h->cfg.precision, false, plan, h->cfg.direct_host_outputs != 0);
         size_t off = 0;
         int st = SPINSIM_OK;
         if (!pool_carve(h, round_up(plan.total, 256), &off)) st = SPINSIM_E_NOMEM;   // total() bounds plan.total
@@ -1517,7 +1519,7 @@ int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result*
     tk.bytes = 0;
     if (c.status == SPINSIM_OK) {
         tk.staged = staging_bytes(*req, *res, c.K, false, h->cfg.direct_host_outputs != 0);
-        Footprint fp;
+        Footprint fp(h->cfg.precision);
         fp.add(req->spin_x2, request_variant(h->cfg, *req, c.K, c.L), c.K, tk.staged);
         tk.bytes = round_up(fp.total(), 256);
         if (tk.bytes > h->budget) c.status = res->status = SPINSIM_E_NOMEM;   // could never be admitted

@@ -163,7 +163,10 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     const size_t soff_off = off; off += 256;
     const size_t loff_off = off; off += up256(kMaxLevels * 2 * sizeof(int64_t));
     const size_t counter_off = off; off += 256;
-    const size_t U_off = off; off += up256((size_t)K * opd * 8);
+    const int variant = request_variant(*cfg, *req, K, L);
+    // operator slots: the paired kernels place an odd K's pairs in K + 1 slots
+    const int64_t slots = variant_pairs(spin, cfg->precision, variant) ? pair_slots(K) : K;
+    const size_t U_off = off; off += up256((size_t)slots * opd * 8);
     const int64_t phase_n = phase_entries(K);
     const size_t phase_off = off; off += up256((size_t)phase_n * 2 * sizeof(double));
     const size_t chain_off = off; off += cl.bytes;
@@ -180,7 +183,6 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     d.eb_off = 0;
     d.chain_run = cg.run;
     d.chain_top = cg.top;
-    const int variant = request_variant(*cfg, *req, K, L);
     res->trotter_squares = d.tau;
     // the parameter table (the record, sample offsets {0, K}, per chain level
     // the node offsets {0, nodes}) and a cleared tile counter, written on the
@@ -213,13 +215,14 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         ia.sims = reinterpret_cast<const DevSim*>(base + sims_off);
         ia.sample_offsets = reinterpret_cast<const int64_t*>(base + soff_off);
         ia.n_sims = 1;
-        ia.total_samples = K;
+        ia.total_samples = slots;
         ia.U = reinterpret_cast<double*>(base + U_off);
         ia.tau = tau;
         ia.tile_counter = reinterpret_cast<unsigned long long*>(base + counter_off);
         if (cfg->blocks_per_sm > 0) per_sm = std::min(per_sm, cfg->blocks_per_sm);
         const int64_t wave_blocks = (int64_t)n_sm * std::max(per_sm, 1);
-        integrate_tiles(K, lanes, block, wave_blocks, seg_log2_of(L), ia);
+        integrate_tiles(slots, lanes, block, wave_blocks, seg_log2_of(L), ia,
+                        variant_pairs(spin, cfg->precision, variant) ? 2 : 1);
         const int grid =
             (int)std::max<int64_t>(1, std::min<int64_t>((ia.n_tiles + block / 32 - 1) / (block / 32), wave_blocks));
         if (launch_integrate(spin, cfg->precision, cfg->method, block, grid, variant, ia, stream, phase_n > 0) !=
