@@ -173,7 +173,7 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
     }
 }
 
-// The paired body (spin-one FP32-bulk, the small-angle kernels at tau = 0):
+// The paired body (spin-one FP32-bulk, the small-angle kernels):
 // every slot of a tile is a pair of consecutive samples (k, k + 1) of one
 // simulation, advanced together in F2 (lanes2.cuh: one packed f32x2
 // instruction for both samples, each lane rounded as the scalar float
@@ -243,7 +243,7 @@ __device__ __forceinline__ void integrate_pair_body(const IntegrateArgs& a)
                     DrivePhasors<F2> dp;
                     drive_phasors_at<F2, METHOD>(c, lo, dp);
 #pragma unroll 1
-                    for (int64_t l = lo; l < hi; l++) step_apply<F2, METHOD, SMALL, false>(c, F2((float)l), 0, X, &dp);
+                    for (int64_t l = lo; l < hi; l++) step_apply<F2, METHOD, SMALL, false>(c, F2((float)l), c.tau, X, &dp);
                     int h = 0;
 #pragma unroll 1
                     while ((q >> h) & 1) {
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
     integrate_body<N, R, METHOD, SMALL, false>(a);
 }
 
-// The paired small-angle kernels (spin-one, FP32-bulk, tau = 0).
+// The paired small-angle kernels (spin-one, FP32-bulk).
 template <int METHOD, int SMALL>
 __global__ void __launch_bounds__(256) integrate_pair_kernel(IntegrateArgs a)
 {
@@ -404,35 +404,46 @@ static void* pick_method(int method)
     }
 }
 
+template <int SMALL>
+static void* pick_pair(int method)
+{
+    switch (method) {
+        case 0: return (void*)integrate_pair_kernel<0, SMALL>;
+        case 1: return (void*)integrate_pair_kernel<1, SMALL>;
+        case 2: return (void*)integrate_pair_kernel<2, SMALL>;
+        default: return nullptr;
+    }
+}
+
 template <int N, typename R>
 static void* pick_variant(int method, int variant)
 {
     switch (variant) {
         case kVariantGeneral: return pick_method<N, R, false, false>(method);
         case kVariantTones: return pick_method<N, R, false, true>(method);
+        // the small-angle variants exist for FP32-bulk only; FP64 keeps the
+        // general series (its terms are sized for double precision); spin-one
+        // runs them in the paired kernel, two samples per thread (the tau = 0
+        // variants exist for spin-one only: spin-half has no squarings)
         case kVariantSmall:
-            // the small-angle variants exist for FP32-bulk only; FP64 keeps the
-            // general series (its terms are sized for double precision)
-            if constexpr (sizeof(R) == 4) return pick_method<N, R, 1, false>(method);
-            else return nullptr;
-        case kVariantSmallSine:
-            if constexpr (sizeof(R) == 4) return pick_method<N, R, 2, false>(method);
-            else return nullptr;
-        case kVariantSmallTau0:
-            // spin-one only (spin-half has no squarings to specialise away):
-            // the paired kernel, two samples per thread
-            if constexpr (N == 3 && sizeof(R) == 4) {
-                switch (method) {
-                    case 0: return (void*)integrate_pair_kernel<0, kSmallGauss | kSmallTau0>;
-                    case 1: return (void*)integrate_pair_kernel<1, kSmallGauss | kSmallTau0>;
-                    case 2: return (void*)integrate_pair_kernel<2, kSmallGauss | kSmallTau0>;
-                    default: return nullptr;
-                }
+            if constexpr (sizeof(R) == 4) {
+                if constexpr (N == 3) return pick_pair<kSmallGauss>(method);
+                else return pick_method<N, R, kSmallGauss, false>(method);
             } else {
                 return nullptr;
             }
+        case kVariantSmallSine:
+            if constexpr (sizeof(R) == 4) {
+                if constexpr (N == 3) return pick_pair<kSmallSine>(method);
+                else return pick_method<N, R, kSmallSine, false>(method);
+            } else {
+                return nullptr;
+            }
+        case kVariantSmallTau0:
+            if constexpr (N == 3 && sizeof(R) == 4) return pick_pair<kSmallGauss | kSmallTau0>(method);
+            else return nullptr;
         case kVariantSmallSineTau0:
-            if constexpr (N == 3 && sizeof(R) == 4) return pick_method<N, R, kSmallSine | kSmallTau0, false>(method);
+            if constexpr (N == 3 && sizeof(R) == 4) return pick_pair<kSmallSine | kSmallTau0>(method);
             else return nullptr;
         case kVariantSU3:
             if constexpr (N == 3 && sizeof(R) == 8) {

@@ -70,6 +70,28 @@ __device__ __forceinline__ void second_order_sincos(F2 x, F2& s, F2& c)
     c = F2::of(c0, c1);
 }
 
+// The single-sine-cycle pulse shape, lane by lane.
+__device__ __forceinline__ F2 sine_cycle(F2 u) { return F2::of(sine_cycle<float>(u.v.x), sine_cycle<float>(u.v.y)); }
+
+// The transverse axis and angle of expm_one_res_n, lane by lane.
+__device__ __forceinline__ void transverse_axis_lanes(F2 vx, F2 vy, F2 vp2, F2 inv_n, F2& epr, F2& epi, F2& Phi)
+{
+    float r[2] = {1.0f, 1.0f}, i[2] = {0.0f, 0.0f}, p[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const float q = lane(vp2, h);
+        if (q > 0.0f) {
+            const float rinv = rsqrtf(q);
+            r[h] = lane(vx, h) * rinv;
+            i[h] = lane(vy, h) * rinv;
+            p[h] = q * rinv * lane(inv_n, h);
+        }
+    }
+    epr = F2::of(r[0], r[1]);
+    epi = F2::of(i[0], i[1]);
+    Phi = F2::of(p[0], p[1]);
+}
+
 // The contexts of two consecutive samples of one simulation, lane by lane
 // (the per-simulation integers are the same in both).
 __device__ __forceinline__ void pack(const SampleCtx<float> (&c)[2], SampleCtx<F2>& v)
