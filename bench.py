@@ -340,11 +340,12 @@ def measure_batch(args, reqs, prec, dev, local, world, tag):
                     for r, t in zip(reqs, taus))
     mean_int = float(np.mean(integ_ms))
     achieved = flops / (mean_int / 1e3) / 1e12
-    sine = prec == S.PREC_FP32_BULK and any(len(p) > 3 and p[3] == "sine" for r in reqs
-                                             for p in r["field"].get("pulses", ()))
+    # FP32-bulk spin-one requests in the rotating frame take the small-angle
+    # variants, which run in the paired kernel (two samples per thread)
+    paired = prec == S.PREC_FP32_BULK and all(r["spin_x2"] == 2 for r in reqs)
     kernel = ("integrate_su3_kernel" if su3 else
               "integrate_tones_kernel" if any(r["field"].get("tones") for r in reqs) else
-              "integrate_sine_kernel" if sine else "integrate_kernel")
+              "integrate_pair_kernel" if paired else "integrate_kernel")
     roofline = {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3),
                 "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4),
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
