@@ -281,6 +281,26 @@ def test_alone_equals_in_batch():
         assert np.array_equal(outs[len(reqs) - 1 - i]["states"].cpu().numpy(), alone[i])
 
 
+def test_paired_kernel_odd_sample_counts(oracle_mod):
+    """Spin-one FP32-bulk small-angle requests run two samples per thread;
+    the host places every simulation of the launch at an even operator index
+    (an odd K takes one unused slot).  Simulations of odd and even K (1 to 129,
+    both tau = 0 and tau at run time) in one batch equal their runs alone bit
+    for bit, whatever their place in the batch, and match the oracle."""
+    base = W.field(bias_hz=700e3, drive_x_hz=2e3, drive_hz=700.3e3, quad_hz=300.0, pulses=[(40.0, 1e-5, 3e-5)])
+    reqs = [W.request(2, base, 0.0, K * 1e-6, 1e-8 if K % 2 else 2e-8, 1e-6) for K in (1, 2, 3, 5, 64, 65, 128, 129)]
+    strong = W.field(bias_hz=700e3, drive_x_hz=20e3, drive_hz=700.3e3, quad_hz=300.0, pulses=[(2e3, 3e-5, 2e-5)])
+    reqs.append(W.request(2, strong, 0.0, 77e-6, 1e-7, 1e-6))        # a strong drive: tau > 0 at run time
+    outs, _ = gpu_run(reqs, precision=S.PREC_FP32_BULK)
+    outs_rev, _ = gpu_run(reqs[::-1], precision=S.PREC_FP32_BULK)
+    for i, q in enumerate(reqs):
+        (alone,), _ = gpu_run([q], precision=S.PREC_FP32_BULK)
+        a = alone["states"].cpu().numpy()
+        assert np.array_equal(outs[i]["states"].cpu().numpy(), a), i
+        assert np.array_equal(outs_rev[len(reqs) - 1 - i]["states"].cpu().numpy(), a), i
+        assert_parity(outs[i], oracle_run(oracle_mod, q), TOL[S.PREC_FP32_BULK], f"K={a.shape[0]}")
+
+
 def test_host_buffers_match_device_buffers():
     req = W.spin_one_sensing(t_end=2e-3)
     (dev,), _ = gpu_run([req], precision=S.PREC_FP32_BULK)
