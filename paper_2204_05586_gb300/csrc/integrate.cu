@@ -173,7 +173,7 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
     }
 }
 
-// The paired body (spin-one FP32-bulk, the small-angle kernels):
+// The paired body (FP32-bulk, the small-angle kernels):
 // every slot of a tile is a pair of consecutive samples (k, k + 1) of one
 // simulation, advanced together in F2 (lanes2.cuh: one packed f32x2
 // instruction for both samples, each lane rounded as the scalar float
@@ -184,11 +184,11 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
 // with its partner's context and not stored.  Tiles hold 2 x (32 >> lg)
 // samples, G = 2^lg lanes per pair as in integrate_body; the epilogue's lanes
 // finish both samples of their pair.
-template <int METHOD, int SMALL>
+template <int N, int METHOD, int SMALL>
 __device__ __forceinline__ void integrate_pair_body(const IntegrateArgs& a)
 {
-    using Res = Res3<F2>;
-    constexpr int OPD = 18;
+    using Res = typename ResType<N, F2>::type;
+    constexpr int OPD = N == 3 ? 18 : 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Res* rec = reinterpret_cast<Res*>(smem_raw);                                                 // [blockDim][kSlots]
     double2* bg = reinterpret_cast<double2*>(smem_raw + (size_t)blockDim.x * kSlots * sizeof(Res));  // [blockDim][2]
@@ -225,8 +225,8 @@ __device__ __forceinline__ void integrate_pair_body(const IntegrateArgs& a)
                 const int64_t k1 = k + 1 < s.K ? k + 1 : k;   // past the end: the partner's context again
                 SampleCtx<float> c1[2];
                 double beta0 = 0.0, beta1 = 0.0;
-                const double gsum0 = make_ctx<float, 3>(s, k, c1[0], beta0);
-                const double gsum1 = make_ctx<float, 3>(s, k1, c1[1], beta1);
+                const double gsum0 = make_ctx<float, N>(s, k, c1[0], beta0);
+                const double gsum1 = make_ctx<float, N>(s, k1, c1[1], beta1);
                 if (lane == 0) {
                     bg[2 * (w0 + slot)] = make_double2(beta0, gsum0);
                     bg[2 * (w0 + slot) + 1] = make_double2(beta1, gsum1);
@@ -240,10 +240,16 @@ __device__ __forceinline__ void integrate_pair_body(const IntegrateArgs& a)
                     const int64_t lo = (sg * L) >> s.seg_log2, hi = ((sg + 1) * L) >> s.seg_log2;
                     Res X;
                     res_zero(X);
-                    DrivePhasors<F2> dp;
-                    drive_phasors_at<F2, METHOD>(c, lo, dp);
+                    if constexpr (N == 3) {
+                        DrivePhasors<F2> dp;
+                        drive_phasors_at<F2, METHOD>(c, lo, dp);
 #pragma unroll 1
-                    for (int64_t l = lo; l < hi; l++) step_apply<F2, METHOD, SMALL, false>(c, F2((float)l), c.tau, X, &dp);
+                        for (int64_t l = lo; l < hi; l++)
+                            step_apply<F2, METHOD, SMALL, false>(c, F2((float)l), c.tau, X, &dp);
+                    } else {
+#pragma unroll 1
+                        for (int64_t l = lo; l < hi; l++) step_apply<F2, METHOD, SMALL, false>(c, F2((float)l), c.tau, X);
+                    }
                     int h = 0;
 #pragma unroll 1
                     while ((q >> h) & 1) {
@@ -285,13 +291,13 @@ __device__ __forceinline__ void integrate_pair_body(const IntegrateArgs& a)
                     if (kh >= s.K) break;                    // the unused slot of an odd simulation
                     double* out = a.U + (gp + h) * OPD;
                     if (kh == 0) {
-                        store_identity(3, out);
+                        store_identity(N, out);
                     } else {
-                        Res3<float> r;
+                        typename ResType<N, float>::type r;
                         unpack(lanes[spl_log2], h, r);
                         const double2 b = bg[2 * (w0 + t) + h];
                         SampleExact sx;
-                        make_exact<3, false>(s, kh, b.x, b.y, sx);
+                        make_exact<N, false>(s, kh, b.x, b.y, sx);
                         finish<false>(r, s, sx, out);
                     }
                 }
@@ -308,20 +314,11 @@ __global__ void __launch_bounds__(256) integrate_kernel(IntegrateArgs a)
     integrate_body<N, R, METHOD, SMALL, false>(a);
 }
 
-// The paired small-angle kernels (spin-one, FP32-bulk).
-template <int METHOD, int SMALL>
+// The paired small-angle kernels (FP32-bulk).
+template <int N, int METHOD, int SMALL>
 __global__ void __launch_bounds__(256) integrate_pair_kernel(IntegrateArgs a)
 {
-    integrate_pair_body<METHOD, SMALL>(a);
-}
-
-// The small-angle variants with single sine cycles, held to 128 registers
-// (two 256-thread blocks per SM): at tau = 0 the compiler otherwise takes 164
-// and one block fits.
-template <int N, typename R, int METHOD, int SMALL>
-__global__ void __launch_bounds__(256, 2) integrate_sine_kernel(IntegrateArgs a)
-{
-    integrate_body<N, R, METHOD, SMALL, false>(a);
+    integrate_pair_body<N, METHOD, SMALL>(a);
 }
 
 // The variant with further drive tones; in FP32 held to 128 registers (two
@@ -389,7 +386,6 @@ template <int N, typename R, int METHOD, int SMALL, bool TONES>
 static void* kernel_ptr()
 {
     if constexpr (TONES) return (void*)integrate_tones_kernel<N, R, METHOD>;
-    else if constexpr ((SMALL & kSmallSine) != 0) return (void*)integrate_sine_kernel<N, R, METHOD, SMALL>;
     else return (void*)integrate_kernel<N, R, METHOD, SMALL>;
 }
 
@@ -404,13 +400,13 @@ static void* pick_method(int method)
     }
 }
 
-template <int SMALL>
+template <int N, int SMALL>
 static void* pick_pair(int method)
 {
     switch (method) {
-        case 0: return (void*)integrate_pair_kernel<0, SMALL>;
-        case 1: return (void*)integrate_pair_kernel<1, SMALL>;
-        case 2: return (void*)integrate_pair_kernel<2, SMALL>;
+        case 0: return (void*)integrate_pair_kernel<N, 0, SMALL>;
+        case 1: return (void*)integrate_pair_kernel<N, 1, SMALL>;
+        case 2: return (void*)integrate_pair_kernel<N, 2, SMALL>;
         default: return nullptr;
     }
 }
@@ -421,29 +417,21 @@ static void* pick_variant(int method, int variant)
     switch (variant) {
         case kVariantGeneral: return pick_method<N, R, false, false>(method);
         case kVariantTones: return pick_method<N, R, false, true>(method);
-        // the small-angle variants exist for FP32-bulk only; FP64 keeps the
-        // general series (its terms are sized for double precision); spin-one
-        // runs them in the paired kernel, two samples per thread (the tau = 0
-        // variants exist for spin-one only: spin-half has no squarings)
+        // the small-angle variants exist for FP32-bulk only (FP64 keeps the
+        // general series, its terms sized for double precision) and run in the
+        // paired kernel, two samples per thread (the tau = 0 variants exist for
+        // spin-one only: spin-half has no squarings)
         case kVariantSmall:
-            if constexpr (sizeof(R) == 4) {
-                if constexpr (N == 3) return pick_pair<kSmallGauss>(method);
-                else return pick_method<N, R, kSmallGauss, false>(method);
-            } else {
-                return nullptr;
-            }
+            if constexpr (sizeof(R) == 4) return pick_pair<N, kSmallGauss>(method);
+            else return nullptr;
         case kVariantSmallSine:
-            if constexpr (sizeof(R) == 4) {
-                if constexpr (N == 3) return pick_pair<kSmallSine>(method);
-                else return pick_method<N, R, kSmallSine, false>(method);
-            } else {
-                return nullptr;
-            }
+            if constexpr (sizeof(R) == 4) return pick_pair<N, kSmallSine>(method);
+            else return nullptr;
         case kVariantSmallTau0:
-            if constexpr (N == 3 && sizeof(R) == 4) return pick_pair<kSmallGauss | kSmallTau0>(method);
+            if constexpr (N == 3 && sizeof(R) == 4) return pick_pair<N, kSmallGauss | kSmallTau0>(method);
             else return nullptr;
         case kVariantSmallSineTau0:
-            if constexpr (N == 3 && sizeof(R) == 4) return pick_pair<kSmallSine | kSmallTau0>(method);
+            if constexpr (N == 3 && sizeof(R) == 4) return pick_pair<N, kSmallSine | kSmallTau0>(method);
             else return nullptr;
         case kVariantSU3:
             if constexpr (N == 3 && sizeof(R) == 8) {
@@ -472,7 +460,7 @@ static void* select_kernel(int spin_x2, int precision, int method, int variant)
 size_t integrate_smem_bytes(int spin_x2, int precision, int block, int variant)
 {
     if (variant_pairs(spin_x2, precision, variant))
-        return (size_t)block * (kSlots * sizeof(Res3<F2>) + 2 * sizeof(double2));
+        return (size_t)block * (kSlots * (spin_x2 == 2 ? sizeof(Res3<F2>) : sizeof(Res2<F2>)) + 2 * sizeof(double2));
     size_t res;
     if (spin_x2 == 2) res = precision ? sizeof(Res3<float>) : sizeof(Res3<double>);
     else res = precision ? sizeof(Res2<float>) : sizeof(Res2<double>);

@@ -352,12 +352,13 @@ constexpr int kMaxGroups = 2 * kVariants;   // launch groups of one batch: spin-
 // well (1 or 2); bit 2 (added to either) tau = 0 known at compile time.
 constexpr int kSmallGauss = 1, kSmallSine = 2, kSmallTau0 = 4;
 // The paired kernels (integrate_pair_kernel: two consecutive samples per
-// thread in packed f32x2 arithmetic) run the spin-one small-angle requests in
+// thread in packed f32x2 arithmetic) run the small-angle requests in
 // FP32-bulk.  Their launch groups place every simulation at an even index of
 // the operator buffer: K samples take pair_slots(K) slots.
 inline bool variant_pairs(int spin_x2, int precision, int variant)
 {
-    return spin_x2 == 2 && precision == SPINSIM_PREC_FP32_BULK &&
+    (void)spin_x2;
+    return precision == SPINSIM_PREC_FP32_BULK &&
            (variant == kVariantSmall || variant == kVariantSmallSine || variant == kVariantSmallTau0 ||
             variant == kVariantSmallSineTau0);
 }

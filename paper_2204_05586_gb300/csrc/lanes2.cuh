@@ -92,6 +92,17 @@ __device__ __forceinline__ void transverse_axis_lanes(F2 vx, F2 vy, F2 vp2, F2 i
     Phi = F2::of(p[0], p[1]);
 }
 
+// The SU(2) exponential's half-angle terms, lane by lane (each lane takes the
+// series or the library functions by its own angle, as the scalar code does).
+__device__ __forceinline__ void half_angle_terms(F2 t2, F2& fm, F2& g)
+{
+    float f0, g0, f1, g1;
+    half_angle_terms<float>(t2.v.x, f0, g0);
+    half_angle_terms<float>(t2.v.y, f1, g1);
+    fm = F2::of(f0, f1);
+    g = F2::of(g0, g1);
+}
+
 // The contexts of two consecutive samples of one simulation, lane by lane
 // (the per-simulation integers are the same in both).
 __device__ __forceinline__ void pack(const SampleCtx<float> (&c)[2], SampleCtx<F2>& v)
@@ -114,6 +125,15 @@ __device__ __forceinline__ void pack(const SampleCtx<float> (&c)[2], SampleCtx<F
     v.ng = c[0].ng;
     v.tau = c[0].tau;
     v.counter_on = c[0].counter_on;
+}
+
+// Lane h of a paired spin-half residual.
+__device__ __forceinline__ void unpack(const Res2<F2>& v, int h, Res2<float>& x)
+{
+#pragma unroll
+    for (int q = 0; q < 3; q++) x.g[q] = lane(v.g[q], h);
+    x.a = cmk(lane(v.a.r, h), lane(v.a.i, h));
+    x.b = cmk(lane(v.b.r, h), lane(v.b.i, h));
 }
 
 // Lane h of a paired spin-one residual.
