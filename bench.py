@@ -62,7 +62,7 @@ L2_FLUSH_BYTES = 256 << 20
 # the 512-simulation sweep's tau = 0 launch scaled by samples to the 4096-simulation
 # sweep's, whose 12.8 GB of operators go to HBM)
 INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 88320, ("multitone", "fp32"): 121088, ("su3", "fp64"): 1419776,
-                           ("sweep", "fp32"): 12360000000}
+                           ("sweep", "fp32"): 12340000000}
 
 
 def algorithmic_flops_per_step(spin_x2: int, tau: int, n_tones: int = 0) -> float:
