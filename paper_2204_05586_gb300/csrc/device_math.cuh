@@ -78,6 +78,52 @@ struct BulkTraits {
 template <typename R>
 constexpr bool kFP32 = BulkTraits<R>::fp32;
 
+SPINSIM_HD int clz32(uint32_t x)
+{
+#if defined(__CUDA_ARCH__)
+    return __clz((int)x);
+#else
+    return x ? __builtin_clz(x) : 32;
+#endif
+}
+
+// Exact widening of an FP32 value to FP64 from the fields of the two IEEE 754
+// binary formats, returning the FP64 bit pattern: the sign kept, the exponent
+// rebiased (+1023 - 127), the 23 mantissa bits moved to the top of the 52; a
+// subnormal input (m x 2^-149) normalised; zero, the infinities and NaN
+// (payload kept) mapped to theirs.
+SPINSIM_HD uint64_t widen_bits(uint32_t b)
+{
+    const uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    uint32_t E, M;
+    if (e == 0u) {
+        const int sh = m ? clz32(m) - 8 : 0;   // moves the leading 1 to the implicit bit
+        E = m ? 897u - (uint32_t)sh : 0u;
+        M = (m << sh) & 0x7fffffu;
+    } else {
+        E = e == 0xffu ? 0x7ffu : e + 896u;
+        M = m;
+    }
+    return ((uint64_t)((b & 0x80000000u) | (E << 20) | (M >> 3)) << 32) | (uint64_t)(M << 29);
+}
+
+// FP32 -> FP64 in the spin-half sample epilogue.  On the device by
+// widen_bits (integer instructions): the conversion instruction runs on the
+// FP64 pipe, where one warp instruction holds a sub-partition's unit as long
+// as an FP64 multiply-add does.  (Measured on GB300: 1 % faster for the
+// spin-half kernels; the spin-one epilogue, with 19 conversions per sample,
+// ran slower with it and converts directly.)  On the host the plain
+// conversion (the same value).
+SPINSIM_HD double widen(float f)
+{
+#if defined(__CUDA_ARCH__)
+    return __longlong_as_double((long long)widen_bits(__float_as_uint(f)));
+#else
+    return (double)f;
+#endif
+}
+SPINSIM_HD double widen(double d) { return d; }
+
 template <typename R>
 struct cx {
     R r, i;

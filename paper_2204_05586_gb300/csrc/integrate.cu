@@ -105,20 +105,25 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
                     const int64_t lo = (sg * L) >> s.seg_log2, hi = ((sg + 1) * L) >> s.seg_log2;
                     Res X;
                     res_zero(X);
+                    // the step index as R, counted (exact: L <= 2^24), not
+                    // converted from the integer each step (a 64-bit integer
+                    // conversion is an FP64-pipe instruction)
+                    const int n_steps = (int)(hi - lo);
+                    R lf = (R)lo;
                     if constexpr (SU3) {
                         CounterPhasors<R> ph;
                         counter_phasors_at<R, METHOD>(c, lo, ph);
 #pragma unroll 1
-                        for (int64_t l = lo; l < hi; l++) step_apply_su3<R, METHOD, TONES>(c, (R)l, ph, X);
+                        for (int i = 0; i < n_steps; i++, lf += R(1)) step_apply_su3<R, METHOD, TONES>(c, lf, ph, X);
                     } else if constexpr (SMALL && N == 3) {
                         // small angles: the drive phasors turned per step from the segment's start
                         DrivePhasors<R> dp;
                         drive_phasors_at<R, METHOD>(c, lo, dp);
 #pragma unroll 1
-                        for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES>(c, (R)l, c.tau, X, &dp);
+                        for (int i = 0; i < n_steps; i++, lf += R(1)) step_apply<R, METHOD, SMALL, TONES>(c, lf, c.tau, X, &dp);
                     } else {
 #pragma unroll 1
-                        for (int64_t l = lo; l < hi; l++) step_apply<R, METHOD, SMALL, TONES>(c, (R)l, c.tau, X);   // U <- u_l U
+                        for (int i = 0; i < n_steps; i++, lf += R(1)) step_apply<R, METHOD, SMALL, TONES>(c, lf, c.tau, X);   // U <- u_l U
                     }
                     // canonical tree over the lane's segments: a finished pair of
                     // equal sub-trees merges (later on the left) until the sizes differ
@@ -240,15 +245,18 @@ __device__ __forceinline__ void integrate_pair_body(const IntegrateArgs& a)
                     const int64_t lo = (sg * L) >> s.seg_log2, hi = ((sg + 1) * L) >> s.seg_log2;
                     Res X;
                     res_zero(X);
+                    // the step index counted in FP32 (exact: L <= 2^24)
+                    const int n_steps = (int)(hi - lo);
+                    float lf = (float)lo;
                     if constexpr (N == 3) {
                         DrivePhasors<F2> dp;
                         drive_phasors_at<F2, METHOD>(c, lo, dp);
 #pragma unroll 1
-                        for (int64_t l = lo; l < hi; l++)
-                            step_apply<F2, METHOD, SMALL, false>(c, F2((float)l), c.tau, X, &dp);
+                        for (int i = 0; i < n_steps; i++, lf += 1.0f)
+                            step_apply<F2, METHOD, SMALL, false>(c, F2(lf), c.tau, X, &dp);
                     } else {
 #pragma unroll 1
-                        for (int64_t l = lo; l < hi; l++) step_apply<F2, METHOD, SMALL, false>(c, F2((float)l), c.tau, X);
+                        for (int i = 0; i < n_steps; i++, lf += 1.0f) step_apply<F2, METHOD, SMALL, false>(c, F2(lf), c.tau, X);
                     }
                     int h = 0;
 #pragma unroll 1

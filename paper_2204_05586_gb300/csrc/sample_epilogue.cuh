@@ -89,9 +89,9 @@ SPINSIM_HD void promote(const Res2<R>& P, const DevSim& s, const SampleExact& x,
 {
     double gx, gy;
     first_order_exact<TONES>(s, x, gx, gy);
-    const double gz = (double)P.g[2];
-    a = cmk((double)P.a.r, (double)P.a.i - 0.5 * gz);
-    b = cmk((double)P.b.r + 0.5 * gy, (double)P.b.i - 0.5 * gx);
+    const double gz = widen(P.g[2]);
+    a = cmk(widen(P.a.r), widen(P.a.i) - 0.5 * gz);
+    b = cmk(widen(P.b.r) + 0.5 * gy, widen(P.b.i) - 0.5 * gx);
 }
 
 SPINSIM_HD void store_half(cx<double> al, cx<double> be, const SampleExact& x, double* out)

@@ -173,6 +173,11 @@ void hh_first_order(const spinsim_config* cfg, const spinsim_request* r, int64_t
     out[1] = gy;
     out[2] = gsum;
 }
+// The epilogue's integer FP32 -> FP64 widening of n bit patterns.
+void hh_widen_bits(const uint32_t* in, uint64_t* out, int64_t n)
+{
+    for (int64_t i = 0; i < n; i++) out[i] = widen_bits(in[i]);
+}
 // The fractional drive cycles f (t0 + m dt) (drive_cycles_frac).
 double hh_drive_cycles_frac(double f, double t0, double dt, int64_t m) { return drive_cycles_frac(f, t0, dt, m); }
 

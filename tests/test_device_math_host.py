@@ -48,6 +48,7 @@ def hh(tmp_path_factory):
     L.hh_request_variant.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.POINTER(ctypes.c_int)]
     L.hh_first_order.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, DP]
+    L.hh_widen_bits.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
     L.hh_drive_cycles_frac.restype = ctypes.c_double
     L.hh_drive_cycles_frac.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int64]
     L.hh_drive_phasor.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
@@ -531,3 +532,27 @@ def test_drive_phasor_tables_match_the_exact_phasor(hh, K):
         worst_sin = max(worst_sin, abs(complex(old[0], old[1]) - ex))
     assert worst_tab < 1.5e-15, worst_tab
     assert worst_sin < 1e-10, worst_sin
+
+
+def test_integer_widening_is_the_ieee_conversion(hh):
+    """widen_bits (the epilogue's FP32 -> FP64 in integer instructions)
+    against the exact conversion numpy performs, bit for bit: both zeros,
+    every subnormal exponent (each mantissa bit alone, plus the smallest and
+    the largest subnormal), the normal range's edges, the infinities, and 2^21
+    random bit patterns; NaN inputs give NaN of the same sign."""
+    pats = [0x00000000, 0x80000000, 0x00000001, 0x80000001, 0x007fffff, 0x807fffff, 0x00800000,
+            0x7f7fffff, 0xff7fffff, 0x3f800000, 0xbf800000, 0x7f800000, 0xff800000]
+    pats += [1 << b for b in range(23)] + [(1 << b) | 0x80000000 for b in range(23)]
+    pats += [(1 << b) | 1 for b in range(1, 23)]
+    rng = np.random.default_rng(11)
+    bits = np.concatenate([np.array(pats, dtype=np.uint32), rng.integers(0, 2**32, 1 << 21, dtype=np.uint32)])
+    out = np.zeros(bits.size, dtype=np.uint64)
+    hh.hh_widen_bits(bits.ctypes.data, out.ctypes.data, bits.size)
+    f = bits.view(np.float32)
+    got = out.view(np.float64)
+    nan = np.isnan(f)
+    assert nan.sum() > 1000 and (~nan).sum() > 1_000_000
+    want = f[~nan].astype(np.float64)
+    assert np.array_equal(got[~nan].view(np.uint64), want.view(np.uint64))
+    assert np.isnan(got[nan]).all()
+    assert np.array_equal(np.signbit(got[nan]), np.signbit(f[nan]))
