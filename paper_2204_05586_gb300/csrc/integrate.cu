@@ -271,20 +271,21 @@ __device__ __forceinline__ void integrate_pair_body(const IntegrateArgs& a)
             }
         }
         __syncwarp();
-        // epilogue, one lane per pair of the tile: the lanes' sub-trees
-        // combined in the canonical tree, then the FP64 part of both samples
         grid_dependency_wait();
-        if (wl < spw) {
-            const int t = wl;
-            const int64_t gp = base + 2 * t;
+        // epilogue: the lanes' sub-trees of a pair combined in the canonical
+        // tree (one lane per pair), then the FP64 part of both samples: in a
+        // tile of 32 pairs each lane finishes both samples of its pair, in a
+        // smaller tile two lanes share a pair, one sample each (an FP64 warp
+        // instruction costs the same however few lanes are active)
+        if (wl < spw && lg > 0) {
+            const int64_t gp = base + 2 * wl;
             const int si = gp < a.total_samples ? find_index(a.sample_offsets, a.n_sims, gp) : 0;
             if (gp < a.total_samples && SPINSIM_INB(si >= 0 && si < a.n_sims, 0) &&
                 SPINSIM_INB(gp - a.sample_offsets[si] >= 0, 1) && gp - a.sample_offsets[si] < a.sims[si].K) {
-                const int64_t k = gp - a.sample_offsets[si];
                 const DevSim& s = a.sims[si];
                 const int lg_use = min(lg, (int)s.seg_log2);
                 const int spl_log2 = s.seg_log2 - lg_use;
-                Res* lanes = rec + (size_t)(w0 + (t << lg)) * kSlots;   // lane j's result: lanes[j * kSlots + spl_log2]
+                Res* lanes = rec + (size_t)(w0 + (wl << lg)) * kSlots;   // lane j's result: lanes[j * kSlots + spl_log2]
 #pragma unroll 1
                 for (int d = 0; d < lg_use; d++)
 #pragma unroll 1
@@ -293,8 +294,23 @@ __device__ __forceinline__ void integrate_pair_body(const IntegrateArgs& a)
                         res_mul(lanes[(j + (1 << d)) * kSlots + spl_log2], lanes[j * kSlots + spl_log2], tmp);
                         lanes[j * kSlots + spl_log2] = tmp;
                     }
+            }
+        }
+        __syncwarp();
+        const int share = lg > 0 ? 1 : 0;                  // log2 of lanes per pair in the FP64 part
+        if (wl < (spw << share)) {
+            const int t = wl >> share;
+            const int64_t gp = base + 2 * t;
+            const int si = gp < a.total_samples ? find_index(a.sample_offsets, a.n_sims, gp) : 0;
+            if (gp < a.total_samples && SPINSIM_INB(si >= 0 && si < a.n_sims, 0) &&
+                SPINSIM_INB(gp - a.sample_offsets[si] >= 0, 1) && gp - a.sample_offsets[si] < a.sims[si].K) {
+                const int64_t k = gp - a.sample_offsets[si];
+                const DevSim& s = a.sims[si];
+                const int lg_use = min(lg, (int)s.seg_log2);
+                const int spl_log2 = s.seg_log2 - lg_use;
+                const Res& pr = rec[(size_t)(w0 + (t << lg)) * kSlots + spl_log2];
 #pragma unroll 1
-                for (int h = 0; h < 2; h++) {
+                for (int h = share ? (wl & 1) : 0; h < 2; h += 1 + share) {
                     const int64_t kh = k + h;
                     if (kh >= s.K) break;                    // the unused slot of an odd simulation
                     double* out = a.U + (gp + h) * OPD;
@@ -302,7 +318,7 @@ __device__ __forceinline__ void integrate_pair_body(const IntegrateArgs& a)
                         store_identity(N, out);
                     } else {
                         typename ResType<N, float>::type r;
-                        unpack(lanes[spl_log2], h, r);
+                        unpack(pr, h, r);
                         const double2 b = bg[2 * (w0 + t) + h];
                         SampleExact sx;
                         make_exact<N, false>(s, kh, b.x, b.y, sx);

@@ -268,6 +268,15 @@ def test_launch_shape_does_not_change_results():
             got.append(out["states"].cpu().numpy())
     for g in got[1:]:
         assert np.array_equal(g, got[0])
+    # the full sensing run: one round of bulk tiles and a tail whose split
+    # (lanes per pair) follows from the shape, every shape bit for bit alike
+    req = W.spin_one_sensing()
+    got = []
+    for lanes, block in ((1, 256), (1, 64), (2, 128), (4, 64)):
+        (out,), _ = gpu_run([req], precision=S.PREC_FP32_BULK, lanes=lanes, block=block)
+        got.append(out["states"].cpu().numpy())
+    for g in got[1:]:
+        assert np.array_equal(g, got[0])
 
 
 def test_alone_equals_in_batch():
