@@ -57,12 +57,12 @@ def chain_flops_per_sample(spin_x2: int, run: int) -> float:
     return (run - 1) / run * 32.0 + 16.0 + 30.0
 L2_FLUSH_BYTES = 256 << 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one integrate launch
-# (profiles/integrate_kernel_spin_one_sensing.md, integrate_tones_kernel_multitone.md,
-# integrate_su3_kernel_su3.md: the operators stay in L2; profiles/launches_sweep512.md:
-# the 512-simulation sweep's tau = 0 launch scaled by samples to the 4096-simulation
-# sweep's, whose 12.8 GB of operators go to HBM)
-INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 88320, ("multitone", "fp32"): 121088, ("su3", "fp64"): 1419776,
-                           ("sweep", "fp32"): 12340000000}
+# (profiles/integrate_kernel_spin_one_sensing.md, integrate_kernel_neural.md,
+# integrate_tones_kernel_multitone.md, integrate_su3_kernel_su3.md: the operators stay
+# in L2; profiles/launches_sweep512.md: the 512-simulation sweep's tau = 0 launch scaled
+# by samples to the 4096-simulation sweep's, whose 12.8 GB of operators go to HBM)
+INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 87808, ("neural", "fp32"): 98304, ("multitone", "fp32"): 121088,
+                           ("su3", "fp64"): 1419776, ("sweep", "fp32"): 12330000000}
 
 
 def algorithmic_flops_per_step(spin_x2: int, tau: int, n_tones: int = 0) -> float:
