@@ -187,8 +187,9 @@ __device__ __forceinline__ void integrate_body(const IntegrateArgs& a)
 // odd sample count by one unused slot), so a pair never spans two
 // simulations; the slot past an odd simulation's last sample is computed
 // with its partner's context and not stored.  Tiles hold 2 x (32 >> lg)
-// samples, G = 2^lg lanes per pair as in integrate_body; the epilogue's lanes
-// finish both samples of their pair.
+// samples, G = 2^lg lanes per pair as in integrate_body; in the epilogue a
+// lane finishes both samples of its pair in a tile of 32 pairs, one of them
+// in a smaller tile (two lanes per pair).
 template <int N, int METHOD, int SMALL>
 __device__ __forceinline__ void integrate_pair_body(const IntegrateArgs& a)
 {
