@@ -310,6 +310,25 @@ def test_paired_kernel_odd_sample_counts(oracle_mod):
         assert_parity(outs[i], oracle_run(oracle_mod, q), TOL[S.PREC_FP32_BULK], f"K={a.shape[0]}")
 
 
+def test_paired_tail_tiles_mix_segment_splits(oracle_mod):
+    """One batch of more than a wave of paired samples whose simulations take
+    5, 20 and 150 steps per sample (segment splits 2, 4 and 8): its tail tiles
+    use as many lanes per pair as the smallest split allows, so they hold pairs
+    whose lanes each run several segments, and two lanes per pair share the
+    FP64 epilogue.  Every simulation equals its run alone bit for bit, in
+    either order, and matches the oracle."""
+    base = W.field(bias_hz=700e3, drive_x_hz=1e3, drive_hz=700.2e3, quad_hz=300.0, pulses=[(30.0, 6e-3, 2e-3)])
+    reqs = [W.request(2, base, 0.0, K * 1e-6, 1e-6 / L, 1e-6) for K, L in ((26001, 5), (31000, 20), (27003, 150))]
+    outs, _ = gpu_run(reqs, precision=S.PREC_FP32_BULK, lanes=1, block=256)
+    outs_rev, _ = gpu_run(reqs[::-1], precision=S.PREC_FP32_BULK, lanes=1, block=256)
+    for i, q in enumerate(reqs):
+        (alone,), _ = gpu_run([q], precision=S.PREC_FP32_BULK, lanes=1, block=256)
+        a = alone["states"].cpu().numpy()
+        assert np.array_equal(outs[i]["states"].cpu().numpy(), a), i
+        assert np.array_equal(outs_rev[len(reqs) - 1 - i]["states"].cpu().numpy(), a), i
+        assert_parity(outs[i], oracle_run(oracle_mod, q), TOL[S.PREC_FP32_BULK], f"L={round(q['dt_out'] / q['dt'])}")
+
+
 def test_host_buffers_match_device_buffers():
     req = W.spin_one_sensing(t_end=2e-3)
     (dev,), _ = gpu_run([req], precision=S.PREC_FP32_BULK)
