@@ -605,6 +605,8 @@ def run_ours(args, world, rank, local):
                 "steps": args.serve_requests, "warmup": 8, "ms_per_step": sv["span_s"] * 1e3 / args.serve_requests,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 bulk / f64 chain",
                 "data": "synthetic", "config": {"workload": sv["workload"]}, "serving": sv}
+        if sv.get("clocks"):
+            line["clocks"] = sv["clocks"]      # sampled over the served stream
         if rank == 0:
             print(json.dumps(line), flush=True)
         if world > 1:
