@@ -392,30 +392,58 @@ SPINSIM_HD double drive_cycles_frac(double f, double t0, double dt, int64_t m)
     return x - floor(x);
 }
 
-// Entry e of a simulation's drive phasor tables (see kPhaseLo): the turn
-// e^{i 2 pi f_d dt_out e} for e < kPhaseLo, else e^{i beta} at interval
+// Entry e of one phasor table (see kPhaseLo) of a tone of frequency hz and
+// phase `phase` (the drive or a further tone): the turn e^{i 2 pi hz dt_out e}
+// for e < kPhaseLo, else the tone's phasor e^{i beta} at interval
 // k - 1 = (e - kPhaseLo) kPhaseLo.
-SPINSIM_HD cx<double> drive_phasor_entry(const DevSim& s, int64_t e)
+SPINSIM_HD cx<double> phasor_entry(double hz, double phase, const DevSim& s, int64_t e)
 {
     const bool turn = e < kPhaseLo;
-    const double cyc = turn ? drive_cycles_frac(s.drive_hz, 0.0, s.dt_out, e)
-                            : drive_cycles_frac(s.drive_hz, s.t_start, s.dt_out, (e - kPhaseLo) << kPhaseLoLog2);
-    double b = kTwoPi * cyc + (turn ? 0.0 : s.drive_phase);
+    const double cyc = turn ? drive_cycles_frac(hz, 0.0, s.dt_out, e)
+                            : drive_cycles_frac(hz, s.t_start, s.dt_out, (e - kPhaseLo) << kPhaseLoLog2);
+    double b = kTwoPi * cyc + (turn ? 0.0 : phase);
     b -= kTwoPi * rint(b * (1.0 / kTwoPi));
     const SinCos<double> sc = sincos_cold(b);
     return cmk(sc.c, sc.s);
 }
 
-// e^{i beta_k} of interval k >= 1 from the tables (two roundings): the
-// epilogue's FP64 drive phasor.  (The bulk keeps its FP32 sine and cosine of
-// the drive phase: reading the table at the start of every tile measured
-// slower in the issue-bound step loop.)
-SPINSIM_HD cx<double> drive_phasor_tab(const DevSim& s, int64_t k)
+SPINSIM_HD cx<double> drive_phasor_entry(const DevSim& s, int64_t e)
+{
+    return phasor_entry(s.drive_hz, s.drive_phase, s, e);
+}
+
+// Entry e of all of a simulation's tables (phasor_entries(K, n_tones) in
+// all): table e / phase_entries(K), the drive's first, then further tone j's.
+SPINSIM_HD cx<double> sim_phasor_entry(const DevSim& s, int64_t e)
+{
+    const int64_t n = phase_entries(s.K);
+    const int t = (int)(e / n);
+    const int64_t r = e - (int64_t)t * n;
+    return t == 0 ? drive_phasor_entry(s, r) : phasor_entry(s.tone_hz[t - 1], s.tone_phase[t - 1], s, r);
+}
+
+// A tone's phasor at interval k >= 1 from its table (two roundings).
+SPINSIM_HD cx<double> phasor_tab(const double* tab, int64_t k)
 {
     const int64_t m = k - 1;
-    const double* lo = s.eb_tab + 2 * (m & (kPhaseLo - 1));
-    const double* hi = s.eb_tab + 2 * (kPhaseLo + (m >> kPhaseLoLog2));
+    const double* lo = tab + 2 * (m & (kPhaseLo - 1));
+    const double* hi = tab + 2 * (kPhaseLo + (m >> kPhaseLoLog2));
     return cmul(cmk(hi[0], hi[1]), cmk(lo[0], lo[1]));
+}
+
+// e^{i beta_k} of interval k >= 1 from the tables: the epilogue's FP64 drive
+// phasor.  (The bulk keeps its FP32 sine and cosine of the drive phase:
+// reading the table at the start of every tile measured slower in the
+// issue-bound step loop.)
+SPINSIM_HD cx<double> drive_phasor_tab(const DevSim& s, int64_t k)
+{
+    return phasor_tab(s.eb_tab, k);
+}
+
+// e^{i beta_j,k} of further tone j at interval k >= 1 from its table.
+SPINSIM_HD cx<double> tone_phasor_tab(const DevSim& s, int j, int64_t k)
+{
+    return phasor_tab(s.eb_tab + 2 * (int64_t)(j + 1) * phase_entries(s.K), k);
 }
 
 // Shape of z pulse p at u = (t - c_p) / w_p: a Gaussian exp(-u^2/2) (w_p the
@@ -602,9 +630,15 @@ SPINSIM_HD void make_exact(const DevSim& s, int64_t k, double beta, double gsum,
     if constexpr (TONES) {
         const double t_prev = s.t_start + (double)(k - 1) * s.dt_out;
         for (int j = 0; j < s.n_tones; j++) {
-            const SinCos<double> e = sincos_cold(tone_phase_at(s.tone_hz[j], s.tone_phase[j], t_prev));
-            x.tb_re[j] = e.c;
-            x.tb_im[j] = e.s;
+            if (s.eb_tab) {
+                const cx<double> e = tone_phasor_tab(s, j, k);
+                x.tb_re[j] = e.r;
+                x.tb_im[j] = e.i;
+            } else {
+                const SinCos<double> e = sincos_cold(tone_phase_at(s.tone_hz[j], s.tone_phase[j], t_prev));
+                x.tb_re[j] = e.c;
+                x.tb_im[j] = e.s;
+            }
         }
     } else {
         (void)k;

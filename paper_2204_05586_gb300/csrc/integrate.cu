@@ -366,9 +366,10 @@ __global__ void __launch_bounds__(256) integrate_su3_kernel(IntegrateArgs a)
     integrate_body<3, double, METHOD, false, true, true>(a);
 }
 
-// The drive phasor tables of a launch group, one thread per entry: the
-// simulation that owns entry j is the last one whose first entry is at most j
-// (simulations with no entries share their successor's offset).
+// The phasor tables (drive and further tones) of a launch group, one thread
+// per entry: the simulation that owns entry j is the last one whose first
+// entry is at most j (simulations with no entries share their successor's
+// offset).
 __global__ void __launch_bounds__(256) phase_table_kernel(const DevSim* sims, int n_sims, int64_t n_entries,
                                                           double* tab)
 {
@@ -385,8 +386,8 @@ __global__ void __launch_bounds__(256) phase_table_kernel(const DevSim* sims, in
         }
         const DevSim& s = sims[lo];
         const int64_t e = j - s.eb_off;
-        if (!SPINSIM_INB(e >= 0, 2) || e >= phase_entries(s.K)) continue;   // past the last entry (layout slack)
-        const cx<double> v = drive_phasor_entry(s, e);
+        if (!SPINSIM_INB(e >= 0, 2) || e >= phasor_entries(s.K, s.n_tones)) continue;   // past the last entry (layout slack)
+        const cx<double> v = sim_phasor_entry(s, e);
         tab[2 * j] = v.r;
         tab[2 * j + 1] = v.i;
     }

@@ -66,17 +66,14 @@ inline ChainGeom chain_geom(int64_t K)
 // e^{i beta_k} with beta_k the drive phase at t_{k-1}, is the product of two
 // table entries, hi[(k - 1) >> kPhaseLoLog2] (the phasor at every kPhaseLo-th
 // interval) and lo[(k - 1) & (kPhaseLo - 1)] (the turn over the remaining
-// intervals), instead of a sine and cosine per sample.  Entries of one
-// simulation: the kPhaseLo turns, then the hi phasors.
+// intervals), instead of a sine and cosine per sample.  One table of a
+// simulation: the kPhaseLo turns, then the hi phasors (phase_entries(K)
+// entries); a simulation with further tones has one such table per tone after
+// the drive's (phasor_entries(K, n_tones) entries in all).
 constexpr int kPhaseLoLog2 = 7;
 constexpr int kPhaseLo = 1 << kPhaseLoLog2;
 __host__ __device__ inline int64_t phase_entries(int64_t K) { return K >= 2 ? kPhaseLo + ((K - 2) >> kPhaseLoLog2) + 1 : 0; }
-// An upper bound of the entries of `count` simulations with `samples` samples
-// in all (the arena layout of a group).
-inline int64_t phase_entries_bound(int64_t count, int64_t samples)
-{
-    return count * (kPhaseLo + 1) + samples / kPhaseLo;
-}
+__host__ __device__ inline int64_t phasor_entries(int64_t K, int n_tones) { return phase_entries(K) * (1 + n_tones); }
 
 // Per-simulation parameters on the device, precomputed on the host in FP64.
 struct DevSim {
@@ -85,8 +82,8 @@ struct DevSim {
     double* ops;                 // [K][N][N] complex or nullptr
     int64_t K, L;
     int64_t sample_offset;       // first sample of this simulation in the operator buffer
-    // drive phasor tables of this simulation, (re, im) pairs in FP64
-    // (nullptr: a sine and cosine of the drive phase per sample instead)
+    // phasor tables of this simulation's drive and further tones, (re, im)
+    // pairs in FP64 (nullptr: a sine and cosine of each phase per sample instead)
     const double* eb_tab;
     int64_t eb_off;              // first entry of this simulation in its launch group's table
     int32_t chain_run;           // samples per lane run at the bottom of the chain tree

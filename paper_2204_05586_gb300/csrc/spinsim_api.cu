@@ -67,7 +67,7 @@ struct Group {
     int levels = 1;                // chain-tree levels of the tallest simulation
     int64_t nodes[kMaxLevels] = {};  // chain-tree nodes per level, all simulations
     size_t sims_off = 0, soff_off = 0, loff_off = 0, counter_off = 0, U_off = 0, chain_off = 0;
-    size_t phase_off = 0;                   // drive phasor tables (FP64 pairs)
+    size_t phase_off = 0;                   // phasor tables of the drives and further tones (FP64 pairs)
     int64_t phase_n = 0;                    // their entries, all simulations of the group
     ChainLayout chain{};
 };
@@ -298,7 +298,7 @@ size_t table_bytes(int64_t n, int levels)
 }
 
 // Scratch bytes of one group (spin) of a batch.
-// The drive phasor tables of `entries` entries: FP64 (re, im) pairs.
+// The phasor tables of `entries` entries: FP64 (re, im) pairs.
 size_t phase_bytes(int64_t entries) { return round_up((size_t)entries * 2 * sizeof(double), 256); }
 
 size_t group_bytes(int spin_x2, int64_t n, int64_t samples, const int64_t* nodes, int levels, int64_t phase_n)
@@ -363,12 +363,12 @@ struct Footprint {
     {
         for (int& l : levels) l = 1;
     }
-    void add(int spin_x2, int variant, int64_t K, size_t staged_bytes)
+    void add(int spin_x2, int variant, int64_t K, int n_tones, size_t staged_bytes)
     {
         const int g = (spin_x2 - 1) * kVariants + variant;
         count[g] += 1;
         samples[g] += variant_pairs(spin_x2, precision, variant) ? pair_slots(K) : K;
-        phase[g] += phase_entries(K);
+        phase[g] += phasor_entries(K, n_tones);
         const ChainGeom cg = chain_geom(K);
         levels[g] = std::max(levels[g], cg.top + 1);
         for (int l = 0; l <= cg.top; l++) nodes[g][l] += cg.nodes[l];
@@ -408,7 +408,7 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
             if (checked[i].status == SPINSIM_OK && reqs[i].spin_x2 == spin && checked[i].variant == variant) {
                 g.idx.push_back(i);
                 g.samples += variant_pairs(spin, precision, variant) ? pair_slots(checked[i].K) : checked[i].K;
-                g.phase_n += phase_entries(checked[i].K);
+                g.phase_n += phasor_entries(checked[i].K, reqs[i].field.n_tones);
                 g.steps += (double)checked[i].K * (double)checked[i].L;
                 g.min_seg_log2 = std::min(g.min_seg_log2, seg_log2_of(checked[i].L));
                 const ChainGeom cg = chain_geom(checked[i].K);
@@ -493,7 +493,7 @@ void fill_tables(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res,
             so += variant_pairs(g.spin_x2, h->cfg.precision, g.variant) ? pair_slots(d.K) : d.K;
             d.eb_tab = reinterpret_cast<const double*>(base + g.phase_off) + 2 * eo;
             d.eb_off = eo;
-            eo += phase_entries(d.K);
+            eo += phasor_entries(d.K, d.n_tones);
             const ChainGeom cg = chain_geom(d.K);
             d.chain_run = cg.run;
             d.chain_top = cg.top;
@@ -963,7 +963,7 @@ int64_t spinsim_footprint(spinsim_handle h, const spinsim_request* reqs, int64_t
     for (int64_t i = 0; i < n; i++) {
         Checked c = check_request(&reqs[i]);
         if (c.status != SPINSIM_OK) return c.status;
-        fp.add(reqs[i].spin_x2, request_variant(h->cfg, reqs[i], c.K, c.L), c.K, 0);
+        fp.add(reqs[i].spin_x2, request_variant(h->cfg, reqs[i], c.K, c.L), c.K, reqs[i].field.n_tones, 0);
     }
     return n > 0 ? (int64_t)fp.total() : 0;
 }
@@ -1452,7 +1452,7 @@ static int serving_pump(spinsim_s* h)
             if (c.status == SPINSIM_OK) c.status = precision_status(h->cfg, tk.req);
             if (c.status == SPINSIM_OK) c.variant = request_variant(h->cfg, tk.req, c.K, c.L);
             Footprint next = fp;
-            next.add(tk.req.spin_x2, c.variant, c.K, tk.staged);
+            next.add(tk.req.spin_x2, c.variant, c.K, tk.req.field.n_tones, tk.staged);
             if (next.total() > room) break;
             fp = next;
             h->pending.pop_front();
@@ -1520,7 +1520,7 @@ int spinsim_submit(spinsim_handle h, const spinsim_request* req, spinsim_result*
     if (c.status == SPINSIM_OK) {
         tk.staged = staging_bytes(*req, *res, c.K, false, h->cfg.direct_host_outputs != 0);
         Footprint fp(h->cfg.precision);
-        fp.add(req->spin_x2, request_variant(h->cfg, *req, c.K, c.L), c.K, tk.staged);
+        fp.add(req->spin_x2, request_variant(h->cfg, *req, c.K, c.L), c.K, req->field.n_tones, tk.staged);
         tk.bytes = round_up(fp.total(), 256);
         if (tk.bytes > h->budget) c.status = res->status = SPINSIM_E_NOMEM;   // could never be admitted
     }

@@ -167,7 +167,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
     // operator slots: the paired kernels place an odd K's pairs in K + 1 slots
     const int64_t slots = variant_pairs(spin, cfg->precision, variant) ? pair_slots(K) : K;
     const size_t U_off = off; off += up256((size_t)slots * opd * 8);
-    const int64_t phase_n = phase_entries(K);
+    const int64_t phase_n = phasor_entries(K, req->field.n_tones);
     const size_t phase_off = off; off += up256((size_t)phase_n * 2 * sizeof(double));
     const size_t chain_off = off; off += cl.bytes;
     if (off > kStaticScratchBytes) return res->status = SPINSIM_E_NOMEM;   // K beyond the static maximum

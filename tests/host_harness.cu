@@ -181,32 +181,35 @@ void hh_widen_bits(const uint32_t* in, uint64_t* out, int64_t n)
 // The fractional drive cycles f (t0 + m dt) (drive_cycles_frac).
 double hh_drive_cycles_frac(double f, double t0, double dt, int64_t m) { return drive_cycles_frac(f, t0, dt, m); }
 
-// The FP64 drive phasor e^{i beta_k} of interval k of a request, from the
-// two-level tables the integrate epilogue reads (built here on the host by
-// drive_phasor_entry, read by drive_phasor_tab; table = 1), or from the drive
-// phase and a sine and cosine (table = 0): out = (re, im).
-void hh_drive_phasor(const spinsim_config* cfg, const spinsim_request* r, int64_t K, int64_t L, int64_t k, int table,
-                     double* out)
+// The FP64 phasor e^{i beta_k} of interval k of a request's drive (tone = -1)
+// or of its further tone `tone`, from the two-level tables the integrate
+// epilogue reads (all of the request's tables built here on the host by
+// sim_phasor_entry, read by drive_phasor_tab / tone_phasor_tab; table = 1), or
+// from the phase and a sine and cosine (table = 0): out = (re, im).
+void hh_phasor(const spinsim_config* cfg, const spinsim_request* r, int64_t K, int64_t L, int64_t k, int tone,
+               int table, double* out)
 {
     DevSim d;
     fill_devsim(*cfg, *r, K, L, d);
+    cx<double> v;
     if (table) {
-        const int64_t n = phase_entries(K);
+        const int64_t n = phasor_entries(K, d.n_tones);
         std::vector<double> tab((size_t)(2 * n));
         for (int64_t e = 0; e < n; e++) {
-            const cx<double> v = drive_phasor_entry(d, e);
-            tab[(size_t)(2 * e)] = v.r;
-            tab[(size_t)(2 * e + 1)] = v.i;
+            const cx<double> x = sim_phasor_entry(d, e);
+            tab[(size_t)(2 * e)] = x.r;
+            tab[(size_t)(2 * e + 1)] = x.i;
         }
         d.eb_tab = tab.data();
-        const cx<double> v = drive_phasor_tab(d, k);
-        out[0] = v.r;
-        out[1] = v.i;
+        v = tone < 0 ? drive_phasor_tab(d, k) : tone_phasor_tab(d, tone, k);
     } else {
-        const SinCos<double> e = sincos_cold(drive_phase_at(d, k));
-        out[0] = e.c;
-        out[1] = e.s;
+        const double b = tone < 0 ? drive_phase_at(d, k)
+                                  : tone_phase_at(d.tone_hz[tone], d.tone_phase[tone], d.t_start + (double)(k - 1) * d.dt_out);
+        const SinCos<double> e = sincos_cold(b);
+        v = cmk(e.c, e.s);
     }
+    out[0] = v.r;
+    out[1] = v.i;
 }
 
 // rest part only (U - I - F(v)) in double

@@ -51,8 +51,8 @@ def hh(tmp_path_factory):
     L.hh_widen_bits.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
     L.hh_drive_cycles_frac.restype = ctypes.c_double
     L.hh_drive_cycles_frac.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int64]
-    L.hh_drive_phasor.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
-                                  ctypes.c_int, DP]
+    L.hh_phasor.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                            ctypes.c_int, ctypes.c_int, DP]
     L.hh_series_match.argtypes = [ctypes.c_double, ctypes.c_int]
     L.hh_expm_general.argtypes = [DP, DP]
     L.hh_expm_general_rest.argtypes = [DP, DP]
@@ -522,16 +522,45 @@ def test_drive_phasor_tables_match_the_exact_phasor(hh, K):
     worst_tab, worst_sin = 0.0, 0.0
     for k in ks:
         out = np.zeros(4)
-        hh.hh_drive_phasor(ctypes.addressof(cfg), ctypes.addressof(r), K, 100, k, 1, P(out))
+        hh.hh_phasor(ctypes.addressof(cfg), ctypes.addressof(r), K, 100, k, -1, 1, P(out))
         cyc = exact_cycles(f["drive_hz"], req["t_start"], dt_out, k - 1)
         b = 2 * mpmath.pi * mpmath.mpf(cyc.numerator) / cyc.denominator + f["drive_phase"]
         ex = complex(mpmath.cos(b), mpmath.sin(b))
         worst_tab = max(worst_tab, abs(complex(out[0], out[1]) - ex))
         old = np.zeros(4)
-        hh.hh_drive_phasor(ctypes.addressof(cfg), ctypes.addressof(r), K, 100, k, 0, P(old))
+        hh.hh_phasor(ctypes.addressof(cfg), ctypes.addressof(r), K, 100, k, -1, 0, P(old))
         worst_sin = max(worst_sin, abs(complex(old[0], old[1]) - ex))
     assert worst_tab < 1.5e-15, worst_tab
     assert worst_sin < 1e-10, worst_sin
+
+
+@pytest.mark.parametrize("K", [2, 130, 100001])
+def test_tone_phasor_tables_match_the_exact_phasor(hh, K):
+    """Each further tone's table (after the drive's in the same block) gives
+    e^{i beta_j,k} within 1.5e-15 of the exact phase's 30-digit sin/cos, for
+    every tone, both table edges and the last interval; the drive's entries
+    are unchanged by the tones' tables behind them."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    from paper_2204_05586_gb300 import spinsim as S, workloads as W
+    tones = [(1e3, 1e3, 700.5e3, 0.4), (0.5e3, 0.0, 698e3, 1.1), (0.0, 0.8e3, 705.3e3, -0.6)]
+    f = W.field(bias_hz=700e3, drive_x_hz=2e3, drive_hz=700.7e3, drive_phase=1.1, quad_hz=400.0, tones=tones)
+    dt_out = 1e-6
+    req = W.request(2, f, 3e-3, 3e-3 + K * dt_out, 1e-8, dt_out)
+    cfg = S.make_config(precision=S.PREC_FP64)
+    r = S.make_request(req)
+    assert S.spinsim_counts(r)[1] == K
+    ks = sorted({1, min(128, K - 1), min(129, K - 1), K - 1, K // 2 + 1})
+    worst = 0.0
+    for j in range(-1, len(tones)):
+        hz, ph = (f["drive_hz"], f["drive_phase"]) if j < 0 else (tones[j][2], tones[j][3])
+        for k in ks:
+            out = np.zeros(2)
+            hh.hh_phasor(ctypes.addressof(cfg), ctypes.addressof(r), K, 100, k, j, 1, P(out))
+            cyc = exact_cycles(hz, req["t_start"], dt_out, k - 1)
+            b = 2 * mpmath.pi * mpmath.mpf(cyc.numerator) / cyc.denominator + ph
+            worst = max(worst, abs(complex(out[0], out[1]) - complex(mpmath.cos(b), mpmath.sin(b))))
+    assert worst < 1.5e-15, worst
 
 
 def test_integer_widening_is_the_ieee_conversion(hh):
