@@ -180,6 +180,7 @@ SampleFn pick_variant4(int method, int variant)
         case kVariantSmallSine:
         case kVariantSmallSineTau0: return pick_method4<N, 2, false>(method);
         case kVariantTones: return pick_method4<N, false, true>(method);
+        case kVariantSmallTones: return pick_method4<N, 1, true>(method);
         default: return nullptr;
     }
 }
@@ -208,6 +209,9 @@ SampleFn pick_variant(int method, int variant)
     switch (variant) {
         case kVariantGeneral: return pick_method<N, R, false, false>(method);
         case kVariantTones: return pick_method<N, R, false, true>(method);
+        case kVariantSmallTones:
+            if constexpr (sizeof(R) == 4) return pick_method<N, R, 1, true>(method);
+            else return nullptr;
         case kVariantSmall:
         case kVariantSmallTau0:
             if constexpr (sizeof(R) == 4) return pick_method<N, R, 1, false>(method);

@@ -353,10 +353,10 @@ __global__ void __launch_bounds__(256) integrate_pair_kernel(IntegrateArgs a)
 // ms).  The cap is on this kernel alone: given to the others, even as a
 // minimum of one block, it changes their register allocation (126 -> 140) and
 // costs 9%.
-template <int N, typename R, int METHOD>
+template <int N, typename R, int METHOD, int SMALL>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) integrate_tones_kernel(IntegrateArgs a)
 {
-    integrate_body<N, R, METHOD, false, true>(a);
+    integrate_body<N, R, METHOD, SMALL, true>(a);
 }
 
 // Full su(3) spin-one Hamiltonians (quadrupole drives, tones included): FP64.
@@ -411,7 +411,7 @@ static void* su3_kernel_ptr()
 template <int N, typename R, int METHOD, int SMALL, bool TONES>
 static void* kernel_ptr()
 {
-    if constexpr (TONES) return (void*)integrate_tones_kernel<N, R, METHOD>;
+    if constexpr (TONES) return (void*)integrate_tones_kernel<N, R, METHOD, SMALL>;
     else return (void*)integrate_kernel<N, R, METHOD, SMALL>;
 }
 
@@ -443,6 +443,9 @@ static void* pick_variant(int method, int variant)
     switch (variant) {
         case kVariantGeneral: return pick_method<N, R, false, false>(method);
         case kVariantTones: return pick_method<N, R, false, true>(method);
+        case kVariantSmallTones:
+            if constexpr (sizeof(R) == 4) return pick_method<N, R, kSmallGauss, true>(method);
+            else return nullptr;
         // the small-angle variants exist for FP32-bulk only (FP64 keeps the
         // general series, its terms sized for double precision) and run in the
         // paired kernel, two samples per thread (the tau = 0 variants exist for

@@ -332,7 +332,8 @@ bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, in
 // The small-angle variants of spin-one requests whose Lie-Trotter squarings
 // come out as tau = 0 (the usual case in the rotating frame) have kernels of
 // their own, with the closed-form exponential and no runtime tau branch in the
-// step loop.
+// step loop.  Requests with further tones inside the small-angle bounds (and
+// Gaussian pulses only) run the tones kernel with the small-angle series.
 enum IntegrateVariant {
     kVariantGeneral = 0,
     kVariantSmall = 1,
@@ -340,9 +341,10 @@ enum IntegrateVariant {
     kVariantSU3 = 3,
     kVariantSmallSine = 4,
     kVariantSmallTau0 = 5,
-    kVariantSmallSineTau0 = 6
+    kVariantSmallSineTau0 = 6,
+    kVariantSmallTones = 7
 };
-constexpr int kVariants = 7;
+constexpr int kVariants = 8;
 constexpr int kMaxGroups = 2 * kVariants;   // launch groups of one batch: spin-half and spin-one
 // The kernels' SMALL template argument: 0 general series; bit 0 the
 // small-angle series with Gaussian pulses, bit 1 with single sine cycles as

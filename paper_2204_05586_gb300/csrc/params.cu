@@ -136,14 +136,16 @@ Checked check_request(const spinsim_request* r)
 //   |w_d - w_r| <= |w_co0| + sum_p |amp_p| in the frame (w_co0 = 2 pi f_d in the lab);
 //   the half phases h_j of the Lie-Trotter diagonal, |h_j| <= |z|/2 + |q|/3 with
 //   |z| <= (|a| + |b|) dt (sum_p |amp_p| (+ 2 pi |B| in the lab)), |q| = |a + b| dt 2 pi |q_hz|;
-//   Phi/2 <= (|a| + |b|) dt (|Om+| + |Om-|) / 2.
+//   Phi/2 <= (|a| + |b|) dt (|Om+| + |Om-|) / 2, the sum over the drive and every
+//   further tone (the tones' own phasors are evaluated with the range-checked
+//   series, so their phases need no bound).
 // These bounds hold for every number of squarings (each divides the angles by 2^tau).
 // The small-angle variant evaluates Gaussian pulses only: a request with a
 // single-sine-cycle pulse takes the general variant.
 bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, int64_t L)
 {
     if (cfg.precision != SPINSIM_PREC_FP32_BULK || L < 1) return false;
-    if (r.field.n_tones > 0 || r.field.qd_on) return false;
+    if (r.field.qd_on) return false;
     const MethodNodes m = method_nodes(cfg.method);
     const spinsim_field& f = r.field;
     const double dt = r.dt_out / (double)L;
@@ -154,7 +156,10 @@ bool small_angle_request(const spinsim_config& cfg, const spinsim_request& r, in
     const double co = w_co * r.dt_out;
     const double z = wabs * dt * (pulse_w + (frame ? 0.0 : kTwoPiH * std::fabs(f.bias_hz)));
     const double q = r.spin_x2 == 2 ? wsum * dt * kTwoPiH * std::fabs(f.quad_hz) : 0.0;
-    const double om_perp = 0.5 * kTwoPiH * (std::fabs(f.drive_x_hz + f.drive_y_hz) + std::fabs(f.drive_x_hz - f.drive_y_hz));
+    // the transverse amplitude: the drive's |Om+| + |Om-| and each further tone's
+    double om_perp = 0.5 * kTwoPiH * (std::fabs(f.drive_x_hz + f.drive_y_hz) + std::fabs(f.drive_x_hz - f.drive_y_hz));
+    for (int j = 0; j < f.n_tones; j++)
+        om_perp += 0.5 * kTwoPiH * (std::fabs(f.tone_x_hz[j] + f.tone_y_hz[j]) + std::fabs(f.tone_x_hz[j] - f.tone_y_hz[j]));
     const double half_phi = 0.5 * wabs * dt * om_perp;
     const double h = 0.5 * z + q / 3.0;
     return co <= kTinyAngleBound && h <= kTinyAngleBound && half_phi <= kTinyAngleBound;
@@ -182,9 +187,10 @@ int request_tau(const spinsim_config& cfg, const spinsim_request& r, int64_t K, 
 int request_variant(const spinsim_config& cfg, const spinsim_request& r, int64_t K, int64_t L)
 {
     if (r.field.qd_on) return kVariantSU3;
-    if (r.field.n_tones > 0) return kVariantTones;
-    if (!small_angle_request(cfg, r, L)) return kVariantGeneral;
+    const bool small = small_angle_request(cfg, r, L);
     const bool sine = r.field.n_pulses > 0 && (r.field.pulse_sine_mask & ((1 << r.field.n_pulses) - 1)) != 0;
+    if (r.field.n_tones > 0) return small && !sine ? kVariantSmallTones : kVariantTones;
+    if (!small) return kVariantGeneral;
     if (r.spin_x2 == 2 && request_tau(cfg, r, K, L) == 0) return sine ? kVariantSmallSineTau0 : kVariantSmallTau0;
     return sine ? kVariantSmallSine : kVariantSmall;
 }

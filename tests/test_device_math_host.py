@@ -314,7 +314,7 @@ def test_tau0_variants_follow_the_squarings(hh):
     spin-half never takes them (no squarings); FP64 never takes a small-angle
     kernel."""
     from paper_2204_05586_gb300 import spinsim as S, workloads as W
-    GEN, SMALL, SINE, T0, SINE_T0 = 0, 1, 4, 5, 6
+    GEN, SMALL, TONES, SINE, T0, SINE_T0, SMALL_TONES = 0, 1, 2, 4, 5, 6, 7
 
     def pick(req, **cfg):
         c = S.make_config(**cfg)
@@ -335,6 +335,17 @@ def test_tau0_variants_follow_the_squarings(hh):
     for req in W.sweep(64, seed=W.SEED):
         v, tau = pick(req)
         assert v == (T0 if tau == 0 else SMALL), (v, tau)
+    # further tones: the small-angle tones kernel inside the bounds (tau at run
+    # time), the general one outside them, with a sine-cycle pulse, or in FP64
+    v, tau = pick(W.multitone_sensing())
+    assert v == SMALL_TONES and tau == 1, (v, tau)
+    assert pick(W.multitone_sensing(), precision=S.PREC_FP64)[0] == TONES
+    strong = W.multitone_sensing()
+    strong["field"]["tones"] = [(1e6, 0.0, 700e3, 0.0)]        # a 1 MHz tone: Phi/2 > 2^-6
+    assert pick(strong)[0] == TONES
+    sine = W.multitone_sensing()
+    sine["field"]["pulses"] = [(50.0, 0.05, 1e-3, "sine")]
+    assert pick(sine)[0] == TONES
 
 
 def test_small_angle_rule_on_workloads(hh):
@@ -355,6 +366,8 @@ def test_small_angle_rule_on_workloads(hh):
         assert rule(req) == 1
         assert rule(req, precision=S.PREC_FP64) == 0
     assert rule(W.spin_one_sensing(), rotating_frame=False) == 0
+    assert rule(W.multitone_sensing()) == 1     # further tones count in the transverse bound
+    assert rule(W.multitone_sensing(), precision=S.PREC_FP64) == 0
     assert rule(W.neural_pulse()) == 1          # sine-cycle pulse: the small-angle twin with sine cycles
     assert rule(W.neural_pulse(), precision=S.PREC_FP64) == 0
     big = W.spin_one_sensing(dt=1e-7)           # 10x larger steps: still inside the bound
