@@ -61,7 +61,7 @@ L2_FLUSH_BYTES = 256 << 20
 # integrate_tones_kernel_multitone.md, integrate_su3_kernel_su3.md: the operators stay
 # in L2; profiles/launches_sweep512.md: the 512-simulation sweep's tau = 0 launch scaled
 # by samples to the 4096-simulation sweep's, whose 12.8 GB of operators go to HBM)
-INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 87808, ("neural", "fp32"): 98304, ("multitone", "fp32"): 163840,
+INTEGRATE_TRAFFIC_BYTES = {("sensing", "fp32"): 87808, ("neural", "fp32"): 98304, ("multitone", "fp32"): 183552,
                            ("su3", "fp64"): 1012736, ("sweep", "fp32"): 12330000000}
 
 
