@@ -148,6 +148,23 @@ def test_methods_and_frames_fp64(oracle_mod, spin, frame, method):
     assert_parity(out, ref, 1e-10, f"spin={spin} frame={frame} method={method}")
 
 
+@pytest.mark.parametrize("spin", [1, 2])
+@pytest.mark.parametrize("method", [S.METHOD_MIDPOINT, S.METHOD_HEUN])
+@pytest.mark.parametrize("tones", [(), ((1e3, 0.5e3, 300.5e3, 0.3),)])
+def test_methods_fp32_bulk(oracle_mod, spin, method, tones):
+    """FP32-bulk at the midpoint and Heun methods (rotating frame, small
+    angles): the paired kernels, and with a further tone the tones kernel with
+    the small-angle series, against the oracle at the same method."""
+    f = W.field(bias_hz=300e3, drive_x_hz=3e3, drive_y_hz=1e3, drive_hz=300.2e3, drive_phase=0.7,
+                quad_hz=450.0 if spin == 2 else 0.0, pulses=[(120.0, 4e-4, 1e-4), (-60.0, 6e-4, 2e-4)],
+                tones=list(tones))
+    rng = np.random.default_rng(5)
+    req = W.request(spin, f, 1e-4, 2.1e-3, 2e-8, 1e-6, psi0=W.random_state(spin + 1, rng))
+    (out,), _ = gpu_run([req], precision=S.PREC_FP32_BULK, method=method)
+    ref = oracle_run(oracle_mod, req, method=method)
+    assert_parity(out, ref, TOL[S.PREC_FP32_BULK], f"spin={spin} method={method} tones={len(tones)}")
+
+
 @pytest.mark.parametrize("tau", [0, 3, 8])
 def test_trotter_squares_parameter(oracle_mod, tau):
     req = W.spin_one_sensing(t_end=5e-4, dt=1e-7)
