@@ -241,7 +241,7 @@ def samples_of(r):
 
 def chain_run(K):
     """The library's lane-run length of the chain (a function of K alone)."""
-    return min(8, max(4, -(-K // (32 * 608))))
+    return min(8, max(6 if K >= 16384 else 4, -(-K // (32 * 608))))
 
 
 def stratified(reqs, n):

@@ -32,14 +32,17 @@ constexpr int kFan = 32;                 // children of a node: one per lane of 
 constexpr int kMaxLevels = 12;           // 256 x 32^11 samples exceed any valid K
 constexpr int kLeftPerNode = kFan - 1;   // stored left-child products of a node's binary tree
 // The run length depends on K alone, so a simulation's result does not depend
-// on the batch it is in: at least 4 samples per lane, more once a simulation
-// has more level-0 nodes than a 152-SM GPU has SM sub-partitions (608), at
-// most 8.
+// on the batch it is in: at least 4 samples per lane (6 from 16384 samples:
+// fewer tree products per sample where a batch of long simulations fills the
+// GPU, while short requests keep their latency), more once a simulation has
+// more level-0 nodes than a 152-SM GPU has SM sub-partitions (608), at most 8.
 constexpr int64_t kRunSpread = 32 * 608;
+constexpr int64_t kLongRunK = 16384;
 inline int chain_run(int64_t K)
 {
     const int64_t r = (K + kRunSpread - 1) / kRunSpread;
-    return (int)(r < 4 ? 4 : (r > 8 ? 8 : r));
+    const int64_t lo = K >= kLongRunK ? 6 : 4;
+    return (int)(r < lo ? lo : (r > 8 ? 8 : r));
 }
 
 struct ChainGeom {
