@@ -171,13 +171,20 @@ def test_arena_and_pool_share_the_budget():
     assert np.array_equal(o["states"].cpu().numpy(), a)
 
 
-def test_footprint_is_what_the_arena_takes():
-    """On a fresh handle the arena is the batch's footprint rounded up to 1 MiB."""
+@pytest.mark.parametrize("prec", [S.PREC_FP32_BULK, S.PREC_FP64])
+@pytest.mark.parametrize("tones", [False, True])
+def test_footprint_is_what_the_arena_takes(prec, tones):
+    """On a fresh handle the arena is the batch's footprint rounded up to 1 MiB,
+    with requests with further tones (whose phasor tables follow the drive's)
+    in the batch too."""
     reqs = W.sweep(6, t_min=1e-4, t_max=3e-3)
-    with S.Simulator(precision=S.PREC_FP32_BULK) as sim:
+    if tones:
+        reqs += [W.multitone_sensing(t_end=3e-3), W.multitone_sensing(t_end=1.3e-3)]
+    with S.Simulator(precision=prec) as sim:
         need = S.spinsim_footprint(sim.handle, [S.make_request(q) for q in reqs])
-        sim.simulate(reqs)
+        outs = sim.simulate(reqs)
         m = S.spinsim_memory(sim.handle)
+    assert all(o["status"] == S.OK for o in outs)
     mib = 1 << 20
     assert m["arena"] == -(-need // mib) * mib
 
