@@ -346,9 +346,15 @@ template <int N>
 constexpr int state_doubles() { return 63 * 2 * N; }
 constexpr int kChainWarps = 4;   // warps per block of the chain kernels
 constexpr int kMaxRun = 8;       // the longest lane run (chain_run)
-// staged outputs of one level-0 node: 32 x kMaxRun samples of psi_k and <J>_k
+// The apply kernel's staging is sized for the batch's longest run (at most
+// kMaxRun), so that batches of shorter runs fit more blocks per SM.
+__host__ __device__ inline int apply_run(const ChainArgs& a)
+{
+    return a.max_run >= 1 && a.max_run <= kMaxRun ? a.max_run : kMaxRun;
+}
+// staged outputs of one level-0 node: 32 x run samples of psi_k and <J>_k
 template <int N>
-constexpr int stage_doubles() { return kFan * kMaxRun * (2 * N + 3); }
+__host__ __device__ constexpr int stage_doubles(int run) { return kFan * run * (2 * N + 3); }
 
 // ------------------------------------------------------------------ kernels
 // The up-sweep work of one node: its binary tree over the leaves already in
@@ -485,9 +491,10 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
     extern __shared__ __align__(16) double smem[];
     grid_dependency_wait();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double* V = smem + warp * (state_doubles<N>() + stage_doubles<N>());
+    const int mr = apply_run(a);
+    double* V = smem + warp * (state_doubles<N>() + stage_doubles<N>(mr));
     double* stage_psi = V + state_doubles<N>();            // [32 run][2N]
-    double* stage_spin = stage_psi + kFan * kMaxRun * SV;   // [32 run][3]
+    double* stage_spin = stage_psi + kFan * mr * SV;        // [32 run][3]
     const int64_t stride = a.n_sims + 1;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t node = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; node < a.nodes[0]; node += warps) {
@@ -547,13 +554,13 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
         // U_{k+1} is loaded while sample k is computed and written
         Op<N, T> u;
         if (k0 < k1) {
-            if (SPINSIM_INB(k0 >= 0 && k0 < s.K && k0 - kn < (int64_t)kFan * kMaxRun, 14)) u.load(U + k0 * D);
+            if (SPINSIM_INB(k0 >= 0 && k0 < s.K && k0 - kn < (int64_t)kFan * mr, 14)) u.load(U + k0 * D);
             else u.identity();
         }
         for (int64_t k = k0; k < k1; k++) {
             Op<N, T> un;
             if (k + 1 < k1) {
-                if (SPINSIM_INB(k + 1 < s.K && k + 1 - kn < (int64_t)kFan * kMaxRun, 14)) un.load(U + (k + 1) * D);
+                if (SPINSIM_INB(k + 1 < s.K && k + 1 - kn < (int64_t)kFan * mr, 14)) un.load(U + (k + 1) * D);
                 else un.identity();
             }
             u.apply(psi, nxt);
@@ -591,7 +598,7 @@ __global__ void __launch_bounds__(128) chain_apply_kernel(ChainArgs a)
         __syncwarp();
         // the node's span [kn, kn + m): psi_k as N double2 words per sample,
         // <J>_k as 3 doubles per sample (kn is a multiple of 4: whole words)
-        const int64_t m = SPINSIM_INB(run <= kMaxRun && kn + min((int64_t)kFan * run, s.K - kn) <= s.K, 15)
+        const int64_t m = SPINSIM_INB(run <= mr && kn + min((int64_t)kFan * run, s.K - kn) <= s.K, 15)
                               ? min((int64_t)kFan * run, s.K - kn) : 0;
         {
             const double2* src = reinterpret_cast<const double2*>(stage_psi);
@@ -619,7 +626,8 @@ static cudaError_t launch_chain_nt(const ChainArgs& a, int n_sm, cudaStream_t st
     const int block = 32 * kChainWarps;
     const size_t up_smem = (size_t)kChainWarps * tree_doubles<N>() * sizeof(double);
     const size_t upper_smem = (size_t)tree_doubles<N>() * sizeof(double);
-    const size_t apply_smem = (size_t)kChainWarps * (state_doubles<N>() + stage_doubles<N>()) * sizeof(double);
+    const size_t apply_smem = (size_t)kChainWarps * (state_doubles<N>() + stage_doubles<N>(apply_run(a))) * sizeof(double);
+    const size_t apply_smem_max = (size_t)kChainWarps * (state_doubles<N>() + stage_doubles<N>(kMaxRun)) * sizeof(double);
     // the apply kernel's staging exceeds the default 48 KB of dynamic shared
     // memory: raise its limit once per device (before any capture: the first
     // launch of a batch shape is always eager)
@@ -628,7 +636,7 @@ static cudaError_t launch_chain_nt(const ChainArgs& a, int n_sm, cudaStream_t st
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
         const cudaError_t e = cudaFuncSetAttribute(chain_apply_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)apply_smem);
+                                                   (int)apply_smem_max);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }

@@ -180,6 +180,8 @@ struct ChainArgs {
     double* left[kMaxLevels];         // [nodes][kLeftPerNode] left-child products of the node's binary tree
     double* state[kMaxLevels];        // [nodes][N] complex state entering the node (written for the
                                       // children of top nodes by the up-sweep)
+    int max_run;                      // the longest lane run of the simulations (chain_run): sizes the
+                                      // apply kernel's output staging (0: the longest possible)
 };
 
 // Doubles per stored operator in the operator buffer and chain scratch.

@@ -65,6 +65,7 @@ struct Group {
     double steps = 0.0;            // CF4 (or sampling) steps of the group
     int min_seg_log2 = kSegLog2;   // smallest canonical segment split among the group's simulations
     int levels = 1;                // chain-tree levels of the tallest simulation
+    int max_run = 0;               // the longest chain lane run among the group's simulations
     int64_t nodes[kMaxLevels] = {};  // chain-tree nodes per level, all simulations
     size_t sims_off = 0, soff_off = 0, loff_off = 0, counter_off = 0, U_off = 0, chain_off = 0;
     size_t phase_off = 0;                   // phasor tables of the drives and further tones (FP64 pairs)
@@ -413,6 +414,7 @@ int build_plan(const spinsim_request* reqs, spinsim_result* res, int64_t n, cons
                 g.min_seg_log2 = std::min(g.min_seg_log2, seg_log2_of(checked[i].L));
                 const ChainGeom cg = chain_geom(checked[i].K);
                 g.levels = std::max(g.levels, cg.top + 1);
+                g.max_run = std::max(g.max_run, cg.run);
                 for (int l = 0; l <= cg.top; l++) g.nodes[l] += cg.nodes[l];
             }
         if (g.idx.empty()) continue;
@@ -761,6 +763,7 @@ int run_batch(spinsim_s* h, const spinsim_request* reqs, spinsim_result* res, co
             ca.level_off = reinterpret_cast<const int64_t*>(base + g.loff_off);
             ca.U = ia.U;
             chain_args_set(ca, g.chain, base + g.chain_off);
+            ca.max_run = g.max_run;
             ca.mode = phase == kPhaseBegin ? kChainUp : (phase == kPhaseFinish ? kChainDown : kChainFull);
             int chain_k = 0;
             if (inject_launch_failure(h) ||

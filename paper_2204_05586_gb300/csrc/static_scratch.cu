@@ -234,6 +234,7 @@ extern "C" int spinsim_simulate_static(const spinsim_config* cfg, const spinsim_
         ca.level_off = reinterpret_cast<const int64_t*>(base + loff_off);
         ca.U = ia.U;
         chain_args_set(ca, cl, base + chain_off);
+        ca.max_run = cg.run;
         int chain_k = 0;
         if (launch_chain(spin, ca, n_sm, stream, &chain_k, cfg->chain_precision == 1) != cudaSuccess)
             return res->status = SPINSIM_E_CUDA;
