@@ -173,6 +173,14 @@ void hh_first_order(const spinsim_config* cfg, const spinsim_request* r, int64_t
     out[1] = gy;
     out[2] = gsum;
 }
+// The chain's lane-run length and top level of a simulation of K samples.
+void hh_chain_geom(int64_t K, int* run, int* top)
+{
+    const ChainGeom g = chain_geom(K);
+    *run = g.run;
+    *top = g.top;
+}
+
 // The epilogue's integer FP32 -> FP64 widening of n bit patterns.
 void hh_widen_bits(const uint32_t* in, uint64_t* out, int64_t n)
 {

@@ -49,6 +49,7 @@ def hh(tmp_path_factory):
                                      ctypes.POINTER(ctypes.c_int)]
     L.hh_first_order.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, DP]
     L.hh_widen_bits.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+    L.hh_chain_geom.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.hh_drive_cycles_frac.restype = ctypes.c_double
     L.hh_drive_cycles_frac.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int64]
     L.hh_phasor.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
@@ -598,3 +599,22 @@ def test_integer_widening_is_the_ieee_conversion(hh):
     assert np.array_equal(got[~nan].view(np.uint64), want.view(np.uint64))
     assert np.isnan(got[nan]).all()
     assert np.array_equal(np.signbit(got[nan]), np.signbit(f[nan]))
+
+
+def test_chain_run_rule(hh):
+    """The chain's lane runs depend on K alone: 4 below 16384 samples, at least
+    6 from there, one more per 19456 samples beyond 6 x 19456, at most 8; the
+    bench's flop model uses the same rule."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    want = {1: 4, 16383: 4, 16384: 6, 100000: 6, 116736: 6, 116737: 7, 136192: 7, 136193: 8, 10**7: 8}
+    run, top = ctypes.c_int(), ctypes.c_int()
+    for K, r in want.items():
+        hh.hh_chain_geom(K, ctypes.byref(run), ctypes.byref(top))
+        assert run.value == r, (K, run.value)
+        assert bench.chain_run(K) == r, K
+    for K in range(1, 300000, 997):
+        hh.hh_chain_geom(K, ctypes.byref(run), ctypes.byref(top))
+        assert bench.chain_run(K) == run.value, K
